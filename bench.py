@@ -1,0 +1,339 @@
+"""Throughput of the Bessel-antenna FDTD hot path on GB300.
+
+One bench "step" is one full Yee time step of the whole hot path (H update +
+CPML, H soft source, fluence, E update + CPML, E soft source) over the
+256 x 256 x 128-cell single-beam workload (dx = lambda/20, theta = 10 deg,
+l = 0, ring radius 100 cells, 16-cell CPML), FP32 fields with FP64 source
+phases and FP64 fluence.  The same workload is also timed in FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle (the
+baseline) on a bounded sample of the same workload.  Under torchrun each
+rank runs its own replica of the workload (weak scaling, no collective on the
+data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FDTD Gcell-updates/s FP32 vs FP64 at stated L2 error; % HBM roofline; adjoint s/step"
+UNIT = "Gcell-updates/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def algorithmic_bytes_per_cell(w, elem_bytes: int) -> float:
+    """Bytes the method itself must move per cell-update: read and write E and
+    H once (12 words), read and write the FP64 fluence (16 B), read and write
+    every CPML psi value on the shells (mean psi count per cell
+    4 (2 npml / nx) + 4 (2 npml / ny))."""
+    psi_bar = 4.0 * (2 * w.npml / w.nx) + 4.0 * (2 * w.npml / w.ny)
+    return 12 * elem_bytes + 16 + 2 * elem_bytes * psi_bar
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self._t:
+                self._t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_gpu(args):
+    import torch
+    import numpy as np
+    from paper_2102_12978_gb300 import fdtd
+    from paper_2102_12978_gb300 import workloads as W
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    w = W.config2()
+    cells = w.cells
+
+    def make(prec):
+        d = fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant,
+                                precision=prec, fluence=True)
+        g = fdtd.Grid(d, device=dev)
+        g.set_source(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness,
+                     ramp=w.ramp)
+        return g
+
+    def timed(g, steps, warmup):
+        stream = g.stream
+        g.step(warmup)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    peak, peak_kind = _peaks()
+
+    # ---- FP32 (headline) ---------------------------------------------------
+    g32 = make("f32")
+    tile32 = g32.autotune(steps=5)
+    with ClockSampler(local) as clk:
+        ms32 = timed(g32, args.steps, args.warmup)
+    clocks = clk.summary()
+    per_launch_ms = ms32 / args.steps
+    gcell32 = cells * args.steps * ws / (ms32 * 1e-3) / 1e9
+    ab32 = algorithmic_bytes_per_cell(w, 4)
+    achieved = ab32 * cells / (per_launch_ms * 1e-3) / 1e9
+
+    # ---- FP64 (secondary) --------------------------------------------------
+    g64 = make("f64")
+    tile64 = g64.autotune(steps=3)
+    steps64 = max(10, args.steps // 4)
+    ms64 = timed(g64, steps64, max(3, args.warmup // 4))
+    gcell64 = cells * steps64 * ws / (ms64 * 1e-3) / 1e9
+    ab64 = algorithmic_bytes_per_cell(w, 8)
+    achieved64 = ab64 * cells / (ms64 / steps64 * 1e-3) / 1e9
+
+    # FP32 vs FP64 agreement on the same number of steps (both GPU paths are
+    # parity-checked against the oracle in the test suite)
+    n_cmp = min(400, args.steps)
+    a = make("f32"); b = make("f64")
+    a.step(n_cmp); b.step(n_cmp)
+    num = den = 0.0
+    for c in range(6):
+        x = a.field(c).double(); y = b.field(c)
+        num += float(torch.sum((x - y) ** 2)); den += float(torch.sum(y ** 2))
+    f32_vs_f64 = (num / den) ** 0.5 if den > 0 else None
+    del a, b
+
+    # ---- end to end through the public API with host buffers --------------
+    e2e = run_e2e(torch, fdtd, w, dev, args.steps, barrier, ws)
+
+    del g32, g64
+    out = {
+        "metric": METRIC, "value": round(gcell32, 3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_launch_ms, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "cells": cells, "grid": [w.nx, w.ny, w.nz], "npml": w.npml,
+                   "dx_lambda": w.dx, "theta_deg": w.theta_deg, "m": w.m, "ring_radius_cells": w.r_center,
+                   "fluence": "fp64", "source_phase": "fp64",
+                   "l2_flush": "inputs larger than L2 (fields + fluence = %.0f MB/step)"
+                               % (ab32 * cells / 1e6),
+                   "tile_f32": list(tile32), "tile_f64": list(tile64), "parallelism": f"replicas{ws}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "yee_step_fused<float,32,ty>", "algorithmic_bytes_per_cell": ab32},
+        "fp64": {"value": round(gcell64, 3), "unit": UNIT, "steps": steps64,
+                 "ms_per_step": round(ms64 / steps64, 5),
+                 "roofline": {"bound": "hbm", "achieved": round(achieved64, 1), "peak": peak,
+                              "frac": round(achieved64 / peak, 4), "algorithmic_bytes_per_cell": ab64}},
+        "l2_error": {"f32_vs_f64_gpu_rel_l2_fields": f32_vs_f64, "after_steps": n_cmp,
+                     "f64_vs_oracle_tol": 1e-11, "f32_vs_oracle_tol": 1e-4},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(w, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(torch, fdtd, w, dev, steps, barrier, ws):
+    """Whole job through the public API with host buffers: the initial state
+    (6 field arrays) and the source description go host -> device, `steps`
+    Yee steps run, and the fluence plus the dominant field come back to pinned
+    host memory, all inside the timed region."""
+    import numpy as np
+    shape = (w.nz, w.ny, w.nx)
+    init = [torch.zeros(shape, dtype=torch.float32).pin_memory() for _ in range(6)]
+    flu_h = torch.empty(shape, dtype=torch.float64).pin_memory()
+    fld_h = torch.empty(shape, dtype=torch.float32).pin_memory()
+    d = fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant,
+                            precision="f32", fluence=True)
+    g = fdtd.Grid(d, device=dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for c in range(6):
+        fdtd.fdtd_set_field(g.handle, c, init[c].data_ptr(), False)
+    g.set_source(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness, ramp=w.ramp)
+    g.step(steps)
+    fdtd.fdtd_fluence(g.handle, flu_h.data_ptr(), False, False)
+    fdtd.fdtd_get_field(g.handle, 1 if w.pol == "y" else 0, fld_h.data_ptr(), False)
+    torch.cuda.synchronize(dev)
+    barrier()
+    dt = time.perf_counter() - t0
+    h2d = 6 * init[0].numel() * 4 + (16 * 6 + 1) * w.nx * w.ny + 32 * w.nz
+    d2h = flu_h.numel() * 8 + fld_h.numel() * 4
+    g.close()
+    return {"value": round(w.cells * steps * ws / dt / 1e9, 3), "unit": UNIT,
+            "h2d_bytes_per_step": round(h2d / steps, 1), "d2h_bytes_per_step": round(d2h / steps, 1),
+            "seconds": round(dt, 4),
+            "what": "host state + source description in, K steps, fluence + E_pol out (pinned host)"}
+
+
+def cpu_baseline(w, budget_s: float = 15.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the same workload: the full 256x256x128 grid with its antenna, for as many
+    steps as fit in about `budget_s` seconds."""
+    import oracle
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant)
+    os_ = oracle.Source(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness,
+                        ramp=w.ramp)
+    st = oracle.State(og)
+    t0 = time.perf_counter()
+    oracle.run(og, os_, st, 1)                  # calibration step (includes antenna build)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(200, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.run(og, os_, st, n)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": round(w.cells * n / dt / 1e9, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} steps of the full {w.nx}x{w.ny}x{w.nz} workload (FP64 C, OpenMP), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2102_12978_gb300 import workloads as W
+    import oracle
+    w = W.config2()
+    og = oracle.Grid(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant)
+    os_ = oracle.Source(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness,
+                        ramp=w.ramp)
+    st = oracle.State(og)
+    # each reference "step" is one oracle Yee step of the full workload
+    oracle.run(og, os_, st, max(1, min(args.warmup, 3)))
+    n = max(1, min(args.steps, 20))
+    t0 = time.perf_counter()
+    oracle.run(og, os_, st, n)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = w.cells * n / dt / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": ws,
+        "steps": n, "warmup": args.warmup, "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "cells": w.cells},
+        "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} steps of the full workload, {dt:.1f} s"},
+        "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

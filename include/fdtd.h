@@ -1,0 +1,211 @@
+/*
+ * fdtd.h -- C ABI of the GB300 Bessel-antenna FDTD library (libfdtd_gb300.so).
+ *
+ * Method (Ardaneh, Giust, Morel, Courvoisier, "Generation of a Bessel beam in
+ * FDTD using a cylindrical antenna", arXiv:2102.12978):
+ *   - standard second-order Yee leapfrog of E and H (Section 4);
+ *   - z periodic (Section 1 and Section 4: the box spans whole axial periods),
+ *     CPML on the transverse x/y faces (Section 4, Roden-Gedney CPML),
+ *     PEC behind the CPML;
+ *   - a hollow cylindrical annulus ("Bessel antenna", Fig. 3) that adds, after
+ *     each curl update, the analytic order-m vector Bessel field of Eq. 12 built
+ *     from the Hertz-potential solutions Eq. 5-9 (soft source, Eq. 13);
+ *   - the time-integrated fluence, integral of |S| dt (Section 2), which per
+ *     window of whole periods gives the intensity of Section 5.
+ *
+ * Units: c = eps0 = mu0 = 1 (eta = 1); lengths in source wavelengths
+ * (lambda = 1), times in optical periods (omega = 2 pi).  The paper's SI
+ * setup has lambda = 0.8 um.
+ *
+ * Conventions for every call:
+ *   - No call aborts or exits; every failure is a status code, and
+ *     fdtd_last_error() gives a one-line reason (thread-local).
+ *   - Device memory is owned by the caller: fdtd_required_bytes() gives the
+ *     size of one device arena that the caller allocates (e.g. a torch uint8
+ *     tensor) and passes to fdtd_create_grid(); the library carves fields,
+ *     CPML auxiliaries, fluence and source tables out of it, and allocates no
+ *     device memory of its own.  The arena must stay alive until
+ *     fdtd_destroy_grid().
+ *   - Work is queued on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  Calls that return data to the host
+ *     synchronise that stream and report asynchronous CUDA errors.
+ *   - Field storage: structure of arrays, one array per component, x fastest,
+ *     rows padded to a pitch of 32 elements; two copies of E, H and the
+ *     H-side CPML auxiliaries are kept (ping-pong), because the fused step
+ *     reads step n from one copy while writing step n+1 into the other.
+ *   - Yee positions (in cells, from the box corner): Ex (i+1/2, j, k),
+ *     Ey (i, j+1/2, k), Ez (i, j, k+1/2), Hx (i, j+1/2, k+1/2),
+ *     Hy (i+1/2, j, k+1/2), Hz (i+1/2, j+1/2, k); E at t = n dt and H at
+ *     (n - 1/2) dt.  The beam axis is at (nx/2, ny/2).  Tangential E on the
+ *     planes i = 0 and j = 0 (and on the virtual walls i = nx, j = ny) is zero.
+ */
+#ifndef FDTD_GB300_H
+#define FDTD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDTD_OK = 0,
+    FDTD_EINVAL = 1,   /* invalid argument or descriptor                     */
+    FDTD_ENOMEM = 2,   /* arena too small / host allocation failed           */
+    FDTD_ECUDA = 3,    /* a CUDA runtime call or kernel failed               */
+    FDTD_ETIMEOUT = 4, /* a bounded device-side wait expired                 */
+    FDTD_ESTATE = 5    /* call not valid in the grid's current state         */
+} fdtd_status;
+
+typedef enum { FDTD_F32 = 0, FDTD_F64 = 1 } fdtd_precision;
+
+/* Field components for get/set calls. */
+enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, FDTD_HZ = 5 };
+
+/* Polarisation of the injected beam: which Hertz potential of Eq. 5 drives it. */
+enum {
+    FDTD_POL_Y = 0,          /* Pi_x (Eq. 6): linear, y-polarised (paper default)  */
+    FDTD_POL_X = 1,          /* Pi_y (Eq. 7): linear, x-polarised                  */
+    FDTD_POL_CIRC_PLUS = 2,  /* (Pi_x + i Pi_y)/sqrt 2                             */
+    FDTD_POL_CIRC_MINUS = 3  /* (Pi_x - i Pi_y)/sqrt 2                             */
+};
+enum { FDTD_TE = 0, FDTD_TM = 1 };                    /* Eq. 9a / Eq. 9b       */
+enum { FDTD_ENV_CW_SIN2 = 0, FDTD_ENV_GAUSS = 1 };     /* CW ramp / Eq. 12 f(t) */
+enum { FDTD_INJECT_ALL = 0, FDTD_INJECT_TANGENTIAL = 1 };
+
+/* Grid descriptor.  Section 4 fixes a cubic mesh and z-periodicity; the CPML
+ * constants are not given by the paper and are exposed here (defaults in
+ * brackets: order 3, sigma scale 0.8, kappa_max 1, alpha_max 0.05 * 2 pi). */
+typedef struct {
+    int nx, ny, nz;          /* cells; nx, ny >= 2*npml + 2, nz >= 1               */
+    int npml;                /* CPML cells on each transverse face (0 = PEC box)   */
+    double dx, dy, dz;       /* cell sizes in wavelengths                          */
+    double dt;               /* time step in periods; 0 => courant * Yee limit     */
+    double courant;          /* used when dt == 0, must be in (0, 1]               */
+    double pml_order;        /* sigma = sigma_max u^order                          */
+    double pml_sigma_scale;  /* sigma_max = scale (order+1) / (eta d)              */
+    double pml_kappa_max;    /* kappa = 1 + (kappa_max - 1) u^order                */
+    double pml_alpha_max;    /* alpha = alpha_max (1 - u)                          */
+    int precision;           /* fdtd_precision of the field arithmetic             */
+    int fluence;             /* 1: accumulate the fluence (FP64 accumulator)       */
+} fdtd_grid_desc;
+
+/* Bessel-antenna descriptor (Section 4, Fig. 3, Eq. 12-13).  The antenna is
+ * every Yee point of each component whose distance r from the beam axis, in
+ * cells, satisfies r_center - thickness/2 <= r < r_center + thickness/2,
+ * along the whole z length.  The value added after the curl update at such a
+ * point p of component c, at that component's own time t, is
+ *     f(t) * Re{ w_amp[col] e^{i w_phase[col]} A_c(p) e^{-i omega t'} }
+ * with A the complex E (or H) amplitude of the TE/TM order-m beam (Eq. 6-9,
+ * e^{+i beta z} carried in A), t' = t (CW) or t - T0 (Gaussian), and col the
+ * point's column j*nx + i.  Both weight arrays are host arrays of nx*ny
+ * doubles, copied by the call; NULL means amplitude 1 / phase 0. */
+typedef struct {
+    int m;                   /* Bessel order                                       */
+    double theta;            /* cone angle, radians (K = k sin, beta = k cos)      */
+    int pol;                 /* FDTD_POL_*                                         */
+    int mode;                /* FDTD_TE / FDTD_TM                                  */
+    double E0;               /* field amplitude of Eq. 9                           */
+    double r_center;         /* ring centre radius, cells of dx                    */
+    double thickness;        /* ring thickness, cells of dx                        */
+    int envelope;            /* FDTD_ENV_*                                         */
+    double ramp;             /* CW: f = sin^2(pi t / (2 ramp)) for t < ramp, else 1 */
+    double T, T0;            /* Gaussian: f = exp(-(t-T0)^2 / T^2)                 */
+    int inject;              /* FDTD_INJECT_ALL (Eq. 13) or _TANGENTIAL (drop the
+                                radial x/y projection at each point)               */
+    const double* w_amp;     /* host, nx*ny, or NULL                               */
+    const double* w_phase;   /* host, nx*ny, or NULL                               */
+} fdtd_annulus_desc;
+
+typedef struct fdtd_grid fdtd_grid;
+typedef struct fdtd_batch fdtd_batch;
+
+/* Fill *d with the defaults (courant 0.95, CPML constants above, F32, fluence on). */
+void fdtd_grid_desc_default(fdtd_grid_desc* d);
+
+/* Bytes of device arena a grid with this descriptor needs (0 if invalid). */
+size_t fdtd_required_bytes(const fdtd_grid_desc* d);
+
+/* Create a grid on the current CUDA device.  `arena` is a device pointer to
+ * at least fdtd_required_bytes(d) bytes, 256-byte aligned, owned by the caller;
+ * `stream` is a cudaStream_t (or NULL).  Zeroes the fields, CPML auxiliaries
+ * and fluence, uploads the CPML profiles (Section 4), and sets the step
+ * counter to 0.  Returns EINVAL on a bad descriptor (Courant > 1, CPML wider
+ * than a quarter of the box, ...), ENOMEM if arena_bytes is too small. */
+fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_bytes,
+                             void* stream, fdtd_grid** out);
+
+/* Build the antenna (Fig. 3) and its FP64 coefficients A_c (Eq. 6-9, Eq. 12)
+ * on the host and upload them into the arena.  Replaces any earlier source.
+ * EINVAL if the ring reaches into the CPML or outside the box. */
+fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s);
+
+/* Remove the source (source-free runs). */
+fdtd_status fdtd_clear_source(fdtd_grid* g);
+
+/* Advance nsteps full Yee steps (asynchronous on the grid's stream).  Each
+ * step n: H^{n+1/2} (with CPML psi) -> H soft source at (n+1/2) dt ->
+ * fluence += |E^n x (H^{n-1/2}+H^{n+1/2})/2| dt at cell centres ->
+ * E^{n+1} (with CPML psi) -> E soft source at (n+1) dt (Eq. 13).  One fused
+ * kernel launch per step. */
+fdtd_status fdtd_step(fdtd_grid* g, int nsteps);
+
+/* Copy the fluence (nz*ny*nx doubles, x fastest, dense) to dst (device if
+ * on_device, else host), then zero the accumulator if reset.  Synchronises
+ * the stream.  Cell (i,j,k) is centred at (i+1/2, j+1/2, k+1/2). */
+fdtd_status fdtd_fluence(fdtd_grid* g, void* dst, int on_device, int reset);
+
+/* Copy one field component (FDTD_EX..FDTD_HZ) as a dense nz*ny*nx array of the
+ * grid's precision (float or double) to / from dst (device if on_device).
+ * fdtd_get_field synchronises the stream. */
+fdtd_status fdtd_get_field(fdtd_grid* g, int component, void* dst, int on_device);
+fdtd_status fdtd_set_field(fdtd_grid* g, int component, const void* src, int on_device);
+
+/* Full state (fields, CPML auxiliaries, fluence, step counter): its size in
+ * bytes, and device-to-device save / load (dst/src are device pointers of at
+ * least fdtd_state_bytes bytes).  Used for checkpoints and resume. */
+size_t fdtd_state_bytes(const fdtd_grid* g);
+fdtd_status fdtd_save_state(fdtd_grid* g, void* dev_dst);
+fdtd_status fdtd_load_state(fdtd_grid* g, const void* dev_src);
+
+/* Step counter, time step and antenna point count of component c. */
+int64_t fdtd_get_step(const fdtd_grid* g);
+fdtd_status fdtd_set_step(fdtd_grid* g, int64_t n);
+double fdtd_get_dt(const fdtd_grid* g);
+int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
+
+/* Tile configuration of the fused step kernel: a CTA of 32 x ty threads
+ * (ty in {4, 8, 16}) owns a 32 x ty tile of columns and marches lz planes of
+ * z.  fdtd_create_grid picks a default; fdtd_autotune times the candidates
+ * on this grid (running `steps` steps for each, then restoring the state)
+ * and keeps the fastest.  Results are identical for every configuration. */
+fdtd_status fdtd_set_tile(fdtd_grid* g, int ty, int lz);
+fdtd_status fdtd_get_tile(const fdtd_grid* g, int* ty, int* lz);
+fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state);
+
+/* Synchronise the grid's stream and report any pending CUDA error. */
+fdtd_status fdtd_sync(fdtd_grid* g);
+
+void fdtd_destroy_grid(fdtd_grid* g);
+
+/* Host-only: the per-column source coefficients A_c (see fdtd_annulus_desc)
+ * without weights, evaluated at z = 0 and at z = dz/2 as appropriate for the
+ * component, into out[6][ny][nx] complex doubles (re, im interleaved:
+ * 12*nx*ny doubles), plus the antenna mask out_mask[ny][nx] (bit c set when
+ * column (i,j) holds a point of component c).  Runs no GPU code; exposed so
+ * that the FP64 precompute can be checked on a host without a GPU. */
+fdtd_status fdtd_source_coefficients(const fdtd_grid_desc* d, const fdtd_annulus_desc* s,
+                                     double* out, uint8_t* out_mask);
+
+/* Host-only: the Bessel function J_n(x) the precompute uses (Miller backward
+ * recurrence with the Neumann-series normalisation). */
+double fdtd_bessel_j(int n, double x);
+
+const char* fdtd_status_string(fdtd_status s);
+const char* fdtd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FDTD_GB300_H */

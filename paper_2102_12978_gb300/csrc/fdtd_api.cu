@@ -1,0 +1,622 @@
+// fdtd_api.cu -- host side of the C ABI declared in include/fdtd.h: grid
+// descriptors, arena layout, FP64 precompute of the CPML profiles (Section 4,
+// Roden-Gedney CPML) and of the antenna tables (Eq. 6-9, 12, 13), kernel
+// dispatch, state save/load and error reporting.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "engine.h"
+#include "grid_impl.h"
+#include "yee_fused.cuh"
+
+namespace fdtd {
+
+thread_local char g_last_error[512] = "";
+
+fdtd_status fail(fdtd_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+fdtd_status cuda_check(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return FDTD_OK;
+    return fail(FDTD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Arena layout: the dynamic state (fields, CPML psi, fluence) first, then the
+// static tables.  Every block starts on a 256-byte boundary.
+bool compute_layout(const fdtd_grid_desc& d, Layout& L)
+{
+    const size_t b = d.precision == FDTD_F64 ? 8 : 4;
+    L.elem = b;
+    L.pitch = static_cast<int>(align_up(static_cast<size_t>(d.nx), 32));
+    const size_t nz = d.nz, ny = d.ny, nx = d.nx, p = L.pitch, w2 = 2 * size_t(d.npml);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    L.field_elems = nz * ny * p;
+    for (int buf = 0; buf < 2; ++buf)
+        for (int c = 0; c < 6; ++c) L.field[buf][c] = take(L.field_elems * b);
+    L.psx_elems = nz * ny * w2;
+    L.psy_elems = nz * w2 * p;
+    for (int buf = 0; buf < 2; ++buf)
+        for (int c = 0; c < 2; ++c) {
+            L.phx[buf][c] = take(L.psx_elems * b);
+            L.phy[buf][c] = take(L.psy_elems * b);
+        }
+    for (int c = 0; c < 2; ++c) {
+        L.pex[c] = take(L.psx_elems * b);
+        L.pey[c] = take(L.psy_elems * b);
+    }
+    L.fluence = d.fluence ? take(nz * ny * p * 8) : 0;
+    L.dynamic_bytes = off;
+    L.chx = take(nx * b); L.cex = take(nx * b);
+    L.chy = take(ny * b); L.cey = take(ny * b);
+    for (int q = 0; q < 8; ++q) L.prof[q] = take((w2 ? w2 : 1) * b);
+    L.smask = take(nx * ny);
+    L.scoef = take(6 * nx * ny * 16);
+    L.zph = take(2 * nz * 16);
+    L.total = off;
+    return true;
+}
+
+fdtd_status validate(const fdtd_grid_desc* d)
+{
+    if (!d) return fail(FDTD_EINVAL, "null grid descriptor");
+    if (d->nx < 2 || d->ny < 2 || d->nz < 1)
+        return fail(FDTD_EINVAL, "grid %dx%dx%d too small", d->nx, d->ny, d->nz);
+    if (d->npml < 0 || (d->npml > 0 && (4 * d->npml > d->nx || 4 * d->npml > d->ny)))
+        return fail(FDTD_EINVAL, "npml=%d must be >= 0 and at most a quarter of nx, ny", d->npml);
+    if (!(d->dx > 0) || !(d->dy > 0) || !(d->dz > 0))
+        return fail(FDTD_EINVAL, "cell sizes must be positive");
+    if (d->precision != FDTD_F32 && d->precision != FDTD_F64)
+        return fail(FDTD_EINVAL, "unknown precision %d", d->precision);
+    double lim = 1.0 / std::sqrt(1.0 / (d->dx * d->dx) + 1.0 / (d->dy * d->dy) + 1.0 / (d->dz * d->dz));
+    if (d->dt == 0.0) {
+        if (!(d->courant > 0.0) || d->courant > 1.0)
+            return fail(FDTD_EINVAL, "courant=%g must be in (0, 1]", d->courant);
+    } else if (!(d->dt > 0.0) || d->dt > lim) {
+        return fail(FDTD_EINVAL, "dt=%g outside (0, %g] (Yee stability limit)", d->dt, lim);
+    }
+    if (d->npml > 0 && !(d->pml_order >= 0.0 && d->pml_sigma_scale >= 0.0 && d->pml_kappa_max >= 1.0 &&
+                         d->pml_alpha_max >= 0.0))
+        return fail(FDTD_EINVAL, "invalid CPML constants");
+    return FDTD_OK;
+}
+
+double grid_dt(const fdtd_grid_desc& d)
+{
+    if (d.dt != 0.0) return d.dt;
+    return d.courant / std::sqrt(1.0 / (d.dx * d.dx) + 1.0 / (d.dy * d.dy) + 1.0 / (d.dz * d.dz));
+}
+
+// CPML grading along one axis (Roden-Gedney CFS-PML; constants documented in
+// fdtd_grid_desc).  For a position `pos` (cells from the low face) returns
+// b, a and kappa of the auxiliary recursion psi <- b psi + a d(field)/d(axis).
+static void cpml_at(const fdtd_grid_desc& d, int n, double cell, double dt, double pos_cells,
+                    double& b, double& a, double& kappa)
+{
+    b = 1.0; a = 0.0; kappa = 1.0;
+    if (d.npml <= 0) return;
+    double depth_cells = 0.0;
+    if (pos_cells < d.npml) depth_cells = d.npml - pos_cells;
+    else if (pos_cells > n - d.npml) depth_cells = pos_cells - (n - d.npml);
+    if (depth_cells <= 0.0) return;
+    double u = depth_cells / d.npml;
+    double grade = std::pow(u, d.pml_order);
+    double sigma = d.pml_sigma_scale * (d.pml_order + 1.0) / cell * grade;
+    kappa = 1.0 + (d.pml_kappa_max - 1.0) * grade;
+    double alpha = d.pml_alpha_max * (1.0 - u);
+    b = std::exp(-(sigma / kappa + alpha) * dt);
+    if (sigma > 0.0) a = sigma * (b - 1.0) / (kappa * (sigma + kappa * alpha));
+}
+
+template <typename real>
+static void build_axis_tables(const fdtd_grid_desc& d, int n, double cell, double dt,
+                              std::vector<real>& ch, std::vector<real>& ce,
+                              std::vector<real>& bh, std::vector<real>& ah,
+                              std::vector<real>& be, std::vector<real>& ae)
+{
+    const int w2 = 2 * d.npml;
+    ch.assign(n, real(0)); ce.assign(n, real(0));
+    bh.assign(w2 ? w2 : 1, real(1)); ah.assign(w2 ? w2 : 1, real(0));
+    be.assign(w2 ? w2 : 1, real(1)); ae.assign(w2 ? w2 : 1, real(0));
+    for (int i = 0; i < n; ++i) {
+        double b, a, kap;
+        cpml_at(d, n, cell, dt, i + 0.5, b, a, kap);      // H sits half a cell in
+        ch[i] = real(dt / (kap * cell));
+        int sh = (i < d.npml) ? i : (i >= n - d.npml ? i - n + w2 : -1);
+        if (sh >= 0) { bh[sh] = real(b); ah[sh] = real(dt * a / cell); }
+        cpml_at(d, n, cell, dt, double(i), b, a, kap);    // E on the integer position
+        ce[i] = real(dt / (kap * cell));
+        if (sh >= 0) { be[sh] = real(b); ae[sh] = real(dt * a / cell); }
+    }
+}
+
+template <typename real>
+static fdtd_status upload_tables(fdtd_grid* g)
+{
+    std::vector<real> chx, cex, bhx, ahx, bex, aex, chy, cey, bhy, ahy, bey, aey;
+    build_axis_tables<real>(g->desc, g->desc.nx, g->desc.dx, g->dt, chx, cex, bhx, ahx, bex, aex);
+    build_axis_tables<real>(g->desc, g->desc.ny, g->desc.dy, g->dt, chy, cey, bhy, ahy, bey, aey);
+    char* A = static_cast<char*>(g->arena);
+    cudaStream_t s = g->stream;
+    const Layout& L = g->L;
+    struct { size_t off; const std::vector<real>* v; } items[] = {
+        {L.chx, &chx}, {L.cex, &cex}, {L.chy, &chy}, {L.cey, &cey},
+        {L.prof[0], &bhx}, {L.prof[1], &ahx}, {L.prof[2], &bex}, {L.prof[3], &aex},
+        {L.prof[4], &bhy}, {L.prof[5], &ahy}, {L.prof[6], &bey}, {L.prof[7], &aey},
+    };
+    for (auto& it : items) {
+        fdtd_status st = cuda_check(cudaMemcpyAsync(A + it.off, it.v->data(), it.v->size() * sizeof(real),
+                                                    cudaMemcpyHostToDevice, s), "upload CPML tables");
+        if (st != FDTD_OK) return st;
+    }
+    return cuda_check(cudaStreamSynchronize(s), "upload CPML tables");
+}
+
+template <typename real>
+StepArgs<real> make_args(const fdtd_grid* g, int cur)
+{
+    StepArgs<real> a;
+    const Layout& L = g->L;
+    char* A = static_cast<char*>(g->arena);
+    const int nxt = cur ^ 1;
+    a.nx = g->desc.nx; a.ny = g->desc.ny; a.nz = g->desc.nz; a.npml = g->desc.npml; a.pitch = L.pitch;
+    for (int c = 0; c < 3; ++c) {
+        a.ein[c] = reinterpret_cast<const real*>(A + L.field[cur][c]);
+        a.eout[c] = reinterpret_cast<real*>(A + L.field[nxt][c]);
+        a.hin[c] = reinterpret_cast<const real*>(A + L.field[cur][3 + c]);
+        a.hout[c] = reinterpret_cast<real*>(A + L.field[nxt][3 + c]);
+    }
+    for (int c = 0; c < 2; ++c) {
+        a.phx_in[c] = reinterpret_cast<const real*>(A + L.phx[cur][c]);
+        a.phx_out[c] = reinterpret_cast<real*>(A + L.phx[nxt][c]);
+        a.phy_in[c] = reinterpret_cast<const real*>(A + L.phy[cur][c]);
+        a.phy_out[c] = reinterpret_cast<real*>(A + L.phy[nxt][c]);
+        a.pex[c] = reinterpret_cast<real*>(A + L.pex[c]);
+        a.pey[c] = reinterpret_cast<real*>(A + L.pey[c]);
+    }
+    a.chx = reinterpret_cast<const real*>(A + L.chx);
+    a.cex = reinterpret_cast<const real*>(A + L.cex);
+    a.chy = reinterpret_cast<const real*>(A + L.chy);
+    a.cey = reinterpret_cast<const real*>(A + L.cey);
+    a.bhx = reinterpret_cast<const real*>(A + L.prof[0]);
+    a.ahx = reinterpret_cast<const real*>(A + L.prof[1]);
+    a.bex = reinterpret_cast<const real*>(A + L.prof[2]);
+    a.aex = reinterpret_cast<const real*>(A + L.prof[3]);
+    a.bhy = reinterpret_cast<const real*>(A + L.prof[4]);
+    a.ahy = reinterpret_cast<const real*>(A + L.prof[5]);
+    a.bey = reinterpret_cast<const real*>(A + L.prof[6]);
+    a.aey = reinterpret_cast<const real*>(A + L.prof[7]);
+    a.cz = real(g->dt / g->desc.dz);
+    a.dt = g->dt;
+    a.fluence = g->desc.fluence ? reinterpret_cast<double*>(A + L.fluence) : nullptr;
+    a.smask = g->has_source ? reinterpret_cast<const uint8_t*>(A + L.smask) : nullptr;
+    a.scoef = reinterpret_cast<const double2*>(A + L.scoef);
+    a.zph = reinterpret_cast<const double2*>(A + L.zph);
+    a.st = g->srct;
+    return a;
+}
+
+template StepArgs<float> make_args<float>(const fdtd_grid*, int);
+template StepArgs<double> make_args<double>(const fdtd_grid*, int);
+
+// ---- kernel dispatch over (precision, tile)
+template <typename real, int TX, int TY>
+static cudaError_t launch_fused(const fdtd_grid* g, int cur, long long n, int lz, cudaStream_t s)
+{
+    using T = FusedTile<real, TX, TY>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(yee_step_fused<real, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(T::smem_bytes()));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 block(TX, TY);
+    dim3 grid((g->desc.nx + TX - 1) / TX, (g->desc.ny + TY - 1) / TY, (g->desc.nz + lz - 1) / lz);
+    yee_step_fused<real, TX, TY><<<grid, block, T::smem_bytes(), s>>>(make_args<real>(g, cur), n, lz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s)
+{
+    if (g->desc.precision == FDTD_F32) {
+        switch (tc.ty) {
+            case 4: return launch_fused<float, 32, 4>(g, cur, n, tc.lz, s);
+            case 16: return launch_fused<float, 32, 16>(g, cur, n, tc.lz, s);
+            default: return launch_fused<float, 32, 8>(g, cur, n, tc.lz, s);
+        }
+    } else {
+        switch (tc.ty) {
+            case 4: return launch_fused<double, 32, 4>(g, cur, n, tc.lz, s);
+            case 16: return launch_fused<double, 32, 16>(g, cur, n, tc.lz, s);
+            default: return launch_fused<double, 32, 8>(g, cur, n, tc.lz, s);
+        }
+    }
+}
+
+// Default tile: 32 x 8 columns, z split into segments so that about four
+// CTAs per SM are in flight (152 SMs on GB300).
+TileConfig default_tile(const fdtd_grid_desc& d, int sm_count)
+{
+    TileConfig tc;
+    tc.tx = 32; tc.ty = 8;
+    long tiles = long((d.nx + 31) / 32) * long((d.ny + 7) / 8);
+    long want = 4L * (sm_count > 0 ? sm_count : 152);
+    long segs = (want + tiles - 1) / tiles;
+    if (segs < 1) segs = 1;
+    long max_segs = d.nz / 8 > 0 ? d.nz / 8 : 1;
+    if (segs > max_segs) segs = max_segs;
+    tc.lz = int((d.nz + segs - 1) / segs);
+    return tc;
+}
+
+}  // namespace fdtd
+
+using namespace fdtd;
+
+extern "C" {
+
+void fdtd_grid_desc_default(fdtd_grid_desc* d)
+{
+    if (!d) return;
+    std::memset(d, 0, sizeof(*d));
+    d->courant = 0.95;
+    d->pml_order = 3.0;
+    d->pml_sigma_scale = 0.8;
+    d->pml_kappa_max = 1.0;
+    d->pml_alpha_max = 0.05 * 2.0 * M_PI;
+    d->precision = FDTD_F32;
+    d->fluence = 1;
+}
+
+size_t fdtd_required_bytes(const fdtd_grid_desc* d)
+{
+    if (validate(d) != FDTD_OK) return 0;
+    Layout L;
+    compute_layout(*d, L);
+    return L.total;
+}
+
+fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_bytes, void* stream,
+                             fdtd_grid** out)
+{
+    if (!out) return fail(FDTD_EINVAL, "null output pointer");
+    *out = nullptr;
+    fdtd_status st = validate(d);
+    if (st != FDTD_OK) return st;
+    if (!arena) return fail(FDTD_EINVAL, "null arena");
+    if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return fail(FDTD_EINVAL, "arena not 256-byte aligned");
+    Layout L;
+    compute_layout(*d, L);
+    if (arena_bytes < L.total)
+        return fail(FDTD_ENOMEM, "arena of %zu bytes, %zu needed", arena_bytes, L.total);
+    fdtd_grid* g = new (std::nothrow) fdtd_grid();
+    if (!g) return fail(FDTD_ENOMEM, "host allocation failed");
+    g->desc = *d;
+    g->L = L;
+    g->arena = arena;
+    g->arena_bytes = arena_bytes;
+    g->stream = static_cast<cudaStream_t>(stream);
+    g->dt = grid_dt(*d);
+    g->step = 0;
+    g->cur = 0;
+    g->has_source = false;
+    std::memset(&g->srct, 0, sizeof(g->srct));
+    g->srct.dt = g->dt;
+    for (int c = 0; c < 6; ++c) g->counts[c] = 0;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g->sm_count = sms;
+    g->tile = default_tile(*d, sms);
+    st = cuda_check(cudaMemsetAsync(arena, 0, L.total, g->stream), "zero arena");
+    if (st == FDTD_OK)
+        st = (d->precision == FDTD_F64) ? upload_tables<double>(g) : upload_tables<float>(g);
+    if (st != FDTD_OK) { delete g; return st; }
+    *out = g;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
+{
+    if (!g || !s) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_grid_desc& d = g->desc;
+    if (s->pol < 0 || s->pol > 3 || (s->mode != FDTD_TE && s->mode != FDTD_TM) ||
+        (s->envelope != FDTD_ENV_CW_SIN2 && s->envelope != FDTD_ENV_GAUSS) ||
+        (s->inject != FDTD_INJECT_ALL && s->inject != FDTD_INJECT_TANGENTIAL))
+        return fail(FDTD_EINVAL, "invalid enum in annulus descriptor");
+    if (!(s->thickness > 0.0) || !(s->r_center > 0.5 * s->thickness))
+        return fail(FDTD_EINVAL, "ring thickness %g / radius %g invalid", s->thickness, s->r_center);
+    double rout = s->r_center + 0.5 * s->thickness;
+    double room = std::min(0.5 * d.nx, 0.5 * d.ny) - d.npml - 1.0;
+    if (rout > room)
+        return fail(FDTD_EINVAL, "ring outer radius %g cells reaches the CPML (limit %g)", rout, room);
+    if (s->envelope == FDTD_ENV_GAUSS && !(s->T > 0.0)) return fail(FDTD_EINVAL, "Gaussian T must be > 0");
+    if (s->envelope == FDTD_ENV_CW_SIN2 && s->ramp < 0.0) return fail(FDTD_EINVAL, "ramp must be >= 0");
+    GridSpec gs{d.nx, d.ny, d.nz, d.npml, d.dx, d.dy, d.dz, g->dt};
+    SourceSpec ss{s->m, s->theta, s->pol, s->mode, s->E0, s->r_center, s->thickness, s->inject};
+    std::vector<std::complex<double>> coef;
+    std::vector<uint8_t> mask;
+    int64_t counts[6];
+    source_tables(gs, ss, s->w_amp, s->w_phase, coef, mask, counts);
+    // e^{i beta z} on the integer and the half planes
+    const double beta = 2.0 * M_PI * std::cos(s->theta);
+    std::vector<std::complex<double>> zph(2 * size_t(d.nz));
+    for (int k = 0; k < d.nz; ++k) {
+        zph[k] = std::polar(1.0, beta * (k * d.dz));
+        zph[d.nz + k] = std::polar(1.0, beta * ((k + 0.5) * d.dz));
+    }
+    char* A = static_cast<char*>(g->arena);
+    fdtd_status st = cuda_check(cudaMemcpyAsync(A + g->L.scoef, coef.data(), coef.size() * 16,
+                                                cudaMemcpyHostToDevice, g->stream), "upload source");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.smask, mask.data(), mask.size(), cudaMemcpyHostToDevice,
+                                        g->stream), "upload source");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.zph, zph.data(), zph.size() * 16, cudaMemcpyHostToDevice,
+                                        g->stream), "upload source");
+    if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(g->stream), "upload source");
+    if (st != FDTD_OK) return st;
+    g->has_source = true;
+    g->src = *s;
+    g->src.w_amp = nullptr;
+    g->src.w_phase = nullptr;
+    g->srct.gauss = s->envelope == FDTD_ENV_GAUSS;
+    g->srct.ramp = s->ramp;
+    g->srct.T = s->T;
+    g->srct.T0 = s->T0;
+    g->srct.dt = g->dt;
+    for (int c = 0; c < 6; ++c) g->counts[c] = counts[c];
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_clear_source(fdtd_grid* g)
+{
+    if (!g) return fail(FDTD_EINVAL, "null grid");
+    g->has_source = false;
+    for (int c = 0; c < 6; ++c) g->counts[c] = 0;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
+{
+    if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (nsteps < 0) return fail(FDTD_EINVAL, "nsteps < 0");
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = launch_step(g, g->cur, g->step, g->tile, g->stream);
+        if (e != cudaSuccess) return cuda_check(e, "yee_step_fused launch");
+        g->cur ^= 1;
+        g->step += 1;
+    }
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_sync(fdtd_grid* g)
+{
+    if (!g) return fail(FDTD_EINVAL, "null grid");
+    fdtd_status st = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
+    if (st != FDTD_OK) return st;
+    return cuda_check(cudaGetLastError(), "pending CUDA error");
+}
+
+fdtd_status fdtd_fluence(fdtd_grid* g, void* dst, int on_device, int reset)
+{
+    if (!g || !dst) return fail(FDTD_EINVAL, "null argument");
+    if (!g->desc.fluence) return fail(FDTD_ESTATE, "grid created without a fluence accumulator");
+    const fdtd_grid_desc& d = g->desc;
+    char* A = static_cast<char*>(g->arena);
+    fdtd_status st = cuda_check(
+        cudaMemcpy2DAsync(dst, size_t(d.nx) * 8, A + g->L.fluence, size_t(g->L.pitch) * 8, size_t(d.nx) * 8,
+                          size_t(d.ny) * d.nz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          g->stream),
+        "copy fluence");
+    if (st == FDTD_OK && reset)
+        st = cuda_check(cudaMemsetAsync(A + g->L.fluence, 0, g->L.field_elems * 8, g->stream), "reset fluence");
+    if (st != FDTD_OK) return st;
+    return fdtd_sync(g);
+}
+
+fdtd_status fdtd_get_field(fdtd_grid* g, int component, void* dst, int on_device)
+{
+    if (!g || !dst) return fail(FDTD_EINVAL, "null argument");
+    if (component < 0 || component > 5) return fail(FDTD_EINVAL, "component %d out of range", component);
+    const fdtd_grid_desc& d = g->desc;
+    const size_t b = g->L.elem;
+    char* A = static_cast<char*>(g->arena);
+    fdtd_status st = cuda_check(
+        cudaMemcpy2DAsync(dst, size_t(d.nx) * b, A + g->L.field[g->cur][component], size_t(g->L.pitch) * b,
+                          size_t(d.nx) * b, size_t(d.ny) * d.nz,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream),
+        "copy field");
+    if (st != FDTD_OK) return st;
+    return fdtd_sync(g);
+}
+
+fdtd_status fdtd_set_field(fdtd_grid* g, int component, const void* src, int on_device)
+{
+    if (!g || !src) return fail(FDTD_EINVAL, "null argument");
+    if (component < 0 || component > 5) return fail(FDTD_EINVAL, "component %d out of range", component);
+    const fdtd_grid_desc& d = g->desc;
+    const size_t b = g->L.elem;
+    char* A = static_cast<char*>(g->arena);
+    fdtd_status st = cuda_check(
+        cudaMemcpy2DAsync(A + g->L.field[g->cur][component], size_t(g->L.pitch) * b, src, size_t(d.nx) * b,
+                          size_t(d.nx) * b, size_t(d.ny) * d.nz,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream),
+        "set field");
+    if (st != FDTD_OK) return st;
+    return fdtd_sync(g);
+}
+
+size_t fdtd_state_bytes(const fdtd_grid* g)
+{
+    if (!g) return 0;
+    return g->L.dynamic_bytes + 256;
+}
+
+fdtd_status fdtd_save_state(fdtd_grid* g, void* dev_dst)
+{
+    if (!g || !dev_dst) return fail(FDTD_EINVAL, "null argument");
+    int64_t hdr[4] = {g->step, g->cur, 0x46445444, 0};
+    char* D = static_cast<char*>(dev_dst);
+    fdtd_status st = cuda_check(cudaMemcpyAsync(D, g->arena, g->L.dynamic_bytes, cudaMemcpyDeviceToDevice,
+                                                g->stream), "save state");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(D + g->L.dynamic_bytes, hdr, sizeof(hdr), cudaMemcpyHostToDevice,
+                                        g->stream), "save state");
+    if (st != FDTD_OK) return st;
+    return fdtd_sync(g);
+}
+
+fdtd_status fdtd_load_state(fdtd_grid* g, const void* dev_src)
+{
+    if (!g || !dev_src) return fail(FDTD_EINVAL, "null argument");
+    int64_t hdr[4];
+    const char* S = static_cast<const char*>(dev_src);
+    fdtd_status st = cuda_check(cudaMemcpyAsync(hdr, S + g->L.dynamic_bytes, sizeof(hdr), cudaMemcpyDeviceToHost,
+                                                g->stream), "load state");
+    if (st == FDTD_OK) st = fdtd_sync(g);
+    if (st != FDTD_OK) return st;
+    if (hdr[2] != 0x46445444 || (hdr[1] != 0 && hdr[1] != 1))
+        return fail(FDTD_EINVAL, "state blob does not come from fdtd_save_state");
+    st = cuda_check(cudaMemcpyAsync(g->arena, S, g->L.dynamic_bytes, cudaMemcpyDeviceToDevice, g->stream),
+                    "load state");
+    if (st != FDTD_OK) return st;
+    g->step = hdr[0];
+    g->cur = int(hdr[1]);
+    return fdtd_sync(g);
+}
+
+int64_t fdtd_get_step(const fdtd_grid* g) { return g ? g->step : -1; }
+
+fdtd_status fdtd_set_step(fdtd_grid* g, int64_t n)
+{
+    if (!g || n < 0) return fail(FDTD_EINVAL, "invalid argument");
+    g->step = n;
+    return FDTD_OK;
+}
+
+double fdtd_get_dt(const fdtd_grid* g) { return g ? g->dt : 0.0; }
+
+int64_t fdtd_antenna_points(const fdtd_grid* g, int component)
+{
+    if (!g || component < 0 || component > 5) return -1;
+    return g->counts[component];
+}
+
+void fdtd_destroy_grid(fdtd_grid* g) { delete g; }
+
+fdtd_status fdtd_set_tile(fdtd_grid* g, int ty, int lz)
+{
+    if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (ty != 4 && ty != 8 && ty != 16) return fail(FDTD_EINVAL, "ty=%d not in {4, 8, 16}", ty);
+    if (lz < 1) return fail(FDTD_EINVAL, "lz=%d < 1", lz);
+    g->tile.tx = 32;
+    g->tile.ty = ty;
+    g->tile.lz = lz > g->desc.nz ? g->desc.nz : lz;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_get_tile(const fdtd_grid* g, int* ty, int* lz)
+{
+    if (!g || !ty || !lz) return fail(FDTD_EINVAL, "null argument");
+    *ty = g->tile.ty;
+    *lz = g->tile.lz;
+    return FDTD_OK;
+}
+
+// Time every (ty, lz) candidate on this grid with CUDA events and keep the
+// fastest.  The state is saved to `scratch_state` (fdtd_state_bytes bytes of
+// device memory owned by the caller) first and restored afterwards.
+fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
+{
+    if (!g || !scratch_state || steps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    fdtd_status st = fdtd_save_state(g, scratch_state);
+    if (st != FDTD_OK) return st;
+    const int tys[3] = {4, 8, 16};
+    const int nz = g->desc.nz;
+    std::vector<int> lzs;
+    for (int segs : {1, 2, 3, 4, 6, 8, 12, 16}) {
+        int lz = (nz + segs - 1) / segs;
+        if (lz >= 4 || segs == 1) {
+            bool dup = false;
+            for (int v : lzs) dup |= (v == lz);
+            if (!dup) lzs.push_back(lz);
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(FDTD_ECUDA, "event create failed");
+    float best = 1e30f;
+    TileConfig best_tc = g->tile;
+    for (int ty : tys)
+        for (int lz : lzs) {
+            TileConfig tc; tc.tx = 32; tc.ty = ty; tc.lz = lz;
+            cudaError_t e = launch_step(g, g->cur, g->step, tc, g->stream);   // warm-up
+            if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_check(e, "autotune"); }
+            cudaEventRecord(e0, g->stream);
+            for (int s = 0; s < steps; ++s) launch_step(g, (g->cur + 1 + s) & 1, g->step + 1 + s, tc, g->stream);
+            cudaEventRecord(e1, g->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_tc = tc; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->tile = best_tc;
+    return fdtd_load_state(g, scratch_state);
+}
+
+fdtd_status fdtd_source_coefficients(const fdtd_grid_desc* d, const fdtd_annulus_desc* s, double* out,
+                                     uint8_t* out_mask)
+{
+    fdtd_status st = validate(d);
+    if (st != FDTD_OK) return st;
+    if (!s || !out || !out_mask) return fail(FDTD_EINVAL, "null argument");
+    GridSpec gs{d->nx, d->ny, d->nz, d->npml, d->dx, d->dy, d->dz, grid_dt(*d)};
+    SourceSpec ss{s->m, s->theta, s->pol, s->mode, s->E0, s->r_center, s->thickness, s->inject};
+    std::vector<std::complex<double>> coef;
+    std::vector<uint8_t> mask;
+    int64_t counts[6];
+    source_tables(gs, ss, nullptr, nullptr, coef, mask, counts);
+    std::memcpy(out, coef.data(), coef.size() * 16);
+    std::memcpy(out_mask, mask.data(), mask.size());
+    return FDTD_OK;
+}
+
+double fdtd_bessel_j(int n, double x) { return bessel_j(n, x); }
+
+const char* fdtd_status_string(fdtd_status s)
+{
+    switch (s) {
+        case FDTD_OK: return "ok";
+        case FDTD_EINVAL: return "invalid argument";
+        case FDTD_ENOMEM: return "out of memory";
+        case FDTD_ECUDA: return "CUDA error";
+        case FDTD_ETIMEOUT: return "device wait timed out";
+        case FDTD_ESTATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* fdtd_last_error(void) { return g_last_error; }
+
+}  // extern "C"

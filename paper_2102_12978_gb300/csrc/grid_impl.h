@@ -1,0 +1,62 @@
+// grid_impl.h -- host-side grid object and arena layout (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fdtd.h"
+#include "yee_fused.cuh"
+
+namespace fdtd {
+
+struct Layout {
+    size_t elem = 4;
+    int pitch = 0;
+    size_t field_elems = 0, psx_elems = 0, psy_elems = 0;
+    size_t field[2][6] = {};
+    size_t phx[2][2] = {}, phy[2][2] = {};
+    size_t pex[2] = {}, pey[2] = {};
+    size_t fluence = 0;
+    size_t dynamic_bytes = 0;
+    size_t chx = 0, cex = 0, chy = 0, cey = 0;
+    size_t prof[8] = {};   // bhx ahx bex aex bhy ahy bey aey
+    size_t smask = 0, scoef = 0, zph = 0;
+    size_t total = 0;
+};
+
+struct TileConfig {
+    int tx = 32, ty = 8, lz = 32;
+};
+
+fdtd_status fail(fdtd_status st, const char* fmt, ...);
+fdtd_status cuda_check(cudaError_t e, const char* what);
+bool compute_layout(const fdtd_grid_desc& d, Layout& L);
+fdtd_status validate(const fdtd_grid_desc* d);
+double grid_dt(const fdtd_grid_desc& d);
+TileConfig default_tile(const fdtd_grid_desc& d, int sm_count);
+
+}  // namespace fdtd
+
+struct fdtd_grid {
+    fdtd_grid_desc desc;
+    fdtd::Layout L;
+    void* arena;
+    size_t arena_bytes;
+    cudaStream_t stream;
+    double dt;
+    int64_t step;
+    int cur;                 // which ping-pong copy holds the current state
+    bool has_source;
+    fdtd_annulus_desc src;
+    fdtd::SrcTime srct;
+    int64_t counts[6];
+    int sm_count;
+    fdtd::TileConfig tile;
+};
+
+namespace fdtd {
+template <typename real>
+StepArgs<real> make_args(const fdtd_grid* g, int cur);
+cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
+}  // namespace fdtd

@@ -1,0 +1,300 @@
+"""Thin Python binding of libfdtd_gb300.so (include/fdtd.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device arena (a uint8 tensor) and the CUDA
+stream.  If the library cannot be built or loaded this module raises; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_ETIMEOUT, FDTD_ESTATE = range(6)
+FDTD_F32, FDTD_F64 = 0, 1
+EX, EY, EZ, HX, HY, HZ = range(6)
+POL = {"y": 0, "x": 1, "circ+": 2, "circ-": 3}
+MODE = {"TE": 0, "TM": 1}
+ENV = {"cw": 0, "gauss": 1}
+INJ = {"all": 0, "tangential": 1}
+
+
+class FDTDError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status} ({detail})")
+        self.status = status
+
+
+class fdtd_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("npml", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("dt", C.c_double), ("courant", C.c_double),
+                ("pml_order", C.c_double), ("pml_sigma_scale", C.c_double),
+                ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double),
+                ("precision", C.c_int), ("fluence", C.c_int)]
+
+
+class fdtd_annulus_desc(C.Structure):
+    _fields_ = [("m", C.c_int), ("theta", C.c_double), ("pol", C.c_int), ("mode", C.c_int),
+                ("E0", C.c_double), ("r_center", C.c_double), ("thickness", C.c_double),
+                ("envelope", C.c_int), ("ramp", C.c_double), ("T", C.c_double), ("T0", C.c_double),
+                ("inject", C.c_int),
+                ("w_amp", C.POINTER(C.c_double)), ("w_phase", C.POINTER(C.c_double))]
+
+
+_SIGS = {
+    "fdtd_grid_desc_default": (None, [C.POINTER(fdtd_grid_desc)]),
+    "fdtd_required_bytes": (C.c_size_t, [C.POINTER(fdtd_grid_desc)]),
+    "fdtd_create_grid": (C.c_int, [C.POINTER(fdtd_grid_desc), C.c_void_p, C.c_size_t, C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
+    "fdtd_set_annulus_source": (C.c_int, [C.c_void_p, C.POINTER(fdtd_annulus_desc)]),
+    "fdtd_clear_source": (C.c_int, [C.c_void_p]),
+    "fdtd_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "fdtd_fluence": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "fdtd_get_field": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "fdtd_set_field": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "fdtd_state_bytes": (C.c_size_t, [C.c_void_p]),
+    "fdtd_save_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fdtd_load_state": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fdtd_get_step": (C.c_int64, [C.c_void_p]),
+    "fdtd_set_step": (C.c_int, [C.c_void_p, C.c_int64]),
+    "fdtd_get_dt": (C.c_double, [C.c_void_p]),
+    "fdtd_antenna_points": (C.c_int64, [C.c_void_p, C.c_int]),
+    "fdtd_sync": (C.c_int, [C.c_void_p]),
+    "fdtd_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fdtd_destroy_grid": (None, [C.c_void_p]),
+    "fdtd_source_coefficients": (C.c_int, [C.POINTER(fdtd_grid_desc), C.POINTER(fdtd_annulus_desc),
+                                           C.c_void_p, C.c_void_p]),
+    "fdtd_bessel_j": (C.c_double, [C.c_int, C.c_double]),
+    "fdtd_status_string": (C.c_char_p, [C.c_int]),
+    "fdtd_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load (building first if needed) the CUDA library; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def check(status: int, where: str):
+    if status != FDTD_OK:
+        L = lib()
+        raise FDTDError(status, where, L.fdtd_last_error().decode() or L.fdtd_status_string(status).decode())
+
+
+# ---- thin wrappers with the C names -------------------------------------
+
+def fdtd_grid_desc_default() -> fdtd_grid_desc:
+    d = fdtd_grid_desc()
+    lib().fdtd_grid_desc_default(C.byref(d))
+    return d
+
+
+def fdtd_required_bytes(d: fdtd_grid_desc) -> int:
+    return int(lib().fdtd_required_bytes(C.byref(d)))
+
+
+def fdtd_create_grid(d: fdtd_grid_desc, arena_ptr: int, nbytes: int, stream_ptr: int) -> int:
+    h = C.c_void_p()
+    check(lib().fdtd_create_grid(C.byref(d), C.c_void_p(arena_ptr), nbytes, C.c_void_p(stream_ptr),
+                                 C.byref(h)), "fdtd_create_grid")
+    return h.value
+
+
+def fdtd_set_annulus_source(h: int, s: fdtd_annulus_desc):
+    check(lib().fdtd_set_annulus_source(C.c_void_p(h), C.byref(s)), "fdtd_set_annulus_source")
+
+
+def fdtd_step(h: int, nsteps: int):
+    check(lib().fdtd_step(C.c_void_p(h), int(nsteps)), "fdtd_step")
+
+
+def fdtd_fluence(h: int, dst_ptr: int, on_device: bool, reset: bool):
+    check(lib().fdtd_fluence(C.c_void_p(h), C.c_void_p(dst_ptr), int(on_device), int(reset)), "fdtd_fluence")
+
+
+def fdtd_get_field(h: int, comp: int, dst_ptr: int, on_device: bool):
+    check(lib().fdtd_get_field(C.c_void_p(h), comp, C.c_void_p(dst_ptr), int(on_device)), "fdtd_get_field")
+
+
+def fdtd_set_field(h: int, comp: int, src_ptr: int, on_device: bool):
+    check(lib().fdtd_set_field(C.c_void_p(h), comp, C.c_void_p(src_ptr), int(on_device)), "fdtd_set_field")
+
+
+def fdtd_bessel_j(n: int, x: float) -> float:
+    return float(lib().fdtd_bessel_j(int(n), float(x)))
+
+
+def make_grid_desc(nx, ny, nz, npml, dx, dy, dz, courant=0.95, precision="f32", fluence=True,
+                   dt=0.0, **pml) -> fdtd_grid_desc:
+    d = fdtd_grid_desc_default()
+    d.nx, d.ny, d.nz, d.npml = nx, ny, nz, npml
+    d.dx, d.dy, d.dz = dx, dy, dz
+    d.courant, d.dt = courant, dt
+    d.precision = FDTD_F64 if precision in ("f64", "float64", "double") else FDTD_F32
+    d.fluence = 1 if fluence else 0
+    for k, v in pml.items():
+        setattr(d, k, v)
+    return d
+
+
+def make_annulus_desc(m=0, theta=math.radians(20.0), pol="y", mode="TE", E0=1.0, r_center=12.0,
+                      thickness=1.0, envelope="cw", ramp=10.0, T=0.0, T0=0.0, inject="all",
+                      w_amp=None, w_phase=None):
+    s = fdtd_annulus_desc()
+    s.m, s.theta, s.pol, s.mode, s.E0 = m, theta, POL[pol], MODE[mode], E0
+    s.r_center, s.thickness = r_center, thickness
+    s.envelope, s.ramp, s.T, s.T0, s.inject = ENV[envelope], ramp, T, T0, INJ[inject]
+    keep = []
+    dp = C.POINTER(C.c_double)
+    for name, arr in (("w_amp", w_amp), ("w_phase", w_phase)):
+        if arr is None:
+            setattr(s, name, dp())
+        else:
+            a = np.ascontiguousarray(arr, dtype=np.float64)
+            keep.append(a)
+            setattr(s, name, a.ctypes.data_as(dp))
+    return s, keep
+
+
+def source_coefficients(d: fdtd_grid_desc, s: fdtd_annulus_desc):
+    """Host-only FP64 precompute: (coef[6, ny, nx] complex, mask[ny, nx] uint8)."""
+    out = np.zeros((6, d.ny, d.nx, 2))
+    mask = np.zeros((d.ny, d.nx), np.uint8)
+    check(lib().fdtd_source_coefficients(C.byref(d), C.byref(s), out.ctypes.data, mask.ctypes.data),
+          "fdtd_source_coefficients")
+    return out[..., 0] + 1j * out[..., 1], mask
+
+
+# ---- torch-owned grid ----------------------------------------------------
+
+class Grid:
+    """A grid living in a torch-allocated device arena on the current stream."""
+
+    def __init__(self, desc: fdtd_grid_desc, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libfdtd_gb300 needs a CUDA device; there is no CPU fallback")
+        self.torch = torch
+        self.desc = desc
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = fdtd_required_bytes(desc)
+        if nbytes == 0:
+            check(FDTD_EINVAL, "fdtd_required_bytes")
+        self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.arena.data_ptr()
+        off = (-base) % 256
+        self._arena_ptr = base + off
+        with torch.cuda.device(self.device):
+            self.handle = fdtd_create_grid(desc, self._arena_ptr, nbytes, self.stream.cuda_stream)
+        self.dtype = torch.float64 if desc.precision == FDTD_F64 else torch.float32
+        self.shape = (desc.nz, desc.ny, desc.nx)
+        self._keep = None
+
+    # source
+    def set_source(self, **kw):
+        s, keep = make_annulus_desc(**kw)
+        self._keep = keep
+        fdtd_set_annulus_source(self.handle, s)
+
+    def clear_source(self):
+        check(lib().fdtd_clear_source(C.c_void_p(self.handle)), "fdtd_clear_source")
+
+    def step(self, n: int = 1):
+        fdtd_step(self.handle, n)
+
+    def set_tile(self, ty: int, lz: int):
+        check(lib().fdtd_set_tile(C.c_void_p(self.handle), int(ty), int(lz)), "fdtd_set_tile")
+
+    def tile(self):
+        ty, lz = C.c_int(), C.c_int()
+        check(lib().fdtd_get_tile(C.c_void_p(self.handle), C.byref(ty), C.byref(lz)), "fdtd_get_tile")
+        return ty.value, lz.value
+
+    def autotune(self, steps: int = 5):
+        scratch = self.torch.empty(self.state_bytes(), dtype=self.torch.uint8, device=self.device)
+        check(lib().fdtd_autotune(C.c_void_p(self.handle), int(steps), C.c_void_p(scratch.data_ptr())),
+              "fdtd_autotune")
+        del scratch
+        return self.tile()
+
+    def sync(self):
+        check(lib().fdtd_sync(C.c_void_p(self.handle)), "fdtd_sync")
+
+    @property
+    def n(self) -> int:
+        return int(lib().fdtd_get_step(C.c_void_p(self.handle)))
+
+    @property
+    def dt(self) -> float:
+        return float(lib().fdtd_get_dt(C.c_void_p(self.handle)))
+
+    def antenna_points(self, comp: int) -> int:
+        return int(lib().fdtd_antenna_points(C.c_void_p(self.handle), comp))
+
+    def field(self, comp: int):
+        out = self.torch.empty(self.shape, dtype=self.dtype, device=self.device)
+        fdtd_get_field(self.handle, comp, out.data_ptr(), True)
+        return out
+
+    def fields(self):
+        return [self.field(c) for c in range(6)]
+
+    def set_field(self, comp: int, values):
+        t = self.torch.as_tensor(values, dtype=self.dtype).to(self.device).contiguous()
+        assert tuple(t.shape) == self.shape
+        fdtd_set_field(self.handle, comp, t.data_ptr(), True)
+
+    def fluence(self, reset: bool = False):
+        out = self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device)
+        fdtd_fluence(self.handle, out.data_ptr(), True, reset)
+        return out
+
+    def state_bytes(self) -> int:
+        return int(lib().fdtd_state_bytes(C.c_void_p(self.handle)))
+
+    def save_state(self, buf=None):
+        if buf is None:
+            buf = self.torch.empty(self.state_bytes(), dtype=self.torch.uint8, device=self.device)
+        check(lib().fdtd_save_state(C.c_void_p(self.handle), C.c_void_p(buf.data_ptr())), "fdtd_save_state")
+        return buf
+
+    def load_state(self, buf):
+        check(lib().fdtd_load_state(C.c_void_p(self.handle), C.c_void_p(buf.data_ptr())), "fdtd_load_state")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fdtd_destroy_grid(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
