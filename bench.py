@@ -55,7 +55,7 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index):
         self.index = index
         self.proc = None
         self.lines = []
@@ -166,7 +166,9 @@ def run_gpu(args):
     # ---- FP32 (headline) ---------------------------------------------------
     g32 = make("f32")
     tile32 = g32.autotune(steps=5)
-    with ClockSampler(local) as clk:
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    with ClockSampler(gpu_id) as clk:
         ms32 = timed(g32, args.steps, args.warmup)
     clocks = clk.summary()
     per_launch_ms = ms32 / args.steps
