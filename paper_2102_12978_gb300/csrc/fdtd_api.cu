@@ -356,13 +356,11 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     std::vector<uint8_t> mask;
     int64_t counts[6];
     source_tables(gs, ss, s->w_amp, s->w_phase, coef, mask, counts);
-    // e^{i beta z} on the integer and the half planes
+    // e^{i beta k dz}: the coefficients already carry each component's own
+    // half-cell z offset, so one table serves every component
     const double beta = 2.0 * M_PI * std::cos(s->theta);
-    std::vector<std::complex<double>> zph(2 * size_t(d.nz));
-    for (int k = 0; k < d.nz; ++k) {
-        zph[k] = std::polar(1.0, beta * (k * d.dz));
-        zph[d.nz + k] = std::polar(1.0, beta * ((k + 0.5) * d.dz));
-    }
+    std::vector<std::complex<double>> zph(size_t(d.nz));
+    for (int k = 0; k < d.nz; ++k) zph[k] = std::polar(1.0, beta * (k * d.dz));
     char* A = static_cast<char*>(g->arena);
     fdtd_status st = cuda_check(cudaMemcpyAsync(A + g->L.scoef, coef.data(), coef.size() * 16,
                                                 cudaMemcpyHostToDevice, g->stream), "upload source");

@@ -64,7 +64,7 @@ struct StepArgs {
     double* fluence;         // [nz][ny][pitch] or null
     const uint8_t* smask;    // [ny][nx] or null (no source)
     const double2* scoef;    // [6][ny][nx]
-    const double2* zph;      // [2][nz]: e^{i beta k dz}, e^{i beta (k+1/2) dz}
+    const double2* zph;      // [nz]: e^{i beta k dz} (coefficients carry the half-cell z offset)
     SrcTime st;
 };
 
@@ -229,8 +229,8 @@ yee_step_fused(const StepArgs<real> a, long long n, int lz)
             if (mk & 0x38) {
                 const size_t ncol = size_t(nx) * ny, col = size_t(cj) * nx + ci;
                 double c = tf[3], s = tf[4], f = tf[5];
-                if (mk & 0x08) hx += real(source_value(a.scoef[3 * ncol + col], a.zph[nz + kw], c, s, f));
-                if (mk & 0x10) hy += real(source_value(a.scoef[4 * ncol + col], a.zph[nz + kw], c, s, f));
+                if (mk & 0x08) hx += real(source_value(a.scoef[3 * ncol + col], a.zph[kw], c, s, f));
+                if (mk & 0x10) hy += real(source_value(a.scoef[4 * ncol + col], a.zph[kw], c, s, f));
                 if (mk & 0x20) hz += real(source_value(a.scoef[5 * ncol + col], a.zph[kw], c, s, f));
             }
         }
@@ -342,7 +342,7 @@ yee_step_fused(const StepArgs<real> a, long long n, int lz)
                     double c = tf[0], s = tf[1], f = tf[2];
                     if (mk & 0x01) nex += real(source_value(a.scoef[col], a.zph[kw], c, s, f));
                     if (mk & 0x02) ney += real(source_value(a.scoef[ncol + col], a.zph[kw], c, s, f));
-                    if (mk & 0x04) nez += real(source_value(a.scoef[2 * ncol + col], a.zph[nz + kw], c, s, f));
+                    if (mk & 0x04) nez += real(source_value(a.scoef[2 * ncol + col], a.zph[kw], c, s, f));
                 }
             }
             if (j == 0) { nex = real(0); nez = real(0); }    // PEC, tangential E
