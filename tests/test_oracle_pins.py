@@ -384,11 +384,13 @@ def test_bessel_intensity_matches_jm_squared():
     field amplitude), and the intensity is z-invariant within +-2 % (Fig. 5).
     A short ramp and a long run let the near-cutoff transient (components
     with K ~ 0 cannot leave a z-periodic box sideways) die out."""
-    w = W.small(nx=96, ny=96, nz=16, npml=8, theta_deg=20.0, m=0, pol="y", r_center=32.0,
-                steps=2200, ramp=3.0)
+    # theta = 30 deg as in runs A-C of Table 1: the transverse group velocity
+    # c sin(theta) lets the start-up transient leave within ~40 periods
+    w = W.small(nx=96, ny=96, nz=16, npml=8, theta_deg=30.0, m=0, pol="y", r_center=32.0,
+                steps=1200, ramp=3.0)
     # a window of nearly whole periods, so the time average is phase-free
     dt = oracle_grid(w).dt
-    window = min(range(150, 400), key=lambda n: abs(n * dt - round(n * dt)))
+    window = min(range(300, 420), key=lambda n: abs(n * dt - round(n * dt)))
     g, st, I = _mean_epol2(w, window)
     # E_y sits at (i, j+1/2): radius in cells from the axis
     i = np.arange(g.nx)[None, :]
