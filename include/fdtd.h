@@ -153,7 +153,9 @@ fdtd_status fdtd_step(fdtd_grid* g, int nsteps);
 
 /* Copy the fluence (nz*ny*nx doubles, x fastest, dense) to dst (device if
  * on_device, else host), then zero the accumulator if reset.  Synchronises
- * the stream.  Cell (i,j,k) is centred at (i+1/2, j+1/2, k+1/2). */
+ * the stream.  Cell (i,j,k) is centred at (i+1/2, j+1/2, k+1/2).  FP64 grids
+ * accumulate in FP64; FP32 grids keep an FP32 sum plus a Kahan compensation
+ * term, which the export kernel combines in FP64. */
 fdtd_status fdtd_fluence(fdtd_grid* g, void* dst, int on_device, int reset);
 
 /* Copy one field component (FDTD_EX..FDTD_HZ) as a dense nz*ny*nx array of the
@@ -177,14 +179,18 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
 
 /* Tile configuration of the fused step kernel: a CTA of 32 x ty threads
  * (ty in {4, 8, 16}) owns a 32 x ty tile of columns and marches lz planes of
- * z.  fdtd_create_grid picks a default; fdtd_autotune times the candidates
- * on this grid (running `steps` steps for each, then restoring the state)
- * and keeps the fastest.  Results are identical for every configuration. */
-fdtd_status fdtd_set_tile(fdtd_grid* g, int ty, int lz);
-fdtd_status fdtd_get_tile(const fdtd_grid* g, int* ty, int* lz);
+ * z.  variant 1 stages every z plane with TMA bulk-tensor copies into a
+ * multi-stage shared-memory ring (mbarrier completion); variant 0 uses plain
+ * coalesced loads (no FP64 32x16 tile in variant 1).  fdtd_create_grid picks
+ * a default; fdtd_autotune times the candidates on this grid (running `steps`
+ * steps for each, then restoring the state) and keeps the fastest.  Results
+ * are identical for every configuration. */
+fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
+fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz);
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state);
 
-/* Synchronise the grid's stream and report any pending CUDA error. */
+/* Synchronise the grid's stream and report any pending CUDA error; returns
+ * FDTD_ETIMEOUT (and clears the word) if a kernel's bounded wait expired. */
 fdtd_status fdtd_sync(fdtd_grid* g);
 
 void fdtd_destroy_grid(fdtd_grid* g);

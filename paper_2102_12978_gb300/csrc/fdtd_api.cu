@@ -2,6 +2,8 @@
 // descriptors, arena layout, FP64 precompute of the CPML profiles (Section 4,
 // Roden-Gedney CPML) and of the antenna tables (Eq. 6-9, 12, 13), kernel
 // dispatch, state save/load and error reporting.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -16,6 +18,7 @@
 #include "engine.h"
 #include "grid_impl.h"
 #include "yee_fused.cuh"
+#include "fluence.cuh"
 
 namespace fdtd {
 
@@ -70,6 +73,8 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
     L.smask = take(nx * ny);
     L.scoef = take(6 * nx * ny * 16);
     L.zph = take(2 * nz * 16);
+    L.flu_out = d.fluence ? take(nz * ny * nx * 8) : 0;
+    L.err = take(256);
     L.total = off;
     return true;
 }
@@ -205,7 +210,7 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
     a.aey = reinterpret_cast<const real*>(A + L.prof[7]);
     a.cz = real(g->dt / g->desc.dz);
     a.dt = g->dt;
-    a.fluence = g->desc.fluence ? reinterpret_cast<double*>(A + L.fluence) : nullptr;
+    a.fluence = g->desc.fluence ? static_cast<void*>(A + L.fluence) : nullptr;
     a.smask = g->has_source ? reinterpret_cast<const uint8_t*>(A + L.smask) : nullptr;
     a.scoef = reinterpret_cast<const double2*>(A + L.scoef);
     a.zph = reinterpret_cast<const double2*>(A + L.zph);
@@ -216,7 +221,7 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
 template StepArgs<float> make_args<float>(const fdtd_grid*, int);
 template StepArgs<double> make_args<double>(const fdtd_grid*, int);
 
-// ---- kernel dispatch over (precision, tile)
+// ---- kernel dispatch over (variant, precision, tile)
 template <typename real, int TX, int TY>
 static cudaError_t launch_fused(const fdtd_grid* g, int cur, long long n, int lz, cudaStream_t s)
 {
@@ -235,8 +240,99 @@ static cudaError_t launch_fused(const fdtd_grid* g, int cur, long long n, int lz
     return cudaGetLastError();
 }
 
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D tiled tensor map over one pitched [nz][ny][pitch] array; elements past
+// nx / ny (and before 0) read as zero.
+static bool encode_map(CUtensorMap* m, void* base, size_t elem, const fdtd_grid_desc& d, int pitch, int bx,
+                       int by)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {cuuint64_t(d.nx), cuuint64_t(d.ny), cuuint64_t(d.nz)};
+    cuuint64_t strides[2] = {cuuint64_t(pitch) * elem, cuuint64_t(pitch) * d.ny * elem};
+    cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+static int ty_slot(int ty) { return ty == 4 ? 0 : (ty == 8 ? 1 : 2); }
+
+template <typename real, int TY>
+static bool tma_maps(fdtd_grid* g, int cur, TmaMaps** out)
+{
+    int sl = ty_slot(TY);
+    if (!g->maps_ok[cur][sl]) {
+        using T = TmaTile<real, TY>;
+        char* A = static_cast<char*>(g->arena);
+        TmaMaps& m = g->maps[cur][sl];
+        bool ok = true;
+        for (int c = 0; c < 3; ++c) {
+            ok = ok && encode_map(&m.e[c], A + g->L.field[cur][c], sizeof(real), g->desc, g->L.pitch, T::BX, T::EBY);
+            ok = ok && encode_map(&m.h[c], A + g->L.field[cur][3 + c], sizeof(real), g->desc, g->L.pitch, T::BX,
+                                  T::HBY);
+        }
+        void* fbase = g->desc.fluence ? static_cast<void*>(A + g->L.fluence) : static_cast<void*>(A + g->L.field[cur][0]);
+        ok = ok && encode_map(&m.f, fbase, 8, g->desc, g->L.pitch, T::FBX, T::FBY);
+        if (!ok) return false;
+        g->maps_ok[cur][sl] = true;
+    }
+    *out = &g->maps[cur][sl];
+    return true;
+}
+
+template <typename real, int TY, int S>
+static cudaError_t launch_tma(const fdtd_grid* cg, int cur, long long n, int lz, cudaStream_t s)
+{
+    fdtd_grid* g = const_cast<fdtd_grid*>(cg);
+    using T = TmaTile<real, TY>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(yee_step_tma<real, TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(T::smem_bytes(S)));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    TmaMaps* m = nullptr;
+    if (!tma_maps<real, TY>(g, cur, &m)) return cudaErrorInvalidValue;
+    dim3 block(32, TY);
+    dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, (g->desc.nz + lz - 1) / lz);
+    int* err = reinterpret_cast<int*>(static_cast<char*>(g->arena) + g->L.err);
+    yee_step_tma<real, TY, S><<<grid, block, T::smem_bytes(S), s>>>(make_args<real>(g, cur), *m, n, lz, err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s)
 {
+    if (tc.variant == 1) {
+        if (g->desc.precision == FDTD_F32) {
+            switch (tc.ty) {
+                case 4: return launch_tma<float, 4, 6>(g, cur, n, tc.lz, s);
+                case 16: return launch_tma<float, 16, 4>(g, cur, n, tc.lz, s);
+                default: return launch_tma<float, 8, 4>(g, cur, n, tc.lz, s);
+            }
+        } else {
+            switch (tc.ty) {
+                case 4: return launch_tma<double, 4, 4>(g, cur, n, tc.lz, s);
+                default: return launch_tma<double, 8, 4>(g, cur, n, tc.lz, s);
+            }
+        }
+    }
     if (g->desc.precision == FDTD_F32) {
         switch (tc.ty) {
             case 4: return launch_fused<float, 32, 4>(g, cur, n, tc.lz, s);
@@ -257,7 +353,7 @@ cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConf
 TileConfig default_tile(const fdtd_grid_desc& d, int sm_count)
 {
     TileConfig tc;
-    tc.tx = 32; tc.ty = 8;
+    tc.variant = 1; tc.tx = 32; tc.ty = 8;
     long tiles = long((d.nx + 31) / 32) * long((d.ny + 7) / 8);
     long want = 4L * (sm_count > 0 ? sm_count : 152);
     long segs = (want + tiles - 1) / tiles;
@@ -326,6 +422,8 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     g->sm_count = sms;
     g->tile = default_tile(*d, sms);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 3; ++b) g->maps_ok[a][b] = false;
     st = cuda_check(cudaMemsetAsync(arena, 0, L.total, g->stream), "zero arena");
     if (st == FDTD_OK)
         st = (d->precision == FDTD_F64) ? upload_tables<double>(g) : upload_tables<float>(g);
@@ -411,7 +509,18 @@ fdtd_status fdtd_sync(fdtd_grid* g)
     if (!g) return fail(FDTD_EINVAL, "null grid");
     fdtd_status st = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
     if (st != FDTD_OK) return st;
-    return cuda_check(cudaGetLastError(), "pending CUDA error");
+    st = cuda_check(cudaGetLastError(), "pending CUDA error");
+    if (st != FDTD_OK) return st;
+    int err = 0;
+    st = cuda_check(cudaMemcpy(&err, static_cast<char*>(g->arena) + g->L.err, sizeof(int), cudaMemcpyDeviceToHost),
+                    "read error word");
+    if (st != FDTD_OK) return st;
+    if (err != 0) {
+        cudaMemsetAsync(static_cast<char*>(g->arena) + g->L.err, 0, sizeof(int), g->stream);
+        cudaStreamSynchronize(g->stream);
+        return fail(FDTD_ETIMEOUT, "a bounded device-side wait expired (error word %d)", err);
+    }
+    return FDTD_OK;
 }
 
 fdtd_status fdtd_fluence(fdtd_grid* g, void* dst, int on_device, int reset)
@@ -420,11 +529,19 @@ fdtd_status fdtd_fluence(fdtd_grid* g, void* dst, int on_device, int reset)
     if (!g->desc.fluence) return fail(FDTD_ESTATE, "grid created without a fluence accumulator");
     const fdtd_grid_desc& d = g->desc;
     char* A = static_cast<char*>(g->arena);
-    fdtd_status st = cuda_check(
-        cudaMemcpy2DAsync(dst, size_t(d.nx) * 8, A + g->L.fluence, size_t(g->L.pitch) * 8, size_t(d.nx) * 8,
-                          size_t(d.ny) * d.nz, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                          g->stream),
-        "copy fluence");
+    double* out = reinterpret_cast<double*>(A + g->L.flu_out);
+    int blocks = 4 * (g->sm_count > 0 ? g->sm_count : 152);
+    if (d.precision == FDTD_F64)
+        fluence_export<double><<<blocks, 256, 0, g->stream>>>(reinterpret_cast<const double*>(A + g->L.fluence),
+                                                              out, d.nx, d.ny, d.nz, g->L.pitch, 1.0);
+    else
+        fluence_export<float2><<<blocks, 256, 0, g->stream>>>(reinterpret_cast<const float2*>(A + g->L.fluence),
+                                                               out, d.nx, d.ny, d.nz, g->L.pitch, 1.0);
+    fdtd_status st = cuda_check(cudaGetLastError(), "fluence_export launch");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(dst, out, size_t(d.nx) * d.ny * d.nz * 8,
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream),
+                        "copy fluence");
     if (st == FDTD_OK && reset)
         st = cuda_check(cudaMemsetAsync(A + g->L.fluence, 0, g->L.field_elems * 8, g->stream), "reset fluence");
     if (st != FDTD_OK) return st;
@@ -521,20 +638,25 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component)
 
 void fdtd_destroy_grid(fdtd_grid* g) { delete g; }
 
-fdtd_status fdtd_set_tile(fdtd_grid* g, int ty, int lz)
+fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (variant != 0 && variant != 1) return fail(FDTD_EINVAL, "variant=%d not in {0, 1}", variant);
     if (ty != 4 && ty != 8 && ty != 16) return fail(FDTD_EINVAL, "ty=%d not in {4, 8, 16}", ty);
+    if (variant == 1 && ty == 16 && g->desc.precision == FDTD_F64)
+        return fail(FDTD_EINVAL, "the TMA variant has no FP64 32x16 tile");
     if (lz < 1) return fail(FDTD_EINVAL, "lz=%d < 1", lz);
+    g->tile.variant = variant;
     g->tile.tx = 32;
     g->tile.ty = ty;
     g->tile.lz = lz > g->desc.nz ? g->desc.nz : lz;
     return FDTD_OK;
 }
 
-fdtd_status fdtd_get_tile(const fdtd_grid* g, int* ty, int* lz)
+fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz)
 {
-    if (!g || !ty || !lz) return fail(FDTD_EINVAL, "null argument");
+    if (!g || !variant || !ty || !lz) return fail(FDTD_EINVAL, "null argument");
+    *variant = g->tile.variant;
     *ty = g->tile.ty;
     *lz = g->tile.lz;
     return FDTD_OK;
@@ -548,7 +670,9 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     if (!g || !scratch_state || steps < 1) return fail(FDTD_EINVAL, "invalid argument");
     fdtd_status st = fdtd_save_state(g, scratch_state);
     if (st != FDTD_OK) return st;
-    const int tys[3] = {4, 8, 16};
+    struct Cand { int variant, ty; };
+    std::vector<Cand> cands = {{1, 4}, {1, 8}, {1, 16}, {0, 4}, {0, 8}, {0, 16}};
+    if (g->desc.precision == FDTD_F64) cands = {{1, 4}, {1, 8}, {0, 4}, {0, 8}};
     const int nz = g->desc.nz;
     std::vector<int> lzs;
     for (int segs : {1, 2, 3, 4, 6, 8, 12, 16}) {
@@ -564,9 +688,9 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
         return fail(FDTD_ECUDA, "event create failed");
     float best = 1e30f;
     TileConfig best_tc = g->tile;
-    for (int ty : tys)
+    for (const Cand& cd : cands)
         for (int lz : lzs) {
-            TileConfig tc; tc.tx = 32; tc.ty = ty; tc.lz = lz;
+            TileConfig tc; tc.variant = cd.variant; tc.tx = 32; tc.ty = cd.ty; tc.lz = lz;
             cudaError_t e = launch_step(g, g->cur, g->step, tc, g->stream);   // warm-up
             if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_check(e, "autotune"); }
             cudaEventRecord(e0, g->stream);

@@ -7,6 +7,7 @@
 
 #include "../../include/fdtd.h"
 #include "yee_fused.cuh"
+#include "yee_tma.cuh"
 
 namespace fdtd {
 
@@ -22,11 +23,15 @@ struct Layout {
     size_t chx = 0, cex = 0, chy = 0, cey = 0;
     size_t prof[8] = {};   // bhx ahx bex aex bhy ahy bey aey
     size_t smask = 0, scoef = 0, zph = 0;
+    size_t flu_out = 0;    // dense FP64 export of the fluence
+    size_t err = 0;        // device error word (int)
     size_t total = 0;
 };
 
+// variant 0: plain loads into a shared-memory ring (yee_step_fused);
+// variant 1: TMA-staged planes with mbarriers (yee_step_tma).
 struct TileConfig {
-    int tx = 32, ty = 8, lz = 32;
+    int variant = 1, tx = 32, ty = 8, lz = 32;
 };
 
 fdtd_status fail(fdtd_status st, const char* fmt, ...);
@@ -53,6 +58,8 @@ struct fdtd_grid {
     int64_t counts[6];
     int sm_count;
     fdtd::TileConfig tile;
+    fdtd::TmaMaps maps[2][3];   // [read copy][ty = 4, 8, 16]
+    bool maps_ok[2][3];
 };
 
 namespace fdtd {

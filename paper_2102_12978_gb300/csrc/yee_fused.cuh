@@ -61,7 +61,8 @@ struct StepArgs {
     const real* aey;
     real cz;                 // dt / dz
     double dt;
-    double* fluence;         // [nz][ny][pitch] or null
+    void* fluence;           // [nz][ny][pitch] accumulator or null: double (FP64
+                             // grids) or float2 (sum, Kahan compensation) (FP32)
     const uint8_t* smask;    // [ny][nx] or null (no source)
     const double2* scoef;    // [6][ny][nx]
     const double2* zph;      // [nz]: e^{i beta k dz} (coefficients carry the half-cell z offset)
@@ -84,6 +85,24 @@ __device__ __forceinline__ void source_time(const SrcTime& st, double t, double&
         f = 1.0;
     }
 }
+
+// Fluence accumulator of one cell.  FP64 grids add in FP64.  FP32 grids keep
+// an FP32 sum with a Kahan compensation term (no FP64 instruction per cell:
+// GB300's FP64 pipe is a small fraction of its FP32 rate).
+template <typename real> struct FluAcc;
+template <> struct FluAcc<double> {
+    using T = double;
+    __device__ __forceinline__ static T add(T old, double v_dt) { return old + v_dt; }
+};
+template <> struct FluAcc<float> {
+    using T = float2;
+    __device__ __forceinline__ static T add(T old, float v_dt)
+    {
+        const float y = v_dt - old.y;
+        const float t = old.x + y;
+        return make_float2(t, (t - old.x) - y);
+    }
+};
 
 // Value added by the soft source: f Re{ B e^{i beta z} e^{-i Phi} }.
 __device__ __forceinline__ double source_value(double2 B, double2 z, double c, double s, double f)
@@ -381,7 +400,9 @@ yee_step_fused(const StepArgs<real> a, long long n, int lz)
                 real sz = ex * hy - ey * hx;
                 real sm = sqrt(sx * sx + sy * sy + sz * sz);
                 size_t g = size_t(kmw) * plane + size_t(fj) * pitch + fi;
-                a.fluence[g] += double(sm) * a.dt;
+                using Acc = FluAcc<real>;
+                typename Acc::T* F = static_cast<typename Acc::T*>(a.fluence);
+                F[g] = Acc::add(F[g], sm * real(a.dt));
             }
         }
     }

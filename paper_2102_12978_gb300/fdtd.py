@@ -70,8 +70,8 @@ _SIGS = {
     "fdtd_get_dt": (C.c_double, [C.c_void_p]),
     "fdtd_antenna_points": (C.c_int64, [C.c_void_p, C.c_int]),
     "fdtd_sync": (C.c_int, [C.c_void_p]),
-    "fdtd_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
-    "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fdtd_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
     "fdtd_source_coefficients": (C.c_int, [C.POINTER(fdtd_grid_desc), C.POINTER(fdtd_annulus_desc),
@@ -229,13 +229,14 @@ class Grid:
     def step(self, n: int = 1):
         fdtd_step(self.handle, n)
 
-    def set_tile(self, ty: int, lz: int):
-        check(lib().fdtd_set_tile(C.c_void_p(self.handle), int(ty), int(lz)), "fdtd_set_tile")
+    def set_tile(self, variant: int, ty: int, lz: int):
+        check(lib().fdtd_set_tile(C.c_void_p(self.handle), int(variant), int(ty), int(lz)), "fdtd_set_tile")
 
     def tile(self):
-        ty, lz = C.c_int(), C.c_int()
-        check(lib().fdtd_get_tile(C.c_void_p(self.handle), C.byref(ty), C.byref(lz)), "fdtd_get_tile")
-        return ty.value, lz.value
+        v, ty, lz = C.c_int(), C.c_int(), C.c_int()
+        check(lib().fdtd_get_tile(C.c_void_p(self.handle), C.byref(v), C.byref(ty), C.byref(lz)),
+              "fdtd_get_tile")
+        return v.value, ty.value, lz.value
 
     def autotune(self, steps: int = 5):
         scratch = self.torch.empty(self.state_bytes(), dtype=self.torch.uint8, device=self.device)

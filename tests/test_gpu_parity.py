@@ -61,11 +61,21 @@ def test_small_grids_match_oracle(precision, shape):
     _assert(_compare(w, precision), precision)
 
 
-@pytest.mark.parametrize("tile", [(4, 1), (8, 3), (16, 16), (8, 64)])
-def test_tilings_and_z_segments_agree(tile):
-    """Every (ty, lz) tiling, including one-plane z segments, gives the same result."""
+TILES = [(1, 4, 1), (1, 8, 3), (1, 8, 64), (0, 4, 1), (0, 8, 3), (0, 16, 16), (0, 8, 64)]
+
+
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_tilings_and_z_segments_agree(tile, precision):
+    """Every (variant, ty, lz) tiling -- TMA-staged and plain-load kernels,
+    one-plane z segments, ragged tiles -- matches the oracle."""
     w = W.small(nx=40, ny=36, nz=16, npml=6, r_center=9.0, steps=30, ramp=1.0)
-    _assert(_compare(w, "f64", tile=tile), "f64")
+    _assert(_compare(w, precision, tile=tile), precision)
+
+
+def test_tma_f32_tall_tile():
+    w = W.small(nx=72, ny=50, nz=12, npml=6, r_center=12.0, steps=30, ramp=1.0)
+    _assert(_compare(w, "f32", tile=(1, 16, 5)), "f32")
 
 
 @pytest.mark.parametrize("kw", [
