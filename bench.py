@@ -165,6 +165,8 @@ def run_gpu(args):
 
     if args.only != "all":
         g = make(args.only)
+        if args.tile:
+            g.set_tile(*[int(x) for x in args.tile.split(",")])
         g.step(args.warmup)
         g.step(args.steps)
         g.sync()
@@ -339,6 +341,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--only", default="all", choices=["all", "f32", "f64"],
                     help="time only one precision (profiling runs)")
+    ap.add_argument("--tile", default=None, help="variant,ty,lz for --only runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
