@@ -17,6 +17,7 @@
 #include "../../include/fdtd.h"
 #include "engine.h"
 #include "grid_impl.h"
+#include "tma_host.h"
 #include "yee_fused.cuh"
 #include "fluence.cuh"
 
@@ -90,6 +91,9 @@ fdtd_status validate(const fdtd_grid_desc* d)
         return fail(FDTD_EINVAL, "cell sizes must be positive");
     if (d->precision != FDTD_F32 && d->precision != FDTD_F64)
         return fail(FDTD_EINVAL, "unknown precision %d", d->precision);
+    if (double(d->nz) * d->ny * (d->nx + 31) >= 2147483647.0)
+        return fail(FDTD_EINVAL, "grid of %d x %d x %d cells exceeds the 2^31-element limit of one array",
+                    d->nx, d->ny, d->nz);
     double lim = 1.0 / std::sqrt(1.0 / (d->dx * d->dx) + 1.0 / (d->dy * d->dy) + 1.0 / (d->dz * d->dz));
     if (d->dt == 0.0) {
         if (!(d->courant > 0.0) || d->courant > 1.0)
@@ -240,62 +244,6 @@ static cudaError_t launch_fused(const fdtd_grid* g, int cur, long long n, int lz
     return cudaGetLastError();
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-// 3-D tiled tensor map over one pitched [nz][ny][pitch] array; elements past
-// nx / ny (and before 0) read as zero.
-static bool encode_map(CUtensorMap* m, void* base, size_t elem, const fdtd_grid_desc& d, int pitch, int bx,
-                       int by)
-{
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[3] = {cuuint64_t(d.nx), cuuint64_t(d.ny), cuuint64_t(d.nz)};
-    cuuint64_t strides[2] = {cuuint64_t(pitch) * elem, cuuint64_t(pitch) * d.ny * elem};
-    cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(m, elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-static int ty_slot(int ty) { return ty == 4 ? 0 : (ty == 8 ? 1 : 2); }
-
-template <typename real, int TY>
-static bool tma_maps(fdtd_grid* g, int cur, TmaMaps** out)
-{
-    int sl = ty_slot(TY);
-    if (!g->maps_ok[cur][sl]) {
-        using T = TmaTile<real, TY>;
-        char* A = static_cast<char*>(g->arena);
-        TmaMaps& m = g->maps[cur][sl];
-        bool ok = true;
-        for (int c = 0; c < 3; ++c) {
-            ok = ok && encode_map(&m.e[c], A + g->L.field[cur][c], sizeof(real), g->desc, g->L.pitch, T::BX, T::EBY);
-            ok = ok && encode_map(&m.h[c], A + g->L.field[cur][3 + c], sizeof(real), g->desc, g->L.pitch, T::BX,
-                                  T::HBY);
-        }
-        void* fbase = g->desc.fluence ? static_cast<void*>(A + g->L.fluence) : static_cast<void*>(A + g->L.field[cur][0]);
-        ok = ok && encode_map(&m.f, fbase, 8, g->desc, g->L.pitch, T::FBX, T::FBY);
-        if (!ok) return false;
-        g->maps_ok[cur][sl] = true;
-    }
-    *out = &g->maps[cur][sl];
-    return true;
-}
-
 template <typename real, int TY, int S>
 static cudaError_t launch_tma(const fdtd_grid* cg, int cur, long long n, int lz, cudaStream_t s)
 {
@@ -323,13 +271,13 @@ cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConf
         if (g->desc.precision == FDTD_F32) {
             switch (tc.ty) {
                 case 4: return launch_tma<float, 4, 6>(g, cur, n, tc.lz, s);
-                case 16: return launch_tma<float, 16, 4>(g, cur, n, tc.lz, s);
-                default: return launch_tma<float, 8, 4>(g, cur, n, tc.lz, s);
+                case 16: return launch_tma<float, 16, 5>(g, cur, n, tc.lz, s);
+                default: return launch_tma<float, 8, 5>(g, cur, n, tc.lz, s);
             }
         } else {
             switch (tc.ty) {
-                case 4: return launch_tma<double, 4, 4>(g, cur, n, tc.lz, s);
-                default: return launch_tma<double, 8, 4>(g, cur, n, tc.lz, s);
+                case 4: return launch_tma<double, 4, 5>(g, cur, n, tc.lz, s);
+                default: return launch_tma<double, 8, 5>(g, cur, n, tc.lz, s);
             }
         }
     }

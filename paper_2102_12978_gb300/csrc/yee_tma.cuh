@@ -110,18 +110,54 @@ struct TmaTile {
     static constexpr uint32_t E_BYTES = uint32_t(BX * EBY * sizeof(real));
     static constexpr uint32_t H_BYTES = uint32_t(BX * HBY * sizeof(real));
     static constexpr uint32_t F_BYTES = uint32_t(FBX * FBY * 8);
-    static constexpr size_t smem_bytes(int S) { return S * STAGE + 12 * size_t(P) * sizeof(real) + S * 8 + 128; }
+    // stages + 3-slot ring of H^{n+1/2} + mbarriers + alignment slack
+    static constexpr size_t smem_bytes(int S) { return S * STAGE + 9 * size_t(P) * sizeof(real) + S * 8 + 128; }
 };
 
-// H^{n+1/2} of one cell from the staged planes (E of planes k and k+1 in
-// box layout, H^{n-1/2} given); updates and optionally stores the H-side psi.
+// Per-column constants of one H cell (own or halo): CPML shell membership,
+// profile values, compact psi offsets, antenna mask.
+template <typename real>
+struct HCol {
+    bool valid;
+    int ci, cj;
+    real chx, chy;
+    bool xs, ys;
+    real bx, ax, by, ay;
+    int pxo, pyo;          // psi offsets within one plane of the x / y shell arrays
+    uint8_t mk;
+};
+
+template <typename real>
+__device__ __forceinline__ HCol<real> make_hcol(const StepArgs<real>& a, int ci, int cj)
+{
+    HCol<real> c;
+    c.valid = ci >= 0 && ci < a.nx && cj >= 0 && cj < a.ny;
+    c.ci = ci; c.cj = cj;
+    c.chx = real(0); c.chy = real(0); c.xs = false; c.ys = false;
+    c.bx = c.ax = c.by = c.ay = real(0); c.pxo = c.pyo = 0; c.mk = 0;
+    if (!c.valid) return c;
+    c.chx = a.chx[ci]; c.chy = a.chy[cj];
+    const int npml = a.npml, w2 = 2 * npml;
+    if (npml > 0 && (ci < npml || ci >= a.nx - npml)) {
+        const int ii = ci < npml ? ci : ci - a.nx + w2;
+        c.xs = true; c.bx = a.bhx[ii]; c.ax = a.ahx[ii]; c.pxo = cj * w2 + ii;
+    }
+    if (npml > 0 && (cj < npml || cj >= a.ny - npml)) {
+        const int jj = cj < npml ? cj : cj - a.ny + w2;
+        c.ys = true; c.by = a.bhy[jj]; c.ay = a.ahy[jj]; c.pyo = jj * a.pitch + ci;
+    }
+    if (a.smask) c.mk = a.smask[cj * a.nx + ci];
+    return c;
+}
+
+// H^{n+1/2} of one cell from the staged E planes k (e0*) and k+1 (e1*).
 template <typename real, int BX>
-__device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const real* __restrict__ e0x,
-                                              const real* __restrict__ e0y, const real* __restrict__ e0z,
-                                              const real* __restrict__ e1x, const real* __restrict__ e1y,
-                                              int idx, int ci, int cj, int kw, real hx, real hy, real hz,
-                                              real chx, real chy, uint8_t mk, const double* tf, bool store,
-                                              real& ohx, real& ohy, real& ohz)
+__device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCol<real>& c,
+                                              const real* __restrict__ e0x, const real* __restrict__ e0y,
+                                              const real* __restrict__ e0z, const real* __restrict__ e1x,
+                                              const real* __restrict__ e1y, int idx, int kw, int psx_plane,
+                                              int psy_plane, real& hx, real& hy, real& hz, const double* tf,
+                                              bool store)
 {
     const real ex = e0x[idx], ey = e0y[idx], ez = e0z[idx];
     const real dEz_y = e0z[idx + BX] - ez;
@@ -130,114 +166,161 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const rea
     const real dEz_x = e0z[idx + 1] - ez;
     const real dEy_x = e0y[idx + 1] - ey;
     const real dEx_y = e0x[idx + BX] - ex;
-    hx = hx - chy * dEz_y + a.cz * dEy_z;
-    hy = hy - a.cz * dEx_z + chx * dEz_x;
-    hz = hz - chx * dEy_x + chy * dEx_y;
-    const int npml = a.npml, nx = a.nx, ny = a.ny;
-    if (npml > 0) {
-        const int w2 = 2 * npml;
-        if (ci < npml || ci >= nx - npml) {
-            const int ii = ci < npml ? ci : ci - nx + w2;
-            const size_t q = (size_t(kw) * ny + cj) * w2 + ii;
-            const real b = a.bhx[ii], aa = a.ahx[ii];
-            const real p0 = b * a.phx_in[0][q] + aa * dEz_x;   // Hyx
-            const real p1 = b * a.phx_in[1][q] + aa * dEy_x;   // Hzx
-            hy += p0;
-            hz -= p1;
-            if (store) { a.phx_out[0][q] = p0; a.phx_out[1][q] = p1; }
-        }
-        if (cj < npml || cj >= ny - npml) {
-            const int jj = cj < npml ? cj : cj - ny + w2;
-            const size_t q = (size_t(kw) * w2 + jj) * a.pitch + ci;
-            const real b = a.bhy[jj], aa = a.ahy[jj];
-            const real p0 = b * a.phy_in[0][q] + aa * dEz_y;   // Hxy
-            const real p1 = b * a.phy_in[1][q] + aa * dEx_y;   // Hzy
-            hx -= p0;
-            hz += p1;
-            if (store) { a.phy_out[0][q] = p0; a.phy_out[1][q] = p1; }
-        }
+    hx = hx - c.chy * dEz_y + a.cz * dEy_z;
+    hy = hy - a.cz * dEx_z + c.chx * dEz_x;
+    hz = hz - c.chx * dEy_x + c.chy * dEx_y;
+    if (c.xs) {
+        const int q = kw * psx_plane + c.pxo;
+        const real p0 = c.bx * a.phx_in[0][q] + c.ax * dEz_x;   // Hyx
+        const real p1 = c.bx * a.phx_in[1][q] + c.ax * dEy_x;   // Hzx
+        hy += p0;
+        hz -= p1;
+        if (store) { a.phx_out[0][q] = p0; a.phx_out[1][q] = p1; }
     }
-    if (mk & 0x38) {
-        const size_t ncol = size_t(nx) * ny, col = size_t(cj) * nx + ci;
+    if (c.ys) {
+        const int q = kw * psy_plane + c.pyo;
+        const real p0 = c.by * a.phy_in[0][q] + c.ay * dEz_y;   // Hxy
+        const real p1 = c.by * a.phy_in[1][q] + c.ay * dEx_y;   // Hzy
+        hx -= p0;
+        hz += p1;
+        if (store) { a.phy_out[0][q] = p0; a.phy_out[1][q] = p1; }
+    }
+    if (c.mk & 0x38) {
+        const int ncol = a.nx * a.ny, col = c.cj * a.nx + c.ci;
         const double2 z = a.zph[kw];
-        if (mk & 0x08) hx += real(source_value(a.scoef[3 * ncol + col], z, tf[3], tf[4], tf[5]));
-        if (mk & 0x10) hy += real(source_value(a.scoef[4 * ncol + col], z, tf[3], tf[4], tf[5]));
-        if (mk & 0x20) hz += real(source_value(a.scoef[5 * ncol + col], z, tf[3], tf[4], tf[5]));
+        if (c.mk & 0x08) hx += real(source_value(a.scoef[3 * ncol + col], z, tf[3], tf[4], tf[5]));
+        if (c.mk & 0x10) hy += real(source_value(a.scoef[4 * ncol + col], z, tf[3], tf[4], tf[5]));
+        if (c.mk & 0x20) hz += real(source_value(a.scoef[5 * ncol + col], z, tf[3], tf[4], tf[5]));
     }
-    ohx = hx; ohy = hy; ohz = hz;
 }
 
-template <typename real, int TY, int S>
-__global__ void __launch_bounds__(32 * TY)
-yee_step_tma(const StepArgs<real> a, const __grid_constant__ TmaMaps m, long long n, int lz, int* err)
+// Fluence term of one cell: |E_c x Hbar_c| dt added to the accumulator.
+// em*/ek*: staged E planes of the cell (k) and of k+1 (box index ce);
+// hm/hk: staged H^{n-1/2} boxes of planes k, k+1 (box index ce, component
+// stride HS); sm/sk: H^{n+1/2} ring slots of planes k, k+1 (ring index cs).
+// The means' factors (1/4 for E, 1/4 for H-bar) are folded into dt16.
+template <typename real, int BX, int PX, int P, int HS>
+__device__ __forceinline__ void tma_fluence_cell(const real* __restrict__ emx, const real* __restrict__ emy,
+                                                 const real* __restrict__ emz, const real* __restrict__ ekx,
+                                                 const real* __restrict__ eky, const real* __restrict__ hm,
+                                                 const real* __restrict__ hk, const real* __restrict__ sm,
+                                                 const real* __restrict__ sk, int ce, int cs,
+                                                 const typename FluAcc<real>::T& fo, real dt16,
+                                                 typename FluAcc<real>::T* F, int g)
 {
-    static_assert(S >= 4, "the ring needs S >= 4 stages (lead of S-2 planes)");
+    const real ex = (emx[ce] + emx[ce + BX]) + (ekx[ce] + ekx[ce + BX]);
+    const real ey = (emy[ce] + emy[ce + 1]) + (eky[ce] + eky[ce + 1]);
+    const real ez = (emz[ce] + emz[ce + 1]) + (emz[ce + BX] + emz[ce + BX + 1]);
+    const real hx = (hm[ce] + sm[cs]) + (hm[ce + 1] + sm[cs + 1]);
+    const real hy = (hm[HS + ce] + sm[P + cs]) + (hm[HS + ce + BX] + sm[P + cs + PX]);
+    const real hz = (hm[2 * HS + ce] + sm[2 * P + cs]) + (hk[2 * HS + ce] + sk[2 * P + cs]);
+    const real sx = ey * hz - ez * hy;
+    const real sy = ez * hx - ex * hz;
+    const real sz = ex * hy - ey * hx;
+    const real mag = sqrt(sx * sx + sy * sy + sz * sz);
+    F[g] = FluAcc<real>::add(fo, mag * dt16);
+}
+
+// Shared memory of one CTA running tma_march.
+template <typename real, int TY, int S>
+struct MarchSmem {
+    unsigned char* base;   // S stages
+    real* sH;              // [3][3][P] ring of H^{n+1/2}
+    uint64_t* bars;        // S mbarriers
+    double* tf;            // 6 time factors
+    int* abort_flag;
+};
+
+// One CTA marches one (32 x TY) x [kb, ke) block of a grid through one Yee
+// step.  gq0 is the CTA's running plane counter (stage = gq % S, mbarrier
+// parity = (gq / S) & 1), so that a persistent CTA can march many blocks
+// with its mbarriers initialised once.  Returns the updated counter, or -1
+// after a timed-out wait (the error word is raised).
+template <typename real, int TY, int S>
+__device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps& m, long long n, int i0, int j0,
+                                         int kb, int ke, int* err, const MarchSmem<real, TY, S>& sm, int gq0)
+{
+    static_assert(S >= 5, "the ring needs S >= 5 stages (lead of S-3 planes)");
     using T = TmaTile<real, TY>;
+    using Acc = FluAcc<real>;
+    using acc_t = typename Acc::T;
     constexpr int TX = T::TX, BX = T::BX, XA = T::XA, PX = T::PX, P = T::P, NT = T::NT, FBX = T::FBX;
     static_assert(T::NHH <= NT, "tile too small for its halo");
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base =
-        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    real* sH = reinterpret_cast<real*>(base + S * T::STAGE);   // [2][3][P]
-    real* sB = sH + 6 * P;                                      // [2][3][P]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + 6 * P);
-    __shared__ double tf[6];
-    __shared__ int abort_flag;
+    unsigned char* base = sm.base;
+    real* sH = sm.sH;
+    uint64_t* bars = sm.bars;
+    double* tf = sm.tf;
+    int& abort_flag = *sm.abort_flag;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int kb = blockIdx.z * lz;
-    const int ke = min(kb + lz, a.nz);
-    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch, npml = a.npml;
-    const size_t plane = size_t(pitch) * ny;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    const int plane = pitch * ny;
+    const int w2 = 2 * a.npml, psx_plane = ny * w2, psy_plane = w2 * pitch;
     const int i = i0 + tx, j = j0 + ty;
     const bool own = (i < nx) && (j < ny);
     const int so = (ty + 1) * PX + (tx + 1);        // own cell in the sH / sB rings
     const int eo = (ty + 1) * BX + (tx + XA);        // own cell in an E / H box
+    const int gcol = j * pitch + i;
     const bool do_flu = a.fluence != nullptr;
-    const int Q = ke - kb + 3;                       // planes kb-1 .. ke+1
+    acc_t* F = static_cast<acc_t*>(a.fluence);
+    const real dtr = real(a.dt);
+    const int Q = ke - kb + 3;                       // E planes kb-1 .. ke+1
 
-    auto stage = [&](int q) { return base + (q % S) * T::STAGE; };
-    auto Ebox = [&](int q, int c) { return reinterpret_cast<real*>(stage(q) + c * T::EB); };
-    auto Hbox = [&](int q, int c) { return reinterpret_cast<real*>(stage(q) + 3 * T::EB + c * T::HB); };
-    auto Fbox = [&](int q) { return reinterpret_cast<double*>(stage(q) + 3 * T::EB + 3 * T::HB); };
+    auto stage = [&](int s) { return base + s * T::STAGE; };
 
+    // ---- TMA producer (thread 0): plane q of this segment into stage q % S
     auto issue = [&](int q) {
         const int p = kb - 1 + q;
-        const int pw = ((p % nz) + nz) % nz;
+        const int pw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
         const bool needH = p <= ke;
         const bool needF = do_flu && p >= kb && p <= ke - 1;
-        uint64_t* bar = &bars[q % S];
+        const int s = (gq0 + q) % S;
+        uint64_t* bar = &bars[s];
+        unsigned char* st = stage(s);
         mbar_expect_tx(bar, 3 * T::E_BYTES + (needH ? 3 * T::H_BYTES : 0u) + (needF ? T::F_BYTES : 0u));
         #pragma unroll
-        for (int c = 0; c < 3; ++c) tma_load_3d(Ebox(q, c), &m.e[c], bar, i0 - XA, j0 - 1, pw);
+        for (int c = 0; c < 3; ++c) tma_load_3d(st + c * T::EB, &m.e[c], bar, i0 - XA, j0 - 1, pw);
         if (needH) {
             #pragma unroll
-            for (int c = 0; c < 3; ++c) tma_load_3d(Hbox(q, c), &m.h[c], bar, i0 - XA, j0 - 1, pw);
+            for (int c = 0; c < 3; ++c) tma_load_3d(st + 3 * T::EB + c * T::HB, &m.h[c], bar, i0 - XA, j0 - 1, pw);
         }
-        if (needF) tma_load_3d(Fbox(q), &m.f, bar, i0 - 2, j0 - 1, pw);
+        if (needF) tma_load_3d(st + 3 * T::EB + 3 * T::HB, &m.f, bar, i0 - 2, j0 - 1, pw);
     };
 
     int issued = 0;
+    __syncthreads();   // the previous block's readers of every stage are done
     if (tid == 0) {
-        abort_flag = 0;
-        #pragma unroll 1
-        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
-        mbar_fence_init();
+        fence_proxy_async();
         double c, s, f;
         source_time(a.st, (double(n) + 0.5) * a.dt, c, s, f);
         tf[3] = c; tf[4] = s; tf[5] = f;
         source_time(a.st, (double(n) + 1.0) * a.dt, c, s, f);
         tf[0] = c; tf[1] = s; tf[2] = f;
     }
-    for (int q = tid; q < 12 * P; q += NT) sH[q] = real(0);   // sH and sB
+    for (int q = tid; q < 9 * P; q += NT) sH[q] = real(0);    // H^{n+1/2} ring
     __syncthreads();
     if (tid == 0) {
-        for (; issued < S - 2 && issued < Q; ++issued) issue(issued);
+        #pragma unroll 1
+        for (; issued < S - 3 && issued < Q; ++issued) issue(issued);
     }
 
-    // H halo cell of this thread: row j0-1 (tid < TX) or column i0-1
-    int hi_h = -1, hj_h = -1, hs_h = 0, he_h = 0;
+    // per-column constants: own cell and this thread's H halo cell
+    const HCol<real> co = make_hcol(a, own ? i : -1, own ? j : -1);
+    const real cex = own ? a.cex[i] : real(0), cey = own ? a.cey[j] : real(0);
+    bool exs = false, eys = false;
+    real ebx = 0, eax = 0, eby = 0, eay = 0;
+    int epx = 0, epy = 0;
+    if (own && w2 > 0) {
+        if (i < a.npml || i >= nx - a.npml) {
+            const int ii = i < a.npml ? i : i - nx + w2;
+            exs = true; ebx = a.bex[ii]; eax = a.aex[ii]; epx = j * w2 + ii;
+        }
+        if (j < a.npml || j >= ny - a.npml) {
+            const int jj = j < a.npml ? j : j - ny + w2;
+            eys = true; eby = a.bey[jj]; eay = a.aey[jj]; epy = jj * pitch + i;
+        }
+    }
+    int hs_h = 0, he_h = 0, hi_h = -1, hj_h = -1;
     if (tid < T::NHH) {
         if (tid < TX) { hi_h = i0 + tid; hj_h = j0 - 1; hs_h = tid + 1; he_h = tid + XA; }
         else {
@@ -245,71 +328,77 @@ yee_step_tma(const StepArgs<real> a, const __grid_constant__ TmaMaps m, long lon
             hi_h = i0 - 1; hj_h = j0 - 1 + jj; hs_h = jj * PX; he_h = jj * BX + XA - 1;
         }
     }
-    const bool halo_h_in = hi_h >= 0 && hi_h < nx && hj_h >= 0 && hj_h < ny;
-    const uint8_t mk_own = (own && a.smask) ? a.smask[size_t(j) * nx + i] : uint8_t(0);
-    const uint8_t mk_hh = (halo_h_in && a.smask) ? a.smask[size_t(hj_h) * nx + hi_h] : uint8_t(0);
-    const real chx_o = own ? a.chx[i] : real(0), chy_o = own ? a.chy[j] : real(0);
-    const real cex_o = own ? a.cex[i] : real(0), cey_o = own ? a.cey[j] : real(0);
-    const real chx_h = halo_h_in ? a.chx[hi_h] : real(0), chy_h = halo_h_in ? a.chy[hj_h] : real(0);
-    const bool xw = (tx == TX - 1) && (i == nx - 1);
-    const bool yw = (ty == TY - 1) && (j == ny - 1);
+    const HCol<real> ch = make_hcol(a, hi_h, hj_h);
+    // fluence cells: base (i-1, j-1) and, in the last tiles, the wall cells
+    const bool flu_base = (i >= 1) && (j >= 1) && (i <= nx) && (j <= ny);
+    const bool xw = (tx == TX - 1) && (i == nx - 1) && (j >= 1) && (j <= ny);
+    const bool yw = (ty == TY - 1) && (j == ny - 1) && (i >= 1) && (i <= nx);
 
-    int waited = -1;   // highest plane this thread has seen complete
+    int waited = -1;
+    int kw = kb - 1 < 0 ? kb - 1 + nz : kb - 1;    // wrapped plane of iteration k
+    int s0 = gq0 % S;                                // stage of plane q
+    uint32_t par = uint32_t((gq0 / S) & 1);          // mbarrier parity of plane q
+    int r0 = 0, r1 = 2, r2 = 1;                      // H-ring slots of q, q-1, q-2
     #pragma unroll 1
-    for (int q = 0; q <= Q - 2; ++q) {
+    for (int q = 0; q <= Q - 1; ++q) {
         const int k = kb - 1 + q;
+        // wait for plane q+1 (and plane 0 on the first pass)
         bool ok = true;
-        if (q == 0) ok = mbar_wait_bounded(&bars[0], 0);
-        ok = ok && mbar_wait_bounded(&bars[(q + 1) % S], uint32_t(((q + 1) / S) & 1));
+        if (q == 0) ok = mbar_wait_bounded(&bars[s0], par);
+        const int s1 = (s0 + 1 == S) ? 0 : s0 + 1;
+        const uint32_t par1 = (s0 + 1 == S) ? (par ^ 1u) : par;
+        if (q + 1 <= Q - 1) ok = ok && mbar_wait_bounded(&bars[s1], par1);
         if (ok) waited = q + 1;
         else { abort_flag = 1; atomicOr(err, 1); }
-        __syncthreads();   // A: planes k, k+1 landed; readers of plane k-2's stage done
+        __syncthreads();   // planes q, q+1 landed; every reader of plane q-3 is done
         if (abort_flag) break;
         if (tid == 0 && issued < Q) { fence_proxy_async(); issue(issued); ++issued; }
 
-        const int kw = ((k % nz) + nz) % nz;
-        const bool write_k = (k >= kb) && (k < ke);
-        const real* e0x = Ebox(q, 0); const real* e0y = Ebox(q, 1); const real* e0z = Ebox(q, 2);
-        const real* e1x = Ebox(q + 1, 0); const real* e1y = Ebox(q + 1, 1);
-        const real* hbx = Hbox(q, 0); const real* hby = Hbox(q, 1); const real* hbz = Hbox(q, 2);
-        real* hs = sH + (k & 1) * 3 * P;
-        real* bs = sB + (k & 1) * 3 * P;
-        if (own) {
-            const real ox = hbx[eo], oy = hby[eo], oz = hbz[eo];
-            real nxh, nyh, nzh;
-            tma_compute_h<real, BX>(a, e0x, e0y, e0z, e1x, e1y, eo, i, j, kw, ox, oy, oz, chx_o, chy_o,
-                                    mk_own, tf, write_k, nxh, nyh, nzh);
-            hs[so] = nxh; hs[P + so] = nyh; hs[2 * P + so] = nzh;
-            bs[so] = real(0.5) * (ox + nxh); bs[P + so] = real(0.5) * (oy + nyh);
-            bs[2 * P + so] = real(0.5) * (oz + nzh);
-            if (write_k) {
-                const size_t g = size_t(kw) * plane + size_t(j) * pitch + i;
-                a.hout[0][g] = nxh; a.hout[1][g] = nyh; a.hout[2][g] = nzh;
-            }
-        } else {
-            hs[so] = real(0); hs[P + so] = real(0); hs[2 * P + so] = real(0);
-            bs[so] = real(0); bs[P + so] = real(0); bs[2 * P + so] = real(0);
-        }
-        if (tid < T::NHH) {
-            if (halo_h_in) {
-                const real ox = hbx[he_h], oy = hby[he_h], oz = hbz[he_h];
-                real nxh, nyh, nzh;
-                tma_compute_h<real, BX>(a, e0x, e0y, e0z, e1x, e1y, he_h, hi_h, hj_h, kw, ox, oy, oz, chx_h,
-                                        chy_h, mk_hh, tf, false, nxh, nyh, nzh);
-                hs[hs_h] = nxh; hs[P + hs_h] = nyh; hs[2 * P + hs_h] = nzh;
-                bs[hs_h] = real(0.5) * (ox + nxh); bs[P + hs_h] = real(0.5) * (oy + nyh);
-                bs[2 * P + hs_h] = real(0.5) * (oz + nzh);
-            } else {
-                hs[hs_h] = real(0); hs[P + hs_h] = real(0); hs[2 * P + hs_h] = real(0);
-                bs[hs_h] = real(0); bs[P + hs_h] = real(0); bs[2 * P + hs_h] = real(0);
-            }
-        }
-        __syncthreads();   // B: H^{n+1/2} of planes k, k-1 and H-bar visible
+        const unsigned char* st0 = stage(s0);
+        const real* e0x = reinterpret_cast<const real*>(st0);
+        const real* e0y = reinterpret_cast<const real*>(st0 + T::EB);
+        const real* e0z = reinterpret_cast<const real*>(st0 + 2 * T::EB);
 
-        if (write_k && own) {
-            const real* h0 = sH + (k & 1) * 3 * P;
-            const real* h1 = sH + ((k - 1) & 1) * 3 * P;
-            const real ex = e0x[eo], ey = e0y[eo], ez = e0z[eo];
+        // ---- H^{n+1/2} of plane k (tile + low halo)
+        if (k <= ke) {
+            const unsigned char* stn = stage(s1);
+            const real* e1x = reinterpret_cast<const real*>(stn);
+            const real* e1y = reinterpret_cast<const real*>(stn + T::EB);
+            const real* hb = reinterpret_cast<const real*>(st0 + 3 * T::EB);
+            constexpr int HS = int(T::HB / sizeof(real));
+            real* hs = sH + r0 * 3 * P;
+            const bool write_k = (k >= kb) && (k < ke);
+            if (co.valid) {
+                const real ox = hb[eo], oy = hb[HS + eo], oz = hb[2 * HS + eo];
+                real hx = ox, hy = oy, hz = oz;
+                tma_compute_h<real, BX>(a, co, e0x, e0y, e0z, e1x, e1y, eo, kw, psx_plane, psy_plane, hx, hy, hz,
+                                        tf, write_k);
+                hs[so] = hx; hs[P + so] = hy; hs[2 * P + so] = hz;
+                if (write_k) {
+                    const int g = kw * plane + gcol;
+                    a.hout[0][g] = hx; a.hout[1][g] = hy; a.hout[2][g] = hz;
+                }
+            }
+            if (ch.valid) {
+                const real ox = hb[he_h], oy = hb[HS + he_h], oz = hb[2 * HS + he_h];
+                real hx = ox, hy = oy, hz = oz;
+                tma_compute_h<real, BX>(a, ch, e0x, e0y, e0z, e1x, e1y, he_h, kw, psx_plane, psy_plane, hx, hy,
+                                        hz, tf, false);
+                hs[hs_h] = hx; hs[P + hs_h] = hy; hs[2 * P + hs_h] = hz;
+            }
+        }
+
+        // ---- E^{n+1} of plane k-1 (needs H^{n+1/2} of planes k-1, k-2)
+        const int km = k - 1;
+        const int kmw = kw == 0 ? nz - 1 : kw - 1;
+        const int sm1 = s0 == 0 ? S - 1 : s0 - 1;
+        if (own && km >= kb && km < ke) {
+            const real* h0 = sH + r1 * 3 * P;
+            const real* h1 = sH + r2 * 3 * P;
+            const unsigned char* stm = stage(sm1);
+            const real ex = reinterpret_cast<const real*>(stm)[eo];
+            const real ey = reinterpret_cast<const real*>(stm + T::EB)[eo];
+            const real ez = reinterpret_cast<const real*>(stm + 2 * T::EB)[eo];
             const real hx0 = h0[so], hy0 = h0[P + so], hz0 = h0[2 * P + so];
             const real dHz_y = hz0 - h0[2 * P + so - PX];
             const real dHy_z = hy0 - h1[P + so];
@@ -317,87 +406,119 @@ yee_step_tma(const StepArgs<real> a, const __grid_constant__ TmaMaps m, long lon
             const real dHz_x = hz0 - h0[2 * P + so - 1];
             const real dHy_x = hy0 - h0[P + so - 1];
             const real dHx_y = hx0 - h0[so - PX];
-            real nex = ex + cey_o * dHz_y - a.cz * dHy_z;
-            real ney = ey + a.cz * dHx_z - cex_o * dHz_x;
-            real nez = ez + cex_o * dHy_x - cey_o * dHx_y;
-            if (npml > 0) {
-                const int w2 = 2 * npml;
-                if (i < npml || i >= nx - npml) {
-                    const int ii = i < npml ? i : i - nx + w2;
-                    const size_t qq = (size_t(kw) * ny + j) * w2 + ii;
-                    const real b = a.bex[ii], aa = a.aex[ii];
-                    const real p0 = b * a.pex[0][qq] + aa * dHz_x;   // Eyx
-                    const real p1 = b * a.pex[1][qq] + aa * dHy_x;   // Ezx
-                    a.pex[0][qq] = p0; a.pex[1][qq] = p1;
-                    ney -= p0;
-                    nez += p1;
-                }
-                if (j < npml || j >= ny - npml) {
-                    const int jj = j < npml ? j : j - ny + w2;
-                    const size_t qq = (size_t(kw) * w2 + jj) * pitch + i;
-                    const real b = a.bey[jj], aa = a.aey[jj];
-                    const real p0 = b * a.pey[0][qq] + aa * dHz_y;   // Exy
-                    const real p1 = b * a.pey[1][qq] + aa * dHx_y;   // Ezy
-                    a.pey[0][qq] = p0; a.pey[1][qq] = p1;
-                    nex += p0;
-                    nez -= p1;
-                }
+            real nex = ex + cey * dHz_y - a.cz * dHy_z;
+            real ney = ey + a.cz * dHx_z - cex * dHz_x;
+            real nez = ez + cex * dHy_x - cey * dHx_y;
+            if (exs) {
+                const int qq = kmw * psx_plane + epx;
+                const real p0 = ebx * a.pex[0][qq] + eax * dHz_x;   // Eyx
+                const real p1 = ebx * a.pex[1][qq] + eax * dHy_x;   // Ezx
+                a.pex[0][qq] = p0; a.pex[1][qq] = p1;
+                ney -= p0;
+                nez += p1;
             }
-            if (mk_own & 0x07) {
-                const size_t ncol = size_t(nx) * ny, col = size_t(j) * nx + i;
-                const double2 z = a.zph[kw];
-                if (mk_own & 0x01) nex += real(source_value(a.scoef[col], z, tf[0], tf[1], tf[2]));
-                if (mk_own & 0x02) ney += real(source_value(a.scoef[ncol + col], z, tf[0], tf[1], tf[2]));
-                if (mk_own & 0x04) nez += real(source_value(a.scoef[2 * ncol + col], z, tf[0], tf[1], tf[2]));
+            if (eys) {
+                const int qq = kmw * psy_plane + epy;
+                const real p0 = eby * a.pey[0][qq] + eay * dHz_y;   // Exy
+                const real p1 = eby * a.pey[1][qq] + eay * dHx_y;   // Ezy
+                a.pey[0][qq] = p0; a.pey[1][qq] = p1;
+                nex += p0;
+                nez -= p1;
+            }
+            if (co.mk & 0x07) {
+                const int ncol = nx * ny, col = j * nx + i;
+                const double2 z = a.zph[kmw];
+                if (co.mk & 0x01) nex += real(source_value(a.scoef[col], z, tf[0], tf[1], tf[2]));
+                if (co.mk & 0x02) ney += real(source_value(a.scoef[ncol + col], z, tf[0], tf[1], tf[2]));
+                if (co.mk & 0x04) nez += real(source_value(a.scoef[2 * ncol + col], z, tf[0], tf[1], tf[2]));
             }
             if (j == 0) { nex = real(0); nez = real(0); }    // PEC: tangential E
             if (i == 0) { ney = real(0); nez = real(0); }
-            const size_t g = size_t(kw) * plane + size_t(j) * pitch + i;
+            const int g = kmw * plane + gcol;
             a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez;
         }
 
-        if (do_flu && k >= kb + 1) {
-            // cells (fi, fj, k-1), fi in {i-1, i at the +x wall}, fj likewise
-            const int km = k - 1;
-            const int kmw = ((km % nz) + nz) % nz;
-            const real* emx = Ebox(q - 1, 0); const real* emy = Ebox(q - 1, 1); const real* emz = Ebox(q - 1, 2);
-            const real* ekx = e0x; const real* eky = e0y;
-            const real* bm = sB + (km & 1) * 3 * P;
-            const real* bk = sB + (k & 1) * 3 * P;
-            using Acc = FluAcc<real>;
-            const typename Acc::T* fo = reinterpret_cast<const typename Acc::T*>(Fbox(q - 1));
-            typename Acc::T* F = static_cast<typename Acc::T*>(a.fluence);
-            const real dtr = real(a.dt);
-            #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                const int di = qq & 1, dj = qq >> 1;
-                if (di && !xw) continue;
-                if (dj && !yw) continue;
-                const int fi = i - 1 + di, fj = j - 1 + dj;
-                if (fi < 0 || fj < 0 || fi >= nx || fj >= ny) continue;
-                const int ce = eo - BX - 1 + dj * BX + di;      // E box index of (fi, fj)
-                const int cs = so - PX - 1 + dj * PX + di;      // sB index of (fi, fj)
-                const int cf = (ty + dj) * FBX + (tx + 1 + di); // fluence box index of (fi, fj)
-                const real ex = real(0.25) * (emx[ce] + emx[ce + BX] + ekx[ce] + ekx[ce + BX]);
-                const real ey = real(0.25) * (emy[ce] + emy[ce + 1] + eky[ce] + eky[ce + 1]);
-                const real ez = real(0.25) * (emz[ce] + emz[ce + 1] + emz[ce + BX] + emz[ce + BX + 1]);
-                const real hx = real(0.5) * (bm[cs] + bm[cs + 1]);
-                const real hy = real(0.5) * (bm[P + cs] + bm[P + cs + PX]);
-                const real hz = real(0.5) * (bm[2 * P + cs] + bk[2 * P + cs]);
-                const real sx = ey * hz - ez * hy;
-                const real sy = ez * hx - ex * hz;
-                const real sz = ex * hy - ey * hx;
-                const real sm = sqrt(sx * sx + sy * sy + sz * sz);
-                const size_t g = size_t(kmw) * plane + size_t(fj) * pitch + fi;
-                F[g] = Acc::add(fo[cf], sm * dtr);
-            }
+        // ---- fluence of plane k-2: E planes k-2, k-1 and H-bar of k-2, k-1
+        const int kf = k - 2;
+        if (do_flu && kf >= kb && kf < ke && (flu_base || xw || yw)) {
+            const int kfw = kmw == 0 ? nz - 1 : kmw - 1;
+            const int sm2 = sm1 == 0 ? S - 1 : sm1 - 1;
+            const unsigned char* sa = stage(sm2);
+            const unsigned char* sb = stage(sm1);
+            const real* emx = reinterpret_cast<const real*>(sa);
+            const real* emy = reinterpret_cast<const real*>(sa + T::EB);
+            const real* emz = reinterpret_cast<const real*>(sa + 2 * T::EB);
+            const real* ekx = reinterpret_cast<const real*>(sb);
+            const real* eky = reinterpret_cast<const real*>(sb + T::EB);
+            const acc_t* fo = reinterpret_cast<const acc_t*>(sa + 3 * T::EB + 3 * T::HB);
+            const real* hm = reinterpret_cast<const real*>(sa + 3 * T::EB);
+            const real* hk = reinterpret_cast<const real*>(sb + 3 * T::EB);
+            const real* sm = sH + r2 * 3 * P;
+            const real* sk = sH + r1 * 3 * P;
+            constexpr int HS = int(T::HB / sizeof(real));
+            const real dt16 = dtr * real(0.0625);
+            const int gp = kfw * plane;
+            if (flu_base)
+                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo - BX - 1,
+                                                      so - PX - 1, fo[ty * FBX + tx + 1], dt16, F,
+                                                      gp + gcol - pitch - 1);
+            if (xw)
+                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo - BX, so - PX,
+                                                      fo[ty * FBX + tx + 2], dt16, F, gp + gcol - pitch);
+            if (yw)
+                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo - 1, so - 1,
+                                                      fo[(ty + 1) * FBX + tx + 1], dt16, F, gp + gcol - 1);
+            if (xw && yw)
+                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo, so,
+                                                      fo[(ty + 1) * FBX + tx + 2], dt16, F, gp + gcol);
         }
+
+        // rotate stage, parity and H-ring slots
+        if (s0 + 1 == S) par ^= 1u;
+        s0 = s1;
+        r2 = r1; r1 = r0; r0 = (r0 == 2) ? 0 : r0 + 1;
+        kw = (kw + 1 == nz) ? 0 : kw + 1;
     }
     // drain: after an abort, wait (bounded) for the copies issued but never
     // waited for, so that no TMA write lands after the CTA has exited
-    if (tid == 0 && abort_flag) {
-        for (int q = waited + 1; q < issued; ++q) mbar_wait_bounded(&bars[q % S], uint32_t((q / S) & 1));
+    if (abort_flag) {
+        if (tid == 0)
+            for (int q = waited + 1; q < issued; ++q)
+                mbar_wait_bounded(&bars[(gq0 + q) % S], uint32_t(((gq0 + q) / S) & 1));
+        return -1;
     }
+    return gq0 + Q;
+}
+
+template <typename real, int TY, int S>
+__device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init()
+{
+    using T = TmaTile<real, TY>;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ double tf[6];
+    __shared__ int abort_flag;
+    MarchSmem<real, TY, S> sm;
+    sm.base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    sm.sH = reinterpret_cast<real*>(sm.base + S * T::STAGE);
+    sm.bars = reinterpret_cast<uint64_t*>(sm.sH + 9 * T::P);
+    sm.tf = tf;
+    sm.abort_flag = &abort_flag;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        abort_flag = 0;
+        #pragma unroll 1
+        for (int s = 0; s < S; ++s) mbar_init(&sm.bars[s], 1);
+        mbar_fence_init();
+    }
+    return sm;
+}
+
+template <typename real, int TY, int S>
+__global__ void __launch_bounds__(32 * TY)
+yee_step_tma(const StepArgs<real> a, const __grid_constant__ TmaMaps m, long long n, int lz, int* err)
+{
+    const MarchSmem<real, TY, S> sm = march_smem_init<real, TY, S>();
+    const int kb = blockIdx.z * lz;
+    tma_march<real, TY, S>(a, m, n, blockIdx.x * 32, blockIdx.y * TY, kb, min(kb + lz, a.nz), err, sm, 0);
 }
 
 }  // namespace fdtd
