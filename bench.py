@@ -210,6 +210,9 @@ def run_gpu(args):
     # ---- end to end through the public API with host buffers --------------
     e2e = run_e2e(torch, fdtd, w, dev, args.steps, barrier, ws)
 
+    # ---- batched sweep: 16 uneven grids, one persistent launch per step ----
+    batched = run_batched(torch, fdtd, W, dev, args.batch_steps) if args.batch_steps > 0 else None
+
     del g32, g64
     out = {
         "metric": METRIC, "value": round(gcell32, 3), "unit": UNIT, "n_gpus": ws,
@@ -232,6 +235,7 @@ def run_gpu(args):
         "l2_error": {"f32_vs_f64_gpu_rel_l2_fields": f32_vs_f64, "after_steps": n_cmp,
                      "f64_vs_oracle_tol": 1e-11, "f32_vs_oracle_tol": 1e-4},
         "e2e": e2e,
+        "batched": batched,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -242,6 +246,59 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_batched(torch, fdtd, W, dev, steps):
+    """The 16-configuration sweep (l in 0..3 x theta in 5, 10, 20, 30 deg,
+    N^2 x 64 grids with N = 96 .. 640): all grids advanced by one
+    graph-replayed persistent launch per step, against the same grids stepped
+    one launch per grid per step."""
+    ws_ = W.config4()
+
+    def make(wl):
+        d = fdtd.make_grid_desc(wl.nx, wl.ny, wl.nz, wl.npml, wl.dx, wl.dx, wl.dz, courant=wl.courant,
+                                precision="f32", fluence=True)
+        g = fdtd.Grid(d, device=dev)
+        g.set_source(m=wl.m, theta=wl.theta, pol=wl.pol, r_center=wl.r_center, thickness=wl.thickness,
+                     ramp=wl.ramp)
+        return g
+
+    cells = sum(wl.cells for wl in ws_)
+    seq = [make(wl) for wl in ws_]
+    for g in seq:
+        g.step(2)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    stream = seq[0].stream
+    e0.record(stream)
+    for _ in range(steps):
+        for g in seq:
+            g.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_seq = e0.elapsed_time(e1)
+    for g in seq:
+        g.close()
+    del seq
+    bat = [make(wl) for wl in ws_]
+    b = fdtd.Batch(bat)
+    b.step(64)                 # warm-up, builds the graph
+    b.sync()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    b.sync()
+    ms_bat = e0.elapsed_time(e1)
+    items = b.work_items
+    b.close()
+    for g in bat:
+        g.close()
+    return {"value": round(cells * steps / (ms_bat * 1e-3) / 1e9, 3), "unit": UNIT,
+            "sequential_value": round(cells * steps / (ms_seq * 1e-3) / 1e9, 3),
+            "speedup_vs_sequential": round(ms_seq / ms_bat, 3), "grids": len(ws_), "cells": cells,
+            "steps": steps, "work_items": items, "ms_per_step": round(ms_bat / steps, 4),
+            "sequential_ms_per_step": round(ms_seq / steps, 4)}
 
 
 def run_e2e(torch, fdtd, w, dev, steps, barrier, ws):
@@ -342,6 +399,8 @@ def main():
     ap.add_argument("--only", default="all", choices=["all", "f32", "f64"],
                     help="time only one precision (profiling runs)")
     ap.add_argument("--tile", default=None, help="variant,ty,lz for --only runs")
+    ap.add_argument("--batch-steps", type=int, default=128,
+                    help="steps of the 16-grid batched sweep (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

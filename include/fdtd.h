@@ -195,6 +195,25 @@ fdtd_status fdtd_sync(fdtd_grid* g);
 
 void fdtd_destroy_grid(fdtd_grid* g);
 
+/* ---- Batched stepping of many independent grids --------------------------
+ * Several grids (any sizes, sources, cone angles; one precision; all created
+ * on the current device and at the same step parity) advance together: one
+ * persistent kernel launch per step walks every grid's (tile, z segment)
+ * blocks, and K = 64 consecutive steps are replayed from one CUDA graph.
+ * The per-grid arithmetic is exactly fdtd_step's.  `dev_table` is a device
+ * buffer of fdtd_batch_required_bytes bytes (256-byte aligned), owned by the
+ * caller and alive until fdtd_batch_destroy; `stream` is a cudaStream_t.  A
+ * grid in a batch must not be stepped on its own until the batch is
+ * destroyed (ESTATE otherwise).  fdtd_batch_sync waits for the stream and
+ * reports CUDA errors or an expired device wait (ETIMEOUT). */
+size_t fdtd_batch_required_bytes(int n_grids, int precision);
+fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, size_t table_bytes, void* stream,
+                              fdtd_batch** out);
+fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps);
+fdtd_status fdtd_batch_sync(fdtd_batch* b);
+int fdtd_batch_work_items(const fdtd_batch* b);
+void fdtd_batch_destroy(fdtd_batch* b);
+
 /* Host-only: the per-column source coefficients A_c (see fdtd_annulus_desc)
  * without weights, evaluated at z = 0 and at z = dz/2 as appropriate for the
  * component, into out[6][ny][nx] complex doubles (re, im interleaved:

@@ -73,6 +73,7 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
     for (int q = 0; q < 8; ++q) L.prof[q] = take((w2 ? w2 : 1) * b);
     L.smask = take(nx * ny);
     L.scoef = take(6 * nx * ny * 16);
+    L.scoef32 = take(6 * nx * ny * 8);
     L.zph = take(2 * nz * 16);
     L.flu_out = d.fluence ? take(nz * ny * nx * 8) : 0;
     L.err = take(256);
@@ -217,6 +218,7 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
     a.fluence = g->desc.fluence ? static_cast<void*>(A + L.fluence) : nullptr;
     a.smask = g->has_source ? reinterpret_cast<const uint8_t*>(A + L.smask) : nullptr;
     a.scoef = reinterpret_cast<const double2*>(A + L.scoef);
+    a.scoefr = sizeof(real) == 8 ? static_cast<const void*>(A + L.scoef) : static_cast<const void*>(A + L.scoef32);
     a.zph = reinterpret_cast<const double2*>(A + L.zph);
     a.st = g->srct;
     return a;
@@ -249,19 +251,20 @@ static cudaError_t launch_tma(const fdtd_grid* cg, int cur, long long n, int lz,
 {
     fdtd_grid* g = const_cast<fdtd_grid*>(cg);
     using T = TmaTile<real, TY>;
-    static bool attr_set = false;
-    if (!attr_set) {
+    const size_t smem = T::smem_bytes(S, lz);
+    static size_t attr_set = 0;
+    if (smem > attr_set) {
         cudaError_t e = cudaFuncSetAttribute(yee_step_tma<real, TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(T::smem_bytes(S)));
+                                             int(smem));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set = smem;
     }
     TmaMaps* m = nullptr;
     if (!tma_maps<real, TY>(g, cur, &m)) return cudaErrorInvalidValue;
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, (g->desc.nz + lz - 1) / lz);
     int* err = reinterpret_cast<int*>(static_cast<char*>(g->arena) + g->L.err);
-    yee_step_tma<real, TY, S><<<grid, block, T::smem_bytes(S), s>>>(make_args<real>(g, cur), *m, n, lz, err);
+    yee_step_tma<real, TY, S><<<grid, block, smem, s>>>(make_args<real>(g, cur), *m, n, lz, err);
     return cudaGetLastError();
 }
 
@@ -410,6 +413,14 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     char* A = static_cast<char*>(g->arena);
     fdtd_status st = cuda_check(cudaMemcpyAsync(A + g->L.scoef, coef.data(), coef.size() * 16,
                                                 cudaMemcpyHostToDevice, g->stream), "upload source");
+    std::vector<float> coef32(2 * coef.size());
+    for (size_t q = 0; q < coef.size(); ++q) {
+        coef32[2 * q] = float(coef[q].real());
+        coef32[2 * q + 1] = float(coef[q].imag());
+    }
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.scoef32, coef32.data(), coef32.size() * 4, cudaMemcpyHostToDevice,
+                                        g->stream), "upload source");
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(A + g->L.smask, mask.data(), mask.size(), cudaMemcpyHostToDevice,
                                         g->stream), "upload source");

@@ -64,7 +64,8 @@ struct StepArgs {
     void* fluence;           // [nz][ny][pitch] accumulator or null: double (FP64
                              // grids) or float2 (sum, Kahan compensation) (FP32)
     const uint8_t* smask;    // [ny][nx] or null (no source)
-    const double2* scoef;    // [6][ny][nx]
+    const double2* scoef;    // [6][ny][nx]  FP64 antenna coefficients
+    const void* scoefr;      // the same in the field precision (float2 / double2)
     const double2* zph;      // [nz]: e^{i beta k dz} (coefficients carry the half-cell z offset)
     SrcTime st;
 };

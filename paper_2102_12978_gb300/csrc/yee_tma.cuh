@@ -97,7 +97,8 @@ struct TmaTile {
     static constexpr int XA = 16 / int(sizeof(real));   // x alignment in elements
     static constexpr int BX = TX + 2 * XA;              // E / H box width
     static constexpr int EBY = TY + 2;                  // E box rows (j0-1 .. j0+TY)
-    static constexpr int HBY = TY + 1;                  // H box rows (j0-1 .. j0+TY-1)
+    static constexpr int HBY = TY + 2;                  // H box rows (j0-1 .. j0+TY; the last row
+                                                        // is read only at the +y wall, as zeros)
     static constexpr int FBX = TX + 2, FBY = TY + 1;    // fluence box (i0-2 .., j0-1 ..)
     static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
     static constexpr size_t EB = al(size_t(BX) * EBY * sizeof(real));
@@ -110,9 +111,15 @@ struct TmaTile {
     static constexpr uint32_t E_BYTES = uint32_t(BX * EBY * sizeof(real));
     static constexpr uint32_t H_BYTES = uint32_t(BX * HBY * sizeof(real));
     static constexpr uint32_t F_BYTES = uint32_t(FBX * FBY * 8);
-    // stages + 3-slot ring of H^{n+1/2} + mbarriers + alignment slack
-    static constexpr size_t smem_bytes(int S) { return S * STAGE + 9 * size_t(P) * sizeof(real) + S * 8 + 128; }
+    // stages + 3-slot ring of H^{n+1/2} + per-plane source factors (E and H
+    // times, lz + 3 planes) + mbarriers + alignment slack
+    static constexpr size_t smem_bytes(int S, int lz)
+    {
+        return S * STAGE + 9 * size_t(P) * sizeof(real) + 2 * size_t(lz + 3) * 2 * sizeof(real) + S * 8 + 128;
+    }
 };
+
+template <typename real> struct Cpx { real x, y; };
 
 // Per-column constants of one H cell (own or halo): CPML shell membership,
 // profile values, compact psi offsets, antenna mask.
@@ -156,7 +163,7 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
                                               const real* __restrict__ e0x, const real* __restrict__ e0y,
                                               const real* __restrict__ e0z, const real* __restrict__ e1x,
                                               const real* __restrict__ e1y, int idx, int kw, int psx_plane,
-                                              int psy_plane, real& hx, real& hy, real& hz, const double* tf,
+                                              int psy_plane, real& hx, real& hy, real& hz, Cpx<real> u,
                                               bool store)
 {
     const real ex = e0x[idx], ey = e0y[idx], ez = e0z[idx];
@@ -186,11 +193,12 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
         if (store) { a.phy_out[0][q] = p0; a.phy_out[1][q] = p1; }
     }
     if (c.mk & 0x38) {
+        // soft source: Re{ B u }, u = f e^{i (beta z_k - Phi)} of this plane
         const int ncol = a.nx * a.ny, col = c.cj * a.nx + c.ci;
-        const double2 z = a.zph[kw];
-        if (c.mk & 0x08) hx += real(source_value(a.scoef[3 * ncol + col], z, tf[3], tf[4], tf[5]));
-        if (c.mk & 0x10) hy += real(source_value(a.scoef[4 * ncol + col], z, tf[3], tf[4], tf[5]));
-        if (c.mk & 0x20) hz += real(source_value(a.scoef[5 * ncol + col], z, tf[3], tf[4], tf[5]));
+        const Cpx<real>* B = static_cast<const Cpx<real>*>(a.scoefr);
+        if (c.mk & 0x08) { const Cpx<real> b = B[3 * ncol + col]; hx += b.x * u.x - b.y * u.y; }
+        if (c.mk & 0x10) { const Cpx<real> b = B[4 * ncol + col]; hy += b.x * u.x - b.y * u.y; }
+        if (c.mk & 0x20) { const Cpx<real> b = B[5 * ncol + col]; hz += b.x * u.x - b.y * u.y; }
     }
 }
 
@@ -226,6 +234,8 @@ template <typename real, int TY, int S>
 struct MarchSmem {
     unsigned char* base;   // S stages
     real* sH;              // [3][3][P] ring of H^{n+1/2}
+    Cpx<real>* uE;         // per-plane source factor at the E time, lz + 3 planes
+    Cpx<real>* uH;         // the same at the H time
     uint64_t* bars;        // S mbarriers
     double* tf;            // 6 time factors
     int* abort_flag;
@@ -303,6 +313,21 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         #pragma unroll 1
         for (; issued < S - 3 && issued < Q; ++issued) issue(issued);
     }
+    // source factors f e^{i (beta z_k - omega t')} of every plane of this
+    // block, phase in FP64, stored in the field precision (read after the
+    // first barrier of the march)
+    if (a.smask) {
+        for (int q = tid; q < Q; q += NT) {
+            const int p = kb - 1 + q;
+            const int pw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+            const double2 z = a.zph[pw];
+            // z (c - i s) f
+            sm.uE[q].x = real((z.x * tf[0] + z.y * tf[1]) * tf[2]);
+            sm.uE[q].y = real((z.y * tf[0] - z.x * tf[1]) * tf[2]);
+            sm.uH[q].x = real((z.x * tf[3] + z.y * tf[4]) * tf[5]);
+            sm.uH[q].y = real((z.y * tf[3] - z.x * tf[4]) * tf[5]);
+        }
+    }
 
     // per-column constants: own cell and this thread's H halo cell
     const HCol<real> co = make_hcol(a, own ? i : -1, own ? j : -1);
@@ -372,7 +397,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                 const real ox = hb[eo], oy = hb[HS + eo], oz = hb[2 * HS + eo];
                 real hx = ox, hy = oy, hz = oz;
                 tma_compute_h<real, BX>(a, co, e0x, e0y, e0z, e1x, e1y, eo, kw, psx_plane, psy_plane, hx, hy, hz,
-                                        tf, write_k);
+                                        sm.uH[q], write_k);
                 hs[so] = hx; hs[P + so] = hy; hs[2 * P + so] = hz;
                 if (write_k) {
                     const int g = kw * plane + gcol;
@@ -383,7 +408,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                 const real ox = hb[he_h], oy = hb[HS + he_h], oz = hb[2 * HS + he_h];
                 real hx = ox, hy = oy, hz = oz;
                 tma_compute_h<real, BX>(a, ch, e0x, e0y, e0z, e1x, e1y, he_h, kw, psx_plane, psy_plane, hx, hy,
-                                        hz, tf, false);
+                                        hz, sm.uH[q], false);
                 hs[hs_h] = hx; hs[P + hs_h] = hy; hs[2 * P + hs_h] = hz;
             }
         }
@@ -427,10 +452,11 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             }
             if (co.mk & 0x07) {
                 const int ncol = nx * ny, col = j * nx + i;
-                const double2 z = a.zph[kmw];
-                if (co.mk & 0x01) nex += real(source_value(a.scoef[col], z, tf[0], tf[1], tf[2]));
-                if (co.mk & 0x02) ney += real(source_value(a.scoef[ncol + col], z, tf[0], tf[1], tf[2]));
-                if (co.mk & 0x04) nez += real(source_value(a.scoef[2 * ncol + col], z, tf[0], tf[1], tf[2]));
+                const Cpx<real>* B = static_cast<const Cpx<real>*>(a.scoefr);
+                const Cpx<real> u = sm.uE[q - 1];
+                if (co.mk & 0x01) { const Cpx<real> b = B[col]; nex += b.x * u.x - b.y * u.y; }
+                if (co.mk & 0x02) { const Cpx<real> b = B[ncol + col]; ney += b.x * u.x - b.y * u.y; }
+                if (co.mk & 0x04) { const Cpx<real> b = B[2 * ncol + col]; nez += b.x * u.x - b.y * u.y; }
             }
             if (j == 0) { nex = real(0); nez = real(0); }    // PEC: tangential E
             if (i == 0) { ney = real(0); nez = real(0); }
@@ -491,7 +517,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
 }
 
 template <typename real, int TY, int S>
-__device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init()
+__device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init(int lz)
 {
     using T = TmaTile<real, TY>;
     extern __shared__ unsigned char smem_raw[];
@@ -500,7 +526,9 @@ __device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init()
     MarchSmem<real, TY, S> sm;
     sm.base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     sm.sH = reinterpret_cast<real*>(sm.base + S * T::STAGE);
-    sm.bars = reinterpret_cast<uint64_t*>(sm.sH + 9 * T::P);
+    sm.uE = reinterpret_cast<Cpx<real>*>(sm.sH + 9 * T::P);
+    sm.uH = sm.uE + (lz + 3);
+    sm.bars = reinterpret_cast<uint64_t*>(sm.uH + (lz + 3));
     sm.tf = tf;
     sm.abort_flag = &abort_flag;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -512,11 +540,17 @@ __device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init()
     return sm;
 }
 
+// Minimum resident CTAs per SM requested from the register allocator: the
+// FP32 32x8 tile fits three CTAs in shared memory, so cap its registers.
+template <typename real, int TY> struct MinCtas { static constexpr int value = 1; };
+template <> struct MinCtas<float, 8> { static constexpr int value = 3; };
+template <> struct MinCtas<float, 4> { static constexpr int value = 4; };
+
 template <typename real, int TY, int S>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, MinCtas<real, TY>::value)
 yee_step_tma(const StepArgs<real> a, const __grid_constant__ TmaMaps m, long long n, int lz, int* err)
 {
-    const MarchSmem<real, TY, S> sm = march_smem_init<real, TY, S>();
+    const MarchSmem<real, TY, S> sm = march_smem_init<real, TY, S>(lz);
     const int kb = blockIdx.z * lz;
     tma_march<real, TY, S>(a, m, n, blockIdx.x * 32, blockIdx.y * TY, kb, min(kb + lz, a.nz), err, sm, 0);
 }

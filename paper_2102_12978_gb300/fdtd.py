@@ -74,6 +74,13 @@ _SIGS = {
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
+    "fdtd_batch_required_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "fdtd_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
+    "fdtd_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "fdtd_batch_sync": (C.c_int, [C.c_void_p]),
+    "fdtd_batch_work_items": (C.c_int, [C.c_void_p]),
+    "fdtd_batch_destroy": (None, [C.c_void_p]),
     "fdtd_source_coefficients": (C.c_int, [C.POINTER(fdtd_grid_desc), C.POINTER(fdtd_annulus_desc),
                                            C.c_void_p, C.c_void_p]),
     "fdtd_bessel_j": (C.c_double, [C.c_int, C.c_double]),
@@ -292,6 +299,50 @@ class Grid:
     def close(self):
         if getattr(self, "handle", None):
             lib().fdtd_destroy_grid(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Grid objects advanced together by the persistent, graph-replayed
+    batched step (fdtd_batch_*)."""
+
+    def __init__(self, grids):
+        import torch
+        self.torch = torch
+        self.grids = list(grids)
+        g0 = self.grids[0]
+        n = len(self.grids)
+        nbytes = int(lib().fdtd_batch_required_bytes(n, g0.desc.precision))
+        if nbytes == 0:
+            check(FDTD_EINVAL, "fdtd_batch_required_bytes")
+        self.table = torch.empty(nbytes + 256, dtype=torch.uint8, device=g0.device)
+        ptr = self.table.data_ptr()
+        ptr += (-ptr) % 256
+        arr = (C.c_void_p * n)(*[g.handle for g in self.grids])
+        h = C.c_void_p()
+        check(lib().fdtd_batch_create(arr, n, C.c_void_p(ptr), nbytes, C.c_void_p(g0.stream.cuda_stream),
+                                      C.byref(h)), "fdtd_batch_create")
+        self.handle = h.value
+
+    def step(self, n: int = 1):
+        check(lib().fdtd_batch_step(C.c_void_p(self.handle), int(n)), "fdtd_batch_step")
+
+    def sync(self):
+        check(lib().fdtd_batch_sync(C.c_void_p(self.handle)), "fdtd_batch_sync")
+
+    @property
+    def work_items(self) -> int:
+        return int(lib().fdtd_batch_work_items(C.c_void_p(self.handle)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fdtd_batch_destroy(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,73 @@
+"""Batched stepping of several uneven grids in one persistent, graph-replayed
+launch per step: each grid must match its own sequential run bit for bit, and
+the FP64 oracle within the parity tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_12978_gb300 import fdtd
+from paper_2102_12978_gb300 import workloads as W
+from tests.cases import oracle_grid, oracle_source, rel_l2
+from tests.gpu_cases import gpu_grid, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    return [
+        W.small(nx=48, ny=40, nz=16, npml=6, r_center=11.0, m=0, theta_deg=20.0, ramp=1.0),
+        W.small(nx=64, ny=64, nz=8, npml=8, r_center=14.0, m=2, theta_deg=30.0, pol="circ+", ramp=1.0),
+        W.small(nx=37, ny=45, nz=12, npml=6, r_center=9.0, m=1, theta_deg=10.0, pol="x", ramp=1.0),
+        W.small(nx=96, ny=33, nz=5, npml=6, r_center=8.0, m=3, theta_deg=25.0, ramp=1.0),
+    ]
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_batched_equals_sequential_bitwise(precision):
+    """130 steps = two replays of the 64-step graph plus a 2-step remainder."""
+    ws = _cases()
+    ty = 8 if precision == "f32" else 4
+    seq = [gpu_grid(w, precision, tile=(1, ty, 32)) for w in ws]
+    bat = [gpu_grid(w, precision) for w in ws]
+    b = fdtd.Batch(bat)
+    assert b.work_items > 0
+    nsteps = 130
+    for g in seq:
+        g.step(nsteps)
+    b.step(nsteps)
+    b.sync()
+    for gs, gb in zip(seq, bat):
+        assert gb.n == gs.n == nsteps
+        for c in range(6):
+            assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
+        assert np.array_equal(host(gs.fluence()), host(gb.fluence()))
+    b.close()
+
+
+def test_batched_matches_oracle_f64():
+    ws = _cases()
+    grids = [gpu_grid(w, "f64") for w in ws]
+    b = fdtd.Batch(grids)
+    nsteps = 70
+    b.step(nsteps)
+    b.sync()
+    for w, g in zip(ws, grids):
+        og, os_ = oracle_grid(w), oracle_source(w)
+        st = oracle.State(og)
+        oracle.run(og, os_, st, nsteps)
+        for c, ref in enumerate(st.fields()):
+            assert rel_l2(host(g.field(c)), ref) <= 1e-11, (w.name, c)
+        assert rel_l2(host(g.fluence()), st.fluence) <= 1e-11
+    b.close()
+
+
+def test_batched_grid_cannot_step_alone():
+    ws = _cases()[:2]
+    grids = [gpu_grid(w, "f32") for w in ws]
+    b = fdtd.Batch(grids)
+    b.step(3)
+    grids[0].step(1)          # the grid's parity now differs from the batch's
+    with pytest.raises(fdtd.FDTDError) as e:
+        b.step(1)
+    assert e.value.status == fdtd.FDTD_ESTATE
+    b.close()
