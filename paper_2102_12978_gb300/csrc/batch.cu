@@ -60,13 +60,13 @@ yee_batch_tma(BatchHeader* __restrict__ hdr, const BatchGrid<real>* __restrict__
         const int* src = reinterpret_cast<const int*>(&G.args[parity]);
         int* dst = reinterpret_cast<int*>(sargs_raw);
         for (int w = tid; w < int(sizeof(StepArgs<real>) / 4); w += 32 * TY) dst[w] = src[w];
+        __syncthreads();   // publish the copied arguments before tma_march reads them
         int local = item - G.item0;
         const int bz = local % G.nseg;
         local /= G.nseg;
         const int bx = local % G.ntx, by = local / G.ntx;
         const int kb = bz * G.lz;
         const int nz = G.args[parity].nz;
-        // tma_march opens with a barrier, which publishes the copied arguments
         gq = tma_march<real, TY, S>(sa, G.maps[parity], G.step0 + done + offset, bx * 32, by * TY, kb,
                                     min(kb + G.lz, nz), &hdr->err, sm, gq);
         if (gq < 0) return;

@@ -121,6 +121,12 @@ struct TmaTile {
 
 template <typename real> struct Cpx { real x, y; };
 
+// |S| from |S|^2: FP64 grids take the correctly rounded square root; FP32
+// grids take x * rsqrt(x) (a few ulp, far inside the FP32 tolerance of the
+// fluence), which avoids the long correctly-rounded sequence per cell.
+__device__ __forceinline__ double vec_norm(double x) { return sqrt(x); }
+__device__ __forceinline__ float vec_norm(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+
 // Per-column constants of one H cell (own or halo): CPML shell membership,
 // profile values, compact psi offsets, antenna mask.
 template <typename real>
@@ -164,7 +170,7 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
                                               const real* __restrict__ e0z, const real* __restrict__ e1x,
                                               const real* __restrict__ e1y, int idx, int kw, int psx_plane,
                                               int psy_plane, real& hx, real& hy, real& hz, Cpx<real> u,
-                                              bool store)
+                                              bool store, const real (&pp)[4])
 {
     const real ex = e0x[idx], ey = e0y[idx], ez = e0z[idx];
     const real dEz_y = e0z[idx + BX] - ez;
@@ -178,16 +184,16 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
     hz = hz - c.chx * dEy_x + c.chy * dEx_y;
     if (c.xs) {
         const int q = kw * psx_plane + c.pxo;
-        const real p0 = c.bx * a.phx_in[0][q] + c.ax * dEz_x;   // Hyx
-        const real p1 = c.bx * a.phx_in[1][q] + c.ax * dEy_x;   // Hzx
+        const real p0 = c.bx * pp[0] + c.ax * dEz_x;   // Hyx (old value prefetched)
+        const real p1 = c.bx * pp[1] + c.ax * dEy_x;   // Hzx
         hy += p0;
         hz -= p1;
         if (store) { a.phx_out[0][q] = p0; a.phx_out[1][q] = p1; }
     }
     if (c.ys) {
         const int q = kw * psy_plane + c.pyo;
-        const real p0 = c.by * a.phy_in[0][q] + c.ay * dEz_y;   // Hxy
-        const real p1 = c.by * a.phy_in[1][q] + c.ay * dEx_y;   // Hzy
+        const real p0 = c.by * pp[2] + c.ay * dEz_y;   // Hxy
+        const real p1 = c.by * pp[3] + c.ay * dEx_y;   // Hzy
         hx -= p0;
         hz += p1;
         if (store) { a.phy_out[0][q] = p0; a.phy_out[1][q] = p1; }
@@ -225,8 +231,7 @@ __device__ __forceinline__ void tma_fluence_cell(const real* __restrict__ emx, c
     const real sx = ey * hz - ez * hy;
     const real sy = ez * hx - ex * hz;
     const real sz = ex * hy - ey * hx;
-    const real mag = sqrt(sx * sx + sy * sy + sz * sz);
-    F[g] = FluAcc<real>::add(fo, mag * dt16);
+    F[g] = FluAcc<real>::add(fo, vec_norm(sx * sx + sy * sy + sz * sz) * dt16);
 }
 
 // Shared memory of one CTA running tma_march.
@@ -263,6 +268,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     int& abort_flag = *sm.abort_flag;
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+    constexpr int PRODUCER = (TY - 1) * 32;          // lane 0 of the last warp issues TMA
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
     const int plane = pitch * ny;
     const int w2 = 2 * a.npml, psx_plane = ny * w2, psy_plane = w2 * pitch;
@@ -299,8 +305,8 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
 
     int issued = 0;
     __syncthreads();   // the previous block's readers of every stage are done
+    if (tid == PRODUCER) fence_proxy_async();
     if (tid == 0) {
-        fence_proxy_async();
         double c, s, f;
         source_time(a.st, (double(n) + 0.5) * a.dt, c, s, f);
         tf[3] = c; tf[4] = s; tf[5] = f;
@@ -309,7 +315,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     }
     for (int q = tid; q < 9 * P; q += NT) sH[q] = real(0);    // H^{n+1/2} ring
     __syncthreads();
-    if (tid == 0) {
+    if (tid == PRODUCER) {
         #pragma unroll 1
         for (; issued < S - 3 && issued < Q; ++issued) issue(issued);
     }
@@ -345,19 +351,43 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             eys = true; eby = a.bey[jj]; eay = a.aey[jj]; epy = jj * pitch + i;
         }
     }
+    // halo H cells: the row j0-1 on warp 0, the column i0-1 (TY+1 cells) on
+    // warp TY/2, so that no warp carries both; the TMA producer is lane 0 of
+    // warp TY-1
     int hs_h = 0, he_h = 0, hi_h = -1, hj_h = -1;
-    if (tid < T::NHH) {
-        if (tid < TX) { hi_h = i0 + tid; hj_h = j0 - 1; hs_h = tid + 1; he_h = tid + XA; }
-        else {
-            const int jj = tid - TX;
-            hi_h = i0 - 1; hj_h = j0 - 1 + jj; hs_h = jj * PX; he_h = jj * BX + XA - 1;
-        }
+    if (ty == 0) { hi_h = i0 + tx; hj_h = j0 - 1; hs_h = tx + 1; he_h = tx + XA; }
+    else if (ty == TY / 2 && tx <= TY) {
+        const int jj = tx;
+        hi_h = i0 - 1; hj_h = j0 - 1 + jj; hs_h = jj * PX; he_h = jj * BX + XA - 1;
     }
     const HCol<real> ch = make_hcol(a, hi_h, hj_h);
     // fluence cells: base (i-1, j-1) and, in the last tiles, the wall cells
     const bool flu_base = (i >= 1) && (j >= 1) && (i <= nx) && (j <= ny);
     const bool xw = (tx == TX - 1) && (i == nx - 1) && (j >= 1) && (j <= ny);
     const bool yw = (ty == TY - 1) && (j == ny - 1) && (i >= 1) && (i <= nx);
+
+    // CPML psi of the next plane, prefetched into registers one iteration ahead
+    // (H side: own and halo cell, read copy; E side: own cell, updated in place)
+    real ppo[4] = {0, 0, 0, 0}, pph[4] = {0, 0, 0, 0}, ppe[4] = {0, 0, 0, 0};
+    auto fetch_psi_h = [&](const HCol<real>& c, int plane_w, real (&pp)[4]) {
+        if (c.xs) {
+            const int q = plane_w * psx_plane + c.pxo;
+            pp[0] = a.phx_in[0][q]; pp[1] = a.phx_in[1][q];
+        }
+        if (c.ys) {
+            const int q = plane_w * psy_plane + c.pyo;
+            pp[2] = a.phy_in[0][q]; pp[3] = a.phy_in[1][q];
+        }
+    };
+    auto fetch_psi_e = [&](int plane_w) {
+        if (exs) { const int q = plane_w * psx_plane + epx; ppe[0] = a.pex[0][q]; ppe[1] = a.pex[1][q]; }
+        if (eys) { const int q = plane_w * psy_plane + epy; ppe[2] = a.pey[0][q]; ppe[3] = a.pey[1][q]; }
+    };
+    {
+        const int k0w = kb - 1 < 0 ? kb - 1 + nz : kb - 1;
+        fetch_psi_h(co, k0w, ppo);
+        fetch_psi_h(ch, k0w, pph);
+    }
 
     int waited = -1;
     int kw = kb - 1 < 0 ? kb - 1 + nz : kb - 1;    // wrapped plane of iteration k
@@ -377,7 +407,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         else { abort_flag = 1; atomicOr(err, 1); }
         __syncthreads();   // planes q, q+1 landed; every reader of plane q-3 is done
         if (abort_flag) break;
-        if (tid == 0 && issued < Q) { fence_proxy_async(); issue(issued); ++issued; }
+        if (tid == PRODUCER && issued < Q) { fence_proxy_async(); issue(issued); ++issued; }
 
         const unsigned char* st0 = stage(s0);
         const real* e0x = reinterpret_cast<const real*>(st0);
@@ -397,7 +427,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                 const real ox = hb[eo], oy = hb[HS + eo], oz = hb[2 * HS + eo];
                 real hx = ox, hy = oy, hz = oz;
                 tma_compute_h<real, BX>(a, co, e0x, e0y, e0z, e1x, e1y, eo, kw, psx_plane, psy_plane, hx, hy, hz,
-                                        sm.uH[q], write_k);
+                                        sm.uH[q], write_k, ppo);
                 hs[so] = hx; hs[P + so] = hy; hs[2 * P + so] = hz;
                 if (write_k) {
                     const int g = kw * plane + gcol;
@@ -408,7 +438,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                 const real ox = hb[he_h], oy = hb[HS + he_h], oz = hb[2 * HS + he_h];
                 real hx = ox, hy = oy, hz = oz;
                 tma_compute_h<real, BX>(a, ch, e0x, e0y, e0z, e1x, e1y, he_h, kw, psx_plane, psy_plane, hx, hy,
-                                        hz, sm.uH[q], false);
+                                        hz, sm.uH[q], false, pph);
                 hs[hs_h] = hx; hs[P + hs_h] = hy; hs[2 * P + hs_h] = hz;
             }
         }
@@ -436,16 +466,16 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             real nez = ez + cex * dHy_x - cey * dHx_y;
             if (exs) {
                 const int qq = kmw * psx_plane + epx;
-                const real p0 = ebx * a.pex[0][qq] + eax * dHz_x;   // Eyx
-                const real p1 = ebx * a.pex[1][qq] + eax * dHy_x;   // Ezx
+                const real p0 = ebx * ppe[0] + eax * dHz_x;   // Eyx (old value prefetched)
+                const real p1 = ebx * ppe[1] + eax * dHy_x;   // Ezx
                 a.pex[0][qq] = p0; a.pex[1][qq] = p1;
                 ney -= p0;
                 nez += p1;
             }
             if (eys) {
                 const int qq = kmw * psy_plane + epy;
-                const real p0 = eby * a.pey[0][qq] + eay * dHz_y;   // Exy
-                const real p1 = eby * a.pey[1][qq] + eay * dHx_y;   // Ezy
+                const real p0 = eby * ppe[2] + eay * dHz_y;   // Exy
+                const real p1 = eby * ppe[3] + eay * dHx_y;   // Ezy
                 a.pey[0][qq] = p0; a.pey[1][qq] = p1;
                 nex += p0;
                 nez -= p1;
@@ -499,6 +529,13 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                                                       fo[(ty + 1) * FBX + tx + 2], dt16, F, gp + gcol);
         }
 
+        // prefetch psi for the next iteration: H at plane k+1, E at plane k
+        {
+            const int kn = (kw + 1 == nz) ? 0 : kw + 1;
+            fetch_psi_h(co, kn, ppo);
+            fetch_psi_h(ch, kn, pph);
+            fetch_psi_e(kw);
+        }
         // rotate stage, parity and H-ring slots
         if (s0 + 1 == S) par ^= 1u;
         s0 = s1;
@@ -508,7 +545,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     // drain: after an abort, wait (bounded) for the copies issued but never
     // waited for, so that no TMA write lands after the CTA has exited
     if (abort_flag) {
-        if (tid == 0)
+        if (tid == PRODUCER)
             for (int q = waited + 1; q < issued; ++q)
                 mbar_wait_bounded(&bars[(gq0 + q) % S], uint32_t(((gq0 + q) / S) & 1));
         return -1;
