@@ -86,6 +86,9 @@ def lib():
             L.or_source_time.argtypes = [C.POINTER(_Source), C.c_double, dp, dp, dp]
             L.or_run.restype = C.c_int
             L.or_run.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(_State), C.c_long, C.c_int]
+            L.or_adjoint_step.restype = C.c_int
+            L.or_adjoint_step.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(_State), C.c_long,
+                                          dp, dp]
             L.or_antenna_counts.restype = C.c_int
             L.or_antenna_counts.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(C.c_long)]
             _lib = L
@@ -217,6 +220,23 @@ def run(grid: Grid, source: Source | None, state: State, nsteps: int) -> State:
         raise RuntimeError(f"oracle run failed ({rc})")
     state.n += nsteps
     return state
+
+
+def adjoint_step(grid: Grid, source: Source | None, adj: State, n: int, grad_amp=None, grad_phase=None):
+    """One reverse step: the exact transpose of forward step n applied to the
+    adjoint state `adj` (adjoints of E^{n+1}, H^{n+1/2}, psi on entry; of
+    E^n, H^{n-1/2}, psi on return).  grad_amp / grad_phase (ny, nx) arrays
+    accumulate dL/dw of the source terms of step n."""
+    dp = C.POINTER(C.c_double)
+    g = grid._c()
+    s = source._c() if source is not None else None
+    st = adj._c()
+    ga = grad_amp.ctypes.data_as(dp) if grad_amp is not None else dp()
+    gp = grad_phase.ctypes.data_as(dp) if grad_phase is not None else dp()
+    rc = lib().or_adjoint_step(C.byref(g), C.byref(s) if s is not None else None, C.byref(st), int(n), ga, gp)
+    if rc != 0:
+        raise RuntimeError("oracle adjoint step failed")
+    return adj
 
 
 def source_field(source: Source, x: float, y: float, z: float):

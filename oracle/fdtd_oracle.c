@@ -427,6 +427,8 @@ static void update_e(const or_grid *g, or_state *s)
                     double dHy_dz = (at(g, Hy, i, j, k) - at(g, Hy, i, j, k - 1)) / g->dz;
                     s->psi_e[0][id] = bye * s->psi_e[0][id] + aye * dHz_dy;
                     Ex[id] += dt * ((dHz_dy / kye + s->psi_e[0][id]) - dHy_dz);
+                } else {
+                    Ex[id] = 0.0;   /* PEC: tangential E on the y = 0 wall */
                 }
                 /* Ey at (i, j+1/2, k): dHx/dz - dHz/dx ; tangential to x = 0 at i = 0 */
                 if (i > 0) {
@@ -434,6 +436,8 @@ static void update_e(const or_grid *g, or_state *s)
                     double dHz_dx = (at(g, Hz, i, j, k) - at(g, Hz, i - 1, j, k)) / g->dx;
                     s->psi_e[2][id] = bxe * s->psi_e[2][id] + axe * dHz_dx;
                     Ey[id] += dt * (dHx_dz - (dHz_dx / kxe + s->psi_e[2][id]));
+                } else {
+                    Ey[id] = 0.0;   /* PEC: tangential E on the x = 0 wall */
                 }
                 /* Ez at (i, j, k+1/2): dHy/dx - dHx/dy ; tangential to both walls */
                 if (i > 0 && j > 0) {
@@ -442,6 +446,8 @@ static void update_e(const or_grid *g, or_state *s)
                     s->psi_e[3][id] = bxe * s->psi_e[3][id] + axe * dHy_dx;
                     s->psi_e[1][id] = bye * s->psi_e[1][id] + aye * dHx_dy;
                     Ez[id] += dt * ((dHy_dx / kxe + s->psi_e[3][id]) - (dHx_dy / kye + s->psi_e[1][id]));
+                } else {
+                    Ez[id] = 0.0;   /* PEC: tangential on both walls */
                 }
             }
         }
@@ -524,5 +530,182 @@ int or_antenna_counts(const or_grid *g, const or_source *src, long counts[6])
     if (or_antenna_build(g, src, &ant) != 0) { or_antenna_free(&ant); return -1; }
     for (int c = 0; c < 6; ++c) counts[c] = ant.npts[c];
     or_antenna_free(&ant);
+    return 0;
+}
+
+/* ------------------------------------------------------------- adjoint */
+
+/* Derivatives of the value added at one antenna point with respect to its
+ * column's amplitude and phase weights (s = f Re{ w e^{i phi_w} A e^{-i Phi} }). */
+static void src_dweights(const or_source *s, const or_point *p, double cphi, double sphi, double f,
+                         double *ds_damp, double *ds_dphase)
+{
+    double wa = s->w_amp ? s->w_amp[p->col] : 1.0;
+    double wp = s->w_phase ? s->w_phase[p->col] : 0.0;
+    double zre = cos(wp) * p->are - sin(wp) * p->aim;   /* e^{i phi_w} A */
+    double zim = cos(wp) * p->aim + sin(wp) * p->are;
+    *ds_damp = f * (zre * cphi + zim * sphi);
+    *ds_dphase = f * wa * (-zim * cphi + zre * sphi);
+}
+
+static void source_grad(const or_antenna *ant, const or_state *adj, int first, double t,
+                        double *grad_amp, double *grad_phase)
+{
+    double cphi, sphi, f;
+    or_source_time(&ant->src, t, &cphi, &sphi, &f);
+    for (int c = first; c < first + 3; ++c) {
+        const double *lam = (c < 3) ? adj->e[c] : adj->h[c - 3];
+        for (long q = 0; q < ant->npts[c]; ++q) {
+            const or_point *p = &ant->pts[c][q];
+            double da, dp;
+            src_dweights(&ant->src, p, cphi, sphi, f, &da, &dp);
+            if (grad_amp) grad_amp[p->col] += lam[p->idx] * da;
+            if (grad_phase) grad_phase[p->col] += lam[p->idx] * dp;
+        }
+    }
+}
+
+/* add v at (i, j, k) unless (i, j) lies on the virtual +x / +y wall; k wraps */
+static inline void acc(const or_grid *g, double *f, long i, long j, long k, double v)
+{
+    if (i >= g->nx || j >= g->ny || i < 0 || j < 0) return;
+    k = ((k % g->nz) + g->nz) % g->nz;
+    f[IDX(g, i, j, k)] += v;
+}
+
+/* Transpose of update_e: adjoint of E^{n+1} (adj->e), of psi_E^{n+1}
+ * (adj->psi_e) -> contributions to the adjoint of H^{n+1/2} (adj->h); psi_E
+ * adjoint carried back to step n.  The adjoint of E passes through unchanged. */
+static void adjoint_update_e(const or_grid *g, or_state *adj)
+{
+    double dt = g->dt;
+    or_prof px, py;
+    prof_build(g, 0, 0, &px);
+    prof_build(g, 1, 0, &py);
+    for (long k = 0; k < g->nz; ++k)
+        for (long j = 0; j < g->ny; ++j)
+            for (long i = 0; i < g->nx; ++i) {
+                long id = IDX(g, i, j, k);
+                double bye = py.b[j], aye = py.a[j], kye = py.kappa[j];
+                double bxe = px.b[i], axe = px.a[i], kxe = px.kappa[i];
+                if (j > 0) {   /* Ex */
+                    double e = adj->e[0][id];
+                    double ps = adj->psi_e[0][id] + dt * e;
+                    double gzy = dt / kye * e + aye * ps;   /* on dHz/dy */
+                    double gyz = -dt * e;                  /* on dHy/dz */
+                    acc(g, adj->h[2], i, j, k, gzy / g->dy);
+                    acc(g, adj->h[2], i, j - 1, k, -gzy / g->dy);
+                    acc(g, adj->h[1], i, j, k, gyz / g->dz);
+                    acc(g, adj->h[1], i, j, k - 1, -gyz / g->dz);
+                    adj->psi_e[0][id] = bye * ps;
+                }
+                if (i > 0) {   /* Ey */
+                    double e = adj->e[1][id];
+                    double ps = adj->psi_e[2][id] - dt * e;
+                    double gzx = -dt / kxe * e + axe * ps;  /* on dHz/dx */
+                    double gxz = dt * e;                    /* on dHx/dz */
+                    acc(g, adj->h[2], i, j, k, gzx / g->dx);
+                    acc(g, adj->h[2], i - 1, j, k, -gzx / g->dx);
+                    acc(g, adj->h[0], i, j, k, gxz / g->dz);
+                    acc(g, adj->h[0], i, j, k - 1, -gxz / g->dz);
+                    adj->psi_e[2][id] = bxe * ps;
+                }
+                if (i > 0 && j > 0) {   /* Ez */
+                    double e = adj->e[2][id];
+                    double psx = adj->psi_e[3][id] + dt * e;
+                    double psy = adj->psi_e[1][id] - dt * e;
+                    double gyx = dt / kxe * e + axe * psx;   /* on dHy/dx */
+                    double gxy = -dt / kye * e + aye * psy;  /* on dHx/dy */
+                    acc(g, adj->h[1], i, j, k, gyx / g->dx);
+                    acc(g, adj->h[1], i - 1, j, k, -gyx / g->dx);
+                    acc(g, adj->h[0], i, j, k, gxy / g->dy);
+                    acc(g, adj->h[0], i, j - 1, k, -gxy / g->dy);
+                    adj->psi_e[3][id] = bxe * psx;
+                    adj->psi_e[1][id] = bye * psy;
+                }
+            }
+    prof_free(&px);
+    prof_free(&py);
+}
+
+/* Transpose of update_h: adjoint of H^{n+1/2} and psi_H^{n+1/2} ->
+ * contributions to the adjoint of E^n; psi_H adjoint carried back. */
+static void adjoint_update_h(const or_grid *g, or_state *adj)
+{
+    double dt = g->dt;
+    or_prof px, py;
+    prof_build(g, 0, 1, &px);
+    prof_build(g, 1, 1, &py);
+    for (long k = 0; k < g->nz; ++k)
+        for (long j = 0; j < g->ny; ++j)
+            for (long i = 0; i < g->nx; ++i) {
+                long id = IDX(g, i, j, k);
+                double byh = py.b[j], ayh = py.a[j], kyh = py.kappa[j];
+                double bxh = px.b[i], axh = px.a[i], kxh = px.kappa[i];
+                {   /* Hx */
+                    double h = adj->h[0][id];
+                    double ps = adj->psi_h[0][id] - dt * h;
+                    double gzy = -dt / kyh * h + ayh * ps;   /* on dEz/dy */
+                    double gyz = dt * h;                    /* on dEy/dz */
+                    acc(g, adj->e[2], i, j + 1, k, gzy / g->dy);
+                    acc(g, adj->e[2], i, j, k, -gzy / g->dy);
+                    acc(g, adj->e[1], i, j, k + 1, gyz / g->dz);
+                    acc(g, adj->e[1], i, j, k, -gyz / g->dz);
+                    adj->psi_h[0][id] = byh * ps;
+                }
+                {   /* Hy */
+                    double h = adj->h[1][id];
+                    double ps = adj->psi_h[2][id] + dt * h;
+                    double gzx = dt / kxh * h + axh * ps;    /* on dEz/dx */
+                    double gxz = -dt * h;                   /* on dEx/dz */
+                    acc(g, adj->e[2], i + 1, j, k, gzx / g->dx);
+                    acc(g, adj->e[2], i, j, k, -gzx / g->dx);
+                    acc(g, adj->e[0], i, j, k + 1, gxz / g->dz);
+                    acc(g, adj->e[0], i, j, k, -gxz / g->dz);
+                    adj->psi_h[2][id] = bxh * ps;
+                }
+                {   /* Hz */
+                    double h = adj->h[2][id];
+                    double psx = adj->psi_h[3][id] - dt * h;
+                    double psy = adj->psi_h[1][id] + dt * h;
+                    double gyx = -dt / kxh * h + axh * psx;  /* on dEy/dx */
+                    double gxy = dt / kyh * h + ayh * psy;   /* on dEx/dy */
+                    acc(g, adj->e[1], i + 1, j, k, gyx / g->dx);
+                    acc(g, adj->e[1], i, j, k, -gyx / g->dx);
+                    acc(g, adj->e[0], i, j + 1, k, gxy / g->dy);
+                    acc(g, adj->e[0], i, j, k, -gxy / g->dy);
+                    adj->psi_h[3][id] = bxh * psx;
+                    adj->psi_h[1][id] = byh * psy;
+                }
+            }
+    prof_free(&px);
+    prof_free(&py);
+}
+
+/* One reverse step: the exact transpose of forward step n (E^n, H^{n-1/2},
+ * psi -> E^{n+1}, H^{n+1/2}, psi), applied to the adjoint state `adj`
+ * (adjoints of E^{n+1}, H^{n+1/2} and psi on entry; of E^n, H^{n-1/2} and
+ * psi on return), accumulating dL/dw_amp and dL/dw_phase (nx*ny each, may be
+ * NULL) from the source terms of step n.  The caller adds dL/dE^{n+1} to
+ * adj->e before the call. */
+int or_adjoint_step(const or_grid *g, const or_source *src, or_state *adj, long n,
+                    double *grad_amp, double *grad_phase)
+{
+    or_antenna ant;
+    int have = src != NULL;
+    if (have && or_antenna_build(g, src, &ant) != 0) { or_antenna_free(&ant); return -1; }
+    /* PEC: E^{n+1} on the walls is forced to zero, so nothing flows back from it */
+    for (long k = 0; k < g->nz; ++k)
+        for (long j = 0; j < g->ny; ++j)
+            for (long i = 0; i < g->nx; ++i) {
+                long id = IDX(g, i, j, k);
+                if (j == 0) { adj->e[0][id] = 0.0; adj->e[2][id] = 0.0; }
+                if (i == 0) { adj->e[1][id] = 0.0; adj->e[2][id] = 0.0; }
+            }
+    if (have) source_grad(&ant, adj, 0, (n + 1.0) * g->dt, grad_amp, grad_phase);
+    adjoint_update_e(g, adj);
+    if (have) source_grad(&ant, adj, 3, (n + 0.5) * g->dt, grad_amp, grad_phase);
+    adjoint_update_h(g, adj);
+    if (have) or_antenna_free(&ant);
     return 0;
 }
