@@ -120,6 +120,7 @@ typedef struct {
 
 typedef struct fdtd_grid fdtd_grid;
 typedef struct fdtd_batch fdtd_batch;
+typedef struct fdtd_adjoint fdtd_adjoint;
 
 /* Fill *d with the defaults (courant 0.95, CPML constants above, F32, fluence on). */
 void fdtd_grid_desc_default(fdtd_grid_desc* d);
@@ -213,6 +214,47 @@ fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps);
 fdtd_status fdtd_batch_sync(fdtd_batch* b);
 int fdtd_batch_work_items(const fdtd_batch* b);
 void fdtd_batch_destroy(fdtd_batch* b);
+
+/* ---- Reverse-time adjoint -------------------------------------------------
+ * Gradient of a loss L(E) with respect to the antenna's per-column amplitude
+ * and phase weights (fdtd_annulus_desc.w_amp / w_phase).  The forward step is
+ * linear in the state and in the weighted source coefficients; the adjoint
+ * applies the exact transpose of the discrete step (CPML and PEC included)
+ * backwards in time.  The paper computes no gradients: this is the transpose
+ * of the method's discrete update.
+ *
+ * The adjoint holds its own state (adjoints of E, H and of the CPML psi, two
+ * copies each) and a per-(component, column) accumulator in a caller-owned
+ * device arena of fdtd_adjoint_required_bytes bytes.  `probe_cells` (host,
+ * n_probes linear cell indices (k*ny + j)*nx + i) are the points of E
+ * component `component` (FDTD_EX..FDTD_EZ) at which the loss reads E.
+ *
+ *   fdtd_probe_read     forward field at the probes from the grid's current
+ *                       state (device buffer of n_probes field-precision
+ *                       values); asynchronous.
+ *   fdtd_adjoint_reset  zero the adjoint state and gradient and place the
+ *                       adjoint at forward step n_end (the adjoint of
+ *                       E^{n_end}, H^{n_end - 1/2}).
+ *   fdtd_adjoint_step   nsteps reverse steps.  Before reversing forward step
+ *                       m -> m+1 (m = position - 1 - r), row r of dLdE (device,
+ *                       field precision, row stride ld elements, n_probes
+ *                       values) is added at the probes as dL/dE^{m+1}; NULL
+ *                       injects nothing.  The source terms of every reversed
+ *                       step enter the weight gradient.
+ *   fdtd_adjoint_gradient  dL/dw_amp and dL/dw_phase per column (nx*ny
+ *                       doubles each, host or device); synchronises.
+ *   fdtd_adjoint_get    copy one adjoint component (0..2 E, 3..5 H) to a
+ *                       dense device array; synchronises. */
+size_t fdtd_adjoint_required_bytes(const fdtd_grid* g, int64_t n_probes);
+fdtd_status fdtd_adjoint_create(fdtd_grid* g, int component, const int64_t* probe_cells, int64_t n_probes,
+                                void* arena, size_t bytes, fdtd_adjoint** out);
+fdtd_status fdtd_adjoint_reset(fdtd_adjoint* a, int64_t n_end);
+fdtd_status fdtd_probe_read(fdtd_adjoint* a, void* dev_out);
+fdtd_status fdtd_adjoint_step(fdtd_adjoint* a, int nsteps, const void* dLdE, int64_t ld);
+int64_t fdtd_adjoint_position(const fdtd_adjoint* a);
+fdtd_status fdtd_adjoint_get(fdtd_adjoint* a, int component, void* dst);
+fdtd_status fdtd_adjoint_gradient(fdtd_adjoint* a, double* dLdw_amp, double* dLdw_phase, int on_device);
+void fdtd_adjoint_destroy(fdtd_adjoint* a);
 
 /* Host-only: the per-column source coefficients A_c (see fdtd_annulus_desc)
  * without weights, evaluated at z = 0 and at z = dz/2 as appropriate for the

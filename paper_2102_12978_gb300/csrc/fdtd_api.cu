@@ -74,6 +74,9 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
     L.smask = take(nx * ny);
     L.scoef = take(6 * nx * ny * 16);
     L.scoef32 = take(6 * nx * ny * 8);
+    L.scoef_unw = take(6 * nx * ny * 16);
+    L.wamp = take(nx * ny * 8);
+    L.wphase = take(nx * ny * 8);
     L.zph = take(2 * nz * 16);
     L.flu_out = d.fluence ? take(nz * ny * nx * 8) : 0;
     L.err = take(256);
@@ -401,10 +404,16 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     if (s->envelope == FDTD_ENV_CW_SIN2 && s->ramp < 0.0) return fail(FDTD_EINVAL, "ramp must be >= 0");
     GridSpec gs{d.nx, d.ny, d.nz, d.npml, d.dx, d.dy, d.dz, g->dt};
     SourceSpec ss{s->m, s->theta, s->pol, s->mode, s->E0, s->r_center, s->thickness, s->inject};
-    std::vector<std::complex<double>> coef;
+    std::vector<std::complex<double>> coef, coef_unw;
     std::vector<uint8_t> mask;
     int64_t counts[6];
-    source_tables(gs, ss, s->w_amp, s->w_phase, coef, mask, counts);
+    source_tables(gs, ss, nullptr, nullptr, coef_unw, mask, counts);
+    const size_t ncol = size_t(d.nx) * d.ny;
+    std::vector<double> wamp(ncol, 1.0), wph(ncol, 0.0);
+    if (s->w_amp) std::memcpy(wamp.data(), s->w_amp, ncol * 8);
+    if (s->w_phase) std::memcpy(wph.data(), s->w_phase, ncol * 8);
+    coef.resize(coef_unw.size());
+    for (size_t q = 0; q < coef_unw.size(); ++q) coef[q] = std::polar(wamp[q % ncol], wph[q % ncol]) * coef_unw[q];
     // e^{i beta k dz}: the coefficients already carry each component's own
     // half-cell z offset, so one table serves every component
     const double beta = 2.0 * M_PI * std::cos(s->theta);
@@ -424,6 +433,15 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(A + g->L.smask, mask.data(), mask.size(), cudaMemcpyHostToDevice,
                                         g->stream), "upload source");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.scoef_unw, coef_unw.data(), coef_unw.size() * 16,
+                                        cudaMemcpyHostToDevice, g->stream), "upload source");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.wamp, wamp.data(), ncol * 8, cudaMemcpyHostToDevice, g->stream),
+                        "upload source");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.wphase, wph.data(), ncol * 8, cudaMemcpyHostToDevice, g->stream),
+                        "upload source");
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(A + g->L.zph, zph.data(), zph.size() * 16, cudaMemcpyHostToDevice,
                                         g->stream), "upload source");

@@ -23,6 +23,7 @@ struct Layout {
     size_t chx = 0, cex = 0, chy = 0, cey = 0;
     size_t prof[8] = {};   // bhx ahx bex aex bhy ahy bey aey
     size_t smask = 0, scoef = 0, scoef32 = 0, zph = 0;
+    size_t scoef_unw = 0, wamp = 0, wphase = 0;   // unweighted coefficients and the weights
     size_t flu_out = 0;    // dense FP64 export of the fluence
     size_t err = 0;        // device error word (int)
     size_t total = 0;

@@ -81,6 +81,16 @@ _SIGS = {
     "fdtd_batch_sync": (C.c_int, [C.c_void_p]),
     "fdtd_batch_work_items": (C.c_int, [C.c_void_p]),
     "fdtd_batch_destroy": (None, [C.c_void_p]),
+    "fdtd_adjoint_required_bytes": (C.c_size_t, [C.c_void_p, C.c_int64]),
+    "fdtd_adjoint_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t,
+                                      C.POINTER(C.c_void_p)]),
+    "fdtd_adjoint_reset": (C.c_int, [C.c_void_p, C.c_int64]),
+    "fdtd_probe_read": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fdtd_adjoint_step": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "fdtd_adjoint_position": (C.c_int64, [C.c_void_p]),
+    "fdtd_adjoint_get": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fdtd_adjoint_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "fdtd_adjoint_destroy": (None, [C.c_void_p]),
     "fdtd_source_coefficients": (C.c_int, [C.POINTER(fdtd_grid_desc), C.POINTER(fdtd_annulus_desc),
                                            C.c_void_p, C.c_void_p]),
     "fdtd_bessel_j": (C.c_double, [C.c_int, C.c_double]),
@@ -343,6 +353,79 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             lib().fdtd_batch_destroy(C.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Adjoint:
+    """Reverse-time adjoint of a Grid (fdtd_adjoint_*): probes of one E
+    component, loss-gradient injection, and dL/dw per antenna column."""
+
+    def __init__(self, grid: Grid, component: int, probe_cells):
+        import torch
+        self.torch = torch
+        self.grid = grid
+        cells = np.ascontiguousarray(np.asarray(probe_cells, dtype=np.int64).ravel())
+        self.n_probes = int(cells.size)
+        nbytes = int(lib().fdtd_adjoint_required_bytes(C.c_void_p(grid.handle), self.n_probes))
+        if nbytes == 0:
+            check(FDTD_EINVAL, "fdtd_adjoint_required_bytes")
+        self.arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=grid.device)
+        ptr = self.arena.data_ptr()
+        ptr += (-ptr) % 256
+        h = C.c_void_p()
+        check(lib().fdtd_adjoint_create(C.c_void_p(grid.handle), int(component), cells.ctypes.data,
+                                        self.n_probes, C.c_void_p(ptr), nbytes, C.byref(h)), "fdtd_adjoint_create")
+        self.handle = h.value
+        self.component = component
+
+    def probe_read(self, out=None):
+        if out is None:
+            out = self.torch.empty(self.n_probes, dtype=self.grid.dtype, device=self.grid.device)
+        check(lib().fdtd_probe_read(C.c_void_p(self.handle), C.c_void_p(out.data_ptr())), "fdtd_probe_read")
+        return out
+
+    def reset(self, n_end: int):
+        check(lib().fdtd_adjoint_reset(C.c_void_p(self.handle), int(n_end)), "fdtd_adjoint_reset")
+
+    def step(self, nsteps: int, dLdE=None):
+        """nsteps reverse steps; dLdE (nsteps, n_probes) device tensor of the
+        grid's precision, row r = dL/dE at the (r+1)-th latest state, or None."""
+        if dLdE is None:
+            check(lib().fdtd_adjoint_step(C.c_void_p(self.handle), int(nsteps), None, 0), "fdtd_adjoint_step")
+        else:
+            t = dLdE.to(self.grid.dtype).contiguous()
+            assert t.shape[0] >= nsteps and t.shape[1] == self.n_probes
+            check(lib().fdtd_adjoint_step(C.c_void_p(self.handle), int(nsteps), C.c_void_p(t.data_ptr()),
+                                          self.n_probes), "fdtd_adjoint_step")
+            self._keep = t
+
+    @property
+    def position(self) -> int:
+        return int(lib().fdtd_adjoint_position(C.c_void_p(self.handle)))
+
+    def field(self, comp: int):
+        out = self.torch.empty(self.grid.shape, dtype=self.grid.dtype, device=self.grid.device)
+        check(lib().fdtd_adjoint_get(C.c_void_p(self.handle), int(comp), C.c_void_p(out.data_ptr())),
+              "fdtd_adjoint_get")
+        return out
+
+    def gradient(self):
+        d = self.grid.desc
+        ga = self.torch.empty((d.ny, d.nx), dtype=self.torch.float64, device=self.grid.device)
+        gp = self.torch.empty((d.ny, d.nx), dtype=self.torch.float64, device=self.grid.device)
+        check(lib().fdtd_adjoint_gradient(C.c_void_p(self.handle), C.c_void_p(ga.data_ptr()),
+                                          C.c_void_p(gp.data_ptr()), 1), "fdtd_adjoint_gradient")
+        return ga, gp
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fdtd_adjoint_destroy(C.c_void_p(self.handle))
             self.handle = None
 
     def __del__(self):
