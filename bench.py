@@ -213,6 +213,9 @@ def run_gpu(args):
     # ---- batched sweep: 16 uneven grids, one persistent launch per step ----
     batched = run_batched(torch, fdtd, W, dev, args.batch_steps) if args.batch_steps > 0 else None
 
+    # ---- adjoint: 384x384x96 FP32 reverse steps ---------------------------
+    adjoint = run_adjoint(torch, fdtd, W, dev, args.adjoint_steps) if args.adjoint_steps > 0 else None
+
     del g32, g64
     out = {
         "metric": METRIC, "value": round(gcell32, 3), "unit": UNIT, "n_gpus": ws,
@@ -236,6 +239,7 @@ def run_gpu(args):
                      "f64_vs_oracle_tol": 1e-11, "f32_vs_oracle_tol": 1e-4},
         "e2e": e2e,
         "batched": batched,
+        "adjoint": adjoint,
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
@@ -299,6 +303,44 @@ def run_batched(torch, fdtd, W, dev, steps):
             "speedup_vs_sequential": round(ms_seq / ms_bat, 3), "grids": len(ws_), "cells": cells,
             "steps": steps, "work_items": items, "ms_per_step": round(ms_bat / steps, 4),
             "sequential_ms_per_step": round(ms_seq / steps, 4)}
+
+
+def run_adjoint(torch, fdtd, W, dev, steps):
+    """Seconds per reverse (adjoint) step and per forward step on the
+    384 x 384 x 96 FP32 adjoint workload (3-cell ring, 16-cell CPML); one
+    checkpointed gradient costs a forward, a recomputing forward and an
+    adjoint step per step."""
+    import numpy as np
+    wl = W.config5()
+    d = fdtd.make_grid_desc(wl.nx, wl.ny, wl.nz, wl.npml, wl.dx, wl.dx, wl.dz, courant=wl.courant,
+                            precision="f32", fluence=False)
+    g = fdtd.Grid(d, device=dev)
+    g.set_source(m=wl.m, theta=wl.theta, pol=wl.pol, r_center=wl.r_center, thickness=wl.thickness,
+                 ramp=wl.ramp)
+    g.autotune(steps=3)
+    g.step(steps + 8)
+    i = np.arange(wl.nx)[None, :]
+    j = np.arange(wl.ny)[:, None]
+    r0 = 0.383 / np.sin(wl.theta) / wl.dx
+    cols = np.flatnonzero((np.hypot(i - wl.nx / 2, j + 0.5 - wl.ny / 2) < 3 * r0).ravel())
+    probes = (np.arange(wl.nz)[:, None] * (wl.nx * wl.ny) + cols[None, :]).ravel()
+    adj = fdtd.Adjoint(g, fdtd.EY, probes)
+    adj.reset(g.n)
+    stream = g.stream
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    adj.step(4)
+    torch.cuda.synchronize(dev)
+    e0.record(stream); adj.step(steps); e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_adj = e0.elapsed_time(e1) / steps
+    e0.record(stream); g.step(steps); e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_fwd = e0.elapsed_time(e1) / steps
+    adj.close(); g.close()
+    return {"s_per_step": round(ms_adj * 1e-3, 7), "forward_s_per_step": round(ms_fwd * 1e-3, 7),
+            "gradient_s_per_step": round((ms_adj + 2 * ms_fwd) * 1e-3, 7), "grid": [wl.nx, wl.ny, wl.nz],
+            "probes": int(probes.size), "steps_timed": steps, "dtype": "f32",
+            "adjoint_gcell_per_s": round(wl.cells / (ms_adj * 1e-3) / 1e9, 3)}
 
 
 def run_e2e(torch, fdtd, w, dev, steps, barrier, ws):
@@ -401,6 +443,8 @@ def main():
     ap.add_argument("--tile", default=None, help="variant,ty,lz for --only runs")
     ap.add_argument("--batch-steps", type=int, default=128,
                     help="steps of the 16-grid batched sweep (0 skips it)")
+    ap.add_argument("--adjoint-steps", type=int, default=100,
+                    help="reverse steps timed on the adjoint workload (0 skips it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
