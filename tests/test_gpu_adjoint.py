@@ -40,10 +40,15 @@ def test_adjoint_matches_oracle(precision, tol_f, tol_g):
         if r < window:
             np.add.at(ao.e[1].reshape(-1), probes, dlde[r])
         oracle.adjoint_step(og, src, ao, n, gao, gpo)
-    for c, ref in enumerate(ao.fields()):
-        assert rel_l2(host(adj.field(c)), ref) <= tol_f, c
-    assert rel_l2(ga, gao) <= tol_g
-    assert rel_l2(gp, gpo) <= tol_g
+    # errors per component against the norm of the whole adjoint state (a
+    # component can be orders of magnitude smaller than the others)
+    refs = ao.fields()
+    total = np.sqrt(sum(float(np.sum(r ** 2)) for r in refs))
+    errs = [float(np.linalg.norm(host(adj.field(c)) - r)) / total for c, r in enumerate(refs)]
+    rels = [rel_l2(host(adj.field(c)), r) for c, r in enumerate(refs)]
+    assert max(errs) <= tol_f, (errs, rels)
+    assert rel_l2(ga, gao) <= tol_g, rel_l2(ga, gao)
+    assert rel_l2(gp, gpo) <= tol_g, rel_l2(gp, gpo)
 
 
 def _problem(w, precision, steps, window, checkpoint, seed=4):
