@@ -67,6 +67,7 @@ class BeamLoss(torch.autograd.Function):
         tnorm = torch.linalg.norm(prob.target)
         loss = torch.linalg.norm(diff) / tnorm
         ctx.grid, ctx.adj, ctx.ckpts, ctx.prob = grid, adj, ckpts, prob
+        ctx.w_device, ctx.w_dtype = w_amp.device, w_amp.dtype
         ctx.save_for_backward(diff, tnorm.reshape(1), loss.reshape(1))
         return loss
 
@@ -93,7 +94,7 @@ class BeamLoss(torch.autograd.Function):
             else:
                 adj.step(s1 - s0)
         ga, gp = adj.gradient()
-        return ga, gp, None
+        return ga.to(ctx.w_device, ctx.w_dtype), gp.to(ctx.w_device, ctx.w_dtype), None
 
 
 def beam_loss(w_amp: torch.Tensor, w_phase: torch.Tensor, prob: BeamProblem) -> torch.Tensor:
