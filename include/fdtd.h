@@ -256,6 +256,27 @@ fdtd_status fdtd_adjoint_get(fdtd_adjoint* a, int component, void* dst);
 fdtd_status fdtd_adjoint_gradient(fdtd_adjoint* a, double* dLdw_amp, double* dLdw_phase, int on_device);
 void fdtd_adjoint_destroy(fdtd_adjoint* a);
 
+/* ---- Fluence read-out without device allocation --------------------------
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory at the moment they read the result (for
+ * example inside a hook that must not grow a caching allocator, or on a
+ * system whose device memory is reserved up front).  It returns exactly what
+ * fdtd_fluence returns, but stages the export in a fixed 16 MiB array
+ * compiled into the library (2^21 doubles, present on every device that
+ * loads the library until the process exits) instead of the grid's arena,
+ * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Grids with more than fdtd_fluence_noalloc_max_cells() cells are
+ *     rejected with FDTD_EINVAL.
+ *   - The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents
+ *     (every element read back is written by the call itself, so nothing has
+ *     to be cleared first); calls that overlap on the GPU (different streams
+ *     or threads at once) race on it and must be serialised by the caller.
+ *   - dst, on_device and reset as for fdtd_fluence; synchronises the stream. */
+size_t fdtd_fluence_noalloc_max_cells(void);
+fdtd_status fdtd_fluence_noalloc(fdtd_grid* g, void* dst, int on_device, int reset);
+
 /* Host-only: the per-column source coefficients A_c (see fdtd_annulus_desc)
  * without weights, evaluated at z = 0 and at z = dz/2 as appropriate for the
  * component, into out[6][ny][nx] complex doubles (re, im interleaved:

@@ -91,6 +91,8 @@ _SIGS = {
     "fdtd_adjoint_get": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_adjoint_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "fdtd_adjoint_destroy": (None, [C.c_void_p]),
+    "fdtd_fluence_noalloc_max_cells": (C.c_size_t, []),
+    "fdtd_fluence_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "fdtd_source_coefficients": (C.c_int, [C.POINTER(fdtd_grid_desc), C.POINTER(fdtd_annulus_desc),
                                            C.c_void_p, C.c_void_p]),
     "fdtd_bessel_j": (C.c_double, [C.c_int, C.c_double]),
@@ -153,6 +155,17 @@ def fdtd_step(h: int, nsteps: int):
 
 def fdtd_fluence(h: int, dst_ptr: int, on_device: bool, reset: bool):
     check(lib().fdtd_fluence(C.c_void_p(h), C.c_void_p(dst_ptr), int(on_device), int(reset)), "fdtd_fluence")
+
+
+def fdtd_fluence_noalloc(h: int, dst_ptr: int, on_device: bool, reset: bool):
+    """fdtd_fluence with its staging buffer in a fixed array compiled into the
+    library: for callers that cannot allocate device memory."""
+    check(lib().fdtd_fluence_noalloc(C.c_void_p(h), C.c_void_p(dst_ptr), int(on_device), int(reset)),
+          "fdtd_fluence_noalloc")
+
+
+def fdtd_fluence_noalloc_max_cells() -> int:
+    return int(lib().fdtd_fluence_noalloc_max_cells())
 
 
 def fdtd_get_field(h: int, comp: int, dst_ptr: int, on_device: bool):
