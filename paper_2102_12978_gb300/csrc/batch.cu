@@ -67,7 +67,7 @@ yee_batch_tma(BatchHeader* __restrict__ hdr, const BatchGrid<real>* __restrict__
         const int bx = local % G.ntx, by = local / G.ntx;
         const int kb = bz * G.lz;
         const int nz = G.args[parity].nz;
-        gq = tma_march<real, TY, S>(sa, G.maps[parity], G.step0 + done + offset, bx * 32, by * TY, kb,
+        gq = tma_march_any<real, TY, S>(sa, G.maps[parity], G.step0 + done + offset, bx * 32, by * TY, kb,
                                     min(kb + G.lz, nz), &hdr->err, sm, gq);
         if (gq < 0) return;
     }

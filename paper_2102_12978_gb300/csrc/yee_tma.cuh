@@ -140,31 +140,32 @@ struct HCol {
     uint8_t mk;
 };
 
-template <typename real>
+template <typename real, bool GEN, bool SRC>
 __device__ __forceinline__ HCol<real> make_hcol(const StepArgs<real>& a, int ci, int cj)
 {
     HCol<real> c;
     c.valid = ci >= 0 && ci < a.nx && cj >= 0 && cj < a.ny;
+    if (!GEN) c.valid = ci != -1 || cj != -1;   // interior block: only "no cell" is invalid
     c.ci = ci; c.cj = cj;
     c.chx = real(0); c.chy = real(0); c.xs = false; c.ys = false;
     c.bx = c.ax = c.by = c.ay = real(0); c.pxo = c.pyo = 0; c.mk = 0;
     if (!c.valid) return c;
     c.chx = a.chx[ci]; c.chy = a.chy[cj];
     const int npml = a.npml, w2 = 2 * npml;
-    if (npml > 0 && (ci < npml || ci >= a.nx - npml)) {
+    if (GEN && npml > 0 && (ci < npml || ci >= a.nx - npml)) {
         const int ii = ci < npml ? ci : ci - a.nx + w2;
         c.xs = true; c.bx = a.bhx[ii]; c.ax = a.ahx[ii]; c.pxo = cj * w2 + ii;
     }
-    if (npml > 0 && (cj < npml || cj >= a.ny - npml)) {
+    if (GEN && npml > 0 && (cj < npml || cj >= a.ny - npml)) {
         const int jj = cj < npml ? cj : cj - a.ny + w2;
         c.ys = true; c.by = a.bhy[jj]; c.ay = a.ahy[jj]; c.pyo = jj * a.pitch + ci;
     }
-    if (a.smask) c.mk = a.smask[cj * a.nx + ci];
+    if (SRC && a.smask) c.mk = a.smask[cj * a.nx + ci];
     return c;
 }
 
 // H^{n+1/2} of one cell from the staged E planes k (e0*) and k+1 (e1*).
-template <typename real, int BX>
+template <typename real, int BX, bool GEN, bool SRC>
 __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCol<real>& c,
                                               const real* __restrict__ e0x, const real* __restrict__ e0y,
                                               const real* __restrict__ e0z, const real* __restrict__ e1x,
@@ -182,7 +183,7 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
     hx = hx - c.chy * dEz_y + a.cz * dEy_z;
     hy = hy - a.cz * dEx_z + c.chx * dEz_x;
     hz = hz - c.chx * dEy_x + c.chy * dEx_y;
-    if (c.xs) {
+    if (GEN && c.xs) {
         const int q = kw * psx_plane + c.pxo;
         const real p0 = c.bx * pp[0] + c.ax * dEz_x;   // Hyx (old value prefetched)
         const real p1 = c.bx * pp[1] + c.ax * dEy_x;   // Hzx
@@ -190,7 +191,7 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
         hz -= p1;
         if (store) { a.phx_out[0][q] = p0; a.phx_out[1][q] = p1; }
     }
-    if (c.ys) {
+    if (GEN && c.ys) {
         const int q = kw * psy_plane + c.pyo;
         const real p0 = c.by * pp[2] + c.ay * dEz_y;   // Hxy
         const real p1 = c.by * pp[3] + c.ay * dEx_y;   // Hzy
@@ -198,7 +199,7 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
         hz += p1;
         if (store) { a.phy_out[0][q] = p0; a.phy_out[1][q] = p1; }
     }
-    if (c.mk & 0x38) {
+    if (SRC && (c.mk & 0x38)) {
         // soft source: Re{ B u }, u = f e^{i (beta z_k - Phi)} of this plane
         const int ncol = a.nx * a.ny, col = c.cj * a.nx + c.ci;
         const Cpx<real>* B = static_cast<const Cpx<real>*>(a.scoefr);
@@ -251,7 +252,11 @@ struct MarchSmem {
 // parity = (gq / S) & 1), so that a persistent CTA can march many blocks
 // with its mbarriers initialised once.  Returns the updated counter, or -1
 // after a timed-out wait (the error word is raised).
-template <typename real, int TY, int S>
+// GEN: the block may touch the CPML shell, a PEC wall, the last (wall or
+// ragged) tile of an axis; every per-cell check is compiled in.  !GEN: an
+// interior block, where all of them are known false and compiled out.
+// SRC: the block holds antenna cells (compiled out otherwise).
+template <typename real, int TY, int S, bool GEN, bool SRC>
 __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps& m, long long n, int i0, int j0,
                                          int kb, int ke, int* err, const MarchSmem<real, TY, S>& sm, int gq0)
 {
@@ -273,7 +278,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     const int plane = pitch * ny;
     const int w2 = 2 * a.npml, psx_plane = ny * w2, psy_plane = w2 * pitch;
     const int i = i0 + tx, j = j0 + ty;
-    const bool own = (i < nx) && (j < ny);
+    const bool own = !GEN || ((i < nx) && (j < ny));
     const int so = (ty + 1) * PX + (tx + 1);        // own cell in the sH / sB rings
     const int eo = (ty + 1) * BX + (tx + XA);        // own cell in an E / H box
     const int gcol = j * pitch + i;
@@ -322,7 +327,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     // source factors f e^{i (beta z_k - omega t')} of every plane of this
     // block, phase in FP64, stored in the field precision (read after the
     // first barrier of the march)
-    if (a.smask) {
+    if (SRC && a.smask) {
         for (int q = tid; q < Q; q += NT) {
             const int p = kb - 1 + q;
             const int pw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
@@ -336,12 +341,12 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     }
 
     // per-column constants: own cell and this thread's H halo cell
-    const HCol<real> co = make_hcol(a, own ? i : -1, own ? j : -1);
+    const HCol<real> co = make_hcol<real, GEN, SRC>(a, own ? i : -1, own ? j : -1);
     const real cex = own ? a.cex[i] : real(0), cey = own ? a.cey[j] : real(0);
     bool exs = false, eys = false;
     real ebx = 0, eax = 0, eby = 0, eay = 0;
     int epx = 0, epy = 0;
-    if (own && w2 > 0) {
+    if (GEN && own && w2 > 0) {
         if (i < a.npml || i >= nx - a.npml) {
             const int ii = i < a.npml ? i : i - nx + w2;
             exs = true; ebx = a.bex[ii]; eax = a.aex[ii]; epx = j * w2 + ii;
@@ -360,16 +365,17 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         const int jj = tx;
         hi_h = i0 - 1; hj_h = j0 - 1 + jj; hs_h = jj * PX; he_h = jj * BX + XA - 1;
     }
-    const HCol<real> ch = make_hcol(a, hi_h, hj_h);
+    const HCol<real> ch = make_hcol<real, GEN, SRC>(a, hi_h, hj_h);
     // fluence cells: base (i-1, j-1) and, in the last tiles, the wall cells
-    const bool flu_base = (i >= 1) && (j >= 1) && (i <= nx) && (j <= ny);
-    const bool xw = (tx == TX - 1) && (i == nx - 1) && (j >= 1) && (j <= ny);
-    const bool yw = (ty == TY - 1) && (j == ny - 1) && (i >= 1) && (i <= nx);
+    const bool flu_base = !GEN || ((i >= 1) && (j >= 1) && (i <= nx) && (j <= ny));
+    const bool xw = GEN && (tx == TX - 1) && (i == nx - 1) && (j >= 1) && (j <= ny);
+    const bool yw = GEN && (ty == TY - 1) && (j == ny - 1) && (i >= 1) && (i <= nx);
 
     // CPML psi of the next plane, prefetched into registers one iteration ahead
     // (H side: own and halo cell, read copy; E side: own cell, updated in place)
     real ppo[4] = {0, 0, 0, 0}, pph[4] = {0, 0, 0, 0}, ppe[4] = {0, 0, 0, 0};
     auto fetch_psi_h = [&](const HCol<real>& c, int plane_w, real (&pp)[4]) {
+        if (!GEN) return;
         if (c.xs) {
             const int q = plane_w * psx_plane + c.pxo;
             pp[0] = a.phx_in[0][q]; pp[1] = a.phx_in[1][q];
@@ -380,6 +386,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         }
     };
     auto fetch_psi_e = [&](int plane_w) {
+        if (!GEN) return;
         if (exs) { const int q = plane_w * psx_plane + epx; ppe[0] = a.pex[0][q]; ppe[1] = a.pex[1][q]; }
         if (eys) { const int q = plane_w * psy_plane + epy; ppe[2] = a.pey[0][q]; ppe[3] = a.pey[1][q]; }
     };
@@ -426,7 +433,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             if (co.valid) {
                 const real ox = hb[eo], oy = hb[HS + eo], oz = hb[2 * HS + eo];
                 real hx = ox, hy = oy, hz = oz;
-                tma_compute_h<real, BX>(a, co, e0x, e0y, e0z, e1x, e1y, eo, kw, psx_plane, psy_plane, hx, hy, hz,
+                tma_compute_h<real, BX, GEN, SRC>(a, co, e0x, e0y, e0z, e1x, e1y, eo, kw, psx_plane, psy_plane, hx, hy, hz,
                                         sm.uH[q], write_k, ppo);
                 hs[so] = hx; hs[P + so] = hy; hs[2 * P + so] = hz;
                 if (write_k) {
@@ -437,7 +444,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             if (ch.valid) {
                 const real ox = hb[he_h], oy = hb[HS + he_h], oz = hb[2 * HS + he_h];
                 real hx = ox, hy = oy, hz = oz;
-                tma_compute_h<real, BX>(a, ch, e0x, e0y, e0z, e1x, e1y, he_h, kw, psx_plane, psy_plane, hx, hy,
+                tma_compute_h<real, BX, GEN, SRC>(a, ch, e0x, e0y, e0z, e1x, e1y, he_h, kw, psx_plane, psy_plane, hx, hy,
                                         hz, sm.uH[q], false, pph);
                 hs[hs_h] = hx; hs[P + hs_h] = hy; hs[2 * P + hs_h] = hz;
             }
@@ -464,7 +471,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             real nex = ex + cey * dHz_y - a.cz * dHy_z;
             real ney = ey + a.cz * dHx_z - cex * dHz_x;
             real nez = ez + cex * dHy_x - cey * dHx_y;
-            if (exs) {
+            if (GEN && exs) {
                 const int qq = kmw * psx_plane + epx;
                 const real p0 = ebx * ppe[0] + eax * dHz_x;   // Eyx (old value prefetched)
                 const real p1 = ebx * ppe[1] + eax * dHy_x;   // Ezx
@@ -472,7 +479,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                 ney -= p0;
                 nez += p1;
             }
-            if (eys) {
+            if (GEN && eys) {
                 const int qq = kmw * psy_plane + epy;
                 const real p0 = eby * ppe[2] + eay * dHz_y;   // Exy
                 const real p1 = eby * ppe[3] + eay * dHx_y;   // Ezy
@@ -480,7 +487,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                 nex += p0;
                 nez -= p1;
             }
-            if (co.mk & 0x07) {
+            if (SRC && (co.mk & 0x07)) {
                 const int ncol = nx * ny, col = j * nx + i;
                 const Cpx<real>* B = static_cast<const Cpx<real>*>(a.scoefr);
                 const Cpx<real> u = sm.uE[q - 1];
@@ -488,8 +495,10 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
                 if (co.mk & 0x02) { const Cpx<real> b = B[ncol + col]; ney += b.x * u.x - b.y * u.y; }
                 if (co.mk & 0x04) { const Cpx<real> b = B[2 * ncol + col]; nez += b.x * u.x - b.y * u.y; }
             }
-            if (j == 0) { nex = real(0); nez = real(0); }    // PEC: tangential E
-            if (i == 0) { ney = real(0); nez = real(0); }
+            if (GEN) {
+                if (j == 0) { nex = real(0); nez = real(0); }    // PEC: tangential E
+                if (i == 0) { ney = real(0); nez = real(0); }
+            }
             const int g = kmw * plane + gcol;
             a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez;
         }
@@ -553,6 +562,37 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     return gq0 + Q;
 }
 
+// Class of a block: general (touches the CPML shell, a PEC wall or the last
+// tile of an axis) or interior; an interior block also reports whether any of
+// its cells (own or low halo) carries an antenna point (CTA-wide vote).
+template <typename real, int TY>
+__device__ __forceinline__ void block_class(const StepArgs<real>& a, int i0, int j0, bool& gen, bool& src)
+{
+    const int nx = a.nx, ny = a.ny, npml = a.npml;
+    gen = i0 == 0 || j0 == 0 || i0 + 32 >= nx || j0 + TY >= ny ||
+          (npml > 0 && (i0 - 1 < npml || i0 + 31 >= nx - npml || j0 - 1 < npml || j0 + TY - 1 >= ny - npml));
+    src = false;
+    if (!gen && a.smask) {
+        const int tx = threadIdx.x, ty = threadIdx.y;
+        bool mine = a.smask[(j0 + ty) * nx + i0 + tx] != 0;
+        if (ty == 0) mine = mine || a.smask[(j0 - 1) * nx + i0 + tx] != 0;
+        if (tx == 0) mine = mine || a.smask[(j0 + ty) * nx + i0 - 1] != 0;
+        if (tx == 0 && ty == 0) mine = mine || a.smask[(j0 - 1) * nx + i0 - 1] != 0;
+        src = __syncthreads_or(mine) != 0;
+    }
+}
+
+template <typename real, int TY, int S>
+__device__ __forceinline__ int tma_march_any(const StepArgs<real>& a, const TmaMaps& m, long long n, int i0, int j0,
+                                             int kb, int ke, int* err, const MarchSmem<real, TY, S>& sm, int gq0)
+{
+    bool gen, src;
+    block_class<real, TY>(a, i0, j0, gen, src);
+    if (gen) return tma_march<real, TY, S, true, true>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
+    if (src) return tma_march<real, TY, S, false, true>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
+    return tma_march<real, TY, S, false, false>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
+}
+
 template <typename real, int TY, int S>
 __device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init(int lz)
 {
@@ -589,7 +629,7 @@ yee_step_tma(const StepArgs<real> a, const __grid_constant__ TmaMaps m, long lon
 {
     const MarchSmem<real, TY, S> sm = march_smem_init<real, TY, S>(lz);
     const int kb = blockIdx.z * lz;
-    tma_march<real, TY, S>(a, m, n, blockIdx.x * 32, blockIdx.y * TY, kb, min(kb + lz, a.nz), err, sm, 0);
+    tma_march_any<real, TY, S>(a, m, n, blockIdx.x * 32, blockIdx.y * TY, kb, min(kb + lz, a.nz), err, sm, 0);
 }
 
 }  // namespace fdtd
