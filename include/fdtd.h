@@ -178,14 +178,21 @@ fdtd_status fdtd_set_step(fdtd_grid* g, int64_t n);
 double fdtd_get_dt(const fdtd_grid* g);
 int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
 
-/* Tile configuration of the fused step kernel: a CTA of 32 x ty threads
- * (ty in {4, 8, 16}) owns a 32 x ty tile of columns and marches lz planes of
- * z.  variant 1 stages every z plane with TMA bulk-tensor copies into a
- * multi-stage shared-memory ring (mbarrier completion); variant 0 uses plain
- * coalesced loads (no FP64 32x16 tile in variant 1).  fdtd_create_grid picks
- * a default; fdtd_autotune times the candidates on this grid (running `steps`
- * steps for each, then restoring the state) and keeps the fastest.  Results
- * are identical for every configuration. */
+/* Tile configuration of the step.  A CTA owns a 32 x ty block of columns
+ * (ty in {4, 8, 16}); variants 0-4 march lz planes of z per CTA:
+ *   0  one pass, plain coalesced loads into a shared-memory ring;
+ *   1  one pass, every z plane staged by TMA bulk-tensor copies into a
+ *      multi-stage shared-memory ring (mbarrier completion);
+ *   2  variant 1 with two rows of the tile per thread;
+ *   3  two passes (H, then E with the fluence term), plain loads;
+ *   4  two passes, a TMA-staged H pass with the fluence term, then E;
+ *   5  two cell-parallel passes, one thread per cell (lz unused; needs
+ *      nz <= 65535, else EINVAL).
+ * The TMA variants (1, 2, 4) have no FP64 32x16 tile (EINVAL).
+ * fdtd_create_grid picks a default (variant 5, ty 4); fdtd_autotune times
+ * the candidates on this grid (running `steps` steps for each, then
+ * restoring the state) and keeps the fastest.  Results agree to rounding
+ * for every configuration. */
 fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
 fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz);
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state);

@@ -2,7 +2,7 @@
 // angles, ring radii and transverse sizes) advanced together.
 //
 // Each grid runs the unchanged method of its own descriptor (Section 4,
-// Eq. 12-13).  The batch flattens every grid's (32 x TY tile, z segment)
+// Eq. 12-13).  The batch flattens every grid's (32 x TR tile, z segment)
 // blocks into one work list; a persistent kernel with one CTA per resident
 // slot (SM count x occupancy) walks the list with a grid stride, marching
 // each block with the TMA-staged fused step (tma_march).  The CTA's
@@ -31,7 +31,7 @@ struct BatchHeader {
 };
 
 template <typename real>
-struct alignas(64) BatchGrid {
+struct alignas(128) BatchGrid {
     TmaMaps maps[2];        // by copy being read
     StepArgs<real> args[2];
     long long step0;        // the grid's step counter when the batch was created
@@ -40,11 +40,14 @@ struct alignas(64) BatchGrid {
 
 constexpr int kBatchLz = 32;   // z segment of a batched block
 
-template <typename real, int TY, int S>
-__global__ void __launch_bounds__(32 * TY, MinCtas<real, TY>::value)
+// One CTA of 32 x (TR / R) threads per resident slot; each block is a
+// 32 x TR tile of one grid.
+template <typename real, int TR, int R, int S>
+__global__ void __launch_bounds__(32 * (TR / R), MinCtas<real, TR, R>::value)
 yee_batch_tma(BatchHeader* __restrict__ hdr, const BatchGrid<real>* __restrict__ grids, int parity, int offset)
 {
-    const MarchSmem<real, TY, S> sm = march_smem_init<real, TY, S>(kBatchLz);
+    constexpr int NT = 32 * (TR / R);
+    const MarchSmem<real, TR, S> sm = march_smem_init<real, TR, S>(kBatchLz);
     __shared__ __align__(16) unsigned char sargs_raw[sizeof(StepArgs<real>)];
     const StepArgs<real>& sa = *reinterpret_cast<const StepArgs<real>*>(sargs_raw);
     const int ngrids = hdr->ngrids, nitems = hdr->nitems;
@@ -59,7 +62,7 @@ yee_batch_tma(BatchHeader* __restrict__ hdr, const BatchGrid<real>* __restrict__
         __syncthreads();   // every reader of the previous block's arguments is done
         const int* src = reinterpret_cast<const int*>(&G.args[parity]);
         int* dst = reinterpret_cast<int*>(sargs_raw);
-        for (int w = tid; w < int(sizeof(StepArgs<real>) / 4); w += 32 * TY) dst[w] = src[w];
+        for (int w = tid; w < int(sizeof(StepArgs<real>) / 4); w += NT) dst[w] = src[w];
         __syncthreads();   // publish the copied arguments before tma_march reads them
         int local = item - G.item0;
         const int bz = local % G.nseg;
@@ -67,8 +70,8 @@ yee_batch_tma(BatchHeader* __restrict__ hdr, const BatchGrid<real>* __restrict__
         const int bx = local % G.ntx, by = local / G.ntx;
         const int kb = bz * G.lz;
         const int nz = G.args[parity].nz;
-        gq = tma_march_any<real, TY, S>(sa, G.maps[parity], G.step0 + done + offset, bx * 32, by * TY, kb,
-                                    min(kb + G.lz, nz), &hdr->err, sm, gq);
+        gq = tma_march_any<real, TR, R, S>(sa, G.maps[parity], G.step0 + done + offset, bx * 32, by * TR, kb,
+                                           min(kb + G.lz, nz), &hdr->err, sm, gq);
         if (gq < 0) return;
     }
 }
@@ -107,33 +110,35 @@ size_t grid_entry_bytes(int precision)
     return precision == FDTD_F64 ? sizeof(BatchGrid<double>) : sizeof(BatchGrid<float>);
 }
 
-template <typename real, int TY, int S>
+// Block shape of the batch: 32 x TR tiles, R rows per thread, S stages
+// (FP32: 32 x 8, FP64: 32 x 4, one row per thread, five stages).
+template <typename real, int TR, int R, int S>
 cudaError_t batch_launch(fdtd_batch* b, int parity, int offset, cudaStream_t s)
 {
-    using T = TmaTile<real, TY>;
+    using T = TmaTile<real, TR>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(yee_batch_tma<real, TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(T::smem_bytes(S, kBatchLz)));
+        cudaError_t e = cudaFuncSetAttribute(yee_batch_tma<real, TR, R, S>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(T::smem_bytes(S, kBatchLz)));
         if (e != cudaSuccess) return e;
         attr = true;
     }
     char* tab = static_cast<char*>(b->table);
-    yee_batch_tma<real, TY, S><<<b->nblocks, dim3(32, TY), T::smem_bytes(S, kBatchLz), s>>>(
+    yee_batch_tma<real, TR, R, S><<<b->nblocks, dim3(32, TR / R), T::smem_bytes(S, kBatchLz), s>>>(
         reinterpret_cast<BatchHeader*>(tab), reinterpret_cast<const BatchGrid<real>*>(tab + 256), parity, offset);
     return cudaGetLastError();
 }
 
 cudaError_t batch_launch_any(fdtd_batch* b, int parity, int offset, cudaStream_t s)
 {
-    if (b->precision == FDTD_F64) return batch_launch<double, 4, 5>(b, parity, offset, s);
-    return batch_launch<float, 8, 5>(b, parity, offset, s);
+    if (b->precision == FDTD_F64) return batch_launch<double, 4, 1, 5>(b, parity, offset, s);
+    return batch_launch<float, 8, 1, 5>(b, parity, offset, s);
 }
 
-template <typename real, int TY, int S>
+template <typename real, int TR, int R, int S>
 fdtd_status batch_fill(fdtd_batch* b)
 {
-    using T = TmaTile<real, TY>;
+    using T = TmaTile<real, TR>;
     const int n = int(b->grids.size());
     std::vector<BatchGrid<real>> host(n);
     int items = 0;
@@ -143,7 +148,7 @@ fdtd_status batch_fill(fdtd_batch* b)
         std::memset(&G, 0, sizeof(G));
         for (int cur = 0; cur < 2; ++cur) {
             TmaMaps* m = nullptr;
-            if (!tma_maps<real, TY>(g, cur, &m)) return fail(FDTD_ECUDA, "tensor map encoding failed");
+            if (!tma_maps<real, TR>(g, cur, &m)) return fail(FDTD_ECUDA, "tensor map encoding failed");
             G.maps[cur] = *m;
             G.args[cur] = make_args<real>(g, cur);
         }
@@ -151,7 +156,7 @@ fdtd_status batch_fill(fdtd_batch* b)
         G.lz = g->desc.nz < kBatchLz ? g->desc.nz : kBatchLz;
         G.nseg = (g->desc.nz + G.lz - 1) / G.lz;
         G.ntx = (g->desc.nx + 31) / 32;
-        G.nty = (g->desc.ny + TY - 1) / TY;
+        G.nty = (g->desc.ny + TR - 1) / TR;
         G.item0 = items;
         items += G.ntx * G.nty * G.nseg;
     }
@@ -166,16 +171,16 @@ fdtd_status batch_fill(fdtd_batch* b)
         st = cuda_check(cudaMemcpy(tab + 256, host.data(), sizeof(BatchGrid<real>) * n, cudaMemcpyHostToDevice),
                         "batch table");
     if (st != FDTD_OK) return st;
-    cudaError_t e = cudaFuncSetAttribute(yee_batch_tma<real, TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(yee_batch_tma<real, TR, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(T::smem_bytes(S, kBatchLz)));
     if (e != cudaSuccess) return cuda_check(e, "batch kernel attribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_batch_tma<real, TY, S>, 32 * TY,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_batch_tma<real, TR, R, S>, 32 * (TR / R),
                                                       T::smem_bytes(S, kBatchLz));
     if (e != cudaSuccess || per_sm < 1) return fail(FDTD_ECUDA, "batch kernel does not fit on an SM");
     const int sms = b->grids[0]->sm_count > 0 ? b->grids[0]->sm_count : 152;
     b->nblocks = per_sm * sms < items ? per_sm * sms : items;
-    b->ty = TY;
+    b->ty = TR;
     b->S = S;
     return FDTD_OK;
 }
@@ -240,7 +245,7 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
     st = cuda_check(cudaStreamSynchronize(b->stream), "batch create");
-    if (st == FDTD_OK) st = prec == FDTD_F64 ? batch_fill<double, 4, 5>(b) : batch_fill<float, 8, 5>(b);
+    if (st == FDTD_OK) st = prec == FDTD_F64 ? batch_fill<double, 4, 1, 5>(b) : batch_fill<float, 8, 1, 5>(b);
     if (st != FDTD_OK) { cudaStreamDestroy(b->capture); delete b; return st; }
     *out = b;
     return FDTD_OK;

@@ -77,7 +77,8 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
     L.scoef_unw = take(6 * nx * ny * 16);
     L.wamp = take(nx * ny * 8);
     L.wphase = take(nx * ny * 8);
-    L.zph = take(2 * nz * 16);
+    L.zph = take(nz * 16);
+    L.zph32 = take(nz * 8);
     L.flu_out = d.fluence ? take(nz * ny * nx * 8) : 0;
     L.err = take(256);
     L.total = off;
@@ -223,6 +224,7 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
     a.scoef = reinterpret_cast<const double2*>(A + L.scoef);
     a.scoefr = sizeof(real) == 8 ? static_cast<const void*>(A + L.scoef) : static_cast<const void*>(A + L.scoef32);
     a.zph = reinterpret_cast<const double2*>(A + L.zph);
+    a.zphr = sizeof(real) == 8 ? static_cast<const void*>(A + L.zph) : static_cast<const void*>(A + L.zph32);
     a.st = g->srct;
     return a;
 }
@@ -249,41 +251,57 @@ static cudaError_t launch_fused(const fdtd_grid* g, int cur, long long n, int lz
     return cudaGetLastError();
 }
 
-template <typename real, int TY, int S>
+// 32 x TR tiles, R rows per thread (32 x TR/R threads), S stages.
+template <typename real, int TR, int R, int S>
 static cudaError_t launch_tma(const fdtd_grid* cg, int cur, long long n, int lz, cudaStream_t s)
 {
     fdtd_grid* g = const_cast<fdtd_grid*>(cg);
-    using T = TmaTile<real, TY>;
+    using T = TmaTile<real, TR>;
     const size_t smem = T::smem_bytes(S, lz);
     static size_t attr_set = 0;
     if (smem > attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(yee_step_tma<real, TY, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
+        cudaError_t e = cudaFuncSetAttribute(yee_step_tma<real, TR, R, S>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         attr_set = smem;
     }
     TmaMaps* m = nullptr;
-    if (!tma_maps<real, TY>(g, cur, &m)) return cudaErrorInvalidValue;
-    dim3 block(32, TY);
-    dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, (g->desc.nz + lz - 1) / lz);
+    if (!tma_maps<real, TR>(g, cur, &m)) return cudaErrorInvalidValue;
+    dim3 block(32, TR / R);
+    dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TR - 1) / TR, (g->desc.nz + lz - 1) / lz);
     int* err = reinterpret_cast<int*>(static_cast<char*>(g->arena) + g->L.err);
-    yee_step_tma<real, TY, S><<<grid, block, smem, s>>>(make_args<real>(g, cur), *m, n, lz, err);
+    yee_step_tma<real, TR, R, S><<<grid, block, smem, s>>>(make_args<real>(g, cur), *m, n, lz, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s)
 {
+    if (tc.variant >= 3) return launch_split(g, cur, n, tc, s);
     if (tc.variant == 1) {
         if (g->desc.precision == FDTD_F32) {
             switch (tc.ty) {
-                case 4: return launch_tma<float, 4, 6>(g, cur, n, tc.lz, s);
-                case 16: return launch_tma<float, 16, 5>(g, cur, n, tc.lz, s);
-                default: return launch_tma<float, 8, 5>(g, cur, n, tc.lz, s);
+                case 4: return launch_tma<float, 4, 1, 6>(g, cur, n, tc.lz, s);
+                case 16: return launch_tma<float, 16, 1, 5>(g, cur, n, tc.lz, s);
+                default: return launch_tma<float, 8, 1, 5>(g, cur, n, tc.lz, s);
             }
         } else {
             switch (tc.ty) {
-                case 4: return launch_tma<double, 4, 5>(g, cur, n, tc.lz, s);
-                default: return launch_tma<double, 8, 5>(g, cur, n, tc.lz, s);
+                case 4: return launch_tma<double, 4, 1, 5>(g, cur, n, tc.lz, s);
+                default: return launch_tma<double, 8, 1, 5>(g, cur, n, tc.lz, s);
+            }
+        }
+    }
+    if (tc.variant == 2) {
+        if (g->desc.precision == FDTD_F32) {
+            switch (tc.ty) {
+                case 4: return launch_tma<float, 4, 2, 6>(g, cur, n, tc.lz, s);
+                case 16: return launch_tma<float, 16, 2, 5>(g, cur, n, tc.lz, s);
+                default: return launch_tma<float, 8, 2, 5>(g, cur, n, tc.lz, s);
+            }
+        } else {
+            switch (tc.ty) {
+                case 4: return launch_tma<double, 4, 2, 5>(g, cur, n, tc.lz, s);
+                default: return launch_tma<double, 8, 2, 5>(g, cur, n, tc.lz, s);
             }
         }
     }
@@ -302,11 +320,17 @@ cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConf
     }
 }
 
-// Default tile: 32 x 8 columns, z split into segments so that about four
-// CTAs per SM are in flight (152 SMs on GB300).
+// Default tile: the cell-parallel two-pass step on 32 x 4 blocks; grids with
+// more than 65535 planes take the one-pass TMA step on 32 x 8 tiles, with z
+// split into segments so that about four CTAs per SM are in flight (152 SMs
+// on GB300).
 TileConfig default_tile(const fdtd_grid_desc& d, int sm_count)
 {
     TileConfig tc;
+    if (d.nz <= 65535) {
+        tc.variant = 5; tc.tx = 32; tc.ty = 4; tc.lz = d.nz;
+        return tc;
+    }
     tc.variant = 1; tc.tx = 32; tc.ty = 8;
     long tiles = long((d.nx + 31) / 32) * long((d.ny + 7) / 8);
     long want = 4L * (sm_count > 0 ? sm_count : 152);
@@ -377,7 +401,7 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->sm_count = sms;
     g->tile = default_tile(*d, sms);
     for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 3; ++b) g->maps_ok[a][b] = false;
+        for (int b = 0; b < 3; ++b) g->maps_ok[a][b] = g->hmaps_ok[a][b] = false;
     st = cuda_check(cudaMemsetAsync(arena, 0, L.total, g->stream), "zero arena");
     if (st == FDTD_OK)
         st = (d->precision == FDTD_F64) ? upload_tables<double>(g) : upload_tables<float>(g);
@@ -444,6 +468,14 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
                         "upload source");
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(A + g->L.zph, zph.data(), zph.size() * 16, cudaMemcpyHostToDevice,
+                                        g->stream), "upload source");
+    std::vector<float> zph32(2 * zph.size());
+    for (size_t q = 0; q < zph.size(); ++q) {
+        zph32[2 * q] = float(zph[q].real());
+        zph32[2 * q + 1] = float(zph[q].imag());
+    }
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.zph32, zph32.data(), zph32.size() * 4, cudaMemcpyHostToDevice,
                                         g->stream), "upload source");
     if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(g->stream), "upload source");
     if (st != FDTD_OK) return st;
@@ -618,10 +650,11 @@ void fdtd_destroy_grid(fdtd_grid* g) { delete g; }
 fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
-    if (variant != 0 && variant != 1) return fail(FDTD_EINVAL, "variant=%d not in {0, 1}", variant);
+    if (variant < 0 || variant > 5) return fail(FDTD_EINVAL, "variant=%d not in {0, ..., 5}", variant);
     if (ty != 4 && ty != 8 && ty != 16) return fail(FDTD_EINVAL, "ty=%d not in {4, 8, 16}", ty);
-    if (variant == 1 && ty == 16 && g->desc.precision == FDTD_F64)
-        return fail(FDTD_EINVAL, "the TMA variant has no FP64 32x16 tile");
+    if (variant == 5 && g->desc.nz > 65535) return fail(FDTD_EINVAL, "variant 5 takes nz <= 65535");
+    if ((variant == 1 || variant == 2 || variant == 4) && ty == 16 && g->desc.precision == FDTD_F64)
+        return fail(FDTD_EINVAL, "the TMA variants have no FP64 32x16 tile");
     if (lz < 1) return fail(FDTD_EINVAL, "lz=%d < 1", lz);
     g->tile.variant = variant;
     g->tile.tx = 32;
@@ -648,8 +681,12 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     fdtd_status st = fdtd_save_state(g, scratch_state);
     if (st != FDTD_OK) return st;
     struct Cand { int variant, ty; };
-    std::vector<Cand> cands = {{1, 4}, {1, 8}, {1, 16}, {0, 4}, {0, 8}, {0, 16}};
-    if (g->desc.precision == FDTD_F64) cands = {{1, 4}, {1, 8}, {0, 4}, {0, 8}};
+    std::vector<Cand> cands = {{5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {4, 16}, {3, 4}, {3, 8}, {3, 16},
+                               {2, 8}, {2, 16}, {1, 4}, {1, 8}, {1, 16}, {0, 4}, {0, 8}, {0, 16}};
+    if (g->desc.precision == FDTD_F64)
+        cands = {{5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {3, 4}, {3, 8}, {2, 8}, {2, 4}, {1, 4}, {1, 8},
+                 {0, 4}, {0, 8}};
+    if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 3);
     const int nz = g->desc.nz;
     std::vector<int> lzs;
     for (int segs : {1, 2, 3, 4, 6, 8, 12, 16}) {
@@ -667,6 +704,7 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     TileConfig best_tc = g->tile;
     for (const Cand& cd : cands)
         for (int lz : lzs) {
+            if (cd.variant == 5 && lz != lzs[0]) continue;   // one cell per thread: no z segments
             TileConfig tc; tc.variant = cd.variant; tc.tx = 32; tc.ty = cd.ty; tc.lz = lz;
             cudaError_t e = launch_step(g, g->cur, g->step, tc, g->stream);   // warm-up
             if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_check(e, "autotune"); }

@@ -22,7 +22,7 @@ struct Layout {
     size_t dynamic_bytes = 0;
     size_t chx = 0, cex = 0, chy = 0, cey = 0;
     size_t prof[8] = {};   // bhx ahx bex aex bhy ahy bey aey
-    size_t smask = 0, scoef = 0, scoef32 = 0, zph = 0;
+    size_t smask = 0, scoef = 0, scoef32 = 0, zph = 0, zph32 = 0;
     size_t scoef_unw = 0, wamp = 0, wphase = 0;   // unweighted coefficients and the weights
     size_t flu_out = 0;    // dense FP64 export of the fluence
     size_t err = 0;        // device error word (int)
@@ -30,7 +30,11 @@ struct Layout {
 };
 
 // variant 0: plain loads into a shared-memory ring (yee_step_fused);
-// variant 1: TMA-staged planes with mbarriers (yee_step_tma).
+// variant 1: TMA-staged planes with mbarriers (yee_step_tma), one row per thread;
+// variant 2: the same with two rows of the tile per thread;
+// variant 3: two plain-load passes, H then E with the fluence term;
+// variant 4: two passes, TMA-staged H with the fluence term, then plain-load E;
+// variant 5: two cell-parallel passes, H then E with the fluence term.
 struct TileConfig {
     int variant = 1, tx = 32, ty = 8, lz = 32;
 };
@@ -61,10 +65,16 @@ struct fdtd_grid {
     fdtd::TileConfig tile;
     fdtd::TmaMaps maps[2][3];   // [read copy][ty = 4, 8, 16]
     bool maps_ok[2][3];
+    fdtd::TmaMaps hmaps[2][3];  // the same for the boxes of yee_hflu_tma
+    bool hmaps_ok[2][3];
 };
 
 namespace fdtd {
 template <typename real>
 StepArgs<real> make_args(const fdtd_grid* g, int cur);
 cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
+// The two-pass steps on stream s: variant 3 yee_h_pass then yee_e_pass (with
+// the fluence term); variant 4 yee_hflu_tma (with the fluence term) then
+// yee_e_pass.
+cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
 }  // namespace fdtd

@@ -1,0 +1,242 @@
+// yee_cell.cuh -- the Yee step as two cell-parallel passes (sm_103a).
+//
+// yee_h_cell: H^{n-1/2} -> H^{n+1/2} (curl of E^n, CPML psi of the H side,
+// soft source at (n+1/2) dt), Section 4 / Eq. 13.
+// yee_e_cell: E^n -> E^{n+1} (curl of H^{n+1/2}, CPML psi of the E side,
+// PEC walls, soft source at (n+1) dt) and the fluence term
+// |E^n_c x Hbar^n_c| dt of every cell (Section 2), Hbar the mean of
+// H^{n-1/2} and H^{n+1/2}.
+//
+// One thread per cell, a CTA per 32 x TY x 1 block of cells: no loop, no
+// barrier, no shared memory and few registers, so that an SM holds enough
+// warps -- and enough loads in flight -- to stream HBM at close to its copy
+// rate.  The +-1 neighbours of a cell are read through the L1 / L2 caches
+// (those of the same plane from adjacent threads, those of planes k +- 1
+// from the blocks of the neighbouring plane, which run at about the same
+// time).  Blocks that touch a wall, a ragged edge or the CPML shell compile
+// every check in; the others none.  The source factor f e^{i (beta z_k -
+// omega t)} of a plane is the product of a per-plane table e^{i beta z_k}
+// and the per-step factor f e^{-i omega t} evaluated on the host in FP64,
+// both in the field precision.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "yee_fused.cuh"
+#include "yee_tma.cuh"
+
+namespace fdtd {
+
+// f e^{-i Phi} at the H time (n + 1/2) dt and the E time (n + 1) dt.
+template <typename real>
+struct StepTime {
+    Cpx<real> th, te;
+};
+
+template <typename real>
+__device__ __forceinline__ Cpx<real> plane_factor(const StepArgs<real>& a, int k, Cpx<real> t)
+{
+    const Cpx<real> z = static_cast<const Cpx<real>*>(a.zphr)[k];
+    return Cpx<real>{z.x * t.x - z.y * t.y, z.x * t.y + z.y * t.x};
+}
+
+template <typename real>
+__device__ __forceinline__ real src_add(const StepArgs<real>& a, int c, int col, Cpx<real> u)
+{
+    const Cpx<real> b = static_cast<const Cpx<real>*>(a.scoefr)[c * a.nx * a.ny + col];
+    return b.x * u.x - b.y * u.y;
+}
+
+template <typename real, bool GEN>
+__device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, int i, int j, int k)
+{
+    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    if (GEN && (i >= nx || j >= ny)) return;
+    const int plane = pitch * ny, g = k * plane + j * pitch + i;
+    const int gn = (k + 1 == nz) ? g - k * plane : g + plane;
+    const real* __restrict__ Ex = a.ein[0];
+    const real* __restrict__ Ey = a.ein[1];
+    const real* __restrict__ Ez = a.ein[2];
+    const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
+    const real ex = __ldg(Ex + g), ey = __ldg(Ey + g), ez = __ldg(Ez + g);
+    const real ex1 = __ldg(Ex + gn), ey1 = __ldg(Ey + gn);
+    const real ezj = yin ? __ldg(Ez + g + pitch) : real(0);
+    const real exj = yin ? __ldg(Ex + g + pitch) : real(0);
+    const real ezi = xin ? __ldg(Ez + g + 1) : real(0);
+    const real eyi = xin ? __ldg(Ey + g + 1) : real(0);
+    real hx = __ldg(a.hin[0] + g), hy = __ldg(a.hin[1] + g), hz = __ldg(a.hin[2] + g);
+    const real chx = __ldg(a.chx + i), chy = __ldg(a.chy + j), cz = a.cz;
+    const real dEz_y = ezj - ez, dEy_z = ey1 - ey, dEx_z = ex1 - ex;
+    const real dEz_x = ezi - ez, dEy_x = eyi - ey, dEx_y = exj - ex;
+    hx = hx - chy * dEz_y + cz * dEy_z;
+    hy = hy - cz * dEx_z + chx * dEz_x;
+    hz = hz - chx * dEy_x + chy * dEx_y;
+    if (GEN && a.npml > 0) {
+        const int npml = a.npml, w2 = 2 * npml;
+        if (i < npml || i >= nx - npml) {
+            const int ii = i < npml ? i : i - nx + w2;
+            const int q = (k * ny + j) * w2 + ii;
+            const real b = a.bhx[ii], aa = a.ahx[ii];
+            const real p0 = b * a.phx_in[0][q] + aa * dEz_x;   // Hyx
+            const real p1 = b * a.phx_in[1][q] + aa * dEy_x;   // Hzx
+            hy += p0;
+            hz -= p1;
+            a.phx_out[0][q] = p0; a.phx_out[1][q] = p1;
+        }
+        if (j < npml || j >= ny - npml) {
+            const int jj = j < npml ? j : j - ny + w2;
+            const int q = (k * w2 + jj) * pitch + i;
+            const real b = a.bhy[jj], aa = a.ahy[jj];
+            const real p0 = b * a.phy_in[0][q] + aa * dEz_y;   // Hxy
+            const real p1 = b * a.phy_in[1][q] + aa * dEx_y;   // Hzy
+            hx -= p0;
+            hz += p1;
+            a.phy_out[0][q] = p0; a.phy_out[1][q] = p1;
+        }
+    }
+    if (a.smask) {
+        const int col = j * nx + i;
+        const uint8_t mk = __ldg(a.smask + col) & 0x38;
+        if (mk) {
+            const Cpx<real> u = plane_factor(a, k, th);
+            if (mk & 0x08) hx += src_add(a, 3, col, u);
+            if (mk & 0x10) hy += src_add(a, 4, col, u);
+            if (mk & 0x20) hz += src_add(a, 5, col, u);
+        }
+    }
+    a.hout[0][g] = hx; a.hout[1][g] = hy; a.hout[2][g] = hz;
+}
+
+template <typename real, bool GEN>
+__device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, int i, int j, int k)
+{
+    using Acc = FluAcc<real>;
+    using acc_t = typename Acc::T;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
+    if (GEN && (i >= nx || j >= ny)) return;
+    const int plane = pitch * ny, g = k * plane + j * pitch + i;
+    const int gm = (k == 0) ? g + (nz - 1) * plane : g - plane;
+    const real* __restrict__ Hx = a.hout[0];   // H^{n+1/2}
+    const real* __restrict__ Hy = a.hout[1];
+    const real* __restrict__ Hz = a.hout[2];
+    const bool xlo = !GEN || i > 0, ylo = !GEN || j > 0;
+    const real hx = __ldg(Hx + g), hy = __ldg(Hy + g), hz = __ldg(Hz + g);
+    const real hxm = __ldg(Hx + gm), hym = __ldg(Hy + gm);
+    const real hyi = xlo ? __ldg(Hy + g - 1) : real(0);
+    const real hzi = xlo ? __ldg(Hz + g - 1) : real(0);
+    const real hxj = ylo ? __ldg(Hx + g - pitch) : real(0);
+    const real hzj = ylo ? __ldg(Hz + g - pitch) : real(0);
+    const real ex = __ldg(a.ein[0] + g), ey = __ldg(a.ein[1] + g), ez = __ldg(a.ein[2] + g);
+    const real cex = __ldg(a.cex + i), cey = __ldg(a.cey + j), cz = a.cz;
+    const real dHz_y = hz - hzj, dHy_z = hy - hym, dHx_z = hx - hxm;
+    const real dHz_x = hz - hzi, dHy_x = hy - hyi, dHx_y = hx - hxj;
+    real nex = ex + cey * dHz_y - cz * dHy_z;
+    real ney = ey + cz * dHx_z - cex * dHz_x;
+    real nez = ez + cex * dHy_x - cey * dHx_y;
+    if (GEN && a.npml > 0) {
+        const int npml = a.npml, w2 = 2 * npml;
+        if (i < npml || i >= nx - npml) {
+            const int ii = i < npml ? i : i - nx + w2;
+            const int q = (k * ny + j) * w2 + ii;
+            const real b = a.bex[ii], aa = a.aex[ii];
+            const real p0 = b * a.pex[0][q] + aa * dHz_x;   // Eyx
+            const real p1 = b * a.pex[1][q] + aa * dHy_x;   // Ezx
+            a.pex[0][q] = p0; a.pex[1][q] = p1;
+            ney -= p0;
+            nez += p1;
+        }
+        if (j < npml || j >= ny - npml) {
+            const int jj = j < npml ? j : j - ny + w2;
+            const int q = (k * w2 + jj) * pitch + i;
+            const real b = a.bey[jj], aa = a.aey[jj];
+            const real p0 = b * a.pey[0][q] + aa * dHz_y;   // Exy
+            const real p1 = b * a.pey[1][q] + aa * dHx_y;   // Ezy
+            a.pey[0][q] = p0; a.pey[1][q] = p1;
+            nex += p0;
+            nez -= p1;
+        }
+    }
+    if (a.smask) {
+        const int col = j * nx + i;
+        const uint8_t mk = __ldg(a.smask + col) & 0x07;
+        if (mk) {
+            const Cpx<real> u = plane_factor(a, k, te);
+            if (mk & 0x01) nex += src_add(a, 0, col, u);
+            if (mk & 0x02) ney += src_add(a, 1, col, u);
+            if (mk & 0x04) nez += src_add(a, 2, col, u);
+        }
+    }
+    if (GEN) {
+        if (j == 0) { nex = real(0); nez = real(0); }   // PEC: tangential E
+        if (i == 0) { ney = real(0); nez = real(0); }
+    }
+    a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez;
+
+    if (a.fluence) {
+        // cell centre (i+1/2, j+1/2, k+1/2): E over four edges, Hbar over two
+        // faces and two times (the 1/16 is folded into dt16)
+        const real* __restrict__ Ex = a.ein[0];
+        const real* __restrict__ Ey = a.ein[1];
+        const real* __restrict__ Ez = a.ein[2];
+        const real* __restrict__ Ox = a.hin[0];   // H^{n-1/2}
+        const real* __restrict__ Oy = a.hin[1];
+        const real* __restrict__ Oz = a.hin[2];
+        const int gn = (k + 1 == nz) ? g - k * plane : g + plane;
+        const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
+        const real ex1 = __ldg(Ex + gn), ey1 = __ldg(Ey + gn);
+        const real exj = yin ? __ldg(Ex + g + pitch) : real(0);
+        const real exj1 = yin ? __ldg(Ex + gn + pitch) : real(0);
+        const real eyi = xin ? __ldg(Ey + g + 1) : real(0);
+        const real eyi1 = xin ? __ldg(Ey + gn + 1) : real(0);
+        const real ezi = xin ? __ldg(Ez + g + 1) : real(0);
+        const real ezj = yin ? __ldg(Ez + g + pitch) : real(0);
+        const real ezij = (xin && yin) ? __ldg(Ez + g + pitch + 1) : real(0);
+        const real hxi = xin ? __ldg(Hx + g + 1) : real(0);
+        const real hyj = yin ? __ldg(Hy + g + pitch) : real(0);
+        const real hz1 = __ldg(Hz + gn);
+        const real ox = __ldg(Ox + g), oy = __ldg(Oy + g), oz = __ldg(Oz + g), oz1 = __ldg(Oz + gn);
+        const real oxi = xin ? __ldg(Ox + g + 1) : real(0);
+        const real oyj = yin ? __ldg(Oy + g + pitch) : real(0);
+        const real cx = (ex + exj) + (ex1 + exj1);
+        const real cy = (ey + eyi) + (ey1 + eyi1);
+        const real cc = (ez + ezi) + (ezj + ezij);
+        const real hbx = (ox + hx) + (oxi + hxi);
+        const real hby = (oy + hy) + (oyj + hyj);
+        const real hbz = (oz + hz) + (oz1 + hz1);
+        const real sx = cy * hbz - cc * hby;
+        const real sy = cc * hbx - cx * hbz;
+        const real sz = cx * hby - cy * hbx;
+        acc_t* F = static_cast<acc_t*>(a.fluence);
+        const real dt16 = real(a.dt) * real(0.0625);
+        F[g] = Acc::add(F[g], vec_norm(sx * sx + sy * sy + sz * sz) * dt16);
+    }
+}
+
+// Grid: (ceil(nx/32), ceil(ny/TY), nz) CTAs of 32 x TY threads, one cell each.
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_h_cell(const StepArgs<real> a, const StepTime<real> t)
+{
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int nx = a.nx, ny = a.ny, npml = a.npml;
+    const bool gen = i0 + 32 >= nx || j0 + TY >= ny ||
+                     (npml > 0 && (i0 < npml || i0 + 31 >= nx - npml || j0 < npml || j0 + TY - 1 >= ny - npml));
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (gen) h_cell<real, true>(a, t.th, i, j, k);
+    else h_cell<real, false>(a, t.th, i, j, k);
+}
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_e_cell(const StepArgs<real> a, const StepTime<real> t)
+{
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int nx = a.nx, ny = a.ny, npml = a.npml;
+    const bool gen = i0 == 0 || j0 == 0 || i0 + 32 >= nx || j0 + TY >= ny ||
+                     (npml > 0 && (i0 < npml || i0 + 31 >= nx - npml || j0 < npml || j0 + TY - 1 >= ny - npml));
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (gen) e_cell<real, true>(a, t.te, i, j, k);
+    else e_cell<real, false>(a, t.te, i, j, k);
+}
+
+}  // namespace fdtd

@@ -67,15 +67,24 @@ struct StepArgs {
     const double2* scoef;    // [6][ny][nx]  FP64 antenna coefficients
     const void* scoefr;      // the same in the field precision (float2 / double2)
     const double2* zph;      // [nz]: e^{i beta k dz} (coefficients carry the half-cell z offset)
+    const void* zphr;        // the same in the field precision (float2 / double2)
     SrcTime st;
 };
 
-__device__ __forceinline__ void source_time(const SrcTime& st, double t, double& c, double& s,
-                                            double& f)
+// Time factor of the soft source at time t: cos / sin of the phase
+// 2 pi frac(t') (t' = t, or t - T0 for the Gaussian) and the envelope f.
+// Host and device evaluate it in FP64.
+__host__ __device__ __forceinline__ void source_time(const SrcTime& st, double t, double& c, double& s,
+                                                     double& f)
 {
     double tp = st.gauss ? t - st.T0 : t;
     double ph = 2.0 * 3.14159265358979323846 * (tp - floor(tp));
+#ifdef __CUDA_ARCH__
     sincos(ph, &s, &c);
+#else
+    s = sin(ph);
+    c = cos(ph);
+#endif
     if (st.gauss) {
         double u = (t - st.T0) / st.T;
         f = exp(-u * u);

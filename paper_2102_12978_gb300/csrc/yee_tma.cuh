@@ -91,23 +91,22 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-template <typename real, int TY>
+// Box and ring geometry of a tile of 32 x TR columns (TR rows).
+template <typename real, int TR>
 struct TmaTile {
     static constexpr int TX = 32;
     static constexpr int XA = 16 / int(sizeof(real));   // x alignment in elements
     static constexpr int BX = TX + 2 * XA;              // E / H box width
-    static constexpr int EBY = TY + 2;                  // E box rows (j0-1 .. j0+TY)
-    static constexpr int HBY = TY + 2;                  // H box rows (j0-1 .. j0+TY; the last row
+    static constexpr int EBY = TR + 2;                  // E box rows (j0-1 .. j0+TR)
+    static constexpr int HBY = TR + 2;                  // H box rows (j0-1 .. j0+TR; the last row
                                                         // is read only at the +y wall, as zeros)
-    static constexpr int FBX = TX + 2, FBY = TY + 1;    // fluence box (i0-2 .., j0-1 ..)
+    static constexpr int FBX = TX + 2, FBY = TR + 1;    // fluence box (i0-2 .., j0-1 ..)
     static constexpr size_t al(size_t v) { return (v + 127) / 128 * 128; }
     static constexpr size_t EB = al(size_t(BX) * EBY * sizeof(real));
     static constexpr size_t HB = al(size_t(BX) * HBY * sizeof(real));
     static constexpr size_t FB = al(size_t(FBX) * FBY * 8);
     static constexpr size_t STAGE = 3 * EB + 3 * HB + FB;
-    static constexpr int PX = TX + 2, PY = TY + 2, P = PX * PY;   // H^{n+1/2} and H-bar rings
-    static constexpr int NT = TX * TY;
-    static constexpr int NHH = TX + TY + 1;
+    static constexpr int PX = TX + 2, PY = TR + 2, P = PX * PY;   // H^{n+1/2} ring
     static constexpr uint32_t E_BYTES = uint32_t(BX * EBY * sizeof(real));
     static constexpr uint32_t H_BYTES = uint32_t(BX * HBY * sizeof(real));
     static constexpr uint32_t F_BYTES = uint32_t(FBX * FBY * 8);
@@ -127,51 +126,43 @@ template <typename real> struct Cpx { real x, y; };
 __device__ __forceinline__ double vec_norm(double x) { return sqrt(x); }
 __device__ __forceinline__ float vec_norm(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
-// Per-column constants of one H cell (own or halo): CPML shell membership,
-// profile values, compact psi offsets, antenna mask.
+// Per-column constants of one H cell: curl coefficients, CPML shell indices
+// (-1 outside the shell; the profile values are re-read from the small,
+// cache-resident tables), antenna mask.
 template <typename real>
 struct HCol {
     bool valid;
     int ci, cj;
     real chx, chy;
-    bool xs, ys;
-    real bx, ax, by, ay;
-    int pxo, pyo;          // psi offsets within one plane of the x / y shell arrays
+    int ii, jj;            // x / y shell index, or -1
     uint8_t mk;
 };
 
 template <typename real, bool GEN, bool SRC>
-__device__ __forceinline__ HCol<real> make_hcol(const StepArgs<real>& a, int ci, int cj)
+__device__ __forceinline__ HCol<real> make_hcol(const StepArgs<real>& a, int ci, int cj, bool valid)
 {
     HCol<real> c;
-    c.valid = ci >= 0 && ci < a.nx && cj >= 0 && cj < a.ny;
-    if (!GEN) c.valid = ci != -1 || cj != -1;   // interior block: only "no cell" is invalid
+    c.valid = valid;
     c.ci = ci; c.cj = cj;
-    c.chx = real(0); c.chy = real(0); c.xs = false; c.ys = false;
-    c.bx = c.ax = c.by = c.ay = real(0); c.pxo = c.pyo = 0; c.mk = 0;
-    if (!c.valid) return c;
+    c.chx = real(0); c.chy = real(0); c.ii = -1; c.jj = -1; c.mk = 0;
+    if (!valid) return c;
     c.chx = a.chx[ci]; c.chy = a.chy[cj];
     const int npml = a.npml, w2 = 2 * npml;
-    if (GEN && npml > 0 && (ci < npml || ci >= a.nx - npml)) {
-        const int ii = ci < npml ? ci : ci - a.nx + w2;
-        c.xs = true; c.bx = a.bhx[ii]; c.ax = a.ahx[ii]; c.pxo = cj * w2 + ii;
-    }
-    if (GEN && npml > 0 && (cj < npml || cj >= a.ny - npml)) {
-        const int jj = cj < npml ? cj : cj - a.ny + w2;
-        c.ys = true; c.by = a.bhy[jj]; c.ay = a.ahy[jj]; c.pyo = jj * a.pitch + ci;
-    }
+    if (GEN && npml > 0 && (ci < npml || ci >= a.nx - npml)) c.ii = ci < npml ? ci : ci - a.nx + w2;
+    if (GEN && npml > 0 && (cj < npml || cj >= a.ny - npml)) c.jj = cj < npml ? cj : cj - a.ny + w2;
     if (SRC && a.smask) c.mk = a.smask[cj * a.nx + ci];
     return c;
 }
 
-// H^{n+1/2} of one cell from the staged E planes k (e0*) and k+1 (e1*).
+// H^{n+1/2} of one cell from the staged E planes k (e0*) and k+1 (e1*); the
+// CPML psi of the H side (old values in pp, prefetched from the read copy)
+// is written, if `store`, to the write copy.
 template <typename real, int BX, bool GEN, bool SRC>
 __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCol<real>& c,
                                               const real* __restrict__ e0x, const real* __restrict__ e0y,
                                               const real* __restrict__ e0z, const real* __restrict__ e1x,
-                                              const real* __restrict__ e1y, int idx, int kw, int psx_plane,
-                                              int psy_plane, real& hx, real& hy, real& hz, Cpx<real> u,
-                                              bool store, const real (&pp)[4])
+                                              const real* __restrict__ e1y, int idx, int kw, real& hx, real& hy,
+                                              real& hz, Cpx<real> u, bool store, const real (&pp)[4])
 {
     const real ex = e0x[idx], ey = e0y[idx], ez = e0z[idx];
     const real dEz_y = e0z[idx + BX] - ez;
@@ -183,18 +174,22 @@ __device__ __forceinline__ void tma_compute_h(const StepArgs<real>& a, const HCo
     hx = hx - c.chy * dEz_y + a.cz * dEy_z;
     hy = hy - a.cz * dEx_z + c.chx * dEz_x;
     hz = hz - c.chx * dEy_x + c.chy * dEx_y;
-    if (GEN && c.xs) {
-        const int q = kw * psx_plane + c.pxo;
-        const real p0 = c.bx * pp[0] + c.ax * dEz_x;   // Hyx (old value prefetched)
-        const real p1 = c.bx * pp[1] + c.ax * dEy_x;   // Hzx
+    if (GEN && c.ii >= 0) {
+        const int w2 = 2 * a.npml;
+        const int q = (kw * a.ny + c.cj) * w2 + c.ii;
+        const real b = a.bhx[c.ii], aa = a.ahx[c.ii];
+        const real p0 = b * pp[0] + aa * dEz_x;   // Hyx (old value prefetched)
+        const real p1 = b * pp[1] + aa * dEy_x;   // Hzx
         hy += p0;
         hz -= p1;
         if (store) { a.phx_out[0][q] = p0; a.phx_out[1][q] = p1; }
     }
-    if (GEN && c.ys) {
-        const int q = kw * psy_plane + c.pyo;
-        const real p0 = c.by * pp[2] + c.ay * dEz_y;   // Hxy
-        const real p1 = c.by * pp[3] + c.ay * dEx_y;   // Hzy
+    if (GEN && c.jj >= 0) {
+        const int w2 = 2 * a.npml;
+        const int q = (kw * w2 + c.jj) * a.pitch + c.ci;
+        const real b = a.bhy[c.jj], aa = a.ahy[c.jj];
+        const real p0 = b * pp[2] + aa * dEz_y;   // Hxy
+        const real p1 = b * pp[3] + aa * dEx_y;   // Hzy
         hx -= p0;
         hz += p1;
         if (store) { a.phy_out[0][q] = p0; a.phy_out[1][q] = p1; }
@@ -236,7 +231,7 @@ __device__ __forceinline__ void tma_fluence_cell(const real* __restrict__ emx, c
 }
 
 // Shared memory of one CTA running tma_march.
-template <typename real, int TY, int S>
+template <typename real, int TR, int S>
 struct MarchSmem {
     unsigned char* base;   // S stages
     real* sH;              // [3][3][P] ring of H^{n+1/2}
@@ -247,41 +242,43 @@ struct MarchSmem {
     int* abort_flag;
 };
 
-// One CTA marches one (32 x TY) x [kb, ke) block of a grid through one Yee
-// step.  gq0 is the CTA's running plane counter (stage = gq % S, mbarrier
-// parity = (gq / S) & 1), so that a persistent CTA can march many blocks
-// with its mbarriers initialised once.  Returns the updated counter, or -1
-// after a timed-out wait (the error word is raised).
-// GEN: the block may touch the CPML shell, a PEC wall, the last (wall or
-// ragged) tile of an axis; every per-cell check is compiled in.  !GEN: an
-// interior block, where all of them are known false and compiled out.
-// SRC: the block holds antenna cells (compiled out otherwise).
-template <typename real, int TY, int S, bool GEN, bool SRC>
+// One CTA of TW = TR / R warps marches one (32 x TR) x [kb, ke) block of a
+// grid through one Yee step; each thread owns R rows of its column (rows
+// ty, ty + TW, ...), which shares the per-plane control, waits and barrier
+// between R independent cells.  gq0 is the CTA's running plane counter
+// (stage = gq % S, mbarrier parity = (gq / S) & 1), so that a persistent CTA
+// can march many blocks with its mbarriers initialised once.  Returns the
+// updated counter, or -1 after a timed-out wait (the error word is raised).
+// GEN: the block may touch the CPML shell, a PEC wall or the last (wall or
+// ragged) tile of an axis, and every per-cell check is compiled in; !GEN
+// compiles them out.  SRC: the block holds antenna cells.
+template <typename real, int TR, int R, int S, bool GEN, bool SRC>
 __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps& m, long long n, int i0, int j0,
-                                         int kb, int ke, int* err, const MarchSmem<real, TY, S>& sm, int gq0)
+                                         int kb, int ke, int* err, const MarchSmem<real, TR, S>& sm, int gq0)
 {
     static_assert(S >= 5, "the ring needs S >= 5 stages (lead of S-3 planes)");
-    using T = TmaTile<real, TY>;
+    static_assert(TR % R == 0, "tile rows must be a multiple of the rows per thread");
+    using T = TmaTile<real, TR>;
     using Acc = FluAcc<real>;
     using acc_t = typename Acc::T;
-    constexpr int TX = T::TX, BX = T::BX, XA = T::XA, PX = T::PX, P = T::P, NT = T::NT, FBX = T::FBX;
-    static_assert(T::NHH <= NT, "tile too small for its halo");
+    constexpr int TX = T::TX, BX = T::BX, XA = T::XA, PX = T::PX, P = T::P, FBX = T::FBX;
+    constexpr int TW = TR / R;                       // warps
+    constexpr int NT = 32 * TW;
+    constexpr int HS = int(T::HB / sizeof(real));
+    static_assert(TR + 1 <= 32, "the halo column must fit one warp");
+    static_assert(TW >= 2, "the halo row and column need two warps");
     unsigned char* base = sm.base;
     real* sH = sm.sH;
     uint64_t* bars = sm.bars;
     double* tf = sm.tf;
     int& abort_flag = *sm.abort_flag;
 
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    constexpr int PRODUCER = (TY - 1) * 32;          // lane 0 of the last warp issues TMA
+    const int tx = threadIdx.x, tw = threadIdx.y, tid = tw * TX + tx;
+    constexpr int PRODUCER = (TW - 1) * 32;          // lane 0 of the last warp issues TMA
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
     const int plane = pitch * ny;
     const int w2 = 2 * a.npml, psx_plane = ny * w2, psy_plane = w2 * pitch;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool own = !GEN || ((i < nx) && (j < ny));
-    const int so = (ty + 1) * PX + (tx + 1);        // own cell in the sH / sB rings
-    const int eo = (ty + 1) * BX + (tx + XA);        // own cell in an E / H box
-    const int gcol = j * pitch + i;
+    const int i = i0 + tx;
     const bool do_flu = a.fluence != nullptr;
     acc_t* F = static_cast<acc_t*>(a.fluence);
     const real dtr = real(a.dt);
@@ -289,7 +286,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
 
     auto stage = [&](int s) { return base + s * T::STAGE; };
 
-    // ---- TMA producer (thread 0): plane q of this segment into stage q % S
+    // ---- TMA producer: plane q of this block into stage (gq0 + q) % S
     auto issue = [&](int q) {
         const int p = kb - 1 + q;
         const int pw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
@@ -325,14 +322,12 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         for (; issued < S - 3 && issued < Q; ++issued) issue(issued);
     }
     // source factors f e^{i (beta z_k - omega t')} of every plane of this
-    // block, phase in FP64, stored in the field precision (read after the
-    // first barrier of the march)
+    // block, phase in FP64, stored in the field precision
     if (SRC && a.smask) {
         for (int q = tid; q < Q; q += NT) {
             const int p = kb - 1 + q;
             const int pw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
             const double2 z = a.zph[pw];
-            // z (c - i s) f
             sm.uE[q].x = real((z.x * tf[0] + z.y * tf[1]) * tf[2]);
             sm.uE[q].y = real((z.y * tf[0] - z.x * tf[1]) * tf[2]);
             sm.uH[q].x = real((z.x * tf[3] + z.y * tf[4]) * tf[5]);
@@ -340,61 +335,80 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         }
     }
 
-    // per-column constants: own cell and this thread's H halo cell
-    const HCol<real> co = make_hcol<real, GEN, SRC>(a, own ? i : -1, own ? j : -1);
-    const real cex = own ? a.cex[i] : real(0), cey = own ? a.cey[j] : real(0);
-    bool exs = false, eys = false;
-    real ebx = 0, eax = 0, eby = 0, eay = 0;
-    int epx = 0, epy = 0;
-    if (GEN && own && w2 > 0) {
-        if (i < a.npml || i >= nx - a.npml) {
-            const int ii = i < a.npml ? i : i - nx + w2;
-            exs = true; ebx = a.bex[ii]; eax = a.aex[ii]; epx = j * w2 + ii;
+    // ---- per-row constants of this thread's R cells
+    int jr[R], so[R], eo[R], gcol[R];
+    bool own[R], flu_base[R], xw[R], yw[R];
+    HCol<real> co[R];
+    real cex = real(0), cey[R];
+    int eii[R], ejj[R];                              // E-side CPML shell indices or -1
+    #pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int ty = tw + r * TW;
+        const int j = j0 + ty;
+        jr[r] = j;
+        so[r] = (ty + 1) * PX + (tx + 1);
+        eo[r] = (ty + 1) * BX + (tx + XA);
+        gcol[r] = j * pitch + i;
+        own[r] = !GEN || ((i < nx) && (j < ny));
+        co[r] = make_hcol<real, GEN, SRC>(a, i, j, own[r]);
+        cey[r] = own[r] ? a.cey[j] : real(0);
+        eii[r] = -1; ejj[r] = -1;
+        if (GEN && own[r] && w2 > 0) {
+            if (i < a.npml || i >= nx - a.npml) eii[r] = i < a.npml ? i : i - nx + w2;
+            if (j < a.npml || j >= ny - a.npml) ejj[r] = j < a.npml ? j : j - ny + w2;
         }
-        if (j < a.npml || j >= ny - a.npml) {
-            const int jj = j < a.npml ? j : j - ny + w2;
-            eys = true; eby = a.bey[jj]; eay = a.aey[jj]; epy = jj * pitch + i;
-        }
+        flu_base[r] = !GEN || ((i >= 1) && (j >= 1) && (i <= nx) && (j <= ny));
+        xw[r] = GEN && (tx == TX - 1) && (i == nx - 1) && (j >= 1) && (j <= ny);
+        yw[r] = GEN && (ty == TR - 1) && (j == ny - 1) && (i >= 1) && (i <= nx);
     }
-    // halo H cells: the row j0-1 on warp 0, the column i0-1 (TY+1 cells) on
-    // warp TY/2, so that no warp carries both; the TMA producer is lane 0 of
-    // warp TY-1
+    if (own[0]) cex = a.cex[i];
+    // halo H cells: the row j0-1 on warp 0, the column i0-1 (TR+1 cells) on
+    // warp TW/2, so that no warp carries both
     int hs_h = 0, he_h = 0, hi_h = -1, hj_h = -1;
-    if (ty == 0) { hi_h = i0 + tx; hj_h = j0 - 1; hs_h = tx + 1; he_h = tx + XA; }
-    else if (ty == TY / 2 && tx <= TY) {
-        const int jj = tx;
-        hi_h = i0 - 1; hj_h = j0 - 1 + jj; hs_h = jj * PX; he_h = jj * BX + XA - 1;
+    if (tw == 0) { hi_h = i0 + tx; hj_h = j0 - 1; hs_h = tx + 1; he_h = tx + XA; }
+    else if (tw == TW / 2 && tx <= TR) {
+        hi_h = i0 - 1; hj_h = j0 - 1 + tx; hs_h = tx * PX; he_h = tx * BX + XA - 1;
     }
-    const HCol<real> ch = make_hcol<real, GEN, SRC>(a, hi_h, hj_h);
-    // fluence cells: base (i-1, j-1) and, in the last tiles, the wall cells
-    const bool flu_base = !GEN || ((i >= 1) && (j >= 1) && (i <= nx) && (j <= ny));
-    const bool xw = GEN && (tx == TX - 1) && (i == nx - 1) && (j >= 1) && (j <= ny);
-    const bool yw = GEN && (ty == TY - 1) && (j == ny - 1) && (i >= 1) && (i <= nx);
+    const bool hvalid = GEN ? (hi_h >= 0 && hi_h < nx && hj_h >= 0 && hj_h < ny) : (hi_h != -1 || hj_h != -1);
+    const HCol<real> ch = make_hcol<real, GEN, SRC>(a, hi_h, hj_h, hvalid);
 
-    // CPML psi of the next plane, prefetched into registers one iteration ahead
-    // (H side: own and halo cell, read copy; E side: own cell, updated in place)
-    real ppo[4] = {0, 0, 0, 0}, pph[4] = {0, 0, 0, 0}, ppe[4] = {0, 0, 0, 0};
-    auto fetch_psi_h = [&](const HCol<real>& c, int plane_w, real (&pp)[4]) {
+    // CPML psi of the next plane, prefetched into registers one iteration
+    // ahead (H side: own and halo cells, read copy; E side: own cells,
+    // updated in place)
+    real ppo[R][4], ppe[R][4], pph[4] = {0, 0, 0, 0};
+    #pragma unroll
+    for (int r = 0; r < R; ++r)
+        #pragma unroll
+        for (int c = 0; c < 4; ++c) { ppo[r][c] = real(0); ppe[r][c] = real(0); }
+    auto fetch_psi_h = [&](const HCol<real>& c, int pw, real (&pp)[4]) {
         if (!GEN) return;
-        if (c.xs) {
-            const int q = plane_w * psx_plane + c.pxo;
+        if (c.ii >= 0) {
+            const int q = pw * psx_plane + c.cj * w2 + c.ii;
             pp[0] = a.phx_in[0][q]; pp[1] = a.phx_in[1][q];
         }
-        if (c.ys) {
-            const int q = plane_w * psy_plane + c.pyo;
+        if (c.jj >= 0) {
+            const int q = pw * psy_plane + c.jj * pitch + c.ci;
             pp[2] = a.phy_in[0][q]; pp[3] = a.phy_in[1][q];
         }
     };
-    auto fetch_psi_e = [&](int plane_w) {
-        if (!GEN) return;
-        if (exs) { const int q = plane_w * psx_plane + epx; ppe[0] = a.pex[0][q]; ppe[1] = a.pex[1][q]; }
-        if (eys) { const int q = plane_w * psy_plane + epy; ppe[2] = a.pey[0][q]; ppe[3] = a.pey[1][q]; }
+    auto fetch_psi = [&](int pw_h, int pw_e, bool e) {
+        if (GEN) {
+            #pragma unroll
+            for (int r = 0; r < R; ++r) {
+                fetch_psi_h(co[r], pw_h, ppo[r]);
+                if (e && eii[r] >= 0) {
+                    const int q = pw_e * psx_plane + jr[r] * w2 + eii[r];
+                    ppe[r][0] = a.pex[0][q]; ppe[r][1] = a.pex[1][q];
+                }
+                if (e && ejj[r] >= 0) {
+                    const int q = pw_e * psy_plane + ejj[r] * pitch + i;
+                    ppe[r][2] = a.pey[0][q]; ppe[r][3] = a.pey[1][q];
+                }
+            }
+            fetch_psi_h(ch, pw_h, pph);
+        }
     };
-    {
-        const int k0w = kb - 1 < 0 ? kb - 1 + nz : kb - 1;
-        fetch_psi_h(co, k0w, ppo);
-        fetch_psi_h(ch, k0w, pph);
-    }
+    fetch_psi(kb - 1 < 0 ? kb - 1 + nz : kb - 1, 0, false);
 
     int waited = -1;
     int kw = kb - 1 < 0 ? kb - 1 + nz : kb - 1;    // wrapped plane of iteration k
@@ -427,25 +441,27 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             const real* e1x = reinterpret_cast<const real*>(stn);
             const real* e1y = reinterpret_cast<const real*>(stn + T::EB);
             const real* hb = reinterpret_cast<const real*>(st0 + 3 * T::EB);
-            constexpr int HS = int(T::HB / sizeof(real));
             real* hs = sH + r0 * 3 * P;
             const bool write_k = (k >= kb) && (k < ke);
-            if (co.valid) {
-                const real ox = hb[eo], oy = hb[HS + eo], oz = hb[2 * HS + eo];
-                real hx = ox, hy = oy, hz = oz;
-                tma_compute_h<real, BX, GEN, SRC>(a, co, e0x, e0y, e0z, e1x, e1y, eo, kw, psx_plane, psy_plane, hx, hy, hz,
-                                        sm.uH[q], write_k, ppo);
-                hs[so] = hx; hs[P + so] = hy; hs[2 * P + so] = hz;
-                if (write_k) {
-                    const int g = kw * plane + gcol;
-                    a.hout[0][g] = hx; a.hout[1][g] = hy; a.hout[2][g] = hz;
+            Cpx<real> uh;
+            if (SRC) uh = sm.uH[q];
+            #pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (co[r].valid) {
+                    real hx = hb[eo[r]], hy = hb[HS + eo[r]], hz = hb[2 * HS + eo[r]];
+                    tma_compute_h<real, BX, GEN, SRC>(a, co[r], e0x, e0y, e0z, e1x, e1y, eo[r], kw, hx, hy, hz, uh,
+                                                      write_k, ppo[r]);
+                    hs[so[r]] = hx; hs[P + so[r]] = hy; hs[2 * P + so[r]] = hz;
+                    if (write_k) {
+                        const int g = kw * plane + gcol[r];
+                        a.hout[0][g] = hx; a.hout[1][g] = hy; a.hout[2][g] = hz;
+                    }
                 }
             }
             if (ch.valid) {
-                const real ox = hb[he_h], oy = hb[HS + he_h], oz = hb[2 * HS + he_h];
-                real hx = ox, hy = oy, hz = oz;
-                tma_compute_h<real, BX, GEN, SRC>(a, ch, e0x, e0y, e0z, e1x, e1y, he_h, kw, psx_plane, psy_plane, hx, hy,
-                                        hz, sm.uH[q], false, pph);
+                real hx = hb[he_h], hy = hb[HS + he_h], hz = hb[2 * HS + he_h];
+                tma_compute_h<real, BX, GEN, SRC>(a, ch, e0x, e0y, e0z, e1x, e1y, he_h, kw, hx, hy, hz, uh, false,
+                                                  pph);
                 hs[hs_h] = hx; hs[P + hs_h] = hy; hs[2 * P + hs_h] = hz;
             }
         }
@@ -454,58 +470,67 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         const int km = k - 1;
         const int kmw = kw == 0 ? nz - 1 : kw - 1;
         const int sm1 = s0 == 0 ? S - 1 : s0 - 1;
-        if (own && km >= kb && km < ke) {
+        if (km >= kb && km < ke) {
             const real* h0 = sH + r1 * 3 * P;
             const real* h1 = sH + r2 * 3 * P;
             const unsigned char* stm = stage(sm1);
-            const real ex = reinterpret_cast<const real*>(stm)[eo];
-            const real ey = reinterpret_cast<const real*>(stm + T::EB)[eo];
-            const real ez = reinterpret_cast<const real*>(stm + 2 * T::EB)[eo];
-            const real hx0 = h0[so], hy0 = h0[P + so], hz0 = h0[2 * P + so];
-            const real dHz_y = hz0 - h0[2 * P + so - PX];
-            const real dHy_z = hy0 - h1[P + so];
-            const real dHx_z = hx0 - h1[so];
-            const real dHz_x = hz0 - h0[2 * P + so - 1];
-            const real dHy_x = hy0 - h0[P + so - 1];
-            const real dHx_y = hx0 - h0[so - PX];
-            real nex = ex + cey * dHz_y - a.cz * dHy_z;
-            real ney = ey + a.cz * dHx_z - cex * dHz_x;
-            real nez = ez + cex * dHy_x - cey * dHx_y;
-            if (GEN && exs) {
-                const int qq = kmw * psx_plane + epx;
-                const real p0 = ebx * ppe[0] + eax * dHz_x;   // Eyx (old value prefetched)
-                const real p1 = ebx * ppe[1] + eax * dHy_x;   // Ezx
-                a.pex[0][qq] = p0; a.pex[1][qq] = p1;
-                ney -= p0;
-                nez += p1;
+            const real* epx = reinterpret_cast<const real*>(stm);
+            const real* epy = reinterpret_cast<const real*>(stm + T::EB);
+            const real* epz = reinterpret_cast<const real*>(stm + 2 * T::EB);
+            Cpx<real> ue;
+            if (SRC) ue = sm.uE[q - 1];
+            #pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!own[r]) continue;
+                const int o = so[r];
+                const real ex = epx[eo[r]], ey = epy[eo[r]], ez = epz[eo[r]];
+                const real hx0 = h0[o], hy0 = h0[P + o], hz0 = h0[2 * P + o];
+                const real dHz_y = hz0 - h0[2 * P + o - PX];
+                const real dHy_z = hy0 - h1[P + o];
+                const real dHx_z = hx0 - h1[o];
+                const real dHz_x = hz0 - h0[2 * P + o - 1];
+                const real dHy_x = hy0 - h0[P + o - 1];
+                const real dHx_y = hx0 - h0[o - PX];
+                real nex = ex + cey[r] * dHz_y - a.cz * dHy_z;
+                real ney = ey + a.cz * dHx_z - cex * dHz_x;
+                real nez = ez + cex * dHy_x - cey[r] * dHx_y;
+                if (GEN && eii[r] >= 0) {
+                    const int qq = (kmw * ny + jr[r]) * w2 + eii[r];
+                    const real b = a.bex[eii[r]], aa = a.aex[eii[r]];
+                    const real p0 = b * ppe[r][0] + aa * dHz_x;   // Eyx (old value prefetched)
+                    const real p1 = b * ppe[r][1] + aa * dHy_x;   // Ezx
+                    a.pex[0][qq] = p0; a.pex[1][qq] = p1;
+                    ney -= p0;
+                    nez += p1;
+                }
+                if (GEN && ejj[r] >= 0) {
+                    const int qq = (kmw * w2 + ejj[r]) * pitch + i;
+                    const real b = a.bey[ejj[r]], aa = a.aey[ejj[r]];
+                    const real p0 = b * ppe[r][2] + aa * dHz_y;   // Exy
+                    const real p1 = b * ppe[r][3] + aa * dHx_y;   // Ezy
+                    a.pey[0][qq] = p0; a.pey[1][qq] = p1;
+                    nex += p0;
+                    nez -= p1;
+                }
+                if (SRC && (co[r].mk & 0x07)) {
+                    const int ncol = nx * ny, col = jr[r] * nx + i;
+                    const Cpx<real>* B = static_cast<const Cpx<real>*>(a.scoefr);
+                    if (co[r].mk & 0x01) { const Cpx<real> b = B[col]; nex += b.x * ue.x - b.y * ue.y; }
+                    if (co[r].mk & 0x02) { const Cpx<real> b = B[ncol + col]; ney += b.x * ue.x - b.y * ue.y; }
+                    if (co[r].mk & 0x04) { const Cpx<real> b = B[2 * ncol + col]; nez += b.x * ue.x - b.y * ue.y; }
+                }
+                if (GEN) {
+                    if (jr[r] == 0) { nex = real(0); nez = real(0); }    // PEC: tangential E
+                    if (i == 0) { ney = real(0); nez = real(0); }
+                }
+                const int g = kmw * plane + gcol[r];
+                a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez;
             }
-            if (GEN && eys) {
-                const int qq = kmw * psy_plane + epy;
-                const real p0 = eby * ppe[2] + eay * dHz_y;   // Exy
-                const real p1 = eby * ppe[3] + eay * dHx_y;   // Ezy
-                a.pey[0][qq] = p0; a.pey[1][qq] = p1;
-                nex += p0;
-                nez -= p1;
-            }
-            if (SRC && (co.mk & 0x07)) {
-                const int ncol = nx * ny, col = j * nx + i;
-                const Cpx<real>* B = static_cast<const Cpx<real>*>(a.scoefr);
-                const Cpx<real> u = sm.uE[q - 1];
-                if (co.mk & 0x01) { const Cpx<real> b = B[col]; nex += b.x * u.x - b.y * u.y; }
-                if (co.mk & 0x02) { const Cpx<real> b = B[ncol + col]; ney += b.x * u.x - b.y * u.y; }
-                if (co.mk & 0x04) { const Cpx<real> b = B[2 * ncol + col]; nez += b.x * u.x - b.y * u.y; }
-            }
-            if (GEN) {
-                if (j == 0) { nex = real(0); nez = real(0); }    // PEC: tangential E
-                if (i == 0) { ney = real(0); nez = real(0); }
-            }
-            const int g = kmw * plane + gcol;
-            a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez;
         }
 
         // ---- fluence of plane k-2: E planes k-2, k-1 and H-bar of k-2, k-1
         const int kf = k - 2;
-        if (do_flu && kf >= kb && kf < ke && (flu_base || xw || yw)) {
+        if (do_flu && kf >= kb && kf < ke) {
             const int kfw = kmw == 0 ? nz - 1 : kmw - 1;
             const int sm2 = sm1 == 0 ? S - 1 : sm1 - 1;
             const unsigned char* sa = stage(sm2);
@@ -518,33 +543,35 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
             const acc_t* fo = reinterpret_cast<const acc_t*>(sa + 3 * T::EB + 3 * T::HB);
             const real* hm = reinterpret_cast<const real*>(sa + 3 * T::EB);
             const real* hk = reinterpret_cast<const real*>(sb + 3 * T::EB);
-            const real* sm = sH + r2 * 3 * P;
-            const real* sk = sH + r1 * 3 * P;
-            constexpr int HS = int(T::HB / sizeof(real));
+            const real* smm = sH + r2 * 3 * P;
+            const real* skk = sH + r1 * 3 * P;
             const real dt16 = dtr * real(0.0625);
             const int gp = kfw * plane;
-            if (flu_base)
-                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo - BX - 1,
-                                                      so - PX - 1, fo[ty * FBX + tx + 1], dt16, F,
-                                                      gp + gcol - pitch - 1);
-            if (xw)
-                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo - BX, so - PX,
-                                                      fo[ty * FBX + tx + 2], dt16, F, gp + gcol - pitch);
-            if (yw)
-                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo - 1, so - 1,
-                                                      fo[(ty + 1) * FBX + tx + 1], dt16, F, gp + gcol - 1);
-            if (xw && yw)
-                tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, sm, sk, eo, so,
-                                                      fo[(ty + 1) * FBX + tx + 2], dt16, F, gp + gcol);
+            #pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int ty = tw + r * TW;
+                if (flu_base[r])
+                    tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, smm, skk, eo[r] - BX - 1,
+                                                          so[r] - PX - 1, fo[ty * FBX + tx + 1], dt16, F,
+                                                          gp + gcol[r] - pitch - 1);
+                if (GEN) {
+                    if (xw[r])
+                        tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, smm, skk, eo[r] - BX,
+                                                              so[r] - PX, fo[ty * FBX + tx + 2], dt16, F,
+                                                              gp + gcol[r] - pitch);
+                    if (yw[r])
+                        tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, smm, skk, eo[r] - 1,
+                                                              so[r] - 1, fo[(ty + 1) * FBX + tx + 1], dt16, F,
+                                                              gp + gcol[r] - 1);
+                    if (xw[r] && yw[r])
+                        tma_fluence_cell<real, BX, PX, P, HS>(emx, emy, emz, ekx, eky, hm, hk, smm, skk, eo[r], so[r],
+                                                              fo[(ty + 1) * FBX + tx + 2], dt16, F, gp + gcol[r]);
+                }
+            }
         }
 
         // prefetch psi for the next iteration: H at plane k+1, E at plane k
-        {
-            const int kn = (kw + 1 == nz) ? 0 : kw + 1;
-            fetch_psi_h(co, kn, ppo);
-            fetch_psi_h(ch, kn, pph);
-            fetch_psi_e(kw);
-        }
+        fetch_psi((kw + 1 == nz) ? 0 : kw + 1, kw, true);
         // rotate stage, parity and H-ring slots
         if (s0 + 1 == S) par ^= 1u;
         s0 = s1;
@@ -565,42 +592,45 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
 // Class of a block: general (touches the CPML shell, a PEC wall or the last
 // tile of an axis) or interior; an interior block also reports whether any of
 // its cells (own or low halo) carries an antenna point (CTA-wide vote).
-template <typename real, int TY>
+template <typename real, int TR, int R>
 __device__ __forceinline__ void block_class(const StepArgs<real>& a, int i0, int j0, bool& gen, bool& src)
 {
     const int nx = a.nx, ny = a.ny, npml = a.npml;
-    gen = i0 == 0 || j0 == 0 || i0 + 32 >= nx || j0 + TY >= ny ||
-          (npml > 0 && (i0 - 1 < npml || i0 + 31 >= nx - npml || j0 - 1 < npml || j0 + TY - 1 >= ny - npml));
+    gen = i0 == 0 || j0 == 0 || i0 + 32 >= nx || j0 + TR >= ny ||
+          (npml > 0 && (i0 - 1 < npml || i0 + 31 >= nx - npml || j0 - 1 < npml || j0 + TR - 1 >= ny - npml));
     src = false;
     if (!gen && a.smask) {
-        const int tx = threadIdx.x, ty = threadIdx.y;
-        bool mine = a.smask[(j0 + ty) * nx + i0 + tx] != 0;
-        if (ty == 0) mine = mine || a.smask[(j0 - 1) * nx + i0 + tx] != 0;
-        if (tx == 0) mine = mine || a.smask[(j0 + ty) * nx + i0 - 1] != 0;
-        if (tx == 0 && ty == 0) mine = mine || a.smask[(j0 - 1) * nx + i0 - 1] != 0;
+        constexpr int TW = TR / R;
+        const int tx = threadIdx.x, tw = threadIdx.y;
+        bool mine = false;
+        #pragma unroll
+        for (int r = 0; r < R; ++r) mine = mine || a.smask[(j0 + tw + r * TW) * nx + i0 + tx] != 0;
+        if (tw == 0) mine = mine || a.smask[(j0 - 1) * nx + i0 + tx] != 0;
+        if (tx == 0 && tw == 0)
+            for (int jj = -1; jj < TR; ++jj) mine = mine || a.smask[(j0 + jj) * nx + i0 - 1] != 0;
         src = __syncthreads_or(mine) != 0;
     }
 }
 
-template <typename real, int TY, int S>
+template <typename real, int TR, int R, int S>
 __device__ __forceinline__ int tma_march_any(const StepArgs<real>& a, const TmaMaps& m, long long n, int i0, int j0,
-                                             int kb, int ke, int* err, const MarchSmem<real, TY, S>& sm, int gq0)
+                                             int kb, int ke, int* err, const MarchSmem<real, TR, S>& sm, int gq0)
 {
     bool gen, src;
-    block_class<real, TY>(a, i0, j0, gen, src);
-    if (gen) return tma_march<real, TY, S, true, true>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
-    if (src) return tma_march<real, TY, S, false, true>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
-    return tma_march<real, TY, S, false, false>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
+    block_class<real, TR, R>(a, i0, j0, gen, src);
+    if (gen) return tma_march<real, TR, R, S, true, true>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
+    if (src) return tma_march<real, TR, R, S, false, true>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
+    return tma_march<real, TR, R, S, false, false>(a, m, n, i0, j0, kb, ke, err, sm, gq0);
 }
 
-template <typename real, int TY, int S>
-__device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init(int lz)
+template <typename real, int TR, int S>
+__device__ __forceinline__ MarchSmem<real, TR, S> march_smem_init(int lz)
 {
-    using T = TmaTile<real, TY>;
+    using T = TmaTile<real, TR>;
     extern __shared__ unsigned char smem_raw[];
     __shared__ double tf[6];
     __shared__ int abort_flag;
-    MarchSmem<real, TY, S> sm;
+    MarchSmem<real, TR, S> sm;
     sm.base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     sm.sH = reinterpret_cast<real*>(sm.base + S * T::STAGE);
     sm.uE = reinterpret_cast<Cpx<real>*>(sm.sH + 9 * T::P);
@@ -617,19 +647,21 @@ __device__ __forceinline__ MarchSmem<real, TY, S> march_smem_init(int lz)
     return sm;
 }
 
-// Minimum resident CTAs per SM requested from the register allocator: the
-// FP32 32x8 tile fits three CTAs in shared memory, so cap its registers.
-template <typename real, int TY> struct MinCtas { static constexpr int value = 1; };
-template <> struct MinCtas<float, 8> { static constexpr int value = 3; };
-template <> struct MinCtas<float, 4> { static constexpr int value = 4; };
+// Minimum resident CTAs per SM requested from the register allocator (the
+// shared memory of a 32x8 FP32 tile fits three CTAs).
+template <typename real, int TR, int R> struct MinCtas { static constexpr int value = 1; };
+template <> struct MinCtas<float, 8, 1> { static constexpr int value = 3; };
+template <> struct MinCtas<float, 8, 2> { static constexpr int value = 3; };
+template <> struct MinCtas<float, 4, 1> { static constexpr int value = 4; };
 
-template <typename real, int TY, int S>
-__global__ void __launch_bounds__(32 * TY, MinCtas<real, TY>::value)
+// Grid: (ceil(nx/32), ceil(ny/TR), ceil(nz/lz)) CTAs of 32 x (TR/R) threads.
+template <typename real, int TR, int R, int S>
+__global__ void __launch_bounds__(32 * (TR / R), MinCtas<real, TR, R>::value)
 yee_step_tma(const StepArgs<real> a, const __grid_constant__ TmaMaps m, long long n, int lz, int* err)
 {
-    const MarchSmem<real, TY, S> sm = march_smem_init<real, TY, S>(lz);
+    const MarchSmem<real, TR, S> sm = march_smem_init<real, TR, S>(lz);
     const int kb = blockIdx.z * lz;
-    tma_march_any<real, TY, S>(a, m, n, blockIdx.x * 32, blockIdx.y * TY, kb, min(kb + lz, a.nz), err, sm, 0);
+    tma_march_any<real, TR, R, S>(a, m, n, blockIdx.x * 32, blockIdx.y * TR, kb, min(kb + lz, a.nz), err, sm, 0);
 }
 
 }  // namespace fdtd
