@@ -28,6 +28,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "FDTD Gcell-updates/s FP32 vs FP64 at stated L2 error; % HBM roofline; adjoint s/step"
+
+# DRAM bytes (read + write) per launch of a kernel on the 256x256x128 FP32
+# workload, from one ncu capture of the kernel as it stands (summary and
+# command in profiles/); None where no capture of the current kernel exists.
+TRAFFIC: dict[str, float] = {}
 UNIT = "Gcell-updates/s"
 
 
@@ -39,13 +44,54 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def psi_per_cell(w) -> float:
+    """Mean number of CPML psi values per cell (H and E sides together):
+    4 on the x shells (2 npml / nx of the cells), 4 on the y shells."""
+    return 4.0 * (2 * w.npml / w.nx) + 4.0 * (2 * w.npml / w.ny)
+
+
 def algorithmic_bytes_per_cell(w, elem_bytes: int) -> float:
-    """Bytes the method itself must move per cell-update: read and write E and
-    H once (12 words), read and write the FP64 fluence (16 B), read and write
-    every CPML psi value on the shells (mean psi count per cell
-    4 (2 npml / nx) + 4 (2 npml / ny))."""
-    psi_bar = 4.0 * (2 * w.npml / w.nx) + 4.0 * (2 * w.npml / w.ny)
-    return 12 * elem_bytes + 16 + 2 * elem_bytes * psi_bar
+    """Bytes one whole step must move per cell-update at the least: read and
+    write E and H once (12 words), read and write the 8-byte fluence
+    accumulator (16 B), read and write every CPML psi value on the shells."""
+    return 12 * elem_bytes + 16 + 2 * elem_bytes * psi_per_cell(w)
+
+
+def pass_bytes_per_cell(w, variant: int, b: int) -> list[tuple[str, float]]:
+    """(kernel, algorithmic bytes per cell) of each kernel of a step: the
+    distinct values that kernel itself must read and write.
+      one pass:            E, H in and out, fluence in and out, all psi;
+      H pass (3, 5):       E^n, H^{n-1/2} in, H^{n+1/2} out, H-side psi;
+      E pass + fluence:    E^n, H^{n+1/2}, H^{n-1/2} in, E^{n+1} out,
+                           fluence in and out, E-side psi;
+      H pass + fluence (4): E^n, H^{n-1/2} in, H^{n+1/2} out, fluence in and
+                           out, H-side psi;  E pass (4): E^n, H^{n+1/2} in,
+                           E^{n+1} out, E-side psi."""
+    psi = psi_per_cell(w)
+    one = 12 * b + 16 + 2 * b * psi
+    h = 9 * b + b * psi
+    if variant <= 2:
+        name = {0: "yee_step_fused", 1: "yee_step_tma", 2: "yee_step_tma (2 rows/thread)"}[variant]
+        return [(name, one)]
+    if variant == 3:
+        return [("yee_h_pass", h), ("yee_e_pass (with fluence)", 12 * b + 16 + b * psi)]
+    if variant == 4:
+        return [("yee_hflu_tma", h + 16), ("yee_e_pass", 9 * b + b * psi)]
+    return [("yee_h_cell", h), ("yee_e_cell", 12 * b + 16 + b * psi)]
+
+
+def kernel_roofline(w, tile, pass_ms, steps, b, peak, cells):
+    """Per-kernel achieved bandwidth (algorithmic bytes / CUDA-event duration)
+    and the dominant (longest) kernel."""
+    table = pass_bytes_per_cell(w, tile[0], b)
+    rows = []
+    for (name, bpc), ms in zip(table, pass_ms):
+        t = ms / steps
+        ach = bpc * cells / (t * 1e-3) / 1e9
+        rows.append({"kernel": name, "ms_per_launch": round(t, 5), "algorithmic_bytes_per_cell": round(bpc, 3),
+                     "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4)})
+    dom = max(rows, key=lambda r: r["ms_per_launch"])
+    return rows, dom
 
 
 class ClockSampler:
@@ -180,20 +226,26 @@ def run_gpu(args):
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
     with ClockSampler(gpu_id) as clk:
         ms32 = timed(g32, args.steps, args.warmup)
+        # the same steps again with CUDA events around every kernel of a step
+        # (the dominant kernel's duration for the roofline)
+        pass32 = g32.step_timed(args.steps)
     clocks = clk.summary()
-    per_launch_ms = ms32 / args.steps
+    step_ms = ms32 / args.steps
     gcell32 = cells * args.steps * ws / (ms32 * 1e-3) / 1e9
     ab32 = algorithmic_bytes_per_cell(w, 4)
-    achieved = ab32 * cells / (per_launch_ms * 1e-3) / 1e9
+    step_achieved = ab32 * cells / (step_ms * 1e-3) / 1e9
+    passes32, dom32 = kernel_roofline(w, tile32, pass32, args.steps, 4, peak, cells)
 
     # ---- FP64 (secondary) --------------------------------------------------
     g64 = make("f64")
     tile64 = g64.autotune(steps=3)
     steps64 = max(10, args.steps // 4)
     ms64 = timed(g64, steps64, max(3, args.warmup // 4))
+    pass64 = g64.step_timed(steps64)
     gcell64 = cells * steps64 * ws / (ms64 * 1e-3) / 1e9
     ab64 = algorithmic_bytes_per_cell(w, 8)
     achieved64 = ab64 * cells / (ms64 / steps64 * 1e-3) / 1e9
+    passes64, dom64 = kernel_roofline(w, tile64, pass64, steps64, 8, peak, cells)
 
     # FP32 vs FP64 agreement on the same number of steps (both GPU paths are
     # parity-checked against the oracle in the test suite)
@@ -219,7 +271,7 @@ def run_gpu(args):
     del g32, g64
     out = {
         "metric": METRIC, "value": round(gcell32, 3), "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_launch_ms, 5),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": w.name, "cells": cells, "grid": [w.nx, w.ny, w.nz], "npml": w.npml,
@@ -228,19 +280,25 @@ def run_gpu(args):
                    "l2_flush": "inputs larger than L2 (fields + fluence = %.0f MB/step)"
                                % (ab32 * cells / 1e6),
                    "tile_f32": list(tile32), "tile_f64": list(tile64), "parallelism": f"replicas{ws}"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "yee_step_fused<float,32,ty>", "algorithmic_bytes_per_cell": ab32},
+        "roofline": {"bound": "hbm", "achieved": dom32["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": dom32["frac"], "traffic": TRAFFIC.get(dom32["kernel"]), "peak_kind": peak_kind,
+                     "kernel": dom32["kernel"], "algorithmic_bytes_per_cell": dom32["algorithmic_bytes_per_cell"],
+                     "ms_per_launch": dom32["ms_per_launch"], "cells_per_launch": cells,
+                     "kernels": passes32,
+                     "step": {"achieved": round(step_achieved, 1), "frac": round(step_achieved / peak, 4),
+                              "algorithmic_bytes_per_cell": ab32, "ms_per_step": round(step_ms, 5)}},
         "fp64": {"value": round(gcell64, 3), "unit": UNIT, "steps": steps64,
                  "ms_per_step": round(ms64 / steps64, 5),
-                 "roofline": {"bound": "hbm", "achieved": round(achieved64, 1), "peak": peak,
-                              "frac": round(achieved64 / peak, 4), "algorithmic_bytes_per_cell": ab64}},
+                 "roofline": {"bound": "alu", "kernels": passes64, "dominant": dom64["kernel"],
+                              "step_achieved_gbs": round(achieved64, 1),
+                              "step_frac_of_hbm": round(achieved64 / peak, 4),
+                              "algorithmic_bytes_per_cell": ab64}},
         "l2_error": {"f32_vs_f64_gpu_rel_l2_fields": f32_vs_f64, "after_steps": n_cmp,
                      "f64_vs_oracle_tol": 1e-11, "f32_vs_oracle_tol": 1e-4},
         "e2e": e2e,
         "batched": batched,
         "adjoint": adjoint,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * len(pass32),
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:

@@ -194,6 +194,16 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
  * restoring the state) and keeps the fastest.  Results agree to rounding
  * for every configuration. */
 fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
+
+/* Measurement (the paper has no counterpart): advance `nsteps` steps like
+ * fdtd_step and time every kernel launch of a step with CUDA events recorded
+ * on the grid's stream.  pass_ms[p] (host array of max_passes floats) gets
+ * the total milliseconds of kernel p of a step summed over the steps;
+ * *n_passes = kernels per step (1 for variants 0-2; 2 for variants 3-5:
+ * [0] H pass, [1] E pass with the fluence term, or for variant 4 [0] H pass
+ * with the fluence term, [1] E pass).  Synchronizes the stream.  EINVAL if
+ * max_passes is smaller than the kernels per step. */
+fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_passes, int* n_passes);
 fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz);
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state);
 

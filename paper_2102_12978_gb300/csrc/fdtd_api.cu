@@ -274,9 +274,10 @@ static cudaError_t launch_tma(const fdtd_grid* cg, int cur, long long n, int lz,
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s)
+cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
+                        cudaEvent_t mid)
 {
-    if (tc.variant >= 3) return launch_split(g, cur, n, tc, s);
+    if (tc.variant >= 3) return launch_split(g, cur, n, tc, s, mid);
     if (tc.variant == 1) {
         if (g->desc.precision == FDTD_F32) {
             switch (tc.ty) {
@@ -511,6 +512,38 @@ fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
         g->step += 1;
     }
     return FDTD_OK;
+}
+
+fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_passes, int* n_passes)
+{
+    if (!g || !pass_ms || !n_passes || nsteps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    const int np = passes_per_step(g->tile);
+    if (max_passes < np) return fail(FDTD_EINVAL, "max_passes=%d < %d kernels per step", max_passes, np);
+    std::vector<cudaEvent_t> ev(size_t(nsteps) * (np + 1), nullptr);
+    fdtd_status st = FDTD_OK;
+    for (auto& e : ev)
+        if (st == FDTD_OK) st = cuda_check(cudaEventCreate(&e), "event create");
+    for (int s = 0; s < nsteps && st == FDTD_OK; ++s) {
+        cudaEvent_t* e = &ev[size_t(s) * (np + 1)];
+        cudaEventRecord(e[0], g->stream);
+        st = cuda_check(launch_step(g, g->cur, g->step, g->tile, g->stream, np == 2 ? e[1] : nullptr), "step launch");
+        cudaEventRecord(e[np], g->stream);
+        if (st == FDTD_OK) { g->cur ^= 1; g->step += 1; }
+    }
+    if (st == FDTD_OK) st = cuda_check(cudaEventSynchronize(ev.back()), "event synchronize");
+    for (int p = 0; p < np; ++p) pass_ms[p] = 0.0f;
+    for (int s = 0; s < nsteps && st == FDTD_OK; ++s)
+        for (int p = 0; p < np; ++p) {
+            float ms = 0.0f;
+            st = cuda_check(cudaEventElapsedTime(&ms, ev[size_t(s) * (np + 1) + p], ev[size_t(s) * (np + 1) + p + 1]),
+                            "event elapsed time");
+            pass_ms[p] += ms;
+        }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    *n_passes = np;
+    if (st != FDTD_OK) return st;
+    return fdtd_sync(g);
 }
 
 fdtd_status fdtd_sync(fdtd_grid* g)

@@ -72,9 +72,15 @@ struct fdtd_grid {
 namespace fdtd {
 template <typename real>
 StepArgs<real> make_args(const fdtd_grid* g, int cur);
-cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
+// One step on stream s.  `mid`, if not null, is recorded between the two
+// kernels of a two-pass variant (ignored by the one-pass variants).
+cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
+                        cudaEvent_t mid = nullptr);
+// Kernel launches per step of a tile configuration (1 or 2).
+inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 ? 2 : 1; }
 // The two-pass steps on stream s: variant 3 yee_h_pass then yee_e_pass (with
 // the fluence term); variant 4 yee_hflu_tma (with the fluence term) then
 // yee_e_pass.
-cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
+cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
+                         cudaEvent_t mid);
 }  // namespace fdtd

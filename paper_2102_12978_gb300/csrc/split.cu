@@ -38,7 +38,7 @@ inline bool hflu_maps(fdtd_grid* g, int cur, TmaMaps** out)
 
 // Two passes (H, then E with the fluence term), 32 x TY threads, one column each.
 template <typename real, int TY>
-static cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, int lz, cudaStream_t s)
+static cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, int lz, cudaStream_t s, cudaEvent_t mid)
 {
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, (g->desc.nz + lz - 1) / lz);
@@ -57,13 +57,14 @@ static cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, int lz
     yee_h_pass<real, TY><<<grid, block, smem, s>>>(a, n, lz);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (mid) cudaEventRecord(mid, s);
     yee_e_pass<real, TY, true><<<grid, block, smem, s>>>(a, n, lz);
     return cudaGetLastError();
 }
 
 // TMA-staged H pass with the fluence term (S stages), then the E pass.
 template <typename real, int TY, int S>
-static cudaError_t launch_hflu(const fdtd_grid* cg, int cur, long long n, int lz, cudaStream_t s)
+static cudaError_t launch_hflu(const fdtd_grid* cg, int cur, long long n, int lz, cudaStream_t s, cudaEvent_t mid)
 {
     fdtd_grid* g = const_cast<fdtd_grid*>(cg);
     using T = HFluTile<real, TY>;
@@ -91,6 +92,7 @@ static cudaError_t launch_hflu(const fdtd_grid* cg, int cur, long long n, int lz
     yee_hflu_tma<real, TY, S><<<grid, block, smem, s>>>(a, *m, n, lz, err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (mid) cudaEventRecord(mid, s);
     yee_e_pass<real, TY, false><<<grid, block, esmem, s>>>(a, n, lz);
     return cudaGetLastError();
 }
@@ -98,7 +100,7 @@ static cudaError_t launch_hflu(const fdtd_grid* cg, int cur, long long n, int lz
 // Cell-parallel passes: yee_h_cell then yee_e_cell (with the fluence term),
 // 32 x TY threads, one cell each, one plane per grid z index.
 template <typename real, int TY>
-static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s)
+static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s, cudaEvent_t mid)
 {
     if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
     StepTime<real> t;
@@ -113,35 +115,37 @@ static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStr
     yee_h_cell<real, TY><<<grid, block, 0, s>>>(a, t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (mid) cudaEventRecord(mid, s);
     yee_e_cell<real, TY><<<grid, block, 0, s>>>(a, t);
     return cudaGetLastError();
 }
 
-cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s)
+cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
+                         cudaEvent_t mid)
 {
     const bool f32 = g->desc.precision == FDTD_F32;
     if (tc.variant == 5) {
         switch (tc.ty) {
-            case 4: return f32 ? launch_cell<float, 4>(g, cur, n, s) : launch_cell<double, 4>(g, cur, n, s);
-            case 16: return f32 ? launch_cell<float, 16>(g, cur, n, s) : launch_cell<double, 16>(g, cur, n, s);
-            default: return f32 ? launch_cell<float, 8>(g, cur, n, s) : launch_cell<double, 8>(g, cur, n, s);
+            case 4: return f32 ? launch_cell<float, 4>(g, cur, n, s, mid) : launch_cell<double, 4>(g, cur, n, s, mid);
+            case 16: return f32 ? launch_cell<float, 16>(g, cur, n, s, mid) : launch_cell<double, 16>(g, cur, n, s, mid);
+            default: return f32 ? launch_cell<float, 8>(g, cur, n, s, mid) : launch_cell<double, 8>(g, cur, n, s, mid);
         }
     }
     if (tc.variant == 4) {
         if (f32) {
             switch (tc.ty) {
-                case 4: return launch_hflu<float, 4, 6>(g, cur, n, tc.lz, s);
-                case 16: return launch_hflu<float, 16, 4>(g, cur, n, tc.lz, s);
-                default: return launch_hflu<float, 8, 4>(g, cur, n, tc.lz, s);
+                case 4: return launch_hflu<float, 4, 6>(g, cur, n, tc.lz, s, mid);
+                case 16: return launch_hflu<float, 16, 4>(g, cur, n, tc.lz, s, mid);
+                default: return launch_hflu<float, 8, 4>(g, cur, n, tc.lz, s, mid);
             }
         }
-        return tc.ty == 4 ? launch_hflu<double, 4, 5>(g, cur, n, tc.lz, s) : launch_hflu<double, 8, 4>(g, cur, n, tc.lz, s);
+        return tc.ty == 4 ? launch_hflu<double, 4, 5>(g, cur, n, tc.lz, s, mid) : launch_hflu<double, 8, 4>(g, cur, n, tc.lz, s, mid);
     }
     switch (tc.ty) {
-        case 4: return f32 ? launch_split<float, 4>(g, cur, n, tc.lz, s) : launch_split<double, 4>(g, cur, n, tc.lz, s);
+        case 4: return f32 ? launch_split<float, 4>(g, cur, n, tc.lz, s, mid) : launch_split<double, 4>(g, cur, n, tc.lz, s, mid);
         case 16:
-            return f32 ? launch_split<float, 16>(g, cur, n, tc.lz, s) : launch_split<double, 16>(g, cur, n, tc.lz, s);
-        default: return f32 ? launch_split<float, 8>(g, cur, n, tc.lz, s) : launch_split<double, 8>(g, cur, n, tc.lz, s);
+            return f32 ? launch_split<float, 16>(g, cur, n, tc.lz, s, mid) : launch_split<double, 16>(g, cur, n, tc.lz, s, mid);
+        default: return f32 ? launch_split<float, 8>(g, cur, n, tc.lz, s, mid) : launch_split<double, 8>(g, cur, n, tc.lz, s, mid);
     }
 }
 

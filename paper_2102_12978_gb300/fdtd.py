@@ -71,6 +71,7 @@ _SIGS = {
     "fdtd_antenna_points": (C.c_int64, [C.c_void_p, C.c_int]),
     "fdtd_sync": (C.c_int, [C.c_void_p]),
     "fdtd_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "fdtd_step_timed": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
@@ -258,6 +259,14 @@ class Grid:
 
     def step(self, n: int = 1):
         fdtd_step(self.handle, n)
+
+    def step_timed(self, n: int) -> list[float]:
+        """Step n times, timing each kernel of a step with CUDA events:
+        milliseconds per kernel of a step, summed over the n steps."""
+        ms = (C.c_float * 4)()
+        npass = C.c_int()
+        check(lib().fdtd_step_timed(C.c_void_p(self.handle), int(n), ms, 4, C.byref(npass)), "fdtd_step_timed")
+        return [float(ms[p]) for p in range(npass.value)]
 
     def set_tile(self, variant: int, ty: int, lz: int):
         check(lib().fdtd_set_tile(C.c_void_p(self.handle), int(variant), int(ty), int(lz)), "fdtd_set_tile")

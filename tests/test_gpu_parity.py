@@ -184,3 +184,19 @@ def test_fluence_reset_window():
     st.fluence[...] = 0
     oracle.run(og, os_, st, 10)
     assert rel_l2(f2, st.fluence) < 1e-11
+
+
+@pytest.mark.parametrize("tile,npass", [((1, 8, 8), 1), ((3, 4, 8), 2), ((4, 8, 8), 2), ((5, 4, 1), 2)])
+def test_step_timed_steps_like_step(tile, npass):
+    """fdtd_step_timed advances the grid exactly like fdtd_step and reports
+    one duration per kernel of a step."""
+    w = W.small(nx=48, ny=40, nz=16, npml=6, r_center=10.0, steps=12, ramp=1.0)
+    a = gpu_grid(w, "f32", tile=tile)
+    b = gpu_grid(w, "f32", tile=tile)
+    a.step(w.steps)
+    ms = b.step_timed(w.steps)
+    assert len(ms) == npass and all(t > 0 for t in ms)
+    assert a.n == b.n == w.steps
+    for c in range(6):
+        assert np.array_equal(host(a.field(c)), host(b.field(c)))
+    assert np.array_equal(host(a.fluence()), host(b.fluence()))
