@@ -77,7 +77,9 @@ def pass_bytes_per_cell(w, variant: int, b: int) -> list[tuple[str, float]]:
         return [("yee_h_pass", h), ("yee_e_pass (with fluence)", 12 * b + 16 + b * psi)]
     if variant == 4:
         return [("yee_hflu_tma", h + 16), ("yee_e_pass", 9 * b + b * psi)]
-    return [("yee_h_cell", h), ("yee_e_cell", 12 * b + 16 + b * psi)]
+    if variant == 5:
+        return [("yee_h_cell", h), ("yee_e_cell", 12 * b + 16 + b * psi)]
+    return [("yee_step_cell", one)]
 
 
 def kernel_roofline(w, tile, pass_ms, steps, b, peak, cells):

@@ -277,7 +277,7 @@ static cudaError_t launch_tma(const fdtd_grid* cg, int cur, long long n, int lz,
 cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
                         cudaEvent_t mid)
 {
-    if (tc.variant >= 3) return launch_split(g, cur, n, tc, s, mid);
+    if (tc.variant >= 3) return launch_split(g, cur, n, tc, s, mid);   // variants 3-6
     if (tc.variant == 1) {
         if (g->desc.precision == FDTD_F32) {
             switch (tc.ty) {
@@ -455,8 +455,20 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(A + g->L.scoef32, coef32.data(), coef32.size() * 4, cudaMemcpyHostToDevice,
                                         g->stream), "upload source");
+    // device copy of the mask: bit 6 marks the columns whose own or +-x / +-y
+    // neighbour column carries an H antenna point (the one-pass cell kernel
+    // evaluates H source terms of recomputed neighbours only there)
+    std::vector<uint8_t> dmask(mask);
+    for (int j = 0; j < d.ny; ++j)
+        for (int i = 0; i < d.nx; ++i) {
+            auto hbits = [&](int ii, int jj) {
+                return ii >= 0 && ii < d.nx && jj >= 0 && jj < d.ny && (mask[size_t(jj) * d.nx + ii] & 0x38);
+            };
+            if (hbits(i, j) || hbits(i - 1, j) || hbits(i + 1, j) || hbits(i, j - 1) || hbits(i, j + 1))
+                dmask[size_t(j) * d.nx + i] |= 0x40;
+        }
     if (st == FDTD_OK)
-        st = cuda_check(cudaMemcpyAsync(A + g->L.smask, mask.data(), mask.size(), cudaMemcpyHostToDevice,
+        st = cuda_check(cudaMemcpyAsync(A + g->L.smask, dmask.data(), dmask.size(), cudaMemcpyHostToDevice,
                                         g->stream), "upload source");
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(A + g->L.scoef_unw, coef_unw.data(), coef_unw.size() * 16,
@@ -683,9 +695,9 @@ void fdtd_destroy_grid(fdtd_grid* g) { delete g; }
 fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
-    if (variant < 0 || variant > 5) return fail(FDTD_EINVAL, "variant=%d not in {0, ..., 5}", variant);
+    if (variant < 0 || variant > 6) return fail(FDTD_EINVAL, "variant=%d not in {0, ..., 6}", variant);
     if (ty != 4 && ty != 8 && ty != 16) return fail(FDTD_EINVAL, "ty=%d not in {4, 8, 16}", ty);
-    if (variant == 5 && g->desc.nz > 65535) return fail(FDTD_EINVAL, "variant 5 takes nz <= 65535");
+    if (variant >= 5 && g->desc.nz > 65535) return fail(FDTD_EINVAL, "variant %d takes nz <= 65535", variant);
     if ((variant == 1 || variant == 2 || variant == 4) && ty == 16 && g->desc.precision == FDTD_F64)
         return fail(FDTD_EINVAL, "the TMA variants have no FP64 32x16 tile");
     if (lz < 1) return fail(FDTD_EINVAL, "lz=%d < 1", lz);
@@ -714,12 +726,12 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     fdtd_status st = fdtd_save_state(g, scratch_state);
     if (st != FDTD_OK) return st;
     struct Cand { int variant, ty; };
-    std::vector<Cand> cands = {{5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {4, 16}, {3, 4}, {3, 8}, {3, 16},
-                               {2, 8}, {2, 16}, {1, 4}, {1, 8}, {1, 16}, {0, 4}, {0, 8}, {0, 16}};
+    std::vector<Cand> cands = {{6, 4}, {6, 8}, {6, 16}, {5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {4, 16}, {3, 4},
+                               {3, 8}, {3, 16}, {2, 8}, {2, 16}, {1, 4}, {1, 8}, {1, 16}, {0, 4}, {0, 8}, {0, 16}};
     if (g->desc.precision == FDTD_F64)
-        cands = {{5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {3, 4}, {3, 8}, {2, 8}, {2, 4}, {1, 4}, {1, 8},
-                 {0, 4}, {0, 8}};
-    if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 3);
+        cands = {{6, 4}, {6, 8}, {6, 16}, {5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {3, 4}, {3, 8}, {2, 8}, {2, 4},
+                 {1, 4}, {1, 8}, {0, 4}, {0, 8}};
+    if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 6);
     const int nz = g->desc.nz;
     std::vector<int> lzs;
     for (int segs : {1, 2, 3, 4, 6, 8, 12, 16}) {
@@ -737,7 +749,7 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     TileConfig best_tc = g->tile;
     for (const Cand& cd : cands)
         for (int lz : lzs) {
-            if (cd.variant == 5 && lz != lzs[0]) continue;   // one cell per thread: no z segments
+            if (cd.variant >= 5 && lz != lzs[0]) continue;   // one cell per thread: no z segments
             TileConfig tc; tc.variant = cd.variant; tc.tx = 32; tc.ty = cd.ty; tc.lz = lz;
             cudaError_t e = launch_step(g, g->cur, g->step, tc, g->stream);   // warm-up
             if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_check(e, "autotune"); }

@@ -34,7 +34,8 @@ struct Layout {
 // variant 2: the same with two rows of the tile per thread;
 // variant 3: two plain-load passes, H then E with the fluence term;
 // variant 4: two passes, TMA-staged H with the fluence term, then plain-load E;
-// variant 5: two cell-parallel passes, H then E with the fluence term.
+// variant 5: two cell-parallel passes, H then E with the fluence term;
+// variant 6: one cell-parallel pass, neighbour H recomputed in registers.
 struct TileConfig {
     int variant = 1, tx = 32, ty = 8, lz = 32;
 };
@@ -77,10 +78,11 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur);
 cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
                         cudaEvent_t mid = nullptr);
 // Kernel launches per step of a tile configuration (1 or 2).
-inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 ? 2 : 1; }
-// The two-pass steps on stream s: variant 3 yee_h_pass then yee_e_pass (with
-// the fluence term); variant 4 yee_hflu_tma (with the fluence term) then
-// yee_e_pass.
+inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 && tc.variant <= 5 ? 2 : 1; }
+// The cell-parallel and two-pass steps on stream s: variant 3 yee_h_pass then
+// yee_e_pass (with the fluence term); variant 4 yee_hflu_tma (with the
+// fluence term) then yee_e_pass; variant 5 yee_h_cell then yee_e_cell;
+// variant 6 yee_step_cell.
 cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
                          cudaEvent_t mid);
 }  // namespace fdtd

@@ -6,6 +6,7 @@
 #include "grid_impl.h"
 #include "tma_host.h"
 #include "yee_cell.cuh"
+#include "yee_step_cell.cuh"
 #include "yee_hflu_tma.cuh"
 #include "yee_split.cuh"
 
@@ -97,18 +98,38 @@ static cudaError_t launch_hflu(const fdtd_grid* cg, int cur, long long n, int lz
     return cudaGetLastError();
 }
 
-// Cell-parallel passes: yee_h_cell then yee_e_cell (with the fluence term),
-// 32 x TY threads, one cell each, one plane per grid z index.
-template <typename real, int TY>
-static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s, cudaEvent_t mid)
+// f e^{-i Phi} of step n at the H and E times, in FP64 on the host.
+template <typename real>
+static StepTime<real> step_time(const fdtd_grid* g, long long n)
 {
-    if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
     StepTime<real> t;
     double c, sn, f;
     source_time(g->srct, (double(n) + 0.5) * g->dt, c, sn, f);
     t.th = Cpx<real>{real(f * c), real(-f * sn)};
     source_time(g->srct, (double(n) + 1.0) * g->dt, c, sn, f);
     t.te = Cpx<real>{real(f * c), real(-f * sn)};
+    return t;
+}
+
+// One cell-parallel pass: yee_step_cell, 32 x TY threads, one cell each.
+template <typename real, int TY>
+static cudaError_t launch_step_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s)
+{
+    if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
+    const StepTime<real> t = step_time<real>(g, n);
+    dim3 block(32, TY);
+    dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
+    yee_step_cell<real, TY><<<grid, block, 0, s>>>(make_args<real>(g, cur), t);
+    return cudaGetLastError();
+}
+
+// Cell-parallel passes: yee_h_cell then yee_e_cell (with the fluence term),
+// 32 x TY threads, one cell each, one plane per grid z index.
+template <typename real, int TY>
+static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s, cudaEvent_t mid)
+{
+    if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
+    const StepTime<real> t = step_time<real>(g, n);
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
     const StepArgs<real> a = make_args<real>(g, cur);
@@ -124,6 +145,14 @@ cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileCon
                          cudaEvent_t mid)
 {
     const bool f32 = g->desc.precision == FDTD_F32;
+    if (tc.variant == 6) {
+        switch (tc.ty) {
+            case 4: return f32 ? launch_step_cell<float, 4>(g, cur, n, s) : launch_step_cell<double, 4>(g, cur, n, s);
+            case 16:
+                return f32 ? launch_step_cell<float, 16>(g, cur, n, s) : launch_step_cell<double, 16>(g, cur, n, s);
+            default: return f32 ? launch_step_cell<float, 8>(g, cur, n, s) : launch_step_cell<double, 8>(g, cur, n, s);
+        }
+    }
     if (tc.variant == 5) {
         switch (tc.ty) {
             case 4: return f32 ? launch_cell<float, 4>(g, cur, n, s, mid) : launch_cell<double, 4>(g, cur, n, s, mid);

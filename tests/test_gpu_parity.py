@@ -62,8 +62,7 @@ def test_small_grids_match_oracle(precision, shape):
 
 
 TILES = [(1, 4, 1), (1, 8, 3), (1, 8, 64), (2, 4, 1), (2, 8, 3), (2, 8, 64), (3, 4, 1), (3, 8, 3), (3, 16, 16),
-         (3, 8, 64), (4, 4, 1), (4, 8, 3), (4, 16, 16), (4, 8, 64), (5, 4, 1), (5, 8, 1), (5, 16, 1), (0, 4, 1),
-         (0, 8, 3), (0, 16, 16), (0, 8, 64)]
+         (3, 8, 64), (4, 4, 1), (4, 8, 3), (4, 16, 16), (4, 8, 64), (5, 4, 1), (5, 8, 1), (5, 16, 1), (6, 4, 1), (6, 8, 1), (6, 16, 1), (0, 4, 1), (0, 8, 3), (0, 16, 16), (0, 8, 64)]
 
 
 def _skip_missing(tile, precision):
@@ -90,7 +89,8 @@ def test_tma_f32_tall_tile(variant):
 
 
 @pytest.mark.parametrize("tile", [(1, 8, 5), (1, 4, 12), (2, 8, 5), (2, 4, 3), (2, 16, 12), (3, 8, 5), (3, 4, 12),
-                                  (3, 16, 3), (4, 8, 5), (4, 4, 12), (4, 16, 3), (5, 4, 1), (5, 8, 1), (5, 16, 1)])
+                                  (3, 16, 3), (4, 8, 5), (4, 4, 12), (4, 16, 3), (5, 4, 1), (5, 8, 1), (5, 16, 1),
+                                  (6, 4, 1), (6, 8, 1), (6, 16, 1)])
 @pytest.mark.parametrize("precision", ["f64", "f32"])
 def test_interior_block_classes(tile, precision):
     """A grid wide enough that the kernels meet all three block classes:
@@ -113,7 +113,7 @@ def test_source_variants_match_oracle(kw):
     _assert(_compare(w, "f64"), "f64")
 
 
-@pytest.mark.parametrize("tile", [(1, 8, 5), (3, 8, 5), (4, 8, 5), (5, 8, 1)])
+@pytest.mark.parametrize("tile", [(1, 8, 5), (3, 8, 5), (4, 8, 5), (5, 8, 1), (6, 8, 1)])
 def test_without_fluence_accumulator(tile):
     """Grids created without a fluence accumulator step the fields alone."""
     w = W.small(nx=44, ny=40, nz=12, npml=6, r_center=9.0, steps=40, ramp=1.0)
@@ -129,7 +129,7 @@ def test_source_free_pec_random_state():
     _assert(_compare(w, "f64", npml=0, source=False, init=init), "f64")
 
 
-@pytest.mark.parametrize("tile", [None, (3, 8, 1), (4, 8, 1), (4, 4, 2), (5, 8, 1)])
+@pytest.mark.parametrize("tile", [None, (3, 8, 1), (4, 8, 1), (4, 4, 2), (5, 8, 1), (6, 8, 1)])
 def test_nz_one_and_two(tile):
     for nz in (1, 2):
         w = W.small(nx=40, ny=40, nz=nz, npml=6, r_center=9.0, steps=25, ramp=1.0)
@@ -186,7 +186,8 @@ def test_fluence_reset_window():
     assert rel_l2(f2, st.fluence) < 1e-11
 
 
-@pytest.mark.parametrize("tile,npass", [((1, 8, 8), 1), ((3, 4, 8), 2), ((4, 8, 8), 2), ((5, 4, 1), 2)])
+@pytest.mark.parametrize("tile,npass", [((1, 8, 8), 1), ((3, 4, 8), 2), ((4, 8, 8), 2), ((5, 4, 1), 2),
+                                        ((6, 4, 1), 1)])
 def test_step_timed_steps_like_step(tile, npass):
     """fdtd_step_timed advances the grid exactly like fdtd_step and reports
     one duration per kernel of a step."""
