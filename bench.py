@@ -314,9 +314,10 @@ def run_gpu(args):
 
 def run_batched(torch, fdtd, W, dev, steps):
     """The 16-configuration sweep (l in 0..3 x theta in 5, 10, 20, 30 deg,
-    N^2 x 64 grids with N = 96 .. 640): all grids advanced by one
-    graph-replayed persistent launch per step, against the same grids stepped
-    one launch per grid per step."""
+    N^2 x 64 grids with N = 96 .. 640), all grids advanced together from a
+    64-step CUDA graph: the cell-pass engine (one H and one E launch per step
+    over every grid) and the persistent TMA engine (one persistent launch per
+    step), against the same grids stepped one grid at a time."""
     ws_ = W.config4()
 
     def make(wl):
@@ -344,24 +345,29 @@ def run_batched(torch, fdtd, W, dev, steps):
     for g in seq:
         g.close()
     del seq
-    bat = [make(wl) for wl in ws_]
-    b = fdtd.Batch(bat)
-    b.step(64)                 # warm-up, builds the graph
-    b.sync()
-    e0.record(stream)
-    b.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    b.sync()
-    ms_bat = e0.elapsed_time(e1)
-    items = b.work_items
-    b.close()
-    for g in bat:
-        g.close()
-    return {"value": round(cells * steps / (ms_bat * 1e-3) / 1e9, 3), "unit": UNIT,
+    engines = {}
+    for name, engine in (("cell", fdtd.BATCH_CELL), ("persistent", fdtd.BATCH_PERSISTENT)):
+        bat = [make(wl) for wl in ws_]
+        b = fdtd.Batch(bat, engine=engine)
+        b.step(64)                 # warm-up, builds the graph
+        b.sync()
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        b.sync()
+        engines[name] = (e0.elapsed_time(e1), b.work_items)
+        b.close()
+        for g in bat:
+            g.close()
+    ms_bat, items = engines["cell"]
+    ms_per, items_per = engines["persistent"]
+    return {"value": round(cells * steps / (ms_bat * 1e-3) / 1e9, 3), "unit": UNIT, "engine": "cell",
             "sequential_value": round(cells * steps / (ms_seq * 1e-3) / 1e9, 3),
+            "persistent_value": round(cells * steps / (ms_per * 1e-3) / 1e9, 3),
             "speedup_vs_sequential": round(ms_seq / ms_bat, 3), "grids": len(ws_), "cells": cells,
-            "steps": steps, "work_items": items, "ms_per_step": round(ms_bat / steps, 4),
+            "steps": steps, "work_items": items, "persistent_work_items": items_per,
+            "ms_per_step": round(ms_bat / steps, 4), "persistent_ms_per_step": round(ms_per / steps, 4),
             "sequential_ms_per_step": round(ms_seq / steps, 4)}
 
 

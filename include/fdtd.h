@@ -215,18 +215,28 @@ void fdtd_destroy_grid(fdtd_grid* g);
 
 /* ---- Batched stepping of many independent grids --------------------------
  * Several grids (any sizes, sources, cone angles; one precision; all created
- * on the current device and at the same step parity) advance together: one
- * persistent kernel launch per step walks every grid's (tile, z segment)
- * blocks, and K = 64 consecutive steps are replayed from one CUDA graph.
- * The per-grid arithmetic is exactly fdtd_step's.  `dev_table` is a device
- * buffer of fdtd_batch_required_bytes bytes (256-byte aligned), owned by the
- * caller and alive until fdtd_batch_destroy; `stream` is a cudaStream_t.  A
- * grid in a batch must not be stepped on its own until the batch is
- * destroyed (ESTATE otherwise).  fdtd_batch_sync waits for the stream and
- * reports CUDA errors or an expired device wait (ETIMEOUT). */
+ * on the current device and at the same step parity) advance together, K =
+ * 64 consecutive steps replayed from one CUDA graph.  Two engines:
+ *   FDTD_BATCH_CELL (default): per step one launch of the H pass and one of
+ *     the E pass over the cell blocks of every grid (the arithmetic of
+ *     tile variant 5, bit for bit); needs nz <= 65535 on every grid.
+ *   FDTD_BATCH_PERSISTENT: one persistent kernel launch per step walks every
+ *     grid's (tile, z segment) blocks with the TMA-staged one-pass step (the
+ *     arithmetic of tile variant 1, bit for bit).
+ * `dev_table` is a device buffer of fdtd_batch_required_bytes bytes
+ * (256-byte aligned), owned by the caller and alive until
+ * fdtd_batch_destroy; `stream` is a cudaStream_t.  A grid in a batch must
+ * not be stepped on its own until the batch is destroyed (ESTATE otherwise).
+ * fdtd_batch_set_engine switches engines between steps (EINVAL for an
+ * unknown engine, or the cell engine with nz > 65535).  fdtd_batch_sync
+ * waits for the stream and reports CUDA errors or an expired device wait
+ * (ETIMEOUT).  fdtd_batch_work_items: blocks per step of the current engine. */
+enum { FDTD_BATCH_PERSISTENT = 0, FDTD_BATCH_CELL = 1 };
 size_t fdtd_batch_required_bytes(int n_grids, int precision);
 fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, size_t table_bytes, void* stream,
                               fdtd_batch** out);
+fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine);
+int fdtd_batch_get_engine(const fdtd_batch* b);
 fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps);
 fdtd_status fdtd_batch_sync(fdtd_batch* b);
 int fdtd_batch_work_items(const fdtd_batch* b);

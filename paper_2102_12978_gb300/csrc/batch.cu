@@ -2,15 +2,25 @@
 // angles, ring radii and transverse sizes) advanced together.
 //
 // Each grid runs the unchanged method of its own descriptor (Section 4,
-// Eq. 12-13).  The batch flattens every grid's (32 x TR tile, z segment)
-// blocks into one work list; a persistent kernel with one CTA per resident
-// slot (SM count x occupancy) walks the list with a grid stride, marching
-// each block with the TMA-staged fused step (tma_march).  The CTA's
-// mbarriers are initialised once and their phases carried from block to
-// block.  A CUDA graph holds K consecutive step launches plus a one-thread
-// kernel that advances the batch's device step counter, so one graph replay
-// advances every grid by K steps and the source phase of step n stays
-// correct on every replay.
+// Eq. 12-13).  A CUDA graph holds K = 64 consecutive steps of every grid;
+// one replay advances them all by K steps.  Two engines:
+//   * persistent (FDTD_BATCH_PERSISTENT): the batch flattens every grid's
+//     (32 x TR tile, z segment) blocks into one work list; one persistent
+//     kernel launch per step, one CTA per resident slot (SM count x
+//     occupancy), walks the list with a grid stride and marches each block
+//     with the TMA-staged one-pass step (tma_march).  The CTA's mbarriers are
+//     initialised once and their phases carried from block to block; a
+//     one-thread kernel at the end of the graph advances the device step
+//     counter from which the source phases are taken.
+//   * cell passes (FDTD_BATCH_CELL, the default): each grid steps with the
+//     cell-parallel H and E passes of the single-grid variant 5 (32 x 4 x 1
+//     blocks, one thread per cell).  The graph gives every grid its own
+//     branch (up to kCellBranches concurrent streams, shared round-robin), so
+//     the passes of small grids run side by side instead of each leaving the
+//     GPU idle in its tail.  The per-step source time factors of every grid
+//     are evaluated on the host in FP64, as for a single grid, and copied
+//     into a device table ahead of each replay; the kernels read their step's
+//     entry.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -20,6 +30,7 @@
 #include "../../include/fdtd.h"
 #include "grid_impl.h"
 #include "tma_host.h"
+#include "yee_cell.cuh"
 #include "yee_tma.cuh"
 
 namespace fdtd {
@@ -83,6 +94,10 @@ __global__ void batch_advance(BatchHeader* hdr, int k)
 
 constexpr int kBatchGraphSteps = 64;   // even, so a replay leaves the read copy unchanged
 
+// ---- cell-pass engine
+constexpr int kCellTY = 4;          // 32 x 4 x 1 cell blocks (tile variant 5)
+constexpr int kCellBranches = 16;   // concurrent graph branches (grids share them round-robin)
+
 }  // namespace fdtd
 
 using namespace fdtd;
@@ -90,17 +105,23 @@ using namespace fdtd;
 struct fdtd_batch {
     std::vector<fdtd_grid*> grids;
     int precision;
+    int engine;                      // FDTD_BATCH_PERSISTENT or FDTD_BATCH_CELL
     int ty, S;
     void* table;
     size_t table_bytes;
+    size_t times_off;                // byte offset of the time table in `table`
     cudaStream_t stream;
     cudaStream_t capture;
-    int nitems;
-    int nblocks;
+    int nitems;                      // persistent engine: work items
+    int nblocks;                     // persistent engine: resident CTAs
+    int cell_blocks;                 // cell engine: blocks per step and pass
+    cudaStream_t branch[kCellBranches];
+    int nbranch;
+    std::vector<unsigned char> host_times;
     int cur;
     int64_t step;
-    cudaGraphExec_t exec[2];
-    bool built[2];
+    cudaGraphExec_t exec[2][2];      // [engine][read copy at the replay's start]
+    bool built[2][2];
 };
 
 namespace {
@@ -108,6 +129,75 @@ namespace {
 size_t grid_entry_bytes(int precision)
 {
     return precision == FDTD_F64 ? sizeof(BatchGrid<double>) : sizeof(BatchGrid<float>);
+}
+
+size_t time_entry_bytes(int precision)
+{
+    return precision == FDTD_F64 ? sizeof(StepTime<double>) : sizeof(StepTime<float>);
+}
+
+size_t times_offset(int n, int precision)
+{
+    return (256 + grid_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
+}
+
+// ---- cell engine
+void cell_fill(fdtd_batch* b)
+{
+    b->cell_blocks = 0;
+    for (const fdtd_grid* g : b->grids)
+        b->cell_blocks += ((g->desc.nx + 31) / 32) * ((g->desc.ny + kCellTY - 1) / kCellTY) * g->desc.nz;
+}
+
+// Step `step` of the replay for grid q on stream s (time factor times[step * n + q]).
+template <typename real>
+cudaError_t cell_launch_grid(fdtd_batch* b, int q, int parity, int step, cudaStream_t s)
+{
+    const fdtd_grid* g = b->grids[q];
+    const StepTime<real>* times =
+        reinterpret_cast<const StepTime<real>*>(static_cast<char*>(b->table) + b->times_off);
+    const int index = step * int(b->grids.size()) + q;
+    const dim3 block(32, kCellTY);
+    const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + kCellTY - 1) / kCellTY, g->desc.nz);
+    const StepArgs<real> a = make_args<real>(g, parity);
+    yee_h_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    yee_e_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+    return cudaGetLastError();
+}
+
+cudaError_t cell_launch_grid_any(fdtd_batch* b, int q, int parity, int step, cudaStream_t s)
+{
+    return b->precision == FDTD_F64 ? cell_launch_grid<double>(b, q, parity, step, s)
+                                    : cell_launch_grid<float>(b, q, parity, step, s);
+}
+
+// One step of every grid on one stream (steps outside a graph replay).
+cudaError_t cell_launch_any(fdtd_batch* b, int parity, int step, cudaStream_t s)
+{
+    for (int q = 0; q < int(b->grids.size()); ++q) {
+        cudaError_t e = cell_launch_grid_any(b, q, parity, step, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Time factors of the next `count` steps of every grid into the device table.
+template <typename real>
+fdtd_status cell_upload_times(fdtd_batch* b, int count)
+{
+    const int n = int(b->grids.size());
+    b->host_times.resize(size_t(count) * n * sizeof(StepTime<real>));
+    StepTime<real>* h = reinterpret_cast<StepTime<real>*>(b->host_times.data());
+    for (int s = 0; s < count; ++s)
+        for (int q = 0; q < n; ++q) {
+            const fdtd_grid* g = b->grids[q];
+            h[size_t(s) * n + q] = step_time<real>(g->srct, g->dt, g->step + s);
+        }
+    return cuda_check(cudaMemcpyAsync(static_cast<char*>(b->table) + b->times_off, h, b->host_times.size(),
+                                      cudaMemcpyHostToDevice, b->stream),
+                      "batch time table");
 }
 
 // Block shape of the batch: 32 x TR tiles, R rows per thread, S stages
@@ -185,25 +275,51 @@ fdtd_status batch_fill(fdtd_batch* b)
     return FDTD_OK;
 }
 
+// The 64 steps of every grid, one branch per grid (streams shared
+// round-robin), forked from and joined back into the capture stream.
+cudaError_t cell_capture(fdtd_batch* b, int parity)
+{
+    cudaEvent_t fork, join[kCellBranches];
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    int made = 0;
+    for (; made < b->nbranch && e == cudaSuccess; ++made) e = cudaEventCreateWithFlags(&join[made], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(fork, b->capture);
+    for (int r = 0; r < b->nbranch && e == cudaSuccess; ++r) {
+        e = cudaStreamWaitEvent(b->branch[r], fork, 0);
+        for (int q = r; q < int(b->grids.size()) && e == cudaSuccess; q += b->nbranch)
+            for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; ++s)
+                e = cell_launch_grid_any(b, q, parity ^ (s & 1), s, b->branch[r]);
+        if (e == cudaSuccess) e = cudaEventRecord(join[r], b->branch[r]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, join[r], 0);
+    }
+    cudaEventDestroy(fork);
+    for (int r = 0; r < made; ++r) cudaEventDestroy(join[r]);
+    return e;
+}
+
 fdtd_status build_graph(fdtd_batch* b, int parity)
 {
     cudaGraph_t graph;
     fdtd_status st = cuda_check(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "capture");
     if (st != FDTD_OK) return st;
     cudaError_t e = cudaSuccess;
-    for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; ++s)
-        e = batch_launch_any(b, parity ^ (s & 1), s, b->capture);
-    if (e == cudaSuccess) {
+    if (b->engine == FDTD_BATCH_CELL)
+        e = cell_capture(b, parity);
+    else
+        for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; ++s)
+            e = batch_launch_any(b, parity ^ (s & 1), s, b->capture);
+    if (e == cudaSuccess && b->engine == FDTD_BATCH_PERSISTENT) {
         batch_advance<<<1, 1, 0, b->capture>>>(reinterpret_cast<BatchHeader*>(b->table), kBatchGraphSteps);
         e = cudaGetLastError();
     }
     cudaError_t e2 = cudaStreamEndCapture(b->capture, &graph);
     if (e != cudaSuccess) return cuda_check(e, "capture batch launches");
     if (e2 != cudaSuccess) return cuda_check(e2, "end capture");
-    e = cudaGraphInstantiate(&b->exec[parity], graph, 0);
+    e = cudaGraphInstantiate(&b->exec[b->engine][parity], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_check(e, "graph instantiate");
-    b->built[parity] = true;
+    b->built[b->engine][parity] = true;
     return FDTD_OK;
 }
 
@@ -214,7 +330,7 @@ extern "C" {
 size_t fdtd_batch_required_bytes(int n_grids, int precision)
 {
     if (n_grids < 1 || (precision != FDTD_F32 && precision != FDTD_F64)) return 0;
-    return 256 + grid_entry_bytes(precision) * size_t(n_grids);
+    return times_offset(n_grids, precision) + size_t(kBatchGraphSteps) * n_grids * time_entry_bytes(precision);
 }
 
 fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, size_t table_bytes, void* stream,
@@ -241,44 +357,96 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->stream = static_cast<cudaStream_t>(stream);
     b->cur = grids[0]->cur;
     b->step = 0;
-    b->built[0] = b->built[1] = false;
+    b->engine = FDTD_BATCH_CELL;
+    b->times_off = times_offset(n, prec);
+    for (int e = 0; e < 2; ++e) b->built[e][0] = b->built[e][1] = false;
+    for (int q = 0; q < n; ++q)
+        if (grids[q]->desc.nz > 65535) b->engine = FDTD_BATCH_PERSISTENT;   // cell grids take nz <= 65535
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
     st = cuda_check(cudaStreamSynchronize(b->stream), "batch create");
     if (st == FDTD_OK) st = prec == FDTD_F64 ? batch_fill<double, 4, 1, 5>(b) : batch_fill<float, 8, 1, 5>(b);
     if (st != FDTD_OK) { cudaStreamDestroy(b->capture); delete b; return st; }
+    cell_fill(b);
+    b->nbranch = n < kCellBranches ? n : kCellBranches;
+    for (int r = 0; r < b->nbranch && st == FDTD_OK; ++r) {
+        st = cuda_check(cudaStreamCreateWithFlags(&b->branch[r], cudaStreamNonBlocking), "branch stream");
+        if (st != FDTD_OK) {
+            for (int q = 0; q < r; ++q) cudaStreamDestroy(b->branch[q]);
+            cudaStreamDestroy(b->capture);
+            delete b;
+            return st;
+        }
+    }
     *out = b;
     return FDTD_OK;
 }
+
+fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine)
+{
+    if (!b) return fail(FDTD_EINVAL, "null batch");
+    if (engine != FDTD_BATCH_PERSISTENT && engine != FDTD_BATCH_CELL)
+        return fail(FDTD_EINVAL, "engine %d is neither FDTD_BATCH_PERSISTENT nor FDTD_BATCH_CELL", engine);
+    if (engine == FDTD_BATCH_CELL)
+        for (fdtd_grid* g : b->grids)
+            if (g->desc.nz > 65535) return fail(FDTD_EINVAL, "the cell engine takes nz <= 65535");
+    if (engine == FDTD_BATCH_PERSISTENT && b->engine != engine) {
+        // the persistent kernel takes the source phase of grid g at step
+        // step0_g + counter: bring the device counter to the batch's step
+        const long long counter = b->step;
+        fdtd_status st = cuda_check(cudaMemcpyAsync(static_cast<char*>(b->table) + offsetof(BatchHeader, counter),
+                                                    &counter, sizeof(counter), cudaMemcpyHostToDevice, b->stream),
+                                    "batch counter");
+        if (st != FDTD_OK) return st;
+        st = cuda_check(cudaStreamSynchronize(b->stream), "batch counter");
+        if (st != FDTD_OK) return st;
+    }
+    b->engine = engine;
+    return FDTD_OK;
+}
+
+int fdtd_batch_get_engine(const fdtd_batch* b) { return b ? b->engine : -1; }
 
 fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps)
 {
     if (!b || nsteps < 0) return fail(FDTD_EINVAL, "invalid argument");
     for (fdtd_grid* g : b->grids)
         if (g->cur != b->cur) return fail(FDTD_ESTATE, "a batched grid was stepped outside the batch");
-    const int full = nsteps / kBatchGraphSteps, rem = nsteps % kBatchGraphSteps;
-    for (int r = 0; r < full; ++r) {
-        if (!b->built[b->cur]) {
-            fdtd_status st = build_graph(b, b->cur);
+    const bool cell = b->engine == FDTD_BATCH_CELL;
+    int done = 0;
+    while (done < nsteps) {
+        const int count = nsteps - done < kBatchGraphSteps ? nsteps - done : kBatchGraphSteps;
+        if (cell) {
+            fdtd_status st = b->precision == FDTD_F64 ? cell_upload_times<double>(b, count)
+                                                      : cell_upload_times<float>(b, count);
             if (st != FDTD_OK) return st;
         }
-        fdtd_status st = cuda_check(cudaGraphLaunch(b->exec[b->cur], b->stream), "graph launch");
-        if (st != FDTD_OK) return st;
-    }
-    for (int s = 0; s < rem; ++s) {
-        cudaError_t e = batch_launch_any(b, b->cur ^ (s & 1), s, b->stream);
-        if (e != cudaSuccess) return cuda_check(e, "batch launch");
-    }
-    if (rem > 0) {
-        batch_advance<<<1, 1, 0, b->stream>>>(reinterpret_cast<BatchHeader*>(b->table), rem);
-        fdtd_status st = cuda_check(cudaGetLastError(), "batch advance");
-        if (st != FDTD_OK) return st;
-        b->cur ^= (rem & 1);
-    }
-    b->step += nsteps;
-    for (fdtd_grid* g : b->grids) {
-        g->step += nsteps;
-        g->cur = b->cur;
+        if (count == kBatchGraphSteps) {
+            if (!b->built[b->engine][b->cur]) {
+                fdtd_status st = build_graph(b, b->cur);
+                if (st != FDTD_OK) return st;
+            }
+            fdtd_status st = cuda_check(cudaGraphLaunch(b->exec[b->engine][b->cur], b->stream), "graph launch");
+            if (st != FDTD_OK) return st;
+        } else {
+            for (int s = 0; s < count; ++s) {
+                cudaError_t e = cell ? cell_launch_any(b, b->cur ^ (s & 1), s, b->stream)
+                                     : batch_launch_any(b, b->cur ^ (s & 1), s, b->stream);
+                if (e != cudaSuccess) return cuda_check(e, "batch launch");
+            }
+            if (!cell) {
+                batch_advance<<<1, 1, 0, b->stream>>>(reinterpret_cast<BatchHeader*>(b->table), count);
+                fdtd_status st = cuda_check(cudaGetLastError(), "batch advance");
+                if (st != FDTD_OK) return st;
+            }
+            b->cur ^= (count & 1);
+        }
+        done += count;
+        b->step += count;
+        for (fdtd_grid* g : b->grids) {
+            g->step += count;
+            g->cur = b->cur;
+        }
     }
     return FDTD_OK;
 }
@@ -300,13 +468,19 @@ fdtd_status fdtd_batch_sync(fdtd_batch* b)
     return FDTD_OK;
 }
 
-int fdtd_batch_work_items(const fdtd_batch* b) { return b ? b->nitems : -1; }
+int fdtd_batch_work_items(const fdtd_batch* b)
+{
+    if (!b) return -1;
+    return b->engine == FDTD_BATCH_CELL ? b->cell_blocks : b->nitems;
+}
 
 void fdtd_batch_destroy(fdtd_batch* b)
 {
     if (!b) return;
-    for (int p = 0; p < 2; ++p)
-        if (b->built[p]) cudaGraphExecDestroy(b->exec[p]);
+    for (int e = 0; e < 2; ++e)
+        for (int p = 0; p < 2; ++p)
+            if (b->built[e][p]) cudaGraphExecDestroy(b->exec[e][p]);
+    for (int r = 0; r < b->nbranch; ++r) cudaStreamDestroy(b->branch[r]);
     cudaStreamDestroy(b->capture);
     delete b;
 }

@@ -98,25 +98,12 @@ static cudaError_t launch_hflu(const fdtd_grid* cg, int cur, long long n, int lz
     return cudaGetLastError();
 }
 
-// f e^{-i Phi} of step n at the H and E times, in FP64 on the host.
-template <typename real>
-static StepTime<real> step_time(const fdtd_grid* g, long long n)
-{
-    StepTime<real> t;
-    double c, sn, f;
-    source_time(g->srct, (double(n) + 0.5) * g->dt, c, sn, f);
-    t.th = Cpx<real>{real(f * c), real(-f * sn)};
-    source_time(g->srct, (double(n) + 1.0) * g->dt, c, sn, f);
-    t.te = Cpx<real>{real(f * c), real(-f * sn)};
-    return t;
-}
-
 // One cell-parallel pass: yee_step_cell, 32 x TY threads, one cell each.
 template <typename real, int TY>
 static cudaError_t launch_step_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s)
 {
     if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
-    const StepTime<real> t = step_time<real>(g, n);
+    const StepTime<real> t = step_time<real>(g->srct, g->dt, n);
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
     yee_step_cell<real, TY><<<grid, block, 0, s>>>(make_args<real>(g, cur), t);
@@ -129,7 +116,7 @@ template <typename real, int TY>
 static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s, cudaEvent_t mid)
 {
     if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
-    const StepTime<real> t = step_time<real>(g, n);
+    const StepTime<real> t = step_time<real>(g->srct, g->dt, n);
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
     const StepArgs<real> a = make_args<real>(g, cur);

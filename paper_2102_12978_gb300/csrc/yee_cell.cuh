@@ -33,6 +33,36 @@ struct StepTime {
     Cpx<real> th, te;
 };
 
+// The time factors of step n, evaluated on the host in FP64 and rounded to
+// the field precision (every launch path of the cell kernels uses this).
+template <typename real>
+inline StepTime<real> step_time(const SrcTime& st, double dt, long long n)
+{
+    StepTime<real> t;
+    double c, sn, f;
+    source_time(st, (double(n) + 0.5) * dt, c, sn, f);
+    t.th = Cpx<real>{real(f * c), real(-f * sn)};
+    source_time(st, (double(n) + 1.0) * dt, c, sn, f);
+    t.te = Cpx<real>{real(f * c), real(-f * sn)};
+    return t;
+}
+
+// Block classes of the cell passes: a 32 x TY block needs the checks (GEN)
+// if its cells or their +x / +y neighbours (and, for the E pass, -x / -y
+// neighbours) reach a wall or a ragged edge, or its cells lie in the shell.
+template <typename real, int TY>
+__host__ __device__ __forceinline__ bool cell_gen_h(const StepArgs<real>& a, int i0, int j0)
+{
+    const int nx = a.nx, ny = a.ny, npml = a.npml;
+    return i0 + 32 >= nx || j0 + TY >= ny ||
+           (npml > 0 && (i0 < npml || i0 + 31 >= nx - npml || j0 < npml || j0 + TY - 1 >= ny - npml));
+}
+template <typename real, int TY>
+__host__ __device__ __forceinline__ bool cell_gen_e(const StepArgs<real>& a, int i0, int j0)
+{
+    return i0 == 0 || j0 == 0 || cell_gen_h<real, TY>(a, i0, j0);
+}
+
 template <typename real>
 __device__ __forceinline__ Cpx<real> plane_factor(const StepArgs<real>& a, int k, Cpx<real> t)
 {
@@ -218,11 +248,8 @@ __global__ void __launch_bounds__(32 * TY)
 yee_h_cell(const StepArgs<real> a, const StepTime<real> t)
 {
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
-    const int nx = a.nx, ny = a.ny, npml = a.npml;
-    const bool gen = i0 + 32 >= nx || j0 + TY >= ny ||
-                     (npml > 0 && (i0 < npml || i0 + 31 >= nx - npml || j0 < npml || j0 + TY - 1 >= ny - npml));
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (gen) h_cell<real, true>(a, t.th, i, j, k);
+    if (cell_gen_h<real, TY>(a, i0, j0)) h_cell<real, true>(a, t.th, i, j, k);
     else h_cell<real, false>(a, t.th, i, j, k);
 }
 
@@ -231,12 +258,34 @@ __global__ void __launch_bounds__(32 * TY)
 yee_e_cell(const StepArgs<real> a, const StepTime<real> t)
 {
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
-    const int nx = a.nx, ny = a.ny, npml = a.npml;
-    const bool gen = i0 == 0 || j0 == 0 || i0 + 32 >= nx || j0 + TY >= ny ||
-                     (npml > 0 && (i0 < npml || i0 + 31 >= nx - npml || j0 < npml || j0 + TY - 1 >= ny - npml));
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (gen) e_cell<real, true>(a, t.te, i, j, k);
+    if (cell_gen_e<real, TY>(a, i0, j0)) e_cell<real, true>(a, t.te, i, j, k);
     else e_cell<real, false>(a, t.te, i, j, k);
+}
+
+// The same passes with the step's time factors read from a device table
+// (times[index]): the batched sweep replays a CUDA graph whose steps take
+// their source phase from a table refreshed before each replay.
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_h_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
+{
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    const Cpx<real> th = times[index].th;
+    if (cell_gen_h<real, TY>(a, i0, j0)) h_cell<real, true>(a, th, i, j, k);
+    else h_cell<real, false>(a, th, i, j, k);
+}
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_e_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
+{
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    const Cpx<real> te = times[index].te;
+    if (cell_gen_e<real, TY>(a, i0, j0)) e_cell<real, true>(a, te, i, j, k);
+    else e_cell<real, false>(a, te, i, j, k);
 }
 
 }  // namespace fdtd

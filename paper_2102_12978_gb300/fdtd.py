@@ -78,6 +78,8 @@ _SIGS = {
     "fdtd_batch_required_bytes": (C.c_size_t, [C.c_int, C.c_int]),
     "fdtd_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
                                     C.POINTER(C.c_void_p)]),
+    "fdtd_batch_set_engine": (C.c_int, [C.c_void_p, C.c_int]),
+    "fdtd_batch_get_engine": (C.c_int, [C.c_void_p]),
     "fdtd_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_batch_sync": (C.c_int, [C.c_void_p]),
     "fdtd_batch_work_items": (C.c_int, [C.c_void_p]),
@@ -340,11 +342,14 @@ class Grid:
             pass
 
 
-class Batch:
-    """Several Grid objects advanced together by the persistent, graph-replayed
-    batched step (fdtd_batch_*)."""
+BATCH_PERSISTENT, BATCH_CELL = 0, 1
 
-    def __init__(self, grids):
+
+class Batch:
+    """Several Grid objects advanced together by the graph-replayed batched
+    step (fdtd_batch_*): engine BATCH_CELL (default) or BATCH_PERSISTENT."""
+
+    def __init__(self, grids, engine: int | None = None):
         import torch
         self.torch = torch
         self.grids = list(grids)
@@ -361,6 +366,15 @@ class Batch:
         check(lib().fdtd_batch_create(arr, n, C.c_void_p(ptr), nbytes, C.c_void_p(g0.stream.cuda_stream),
                                       C.byref(h)), "fdtd_batch_create")
         self.handle = h.value
+        if engine is not None:
+            self.set_engine(engine)
+
+    def set_engine(self, engine: int):
+        check(lib().fdtd_batch_set_engine(C.c_void_p(self.handle), int(engine)), "fdtd_batch_set_engine")
+
+    @property
+    def engine(self) -> int:
+        return int(lib().fdtd_batch_get_engine(C.c_void_p(self.handle)))
 
     def step(self, n: int = 1):
         check(lib().fdtd_batch_step(C.c_void_p(self.handle), int(n)), "fdtd_batch_step")

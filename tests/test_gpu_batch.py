@@ -1,6 +1,7 @@
-"""Batched stepping of several uneven grids in one persistent, graph-replayed
-launch per step: each grid must match its own sequential run bit for bit, and
-the FP64 oracle within the parity tolerance."""
+"""Batched stepping of several uneven grids, graph-replayed (cell-pass engine
+and persistent TMA engine): each grid must match its own sequential run of
+the same arithmetic bit for bit, and the FP64 oracle within the parity
+tolerance."""
 import numpy as np
 import pytest
 
@@ -22,14 +23,19 @@ def _cases():
     ]
 
 
+@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_batched_equals_sequential_bitwise(precision):
-    """130 steps = two replays of the 64-step graph plus a 2-step remainder."""
+def test_batched_equals_sequential_bitwise(precision, engine):
+    """130 steps = two replays of the 64-step graph plus a 2-step remainder;
+    each engine against the single-grid step of the same arithmetic (cell
+    engine: tile variant 5; persistent engine: the TMA one-pass variant 1)."""
     ws = _cases()
     ty = 8 if precision == "f32" else 4
-    seq = [gpu_grid(w, precision, tile=(1, ty, 32)) for w in ws]
+    tile = (5, 4, 1) if engine == fdtd.BATCH_CELL else (1, ty, 32)
+    seq = [gpu_grid(w, precision, tile=tile) for w in ws]
     bat = [gpu_grid(w, precision) for w in ws]
-    b = fdtd.Batch(bat)
+    b = fdtd.Batch(bat, engine=engine)
+    assert b.engine == engine
     assert b.work_items > 0
     nsteps = 130
     for g in seq:
@@ -44,10 +50,33 @@ def test_batched_equals_sequential_bitwise(precision):
     b.close()
 
 
-def test_batched_matches_oracle_f64():
+def test_batch_engine_switch_keeps_source_phase():
+    """Steps split between the engines (a switch between graph replays and
+    remainders) match the single-grid steps within the FP64 parity bound."""
+    ws = _cases()[:3]
+    seq = [gpu_grid(w, "f64", tile=(5, 4, 1)) for w in ws]
+    bat = [gpu_grid(w, "f64") for w in ws]
+    b = fdtd.Batch(bat)
+    b.step(67)
+    b.set_engine(fdtd.BATCH_PERSISTENT)
+    b.step(66)
+    b.set_engine(fdtd.BATCH_CELL)
+    b.step(5)
+    b.sync()
+    for g in seq:
+        g.step(138)
+    for gs, gb in zip(seq, bat):
+        for c in range(6):
+            assert rel_l2(host(gb.field(c)), host(gs.field(c))) <= 1e-12, c
+        assert rel_l2(host(gb.fluence()), host(gs.fluence())) <= 1e-12
+    b.close()
+
+
+@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT])
+def test_batched_matches_oracle_f64(engine):
     ws = _cases()
     grids = [gpu_grid(w, "f64") for w in ws]
-    b = fdtd.Batch(grids)
+    b = fdtd.Batch(grids, engine=engine)
     nsteps = 70
     b.step(nsteps)
     b.sync()
@@ -70,4 +99,21 @@ def test_batched_grid_cannot_step_alone():
     with pytest.raises(fdtd.FDTDError) as e:
         b.step(1)
     assert e.value.status == fdtd.FDTD_ESTATE
+    b.close()
+
+
+def test_batch_of_more_grids_than_one_launch_holds():
+    """More grids (19) than the cell engine's concurrent graph branches (16):
+    grids share branches round-robin."""
+    ws = [W.small(nx=40 + 4 * (q % 3), ny=36, nz=6, npml=6, r_center=8.0, m=q % 3, ramp=1.0) for q in range(19)]
+    seq = [gpu_grid(w, "f32", tile=(5, 4, 1)) for w in ws]
+    bat = [gpu_grid(w, "f32") for w in ws]
+    b = fdtd.Batch(bat)
+    b.step(9)
+    b.sync()
+    for g in seq:
+        g.step(9)
+    for gs, gb in zip(seq, bat):
+        for c in range(6):
+            assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
     b.close()
