@@ -8,19 +8,20 @@
 // has no gradient computation, this is the transpose of the scheme above.
 //
 // One reverse step of forward step n (adjoints of E^{n+1}, H^{n+1/2}, psi in;
-// of E^n, H^{n-1/2}, psi out), per z plane k, mirrors the forward's data flow:
-//   * E side, tile plus a one-cell halo: e' = adjoint of E^{n+1} with the PEC
-//     entries zeroed; per E cell the transposed-difference terms t (curl
-//     coefficient x e' plus the CPML term a x psi-bar, psi-bar carried in a
-//     ping-pong pair so halo readers see the old value);
-//   * H side, tile plus the low halo: h' = h + gathered differences of t over
-//     the forward neighbours (i+1, j+1, k+1), then the per-H-cell terms s;
-//   * E side, own cells: e_new = e' + gathered differences of s over the
-//     backward neighbours (i-1, j-1, k-1).
-// The source gradient is g_c(col) = sum over steps and planes of
-// lambda f e^{i (beta z_k - Phi_n)}, with lambda = e' (E points) or h'
-// (H points); dL/dw follows per column as Re{e^{i phi} A g} and
-// -w Im{e^{i phi} A g} summed over components.
+// of E^n, H^{n-1/2}, psi out) mirrors the forward's data flow:
+//   * e' = adjoint of E^{n+1} with the PEC entries zeroed; per E cell the
+//     transposed-difference terms t (curl coefficient x e' plus the CPML term
+//     a x psi-bar, psi-bar carried in a ping-pong pair so that neighbours
+//     read the old value);
+//   * h' = h + gathered differences of t over the forward neighbours
+//     (i+1, j+1, k+1), then the per-H-cell terms s;
+//   * e_new = e' + gathered differences of s over the backward neighbours
+//     (i-1, j-1, k-1).
+// It runs as two cell-parallel passes (h', then e_new) and a small kernel
+// over the antenna columns for the source gradient
+// g_c(col) = sum over steps and planes of lambda f e^{i (beta z_k - Phi_n)},
+// with lambda = e' (E points) or h' (H points); dL/dw follows per column as
+// Re{e^{i phi} A g} and -w Im{e^{i phi} A g} summed over components.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -53,242 +54,239 @@ struct AdjArgs {
     double2* grad;              // [6][ny][nx] sum of lambda f e^{i (beta z - Phi)}
 };
 
-template <typename real, int TY>
-struct AdjTile {
-    static constexpr int TX = 32, PX = TX + 2, PY = TY + 2, P = PX * PY, NT = TX * TY;
-    // ring of E-side terms (3 planes x 9 values) and of H-side terms (2 x 6)
-    static constexpr size_t smem_bytes(int lz) { return (27 + 12) * size_t(P) * sizeof(real) + 2 * size_t(lz + 3) * 2 * sizeof(real) + 64; }
-};
+// ---- cell-parallel reverse step: two passes and a source-gradient kernel.
+//
+// Pass A (adj_h_cell): h' = lambda_H + gathered differences of the E-side
+// terms t over the forward neighbours (i+1, j+1, k+1); the own cell's t also
+// carries the E-side psi adjoint (written to the other copy).
+// Pass B (adj_e_cell): e_new = e' + gathered differences of the H-side terms
+// s over the backward neighbours (i-1, j-1, k-1), s from h' of pass A; the
+// own cell's s carries the H-side psi adjoint.
+// Every t and s a cell needs is recomputed from the read copies (neighbours
+// never write what a cell reads), so both passes are one thread per cell with
+// no shared memory or barrier, like the forward cell passes.
 
-// E-side terms of one cell at plane pw: t[0..5] = t_Ex_y, t_Ex_z, t_Ey_x,
-// t_Ey_z, t_Ez_x, t_Ez_y; e[0..2] = e'.  Writes the carried psi adjoint of
-// own cells (store).
-template <typename real>
-__device__ __forceinline__ void adj_eterms(const AdjArgs<real>& A, int i, int j, int pw, bool store, real t[6],
-                                           real e[3])
+// E-side terms t[0..5] of (i, j, pw) and e' (PEC-zeroed adjoint of E^{n+1});
+// zero outside the grid.  GEN: the cell may be outside the grid or in the
+// shell.
+template <typename real, bool GEN>
+__device__ __forceinline__ void adj_t(const AdjArgs<real>& A, int i, int j, int pw, bool store, real t[6], real e[3])
 {
     const StepArgs<real>& a = A.f;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
-    if (i < 0 || j < 0 || i >= nx || j >= ny) {
+    if (GEN && (i < 0 || j < 0 || i >= nx || j >= ny)) {
         for (int c = 0; c < 6; ++c) t[c] = real(0);
         e[0] = e[1] = e[2] = real(0);
         return;
     }
     const int g = pw * pitch * ny + j * pitch + i;
-    real ex = A.ein[0][g], ey = A.ein[1][g], ez = A.ein[2][g];
-    if (j == 0) { ex = real(0); ez = real(0); }   // PEC: E^{n+1} forced to zero there
-    if (i == 0) { ey = real(0); ez = real(0); }
+    real ex = __ldg(A.ein[0] + g), ey = __ldg(A.ein[1] + g), ez = __ldg(A.ein[2] + g);
+    if (GEN) {
+        if (j == 0) { ex = real(0); ez = real(0); }   // PEC: E^{n+1} forced to zero there
+        if (i == 0) { ey = real(0); ez = real(0); }
+    }
     e[0] = ex; e[1] = ey; e[2] = ez;
-    const real cex = a.cex[i], cey = a.cey[j];
+    const real cex = __ldg(a.cex + i), cey = __ldg(a.cey + j);
     t[0] = cey * ex;        // on dHz/dy in Ex
     t[1] = -a.cz * ex;      // on dHy/dz in Ex
     t[2] = -cex * ey;       // on dHz/dx in Ey
     t[3] = a.cz * ey;       // on dHx/dz in Ey
     t[4] = cex * ez;        // on dHy/dx in Ez
     t[5] = -cey * ez;       // on dHx/dy in Ez
-    const int npml = a.npml, w2 = 2 * npml;
-    if (npml > 0 && (i < npml || i >= nx - npml)) {
-        const int ii = i < npml ? i : i - nx + w2;
-        const int q = (pw * ny + j) * w2 + ii;
-        const real b = a.bex[ii], aa = a.aex[ii];
-        const real qyx = A.qx_in[0][q] - ey;      // Ey -= psi_Eyx
-        const real qzx = A.qx_in[1][q] + ez;      // Ez += psi_Ezx
-        t[2] += aa * qyx;
-        t[4] += aa * qzx;
-        if (store) { A.qx_out[0][q] = b * qyx; A.qx_out[1][q] = b * qzx; }
-    }
-    if (npml > 0 && (j < npml || j >= ny - npml)) {
-        const int jj = j < npml ? j : j - ny + w2;
-        const int q = (pw * w2 + jj) * pitch + i;
-        const real b = a.bey[jj], aa = a.aey[jj];
-        const real qxy = A.qy_in[0][q] + ex;      // Ex += psi_Exy
-        const real qzy = A.qy_in[1][q] - ez;      // Ez -= psi_Ezy
-        t[0] += aa * qxy;
-        t[5] += aa * qzy;
-        if (store) { A.qy_out[0][q] = b * qxy; A.qy_out[1][q] = b * qzy; }
+    if (GEN && a.npml > 0) {
+        const int npml = a.npml, w2 = 2 * npml;
+        if (i < npml || i >= nx - npml) {
+            const int ii = i < npml ? i : i - nx + w2;
+            const int q = (pw * ny + j) * w2 + ii;
+            const real b = a.bex[ii], aa = a.aex[ii];
+            const real qyx = A.qx_in[0][q] - ey;      // Ey -= psi_Eyx
+            const real qzx = A.qx_in[1][q] + ez;      // Ez += psi_Ezx
+            t[2] += aa * qyx;
+            t[4] += aa * qzx;
+            if (store) { A.qx_out[0][q] = b * qyx; A.qx_out[1][q] = b * qzx; }
+        }
+        if (j < npml || j >= ny - npml) {
+            const int jj = j < npml ? j : j - ny + w2;
+            const int q = (pw * w2 + jj) * pitch + i;
+            const real b = a.bey[jj], aa = a.aey[jj];
+            const real qxy = A.qy_in[0][q] + ex;      // Ex += psi_Exy
+            const real qzy = A.qy_in[1][q] - ez;      // Ez -= psi_Ezy
+            t[0] += aa * qxy;
+            t[5] += aa * qzy;
+            if (store) { A.qy_out[0][q] = b * qxy; A.qy_out[1][q] = b * qzy; }
+        }
     }
 }
 
-// H-side: h' from h and the E-side terms (t0: plane k, t1: plane k+1, ring
-// index r of (i, j)); then s[0..5] = s_Hx_y, s_Hx_z, s_Hy_x, s_Hy_z, s_Hz_x, s_Hz_y.
-template <typename real, int PX, int P>
-__device__ __forceinline__ void adj_hterms(const AdjArgs<real>& A, int i, int j, int pw, bool store,
-                                           const real* t0, const real* t1, int r, real hp[3], real s[6])
+// H-side terms s[0..5] of (i, j, pw) from h' (pass A's output, A.hout);
+// zero outside the grid.
+template <typename real, bool GEN>
+__device__ __forceinline__ void adj_s(const AdjArgs<real>& A, int i, int j, int pw, bool store, real s[6])
 {
     const StepArgs<real>& a = A.f;
     const int nx = a.nx, ny = a.ny, pitch = a.pitch;
+    if (GEN && (i < 0 || j < 0 || i >= nx || j >= ny)) {
+        for (int c = 0; c < 6; ++c) s[c] = real(0);
+        return;
+    }
     const int g = pw * pitch * ny + j * pitch + i;
-    real hx = A.hin[0][g], hy = A.hin[1][g], hz = A.hin[2][g];
-    // t layout in the ring: value c of cell r at t[c * P + r]
-    hx += (t0[3 * P + r] - t1[3 * P + r]) + (t0[5 * P + r] - t0[5 * P + r + PX]);
-    hy += (t0[1 * P + r] - t1[1 * P + r]) + (t0[4 * P + r] - t0[4 * P + r + 1]);
-    hz += (t0[0 * P + r] - t0[0 * P + r + PX]) + (t0[2 * P + r] - t0[2 * P + r + 1]);
-    hp[0] = hx; hp[1] = hy; hp[2] = hz;
-    const real chx = a.chx[i], chy = a.chy[j];
+    const real hx = __ldg(A.hout[0] + g), hy = __ldg(A.hout[1] + g), hz = __ldg(A.hout[2] + g);
+    const real chx = __ldg(a.chx + i), chy = __ldg(a.chy + j);
     s[0] = -chy * hx;      // on dEz/dy in Hx
     s[1] = a.cz * hx;      // on dEy/dz in Hx
     s[2] = chx * hy;       // on dEz/dx in Hy
     s[3] = -a.cz * hy;     // on dEx/dz in Hy
     s[4] = -chx * hz;      // on dEy/dx in Hz
     s[5] = chy * hz;       // on dEx/dy in Hz
-    const int npml = a.npml, w2 = 2 * npml;
-    if (npml > 0 && (i < npml || i >= nx - npml)) {
-        const int ii = i < npml ? i : i - nx + w2;
-        const int q = (pw * ny + j) * w2 + ii;
-        const real b = a.bhx[ii], aa = a.ahx[ii];
-        const real pyx = A.px_in[0][q] + hy;      // Hy += psi_Hyx
-        const real pzx = A.px_in[1][q] - hz;      // Hz -= psi_Hzx
-        s[2] += aa * pyx;
-        s[4] += aa * pzx;
-        if (store) { A.px_out[0][q] = b * pyx; A.px_out[1][q] = b * pzx; }
+    if (GEN && a.npml > 0) {
+        const int npml = a.npml, w2 = 2 * npml;
+        if (i < npml || i >= nx - npml) {
+            const int ii = i < npml ? i : i - nx + w2;
+            const int q = (pw * ny + j) * w2 + ii;
+            const real b = a.bhx[ii], aa = a.ahx[ii];
+            const real pyx = A.px_in[0][q] + hy;      // Hy += psi_Hyx
+            const real pzx = A.px_in[1][q] - hz;      // Hz -= psi_Hzx
+            s[2] += aa * pyx;
+            s[4] += aa * pzx;
+            if (store) { A.px_out[0][q] = b * pyx; A.px_out[1][q] = b * pzx; }
+        }
+        if (j < npml || j >= ny - npml) {
+            const int jj = j < npml ? j : j - ny + w2;
+            const int q = (pw * w2 + jj) * pitch + i;
+            const real b = a.bhy[jj], aa = a.ahy[jj];
+            const real pxy = A.py_in[0][q] - hx;      // Hx -= psi_Hxy
+            const real pzy = A.py_in[1][q] + hz;      // Hz += psi_Hzy
+            s[0] += aa * pxy;
+            s[5] += aa * pzy;
+            if (store) { A.py_out[0][q] = b * pxy; A.py_out[1][q] = b * pzy; }
+        }
     }
-    if (npml > 0 && (j < npml || j >= ny - npml)) {
-        const int jj = j < npml ? j : j - ny + w2;
-        const int q = (pw * w2 + jj) * pitch + i;
-        const real b = a.bhy[jj], aa = a.ahy[jj];
-        const real pxy = A.py_in[0][q] - hx;      // Hx -= psi_Hxy
-        const real pzy = A.py_in[1][q] + hz;      // Hz += psi_Hzy
-        s[0] += aa * pxy;
-        s[5] += aa * pzy;
-        if (store) { A.py_out[0][q] = b * pxy; A.py_out[1][q] = b * pzy; }
+}
+
+template <typename real, bool GEN>
+__device__ __forceinline__ void adj_h_cell(const AdjArgs<real>& A, int i, int j, int k)
+{
+    const StepArgs<real>& a = A.f;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    if (GEN && (i >= nx || j >= ny)) return;
+    const int kp = k + 1 == nz ? 0 : k + 1;
+    real t[6], e[3], tx[6], ty[6], tz[6];
+    adj_t<real, GEN>(A, i, j, k, true, t, e);
+    adj_t<real, GEN>(A, i + 1, j, k, false, tx, e);
+    adj_t<real, GEN>(A, i, j + 1, k, false, ty, e);
+    adj_t<real, GEN>(A, i, j, kp, false, tz, e);
+    const int g = k * a.pitch * ny + j * a.pitch + i;
+    real hx = __ldg(A.hin[0] + g), hy = __ldg(A.hin[1] + g), hz = __ldg(A.hin[2] + g);
+    hx += (t[3] - tz[3]) + (t[5] - ty[5]);
+    hy += (t[1] - tz[1]) + (t[4] - tx[4]);
+    hz += (t[0] - ty[0]) + (t[2] - tx[2]);
+    A.hout[0][g] = hx; A.hout[1][g] = hy; A.hout[2][g] = hz;
+}
+
+template <typename real, bool GEN>
+__device__ __forceinline__ void adj_e_cell(const AdjArgs<real>& A, int i, int j, int k)
+{
+    const StepArgs<real>& a = A.f;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    if (GEN && (i >= nx || j >= ny)) return;
+    const int km = k == 0 ? nz - 1 : k - 1;
+    real s[6], sx[6], sy[6], sz[6];
+    adj_s<real, GEN>(A, i, j, k, true, s);
+    adj_s<real, GEN>(A, i - 1, j, k, false, sx);
+    adj_s<real, GEN>(A, i, j - 1, k, false, sy);
+    adj_s<real, GEN>(A, i, j, km, false, sz);
+    const int g = k * a.pitch * ny + j * a.pitch + i;
+    real ex = __ldg(A.ein[0] + g), ey = __ldg(A.ein[1] + g), ez = __ldg(A.ein[2] + g);
+    if (GEN) {
+        if (j == 0) { ex = real(0); ez = real(0); }
+        if (i == 0) { ey = real(0); ez = real(0); }
     }
+    A.eout[0][g] = ex + (sz[3] - s[3]) + (sy[5] - s[5]);
+    A.eout[1][g] = ey + (sz[1] - s[1]) + (sx[4] - s[4]);
+    A.eout[2][g] = ez + (sy[0] - s[0]) + (sx[2] - s[2]);
+}
+
+// Grid: (ceil(nx/32), ceil(ny/TY), nz) CTAs of 32 x TY threads, one cell each.
+// GEN blocks: cells or the neighbours they read reach a wall, a ragged edge
+// or the shell.
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_adj_h_cell(const AdjArgs<real> A)
+{
+    const StepArgs<real>& a = A.f;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int nx = a.nx, ny = a.ny, npml = a.npml;
+    const bool gen = i0 == 0 || j0 == 0 || i0 + 32 >= nx || j0 + TY >= ny ||
+                     (npml > 0 && (i0 < npml || i0 + 32 >= nx - npml || j0 < npml || j0 + TY >= ny - npml));
+    if (gen) adj_h_cell<real, true>(A, i0 + threadIdx.x, j0 + threadIdx.y, k);
+    else adj_h_cell<real, false>(A, i0 + threadIdx.x, j0 + threadIdx.y, k);
 }
 
 template <typename real, int TY>
 __global__ void __launch_bounds__(32 * TY)
-yee_adjoint_step(const AdjArgs<real> A, long long n, int lz)
+yee_adj_e_cell(const AdjArgs<real> A)
 {
-    using T = AdjTile<real, TY>;
-    constexpr int TX = T::TX, PX = T::PX, P = T::P, NT = T::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    real* tr = reinterpret_cast<real*>(smem_raw);   // [3][9][P]: t (6) and e' (3)
-    real* sr = tr + 27 * P;                          // [2][6][P]
-    Cpx<real>* uE = reinterpret_cast<Cpx<real>*>(sr + 12 * P);
-    Cpx<real>* uH = uE + (lz + 3);
-    __shared__ double tf[6];
-
     const StepArgs<real>& a = A.f;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-    const int kb = blockIdx.z * lz;
-    const int ke = min(kb + lz, a.nz);
-    const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
-    const int i = i0 + tx, j = j0 + ty;
-    const bool own = i < nx && j < ny;
-    const int so = (ty + 1) * PX + (tx + 1);
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int nx = a.nx, ny = a.ny, npml = a.npml;
+    const bool gen = i0 == 0 || j0 == 0 || i0 + 32 >= nx || j0 + TY >= ny ||
+                     (npml > 0 && (i0 - 1 < npml || i0 + 31 >= nx - npml || j0 - 1 < npml || j0 + TY - 1 >= ny - npml));
+    if (gen) adj_e_cell<real, true>(A, i0 + threadIdx.x, j0 + threadIdx.y, k);
+    else adj_e_cell<real, false>(A, i0 + threadIdx.x, j0 + threadIdx.y, k);
+}
 
-    if (tid == 0) {
-        double c, s, f;
-        source_time(a.st, (double(n) + 0.5) * a.dt, c, s, f);
-        tf[3] = c; tf[4] = s; tf[5] = f;
-        source_time(a.st, (double(n) + 1.0) * a.dt, c, s, f);
-        tf[0] = c; tf[1] = s; tf[2] = f;
-    }
-    for (int q = tid; q < 39 * P; q += NT) tr[q] = real(0);
-    __syncthreads();
-    const int Q = ke - kb + 3;
-    if (a.smask) {
-        for (int q = tid; q < Q; q += NT) {
-            const int p = kb - 1 + q;
-            const int pw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
-            const double2 z = a.zph[pw];
-            uE[q].x = real((z.x * tf[0] + z.y * tf[1]) * tf[2]);
-            uE[q].y = real((z.y * tf[0] - z.x * tf[1]) * tf[2]);
-            uH[q].x = real((z.x * tf[3] + z.y * tf[4]) * tf[5]);
-            uH[q].y = real((z.y * tf[3] - z.x * tf[4]) * tf[5]);
-        }
-    }
-    const uint8_t mk = (own && a.smask) ? a.smask[j * nx + i] : uint8_t(0);
-    Cpx<real> gacc[6];
-    for (int c = 0; c < 6; ++c) { gacc[c].x = real(0); gacc[c].y = real(0); }
-
-    // E-side terms of plane p into ring slot (p + 3) % 3 (three slots: plane
-    // k+1 is filled while the previous iteration may still read plane k-1);
-    // the region's cells are shared out flatly over the CTA
-    auto tslot = [&](int p) { return tr + ((p + 3) % 3) * 9 * P; };
-    auto fill_t = [&](int p) {
-        const int pw = ((p % nz) + nz) % nz;
-        real* dst = tslot(p);
-        const bool own_plane = p >= kb && p < ke;
-        for (int r = tid; r < P; r += NT) {
-            const int ri = r % PX, rj = r / PX;
-            const int ci = i0 - 1 + ri, cj = j0 - 1 + rj;
-            const bool owner = own_plane && ri >= 1 && ri <= TX && rj >= 1 && rj <= TY;
-            real t[6], e[3];
-            adj_eterms<real>(A, ci, cj, pw, owner, t, e);
-            for (int c = 0; c < 6; ++c) dst[c * P + r] = t[c];
-            for (int c = 0; c < 3; ++c) dst[(6 + c) * P + r] = e[c];
-        }
-    };
-
-    // H cells of this thread: own, plus one of the low-halo cells
-    int hi = -1, hj = -1, hs = 0;
-    if (tid < TX) { hi = i0 + tid; hj = j0 - 1; hs = tid + 1; }
-    else if (tid < TX + TY + 1) { hi = i0 - 1; hj = j0 - 1 + (tid - TX); hs = (tid - TX) * PX; }
-    const bool halo_in = hi >= 0 && hj >= 0 && hi < nx && hj < ny;
-
-    fill_t(kb - 1);
-    #pragma unroll 1
-    for (int k = kb - 1; k < ke; ++k) {
-        const int q = k - kb + 1;
-        fill_t(k + 1);
-        __syncthreads();   // t of planes k, k+1 ready; readers of plane k-2's s slot done
-        const int kw = ((k % nz) + nz) % nz;
-        const bool write_k = k >= kb;
-        const real* t0 = tslot(k);
-        const real* t1 = tslot(k + 1);
-        real* sk = sr + (k & 1) * 6 * P;
-        if (own) {
-            real hp[3], s[6];
-            adj_hterms<real, PX, P>(A, i, j, kw, write_k, t0, t1, so, hp, s);
-            for (int c = 0; c < 6; ++c) sk[c * P + so] = s[c];
-            if (write_k) {
-                const int g = kw * pitch * ny + j * pitch + i;
-                A.hout[0][g] = hp[0]; A.hout[1][g] = hp[1]; A.hout[2][g] = hp[2];
-                if (mk & 0x38) {
-                    const Cpx<real> u = uH[q];
-                    for (int c = 3; c < 6; ++c)
-                        if (mk & (1 << c)) { gacc[c].x += hp[c - 3] * u.x; gacc[c].y += hp[c - 3] * u.y; }
+// Source gradient of one reverse step: for each antenna column (one warp per
+// column; lanes share out the planes) and component c with an antenna point,
+// g_c(col) += sum_k lambda_c(k) Re/Im{u_c(k)}, lambda = h' (H points, pass
+// A's output) or e' (E points: the PEC-zeroed adjoint of E^{n+1}), u_c(k) =
+// f e^{i (beta z_k - Phi)} at the component's time, in FP64.
+template <typename real>
+__global__ void adj_source_grad(const AdjArgs<real> A, const int* __restrict__ cols, int ncols, double2 te,
+                                double2 th)
+{
+    const StepArgs<real>& a = A.f;
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, plane = a.pitch * ny;
+    for (int w = warp; w < ncols; w += nwarps) {
+        const int col = cols[w];
+        const int j = col / nx, i = col - j * nx;
+        const uint8_t mk = a.smask[col];
+        double2 acc[6];
+        for (int c = 0; c < 6; ++c) acc[c] = make_double2(0.0, 0.0);
+        for (int k = lane; k < nz; k += 32) {
+            const double2 z = a.zph[k];
+            const double2 ue = make_double2(z.x * te.x - z.y * te.y, z.x * te.y + z.y * te.x);
+            const double2 uh = make_double2(z.x * th.x - z.y * th.y, z.x * th.y + z.y * th.x);
+            const int g = k * plane + j * a.pitch + i;
+            for (int c = 0; c < 3; ++c)
+                if (mk & (1 << c)) {
+                    real v = A.ein[c][g];
+                    if ((j == 0 && c != 1) || (i == 0 && c != 0)) v = real(0);   // PEC
+                    acc[c].x += double(v) * ue.x;
+                    acc[c].y += double(v) * ue.y;
                 }
-            }
-        } else {
-            for (int c = 0; c < 6; ++c) sk[c * P + so] = real(0);
+            for (int c = 3; c < 6; ++c)
+                if (mk & (1 << c)) {
+                    const double v = double(A.hout[c - 3][g]);
+                    acc[c].x += v * uh.x;
+                    acc[c].y += v * uh.y;
+                }
         }
-        if (tid < TX + TY + 1) {
-            if (halo_in) {
-                real hp[3], s[6];
-                adj_hterms<real, PX, P>(A, hi, hj, kw, false, t0, t1, hs, hp, s);
-                for (int c = 0; c < 6; ++c) sk[c * P + hs] = s[c];
-            } else {
-                for (int c = 0; c < 6; ++c) sk[c * P + hs] = real(0);
+        for (int c = 0; c < 6; ++c) {
+            if (!(mk & (1 << c))) continue;
+            double x = acc[c].x, y = acc[c].y;
+            for (int o = 16; o > 0; o >>= 1) {
+                x += __shfl_down_sync(0xffffffffu, x, o);
+                y += __shfl_down_sync(0xffffffffu, y, o);
             }
-        }
-        __syncthreads();   // s of planes k, k-1 ready
-        if (write_k && own) {
-            const real* s0 = sr + (k & 1) * 6 * P;
-            const real* s1 = sr + ((k - 1) & 1) * 6 * P;
-            const real ex = t0[6 * P + so], ey = t0[7 * P + so], ez = t0[8 * P + so];
-            // backward differences of s (i-1, j-1, k-1)
-            const real nex = ex + (s1[3 * P + so] - s0[3 * P + so]) + (s0[5 * P + so - PX] - s0[5 * P + so]);
-            const real ney = ey + (s1[1 * P + so] - s0[1 * P + so]) + (s0[4 * P + so - 1] - s0[4 * P + so]);
-            const real nez = ez + (s0[0 * P + so - PX] - s0[0 * P + so]) + (s0[2 * P + so - 1] - s0[2 * P + so]);
-            const int g = kw * pitch * ny + j * pitch + i;
-            A.eout[0][g] = nex; A.eout[1][g] = ney; A.eout[2][g] = nez;
-            if (mk & 0x07) {
-                const Cpx<real> u = uE[q];
-                const real ev[3] = {ex, ey, ez};
-                for (int c = 0; c < 3; ++c)
-                    if (mk & (1 << c)) { gacc[c].x += ev[c] * u.x; gacc[c].y += ev[c] * u.y; }
+            if (lane == 0) {
+                double2& gr = A.grad[c * nx * ny + col];
+                gr.x += x;
+                gr.y += y;
             }
         }
-    }
-    if (mk) {
-        const int ncol = nx * ny, col = j * nx + i;
-        for (int c = 0; c < 6; ++c)
-            if (mk & (1 << c)) {
-                atomicAdd(&A.grad[c * ncol + col].x, double(gacc[c].x));
-                atomicAdd(&A.grad[c * ncol + col].y, double(gacc[c].y));
-            }
     }
 }
 
@@ -344,8 +342,8 @@ struct fdtd_adjoint {
     int cur;
     // arena offsets
     size_t e[2][3], h[2][3], qx[2][2], qy[2][2], px[2][2], py[2][2];
-    size_t grad, cells, dyn_bytes, wout;
-    int lz;
+    size_t grad, cells, dyn_bytes, wout, acols;
+    int nacols;              // antenna columns (any component)
 };
 
 namespace {
@@ -368,6 +366,7 @@ static void adj_layout(const fdtd_grid* g, int64_t nprobes, fdtd_adjoint* a, siz
     a->grad = take(6 * size_t(g->desc.nx) * g->desc.ny * 16);
     a->dyn_bytes = off;
     a->wout = take(2 * size_t(g->desc.nx) * g->desc.ny * 8);
+    a->acols = take(size_t(g->desc.nx) * g->desc.ny * 4);
     a->cells = take(size_t(nprobes > 0 ? nprobes : 1) * 4);
     *total = off;
 }
@@ -399,22 +398,29 @@ AdjArgs<real> adj_args(const fdtd_adjoint* ad)
     return A;
 }
 
+// One reverse step of forward step n: the two cell passes and the source
+// gradient (time factors of step n evaluated on the host in FP64).
 template <typename real, int TY>
-cudaError_t adj_launch(fdtd_adjoint* ad, long long n)
+cudaError_t adj_cell_launch(fdtd_adjoint* ad, long long n)
 {
-    using T = AdjTile<real, TY>;
-    const int lz = ad->lz;
-    const size_t smem = T::smem_bytes(lz);
-    static size_t attr = 0;
-    if (smem > attr) {
-        cudaError_t e = cudaFuncSetAttribute(yee_adjoint_step<real, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
-        attr = smem;
-    }
-    const fdtd_grid_desc& d = ad->g->desc;
-    dim3 grid((d.nx + 31) / 32, (d.ny + TY - 1) / TY, (d.nz + lz - 1) / lz);
-    yee_adjoint_step<real, TY><<<grid, dim3(32, TY), smem, ad->g->stream>>>(adj_args<real>(ad), n, lz);
+    const fdtd_grid* g = ad->g;
+    const fdtd_grid_desc& d = g->desc;
+    const AdjArgs<real> A = adj_args<real>(ad);
+    const dim3 grid((d.nx + 31) / 32, (d.ny + TY - 1) / TY, d.nz), block(32, TY);
+    yee_adj_h_cell<real, TY><<<grid, block, 0, g->stream>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    yee_adj_e_cell<real, TY><<<grid, block, 0, g->stream>>>(A);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || ad->nacols == 0) return e;
+    double c, sn, f;
+    source_time(g->srct, (double(n) + 1.0) * g->dt, c, sn, f);
+    const double2 te = make_double2(f * c, -f * sn);
+    source_time(g->srct, (double(n) + 0.5) * g->dt, c, sn, f);
+    const double2 th = make_double2(f * c, -f * sn);
+    const int* cols = reinterpret_cast<const int*>(static_cast<char*>(ad->arena) + ad->acols);
+    const int threads = 256, blocks = (ad->nacols * 32 + threads - 1) / threads;
+    adj_source_grad<real><<<blocks < 4096 ? blocks : 4096, threads, 0, g->stream>>>(A, cols, ad->nacols, te, th);
     return cudaGetLastError();
 }
 
@@ -476,7 +482,6 @@ fdtd_status fdtd_adjoint_create(fdtd_grid* g, int component, const int64_t* prob
     a->bytes = bytes;
     a->n = g->step;
     a->cur = 0;
-    a->lz = g->desc.nz < 32 ? g->desc.nz : 32;
     // probe cells -> pitched element offsets
     const fdtd_grid_desc& d = g->desc;
     std::vector<int> off(size_t(n_probes > 0 ? n_probes : 1), 0);
@@ -486,7 +491,21 @@ fdtd_status fdtd_adjoint_create(fdtd_grid* g, int component, const int64_t* prob
         const int64_t i = c % d.nx, r = c / d.nx, j = r % d.ny, k = r / d.ny;
         off[size_t(p)] = int((k * d.ny + j) * g->L.pitch + i);
     }
-    fdtd_status st = cuda_check(cudaMemsetAsync(arena, 0, a->dyn_bytes, g->stream), "zero adjoint");
+    // antenna columns (any component) from the grid's mask
+    const size_t ncol = size_t(d.nx) * d.ny;
+    std::vector<uint8_t> mask(ncol);
+    std::vector<int> acols;
+    fdtd_status st = cuda_check(cudaMemcpyAsync(mask.data(), static_cast<char*>(g->arena) + g->L.smask, ncol,
+                                                cudaMemcpyDeviceToHost, g->stream), "read antenna mask");
+    if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(g->stream), "read antenna mask");
+    if (st != FDTD_OK) { delete a; return st; }
+    for (size_t c = 0; c < ncol; ++c)
+        if (mask[c] & 0x3f) acols.push_back(int(c));
+    a->nacols = int(acols.size());
+    st = cuda_check(cudaMemsetAsync(arena, 0, a->dyn_bytes, g->stream), "zero adjoint");
+    if (st == FDTD_OK && !acols.empty())
+        st = cuda_check(cudaMemcpyAsync(static_cast<char*>(arena) + a->acols, acols.data(), acols.size() * 4,
+                                        cudaMemcpyHostToDevice, g->stream), "upload antenna columns");
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(static_cast<char*>(arena) + a->cells, off.data(), off.size() * 4,
                                         cudaMemcpyHostToDevice, g->stream), "upload probes");
@@ -524,7 +543,7 @@ fdtd_status fdtd_adjoint_step(fdtd_adjoint* a, int nsteps, const void* dLdE, int
             if (e != cudaSuccess) return cuda_check(e, "adjoint inject");
         }
         const long long n = a->n - 1;   // reverse forward step n
-        cudaError_t e = eb == 8 ? adj_launch<double, 4>(a, n) : adj_launch<float, 8>(a, n);
+        cudaError_t e = eb == 8 ? adj_cell_launch<double, 4>(a, n) : adj_cell_launch<float, 4>(a, n);
         if (e != cudaSuccess) return cuda_check(e, "adjoint step");
         a->cur ^= 1;
         a->n -= 1;
