@@ -243,6 +243,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, in
 }
 
 // Grid: (ceil(nx/32), ceil(ny/TY), nz) CTAs of 32 x TY threads, one cell each.
+// The H pass takes the blocks in launch order, the E pass in reverse order.
 template <typename real, int TY>
 __global__ void __launch_bounds__(32 * TY)
 yee_h_cell(const StepArgs<real> a, const StepTime<real> t)
@@ -257,7 +258,10 @@ template <typename real, int TY>
 __global__ void __launch_bounds__(32 * TY)
 yee_e_cell(const StepArgs<real> a, const StepTime<real> t)
 {
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    // the E pass walks the grid backwards: it starts on the planes the H pass
+    // touched last, which are still in L2, and ends where the next H pass starts
+    const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
+    const int k = gridDim.z - 1 - blockIdx.z;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (cell_gen_e<real, TY>(a, i0, j0)) e_cell<real, true>(a, t.te, i, j, k);
     else e_cell<real, false>(a, t.te, i, j, k);
@@ -281,7 +285,8 @@ template <typename real, int TY>
 __global__ void __launch_bounds__(32 * TY)
 yee_e_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
 {
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
+    const int k = gridDim.z - 1 - blockIdx.z;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     const Cpx<real> te = times[index].te;
     if (cell_gen_e<real, TY>(a, i0, j0)) e_cell<real, true>(a, te, i, j, k);
