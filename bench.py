@@ -32,7 +32,7 @@ METRIC = "FDTD Gcell-updates/s FP32 vs FP64 at stated L2 error; % HBM roofline; 
 # DRAM bytes (read + write) per launch of a kernel on the 256x256x128 FP32
 # workload, from one ncu capture of the kernel as it stands (summary and
 # command in profiles/); None where no capture of the current kernel exists.
-TRAFFIC: dict[str, float] = {"yee_h_cell": 307.43e6, "yee_e_cell": 543.70e6}
+TRAFFIC: dict[str, float] = {"yee_h_cell": 307.81e6, "yee_e_cell": 545.12e6}
 UNIT = "Gcell-updates/s"
 
 
