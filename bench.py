@@ -29,6 +29,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "FDTD Gcell-updates/s FP32 vs FP64 at stated L2 error; % HBM roofline; adjoint s/step"
 
+NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e, nominal
+
 # DRAM bytes (read + write) per launch of a kernel on the 256x256x128 FP32
 # workload, from one ncu capture of the kernel as it stands (summary and
 # command in profiles/); None where no capture of the current kernel exists.
@@ -160,6 +162,30 @@ def _dist():
     return ws, rank, local
 
 
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ms: float, ws: int, device) -> float:
+    """The slowest rank's time: every rank times its own replica; the job
+    takes as long as the slowest one."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(cells_per_rank: int, steps: int, ws: int, ms: float) -> float:
+    """Whole-job Gcell-updates/s: the cell-updates of all ranks' replicas
+    over the (max-over-ranks) time."""
+    return cells_per_rank * steps * ws / (ms * 1e-3) / 1e9
+
+
 def run_gpu(args):
     import torch
     import numpy as np
@@ -173,10 +199,8 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    def _barrier():
+        barrier(ws)
 
     w = W.config2()
     cells = w.cells
@@ -192,7 +216,7 @@ def run_gpu(args):
     def timed(g, steps, warmup):
         stream = g.stream
         g.step(warmup)
-        barrier()
+        barrier(ws)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -200,14 +224,8 @@ def run_gpu(args):
         g.step(steps)
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        barrier()
-        ms = e0.elapsed_time(e1)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
+        barrier(ws)
+        return max_over_ranks(e0.elapsed_time(e1), ws, dev)
 
     peak, peak_kind = _peaks()
 
@@ -233,7 +251,7 @@ def run_gpu(args):
         pass32 = g32.step_timed(args.steps)
     clocks = clk.summary()
     step_ms = ms32 / args.steps
-    gcell32 = cells * args.steps * ws / (ms32 * 1e-3) / 1e9
+    gcell32 = job_rate(cells, args.steps, ws, ms32)
     ab32 = algorithmic_bytes_per_cell(w, 4)
     step_achieved = ab32 * cells / (step_ms * 1e-3) / 1e9
     passes32, dom32 = kernel_roofline(w, tile32, pass32, args.steps, 4, peak, cells)
@@ -244,7 +262,7 @@ def run_gpu(args):
     steps64 = max(10, args.steps // 4)
     ms64 = timed(g64, steps64, max(3, args.warmup // 4))
     pass64 = g64.step_timed(steps64)
-    gcell64 = cells * steps64 * ws / (ms64 * 1e-3) / 1e9
+    gcell64 = job_rate(cells, steps64, ws, ms64)
     ab64 = algorithmic_bytes_per_cell(w, 8)
     achieved64 = ab64 * cells / (ms64 / steps64 * 1e-3) / 1e9
     passes64, dom64 = kernel_roofline(w, tile64, pass64, steps64, 8, peak, cells)
@@ -262,7 +280,7 @@ def run_gpu(args):
     del a, b
 
     # ---- end to end through the public API with host buffers --------------
-    e2e = run_e2e(torch, fdtd, w, dev, args.steps, barrier, ws)
+    e2e = run_e2e(torch, fdtd, w, dev, args.steps, _barrier, ws)
 
     # ---- batched sweep: 16 uneven grids, one persistent launch per step ----
     batched = run_batched(torch, fdtd, W, dev, args.batch_steps) if args.batch_steps > 0 else None
@@ -284,6 +302,8 @@ def run_gpu(args):
                    "tile_f32": list(tile32), "tile_f64": list(tile64), "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": dom32["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": dom32["frac"], "traffic": TRAFFIC.get(dom32["kernel"]), "peak_kind": peak_kind,
+                     "peak_nominal": NOMINAL_HBM_GBS,
+                     "frac_nominal": round(dom32["achieved_gbs"] / NOMINAL_HBM_GBS, 4),
                      "kernel": dom32["kernel"], "algorithmic_bytes_per_cell": dom32["algorithmic_bytes_per_cell"],
                      "ms_per_launch": dom32["ms_per_launch"], "cells_per_launch": cells,
                      "kernels": passes32,
@@ -433,7 +453,7 @@ def run_e2e(torch, fdtd, w, dev, steps, barrier, ws):
     fdtd.fdtd_get_field(g.handle, 1 if w.pol == "y" else 0, fld_h.data_ptr(), False)
     torch.cuda.synchronize(dev)
     barrier()
-    dt = time.perf_counter() - t0
+    dt = max_over_ranks((time.perf_counter() - t0) * 1e3, ws, dev) * 1e-3
     h2d = 6 * init[0].numel() * 4 + (16 * 6 + 1) * w.nx * w.ny + 32 * w.nz
     d2h = flu_h.numel() * 8 + fld_h.numel() * 4
     g.close()
@@ -446,12 +466,14 @@ def run_e2e(torch, fdtd, w, dev, steps, barrier, ws):
 def cpu_baseline(w, budget_s: float = 15.0):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of
     the same workload: the full 256x256x128 grid with its antenna, for as many
-    steps as fit in about `budget_s` seconds."""
+    steps as fit in about `budget_s` seconds on all cores, then one step on
+    one thread."""
     import oracle
     og = oracle.Grid(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant)
     os_ = oracle.Source(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness,
                         ramp=w.ramp)
     st = oracle.State(og)
+    cores = oracle.threads()
     oracle.run(og, os_, st, 1)                  # antenna build + first step
     t0 = time.perf_counter()
     oracle.run(og, os_, st, 1)                  # calibration step
@@ -460,10 +482,15 @@ def cpu_baseline(w, budget_s: float = 15.0):
     t0 = time.perf_counter()
     oracle.run(og, os_, st, n)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.run(og, os_, st, 1)
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
     return {"value": round(w.cells * n / dt / 1e9, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": round(w.cells / dt1 / 1e9, 5),
             "sample": f"{n} steps of the full {w.nx}x{w.ny}x{w.nz} workload (FP64 C, OpenMP), "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s on {cores} threads; 1 step on 1 thread, {dt1:.1f} s"}
 
 
 def run_reference(args):
@@ -483,7 +510,7 @@ def run_reference(args):
     t0 = time.perf_counter()
     oracle.run(og, os_, st, n)
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
     v = w.cells * n / dt / 1e9
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": ws,

@@ -89,10 +89,23 @@ def lib():
             L.or_adjoint_step.restype = C.c_int
             L.or_adjoint_step.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(_State), C.c_long,
                                           dp, dp]
+            L.or_threads.restype = C.c_int
+            L.or_threads.argtypes = []
+            L.or_set_threads.restype = None
+            L.or_set_threads.argtypes = [C.c_int]
             L.or_antenna_counts.restype = C.c_int
             L.or_antenna_counts.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(C.c_long)]
             _lib = L
     return _lib
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops use."""
+    return int(lib().or_threads())
+
+
+def set_threads(n: int) -> None:
+    lib().or_set_threads(int(n))
 
 
 def courant_dt(dx: float, dy: float, dz: float, courant: float) -> float:

@@ -32,6 +32,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_PI 3.14159265358979323846
 
@@ -521,6 +524,25 @@ int or_run(const or_grid *g, const or_source *src, or_state *s, long n0, int nst
         rc = or_step(g, NULL, s, n0, nsteps);
     }
     return rc;
+}
+
+/* Threads of the OpenMP loops (timing of the oracle on the host cores). */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 /* Number of antenna points per component for a source (for tests). */
