@@ -68,7 +68,8 @@ enum {
     FDTD_POL_Y = 0,          /* Pi_x (Eq. 6): linear, y-polarised (paper default)  */
     FDTD_POL_X = 1,          /* Pi_y (Eq. 7): linear, x-polarised                  */
     FDTD_POL_CIRC_PLUS = 2,  /* (Pi_x + i Pi_y)/sqrt 2                             */
-    FDTD_POL_CIRC_MINUS = 3  /* (Pi_x - i Pi_y)/sqrt 2                             */
+    FDTD_POL_CIRC_MINUS = 3, /* (Pi_x - i Pi_y)/sqrt 2                             */
+    FDTD_POL_Z = 4           /* Pi_z (Eq. 8): for m = 0 azimuthal (TE), radial (TM) */
 };
 enum { FDTD_TE = 0, FDTD_TM = 1 };                    /* Eq. 9a / Eq. 9b       */
 enum { FDTD_ENV_CW_SIN2 = 0, FDTD_ENV_GAUSS = 1 };     /* CW ramp / Eq. 12 f(t) */
@@ -309,7 +310,8 @@ fdtd_status fdtd_fluence_noalloc(fdtd_grid* g, void* dst, int on_device, int res
  * component, into out[6][ny][nx] complex doubles (re, im interleaved:
  * 12*nx*ny doubles), plus the antenna mask out_mask[ny][nx] (bit c set when
  * column (i,j) holds a point of component c).  Runs no GPU code; exposed so
- * that the FP64 precompute can be checked on a host without a GPU. */
+ * that the FP64 precompute can be checked on a host without a GPU.  The
+ * descriptor is checked as by fdtd_set_annulus_source (EINVAL). */
 fdtd_status fdtd_source_coefficients(const fdtd_grid_desc* d, const fdtd_annulus_desc* s,
                                      double* out, uint8_t* out_mask);
 

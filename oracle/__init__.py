@@ -27,7 +27,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-POL = {"y": 0, "x": 1, "circ+": 2, "circ-": 3}
+POL = {"y": 0, "x": 1, "circ+": 2, "circ-": 3, "z": 4}
 MODE = {"TE": 0, "TM": 1}
 ENV = {"cw": 0, "gauss": 1}
 INJ = {"all": 0, "tangential": 1}

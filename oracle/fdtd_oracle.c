@@ -49,7 +49,7 @@ typedef struct {
     double pml_alpha_max;    /* alpha = alpha_max (1 - u)                   */
 } or_grid;
 
-enum { OR_POL_Y = 0, OR_POL_X = 1, OR_POL_CIRC_PLUS = 2, OR_POL_CIRC_MINUS = 3 };
+enum { OR_POL_Y = 0, OR_POL_X = 1, OR_POL_CIRC_PLUS = 2, OR_POL_CIRC_MINUS = 3, OR_POL_Z = 4 };
 enum { OR_TE = 0, OR_TM = 1 };
 enum { OR_ENV_CW_SIN2 = 0, OR_ENV_GAUSS = 1 };
 enum { OR_INJ_ALL = 0, OR_INJ_TANGENTIAL = 1 };
@@ -57,7 +57,7 @@ enum { OR_INJ_ALL = 0, OR_INJ_TANGENTIAL = 1 };
 typedef struct {
     int m;              /* Bessel order                                     */
     double theta;       /* cone angle, radians                              */
-    int pol;            /* OR_POL_*: Y = Pi_x potential, X = Pi_y potential */
+    int pol;            /* OR_POL_*: Y = Pi_x potential, X = Pi_y potential, Z = Pi_z potential */
     int mode;           /* OR_TE / OR_TM                                    */
     double E0;
     double r_center;    /* ring centre radius, in cells of dx               */
@@ -148,7 +148,8 @@ void or_pml_profile(const or_grid *g, int n, double d, double pos,
 
 /* Complex amplitudes (re,im interleaved, 3 components) of E and H of the
  * order-m vector Bessel beam at (x,y,z) measured from the beam axis.
- * Physical field = Re{ A e^{-i omega t'} }.  Eq. 6 (Pi_x), Eq. 7 (Pi_y), Eq. 9. */
+ * Physical field = Re{ A e^{-i omega t'} }.  Eq. 6 (Pi_x), Eq. 7 (Pi_y), Eq. 8 (Pi_z),
+ * Eq. 9. */
 typedef struct { double re, im; } cpx;
 static inline cpx C(double r, double i) { cpx c = {r, i}; return c; }
 static inline cpx cadd(cpx a, cpx b) { return C(a.re + b.re, a.im + b.im); }
@@ -189,6 +190,21 @@ static void qr_linear(int which, int m, double K, double beta, double k,
     }
 }
 
+/* Q and R of Eq. 8 (potential along z), without the common factor
+ * e^{i m phi} e^{i beta z}: azimuthal (TE) or radial (TM) fields for m = 0. */
+static void qr_axial(int m, double K, double beta, double r, double phi, cpx Q[3], cpx R[3])
+{
+    double Kr = K * r;
+    double jm = or_jn(m, Kr), jp1 = or_jn(m + 1, Kr), jm1 = or_jn(m - 1, Kr);
+    cpx p1 = cscale(cexpi(phi), jp1), m1 = cscale(cexpi(-phi), jm1);   /* J_{m+1} e^{i phi}, J_{m-1} e^{-i phi} */
+    Q[0] = cmul(C(0, K / 2.0), cadd(p1, m1));                            /* i K/2 [..+..]          */
+    Q[1] = cscale(csub(p1, m1), K / 2.0);                                /* K/2 [..-..]            */
+    Q[2] = C(0, 0);
+    R[0] = cmul(C(0, -beta * K / 2.0), csub(p1, m1));                    /* -i beta K/2 [..-..]    */
+    R[1] = cscale(cadd(p1, m1), -beta * K / 2.0);                        /* -beta K/2 [..+..]      */
+    R[2] = C(K * K * jm, 0);                                             /* K^2 J_m                */
+}
+
 void or_source_field(const or_source *s, double x, double y, double z,
                      double E[6], double H[6])
 {
@@ -200,6 +216,8 @@ void or_source_field(const or_source *s, double x, double y, double z,
     cpx Qa[3], Ra[3], Qb[3], Rb[3];
     if (s->pol == OR_POL_Y || s->pol == OR_POL_X) {
         qr_linear(s->pol == OR_POL_Y ? 0 : 1, s->m, K, beta, k, r, phi, Q, R);
+    } else if (s->pol == OR_POL_Z) {
+        qr_axial(s->m, K, beta, r, phi, Q, R);
     } else {
         /* (Pi_x +- i Pi_y) / sqrt 2 */
         double sg = (s->pol == OR_POL_CIRC_PLUS) ? 1.0 : -1.0;

@@ -14,7 +14,7 @@ struct GridSpec {
 struct SourceSpec {
     int m;
     double theta;
-    int pol;        // 0: Pi_x, 1: Pi_y, 2: circ+, 3: circ-
+    int pol;        // 0: Pi_x, 1: Pi_y, 2: circ+, 3: circ-, 4: Pi_z
     int mode;       // 0: TE, 1: TM
     double E0;
     double r_center, thickness;

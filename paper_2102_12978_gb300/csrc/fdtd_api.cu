@@ -411,11 +411,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     return FDTD_OK;
 }
 
-fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
+// Checks of an annulus descriptor against its grid (EINVAL with a message).
+static fdtd_status validate_source(const fdtd_grid_desc& d, const fdtd_annulus_desc* s)
 {
-    if (!g || !s) return fail(FDTD_EINVAL, "null argument");
-    const fdtd_grid_desc& d = g->desc;
-    if (s->pol < 0 || s->pol > 3 || (s->mode != FDTD_TE && s->mode != FDTD_TM) ||
+    if (s->pol < FDTD_POL_Y || s->pol > FDTD_POL_Z || (s->mode != FDTD_TE && s->mode != FDTD_TM) ||
         (s->envelope != FDTD_ENV_CW_SIN2 && s->envelope != FDTD_ENV_GAUSS) ||
         (s->inject != FDTD_INJECT_ALL && s->inject != FDTD_INJECT_TANGENTIAL))
         return fail(FDTD_EINVAL, "invalid enum in annulus descriptor");
@@ -427,6 +426,15 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
         return fail(FDTD_EINVAL, "ring outer radius %g cells reaches the CPML (limit %g)", rout, room);
     if (s->envelope == FDTD_ENV_GAUSS && !(s->T > 0.0)) return fail(FDTD_EINVAL, "Gaussian T must be > 0");
     if (s->envelope == FDTD_ENV_CW_SIN2 && s->ramp < 0.0) return fail(FDTD_EINVAL, "ramp must be >= 0");
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
+{
+    if (!g || !s) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_grid_desc& d = g->desc;
+    fdtd_status vst = validate_source(d, s);
+    if (vst != FDTD_OK) return vst;
     GridSpec gs{d.nx, d.ny, d.nz, d.npml, d.dx, d.dy, d.dz, g->dt};
     SourceSpec ss{s->m, s->theta, s->pol, s->mode, s->E0, s->r_center, s->thickness, s->inject};
     std::vector<std::complex<double>> coef, coef_unw;
@@ -773,6 +781,8 @@ fdtd_status fdtd_source_coefficients(const fdtd_grid_desc* d, const fdtd_annulus
     fdtd_status st = validate(d);
     if (st != FDTD_OK) return st;
     if (!s || !out || !out_mask) return fail(FDTD_EINVAL, "null argument");
+    st = validate_source(*d, s);
+    if (st != FDTD_OK) return st;
     GridSpec gs{d->nx, d->ny, d->nz, d->npml, d->dx, d->dy, d->dz, grid_dt(*d)};
     SourceSpec ss{s->m, s->theta, s->pol, s->mode, s->E0, s->r_center, s->thickness, s->inject};
     std::vector<std::complex<double>> coef;

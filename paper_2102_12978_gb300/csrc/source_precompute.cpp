@@ -115,6 +115,7 @@ void beam_fields(const SourceSpec& s, double x, double y, double z, cd E[3], cd 
         case 0: p[0] = 1.0; p[1] = 0.0; p[2] = 0.0; break;              // Pi_x
         case 1: p[0] = 0.0; p[1] = 1.0; p[2] = 0.0; break;              // Pi_y
         case 2: p[0] = 1.0 / std::sqrt(2.0); p[1] = I / std::sqrt(2.0); p[2] = 0.0; break;
+        case 4: p[0] = 0.0; p[1] = 0.0; p[2] = 1.0; break;              // Pi_z
         default: p[0] = 1.0 / std::sqrt(2.0); p[1] = -I / std::sqrt(2.0); p[2] = 0.0; break;
     }
     Derivs d = potential_derivs(s.m, K, beta, x, y);

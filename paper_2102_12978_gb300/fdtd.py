@@ -22,7 +22,7 @@ _lib = None
 FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_ETIMEOUT, FDTD_ESTATE = range(6)
 FDTD_F32, FDTD_F64 = 0, 1
 EX, EY, EZ, HX, HY, HZ = range(6)
-POL = {"y": 0, "x": 1, "circ+": 2, "circ-": 3}
+POL = {"y": 0, "x": 1, "circ+": 2, "circ-": 3, "z": 4}
 MODE = {"TE": 0, "TM": 1}
 ENV = {"cw": 0, "gauss": 1}
 INJ = {"all": 0, "tangential": 1}

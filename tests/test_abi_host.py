@@ -64,7 +64,8 @@ OFF = [(0.5, 0, 0), (0, 0.5, 0), (0, 0, 0.5), (0, 0.5, 0.5), (0.5, 0, 0.5), (0.5
 
 @pytest.mark.parametrize("m,pol,mode,inject", [(0, "y", "TE", "all"), (1, "x", "TE", "all"),
                                                (2, "circ+", "TE", "all"), (3, "y", "TM", "tangential"),
-                                               (1, "circ-", "TM", "all")])
+                                               (1, "circ-", "TM", "all"), (0, "z", "TE", "all"),
+                                               (0, "z", "TM", "all"), (2, "z", "TM", "tangential")])
 def test_host_precompute_matches_oracle_fields(m, pol, mode, inject):
     """A_c at every antenna column: library precompute vs oracle (FP64)."""
     w = W.small(nx=40, ny=36, nz=8, npml=4, theta_deg=23.0, m=m, pol=pol, r_center=9.0,

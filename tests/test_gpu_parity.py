@@ -105,6 +105,7 @@ def test_interior_block_classes(tile, precision):
 @pytest.mark.parametrize("kw", [
     dict(m=2, pol="circ+"), dict(m=3, pol="x", mode="TM"), dict(m=1, pol="circ-", inject="tangential"),
     dict(envelope="gauss", T=0.75, T0=1.5), dict(thickness=3.0, r_center=8.0, theta_deg=30.0),
+    dict(m=0, pol="z"), dict(m=0, pol="z", mode="TM"), dict(m=1, pol="z", mode="TM", inject="tangential"),
 ])
 def test_source_variants_match_oracle(kw):
     base = dict(nx=44, ny=40, nz=12, npml=6, r_center=9.0, steps=50, ramp=1.0)

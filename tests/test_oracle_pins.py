@@ -68,7 +68,7 @@ POINTS = [(0.31, 0.47, 0.13), (-1.2, 0.35, 0.9), (0.9, -2.1, 2.3), (-0.4, -0.77,
 
 @pytest.mark.parametrize("m", [0, 1, 2, 3])
 @pytest.mark.parametrize("theta_deg", [10.0, 25.0, 30.0])
-@pytest.mark.parametrize("pol", ["y", "x", "circ+"])
+@pytest.mark.parametrize("pol", ["y", "x", "circ+", "z"])
 def test_te_electric_field_is_curl_of_hertz_potential(m, theta_deg, pol):
     """E_TE = (E0/k0) curl(Pi) with Pi = unit * J_m(Kr) e^{im phi} e^{i beta z}
     (Eq. 5, Eq. 9a); taken here by numerical differentiation of scipy's J_m."""
@@ -80,18 +80,19 @@ def test_te_electric_field_is_curl_of_hertz_potential(m, theta_deg, pol):
         g = _grad(psi, p)
         qx = np.array([0.0, g[2], -g[1]])          # curl(x psi)
         qy = np.array([-g[2], 0.0, g[0]])          # curl(y psi)
-        Q = {"y": qx, "x": qy, "circ+": (qx + 1j * qy) / np.sqrt(2)}[pol]
+        qz = np.array([g[1], -g[0], 0.0])          # curl(z psi)
+        Q = {"y": qx, "x": qy, "circ+": (qx + 1j * qy) / np.sqrt(2), "z": qz}[pol]
         e, _ = oracle.source_field(src, *p)
         np.testing.assert_allclose(e, 1.7 / k * Q, rtol=0, atol=2e-9 * max(1, np.abs(Q).max()))
 
 
 @pytest.mark.parametrize("m", [0, 1, 3])
 @pytest.mark.parametrize("mode", ["TE", "TM"])
-@pytest.mark.parametrize("pol", ["y", "x", "circ-"])
+@pytest.mark.parametrize("pol", ["y", "x", "circ-", "z"])
 def test_source_fields_satisfy_maxwell(m, mode, pol):
     """curl E = i omega mu0 H and curl H = -i omega eps0 E for e^{-i omega t}
     (Section 3.1 convention); this pins the -i factor on H and every
-    component of Q and R in Eq. 6-7."""
+    component of Q and R in Eq. 6-8."""
     th = np.deg2rad(23.0)
     src = oracle.Source(m=m, theta=th, pol=pol, mode=mode)
     w = 2 * np.pi
@@ -104,12 +105,13 @@ def test_source_fields_satisfy_maxwell(m, mode, pol):
         np.testing.assert_allclose(_curl(Hf, p), -1j * w * e, atol=1e-8 * scale * w)
 
 
-def test_tm_is_dual_of_te():
+@pytest.mark.parametrize("pol", ["y", "z"])
+def test_tm_is_dual_of_te(pol):
     """Eq. 9b: the TM electric field is the curl of the TE electric field up to
     the constant k0 (E_TM = R/k0^2 = curl(Q)/k0^2, E_TE = Q/k0)."""
     th = np.deg2rad(17.0)
-    te = oracle.Source(m=1, theta=th, pol="y", mode="TE")
-    tm = oracle.Source(m=1, theta=th, pol="y", mode="TM")
+    te = oracle.Source(m=1, theta=th, pol=pol, mode="TE")
+    tm = oracle.Source(m=1, theta=th, pol=pol, mode="TM")
     k = 2 * np.pi
     for p in POINTS[:3]:
         curlE = _curl(lambda x, y, z: oracle.source_field(te, x, y, z)[0], p)
@@ -408,3 +410,30 @@ def test_bessel_intensity_matches_jm_squared():
     core = r_cells < 0.5 * 0.383 / np.sin(w.theta) / w.dx
     per_z = I[:, core].mean(axis=1)
     assert np.ptp(per_z) / per_z.mean() * 100 < GOLD["z_invariance_percent"]["value"]
+
+
+@pytest.mark.parametrize("theta_deg", [15.0, 30.0])
+def test_axial_potential_gives_azimuthal_te_and_radial_tm(theta_deg):
+    """Section 3 (after Eq. 8): for m = 0 the Pi_z potential gives a purely
+    azimuthal TE electric field and a TM electric field with no azimuthal
+    part (radial plus longitudinal), whose radial part is proportional to
+    J_1(K r) and its longitudinal part to J_0(K r)."""
+    th = np.deg2rad(theta_deg)
+    te = oracle.Source(m=0, theta=th, pol="z", mode="TE")
+    tm = oracle.Source(m=0, theta=th, pol="z", mode="TM")
+    K = 2 * np.pi * np.sin(th)
+    for p in POINTS:
+        x, y, z = p
+        r = math.hypot(x, y)
+        er = np.array([x / r, y / r])
+        ephi = np.array([-y / r, x / r])
+        e_te, _ = oracle.source_field(te, *p)
+        e_tm, _ = oracle.source_field(tm, *p)
+        scale = max(np.abs(e_te).max(), np.abs(e_tm).max())
+        assert abs(e_te[:2] @ er) < 1e-12 * scale and abs(e_te[2]) < 1e-12 * scale
+        assert abs(e_tm[:2] @ ephi) < 1e-12 * scale
+        # |E_r| / |E_z| = (beta K J_1) / (K^2 J_0) in magnitude (Eq. 8, R)
+        beta = 2 * np.pi * np.cos(th)
+        ratio = abs(e_tm[:2] @ er) / abs(e_tm[2])
+        want = abs(beta * special.jv(1, K * r)) / abs(K * special.jv(0, K * r))
+        assert ratio == pytest.approx(want, rel=1e-9)
