@@ -205,6 +205,16 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
  * with the fluence term, [1] E pass).  Synchronizes the stream.  EINVAL if
  * max_passes is smaller than the kernels per step. */
 fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_passes, int* n_passes);
+
+/* Test hook (the paper has no counterpart): fault injection on the host side
+ * of a device wait.  kind 1 makes the next step of a TMA variant (tile
+ * variants 1 and 2) withhold one plane's bulk copies in its first CTA: that
+ * CTA's bounded mbarrier wait (about 2^32 SM cycles) expires, it raises the
+ * grid's error word, drains its other copies and returns, and the next
+ * synchronising call (fdtd_sync, fdtd_fluence, ...) returns FDTD_ETIMEOUT;
+ * the device context stays usable.  kind 0 clears a pending fault; a fault
+ * applies to one step only.  EINVAL for another kind. */
+fdtd_status fdtd_debug_inject_fault(fdtd_grid* g, int kind);
 fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz);
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state);
 

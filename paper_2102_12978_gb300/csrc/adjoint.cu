@@ -23,6 +23,7 @@
 // with lambda = e' (E points) or h' (H points); dL/dw follows per column as
 // Re{e^{i phi} A g} and -w Im{e^{i phi} A g} summed over components.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <complex>
@@ -531,7 +532,17 @@ fdtd_status fdtd_probe_read(fdtd_adjoint* a, void* dev_out)
     return cuda_check(e, "probe gather");
 }
 
+static fdtd_status adjoint_steps(fdtd_adjoint* a, int nsteps, const void* dLdE, int64_t ld);
+
 fdtd_status fdtd_adjoint_step(fdtd_adjoint* a, int nsteps, const void* dLdE, int64_t ld)
+{
+    nvtxRangePushA("fdtd_adjoint_step");
+    fdtd_status st = adjoint_steps(a, nsteps, dLdE, ld);
+    nvtxRangePop();
+    return st;
+}
+
+static fdtd_status adjoint_steps(fdtd_adjoint* a, int nsteps, const void* dLdE, int64_t ld)
 {
     if (!a || nsteps < 0) return fail(FDTD_EINVAL, "invalid argument");
     if (nsteps > a->n) return fail(FDTD_EINVAL, "cannot step the adjoint before forward step 0");

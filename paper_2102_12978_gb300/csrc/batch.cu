@@ -22,6 +22,7 @@
 //     into a device table ahead of each replay; the kernels read their step's
 //     entry.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstring>
 #include <new>
@@ -407,7 +408,17 @@ fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine)
 
 int fdtd_batch_get_engine(const fdtd_batch* b) { return b ? b->engine : -1; }
 
+static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps);
+
 fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps)
+{
+    nvtxRangePushA("fdtd_batch_step");
+    fdtd_status st = batch_step_ranges(b, nsteps);
+    nvtxRangePop();
+    return st;
+}
+
+static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps)
 {
     if (!b || nsteps < 0) return fail(FDTD_EINVAL, "invalid argument");
     for (fdtd_grid* g : b->grids)

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <complex>
@@ -226,6 +227,7 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
     a.zph = reinterpret_cast<const double2*>(A + L.zph);
     a.zphr = sizeof(real) == 8 ? static_cast<const void*>(A + L.zph) : static_cast<const void*>(A + L.zph32);
     a.st = g->srct;
+    a.fault = g->fault;
     return a;
 }
 
@@ -525,12 +527,23 @@ fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
     if (nsteps < 0) return fail(FDTD_EINVAL, "nsteps < 0");
+    nvtxRangePushA("fdtd_step");
     for (int s = 0; s < nsteps; ++s) {
         cudaError_t e = launch_step(g, g->cur, g->step, g->tile, g->stream);
-        if (e != cudaSuccess) return cuda_check(e, "yee_step_fused launch");
+        g->fault = 0;
+        if (e != cudaSuccess) { nvtxRangePop(); return cuda_check(e, "step launch"); }
         g->cur ^= 1;
         g->step += 1;
     }
+    nvtxRangePop();
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_debug_inject_fault(fdtd_grid* g, int kind)
+{
+    if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (kind != 0 && kind != 1) return fail(FDTD_EINVAL, "fault kind %d not in {0, 1}", kind);
+    g->fault = kind;
     return FDTD_OK;
 }
 
@@ -547,6 +560,7 @@ fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_pa
         cudaEvent_t* e = &ev[size_t(s) * (np + 1)];
         cudaEventRecord(e[0], g->stream);
         st = cuda_check(launch_step(g, g->cur, g->step, g->tile, g->stream, np == 2 ? e[1] : nullptr), "step launch");
+        g->fault = 0;
         cudaEventRecord(e[np], g->stream);
         if (st == FDTD_OK) { g->cur ^= 1; g->step += 1; }
     }
@@ -731,6 +745,7 @@ fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz)
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
 {
     if (!g || !scratch_state || steps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    g->fault = 0;
     fdtd_status st = fdtd_save_state(g, scratch_state);
     if (st != FDTD_OK) return st;
     struct Cand { int variant, ty; };

@@ -68,6 +68,7 @@ struct fdtd_grid {
     bool maps_ok[2][3];
     fdtd::TmaMaps hmaps[2][3];  // the same for the boxes of yee_hflu_tma
     bool hmaps_ok[2][3];
+    int fault;                  // fdtd_debug_inject_fault: applies to the next step only
 };
 
 namespace fdtd {

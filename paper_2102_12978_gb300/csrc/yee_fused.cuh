@@ -69,6 +69,7 @@ struct StepArgs {
     const double2* zph;      // [nz]: e^{i beta k dz} (coefficients carry the half-cell z offset)
     const void* zphr;        // the same in the field precision (float2 / double2)
     SrcTime st;
+    int fault;               // test hook (fdtd_debug_inject_fault): 1 = CTA (0,0,0) withholds one plane's copies
 };
 
 // Time factor of the soft source at time t: cos / sin of the phase

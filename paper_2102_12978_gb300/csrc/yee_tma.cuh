@@ -287,6 +287,9 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     auto stage = [&](int s) { return base + s * T::STAGE; };
 
     // ---- TMA producer: plane q of this block into stage (gq0 + q) % S
+    // test hook: the first CTA arms plane 1's mbarrier but withholds its
+    // copies, so that its bounded wait expires (the drain skips that plane)
+    const int withheld = (a.fault == 1 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) ? 1 : -1;
     auto issue = [&](int q) {
         const int p = kb - 1 + q;
         const int pw = p < 0 ? p + nz : (p >= nz ? p - nz : p);
@@ -296,6 +299,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
         uint64_t* bar = &bars[s];
         unsigned char* st = stage(s);
         mbar_expect_tx(bar, 3 * T::E_BYTES + (needH ? 3 * T::H_BYTES : 0u) + (needF ? T::F_BYTES : 0u));
+        if (q == withheld) return;
         #pragma unroll
         for (int c = 0; c < 3; ++c) tma_load_3d(st + c * T::EB, &m.e[c], bar, i0 - XA, j0 - 1, pw);
         if (needH) {
@@ -583,7 +587,7 @@ __device__ __forceinline__ int tma_march(const StepArgs<real>& a, const TmaMaps&
     if (abort_flag) {
         if (tid == PRODUCER)
             for (int q = waited + 1; q < issued; ++q)
-                mbar_wait_bounded(&bars[(gq0 + q) % S], uint32_t(((gq0 + q) / S) & 1));
+                if (q != withheld) mbar_wait_bounded(&bars[(gq0 + q) % S], uint32_t(((gq0 + q) / S) & 1));
         return -1;
     }
     return gq0 + Q;

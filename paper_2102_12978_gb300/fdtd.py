@@ -72,6 +72,7 @@ _SIGS = {
     "fdtd_sync": (C.c_int, [C.c_void_p]),
     "fdtd_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "fdtd_step_timed": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
+    "fdtd_debug_inject_fault": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
@@ -269,6 +270,11 @@ class Grid:
         npass = C.c_int()
         check(lib().fdtd_step_timed(C.c_void_p(self.handle), int(n), ms, 4, C.byref(npass)), "fdtd_step_timed")
         return [float(ms[p]) for p in range(npass.value)]
+
+    def inject_fault(self, kind: int = 1):
+        """Test hook: the next step of a TMA variant withholds one bulk copy,
+        so that its bounded device wait expires (fdtd_debug_inject_fault)."""
+        check(lib().fdtd_debug_inject_fault(C.c_void_p(self.handle), int(kind)), "fdtd_debug_inject_fault")
 
     def set_tile(self, variant: int, ty: int, lz: int):
         check(lib().fdtd_set_tile(C.c_void_p(self.handle), int(variant), int(ty), int(lz)), "fdtd_set_tile")

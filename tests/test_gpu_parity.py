@@ -39,9 +39,13 @@ def _compare(w, precision, tile=None, npml=None, source=True, init=None, fluence
     g.sync()
     errs = {}
     for c, ref in enumerate(st.fields()):
-        errs["ExEyEzHxHyHz"[2 * c:2 * c + 2]] = rel_l2(host(g.field(c)), ref)
+        got = host(g.field(c))
+        assert np.isfinite(got).all(), "non-finite field values"
+        errs["ExEyEzHxHyHz"[2 * c:2 * c + 2]] = rel_l2(got, ref)
     if fluence:
-        errs["fluence"] = rel_l2(host(g.fluence()), st.fluence)
+        got = host(g.fluence())
+        assert np.isfinite(got).all(), "non-finite fluence values"
+        errs["fluence"] = rel_l2(got, st.fluence)
     if source:
         counts = oracle.antenna_counts(og, os_)
         assert [g.antenna_points(c) for c in range(6)] == counts

@@ -1,0 +1,67 @@
+"""Edge cases of the GPU path: grids smaller than one tile (every variant,
+every cell against the oracle), and the bounded device wait: a withheld bulk
+copy (host-side fault injection) makes the wait expire, the host reads
+FDTD_ETIMEOUT, and the device stays usable."""
+import numpy as np
+import pytest
+
+from paper_2102_12978_gb300 import fdtd
+from paper_2102_12978_gb300 import workloads as W
+from tests.test_gpu_parity import _assert, _compare
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [(0, 4, 1), (1, 4, 1), (1, 8, 2), (2, 8, 2), (3, 4, 1), (4, 4, 1), (5, 4, 1), (5, 16, 1), (6, 4, 1)]
+
+
+def _random_pec_state(w):
+    init = W.random_state((w.nz, w.ny, w.nx), seed=11)
+    init[1][:, :, 0] = 0; init[2][:, :, 0] = 0     # tangential E on the i = 0 wall
+    init[0][:, 0, :] = 0; init[2][:, 0, :] = 0     # and on the j = 0 wall
+    return init
+
+
+@pytest.mark.parametrize("tile", VARIANTS)
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("shape,npml", [((13, 7, 5), 1), ((8, 8, 8), 2), ((4, 4, 4), 0), ((33, 9, 3), 2)])
+def test_grids_smaller_than_a_tile(shape, npml, precision, tile):
+    nx, ny, nz = shape
+    w = W.small(nx=nx, ny=ny, nz=nz, npml=npml, steps=12)
+    _assert(_compare(w, precision, tile=tile, npml=npml, source=False, init=_random_pec_state(w)), precision)
+
+
+@pytest.mark.parametrize("tile", VARIANTS)
+def test_tiny_grid_with_antenna(tile):
+    w = W.small(nx=13, ny=11, nz=5, npml=1, r_center=1.5, thickness=1.0, steps=20, ramp=0.2)
+    _assert(_compare(w, "f64", tile=tile, npml=1), "f64")
+
+
+def test_expired_device_wait_reports_timeout():
+    w = W.small(nx=48, ny=40, nz=16, npml=6, r_center=11.0, steps=6, ramp=1.0)
+    d = fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, precision="f32")
+    g = fdtd.Grid(d)
+    g.set_source(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness, ramp=w.ramp)
+    g.set_tile(1, 8, 8)
+    g.step(2)
+    g.sync()
+    g.inject_fault(1)
+    g.step(1)
+    with pytest.raises(fdtd.FDTDError) as e:
+        g.sync()
+    assert e.value.status == fdtd.FDTD_ETIMEOUT
+    g.sync()                      # the error word was cleared with the report
+    g.step(2)                     # the fault applied to one step only
+    g.sync()
+    g.close()
+    # the device context is still usable: a fresh grid matches the oracle
+    _assert(_compare(W.small(nx=40, ny=36, nz=8, npml=6, r_center=9.0, steps=20, ramp=1.0), "f32",
+                     tile=(1, 8, 8)), "f32")
+
+
+def test_fault_hook_rejects_unknown_kinds():
+    w = W.small(nx=16, ny=16, nz=4, npml=2)
+    g = fdtd.Grid(fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz))
+    with pytest.raises(fdtd.FDTDError) as e:
+        g.inject_fault(7)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    g.close()
