@@ -51,7 +51,13 @@ class _Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("npml", C.c_int),
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("dt", C.c_double),
                 ("pml_order", C.c_double), ("pml_sigma_scale", C.c_double),
-                ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double)]
+                ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double),
+                ("zbc", C.c_int), ("npml_z", C.c_int)]
+
+
+class _Wall(C.Structure):
+    _fields_ = [("theta", C.c_double), ("w0", C.c_double), ("E0", C.c_double), ("envelope", C.c_int),
+                ("ramp", C.c_double), ("T", C.c_double), ("T0", C.c_double), ("plane", C.c_int)]
 
 
 class _Source(C.Structure):
@@ -65,7 +71,8 @@ class _Source(C.Structure):
 class _State(C.Structure):
     _fields_ = [("e", C.POINTER(C.c_double) * 3), ("h", C.POINTER(C.c_double) * 3),
                 ("psi_e", C.POINTER(C.c_double) * 4), ("psi_h", C.POINTER(C.c_double) * 4),
-                ("fluence", C.POINTER(C.c_double))]
+                ("fluence", C.POINTER(C.c_double)),
+                ("psi_ez", C.POINTER(C.c_double) * 2), ("psi_hz", C.POINTER(C.c_double) * 2)]
 
 
 def lib():
@@ -86,6 +93,9 @@ def lib():
             L.or_source_time.argtypes = [C.POINTER(_Source), C.c_double, dp, dp, dp]
             L.or_run.restype = C.c_int
             L.or_run.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(_State), C.c_long, C.c_int]
+            L.or_run_wall.restype = C.c_int
+            L.or_run_wall.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(_Wall), C.POINTER(_State),
+                                      C.c_long, C.c_int]
             L.or_adjoint_step.restype = C.c_int
             L.or_adjoint_step.argtypes = [C.POINTER(_Grid), C.POINTER(_Source), C.POINTER(_State), C.c_long,
                                           dp, dp]
@@ -132,6 +142,8 @@ class Grid:
     pml_sigma_scale: float = 0.8
     pml_kappa_max: float = 1.0
     pml_alpha_max: float = 0.05 * 2.0 * np.pi
+    z_walls: bool = False       # PEC walls at z = 0 and z = nz dz instead of periodic z
+    npml_z: int = 0             # CPML cells inside each z wall (z_walls only)
 
     def __post_init__(self):
         if self.dt is None or self.dt == 0.0:
@@ -139,7 +151,8 @@ class Grid:
 
     def _c(self) -> _Grid:
         return _Grid(self.nx, self.ny, self.nz, self.npml, self.dx, self.dy, self.dz, self.dt,
-                     self.pml_order, self.pml_sigma_scale, self.pml_kappa_max, self.pml_alpha_max)
+                     self.pml_order, self.pml_sigma_scale, self.pml_kappa_max, self.pml_alpha_max,
+                     1 if self.z_walls else 0, self.npml_z if self.z_walls else 0)
 
     @property
     def shape(self):
@@ -190,6 +203,8 @@ class State:
         self.h = [np.zeros(shp) for _ in range(3)]
         self.psi_e = [np.zeros(shp) for _ in range(4)]
         self.psi_h = [np.zeros(shp) for _ in range(4)]
+        self.psi_ez = [np.zeros(shp) for _ in range(2)]
+        self.psi_hz = [np.zeros(shp) for _ in range(2)]
         self.fluence = np.zeros(shp) if fluence else None
         self.n = 0
 
@@ -203,6 +218,9 @@ class State:
             s.psi_e[c] = self.psi_e[c].ctypes.data_as(dp)
             s.psi_h[c] = self.psi_h[c].ctypes.data_as(dp)
         s.fluence = self.fluence.ctypes.data_as(dp) if self.fluence is not None else dp()
+        for c in range(2):
+            s.psi_ez[c] = self.psi_ez[c].ctypes.data_as(dp)
+            s.psi_hz[c] = self.psi_hz[c].ctypes.data_as(dp)
         return s
 
     def copy(self) -> "State":
@@ -211,6 +229,8 @@ class State:
         o.h = [a.copy() for a in self.h]
         o.psi_e = [a.copy() for a in self.psi_e]
         o.psi_h = [a.copy() for a in self.psi_h]
+        o.psi_ez = [a.copy() for a in self.psi_ez]
+        o.psi_hz = [a.copy() for a in self.psi_hz]
         o.fluence = None if self.fluence is None else self.fluence.copy()
         o.n = self.n
         return o
@@ -220,15 +240,35 @@ class State:
         return (*self.e, *self.h)
 
 
-def run(grid: Grid, source: Source | None, state: State, nsteps: int) -> State:
-    """Advance `state` by nsteps Yee steps in place (Section 4, Eq. 13)."""
-    for a in (*state.e, *state.h, *state.psi_e, *state.psi_h):
+@dataclass
+class Wall:
+    """Wall source (the Bessel-Gauss reference of Section 2): a Gaussian beam of
+    waist w0 (wavelengths), polarised along x, with the axicon phase
+    -k r sin(theta), added to E_x on plane `plane` after each E update."""
+    theta: float = np.deg2rad(25.0)
+    w0: float = 7.5
+    E0: float = 1.0
+    envelope: str = "cw"
+    ramp: float = 10.0
+    T: float = 0.0
+    T0: float = 0.0
+    plane: int = 0
+
+    def _c(self) -> _Wall:
+        return _Wall(self.theta, self.w0, self.E0, ENV[self.envelope], self.ramp, self.T, self.T0, self.plane)
+
+
+def run(grid: Grid, source: Source | None, state: State, nsteps: int, wall: Wall | None = None) -> State:
+    """Advance `state` by nsteps Yee steps in place (Section 4, Eq. 13; the
+    wall source of Section 2 if given)."""
+    for a in (*state.e, *state.h, *state.psi_e, *state.psi_h, *state.psi_ez, *state.psi_hz):
         assert a.flags.c_contiguous and a.dtype == np.float64 and a.shape == grid.shape
     g = grid._c()
     s = source._c() if source is not None else None
+    w = wall._c() if wall is not None else None
     st = state._c()
-    rc = lib().or_run(C.byref(g), C.byref(s) if s is not None else None, C.byref(st),
-                      state.n, int(nsteps))
+    rc = lib().or_run_wall(C.byref(g), C.byref(s) if s is not None else None,
+                           C.byref(w) if w is not None else None, C.byref(st), state.n, int(nsteps))
     if rc != 0:
         raise RuntimeError(f"oracle run failed ({rc})")
     state.n += nsteps

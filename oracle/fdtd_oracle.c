@@ -47,7 +47,12 @@ typedef struct {
     double pml_sigma_scale;  /* sigma_max = scale (m+1) / (eta dx)          */
     double pml_kappa_max;    /* kappa = 1 + (kappa_max - 1) u^m             */
     double pml_alpha_max;    /* alpha = alpha_max (1 - u)                   */
+    int zbc;                 /* OR_Z_PERIODIC, or OR_Z_WALLS: PEC walls at z = 0 and
+                                z = nz dz with npml_z CPML cells inside each      */
+    int npml_z;
 } or_grid;
+
+enum { OR_Z_PERIODIC = 0, OR_Z_WALLS = 1 };
 
 enum { OR_POL_Y = 0, OR_POL_X = 1, OR_POL_CIRC_PLUS = 2, OR_POL_CIRC_MINUS = 3, OR_POL_Z = 4 };
 enum { OR_TE = 0, OR_TM = 1 };
@@ -90,7 +95,24 @@ typedef struct {
     double *psi_e[4];   /* Exy, Ezy, Eyx, Ezx  (full grid; nonzero in shells) */
     double *psi_h[4];   /* Hxy, Hzy, Hyx, Hzx                                 */
     double *fluence;    /* nx*ny*nz or NULL                                   */
+    double *psi_ez[2];  /* Exz, Eyz (z shells of OR_Z_WALLS grids)           */
+    double *psi_hz[2];  /* Hxz, Hyz                                           */
 } or_state;
+
+/* Wall source (the Bessel-Gauss reference of Section 2): a Gaussian beam,
+ * polarised along x, with the axicon phase Phi(r) = -k r sin(theta), added
+ * to E_x on the plane k = plane after each E update:
+ *   E_x += f(t) Re{ E0 exp(-r^2 / w0^2) e^{-i k r sin(theta)} e^{-i omega t'} }
+ * at the E_x point (r from the axis at nx dx/2, ny dy/2), t = (n+1) dt,
+ * with f and t' as for the antenna (CW ramp or Gaussian).  The row j = 0
+ * (on the y = 0 PEC wall) is left out, and on a z-walled grid the plane
+ * may not be k = 0 (the z = 0 PEC wall). */
+typedef struct {
+    double theta, w0, E0;
+    int envelope;
+    double ramp, T, T0;
+    int plane;
+} or_wall;
 
 /* ------------------------------------------------------------- helpers */
 
@@ -122,12 +144,12 @@ double or_jn(int n, double x)
  *   u = depth / (npml d),  sigma = sigma_max u^m,  kappa = 1 + (kmax-1) u^m,
  *   alpha = alpha_max (1-u),  b = exp(-(sigma/kappa + alpha) dt),
  *   a = sigma (b-1) / (kappa (sigma + kappa alpha)).                          */
-void or_pml_profile(const or_grid *g, int n, double d, double pos,
-                    double *b, double *a, double *kappa)
+static void pml_profile_n(const or_grid *g, int n, int npml, double d, double pos,
+                          double *b, double *a, double *kappa)
 {
     *b = 1.0; *a = 0.0; *kappa = 1.0;
-    if (g->npml <= 0) return;
-    double L = n * d, w = g->npml * d;
+    if (npml <= 0) return;
+    double L = n * d, w = npml * d;
     double depth = 0.0;
     if (pos < w) depth = w - pos;
     if (pos > L - w) depth = pos - (L - w);
@@ -142,6 +164,12 @@ void or_pml_profile(const or_grid *g, int n, double d, double pos,
     *b = exp(-(sigma / kap + alpha) * g->dt);
     if (sigma > 0.0)
         *a = sigma * (*b - 1.0) / (kap * (sigma + kap * alpha));
+}
+
+void or_pml_profile(const or_grid *g, int n, double d, double pos,
+                    double *b, double *a, double *kappa)
+{
+    pml_profile_n(g, n, g->npml, d, pos, b, a, kappa);
 }
 
 /* ------------------------------------------------ analytic source fields */
@@ -365,11 +393,16 @@ static void add_source(const or_antenna *ant, or_state *st, int first, double t)
 
 /* Field value with the PEC / periodic boundary reading: indices past the
  * +x / +y walls (i == nx, j == ny) are the wall itself, where tangential E
- * and normal H are zero; z wraps. */
+ * and normal H are zero; z wraps, or (OR_Z_WALLS) reads zero past the z
+ * walls in the same way. */
 static inline double at(const or_grid *g, const double *f, long i, long j, long k)
 {
     if (i >= g->nx || j >= g->ny || i < 0 || j < 0) return 0.0;
-    k = ((k % g->nz) + g->nz) % g->nz;
+    if (g->zbc == OR_Z_WALLS) {
+        if (k < 0 || k >= g->nz) return 0.0;
+    } else {
+        k = ((k % g->nz) + g->nz) % g->nz;
+    }
     return f[IDX(g, i, j, k)];
 }
 
@@ -377,15 +410,17 @@ static inline double at(const or_grid *g, const double *f, long i, long j, long 
  * positions of H's transverse derivatives; half = 0: integer positions). */
 typedef struct { double *b, *a, *kappa; } or_prof;
 
+/* axis 0, 1, 2 = x, y, z; the z axis has a CPML only on OR_Z_WALLS grids */
 static void prof_build(const or_grid *g, int axis, int half, or_prof *p)
 {
-    int n = axis == 0 ? g->nx : g->ny;
-    double d = axis == 0 ? g->dx : g->dy;
+    int n = axis == 0 ? g->nx : (axis == 1 ? g->ny : g->nz);
+    double d = axis == 0 ? g->dx : (axis == 1 ? g->dy : g->dz);
+    int npml = axis < 2 ? g->npml : (g->zbc == OR_Z_WALLS ? g->npml_z : 0);
     p->b = (double *)malloc(sizeof(double) * n);
     p->a = (double *)malloc(sizeof(double) * n);
     p->kappa = (double *)malloc(sizeof(double) * n);
     for (int i = 0; i < n; ++i)
-        or_pml_profile(g, n, d, (i + 0.5 * half) * d, &p->b[i], &p->a[i], &p->kappa[i]);
+        pml_profile_n(g, n, npml, d, (i + 0.5 * half) * d, &p->b[i], &p->a[i], &p->kappa[i]);
 }
 
 static void prof_free(or_prof *p) { free(p->b); free(p->a); free(p->kappa); }
@@ -395,13 +430,16 @@ static void update_h(const or_grid *g, or_state *s)
     double *Ex = s->e[0], *Ey = s->e[1], *Ez = s->e[2];
     double *Hx = s->h[0], *Hy = s->h[1], *Hz = s->h[2];
     double dt = g->dt;
-    or_prof px, py;
+    or_prof px, py, pz;
     prof_build(g, 0, 1, &px);
     prof_build(g, 1, 1, &py);
+    prof_build(g, 2, 1, &pz);
+    const int zw = g->zbc == OR_Z_WALLS;
 #pragma omp parallel for schedule(static)
     for (long k = 0; k < g->nz; ++k)
         for (long j = 0; j < g->ny; ++j) {
             double byh = py.b[j], ayh = py.a[j], kyh = py.kappa[j];
+            double bzh = pz.b[k], azh = pz.a[k], kzh = pz.kappa[k];
             for (long i = 0; i < g->nx; ++i) {
                 double bxh = px.b[i], axh = px.a[i], kxh = px.kappa[i];
                 long id = IDX(g, i, j, k);
@@ -409,12 +447,22 @@ static void update_h(const or_grid *g, or_state *s)
                 double dEz_dy = (at(g, Ez, i, j + 1, k) - at(g, Ez, i, j, k)) / g->dy;
                 double dEy_dz = (at(g, Ey, i, j, k + 1) - at(g, Ey, i, j, k)) / g->dz;
                 s->psi_h[0][id] = byh * s->psi_h[0][id] + ayh * dEz_dy;
-                Hx[id] -= dt * (dEz_dy / kyh + s->psi_h[0][id] - dEy_dz);
+                double zx = dEy_dz;
+                if (zw) {
+                    s->psi_hz[0][id] = bzh * s->psi_hz[0][id] + azh * dEy_dz;
+                    zx = dEy_dz / kzh + s->psi_hz[0][id];
+                }
+                Hx[id] -= dt * (dEz_dy / kyh + s->psi_h[0][id] - zx);
                 /* Hy at (i+1/2, j, k+1/2): dEx/dz - dEz/dx */
                 double dEx_dz = (at(g, Ex, i, j, k + 1) - at(g, Ex, i, j, k)) / g->dz;
                 double dEz_dx = (at(g, Ez, i + 1, j, k) - at(g, Ez, i, j, k)) / g->dx;
                 s->psi_h[2][id] = bxh * s->psi_h[2][id] + axh * dEz_dx;
-                Hy[id] -= dt * (dEx_dz - (dEz_dx / kxh + s->psi_h[2][id]));
+                double zy = dEx_dz;
+                if (zw) {
+                    s->psi_hz[1][id] = bzh * s->psi_hz[1][id] + azh * dEx_dz;
+                    zy = dEx_dz / kzh + s->psi_hz[1][id];
+                }
+                Hy[id] -= dt * (zy - (dEz_dx / kxh + s->psi_h[2][id]));
                 /* Hz at (i+1/2, j+1/2, k): dEy/dx - dEx/dy */
                 double dEy_dx = (at(g, Ey, i + 1, j, k) - at(g, Ey, i, j, k)) / g->dx;
                 double dEx_dy = (at(g, Ex, i, j + 1, k) - at(g, Ex, i, j, k)) / g->dy;
@@ -425,6 +473,7 @@ static void update_h(const or_grid *g, or_state *s)
         }
     prof_free(&px);
     prof_free(&py);
+    prof_free(&pz);
 }
 
 static void update_e(const or_grid *g, or_state *s)
@@ -432,33 +481,47 @@ static void update_e(const or_grid *g, or_state *s)
     double *Ex = s->e[0], *Ey = s->e[1], *Ez = s->e[2];
     double *Hx = s->h[0], *Hy = s->h[1], *Hz = s->h[2];
     double dt = g->dt;
-    or_prof px, py;
+    or_prof px, py, pz;
     prof_build(g, 0, 0, &px);
     prof_build(g, 1, 0, &py);
+    prof_build(g, 2, 0, &pz);
+    const int zw = g->zbc == OR_Z_WALLS;
 #pragma omp parallel for schedule(static)
     for (long k = 0; k < g->nz; ++k)
         for (long j = 0; j < g->ny; ++j) {
             double bye = py.b[j], aye = py.a[j], kye = py.kappa[j];
+            double bze = pz.b[k], aze = pz.a[k], kze = pz.kappa[k];
             for (long i = 0; i < g->nx; ++i) {
                 double bxe = px.b[i], axe = px.a[i], kxe = px.kappa[i];
                 long id = IDX(g, i, j, k);
-                /* Ex at (i+1/2, j, k): dHz/dy - dHy/dz ; tangential to the y = 0 wall at j = 0 */
-                if (j > 0) {
+                /* Ex at (i+1/2, j, k): dHz/dy - dHy/dz ; tangential to the y = 0 wall at j = 0
+                 * (and to the z = 0 wall at k = 0 on OR_Z_WALLS grids) */
+                if (j > 0 && !(zw && k == 0)) {
                     double dHz_dy = (at(g, Hz, i, j, k) - at(g, Hz, i, j - 1, k)) / g->dy;
                     double dHy_dz = (at(g, Hy, i, j, k) - at(g, Hy, i, j, k - 1)) / g->dz;
                     s->psi_e[0][id] = bye * s->psi_e[0][id] + aye * dHz_dy;
-                    Ex[id] += dt * ((dHz_dy / kye + s->psi_e[0][id]) - dHy_dz);
+                    double zx = dHy_dz;
+                    if (zw) {
+                        s->psi_ez[0][id] = bze * s->psi_ez[0][id] + aze * dHy_dz;
+                        zx = dHy_dz / kze + s->psi_ez[0][id];
+                    }
+                    Ex[id] += dt * ((dHz_dy / kye + s->psi_e[0][id]) - zx);
                 } else {
-                    Ex[id] = 0.0;   /* PEC: tangential E on the y = 0 wall */
+                    Ex[id] = 0.0;   /* PEC: tangential E on the y = 0 (z = 0) wall */
                 }
-                /* Ey at (i, j+1/2, k): dHx/dz - dHz/dx ; tangential to x = 0 at i = 0 */
-                if (i > 0) {
+                /* Ey at (i, j+1/2, k): dHx/dz - dHz/dx ; tangential to x = 0 at i = 0 (and z = 0) */
+                if (i > 0 && !(zw && k == 0)) {
                     double dHx_dz = (at(g, Hx, i, j, k) - at(g, Hx, i, j, k - 1)) / g->dz;
                     double dHz_dx = (at(g, Hz, i, j, k) - at(g, Hz, i - 1, j, k)) / g->dx;
                     s->psi_e[2][id] = bxe * s->psi_e[2][id] + axe * dHz_dx;
-                    Ey[id] += dt * (dHx_dz - (dHz_dx / kxe + s->psi_e[2][id]));
+                    double zy = dHx_dz;
+                    if (zw) {
+                        s->psi_ez[1][id] = bze * s->psi_ez[1][id] + aze * dHx_dz;
+                        zy = dHx_dz / kze + s->psi_ez[1][id];
+                    }
+                    Ey[id] += dt * (zy - (dHz_dx / kxe + s->psi_e[2][id]));
                 } else {
-                    Ey[id] = 0.0;   /* PEC: tangential E on the x = 0 wall */
+                    Ey[id] = 0.0;   /* PEC: tangential E on the x = 0 (z = 0) wall */
                 }
                 /* Ez at (i, j, k+1/2): dHy/dx - dHx/dy ; tangential to both walls */
                 if (i > 0 && j > 0) {
@@ -474,6 +537,7 @@ static void update_e(const or_grid *g, or_state *s)
         }
     prof_free(&px);
     prof_free(&py);
+    prof_free(&pz);
 }
 
 /* |E_c x Hbar_c| at the centre of cell (i,j,k): E averaged over the four
@@ -495,11 +559,36 @@ static double poynting_mag(const or_grid *g, const or_state *s, double *const ho
     return sqrt(sx * sx + sy * sy + sz * sz);
 }
 
+/* The wall source at time t (E time (n+1) dt): E_x on the plane w->plane. */
+static void add_wall(const or_grid *g, const or_wall *w, or_state *st, double t)
+{
+    or_source tsrc;
+    memset(&tsrc, 0, sizeof(tsrc));
+    tsrc.envelope = w->envelope;
+    tsrc.ramp = w->ramp;
+    tsrc.T = w->T;
+    tsrc.T0 = w->T0;
+    double cphi, sphi, f;
+    or_source_time(&tsrc, t, &cphi, &sphi, &f);
+    const double k = 2.0 * OR_PI, ks = k * sin(w->theta);
+    const double xc = 0.5 * g->nx * g->dx, yc = 0.5 * g->ny * g->dy;
+    for (long j = 1; j < g->ny; ++j)   /* j = 0: E_x is tangential to the y = 0 PEC wall */
+        for (long i = 0; i < g->nx; ++i) {
+            const double x = (i + 0.5) * g->dx - xc, y = j * g->dy - yc;   /* E_x point */
+            const double r = sqrt(x * x + y * y);
+            const double a = w->E0 * exp(-(r * r) / (w->w0 * w->w0));
+            /* Re{ a e^{-i k r sin(theta)} e^{-i Phi} } = a cos(k r sin(theta) + Phi) */
+            const double ph = ks * r;
+            st->e[0][IDX(g, i, j, w->plane)] += f * a * (cos(ph) * cphi - sin(ph) * sphi);
+        }
+}
+
 /* Advance `nsteps` full Yee steps starting at step index n0 (E at n0 dt,
  * H at (n0 - 1/2) dt).  Order in each step: H curl update (with CPML psi),
  * H soft source at (n+1/2) dt, fluence term n, E curl update (with CPML psi),
- * E soft source at (n+1) dt.  Returns 0 on success. */
-int or_step(const or_grid *g, const or_antenna *ant, or_state *s, long n0, int nsteps)
+ * E soft source at (n+1) dt, wall source at (n+1) dt.  Returns 0 on success. */
+static int or_step_all(const or_grid *g, const or_antenna *ant, const or_wall *wall, or_state *s, long n0,
+                       int nsteps)
 {
     long ncell = (long)g->nx * g->ny * g->nz;
     double *hold[3] = {NULL, NULL, NULL};
@@ -523,25 +612,38 @@ int or_step(const or_grid *g, const or_antenna *ant, or_state *s, long n0, int n
         }
         update_e(g, s);
         if (ant) add_source(ant, s, 0, (n + 1.0) * g->dt);
+        if (wall) add_wall(g, wall, s, (n + 1.0) * g->dt);
     }
     for (int c = 0; c < 3; ++c) free(hold[c]);
     return 0;
 }
 
+int or_step(const or_grid *g, const or_antenna *ant, or_state *s, long n0, int nsteps)
+{
+    return or_step_all(g, ant, NULL, s, n0, nsteps);
+}
+
 /* Convenience for callers that only hold flat arrays: build the antenna,
  * run, free.  src may be NULL (source-free run). */
-int or_run(const or_grid *g, const or_source *src, or_state *s, long n0, int nsteps)
+int or_run_wall(const or_grid *g, const or_source *src, const or_wall *wall, or_state *s, long n0, int nsteps)
 {
     or_antenna ant;
     int rc;
+    if (wall && (wall->plane < 0 || wall->plane >= g->nz)) return -1;
+    if (wall && g->zbc == OR_Z_WALLS && wall->plane == 0) return -1;   /* the z = 0 PEC wall */
     if (src) {
         if (or_antenna_build(g, src, &ant) != 0) { or_antenna_free(&ant); return -1; }
-        rc = or_step(g, &ant, s, n0, nsteps);
+        rc = or_step_all(g, &ant, wall, s, n0, nsteps);
         or_antenna_free(&ant);
     } else {
-        rc = or_step(g, NULL, s, n0, nsteps);
+        rc = or_step_all(g, NULL, wall, s, n0, nsteps);
     }
     return rc;
+}
+
+int or_run(const or_grid *g, const or_source *src, or_state *s, long n0, int nsteps)
+{
+    return or_run_wall(g, src, NULL, s, n0, nsteps);
 }
 
 /* Threads of the OpenMP loops (timing of the oracle on the host cores). */
@@ -733,6 +835,7 @@ int or_adjoint_step(const or_grid *g, const or_source *src, or_state *adj, long 
 {
     or_antenna ant;
     int have = src != NULL;
+    if (g->zbc != OR_Z_PERIODIC) return -1;   /* the adjoint covers z-periodic grids only */
     if (have && or_antenna_build(g, src, &ant) != 0) { or_antenna_free(&ant); return -1; }
     /* PEC: E^{n+1} on the walls is forced to zero, so nothing flows back from it */
     for (long k = 0; k < g->nz; ++k)

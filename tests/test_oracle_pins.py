@@ -437,3 +437,76 @@ def test_axial_potential_gives_azimuthal_te_and_radial_tm(theta_deg):
         ratio = abs(e_tm[:2] @ er) / abs(e_tm[2])
         want = abs(beta * special.jv(1, K * r)) / abs(K * special.jv(0, K * r))
         assert ratio == pytest.approx(want, rel=1e-9)
+
+
+# ------------------------------------------- z walls and the wall source
+
+def test_discrete_energy_conserved_with_z_walls():
+    """The same invariant as above with PEC walls at z = 0 and z = nz dz
+    instead of periodic z: tangential E (E_x, E_y) vanishes on the k = 0 wall
+    and fields past the last plane read as the wall."""
+    g = oracle.Grid(10, 9, 8, 0, 0.1, 0.13, 0.07, courant=0.9, z_walls=True)
+    st = _random_pec_state(g, seed=5)
+    st.e[0][0, :, :] = 0; st.e[1][0, :, :] = 0
+    dV = g.dx * g.dy * g.dz
+    Ws = []
+    for n in range(400):
+        e_prev = [a.copy() for a in st.e]
+        h_prev = [a.copy() for a in st.h]
+        oracle.run(g, None, st, 1)
+        Ws.append(0.5 * dV * sum(np.sum(e_prev[c] ** 2) + np.sum(h_prev[c] * st.h[c]) for c in range(3)))
+    Ws = np.array(Ws)
+    assert np.max(np.abs(Ws - Ws[0])) / abs(Ws[0]) < 1e-13
+    assert np.all(st.e[0][0] == 0) and np.all(st.e[1][0] == 0)
+
+
+def test_wall_source_radiates_symmetrically_about_its_plane():
+    """A soft E_x sheet on an E plane radiates the same field to both sides:
+    under z -> 2 z_s - z the Yee scheme maps E_x, E_y and H_z to themselves
+    and E_z, H_x, H_y to minus themselves, so before any wave reaches the
+    z walls (the numerical domain of dependence grows one cell per step)
+    E_x(k_s + d) = E_x(k_s - d) and H_y(k_s + d - 1/2) = -H_y(k_s - d - 1/2)."""
+    g = oracle.Grid(24, 22, 40, 4, 1 / 16, 1 / 16, 1 / 16, courant=0.95, z_walls=True, npml_z=4)
+    ks = 20
+    wall = oracle.Wall(theta=np.deg2rad(25.0), w0=0.4, envelope="cw", ramp=1.0, plane=ks)
+    st = oracle.State(g, fluence=False)
+    oracle.run(g, None, st, 14, wall=wall)
+    Ex, Ey, Hy = st.e[0], st.e[1], st.h[1]
+    assert np.abs(Ex[ks]).max() > 0
+    for d in range(1, 14):
+        np.testing.assert_allclose(Ex[ks + d], Ex[ks - d], rtol=0, atol=1e-13 * np.abs(Ex).max())
+        np.testing.assert_allclose(Ey[ks + d], Ey[ks - d], rtol=0, atol=1e-13 * np.abs(Ex).max())
+        np.testing.assert_allclose(Hy[ks + d - 1], -Hy[ks - d], rtol=0, atol=1e-13 * np.abs(Hy).max())
+
+
+def _z_blob_run(nz_in, npml_z, steps, n_xy=40, npml=8):
+    dx = 1.0 / 16
+    nz = nz_in + 2 * npml_z
+    g = oracle.Grid(n_xy, n_xy, nz, npml, dx, dx, dx, courant=0.95, z_walls=True, npml_z=npml_z)
+    st = oracle.State(g, fluence=False)
+    c = n_xy / 2
+    x = (np.arange(n_xy) + 0.5 - c)[None, None, :]
+    y = (np.arange(n_xy) + 0.5 - c)[None, :, None]
+    z = (np.arange(nz) - nz / 2)[:, None, None]
+    st.h[2][...] = np.exp(-(x * x + y * y + z * z) / (2 * 3.0 ** 2))
+    trace = []
+    for _ in range(steps):
+        oracle.run(g, None, st, 1)
+        lo = nz // 2 - nz_in // 2
+        trace.append(st.e[1][lo:lo + nz_in].copy())
+    return np.array(trace)
+
+
+def test_z_cpml_reflection():
+    """The CPML on the z faces: a 3-D pulse in a box with 8-cell z layers
+    matches the same pulse in a box whose z walls are too far to reflect
+    within the run (both boxes share the same x/y size and x/y CPML, so
+    only the z faces differ), to 1e-3 of the peak."""
+    nz_in, steps = 24, 70
+    tr_s = _z_blob_run(nz_in, 8, steps)
+    tr_b = _z_blob_run(nz_in + 2 * 70, 0, steps)
+    off = (tr_b.shape[1] - nz_in) // 2
+    tr_b = tr_b[:, off:off + nz_in]
+    diff = np.abs(tr_s - tr_b).max()
+    ref = np.abs(tr_b).max()
+    assert diff / ref < 1e-3, diff / ref
