@@ -90,7 +90,19 @@ typedef struct {
     double pml_alpha_max;    /* alpha = alpha_max (1 - u)                          */
     int precision;           /* fdtd_precision of the field arithmetic             */
     int fluence;             /* 1: accumulate the fluence (FP64 accumulator)       */
+    int z_boundary;          /* FDTD_Z_PERIODIC (the antenna boxes of Section 4) or
+                                FDTD_Z_WALLS (the Bessel-Gauss box of Section 2)   */
+    int npml_z;              /* FDTD_Z_WALLS: CPML cells inside each z wall (same
+                                constants as x/y; 2*npml_z + 2 <= nz); else 0      */
 } fdtd_grid_desc;
+
+/* z boundary.  FDTD_Z_WALLS puts PEC walls at z = 0 and z = nz dz (tangential
+ * E_x, E_y zero on the plane k = 0; fields past the last plane read as the
+ * wall) with npml_z CPML cells inside each, and needs nz <= 65535.  A
+ * z-walled grid runs on tile variant 5 and the cell batch engine only
+ * (EINVAL elsewhere), takes no antenna (the antenna boxes are z-periodic,
+ * Section 4) and has no adjoint (EINVAL). */
+enum { FDTD_Z_PERIODIC = 0, FDTD_Z_WALLS = 1 };
 
 /* Bessel-antenna descriptor (Section 4, Fig. 3, Eq. 12-13).  The antenna is
  * every Yee point of each component whose distance r from the beam axis, in
@@ -119,6 +131,27 @@ typedef struct {
     const double* w_phase;   /* host, nx*ny, or NULL                               */
 } fdtd_annulus_desc;
 
+/* Wall source: the Bessel-Gauss reference beam of Section 2, a Gaussian beam
+ * polarised along x with the axicon phase Phi(r) = -k r sin(theta), injected
+ * as a soft E_x sheet on the E plane k = plane.  After each E update (time
+ * t = (n+1) dt, after the antenna's E terms) every E_x point of that plane
+ * with j >= 1 gets
+ *     f(t) Re{ E0 exp(-r^2 / w0^2) e^{-i k r sin(theta)} e^{-i omega t'} }
+ * with r the distance of the E_x point (i+1/2, j) from the beam axis
+ * (nx/2, ny/2) in wavelengths, and f, t' as in fdtd_annulus_desc.  The sheet
+ * radiates to both sides; put it just inside the low-z CPML of a z-walled
+ * grid.  The column coefficients are evaluated on the host in FP64. */
+typedef struct {
+    double theta;            /* cone angle of the axicon, radians                  */
+    double w0;               /* Gaussian waist, wavelengths (> 0)                  */
+    double E0;               /* amplitude                                          */
+    int envelope;            /* FDTD_ENV_*                                         */
+    double ramp;             /* CW ramp length, periods                            */
+    double T, T0;            /* Gaussian envelope, periods                         */
+    int plane;               /* E plane k of the sheet; 0 <= plane < nz, and not
+                                0 on a z-walled grid (the z = 0 PEC wall)          */
+} fdtd_wall_desc;
+
 typedef struct fdtd_grid fdtd_grid;
 typedef struct fdtd_batch fdtd_batch;
 typedef struct fdtd_adjoint fdtd_adjoint;
@@ -146,11 +179,24 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s);
 /* Remove the source (source-free runs). */
 fdtd_status fdtd_clear_source(fdtd_grid* g);
 
+/* Set (w != NULL) or remove (w == NULL) the wall source of fdtd_wall_desc:
+ * its column coefficients are evaluated on the host in FP64 and uploaded into
+ * the arena.  It adds to the antenna, if any.  Set it before the grid joins
+ * a batch.  EINVAL on a bad descriptor or if the grid's tile variant is not
+ * 5. */
+fdtd_status fdtd_set_wall_source(fdtd_grid* g, const fdtd_wall_desc* w);
+
+/* Host-only: the wall source's complex column coefficients
+ * E0 exp(-r^2/w0^2) e^{-i k r sin(theta)} into out[ny][nx] (re, im
+ * interleaved: 2*nx*ny doubles; the row j = 0 is zero).  Runs no GPU code.
+ * EINVAL on a bad descriptor. */
+fdtd_status fdtd_wall_coefficients(const fdtd_grid_desc* d, const fdtd_wall_desc* w, double* out);
+
 /* Advance nsteps full Yee steps (asynchronous on the grid's stream).  Each
  * step n: H^{n+1/2} (with CPML psi) -> H soft source at (n+1/2) dt ->
  * fluence += |E^n x (H^{n-1/2}+H^{n+1/2})/2| dt at cell centres ->
- * E^{n+1} (with CPML psi) -> E soft source at (n+1) dt (Eq. 13).  One fused
- * kernel launch per step. */
+ * E^{n+1} (with CPML psi) -> E soft source at (n+1) dt (Eq. 13) -> wall
+ * source at (n+1) dt.  One or two kernel launches per step (tile variant). */
 fdtd_status fdtd_step(fdtd_grid* g, int nsteps);
 
 /* Copy the fluence (nz*ny*nx doubles, x fastest, dense) to dst (device if
@@ -188,8 +234,11 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
  *   3  two passes (H, then E with the fluence term), plain loads;
  *   4  two passes, a TMA-staged H pass with the fluence term, then E;
  *   5  two cell-parallel passes, one thread per cell (lz unused; needs
- *      nz <= 65535, else EINVAL).
- * The TMA variants (1, 2, 4) have no FP64 32x16 tile (EINVAL).
+ *      nz <= 65535, else EINVAL);
+ *   6  one cell-parallel pass, the neighbouring H recomputed per cell.
+ * The TMA variants (1, 2, 4) have no FP64 32x16 tile (EINVAL).  A z-walled
+ * grid or one with a wall source takes variant 5 only (EINVAL otherwise;
+ * fdtd_autotune then times the ty of variant 5 only).
  * fdtd_create_grid picks a default (variant 5, ty 4); fdtd_autotune times
  * the candidates on this grid (running `steps` steps for each, then
  * restoring the state) and keeps the fastest.  Results agree to rounding
@@ -233,7 +282,9 @@ void fdtd_destroy_grid(fdtd_grid* g);
  *     tile variant 5, bit for bit); needs nz <= 65535 on every grid.
  *   FDTD_BATCH_PERSISTENT: one persistent kernel launch per step walks every
  *     grid's (tile, z segment) blocks with the TMA-staged one-pass step (the
- *     arithmetic of tile variant 1, bit for bit).
+ *     arithmetic of tile variant 1, bit for bit); z-periodic grids without a
+ *     wall source only (EINVAL otherwise, and EINVAL for a batch that mixes
+ *     such grids with grids of nz > 65535).
  * `dev_table` is a device buffer of fdtd_batch_required_bytes bytes
  * (256-byte aligned), owned by the caller and alive until
  * fdtd_batch_destroy; `stream` is a cudaStream_t.  A grid in a batch must
@@ -260,6 +311,8 @@ void fdtd_batch_destroy(fdtd_batch* b);
  * applies the exact transpose of the discrete step (CPML and PEC included)
  * backwards in time.  The paper computes no gradients: this is the transpose
  * of the method's discrete update.
+ *
+ * Grids with z walls or a wall source have no adjoint (EINVAL).
  *
  * The adjoint holds its own state (adjoints of E, H and of the CPML psi, two
  * copies each) and a per-(component, column) accumulator in a caller-owned

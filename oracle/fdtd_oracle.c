@@ -631,6 +631,7 @@ int or_run_wall(const or_grid *g, const or_source *src, const or_wall *wall, or_
     int rc;
     if (wall && (wall->plane < 0 || wall->plane >= g->nz)) return -1;
     if (wall && g->zbc == OR_Z_WALLS && wall->plane == 0) return -1;   /* the z = 0 PEC wall */
+    if (src && g->zbc == OR_Z_WALLS) return -1;   /* the antenna boxes are z-periodic (Section 4) */
     if (src) {
         if (or_antenna_build(g, src, &ant) != 0) { or_antenna_free(&ant); return -1; }
         rc = or_step_all(g, &ant, wall, s, n0, nsteps);

@@ -470,6 +470,7 @@ fdtd_status fdtd_adjoint_create(fdtd_grid* g, int component, const int64_t* prob
     if (!g || !arena || component < 0 || component > 2 || n_probes < 0 || (n_probes > 0 && !probe_cells))
         return fail(FDTD_EINVAL, "invalid adjoint arguments");
     if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return fail(FDTD_EINVAL, "arena not 256-byte aligned");
+    if (needs_cell_passes(g)) return fail(FDTD_EINVAL, "no adjoint for grids with z walls or a wall source");
     if (!g->has_source) return fail(FDTD_ESTATE, "set the antenna source before creating its adjoint");
     fdtd_adjoint* a = new (std::nothrow) fdtd_adjoint();
     if (!a) return fail(FDTD_ENOMEM, "host allocation failed");

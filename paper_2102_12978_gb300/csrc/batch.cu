@@ -194,7 +194,7 @@ fdtd_status cell_upload_times(fdtd_batch* b, int count)
     for (int s = 0; s < count; ++s)
         for (int q = 0; q < n; ++q) {
             const fdtd_grid* g = b->grids[q];
-            h[size_t(s) * n + q] = step_time<real>(g->srct, g->dt, g->step + s);
+            h[size_t(s) * n + q] = step_time<real>(g->srct, g->has_wall ? &g->wallt : nullptr, g->dt, g->step + s);
         }
     return cuda_check(cudaMemcpyAsync(static_cast<char*>(b->table) + b->times_off, h, b->host_times.size(),
                                       cudaMemcpyHostToDevice, b->stream),
@@ -361,8 +361,16 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->engine = FDTD_BATCH_CELL;
     b->times_off = times_offset(n, prec);
     for (int e = 0; e < 2; ++e) b->built[e][0] = b->built[e][1] = false;
-    for (int q = 0; q < n; ++q)
-        if (grids[q]->desc.nz > 65535) b->engine = FDTD_BATCH_PERSISTENT;   // cell grids take nz <= 65535
+    bool need_cell = false, need_persistent = false;
+    for (int q = 0; q < n; ++q) {
+        need_persistent |= grids[q]->desc.nz > 65535;   // cell grids take nz <= 65535
+        need_cell |= needs_cell_passes(grids[q]);        // z walls / wall source: cell passes only
+    }
+    if (need_cell && need_persistent) {
+        delete b;
+        return fail(FDTD_EINVAL, "a batch cannot mix grids with nz > 65535 and grids with z walls or a wall source");
+    }
+    if (need_persistent) b->engine = FDTD_BATCH_PERSISTENT;
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
     st = cuda_check(cudaStreamSynchronize(b->stream), "batch create");
@@ -391,6 +399,10 @@ fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine)
     if (engine == FDTD_BATCH_CELL)
         for (fdtd_grid* g : b->grids)
             if (g->desc.nz > 65535) return fail(FDTD_EINVAL, "the cell engine takes nz <= 65535");
+    if (engine == FDTD_BATCH_PERSISTENT)
+        for (fdtd_grid* g : b->grids)
+            if (needs_cell_passes(g))
+                return fail(FDTD_EINVAL, "the persistent engine takes z-periodic grids without a wall source");
     if (engine == FDTD_BATCH_PERSISTENT && b->engine != engine) {
         // the persistent kernel takes the source phase of grid g at step
         // step0_g + counter: bring the device counter to the batch's step

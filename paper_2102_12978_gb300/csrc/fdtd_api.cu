@@ -67,11 +67,20 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
         L.pex[c] = take(L.psx_elems * b);
         L.pey[c] = take(L.psy_elems * b);
     }
+    const size_t w2z = d.z_boundary == FDTD_Z_WALLS ? 2 * size_t(d.npml_z) : 0;
+    L.psz_elems = w2z * ny * p;
+    for (int buf = 0; buf < 2; ++buf)
+        for (int c = 0; c < 2; ++c) L.phz[buf][c] = take(L.psz_elems * b);
+    for (int c = 0; c < 2; ++c) L.pez[c] = take(L.psz_elems * b);
     L.fluence = d.fluence ? take(nz * ny * p * 8) : 0;
     L.dynamic_bytes = off;
     L.chx = take(nx * b); L.cex = take(nx * b);
     L.chy = take(ny * b); L.cey = take(ny * b);
+    L.chz = take(nz * b); L.cez = take(nz * b);
     for (int q = 0; q < 8; ++q) L.prof[q] = take((w2 ? w2 : 1) * b);
+    for (int q = 8; q < 12; ++q) L.prof[q] = take((w2z ? w2z : 1) * b);
+    L.wcoef = take(nx * ny * 16);
+    L.wcoef32 = take(nx * ny * 8);
     L.smask = take(nx * ny);
     L.scoef = take(6 * nx * ny * 16);
     L.scoef32 = take(6 * nx * ny * 8);
@@ -107,8 +116,17 @@ fdtd_status validate(const fdtd_grid_desc* d)
     } else if (!(d->dt > 0.0) || d->dt > lim) {
         return fail(FDTD_EINVAL, "dt=%g outside (0, %g] (Yee stability limit)", d->dt, lim);
     }
-    if (d->npml > 0 && !(d->pml_order >= 0.0 && d->pml_sigma_scale >= 0.0 && d->pml_kappa_max >= 1.0 &&
-                         d->pml_alpha_max >= 0.0))
+    if (d->z_boundary != FDTD_Z_PERIODIC && d->z_boundary != FDTD_Z_WALLS)
+        return fail(FDTD_EINVAL, "z_boundary=%d is neither FDTD_Z_PERIODIC nor FDTD_Z_WALLS", d->z_boundary);
+    if (d->z_boundary == FDTD_Z_PERIODIC && d->npml_z != 0)
+        return fail(FDTD_EINVAL, "npml_z=%d on a z-periodic grid", d->npml_z);
+    if (d->z_boundary == FDTD_Z_WALLS) {
+        if (d->npml_z < 0 || 2 * d->npml_z + 2 > d->nz)
+            return fail(FDTD_EINVAL, "npml_z=%d must be >= 0 with 2*npml_z + 2 <= nz=%d", d->npml_z, d->nz);
+        if (d->nz > 65535) return fail(FDTD_EINVAL, "a z-walled grid takes nz <= 65535");
+    }
+    if ((d->npml > 0 || d->npml_z > 0) &&
+        !(d->pml_order >= 0.0 && d->pml_sigma_scale >= 0.0 && d->pml_kappa_max >= 1.0 && d->pml_alpha_max >= 0.0))
         return fail(FDTD_EINVAL, "invalid CPML constants");
     return FDTD_OK;
 }
@@ -122,16 +140,16 @@ double grid_dt(const fdtd_grid_desc& d)
 // CPML grading along one axis (Roden-Gedney CFS-PML; constants documented in
 // fdtd_grid_desc).  For a position `pos` (cells from the low face) returns
 // b, a and kappa of the auxiliary recursion psi <- b psi + a d(field)/d(axis).
-static void cpml_at(const fdtd_grid_desc& d, int n, double cell, double dt, double pos_cells,
+static void cpml_at(const fdtd_grid_desc& d, int n, int npml, double cell, double dt, double pos_cells,
                     double& b, double& a, double& kappa)
 {
     b = 1.0; a = 0.0; kappa = 1.0;
-    if (d.npml <= 0) return;
+    if (npml <= 0) return;
     double depth_cells = 0.0;
-    if (pos_cells < d.npml) depth_cells = d.npml - pos_cells;
-    else if (pos_cells > n - d.npml) depth_cells = pos_cells - (n - d.npml);
+    if (pos_cells < npml) depth_cells = npml - pos_cells;
+    else if (pos_cells > n - npml) depth_cells = pos_cells - (n - npml);
     if (depth_cells <= 0.0) return;
-    double u = depth_cells / d.npml;
+    double u = depth_cells / npml;
     double grade = std::pow(u, d.pml_order);
     double sigma = d.pml_sigma_scale * (d.pml_order + 1.0) / cell * grade;
     kappa = 1.0 + (d.pml_kappa_max - 1.0) * grade;
@@ -140,23 +158,25 @@ static void cpml_at(const fdtd_grid_desc& d, int n, double cell, double dt, doub
     if (sigma > 0.0) a = sigma * (b - 1.0) / (kappa * (sigma + kappa * alpha));
 }
 
+// Per-position coefficients dt / (kappa d) of one axis (H at i+1/2, E at i)
+// and the CPML b, a' = dt a / d on its 2 npml shell positions.
 template <typename real>
-static void build_axis_tables(const fdtd_grid_desc& d, int n, double cell, double dt,
+static void build_axis_tables(const fdtd_grid_desc& d, int n, int npml, double cell, double dt,
                               std::vector<real>& ch, std::vector<real>& ce,
                               std::vector<real>& bh, std::vector<real>& ah,
                               std::vector<real>& be, std::vector<real>& ae)
 {
-    const int w2 = 2 * d.npml;
+    const int w2 = 2 * npml;
     ch.assign(n, real(0)); ce.assign(n, real(0));
     bh.assign(w2 ? w2 : 1, real(1)); ah.assign(w2 ? w2 : 1, real(0));
     be.assign(w2 ? w2 : 1, real(1)); ae.assign(w2 ? w2 : 1, real(0));
     for (int i = 0; i < n; ++i) {
         double b, a, kap;
-        cpml_at(d, n, cell, dt, i + 0.5, b, a, kap);      // H sits half a cell in
+        cpml_at(d, n, npml, cell, dt, i + 0.5, b, a, kap);      // H sits half a cell in
         ch[i] = real(dt / (kap * cell));
-        int sh = (i < d.npml) ? i : (i >= n - d.npml ? i - n + w2 : -1);
+        int sh = (i < npml) ? i : (i >= n - npml ? i - n + w2 : -1);
         if (sh >= 0) { bh[sh] = real(b); ah[sh] = real(dt * a / cell); }
-        cpml_at(d, n, cell, dt, double(i), b, a, kap);    // E on the integer position
+        cpml_at(d, n, npml, cell, dt, double(i), b, a, kap);    // E on the integer position
         ce[i] = real(dt / (kap * cell));
         if (sh >= 0) { be[sh] = real(b); ae[sh] = real(dt * a / cell); }
     }
@@ -165,9 +185,12 @@ static void build_axis_tables(const fdtd_grid_desc& d, int n, double cell, doubl
 template <typename real>
 static fdtd_status upload_tables(fdtd_grid* g)
 {
-    std::vector<real> chx, cex, bhx, ahx, bex, aex, chy, cey, bhy, ahy, bey, aey;
-    build_axis_tables<real>(g->desc, g->desc.nx, g->desc.dx, g->dt, chx, cex, bhx, ahx, bex, aex);
-    build_axis_tables<real>(g->desc, g->desc.ny, g->desc.dy, g->dt, chy, cey, bhy, ahy, bey, aey);
+    std::vector<real> chx, cex, bhx, ahx, bex, aex, chy, cey, bhy, ahy, bey, aey, chz, cez, bhz, ahz, bez, aez;
+    const fdtd_grid_desc& d = g->desc;
+    build_axis_tables<real>(d, d.nx, d.npml, d.dx, g->dt, chx, cex, bhx, ahx, bex, aex);
+    build_axis_tables<real>(d, d.ny, d.npml, d.dy, g->dt, chy, cey, bhy, ahy, bey, aey);
+    const int npz = d.z_boundary == FDTD_Z_WALLS ? d.npml_z : 0;
+    build_axis_tables<real>(d, d.nz, npz, d.dz, g->dt, chz, cez, bhz, ahz, bez, aez);
     char* A = static_cast<char*>(g->arena);
     cudaStream_t s = g->stream;
     const Layout& L = g->L;
@@ -175,6 +198,8 @@ static fdtd_status upload_tables(fdtd_grid* g)
         {L.chx, &chx}, {L.cex, &cex}, {L.chy, &chy}, {L.cey, &cey},
         {L.prof[0], &bhx}, {L.prof[1], &ahx}, {L.prof[2], &bex}, {L.prof[3], &aex},
         {L.prof[4], &bhy}, {L.prof[5], &ahy}, {L.prof[6], &bey}, {L.prof[7], &aey},
+        {L.chz, &chz}, {L.cez, &cez},
+        {L.prof[8], &bhz}, {L.prof[9], &ahz}, {L.prof[10], &bez}, {L.prof[11], &aez},
     };
     for (auto& it : items) {
         fdtd_status st = cuda_check(cudaMemcpyAsync(A + it.off, it.v->data(), it.v->size() * sizeof(real),
@@ -228,6 +253,22 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
     a.zphr = sizeof(real) == 8 ? static_cast<const void*>(A + L.zph) : static_cast<const void*>(A + L.zph32);
     a.st = g->srct;
     a.fault = g->fault;
+    a.zw = g->desc.z_boundary == FDTD_Z_WALLS;
+    a.npz = a.zw ? g->desc.npml_z : 0;
+    for (int c = 0; c < 2; ++c) {
+        a.phz_in[c] = reinterpret_cast<const real*>(A + L.phz[cur][c]);
+        a.phz_out[c] = reinterpret_cast<real*>(A + L.phz[nxt][c]);
+        a.pez[c] = reinterpret_cast<real*>(A + L.pez[c]);
+    }
+    a.chz = reinterpret_cast<const real*>(A + L.chz);
+    a.cez = reinterpret_cast<const real*>(A + L.cez);
+    a.bhz = reinterpret_cast<const real*>(A + L.prof[8]);
+    a.ahz = reinterpret_cast<const real*>(A + L.prof[9]);
+    a.bez = reinterpret_cast<const real*>(A + L.prof[10]);
+    a.aez = reinterpret_cast<const real*>(A + L.prof[11]);
+    a.wcoefr = !g->has_wall ? nullptr
+               : sizeof(real) == 8 ? static_cast<const void*>(A + L.wcoef) : static_cast<const void*>(A + L.wcoef32);
+    a.wplane = g->has_wall ? g->wall.plane : -1;
     return a;
 }
 
@@ -279,6 +320,7 @@ static cudaError_t launch_tma(const fdtd_grid* cg, int cur, long long n, int lz,
 cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
                         cudaEvent_t mid)
 {
+    if (tc.variant != 5 && needs_cell_passes(g)) return cudaErrorInvalidValue;   // z walls / wall source
     if (tc.variant >= 3) return launch_split(g, cur, n, tc, s, mid);   // variants 3-6
     if (tc.variant == 1) {
         if (g->desc.precision == FDTD_F32) {
@@ -398,6 +440,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->has_source = false;
     std::memset(&g->srct, 0, sizeof(g->srct));
     g->srct.dt = g->dt;
+    g->has_wall = false;
+    std::memset(&g->wall, 0, sizeof(g->wall));
+    std::memset(&g->wallt, 0, sizeof(g->wallt));
+    g->fault = 0;
     for (int c = 0; c < 6; ++c) g->counts[c] = 0;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -416,6 +462,8 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
 // Checks of an annulus descriptor against its grid (EINVAL with a message).
 static fdtd_status validate_source(const fdtd_grid_desc& d, const fdtd_annulus_desc* s)
 {
+    if (d.z_boundary != FDTD_Z_PERIODIC)
+        return fail(FDTD_EINVAL, "the antenna takes z-periodic grids (Section 4); this grid has z walls");
     if (s->pol < FDTD_POL_Y || s->pol > FDTD_POL_Z || (s->mode != FDTD_TE && s->mode != FDTD_TM) ||
         (s->envelope != FDTD_ENV_CW_SIN2 && s->envelope != FDTD_ENV_GAUSS) ||
         (s->inject != FDTD_INJECT_ALL && s->inject != FDTD_INJECT_TANGENTIAL))
@@ -512,6 +560,86 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     g->srct.T0 = s->T0;
     g->srct.dt = g->dt;
     for (int c = 0; c < 6; ++c) g->counts[c] = counts[c];
+    return FDTD_OK;
+}
+
+// Checks of a wall-source descriptor against its grid (EINVAL with a message).
+static fdtd_status validate_wall(const fdtd_grid_desc& d, const fdtd_wall_desc* w)
+{
+    if (w->envelope != FDTD_ENV_CW_SIN2 && w->envelope != FDTD_ENV_GAUSS)
+        return fail(FDTD_EINVAL, "invalid envelope %d in wall descriptor", w->envelope);
+    if (!(w->w0 > 0.0) || !std::isfinite(w->w0)) return fail(FDTD_EINVAL, "wall waist w0=%g must be > 0", w->w0);
+    if (!std::isfinite(w->theta) || !std::isfinite(w->E0)) return fail(FDTD_EINVAL, "wall theta / E0 not finite");
+    if (w->plane < 0 || w->plane >= d.nz) return fail(FDTD_EINVAL, "wall plane %d outside [0, %d)", w->plane, d.nz);
+    if (d.z_boundary == FDTD_Z_WALLS && w->plane == 0)
+        return fail(FDTD_EINVAL, "wall plane 0 is the z = 0 PEC wall");
+    if (w->envelope == FDTD_ENV_GAUSS && !(w->T > 0.0)) return fail(FDTD_EINVAL, "Gaussian T must be > 0");
+    if (w->envelope == FDTD_ENV_CW_SIN2 && w->ramp < 0.0) return fail(FDTD_EINVAL, "ramp must be >= 0");
+    return FDTD_OK;
+}
+
+// Column coefficients of the wall source (Section 2: Gaussian waist times the
+// axicon phase -k r sin(theta), k = 2 pi) at the E_x points (i+1/2, j) of a
+// plane, FP64; the row j = 0 lies on the y = 0 PEC wall and stays zero.
+static void wall_tables(const fdtd_grid_desc& d, const fdtd_wall_desc* w, std::vector<std::complex<double>>& W)
+{
+    W.assign(size_t(d.nx) * d.ny, std::complex<double>(0.0, 0.0));
+    const double kr = 2.0 * M_PI * std::sin(w->theta);
+    const double xc = 0.5 * d.nx * d.dx, yc = 0.5 * d.ny * d.dy;
+    for (int j = 1; j < d.ny; ++j)
+        for (int i = 0; i < d.nx; ++i) {
+            const double x = (i + 0.5) * d.dx - xc, y = j * d.dy - yc;
+            const double r = std::sqrt(x * x + y * y);
+            W[size_t(j) * d.nx + i] = std::polar(w->E0 * std::exp(-(r * r) / (w->w0 * w->w0)), -kr * r);
+        }
+}
+
+fdtd_status fdtd_set_wall_source(fdtd_grid* g, const fdtd_wall_desc* w)
+{
+    if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (!w) {
+        g->has_wall = false;
+        return FDTD_OK;
+    }
+    fdtd_status st = validate_wall(g->desc, w);
+    if (st != FDTD_OK) return st;
+    if (g->tile.variant != 5)
+        return fail(FDTD_EINVAL, "the wall source runs on tile variant 5 (this grid: %d)", g->tile.variant);
+    std::vector<std::complex<double>> W;
+    wall_tables(g->desc, w, W);
+    std::vector<float> W32(2 * W.size());
+    for (size_t q = 0; q < W.size(); ++q) {
+        W32[2 * q] = float(W[q].real());
+        W32[2 * q + 1] = float(W[q].imag());
+    }
+    char* A = static_cast<char*>(g->arena);
+    st = cuda_check(cudaMemcpyAsync(A + g->L.wcoef, W.data(), W.size() * 16, cudaMemcpyHostToDevice, g->stream),
+                    "upload wall source");
+    if (st == FDTD_OK)
+        st = cuda_check(cudaMemcpyAsync(A + g->L.wcoef32, W32.data(), W32.size() * 4, cudaMemcpyHostToDevice,
+                                        g->stream), "upload wall source");
+    if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(g->stream), "upload wall source");
+    if (st != FDTD_OK) return st;
+    g->has_wall = true;
+    g->wall = *w;
+    g->wallt.gauss = w->envelope == FDTD_ENV_GAUSS;
+    g->wallt.ramp = w->ramp;
+    g->wallt.T = w->T;
+    g->wallt.T0 = w->T0;
+    g->wallt.dt = g->dt;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_wall_coefficients(const fdtd_grid_desc* d, const fdtd_wall_desc* w, double* out)
+{
+    fdtd_status st = validate(d);
+    if (st != FDTD_OK) return st;
+    if (!w || !out) return fail(FDTD_EINVAL, "null argument");
+    st = validate_wall(*d, w);
+    if (st != FDTD_OK) return st;
+    std::vector<std::complex<double>> W;
+    wall_tables(*d, w, W);
+    std::memcpy(out, W.data(), W.size() * 16);
     return FDTD_OK;
 }
 
@@ -720,6 +848,8 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz)
     if (variant < 0 || variant > 6) return fail(FDTD_EINVAL, "variant=%d not in {0, ..., 6}", variant);
     if (ty != 4 && ty != 8 && ty != 16) return fail(FDTD_EINVAL, "ty=%d not in {4, 8, 16}", ty);
     if (variant >= 5 && g->desc.nz > 65535) return fail(FDTD_EINVAL, "variant %d takes nz <= 65535", variant);
+    if (variant != 5 && needs_cell_passes(g))
+        return fail(FDTD_EINVAL, "a grid with z walls or a wall source takes tile variant 5");
     if ((variant == 1 || variant == 2 || variant == 4) && ty == 16 && g->desc.precision == FDTD_F64)
         return fail(FDTD_EINVAL, "the TMA variants have no FP64 32x16 tile");
     if (lz < 1) return fail(FDTD_EINVAL, "lz=%d < 1", lz);
@@ -755,6 +885,7 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
         cands = {{6, 4}, {6, 8}, {6, 16}, {5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {3, 4}, {3, 8}, {2, 8}, {2, 4},
                  {1, 4}, {1, 8}, {0, 4}, {0, 8}};
     if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 6);
+    if (needs_cell_passes(g)) cands = {{5, 4}, {5, 8}, {5, 16}};
     const int nz = g->desc.nz;
     std::vector<int> lzs;
     for (int segs : {1, 2, 3, 4, 6, 8, 12, 16}) {

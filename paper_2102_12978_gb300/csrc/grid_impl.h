@@ -18,10 +18,13 @@ struct Layout {
     size_t field[2][6] = {};
     size_t phx[2][2] = {}, phy[2][2] = {};
     size_t pex[2] = {}, pey[2] = {};
+    size_t psz_elems = 0;                 // z shell psi of z-walled grids: [2 npml_z][ny][pitch]
+    size_t phz[2][2] = {}, pez[2] = {};   // Hxz, Hyz (ping-pong); Exz, Eyz (in place)
     size_t fluence = 0;
     size_t dynamic_bytes = 0;
-    size_t chx = 0, cex = 0, chy = 0, cey = 0;
-    size_t prof[8] = {};   // bhx ahx bex aex bhy ahy bey aey
+    size_t chx = 0, cex = 0, chy = 0, cey = 0, chz = 0, cez = 0;
+    size_t prof[12] = {};  // bhx ahx bex aex bhy ahy bey aey bhz ahz bez aez
+    size_t wcoef = 0, wcoef32 = 0;   // wall-source column coefficients (FP64, FP32)
     size_t smask = 0, scoef = 0, scoef32 = 0, zph = 0, zph32 = 0;
     size_t scoef_unw = 0, wamp = 0, wphase = 0;   // unweighted coefficients and the weights
     size_t flu_out = 0;    // dense FP64 export of the fluence
@@ -69,6 +72,9 @@ struct fdtd_grid {
     fdtd::TmaMaps hmaps[2][3];  // the same for the boxes of yee_hflu_tma
     bool hmaps_ok[2][3];
     int fault;                  // fdtd_debug_inject_fault: applies to the next step only
+    bool has_wall;              // fdtd_set_wall_source
+    fdtd_wall_desc wall;
+    fdtd::SrcTime wallt;        // time envelope of the wall source
 };
 
 namespace fdtd {
@@ -78,6 +84,12 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur);
 // kernels of a two-pass variant (ignored by the one-pass variants).
 cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,
                         cudaEvent_t mid = nullptr);
+// True if the grid needs the cell passes of tile variant 5 (z walls or a
+// wall source: the other variants implement z-periodic grids only).
+inline bool needs_cell_passes(const fdtd_grid* g)
+{
+    return g->desc.z_boundary == FDTD_Z_WALLS || g->has_wall;
+}
 // Kernel launches per step of a tile configuration (1 or 2).
 inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 && tc.variant <= 5 ? 2 : 1; }
 // The cell-parallel and two-pass steps on stream s: variant 3 yee_h_pass then

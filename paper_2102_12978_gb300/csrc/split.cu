@@ -103,7 +103,7 @@ template <typename real, int TY>
 static cudaError_t launch_step_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s)
 {
     if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
-    const StepTime<real> t = step_time<real>(g->srct, g->dt, n);
+    const StepTime<real> t = step_time<real>(g->srct, nullptr, g->dt, n);
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
     yee_step_cell<real, TY><<<grid, block, 0, s>>>(make_args<real>(g, cur), t);
@@ -116,7 +116,7 @@ template <typename real, int TY>
 static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s, cudaEvent_t mid)
 {
     if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
-    const StepTime<real> t = step_time<real>(g->srct, g->dt, n);
+    const StepTime<real> t = step_time<real>(g->srct, g->has_wall ? &g->wallt : nullptr, g->dt, n);
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
     const StepArgs<real> a = make_args<real>(g, cur);

@@ -27,16 +27,18 @@
 
 namespace fdtd {
 
-// f e^{-i Phi} at the H time (n + 1/2) dt and the E time (n + 1) dt.
+// f e^{-i Phi} of the antenna at the H time (n + 1/2) dt and the E time
+// (n + 1) dt, and of the wall source at the E time.
 template <typename real>
 struct StepTime {
-    Cpx<real> th, te;
+    Cpx<real> th, te, tw;
 };
 
 // The time factors of step n, evaluated on the host in FP64 and rounded to
 // the field precision (every launch path of the cell kernels uses this).
+// `wall` is the wall source's envelope, or null.
 template <typename real>
-inline StepTime<real> step_time(const SrcTime& st, double dt, long long n)
+inline StepTime<real> step_time(const SrcTime& st, const SrcTime* wall, double dt, long long n)
 {
     StepTime<real> t;
     double c, sn, f;
@@ -44,6 +46,11 @@ inline StepTime<real> step_time(const SrcTime& st, double dt, long long n)
     t.th = Cpx<real>{real(f * c), real(-f * sn)};
     source_time(st, (double(n) + 1.0) * dt, c, sn, f);
     t.te = Cpx<real>{real(f * c), real(-f * sn)};
+    t.tw = Cpx<real>{real(0), real(0)};
+    if (wall) {
+        source_time(*wall, (double(n) + 1.0) * dt, c, sn, f);
+        t.tw = Cpx<real>{real(f * c), real(-f * sn)};
+    }
     return t;
 }
 
@@ -61,6 +68,14 @@ template <typename real, int TY>
 __host__ __device__ __forceinline__ bool cell_gen_e(const StepArgs<real>& a, int i0, int j0)
 {
     return i0 == 0 || j0 == 0 || cell_gen_h<real, TY>(a, i0, j0);
+}
+
+// Planes of a z-walled grid that need the checks: the PEC plane k = 0, the
+// last plane (its +z neighbours are the wall) and the z CPML shell.
+template <typename real>
+__device__ __forceinline__ bool cell_gen_z(const StepArgs<real>& a, int k)
+{
+    return a.zw && (k == 0 || k + 1 == a.nz || k < a.npz || k >= a.nz - a.npz);
 }
 
 template <typename real>
@@ -88,14 +103,16 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     const real* __restrict__ Ey = a.ein[1];
     const real* __restrict__ Ez = a.ein[2];
     const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
+    const bool ztop = GEN && a.zw && k + 1 == nz;   // E past the +z wall reads zero
     const real ex = __ldg(Ex + g), ey = __ldg(Ey + g), ez = __ldg(Ez + g);
-    const real ex1 = __ldg(Ex + gn), ey1 = __ldg(Ey + gn);
+    const real ex1 = ztop ? real(0) : __ldg(Ex + gn), ey1 = ztop ? real(0) : __ldg(Ey + gn);
     const real ezj = yin ? __ldg(Ez + g + pitch) : real(0);
     const real exj = yin ? __ldg(Ex + g + pitch) : real(0);
     const real ezi = xin ? __ldg(Ez + g + 1) : real(0);
     const real eyi = xin ? __ldg(Ey + g + 1) : real(0);
     real hx = __ldg(a.hin[0] + g), hy = __ldg(a.hin[1] + g), hz = __ldg(a.hin[2] + g);
-    const real chx = __ldg(a.chx + i), chy = __ldg(a.chy + j), cz = a.cz;
+    const real chx = __ldg(a.chx + i), chy = __ldg(a.chy + j);
+    const real cz = (GEN && a.zw) ? __ldg(a.chz + k) : a.cz;
     const real dEz_y = ezj - ez, dEy_z = ey1 - ey, dEx_z = ex1 - ex;
     const real dEz_x = ezi - ez, dEy_x = eyi - ey, dEx_y = exj - ex;
     hx = hx - chy * dEz_y + cz * dEy_z;
@@ -124,6 +141,16 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
             a.phy_out[0][q] = p0; a.phy_out[1][q] = p1;
         }
     }
+    if (GEN && a.npz > 0 && (k < a.npz || k >= nz - a.npz)) {
+        const int w2 = 2 * a.npz, kk = k < a.npz ? k : k - nz + w2;
+        const int q = (kk * ny + j) * pitch + i;
+        const real b = a.bhz[kk], aa = a.ahz[kk];
+        const real p0 = b * a.phz_in[0][q] + aa * dEy_z;   // Hxz
+        const real p1 = b * a.phz_in[1][q] + aa * dEx_z;   // Hyz
+        hx += p0;
+        hy -= p1;
+        a.phz_out[0][q] = p0; a.phz_out[1][q] = p1;
+    }
     if (a.smask) {
         const int col = j * nx + i;
         const uint8_t mk = __ldg(a.smask + col) & 0x38;
@@ -138,7 +165,7 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
 }
 
 template <typename real, bool GEN>
-__device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, int i, int j, int k)
+__device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cpx<real> tw, int i, int j, int k)
 {
     using Acc = FluAcc<real>;
     using acc_t = typename Acc::T;
@@ -150,14 +177,16 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, in
     const real* __restrict__ Hy = a.hout[1];
     const real* __restrict__ Hz = a.hout[2];
     const bool xlo = !GEN || i > 0, ylo = !GEN || j > 0;
+    const bool zbot = GEN && a.zw && k == 0;   // H below the z = 0 wall reads zero
     const real hx = __ldg(Hx + g), hy = __ldg(Hy + g), hz = __ldg(Hz + g);
-    const real hxm = __ldg(Hx + gm), hym = __ldg(Hy + gm);
+    const real hxm = zbot ? real(0) : __ldg(Hx + gm), hym = zbot ? real(0) : __ldg(Hy + gm);
     const real hyi = xlo ? __ldg(Hy + g - 1) : real(0);
     const real hzi = xlo ? __ldg(Hz + g - 1) : real(0);
     const real hxj = ylo ? __ldg(Hx + g - pitch) : real(0);
     const real hzj = ylo ? __ldg(Hz + g - pitch) : real(0);
     const real ex = __ldg(a.ein[0] + g), ey = __ldg(a.ein[1] + g), ez = __ldg(a.ein[2] + g);
-    const real cex = __ldg(a.cex + i), cey = __ldg(a.cey + j), cz = a.cz;
+    const real cex = __ldg(a.cex + i), cey = __ldg(a.cey + j);
+    const real cz = (GEN && a.zw) ? __ldg(a.cez + k) : a.cz;
     const real dHz_y = hz - hzj, dHy_z = hy - hym, dHx_z = hx - hxm;
     const real dHz_x = hz - hzi, dHy_x = hy - hyi, dHx_y = hx - hxj;
     real nex = ex + cey * dHz_y - cz * dHy_z;
@@ -186,6 +215,16 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, in
             nez -= p1;
         }
     }
+    if (GEN && a.npz > 0 && (k < a.npz || k >= nz - a.npz)) {
+        const int w2 = 2 * a.npz, kk = k < a.npz ? k : k - nz + w2;
+        const int q = (kk * ny + j) * pitch + i;
+        const real b = a.bez[kk], aa = a.aez[kk];
+        const real p0 = b * a.pez[0][q] + aa * dHy_z;   // Exz
+        const real p1 = b * a.pez[1][q] + aa * dHx_z;   // Eyz
+        a.pez[0][q] = p0; a.pez[1][q] = p1;
+        nex -= p0;
+        ney += p1;
+    }
     if (a.smask) {
         const int col = j * nx + i;
         const uint8_t mk = __ldg(a.smask + col) & 0x07;
@@ -196,9 +235,14 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, in
             if (mk & 0x04) nez += src_add(a, 2, col, u);
         }
     }
+    if (a.wcoefr && k == a.wplane) {   // wall source (Section 2), after the antenna
+        const Cpx<real> w = static_cast<const Cpx<real>*>(a.wcoefr)[j * nx + i];
+        nex += w.x * tw.x - w.y * tw.y;
+    }
     if (GEN) {
         if (j == 0) { nex = real(0); nez = real(0); }   // PEC: tangential E
         if (i == 0) { ney = real(0); nez = real(0); }
+        if (zbot) { nex = real(0); ney = real(0); }
     }
     a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez;
 
@@ -213,18 +257,20 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, in
         const real* __restrict__ Oz = a.hin[2];
         const int gn = (k + 1 == nz) ? g - k * plane : g + plane;
         const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
-        const real ex1 = __ldg(Ex + gn), ey1 = __ldg(Ey + gn);
+        const bool zin = !GEN || !a.zw || k + 1 < nz;   // plane k+1 inside the z walls
+        const real ex1 = zin ? __ldg(Ex + gn) : real(0), ey1 = zin ? __ldg(Ey + gn) : real(0);
         const real exj = yin ? __ldg(Ex + g + pitch) : real(0);
-        const real exj1 = yin ? __ldg(Ex + gn + pitch) : real(0);
+        const real exj1 = (yin && zin) ? __ldg(Ex + gn + pitch) : real(0);
         const real eyi = xin ? __ldg(Ey + g + 1) : real(0);
-        const real eyi1 = xin ? __ldg(Ey + gn + 1) : real(0);
+        const real eyi1 = (xin && zin) ? __ldg(Ey + gn + 1) : real(0);
         const real ezi = xin ? __ldg(Ez + g + 1) : real(0);
         const real ezj = yin ? __ldg(Ez + g + pitch) : real(0);
         const real ezij = (xin && yin) ? __ldg(Ez + g + pitch + 1) : real(0);
         const real hxi = xin ? __ldg(Hx + g + 1) : real(0);
         const real hyj = yin ? __ldg(Hy + g + pitch) : real(0);
-        const real hz1 = __ldg(Hz + gn);
-        const real ox = __ldg(Ox + g), oy = __ldg(Oy + g), oz = __ldg(Oz + g), oz1 = __ldg(Oz + gn);
+        const real hz1 = zin ? __ldg(Hz + gn) : real(0);
+        const real ox = __ldg(Ox + g), oy = __ldg(Oy + g), oz = __ldg(Oz + g);
+        const real oz1 = zin ? __ldg(Oz + gn) : real(0);
         const real oxi = xin ? __ldg(Ox + g + 1) : real(0);
         const real oyj = yin ? __ldg(Oy + g + pitch) : real(0);
         const real cx = (ex + exj) + (ex1 + exj1);
@@ -244,18 +290,22 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, in
 
 // Grid: (ceil(nx/32), ceil(ny/TY), nz) CTAs of 32 x TY threads, one cell each.
 // The H pass takes the blocks in launch order, the E pass in reverse order.
+// Register budgets: the H pass 32 (2048 threads per SM), the E pass 40 (FP32,
+// 1536 threads) or 64 (FP64, 1024 threads); without them the z-wall checks of
+// the general blocks would cost FP64 grids an eighth to a quarter of their
+// resident warps.
 template <typename real, int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, 2048 / (32 * TY))
 yee_h_cell(const StepArgs<real> a, const StepTime<real> t)
 {
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (cell_gen_h<real, TY>(a, i0, j0)) h_cell<real, true>(a, t.th, i, j, k);
+    if (cell_gen_h<real, TY>(a, i0, j0) || cell_gen_z(a, k)) h_cell<real, true>(a, t.th, i, j, k);
     else h_cell<real, false>(a, t.th, i, j, k);
 }
 
 template <typename real, int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, (sizeof(real) == 8 ? 1024 : 1536) / (32 * TY))
 yee_e_cell(const StepArgs<real> a, const StepTime<real> t)
 {
     // the E pass walks the grid backwards: it starts on the planes the H pass
@@ -263,34 +313,34 @@ yee_e_cell(const StepArgs<real> a, const StepTime<real> t)
     const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
     const int k = gridDim.z - 1 - blockIdx.z;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (cell_gen_e<real, TY>(a, i0, j0)) e_cell<real, true>(a, t.te, i, j, k);
-    else e_cell<real, false>(a, t.te, i, j, k);
+    if (cell_gen_e<real, TY>(a, i0, j0) || cell_gen_z(a, k)) e_cell<real, true>(a, t.te, t.tw, i, j, k);
+    else e_cell<real, false>(a, t.te, t.tw, i, j, k);
 }
 
 // The same passes with the step's time factors read from a device table
 // (times[index]): the batched sweep replays a CUDA graph whose steps take
 // their source phase from a table refreshed before each replay.
 template <typename real, int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, 2048 / (32 * TY))
 yee_h_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
 {
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     const Cpx<real> th = times[index].th;
-    if (cell_gen_h<real, TY>(a, i0, j0)) h_cell<real, true>(a, th, i, j, k);
+    if (cell_gen_h<real, TY>(a, i0, j0) || cell_gen_z(a, k)) h_cell<real, true>(a, th, i, j, k);
     else h_cell<real, false>(a, th, i, j, k);
 }
 
 template <typename real, int TY>
-__global__ void __launch_bounds__(32 * TY)
+__global__ void __launch_bounds__(32 * TY, (sizeof(real) == 8 ? 1024 : 1536) / (32 * TY))
 yee_e_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
 {
     const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
     const int k = gridDim.z - 1 - blockIdx.z;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    const Cpx<real> te = times[index].te;
-    if (cell_gen_e<real, TY>(a, i0, j0)) e_cell<real, true>(a, te, i, j, k);
-    else e_cell<real, false>(a, te, i, j, k);
+    const Cpx<real> te = times[index].te, tw = times[index].tw;
+    if (cell_gen_e<real, TY>(a, i0, j0) || cell_gen_z(a, k)) e_cell<real, true>(a, te, tw, i, j, k);
+    else e_cell<real, false>(a, te, tw, i, j, k);
 }
 
 }  // namespace fdtd

@@ -70,6 +70,21 @@ struct StepArgs {
     const void* zphr;        // the same in the field precision (float2 / double2)
     SrcTime st;
     int fault;               // test hook (fdtd_debug_inject_fault): 1 = CTA (0,0,0) withholds one plane's copies
+    // z walls (Section 2's Bessel-Gauss box; the cell passes only): PEC at
+    // z = 0 and z = nz dz, npz CPML cells inside each
+    int zw, npz;
+    const real* phz_in[2];   // z shell H psi: Hxz, Hyz   [2 npz][ny][pitch]
+    real* phz_out[2];
+    real* pez[2];            // z shell E psi: Exz, Eyz (in place)
+    const real* chz;         // dt / (kappa dz) at H z-positions (k+1/2), length nz
+    const real* cez;         // dt / (kappa dz) at E z-positions k
+    const real* bhz;         // CPML b and a' = dt a / dz on the z shell, length 2 npz
+    const real* ahz;
+    const real* bez;
+    const real* aez;
+    // wall source (Section 2): E_x on plane wplane += Re{ W[col] tw }
+    const void* wcoefr;      // [ny][nx] in the field precision, or null
+    int wplane;
 };
 
 // Time factor of the soft source at time t: cos / sin of the phase

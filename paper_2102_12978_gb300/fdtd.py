@@ -40,7 +40,16 @@ class fdtd_grid_desc(C.Structure):
                 ("dt", C.c_double), ("courant", C.c_double),
                 ("pml_order", C.c_double), ("pml_sigma_scale", C.c_double),
                 ("pml_kappa_max", C.c_double), ("pml_alpha_max", C.c_double),
-                ("precision", C.c_int), ("fluence", C.c_int)]
+                ("precision", C.c_int), ("fluence", C.c_int),
+                ("z_boundary", C.c_int), ("npml_z", C.c_int)]
+
+
+FDTD_Z_PERIODIC, FDTD_Z_WALLS = 0, 1
+
+
+class fdtd_wall_desc(C.Structure):
+    _fields_ = [("theta", C.c_double), ("w0", C.c_double), ("E0", C.c_double), ("envelope", C.c_int),
+                ("ramp", C.c_double), ("T", C.c_double), ("T0", C.c_double), ("plane", C.c_int)]
 
 
 class fdtd_annulus_desc(C.Structure):
@@ -58,6 +67,8 @@ _SIGS = {
                                    C.POINTER(C.c_void_p)]),
     "fdtd_set_annulus_source": (C.c_int, [C.c_void_p, C.POINTER(fdtd_annulus_desc)]),
     "fdtd_clear_source": (C.c_int, [C.c_void_p]),
+    "fdtd_set_wall_source": (C.c_int, [C.c_void_p, C.POINTER(fdtd_wall_desc)]),
+    "fdtd_wall_coefficients": (C.c_int, [C.POINTER(fdtd_grid_desc), C.POINTER(fdtd_wall_desc), C.c_void_p]),
     "fdtd_step": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_fluence": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "fdtd_get_field": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
@@ -185,9 +196,11 @@ def fdtd_bessel_j(n: int, x: float) -> float:
 
 
 def make_grid_desc(nx, ny, nz, npml, dx, dy, dz, courant=0.95, precision="f32", fluence=True,
-                   dt=0.0, **pml) -> fdtd_grid_desc:
+                   dt=0.0, z_walls=False, npml_z=0, **pml) -> fdtd_grid_desc:
     d = fdtd_grid_desc_default()
     d.nx, d.ny, d.nz, d.npml = nx, ny, nz, npml
+    d.z_boundary = FDTD_Z_WALLS if z_walls else FDTD_Z_PERIODIC
+    d.npml_z = npml_z
     d.dx, d.dy, d.dz = dx, dy, dz
     d.courant, d.dt = courant, dt
     d.precision = FDTD_F64 if precision in ("f64", "float64", "double") else FDTD_F32
@@ -214,6 +227,21 @@ def make_annulus_desc(m=0, theta=math.radians(20.0), pol="y", mode="TE", E0=1.0,
             keep.append(a)
             setattr(s, name, a.ctypes.data_as(dp))
     return s, keep
+
+
+def make_wall_desc(theta=math.radians(25.0), w0=7.5, E0=1.0, envelope="cw", ramp=10.0, T=0.0, T0=0.0,
+                   plane=1) -> fdtd_wall_desc:
+    w = fdtd_wall_desc()
+    w.theta, w.w0, w.E0, w.envelope = theta, w0, E0, ENV[envelope]
+    w.ramp, w.T, w.T0, w.plane = ramp, T, T0, plane
+    return w
+
+
+def wall_coefficients(d: fdtd_grid_desc, w: fdtd_wall_desc):
+    """Host-only FP64 precompute of the wall source: complex [ny, nx]."""
+    out = np.zeros((d.ny, d.nx, 2))
+    check(lib().fdtd_wall_coefficients(C.byref(d), C.byref(w), out.ctypes.data), "fdtd_wall_coefficients")
+    return out[..., 0] + 1j * out[..., 1]
 
 
 def source_coefficients(d: fdtd_grid_desc, s: fdtd_annulus_desc):
@@ -259,6 +287,14 @@ class Grid:
 
     def clear_source(self):
         check(lib().fdtd_clear_source(C.c_void_p(self.handle)), "fdtd_clear_source")
+
+    def set_wall_source(self, **kw):
+        """The Bessel-Gauss wall sheet (fdtd_set_wall_source); keywords of make_wall_desc."""
+        w = make_wall_desc(**kw)
+        check(lib().fdtd_set_wall_source(C.c_void_p(self.handle), C.byref(w)), "fdtd_set_wall_source")
+
+    def clear_wall_source(self):
+        check(lib().fdtd_set_wall_source(C.c_void_p(self.handle), None), "fdtd_set_wall_source")
 
     def step(self, n: int = 1):
         fdtd_step(self.handle, n)

@@ -146,6 +146,76 @@ def small(name: str = "small", nx: int = 48, ny: int = 40, nz: int = 16, npml: i
                     m, pol, r_center, thickness, steps, **kw)
 
 
+# One optical period at the paper's lambda = 0.8 um, in femtoseconds.
+FS_PER_PERIOD = 0.8e-6 / 299792458.0 * 1e15
+
+
+@dataclass
+class WallWorkload:
+    """One Bessel-Gauss configuration (Section 2): a z-walled box, CPML on
+    all six faces, and the Gaussian-times-axicon E_x sheet on plane `plane`."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    npml: int                # transverse CPML cells
+    npml_z: int              # CPML cells inside each z wall
+    dx: float
+    dz: float
+    theta_deg: float         # axicon cone angle
+    w0: float                # Gaussian waist, wavelengths
+    plane: int               # E plane of the sheet
+    steps: int
+    envelope: str = "gauss"
+    T: float = 0.0           # Gaussian envelope exp(-(t-T0)^2/T^2), periods
+    T0: float = 0.0
+    ramp: float = 0.0        # CW ramp, periods
+    courant: float = 0.95
+    E0: float = 1.0
+
+    @property
+    def theta(self) -> float:
+        return math.radians(self.theta_deg)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def scaled(self, **kw) -> "WallWorkload":
+        return replace(self, **kw)
+
+
+def bessel_gauss() -> WallWorkload:
+    """The Bessel-Gauss box of Section 2: lambda = 0.8 um, theta = 25 deg, an
+    8 lambda_xy x 8 lambda_xy x 32 lambda_z interior (lambda_xy = lambda /
+    sin(theta), lambda_z = lambda / cos(theta); 15 x 15 x 28 um), waist
+    w0 = 6 um, a Gaussian amplitude of 100 fs FWHM (T = FWHM / (2 sqrt(ln 2)))
+    centred at T0 = 2 T, run to t_run = 266 fs.  Mesh (not given for this
+    run): dx = dz = lambda/20, 16 CPML cells on every face, Courant 0.95 of
+    the cubic Yee limit; the sheet sits on the first plane inside the low-z
+    CPML.  Interior 379 x 379 x 706 cells, 411 x 411 x 738 with the CPML."""
+    th, dx, npml = 25.0, 1.0 / 20, 16
+    lam_xy = 1.0 / math.sin(math.radians(th))
+    lam_z = 1.0 / math.cos(math.radians(th))
+    n_in = round(8 * lam_xy / dx)
+    nz_in = round(32 * lam_z / dx)
+    T = (100.0 / FS_PER_PERIOD) / (2.0 * math.sqrt(math.log(2.0)))
+    courant = 0.95
+    dt = courant * dx / math.sqrt(3.0)
+    steps = math.ceil((266.0 / FS_PER_PERIOD) / dt)
+    return WallWorkload("bessel_gauss_411x411x738", n_in + 2 * npml, n_in + 2 * npml, nz_in + 2 * npml,
+                        npml, npml, dx, dx, th, 6.0 / 0.8, npml, steps, envelope="gauss", T=T, T0=2 * T,
+                        courant=courant)
+
+
+def small_wall(name: str = "small_wall", nx: int = 40, ny: int = 36, nz: int = 32, npml: int = 6,
+               npml_z: int = 6, theta_deg: float = 25.0, w0: float = 0.6, plane: int | None = None,
+               steps: int = 60, dx: float = 1.0 / 16, **kw) -> WallWorkload:
+    """A small z-walled case the oracle finishes in about a second."""
+    return WallWorkload(name, nx, ny, nz, npml, npml_z, dx, dx, theta_deg, w0,
+                        npml_z + 1 if plane is None else plane, steps, **kw)
+
+
 def random_state(shape, scale: float = 1.0, seed: int = SEED):
     """Six seeded random field arrays (Ex, Ey, Ez, Hx, Hy, Hz), FP64."""
     g = rng(seed)

@@ -4,7 +4,7 @@ from __future__ import annotations
 import numpy as np
 
 import oracle
-from paper_2102_12978_gb300.workloads import Workload
+from paper_2102_12978_gb300.workloads import WallWorkload, Workload
 
 
 def oracle_grid(w: Workload, npml: int | None = None) -> oracle.Grid:
@@ -25,3 +25,15 @@ def rel_l2(a, b) -> float:
     den = np.linalg.norm(b.ravel())
     num = np.linalg.norm((a - b).ravel())
     return float(num / den) if den > 0 else float(num)
+
+
+def oracle_wall_grid(w: WallWorkload, z_walls: bool = True) -> oracle.Grid:
+    """The recipe's z-walled box with its z CPML, or (z_walls=False) the same
+    box periodic in z."""
+    return oracle.Grid(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant, z_walls=z_walls,
+                       npml_z=w.npml_z if z_walls else 0)
+
+
+def oracle_wall(w: WallWorkload) -> oracle.Wall:
+    return oracle.Wall(theta=w.theta, w0=w.w0, E0=w.E0, envelope=w.envelope, ramp=w.ramp, T=w.T, T0=w.T0,
+                       plane=w.plane)

@@ -95,3 +95,80 @@ def test_host_precompute_matches_oracle_fields(m, pol, mode, inject):
     counts = oracle.antenna_counts(g, src)
     lib_counts = [int(np.count_nonzero(mask & (1 << c))) * w.nz for c in range(6)]
     assert counts == lib_counts
+
+
+def test_invalid_z_boundaries_rejected():
+    kw = dict(nx=32, ny=32, nz=16, npml=6, dx=0.05, dy=0.05, dz=0.05)
+    assert fdtd.fdtd_required_bytes(fdtd.make_grid_desc(**kw, z_walls=True, npml_z=7)) > 0
+    assert fdtd.fdtd_required_bytes(fdtd.make_grid_desc(**kw, z_walls=True, npml_z=0)) > 0
+    for bad in [dict(z_walls=True, npml_z=8), dict(z_walls=True, npml_z=-1), dict(z_walls=False, npml_z=2)]:
+        assert fdtd.fdtd_required_bytes(fdtd.make_grid_desc(**kw, **bad)) == 0, bad
+    d = fdtd.make_grid_desc(**kw)
+    d.z_boundary = 2
+    assert fdtd.fdtd_required_bytes(d) == 0
+    # z walls take nz <= 65535 (the cell passes index planes by grid z)
+    assert fdtd.fdtd_required_bytes(fdtd.make_grid_desc(4, 4, 70000, 0, 0.05, 0.05, 0.05, z_walls=True)) == 0
+    # the z shell adds its psi arrays to the arena
+    a = fdtd.fdtd_required_bytes(fdtd.make_grid_desc(**kw, z_walls=True, npml_z=4))
+    b = fdtd.fdtd_required_bytes(fdtd.make_grid_desc(**kw, z_walls=True, npml_z=0))
+    assert a > b
+
+
+def test_antenna_rejected_on_z_walls():
+    """The antenna boxes are z-periodic (Section 4): both sides refuse an
+    antenna on a z-walled grid."""
+    d = fdtd.make_grid_desc(40, 40, 16, 6, 1 / 16, 1 / 16, 1 / 16, z_walls=True, npml_z=4)
+    s, _ = fdtd.make_annulus_desc(r_center=9.0)
+    with pytest.raises(fdtd.FDTDError) as e:
+        fdtd.source_coefficients(d, s)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    g = oracle.Grid(40, 40, 16, 6, 1 / 16, 1 / 16, 1 / 16, z_walls=True, npml_z=4)
+    with pytest.raises(RuntimeError):
+        oracle.run(g, oracle.Source(r_center=9.0), oracle.State(g), 1)
+
+
+@pytest.mark.parametrize("z_walls", [False, True])
+def test_wall_coefficients_match_oracle_sheet(z_walls):
+    """The library's FP64 wall coefficients W (Section 2: Gaussian waist times
+    the axicon phase) against the oracle's own sheet: one oracle step from
+    zero fields leaves E_x = f Re{W e^{-i Phi}} on the sheet plane.  A
+    Gaussian envelope with T0 = dt gives Phi = 0 (Re W), with T0 = dt - 1/4
+    gives Phi = pi/2 (Im W); f is divided out."""
+    nx, ny, nz, dx = 37, 30, 12, 1 / 16
+    th, w0, E0, plane = np.deg2rad(25.0), 0.7, 1.3, 5
+    d = fdtd.make_grid_desc(nx, ny, nz, 4, dx, dx, dx, z_walls=z_walls, npml_z=2 if z_walls else 0)
+    Wl = fdtd.wall_coefficients(d, fdtd.make_wall_desc(theta=th, w0=w0, E0=E0, envelope="gauss", T=1.0,
+                                                       T0=0.0, plane=plane))
+    assert np.all(Wl[0] == 0)
+    g = oracle.Grid(nx, ny, nz, 4, dx, dx, dx, z_walls=z_walls, npml_z=2 if z_walls else 0)
+    got = []
+    for shift in (0.0, 0.25):
+        T = 50.0
+        wall = oracle.Wall(theta=th, w0=w0, E0=E0, envelope="gauss", T=T, T0=g.dt - shift, plane=plane)
+        st = oracle.State(g, fluence=False)
+        oracle.run(g, None, st, 1, wall=wall)
+        f = math.exp(-(shift / T) ** 2)
+        got.append(st.e[0][plane] / f)
+        assert np.count_nonzero(st.e[0][np.arange(nz) != plane]) == 0
+    ref = got[0] + 1j * got[1]
+    np.testing.assert_allclose(Wl.real, ref.real, rtol=0, atol=1e-14 * E0)
+    np.testing.assert_allclose(Wl.imag, ref.imag, rtol=0, atol=1e-14 * E0)
+    # the waist: |W| = E0 exp(-r^2/w0^2) at the E_x points
+    x = (np.arange(nx) + 0.5 - nx / 2) * dx
+    y = (np.arange(ny) - ny / 2) * dx
+    r2 = x[None, :] ** 2 + y[:, None] ** 2
+    np.testing.assert_allclose(np.abs(Wl[1:]), (E0 * np.exp(-r2 / w0 ** 2))[1:], rtol=1e-14, atol=0)
+
+
+def test_invalid_wall_descriptors_rejected():
+    d = fdtd.make_grid_desc(32, 32, 16, 6, 0.05, 0.05, 0.05, z_walls=True, npml_z=4)
+    out = np.zeros(2 * 32 * 32)
+    for bad in [dict(w0=0.0), dict(plane=16), dict(plane=-1), dict(plane=0), dict(envelope="gauss", T=0.0),
+                dict(ramp=-1.0)]:
+        w = fdtd.make_wall_desc(**{**dict(plane=5), **bad})
+        assert fdtd.lib().fdtd_wall_coefficients(fdtd.C.byref(d), fdtd.C.byref(w), out.ctypes.data) \
+            == fdtd.FDTD_EINVAL, bad
+    # plane 0 is allowed on a z-periodic grid
+    dp = fdtd.make_grid_desc(32, 32, 16, 6, 0.05, 0.05, 0.05)
+    w = fdtd.make_wall_desc(plane=0)
+    assert fdtd.lib().fdtd_wall_coefficients(fdtd.C.byref(dp), fdtd.C.byref(w), out.ctypes.data) == fdtd.FDTD_OK

@@ -1,0 +1,240 @@
+"""The z-walled box and the Bessel-Gauss wall sheet of Section 2 on the GPU.
+
+Parity of the cell passes (tile variant 5, through the C ABI) with the FP64
+oracle, element by element on the same seeded inputs, at the tolerances of
+the antenna runs (relative L2 per field component and for the fluence):
+  FP64 GPU vs oracle  <= 1e-11
+  FP32 GPU vs oracle  <= 1e-4
+plus the batched cell engine on z-walled grids (bit for bit against the
+single-grid step), the refusals of the paths that implement z-periodic grids
+only, and the physics of the paper's Bessel-Gauss box at full size.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2102_12978_gb300 import fdtd
+from paper_2102_12978_gb300 import workloads as W
+from tests.cases import oracle_wall, oracle_wall_grid, rel_l2
+from tests.gpu_cases import gpu_wall_grid, host
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-11, "f32": 1e-4}
+
+
+def _compare(w, precision, tile=None, wall=True, init=None, fluence=True, z_walls=True):
+    og = oracle_wall_grid(w, z_walls=z_walls)
+    st = oracle.State(og, fluence=fluence)
+    g = gpu_wall_grid(w, precision, fluence=fluence, wall=wall, tile=tile, z_walls=z_walls)
+    assert abs(g.dt - og.dt) <= 1e-15 * og.dt
+    if init is not None:
+        for c in range(3):
+            st.e[c][...] = init[c]
+            st.h[c][...] = init[3 + c]
+        for c in range(6):
+            g.set_field(c, init[c])
+    oracle.run(og, None, st, w.steps, wall=oracle_wall(w) if wall else None)
+    g.step(w.steps)
+    g.sync()
+    errs = {}
+    for c, ref in enumerate(st.fields()):
+        got = host(g.field(c))
+        assert np.isfinite(got).all(), "non-finite field values"
+        errs["ExEyEzHxHyHz"[2 * c:2 * c + 2]] = rel_l2(got, ref)
+    if fluence:
+        got = host(g.fluence())
+        assert np.isfinite(got).all(), "non-finite fluence values"
+        errs["fluence"] = rel_l2(got, st.fluence)
+    if z_walls:
+        # tangential E on the z = 0 wall stays exactly zero
+        assert np.all(host(g.field(fdtd.EX))[0] == 0) and np.all(host(g.field(fdtd.EY))[0] == 0)
+    return errs
+
+
+def _assert(errs, precision):
+    bad = {k: v for k, v in errs.items() if not (v <= TOL[precision])}
+    assert not bad, (precision, errs)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+@pytest.mark.parametrize("shape,npml_z", [((40, 36, 32), 6), ((45, 37, 19), 4), ((64, 33, 26), 8),
+                                          ((33, 40, 14), 0)])
+def test_wall_sheet_in_z_walled_box_matches_oracle(precision, shape, npml_z):
+    """CW sheet in a box with PEC z walls and a z CPML of npml_z cells (0: a
+    bare PEC cavity in z), ragged tiles, 80 steps: long enough for the
+    waves to reach both z faces."""
+    nx, ny, nz = shape
+    w = W.small_wall(nx=nx, ny=ny, nz=nz, npml_z=npml_z, steps=80, envelope="cw", ramp=1.0,
+                     plane=max(npml_z + 1, nz // 3))
+    _assert(_compare(w, precision), precision)
+
+
+@pytest.mark.parametrize("ty", [4, 8, 16])
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_wall_tiles_and_gaussian_envelope(ty, precision):
+    """Every ty of tile variant 5 with the Gaussian envelope of Section 2."""
+    w = W.small_wall(nx=72, ny=50, nz=24, npml_z=5, steps=70, envelope="gauss", T=0.8, T0=1.6)
+    _assert(_compare(w, precision, tile=(5, ty, 1)), precision)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_random_state_in_z_walled_box(precision):
+    """Seeded random fields everywhere (every psi of the x, y and z shells
+    and every wall check busy from the first step), no source."""
+    w = W.small_wall(nx=41, ny=38, nz=20, npml_z=5, steps=40)
+    init = W.random_state((w.nz, w.ny, w.nx), seed=W.SEED + 11)
+    _assert(_compare(w, precision, wall=False, init=init), precision)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_minimal_z_extent(precision):
+    """nz = 2 npml_z + 2, the smallest z-walled box: every plane is in the z
+    shell or next to a wall."""
+    w = W.small_wall(nx=36, ny=34, nz=10, npml_z=4, steps=40, envelope="cw", ramp=0.5, plane=5)
+    _assert(_compare(w, precision), precision)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_wall_sheet_in_periodic_box(precision):
+    """The sheet alone in a z-periodic box (plane 0 allowed there)."""
+    w = W.small_wall(nx=40, ny=36, nz=16, npml_z=0, steps=60, envelope="cw", ramp=1.0, plane=0)
+    _assert(_compare(w, precision, z_walls=False), precision)
+
+
+def test_wall_without_fluence():
+    w = W.small_wall(nx=40, ny=36, nz=20, npml_z=4, steps=50, envelope="cw", ramp=1.0)
+    _assert(_compare(w, "f64", fluence=False), "f64")
+
+
+def test_bessel_gauss_scaled_parity():
+    """The full recipe's geometry scaled down by 6 in every direction (same
+    cone angle, Gaussian envelope, waist in proportion), FP32, against the
+    oracle."""
+    full = W.bessel_gauss()
+    s = 6
+    w = full.scaled(nx=full.nx // s, ny=full.ny // s, nz=full.nz // s, npml=6, npml_z=6, w0=full.w0 / s,
+                    plane=7, steps=120, T=1.0, T0=2.0)
+    _assert(_compare(w, "f32"), "f32")
+
+
+# ---- batch, refusals ---------------------------------------------------------
+
+def _walled_cases():
+    return [
+        W.small_wall(nx=40, ny=36, nz=24, npml_z=5, envelope="cw", ramp=1.0),
+        W.small_wall(nx=57, ny=33, nz=15, npml_z=3, envelope="gauss", T=0.7, T0=1.4, theta_deg=15.0),
+        W.small_wall(nx=33, ny=48, nz=12, npml_z=0, envelope="cw", ramp=0.5, plane=4),
+    ]
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_batch_cell_engine_with_z_walls_bitwise(precision):
+    """z-walled grids with wall sheets next to an antenna grid in one batch:
+    130 batched steps (two 64-step graph replays and a remainder) equal each
+    grid's own variant-5 steps bit for bit."""
+    ws = _walled_cases()
+    seq = [gpu_wall_grid(w, precision) for w in ws]
+    bat = [gpu_wall_grid(w, precision) for w in ws]
+    from tests.gpu_cases import gpu_grid
+    ant = W.small(nx=48, ny=40, nz=16, npml=6, r_center=11.0, ramp=1.0)
+    seq.append(gpu_grid(ant, precision, tile=(5, 4, 1)))
+    bat.append(gpu_grid(ant, precision))
+    b = fdtd.Batch(bat)
+    assert b.engine == fdtd.BATCH_CELL
+    with pytest.raises(fdtd.FDTDError) as e:
+        b.set_engine(fdtd.BATCH_PERSISTENT)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    for g in seq:
+        g.step(130)
+    b.step(130)
+    b.sync()
+    for gs, gb in zip(seq, bat):
+        for c in range(6):
+            assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
+        assert np.array_equal(host(gs.fluence()), host(gb.fluence()))
+    b.close()
+
+
+def test_paths_for_periodic_grids_refuse_z_walls():
+    w = W.small_wall(nx=40, ny=36, nz=20, npml_z=4)
+    g = gpu_wall_grid(w, "f32", wall=False)
+    for variant in (0, 1, 2, 3, 4, 6):
+        with pytest.raises(fdtd.FDTDError) as e:
+            g.set_tile(variant, 8, 4)
+        assert e.value.status == fdtd.FDTD_EINVAL
+    g.set_tile(5, 8, 1)
+    with pytest.raises(fdtd.FDTDError) as e:
+        g.set_source(r_center=8.0)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    # the autotuner keeps to variant 5
+    assert g.autotune(2)[0] == 5
+    # a wall source needs variant 5 on a periodic grid too, and then pins it
+    from tests.gpu_cases import gpu_grid
+    p = gpu_grid(W.small(nx=40, ny=36, nz=16, r_center=9.0, ramp=1.0), "f32", tile=(1, 8, 16))
+    with pytest.raises(fdtd.FDTDError) as e:
+        p.set_wall_source(plane=3)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    p.set_tile(5, 4, 1)
+    p.set_wall_source(plane=3)
+    with pytest.raises(fdtd.FDTDError):
+        p.set_tile(1, 8, 16)
+    with pytest.raises(fdtd.FDTDError) as e:
+        fdtd.Adjoint(p, fdtd.EX, [0])
+    assert e.value.status == fdtd.FDTD_EINVAL
+    p.clear_wall_source()
+    p.set_tile(1, 8, 16)
+    p.step(2)
+    p.sync()
+
+
+def test_wall_sheet_plus_antenna_matches_oracle():
+    """Both sources on one z-periodic grid: the antenna's E terms, then the
+    sheet, after each E update."""
+    from tests.cases import oracle_grid, oracle_source
+    from tests.gpu_cases import gpu_grid
+    a = W.small(nx=44, ny=40, nz=16, npml=6, r_center=9.0, steps=50, ramp=1.0)
+    og = oracle_grid(a)
+    st = oracle.State(og)
+    wall = oracle.Wall(theta=np.deg2rad(25.0), w0=0.5, envelope="gauss", T=0.7, T0=1.2, plane=3)
+    oracle.run(og, oracle_source(a), st, a.steps, wall=wall)
+    g = gpu_grid(a, "f64", tile=(5, 4, 1))
+    g.set_wall_source(theta=wall.theta, w0=wall.w0, envelope="gauss", T=wall.T, T0=wall.T0, plane=3)
+    g.step(a.steps)
+    errs = {c: rel_l2(host(g.field(c)), ref) for c, ref in enumerate(st.fields())}
+    errs["fluence"] = rel_l2(host(g.fluence()), st.fluence)
+    _assert(errs, "f64")
+
+
+# ---- the paper's Bessel-Gauss box at full size -------------------------------
+
+def test_bessel_gauss_full_size_fluence():
+    """Section 2's run at full size, FP32 (411 x 411 x 738 cells, 3635
+    steps): at the plane of the on-axis fluence maximum the transverse
+    fluence has a central lobe whose first minimum lies at the Bessel zero
+    2.405 / (k sin(theta)) = 0.383 lambda / sin(theta) (within 10 %, along
+    x and along y), the maximum lies inside the Bessel zone z < w0 /
+    tan(theta) past the sheet, and nothing is non-finite."""
+    w = W.bessel_gauss()
+    g = gpu_wall_grid(w, "f32")
+    g.step(w.steps)
+    g.sync()
+    F = host(g.fluence())
+    assert np.isfinite(F).all()
+    c = w.nx // 2            # odd nx: cell c is centred on the beam axis
+    lo, hi = w.plane + 1, w.nz - w.npml_z
+    axis = F[lo:hi, c, c]
+    kmax = lo + int(np.argmax(axis))
+    zdist = (kmax - w.plane) * w.dz
+    assert 0 < zdist < w.w0 / math.tan(w.theta), zdist
+    r0 = 0.383 / math.sin(w.theta)
+    for prof in (F[kmax, c, c:], F[kmax, c:, c]):
+        # first local minimum of the radial profile
+        d = np.diff(prof)
+        first_min = int(np.argmax(d > 0))
+        assert first_min > 0
+        r = first_min * w.dx
+        assert abs(r - r0) < 0.1 * r0, (r, r0)
+        assert prof[first_min] < 0.2 * prof[0]
