@@ -48,8 +48,10 @@ def _peaks():
 
 def psi_per_cell(w) -> float:
     """Mean number of CPML psi values per cell (H and E sides together):
-    4 on the x shells (2 npml / nx of the cells), 4 on the y shells."""
-    return 4.0 * (2 * w.npml / w.nx) + 4.0 * (2 * w.npml / w.ny)
+    4 on the x shells (2 npml / nx of the cells), 4 on the y shells, and on
+    z-walled grids 4 on the z shells (2 npml_z / nz)."""
+    return (4.0 * (2 * w.npml / w.nx) + 4.0 * (2 * w.npml / w.ny)
+            + 4.0 * (2 * getattr(w, "npml_z", 0) / w.nz))
 
 
 def algorithmic_bytes_per_cell(w, elem_bytes: int) -> float:
@@ -288,6 +290,10 @@ def run_gpu(args):
     # ---- adjoint: 384x384x96 FP32 reverse steps ---------------------------
     adjoint = run_adjoint(torch, fdtd, W, dev, args.adjoint_steps) if args.adjoint_steps > 0 else None
 
+    # ---- the Bessel-Gauss box of Section 2 (z walls, wall sheet) -----------
+    bessel_gauss = (run_bessel_gauss(torch, fdtd, W, dev, args.bg_steps, peak)
+                    if args.bg_steps > 0 else None)
+
     del g32, g64
     out = {
         "metric": METRIC, "value": round(gcell32, 3), "unit": UNIT, "n_gpus": ws,
@@ -320,6 +326,7 @@ def run_gpu(args):
         "e2e": e2e,
         "batched": batched,
         "adjoint": adjoint,
+        "bessel_gauss": bessel_gauss,
         "gpu_launches": args.steps * len(pass32),
         "clocks": clocks,
     }
@@ -389,6 +396,40 @@ def run_batched(torch, fdtd, W, dev, steps):
             "steps": steps, "work_items": items, "persistent_work_items": items_per,
             "ms_per_step": round(ms_bat / steps, 4), "persistent_ms_per_step": round(ms_per / steps, 4),
             "sequential_ms_per_step": round(ms_seq / steps, 4)}
+
+
+def run_bessel_gauss(torch, fdtd, W, dev, steps, peak):
+    """Section 2's Bessel-Gauss box (411 x 411 x 738 cells with the CPML, z
+    walls, the Gaussian-axicon E_x sheet), FP32 on the cell passes: `steps`
+    of its 3635 steps timed with CUDA events (the fields and fluence, 7.6 GB,
+    exceed L2), then the same number with events around each kernel."""
+    w = W.bessel_gauss()
+    d = fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant,
+                            precision="f32", fluence=True, z_walls=True, npml_z=w.npml_z)
+    g = fdtd.Grid(d, device=dev)
+    g.set_wall_source(theta=w.theta, w0=w.w0, E0=w.E0, envelope=w.envelope, T=w.T, T0=w.T0, plane=w.plane)
+    g.step(5)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.step(steps)
+    e1.record(g.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    pass_ms = g.step_timed(steps)
+    rows, dom = kernel_roofline(w, g.tile(), pass_ms, steps, 4, peak, w.cells)
+    for r in rows:   # z-walled grids run the *_w instantiations of the cell passes
+        r["kernel"] += "_w"
+    out = {"workload": w.name, "cells": w.cells, "grid": [w.nx, w.ny, w.nz], "npml": w.npml,
+           "npml_z": w.npml_z, "theta_deg": w.theta_deg, "w0_lambda": w.w0, "steps_timed": steps,
+           "steps_full_run": w.steps, "value": round(job_rate(w.cells, steps, 1, ms), 3), "unit": UNIT,
+           "ms_per_step": round(ms / steps, 5),
+           "full_run_s": round(ms / steps * w.steps / 1e3, 3), "dtype": "f32", "tile": list(g.tile()),
+           "kernels": rows, "dominant": dom["kernel"], "dominant_frac": dom["frac"]}
+    del g
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_adjoint(torch, fdtd, W, dev, steps):
@@ -536,6 +577,8 @@ def main():
     ap.add_argument("--tile", default=None, help="variant,ty,lz for --only runs")
     ap.add_argument("--batch-steps", type=int, default=128,
                     help="steps of the 16-grid batched sweep (0 skips it)")
+    ap.add_argument("--bg-steps", type=int, default=200,
+                    help="steps of the Bessel-Gauss box timed (0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="reverse steps timed on the adjoint workload (0 skips it)")
     args = ap.parse_args()

@@ -161,10 +161,13 @@ cudaError_t cell_launch_grid(fdtd_batch* b, int q, int parity, int step, cudaStr
     const dim3 block(32, kCellTY);
     const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + kCellTY - 1) / kCellTY, g->desc.nz);
     const StepArgs<real> a = make_args<real>(g, parity);
-    yee_h_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+    const bool wall = needs_cell_passes(g);   // z walls or a wall sheet
+    if (wall) yee_h_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+    else yee_h_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    yee_e_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+    if (wall) yee_e_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+    else yee_e_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
     return cudaGetLastError();
 }
 

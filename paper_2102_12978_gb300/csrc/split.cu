@@ -111,6 +111,7 @@ static cudaError_t launch_step_cell(const fdtd_grid* g, int cur, long long n, cu
 }
 
 // Cell-parallel passes: yee_h_cell then yee_e_cell (with the fluence term),
+// or yee_h_cell_w then yee_e_cell_w on grids with z walls or a wall sheet;
 // 32 x TY threads, one cell each, one plane per grid z index.
 template <typename real, int TY>
 static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s, cudaEvent_t mid)
@@ -120,11 +121,14 @@ static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStr
     dim3 block(32, TY);
     dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
     const StepArgs<real> a = make_args<real>(g, cur);
-    yee_h_cell<real, TY><<<grid, block, 0, s>>>(a, t);
+    const bool wall = needs_cell_passes(g);   // z walls or a wall sheet: the *_w kernels
+    if (wall) yee_h_cell_w<real, TY><<<grid, block, 0, s>>>(a, t);
+    else yee_h_cell<real, TY><<<grid, block, 0, s>>>(a, t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (mid) cudaEventRecord(mid, s);
-    yee_e_cell<real, TY><<<grid, block, 0, s>>>(a, t);
+    if (wall) yee_e_cell_w<real, TY><<<grid, block, 0, s>>>(a, t);
+    else yee_e_cell<real, TY><<<grid, block, 0, s>>>(a, t);
     return cudaGetLastError();
 }
 

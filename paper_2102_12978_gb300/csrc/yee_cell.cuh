@@ -92,7 +92,9 @@ __device__ __forceinline__ real src_add(const StepArgs<real>& a, int c, int col,
     return b.x * u.x - b.y * u.y;
 }
 
-template <typename real, bool GEN>
+// WALL: the grid has z walls or a wall sheet (compiled into the *_w kernels
+// only, so that z-periodic grids run code without any of it).
+template <typename real, bool GEN, bool WALL>
 __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, int i, int j, int k)
 {
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
@@ -103,7 +105,7 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     const real* __restrict__ Ey = a.ein[1];
     const real* __restrict__ Ez = a.ein[2];
     const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
-    const bool ztop = GEN && a.zw && k + 1 == nz;   // E past the +z wall reads zero
+    const bool ztop = WALL && GEN && a.zw && k + 1 == nz;   // E past the +z wall reads zero
     const real ex = __ldg(Ex + g), ey = __ldg(Ey + g), ez = __ldg(Ez + g);
     const real ex1 = ztop ? real(0) : __ldg(Ex + gn), ey1 = ztop ? real(0) : __ldg(Ey + gn);
     const real ezj = yin ? __ldg(Ez + g + pitch) : real(0);
@@ -112,7 +114,7 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     const real eyi = xin ? __ldg(Ey + g + 1) : real(0);
     real hx = __ldg(a.hin[0] + g), hy = __ldg(a.hin[1] + g), hz = __ldg(a.hin[2] + g);
     const real chx = __ldg(a.chx + i), chy = __ldg(a.chy + j);
-    const real cz = (GEN && a.zw) ? __ldg(a.chz + k) : a.cz;
+    const real cz = (WALL && GEN && a.zw) ? __ldg(a.chz + k) : a.cz;
     const real dEz_y = ezj - ez, dEy_z = ey1 - ey, dEx_z = ex1 - ex;
     const real dEz_x = ezi - ez, dEy_x = eyi - ey, dEx_y = exj - ex;
     hx = hx - chy * dEz_y + cz * dEy_z;
@@ -141,7 +143,7 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
             a.phy_out[0][q] = p0; a.phy_out[1][q] = p1;
         }
     }
-    if (GEN && a.npz > 0 && (k < a.npz || k >= nz - a.npz)) {
+    if (WALL && GEN && a.npz > 0 && (k < a.npz || k >= nz - a.npz)) {
         const int w2 = 2 * a.npz, kk = k < a.npz ? k : k - nz + w2;
         const int q = (kk * ny + j) * pitch + i;
         const real b = a.bhz[kk], aa = a.ahz[kk];
@@ -164,7 +166,7 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     a.hout[0][g] = hx; a.hout[1][g] = hy; a.hout[2][g] = hz;
 }
 
-template <typename real, bool GEN>
+template <typename real, bool GEN, bool WALL>
 __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cpx<real> tw, int i, int j, int k)
 {
     using Acc = FluAcc<real>;
@@ -177,7 +179,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
     const real* __restrict__ Hy = a.hout[1];
     const real* __restrict__ Hz = a.hout[2];
     const bool xlo = !GEN || i > 0, ylo = !GEN || j > 0;
-    const bool zbot = GEN && a.zw && k == 0;   // H below the z = 0 wall reads zero
+    const bool zbot = WALL && GEN && a.zw && k == 0;   // H below the z = 0 wall reads zero
     const real hx = __ldg(Hx + g), hy = __ldg(Hy + g), hz = __ldg(Hz + g);
     const real hxm = zbot ? real(0) : __ldg(Hx + gm), hym = zbot ? real(0) : __ldg(Hy + gm);
     const real hyi = xlo ? __ldg(Hy + g - 1) : real(0);
@@ -186,7 +188,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
     const real hzj = ylo ? __ldg(Hz + g - pitch) : real(0);
     const real ex = __ldg(a.ein[0] + g), ey = __ldg(a.ein[1] + g), ez = __ldg(a.ein[2] + g);
     const real cex = __ldg(a.cex + i), cey = __ldg(a.cey + j);
-    const real cz = (GEN && a.zw) ? __ldg(a.cez + k) : a.cz;
+    const real cz = (WALL && GEN && a.zw) ? __ldg(a.cez + k) : a.cz;
     const real dHz_y = hz - hzj, dHy_z = hy - hym, dHx_z = hx - hxm;
     const real dHz_x = hz - hzi, dHy_x = hy - hyi, dHx_y = hx - hxj;
     real nex = ex + cey * dHz_y - cz * dHy_z;
@@ -215,7 +217,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
             nez -= p1;
         }
     }
-    if (GEN && a.npz > 0 && (k < a.npz || k >= nz - a.npz)) {
+    if (WALL && GEN && a.npz > 0 && (k < a.npz || k >= nz - a.npz)) {
         const int w2 = 2 * a.npz, kk = k < a.npz ? k : k - nz + w2;
         const int q = (kk * ny + j) * pitch + i;
         const real b = a.bez[kk], aa = a.aez[kk];
@@ -235,7 +237,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
             if (mk & 0x04) nez += src_add(a, 2, col, u);
         }
     }
-    if (a.wcoefr && k == a.wplane) {   // wall source (Section 2), after the antenna
+    if (WALL && a.wcoefr && k == a.wplane) {   // wall source (Section 2), after the antenna
         const Cpx<real> w = static_cast<const Cpx<real>*>(a.wcoefr)[j * nx + i];
         nex += w.x * tw.x - w.y * tw.y;
     }
@@ -257,7 +259,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
         const real* __restrict__ Oz = a.hin[2];
         const int gn = (k + 1 == nz) ? g - k * plane : g + plane;
         const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
-        const bool zin = !GEN || !a.zw || k + 1 < nz;   // plane k+1 inside the z walls
+        const bool zin = !(WALL && GEN && a.zw) || k + 1 < nz;   // plane k+1 inside the z walls
         const real ex1 = zin ? __ldg(Ex + gn) : real(0), ey1 = zin ? __ldg(Ey + gn) : real(0);
         const real exj = yin ? __ldg(Ex + g + pitch) : real(0);
         const real exj1 = (yin && zin) ? __ldg(Ex + gn + pitch) : real(0);
@@ -289,58 +291,90 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
 }
 
 // Grid: (ceil(nx/32), ceil(ny/TY), nz) CTAs of 32 x TY threads, one cell each.
-// The H pass takes the blocks in launch order, the E pass in reverse order.
-// Register budgets: the H pass 32 (2048 threads per SM), the E pass 40 (FP32,
-// 1536 threads) or 64 (FP64, 1024 threads); without them the z-wall checks of
-// the general blocks would cost FP64 grids an eighth to a quarter of their
-// resident warps.
-template <typename real, int TY>
-__global__ void __launch_bounds__(32 * TY, 2048 / (32 * TY))
-yee_h_cell(const StepArgs<real> a, const StepTime<real> t)
+// The H pass takes the blocks in launch order, the E pass in reverse order:
+// it starts on the planes the H pass touched last, which are still in L2, and
+// ends where the next H pass starts.
+template <typename real, int TY, bool WALL>
+__device__ __forceinline__ void h_block(const StepArgs<real>& a, Cpx<real> th)
 {
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (cell_gen_h<real, TY>(a, i0, j0) || cell_gen_z(a, k)) h_cell<real, true>(a, t.th, i, j, k);
-    else h_cell<real, false>(a, t.th, i, j, k);
+    if (cell_gen_h<real, TY>(a, i0, j0) || (WALL && cell_gen_z(a, k))) h_cell<real, true, WALL>(a, th, i, j, k);
+    else h_cell<real, false, WALL>(a, th, i, j, k);
+}
+
+template <typename real, int TY, bool WALL>
+__device__ __forceinline__ void e_block(const StepArgs<real>& a, Cpx<real> te, Cpx<real> tw)
+{
+    const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
+    const int k = gridDim.z - 1 - blockIdx.z;
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (cell_gen_e<real, TY>(a, i0, j0) || (WALL && cell_gen_z(a, k))) e_cell<real, true, WALL>(a, te, tw, i, j, k);
+    else e_cell<real, false, WALL>(a, te, tw, i, j, k);
+}
+
+// z-periodic grids without a wall sheet.
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_h_cell(const StepArgs<real> a, const StepTime<real> t)
+{
+    h_block<real, TY, false>(a, t.th);
+}
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_e_cell(const StepArgs<real> a, const StepTime<real> t)
+{
+    e_block<real, TY, false>(a, t.te, t.tw);
+}
+
+// Grids with z walls or a wall sheet.  Register budgets: the H pass 32 (2048
+// threads per SM), the E pass 40 (FP32, 1536 threads) or 64 (FP64, 1024
+// threads), the counts of the kernels above; left to itself the compiler
+// spends more on the wall code and loses resident warps.
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY, 2048 / (32 * TY))
+yee_h_cell_w(const StepArgs<real> a, const StepTime<real> t)
+{
+    h_block<real, TY, true>(a, t.th);
 }
 
 template <typename real, int TY>
 __global__ void __launch_bounds__(32 * TY, (sizeof(real) == 8 ? 1024 : 1536) / (32 * TY))
-yee_e_cell(const StepArgs<real> a, const StepTime<real> t)
+yee_e_cell_w(const StepArgs<real> a, const StepTime<real> t)
 {
-    // the E pass walks the grid backwards: it starts on the planes the H pass
-    // touched last, which are still in L2, and ends where the next H pass starts
-    const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
-    const int k = gridDim.z - 1 - blockIdx.z;
-    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (cell_gen_e<real, TY>(a, i0, j0) || cell_gen_z(a, k)) e_cell<real, true>(a, t.te, t.tw, i, j, k);
-    else e_cell<real, false>(a, t.te, t.tw, i, j, k);
+    e_block<real, TY, true>(a, t.te, t.tw);
 }
 
 // The same passes with the step's time factors read from a device table
 // (times[index]): the batched sweep replays a CUDA graph whose steps take
 // their source phase from a table refreshed before each replay.
 template <typename real, int TY>
-__global__ void __launch_bounds__(32 * TY, 2048 / (32 * TY))
+__global__ void __launch_bounds__(32 * TY)
 yee_h_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
 {
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
-    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    const Cpx<real> th = times[index].th;
-    if (cell_gen_h<real, TY>(a, i0, j0) || cell_gen_z(a, k)) h_cell<real, true>(a, th, i, j, k);
-    else h_cell<real, false>(a, th, i, j, k);
+    h_block<real, TY, false>(a, times[index].th);
+}
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY)
+yee_e_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
+{
+    e_block<real, TY, false>(a, times[index].te, Cpx<real>{real(0), real(0)});
+}
+
+template <typename real, int TY>
+__global__ void __launch_bounds__(32 * TY, 2048 / (32 * TY))
+yee_h_cell_wt(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
+{
+    h_block<real, TY, true>(a, times[index].th);
 }
 
 template <typename real, int TY>
 __global__ void __launch_bounds__(32 * TY, (sizeof(real) == 8 ? 1024 : 1536) / (32 * TY))
-yee_e_cell_t(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
+yee_e_cell_wt(const StepArgs<real> a, const StepTime<real>* __restrict__ times, int index)
 {
-    const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
-    const int k = gridDim.z - 1 - blockIdx.z;
-    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    const Cpx<real> te = times[index].te, tw = times[index].tw;
-    if (cell_gen_e<real, TY>(a, i0, j0) || cell_gen_z(a, k)) e_cell<real, true>(a, te, tw, i, j, k);
-    else e_cell<real, false>(a, te, tw, i, j, k);
+    e_block<real, TY, true>(a, times[index].te, times[index].tw);
 }
 
 }  // namespace fdtd

@@ -25,6 +25,24 @@ pytestmark = pytest.mark.gpu
 TOL = {"f64": 1e-11, "f32": 1e-4}
 
 
+def _field_errors(got, ref):
+    """Relative L2 error per component.  An x-directed sheet current leaves
+    H_x identically zero (H is the curl of an x-directed potential), so both
+    sides hold only rounding noise there: a component whose reference norm is
+    below 1e-9 of its field's (E or H) norm is measured against that field's
+    norm instead of its own."""
+    errs = {}
+    for grp in (0, 3):
+        gnorm = math.sqrt(sum(float(np.sum(np.square(ref[grp + c]))) for c in range(3)))
+        for c in range(grp, grp + 3):
+            assert np.isfinite(got[c]).all(), "non-finite field values"
+            rn = float(np.linalg.norm(ref[c].ravel()))
+            den = rn if rn > 1e-9 * gnorm else gnorm
+            errs["ExEyEzHxHyHz"[2 * c:2 * c + 2]] = (float(np.linalg.norm((got[c] - ref[c]).ravel())) / den
+                                                    if den > 0 else float(np.linalg.norm(got[c].ravel())))
+    return errs
+
+
 def _compare(w, precision, tile=None, wall=True, init=None, fluence=True, z_walls=True):
     og = oracle_wall_grid(w, z_walls=z_walls)
     st = oracle.State(og, fluence=fluence)
@@ -39,11 +57,7 @@ def _compare(w, precision, tile=None, wall=True, init=None, fluence=True, z_wall
     oracle.run(og, None, st, w.steps, wall=oracle_wall(w) if wall else None)
     g.step(w.steps)
     g.sync()
-    errs = {}
-    for c, ref in enumerate(st.fields()):
-        got = host(g.field(c))
-        assert np.isfinite(got).all(), "non-finite field values"
-        errs["ExEyEzHxHyHz"[2 * c:2 * c + 2]] = rel_l2(got, ref)
+    errs = _field_errors([host(g.field(c)) for c in range(6)], st.fields())
     if fluence:
         got = host(g.fluence())
         assert np.isfinite(got).all(), "non-finite fluence values"
@@ -203,7 +217,7 @@ def test_wall_sheet_plus_antenna_matches_oracle():
     g = gpu_grid(a, "f64", tile=(5, 4, 1))
     g.set_wall_source(theta=wall.theta, w0=wall.w0, envelope="gauss", T=wall.T, T0=wall.T0, plane=3)
     g.step(a.steps)
-    errs = {c: rel_l2(host(g.field(c)), ref) for c, ref in enumerate(st.fields())}
+    errs = _field_errors([host(g.field(c)) for c in range(6)], st.fields())
     errs["fluence"] = rel_l2(host(g.fluence()), st.fluence)
     _assert(errs, "f64")
 
