@@ -231,6 +231,23 @@ def run_gpu(args):
 
     peak, peak_kind = _peaks()
 
+    if args.only == "bessel_gauss":
+        # profiling run: the Bessel-Gauss box, optionally shrunk, FP32
+        wb = W.bessel_gauss()
+        s = max(1, args.bg_shrink)
+        wb = wb.scaled(nx=wb.nx // s, ny=wb.ny // s, nz=wb.nz // s, w0=wb.w0 / s)
+        d = fdtd.make_grid_desc(wb.nx, wb.ny, wb.nz, wb.npml, wb.dx, wb.dx, wb.dz, courant=wb.courant,
+                                precision="f32", fluence=True, z_walls=True, npml_z=wb.npml_z)
+        g = fdtd.Grid(d, device=dev)
+        g.set_wall_source(theta=wb.theta, w0=wb.w0, E0=wb.E0, envelope=wb.envelope, T=wb.T, T0=wb.T0,
+                          plane=wb.plane)
+        g.step(args.warmup)
+        g.step(args.steps)
+        g.sync()
+        print(json.dumps({"only": "bessel_gauss", "grid": [wb.nx, wb.ny, wb.nz], "steps": args.steps,
+                          "tile": list(g.tile())}))
+        return
+
     if args.only != "all":
         g = make(args.only)
         if args.tile:
@@ -572,13 +589,15 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--only", default="all", choices=["all", "f32", "f64"],
+    ap.add_argument("--only", default="all", choices=["all", "f32", "f64", "bessel_gauss"],
                     help="time only one precision (profiling runs)")
     ap.add_argument("--tile", default=None, help="variant,ty,lz for --only runs")
     ap.add_argument("--batch-steps", type=int, default=128,
                     help="steps of the 16-grid batched sweep (0 skips it)")
     ap.add_argument("--bg-steps", type=int, default=200,
                     help="steps of the Bessel-Gauss box timed (0: skip)")
+    ap.add_argument("--bg-shrink", type=int, default=1,
+                    help="--only bessel_gauss: divide the box's nx, ny, nz by this (profiling runs)")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="reverse steps timed on the adjoint workload (0 skips it)")
     args = ap.parse_args()
