@@ -89,6 +89,9 @@ def lib():
             L.or_pml_profile.argtypes = [C.POINTER(_Grid), C.c_int, C.c_double, C.c_double, dp, dp, dp]
             L.or_source_field.restype = None
             L.or_source_field.argtypes = [C.POINTER(_Source), C.c_double, C.c_double, C.c_double, dp, dp]
+            L.or_bessel_pulse.restype = None
+            L.or_bessel_pulse.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_long,
+                                          dp, dp, dp, dp, C.c_int, dp]
             L.or_source_time.restype = None
             L.or_source_time.argtypes = [C.POINTER(_Source), C.c_double, dp, dp, dp]
             L.or_run.restype = C.c_int
@@ -290,6 +293,22 @@ def adjoint_step(grid: Grid, source: Source | None, adj: State, n: int, grad_amp
     if rc != 0:
         raise RuntimeError("oracle adjoint step failed")
     return adj
+
+
+def bessel_pulse(m: int, theta: float, T: float, T0: float, r, phi, z, t, w0: float = 2 * np.pi,
+                 nq: int = 4001) -> np.ndarray:
+    """Complex E_y of the order-m Bessel pulse of Eq. 11 (Gaussian spectrum of
+    Eq. 10, width T and peak time T0 in periods, centre w0) at the broadcast
+    points (r, phi, z, t), by quadrature, in the e^{-i w t} convention of the
+    source fields: the physical field is the real part."""
+    r, phi, z, t = np.broadcast_arrays(*(np.asarray(a, dtype=np.float64) for a in (r, phi, z, t)))
+    shape = r.shape
+    cols = [np.ascontiguousarray(a.ravel()) for a in (r, phi, z, t)]
+    out = np.zeros(2 * cols[0].size)
+    dp = C.POINTER(C.c_double)
+    lib().or_bessel_pulse(int(m), float(theta), float(T), float(T0), float(w0), cols[0].size,
+                          *(a.ctypes.data_as(dp) for a in cols), int(nq), out.ctypes.data_as(dp))
+    return (out[0::2] + 1j * out[1::2]).reshape(shape)
 
 
 def source_field(source: Source, x: float, y: float, z: float):
