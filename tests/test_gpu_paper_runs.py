@@ -12,11 +12,12 @@ amplitude of the dominant component E_y against |J_m(K r)|:
     the larger boxes deviate more (runs I, H, D: 2, 3, 4 transverse periods);
   * E_x, zero in the injected m = 0 solution, stays far below E_y inside
     the antenna.
-Reading (see the design notes): the paper compares a Gaussian pulse at its
-peak with the pulse integral point by point; this check uses a CW drive with
-a 3-period ramp, 300 periods to steady state, and the relative L2 deviation
-of the period-averaged amplitude (averaged over z, whole periods) from the
-best-fitting a |J_m(K r)| -- radius r from the beam axis at the E_y point."""
+Two drives.  The CW check: a 3-period ramp, 300 periods to steady state,
+and the relative L2 deviation of the period-averaged amplitude (averaged
+over z, whole periods) from the best-fitting a |J_m(K r)| -- radius r from
+the beam axis at the E_y point.  The pulse check (runs A-E, as the paper
+ran them): the Gaussian envelope of Section 5 and the complex E_y amplitude
+at the peak time against the Bessel-pulse integral of Eq. 11."""
 import json
 import math
 import os
@@ -200,13 +201,20 @@ def pulse_runs():
 
 
 def test_pulse_matches_the_bessel_pulse_integral(pulse_runs):
-    """Runs A, B, C (m = 0, 1, 2 at 30 deg) against Eq. 11 at the peak time:
-    the amplitude over the central three lobes within the paper's 7 %."""
+    """Runs A, B, C (m = 0, 1, 2 at 30 deg) against Eq. 11 at the peak time
+    (Section 5, Fig. 6): each within the paper's 7 % over the central three
+    lobes, in amplitude and as complex fields, and their mean below the
+    paper's 3 % for the central lobes."""
     bound = GOLD["relative_deviation_range_percent"]["value"][1] / 100.0
+    central = GOLD["central_lobes_deviation_percent_max"]["value"] / 100.0
     for name in "ABC":
         assert pulse_runs[name]["central"] < bound, (name, pulse_runs[name])
         assert pulse_runs[name]["central_complex"] < bound, (name, pulse_runs[name])
+    assert np.mean([pulse_runs[n]["central"] for n in "ABC"]) < central
 
 
 def test_pulse_larger_cone_angles_agree_better(pulse_runs):
-    assert pulse_runs["A"]["interior"] < pulse_runs["D"]["interior"] < pulse_runs["E"]["interior"]
+    """Section 5 (Fig. 8): 30, 25, 17 deg (runs A, D, E) deviate more and
+    more, over the central lobes and over the interior."""
+    for key in ("central", "interior"):
+        assert pulse_runs["A"][key] < pulse_runs["D"][key] < pulse_runs["E"][key], key
