@@ -361,7 +361,8 @@ def run_batched(torch, fdtd, W, dev, steps):
     N^2 x 64 grids with N = 96 .. 640), all grids advanced together from a
     64-step CUDA graph: the cell-pass engine (one H and one E launch per step
     over every grid) and the persistent TMA engine (one persistent launch per
-    step), against the same grids stepped one grid at a time."""
+    step); and the persistent cell engine (one cooperative launch per 64
+    steps); against the same grids stepped one grid at a time."""
     ws_ = W.config4()
 
     def make(wl):
@@ -390,7 +391,8 @@ def run_batched(torch, fdtd, W, dev, steps):
         g.close()
     del seq
     engines = {}
-    for name, engine in (("cell", fdtd.BATCH_CELL), ("persistent", fdtd.BATCH_PERSISTENT)):
+    for name, engine in (("cell", fdtd.BATCH_CELL), ("persistent", fdtd.BATCH_PERSISTENT),
+                         ("persistent_cell", fdtd.BATCH_PERSISTENT_CELL)):
         bat = [make(wl) for wl in ws_]
         b = fdtd.Batch(bat, engine=engine)
         b.step(64)                 # warm-up, builds the graph
@@ -404,9 +406,13 @@ def run_batched(torch, fdtd, W, dev, steps):
         b.close()
         for g in bat:
             g.close()
-    ms_bat, items = engines["cell"]
     ms_per, items_per = engines["persistent"]
-    return {"value": round(cells * steps / (ms_bat * 1e-3) / 1e9, 3), "unit": UNIT, "engine": "cell",
+    ms_pc, _ = engines["persistent_cell"]
+    best = min(("cell", "persistent_cell"), key=lambda k: engines[k][0])
+    ms_bat, items = engines[best]
+    return {"value": round(cells * steps / (ms_bat * 1e-3) / 1e9, 3), "unit": UNIT, "engine": best,
+            "cell_value": round(cells * steps / (engines["cell"][0] * 1e-3) / 1e9, 3),
+            "persistent_cell_value": round(cells * steps / (ms_pc * 1e-3) / 1e9, 3),
             "sequential_value": round(cells * steps / (ms_seq * 1e-3) / 1e9, 3),
             "persistent_value": round(cells * steps / (ms_per * 1e-3) / 1e9, 3),
             "speedup_vs_sequential": round(ms_seq / ms_bat, 3), "grids": len(ws_), "cells": cells,

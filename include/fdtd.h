@@ -283,8 +283,17 @@ void fdtd_destroy_grid(fdtd_grid* g);
  *   FDTD_BATCH_PERSISTENT: one persistent kernel launch per step walks every
  *     grid's (tile, z segment) blocks with the TMA-staged one-pass step (the
  *     arithmetic of tile variant 1, bit for bit); z-periodic grids without a
- *     wall source only (EINVAL otherwise, and EINVAL for a batch that mixes
- *     such grids with grids of nz > 65535).
+ *     wall source only (EINVAL otherwise).
+ *   FDTD_BATCH_PERSISTENT_CELL: one cooperative kernel launch per 64 steps
+ *     (no graph): every CTA stays resident and walks the rows of cell blocks
+ *     of all grids, H pass, grid barrier, E pass, barrier, step after step
+ *     (the arithmetic of tile variant 5, bit for bit; every grid kind; no
+ *     limit on nz).  Its barrier waits are bounded: an expired wait raises
+ *     the batch's error word and every CTA returns (ETIMEOUT from
+ *     fdtd_batch_sync).
+ * A batch whose grids need both the cell passes (z walls, wall sheet) and
+ * nz > 65535 starts on FDTD_BATCH_PERSISTENT_CELL; one with nz > 65535 only
+ * on FDTD_BATCH_PERSISTENT.
  * `dev_table` is a device buffer of fdtd_batch_required_bytes bytes
  * (256-byte aligned), owned by the caller and alive until
  * fdtd_batch_destroy; `stream` is a cudaStream_t.  A grid in a batch must
@@ -293,12 +302,20 @@ void fdtd_destroy_grid(fdtd_grid* g);
  * unknown engine, or the cell engine with nz > 65535).  fdtd_batch_sync
  * waits for the stream and reports CUDA errors or an expired device wait
  * (ETIMEOUT).  fdtd_batch_work_items: blocks per step of the current engine. */
-enum { FDTD_BATCH_PERSISTENT = 0, FDTD_BATCH_CELL = 1 };
+enum { FDTD_BATCH_PERSISTENT = 0, FDTD_BATCH_CELL = 1, FDTD_BATCH_PERSISTENT_CELL = 2 };
 size_t fdtd_batch_required_bytes(int n_grids, int precision);
 fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, size_t table_bytes, void* stream,
                               fdtd_batch** out);
 fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine);
 int fdtd_batch_get_engine(const fdtd_batch* b);
+/* Test hook (the paper has no counterpart): kind 1 makes CTA 0 of the next
+ * FDTD_BATCH_PERSISTENT_CELL launch return without arriving at the grid
+ * barrier, so that the other CTAs' bounded waits (about 2^32 SM cycles)
+ * expire: they raise the batch's error word and return, and the next
+ * fdtd_batch_sync returns FDTD_ETIMEOUT (and resets the error word and the
+ * barrier); the device context stays usable.  kind 0 clears a pending
+ * fault.  EINVAL for another kind. */
+fdtd_status fdtd_batch_debug_inject_fault(fdtd_batch* b, int kind);
 fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps);
 fdtd_status fdtd_batch_sync(fdtd_batch* b);
 int fdtd_batch_work_items(const fdtd_batch* b);

@@ -12,6 +12,13 @@
 //     initialised once and their phases carried from block to block; a
 //     one-thread kernel at the end of the graph advances the device step
 //     counter from which the source phases are taken.
+//   * persistent cell passes (FDTD_BATCH_PERSISTENT_CELL): one cooperative
+//     kernel launch runs up to K steps of every grid.  Its CTAs (one per
+//     resident slot) walk the rows of 32 x 4 cell blocks of all grids -- a
+//     row is one (grid, block row, plane) -- with a grid stride, doing the
+//     H pass of every grid, a grid barrier, the E pass (rows and blocks in
+//     reverse order), a barrier, and so on.  The cell arithmetic is that of
+//     tile variant 5, bit for bit; the barriers are bounded waits.
 //   * cell passes (FDTD_BATCH_CELL, the default): each grid steps with the
 //     cell-parallel H and E passes of the single-grid variant 5 (32 x 4 x 1
 //     blocks, one thread per cell).  The graph gives every grid its own
@@ -40,6 +47,7 @@ struct BatchHeader {
     int ngrids, nitems;
     long long counter;   // steps taken by the batch since creation
     int err;             // device error word
+    int fault;           // test hook: 1 = CTA 0 of the next persistent cell launch never arrives
 };
 
 template <typename real>
@@ -99,6 +107,128 @@ constexpr int kBatchGraphSteps = 64;   // even, so a replay leaves the read copy
 constexpr int kCellTY = 4;          // 32 x 4 x 1 cell blocks (tile variant 5)
 constexpr int kCellBranches = 16;   // concurrent graph branches (grids share them round-robin)
 
+// ---- persistent cell engine
+template <typename real>
+struct alignas(128) CellGrid {
+    StepArgs<real> args[2];   // by copy being read
+    int ntx, nty, nz;         // 32 x 4 blocks along x, y; planes
+    int row0;                 // first row of the grid in the batch's row list
+    int wall;                 // z walls or a wall sheet: the wall code path
+};
+
+// Grid-wide barrier of a cooperative launch (every CTA resident).  Thread 0
+// of each CTA arrives on `count`; the last one resets it and advances `gen`;
+// the others wait for `gen` to move, for at most 2^32 SM cycles, or until
+// another CTA has raised the error word.  Release / acquire fences on both
+// sides make the field writes of the pass before visible to the loads of the
+// pass after.  Returns false (error word set) if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        int ok = 1;
+        volatile unsigned* vgen = gen;
+        volatile int* verr = err;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            *reinterpret_cast<volatile unsigned*>(count) = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g0) {
+                if (*verr != 0) { ok = 0; break; }
+                if (clock64() - t0 > (1LL << 32)) { atomicExch(err, 3); ok = 0; break; }
+            }
+        }
+        __threadfence();
+        if (*verr != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <typename real>
+struct BatchCellOcc { static constexpr int value = sizeof(real) == 8 ? 8 : 12; };
+
+// `nsteps` steps of every grid (time factors times[s * ngrids + q]).
+template <typename real>
+__global__ void __launch_bounds__(32 * kCellTY, BatchCellOcc<real>::value)
+yee_batch_cell(BatchHeader* __restrict__ hdr, const CellGrid<real>* __restrict__ grids, int ngrids, int nrows,
+               const StepTime<real>* __restrict__ times, int nsteps, int parity0, unsigned* bar)
+{
+    __shared__ __align__(16) unsigned char sargs_raw[sizeof(StepArgs<real>)];
+    const StepArgs<real>& sa = *reinterpret_cast<const StepArgs<real>*>(sargs_raw);
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    if (hdr->fault == 1 && blockIdx.x == 0) return;   // fdtd_batch_debug_inject_fault
+    int cached = -1;   // grid * 2 + copy of the arguments in shared memory (uniform)
+    #pragma unroll 1
+    for (int s = 0; s < nsteps; ++s) {
+        const int parity = parity0 ^ (s & 1);
+        #pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            #pragma unroll 1
+            for (int w = blockIdx.x; w < nrows; w += gridDim.x) {
+                const int row = pass == 0 ? w : nrows - 1 - w;
+                int q = 0;
+                while (q + 1 < ngrids && grids[q + 1].row0 <= row) ++q;
+                const CellGrid<real>& G = grids[q];
+                if (q * 2 + parity != cached) {
+                    __syncthreads();   // every reader of the previous arguments is done
+                    const int* src = reinterpret_cast<const int*>(&G.args[parity]);
+                    int* dst = reinterpret_cast<int*>(sargs_raw);
+                    for (int v = tid; v < int(sizeof(StepArgs<real>) / 4); v += 32 * kCellTY) dst[v] = src[v];
+                    __syncthreads();
+                    cached = q * 2 + parity;
+                }
+                const int local = row - G.row0, k = local / G.nty, by = local - k * G.nty;
+                const int j0 = by * kCellTY, j = j0 + threadIdx.y;
+                const int ntx = G.ntx;
+                const StepTime<real> T = times[s * ngrids + q];
+                if (pass == 0) {
+                    if (G.wall) {
+                        #pragma unroll 1
+                        for (int bx = 0; bx < ntx; ++bx) {
+                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+                            if (cell_gen_h<real, kCellTY>(sa, i0, j0) || cell_gen_z(sa, k))
+                                h_cell<real, true, true, false>(sa, T.th, i, j, k);
+                            else h_cell<real, false, true, false>(sa, T.th, i, j, k);
+                        }
+                    } else {
+                        #pragma unroll 1
+                        for (int bx = 0; bx < ntx; ++bx) {
+                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+                            if (cell_gen_h<real, kCellTY>(sa, i0, j0)) h_cell<real, true, false, false>(sa, T.th, i, j, k);
+                            else h_cell<real, false, false, false>(sa, T.th, i, j, k);
+                        }
+                    }
+                } else {
+                    if (G.wall) {
+                        #pragma unroll 1
+                        for (int bx = ntx - 1; bx >= 0; --bx) {
+                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+                            if (cell_gen_e<real, kCellTY>(sa, i0, j0) || cell_gen_z(sa, k))
+                                e_cell<real, true, true, false>(sa, T.te, T.tw, i, j, k);
+                            else e_cell<real, false, true, false>(sa, T.te, T.tw, i, j, k);
+                        }
+                    } else {
+                        #pragma unroll 1
+                        for (int bx = ntx - 1; bx >= 0; --bx) {
+                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+                            if (cell_gen_e<real, kCellTY>(sa, i0, j0)) e_cell<real, true, false, false>(sa, T.te, T.tw, i, j, k);
+                            else e_cell<real, false, false, false>(sa, T.te, T.tw, i, j, k);
+                        }
+                    }
+                }
+            }
+            if (!grid_barrier(bar, bar + 1, gridDim.x, &hdr->err)) return;
+        }
+    }
+}
+
 }  // namespace fdtd
 
 using namespace fdtd;
@@ -106,7 +236,7 @@ using namespace fdtd;
 struct fdtd_batch {
     std::vector<fdtd_grid*> grids;
     int precision;
-    int engine;                      // FDTD_BATCH_PERSISTENT or FDTD_BATCH_CELL
+    int engine;                      // FDTD_BATCH_PERSISTENT, _CELL or _PERSISTENT_CELL
     int ty, S;
     void* table;
     size_t table_bytes;
@@ -115,7 +245,11 @@ struct fdtd_batch {
     cudaStream_t capture;
     int nitems;                      // persistent engine: work items
     int nblocks;                     // persistent engine: resident CTAs
-    int cell_blocks;                 // cell engine: blocks per step and pass
+    int cell_blocks;                 // cell engines: blocks per step and pass
+    int nrows;                       // persistent cell engine: rows of blocks per pass
+    int pc_blocks;                   // persistent cell engine: resident CTAs
+    size_t cell_off, bar_off;        // byte offsets of its grid table and barrier words
+    int fault;                       // fdtd_batch_debug_inject_fault pending
     cudaStream_t branch[kCellBranches];
     int nbranch;
     std::vector<unsigned char> host_times;
@@ -137,9 +271,25 @@ size_t time_entry_bytes(int precision)
     return precision == FDTD_F64 ? sizeof(StepTime<double>) : sizeof(StepTime<float>);
 }
 
-size_t times_offset(int n, int precision)
+size_t cell_entry_bytes(int precision)
+{
+    return precision == FDTD_F64 ? sizeof(CellGrid<double>) : sizeof(CellGrid<float>);
+}
+
+// Table layout: header (256 B) | BatchGrid[n] | CellGrid[n] | barrier words (256 B) | time factors.
+size_t cell_offset(int n, int precision)
 {
     return (256 + grid_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
+}
+
+size_t bar_offset(int n, int precision)
+{
+    return (cell_offset(n, precision) + cell_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
+}
+
+size_t times_offset(int n, int precision)
+{
+    return bar_offset(n, precision) + 256;
 }
 
 // ---- cell engine
@@ -185,6 +335,55 @@ cudaError_t cell_launch_any(fdtd_batch* b, int parity, int step, cudaStream_t s)
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// ---- persistent cell engine
+template <typename real>
+fdtd_status pcell_fill(fdtd_batch* b)
+{
+    const int n = int(b->grids.size());
+    std::vector<CellGrid<real>> host(n);
+    int rows = 0;
+    for (int q = 0; q < n; ++q) {
+        const fdtd_grid* g = b->grids[q];
+        CellGrid<real>& G = host[q];
+        std::memset(&G, 0, sizeof(G));
+        for (int cur = 0; cur < 2; ++cur) G.args[cur] = make_args<real>(g, cur);
+        G.ntx = (g->desc.nx + 31) / 32;
+        G.nty = (g->desc.ny + kCellTY - 1) / kCellTY;
+        G.nz = g->desc.nz;
+        G.row0 = rows;
+        G.wall = needs_cell_passes(g) ? 1 : 0;
+        rows += G.nty * G.nz;
+    }
+    b->nrows = rows;
+    char* tab = static_cast<char*>(b->table);
+    fdtd_status st = cuda_check(cudaMemcpy(tab + b->cell_off, host.data(), sizeof(CellGrid<real>) * n,
+                                           cudaMemcpyHostToDevice), "batch cell table");
+    if (st == FDTD_OK) st = cuda_check(cudaMemset(tab + b->bar_off, 0, 256), "batch barrier");
+    if (st != FDTD_OK) return st;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_batch_cell<real>, 32 * kCellTY, 0);
+    if (e != cudaSuccess || per_sm < 1) return fail(FDTD_ECUDA, "persistent cell kernel does not fit on an SM");
+    const int sms = b->grids[0]->sm_count > 0 ? b->grids[0]->sm_count : 152;
+    b->pc_blocks = per_sm * sms < rows ? per_sm * sms : rows;
+    return FDTD_OK;
+}
+
+// `count` steps of every grid in one cooperative launch (time factors
+// already in the table).
+template <typename real>
+cudaError_t pcell_launch(fdtd_batch* b, int parity, int count, cudaStream_t s)
+{
+    char* tab = static_cast<char*>(b->table);
+    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(tab);
+    const CellGrid<real>* grids = reinterpret_cast<const CellGrid<real>*>(tab + b->cell_off);
+    const StepTime<real>* times = reinterpret_cast<const StepTime<real>*>(tab + b->times_off);
+    unsigned* bar = reinterpret_cast<unsigned*>(tab + b->bar_off);
+    int ngrids = int(b->grids.size()), nrows = b->nrows;
+    void* args[] = {&hdr, &grids, &ngrids, &nrows, &times, &count, &parity, &bar};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(yee_batch_cell<real>), dim3(b->pc_blocks),
+                                       dim3(32, kCellTY), args, 0, s);
 }
 
 // Time factors of the next `count` steps of every grid into the device table.
@@ -363,23 +562,23 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->step = 0;
     b->engine = FDTD_BATCH_CELL;
     b->times_off = times_offset(n, prec);
+    b->cell_off = cell_offset(n, prec);
+    b->bar_off = bar_offset(n, prec);
     for (int e = 0; e < 2; ++e) b->built[e][0] = b->built[e][1] = false;
     bool need_cell = false, need_persistent = false;
     for (int q = 0; q < n; ++q) {
         need_persistent |= grids[q]->desc.nz > 65535;   // cell grids take nz <= 65535
         need_cell |= needs_cell_passes(grids[q]);        // z walls / wall source: cell passes only
     }
-    if (need_cell && need_persistent) {
-        delete b;
-        return fail(FDTD_EINVAL, "a batch cannot mix grids with nz > 65535 and grids with z walls or a wall source");
-    }
-    if (need_persistent) b->engine = FDTD_BATCH_PERSISTENT;
+    if (need_persistent) b->engine = need_cell ? FDTD_BATCH_PERSISTENT_CELL : FDTD_BATCH_PERSISTENT;
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
     st = cuda_check(cudaStreamSynchronize(b->stream), "batch create");
     if (st == FDTD_OK) st = prec == FDTD_F64 ? batch_fill<double, 4, 1, 5>(b) : batch_fill<float, 8, 1, 5>(b);
     if (st != FDTD_OK) { cudaStreamDestroy(b->capture); delete b; return st; }
     cell_fill(b);
+    if (st == FDTD_OK) st = prec == FDTD_F64 ? pcell_fill<double>(b) : pcell_fill<float>(b);
+    if (st != FDTD_OK) { cudaStreamDestroy(b->capture); delete b; return st; }
     b->nbranch = n < kCellBranches ? n : kCellBranches;
     for (int r = 0; r < b->nbranch && st == FDTD_OK; ++r) {
         st = cuda_check(cudaStreamCreateWithFlags(&b->branch[r], cudaStreamNonBlocking), "branch stream");
@@ -397,8 +596,8 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
 fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine)
 {
     if (!b) return fail(FDTD_EINVAL, "null batch");
-    if (engine != FDTD_BATCH_PERSISTENT && engine != FDTD_BATCH_CELL)
-        return fail(FDTD_EINVAL, "engine %d is neither FDTD_BATCH_PERSISTENT nor FDTD_BATCH_CELL", engine);
+    if (engine != FDTD_BATCH_PERSISTENT && engine != FDTD_BATCH_CELL && engine != FDTD_BATCH_PERSISTENT_CELL)
+        return fail(FDTD_EINVAL, "engine %d is not FDTD_BATCH_PERSISTENT, _CELL or _PERSISTENT_CELL", engine);
     if (engine == FDTD_BATCH_CELL)
         for (fdtd_grid* g : b->grids)
             if (g->desc.nz > 65535) return fail(FDTD_EINVAL, "the cell engine takes nz <= 65535");
@@ -423,6 +622,17 @@ fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine)
 
 int fdtd_batch_get_engine(const fdtd_batch* b) { return b ? b->engine : -1; }
 
+fdtd_status fdtd_batch_debug_inject_fault(fdtd_batch* b, int kind)
+{
+    if (!b) return fail(FDTD_EINVAL, "null batch");
+    if (kind != 0 && kind != 1) return fail(FDTD_EINVAL, "fault kind %d not in {0, 1}", kind);
+    fdtd_status st = cuda_check(cudaMemcpyAsync(static_cast<char*>(b->table) + offsetof(BatchHeader, fault), &kind,
+                                                sizeof(int), cudaMemcpyHostToDevice, b->stream), "fault hook");
+    if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(b->stream), "fault hook");
+    if (st == FDTD_OK) b->fault = kind;
+    return st;
+}
+
 static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps);
 
 fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps)
@@ -440,6 +650,32 @@ static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps)
         if (g->cur != b->cur) return fail(FDTD_ESTATE, "a batched grid was stepped outside the batch");
     const bool cell = b->engine == FDTD_BATCH_CELL;
     int done = 0;
+    if (b->engine == FDTD_BATCH_PERSISTENT_CELL) {
+        while (done < nsteps) {
+            const int count = nsteps - done < kBatchGraphSteps ? nsteps - done : kBatchGraphSteps;
+            fdtd_status st = b->precision == FDTD_F64 ? cell_upload_times<double>(b, count)
+                                                      : cell_upload_times<float>(b, count);
+            if (st != FDTD_OK) return st;
+            cudaError_t e = b->precision == FDTD_F64 ? pcell_launch<double>(b, b->cur, count, b->stream)
+                                                     : pcell_launch<float>(b, b->cur, count, b->stream);
+            if (e != cudaSuccess) return cuda_check(e, "persistent cell launch");
+            if (b->fault) {   // the hook applies to one launch
+                static const int zero = 0;
+                e = cudaMemcpyAsync(static_cast<char*>(b->table) + offsetof(BatchHeader, fault), &zero, sizeof(int),
+                                    cudaMemcpyHostToDevice, b->stream);
+                if (e != cudaSuccess) return cuda_check(e, "clear fault hook");
+                b->fault = 0;
+            }
+            b->cur ^= (count & 1);
+            done += count;
+            b->step += count;
+            for (fdtd_grid* g : b->grids) {
+                g->step += count;
+                g->cur = b->cur;
+            }
+        }
+        return FDTD_OK;
+    }
     while (done < nsteps) {
         const int count = nsteps - done < kBatchGraphSteps ? nsteps - done : kBatchGraphSteps;
         if (cell) {
@@ -489,6 +725,8 @@ fdtd_status fdtd_batch_sync(fdtd_batch* b)
         int zero = 0;
         cudaMemcpy(static_cast<char*>(b->table) + offsetof(BatchHeader, err), &zero, sizeof(int),
                    cudaMemcpyHostToDevice);
+        // an expired grid barrier may have left its arrival count part-way
+        cudaMemset(static_cast<char*>(b->table) + b->bar_off, 0, 256);
         return fail(FDTD_ETIMEOUT, "a bounded device-side wait expired in the batched step");
     }
     return FDTD_OK;
@@ -497,7 +735,7 @@ fdtd_status fdtd_batch_sync(fdtd_batch* b)
 int fdtd_batch_work_items(const fdtd_batch* b)
 {
     if (!b) return -1;
-    return b->engine == FDTD_BATCH_CELL ? b->cell_blocks : b->nitems;
+    return b->engine == FDTD_BATCH_PERSISTENT ? b->nitems : b->cell_blocks;
 }
 
 void fdtd_batch_destroy(fdtd_batch* b)

@@ -92,9 +92,21 @@ __device__ __forceinline__ real src_add(const StepArgs<real>& a, int c, int col,
     return b.x * u.x - b.y * u.y;
 }
 
+// Field loads.  NC: the read-only (non-coherent) path, for kernels in which
+// no array they read is written by another block -- every single-step pass.
+// A kernel that runs several passes reads values other blocks wrote earlier
+// in the same launch and takes the coherent L1 path (ld.global.ca) after its
+// grid barrier's acquire fence.
+template <bool NC, typename T>
+__device__ __forceinline__ T fld(const T* p)
+{
+    if constexpr (NC) return __ldg(p);
+    else return __ldca(p);
+}
+
 // WALL: the grid has z walls or a wall sheet (compiled into the *_w kernels
 // only, so that z-periodic grids run code without any of it).
-template <typename real, bool GEN, bool WALL>
+template <typename real, bool GEN, bool WALL, bool NC = true>
 __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, int i, int j, int k)
 {
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
@@ -106,15 +118,15 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     const real* __restrict__ Ez = a.ein[2];
     const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
     const bool ztop = WALL && GEN && a.zw && k + 1 == nz;   // E past the +z wall reads zero
-    const real ex = __ldg(Ex + g), ey = __ldg(Ey + g), ez = __ldg(Ez + g);
-    const real ex1 = ztop ? real(0) : __ldg(Ex + gn), ey1 = ztop ? real(0) : __ldg(Ey + gn);
-    const real ezj = yin ? __ldg(Ez + g + pitch) : real(0);
-    const real exj = yin ? __ldg(Ex + g + pitch) : real(0);
-    const real ezi = xin ? __ldg(Ez + g + 1) : real(0);
-    const real eyi = xin ? __ldg(Ey + g + 1) : real(0);
-    real hx = __ldg(a.hin[0] + g), hy = __ldg(a.hin[1] + g), hz = __ldg(a.hin[2] + g);
-    const real chx = __ldg(a.chx + i), chy = __ldg(a.chy + j);
-    const real cz = (WALL && GEN && a.zw) ? __ldg(a.chz + k) : a.cz;
+    const real ex = fld<NC>(Ex + g), ey = fld<NC>(Ey + g), ez = fld<NC>(Ez + g);
+    const real ex1 = ztop ? real(0) : fld<NC>(Ex + gn), ey1 = ztop ? real(0) : fld<NC>(Ey + gn);
+    const real ezj = yin ? fld<NC>(Ez + g + pitch) : real(0);
+    const real exj = yin ? fld<NC>(Ex + g + pitch) : real(0);
+    const real ezi = xin ? fld<NC>(Ez + g + 1) : real(0);
+    const real eyi = xin ? fld<NC>(Ey + g + 1) : real(0);
+    real hx = fld<NC>(a.hin[0] + g), hy = fld<NC>(a.hin[1] + g), hz = fld<NC>(a.hin[2] + g);
+    const real chx = fld<NC>(a.chx + i), chy = fld<NC>(a.chy + j);
+    const real cz = (WALL && GEN && a.zw) ? fld<NC>(a.chz + k) : a.cz;
     const real dEz_y = ezj - ez, dEy_z = ey1 - ey, dEx_z = ex1 - ex;
     const real dEz_x = ezi - ez, dEy_x = eyi - ey, dEx_y = exj - ex;
     hx = hx - chy * dEz_y + cz * dEy_z;
@@ -155,7 +167,7 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     }
     if (a.smask) {
         const int col = j * nx + i;
-        const uint8_t mk = __ldg(a.smask + col) & 0x38;
+        const uint8_t mk = fld<NC>(a.smask + col) & 0x38;
         if (mk) {
             const Cpx<real> u = plane_factor(a, k, th);
             if (mk & 0x08) hx += src_add(a, 3, col, u);
@@ -166,7 +178,7 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     a.hout[0][g] = hx; a.hout[1][g] = hy; a.hout[2][g] = hz;
 }
 
-template <typename real, bool GEN, bool WALL>
+template <typename real, bool GEN, bool WALL, bool NC = true>
 __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cpx<real> tw, int i, int j, int k)
 {
     using Acc = FluAcc<real>;
@@ -180,15 +192,15 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
     const real* __restrict__ Hz = a.hout[2];
     const bool xlo = !GEN || i > 0, ylo = !GEN || j > 0;
     const bool zbot = WALL && GEN && a.zw && k == 0;   // H below the z = 0 wall reads zero
-    const real hx = __ldg(Hx + g), hy = __ldg(Hy + g), hz = __ldg(Hz + g);
-    const real hxm = zbot ? real(0) : __ldg(Hx + gm), hym = zbot ? real(0) : __ldg(Hy + gm);
-    const real hyi = xlo ? __ldg(Hy + g - 1) : real(0);
-    const real hzi = xlo ? __ldg(Hz + g - 1) : real(0);
-    const real hxj = ylo ? __ldg(Hx + g - pitch) : real(0);
-    const real hzj = ylo ? __ldg(Hz + g - pitch) : real(0);
-    const real ex = __ldg(a.ein[0] + g), ey = __ldg(a.ein[1] + g), ez = __ldg(a.ein[2] + g);
-    const real cex = __ldg(a.cex + i), cey = __ldg(a.cey + j);
-    const real cz = (WALL && GEN && a.zw) ? __ldg(a.cez + k) : a.cz;
+    const real hx = fld<NC>(Hx + g), hy = fld<NC>(Hy + g), hz = fld<NC>(Hz + g);
+    const real hxm = zbot ? real(0) : fld<NC>(Hx + gm), hym = zbot ? real(0) : fld<NC>(Hy + gm);
+    const real hyi = xlo ? fld<NC>(Hy + g - 1) : real(0);
+    const real hzi = xlo ? fld<NC>(Hz + g - 1) : real(0);
+    const real hxj = ylo ? fld<NC>(Hx + g - pitch) : real(0);
+    const real hzj = ylo ? fld<NC>(Hz + g - pitch) : real(0);
+    const real ex = fld<NC>(a.ein[0] + g), ey = fld<NC>(a.ein[1] + g), ez = fld<NC>(a.ein[2] + g);
+    const real cex = fld<NC>(a.cex + i), cey = fld<NC>(a.cey + j);
+    const real cz = (WALL && GEN && a.zw) ? fld<NC>(a.cez + k) : a.cz;
     const real dHz_y = hz - hzj, dHy_z = hy - hym, dHx_z = hx - hxm;
     const real dHz_x = hz - hzi, dHy_x = hy - hyi, dHx_y = hx - hxj;
     real nex = ex + cey * dHz_y - cz * dHy_z;
@@ -229,7 +241,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
     }
     if (a.smask) {
         const int col = j * nx + i;
-        const uint8_t mk = __ldg(a.smask + col) & 0x07;
+        const uint8_t mk = fld<NC>(a.smask + col) & 0x07;
         if (mk) {
             const Cpx<real> u = plane_factor(a, k, te);
             if (mk & 0x01) nex += src_add(a, 0, col, u);
@@ -260,21 +272,21 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
         const int gn = (k + 1 == nz) ? g - k * plane : g + plane;
         const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
         const bool zin = !(WALL && GEN && a.zw) || k + 1 < nz;   // plane k+1 inside the z walls
-        const real ex1 = zin ? __ldg(Ex + gn) : real(0), ey1 = zin ? __ldg(Ey + gn) : real(0);
-        const real exj = yin ? __ldg(Ex + g + pitch) : real(0);
-        const real exj1 = (yin && zin) ? __ldg(Ex + gn + pitch) : real(0);
-        const real eyi = xin ? __ldg(Ey + g + 1) : real(0);
-        const real eyi1 = (xin && zin) ? __ldg(Ey + gn + 1) : real(0);
-        const real ezi = xin ? __ldg(Ez + g + 1) : real(0);
-        const real ezj = yin ? __ldg(Ez + g + pitch) : real(0);
-        const real ezij = (xin && yin) ? __ldg(Ez + g + pitch + 1) : real(0);
-        const real hxi = xin ? __ldg(Hx + g + 1) : real(0);
-        const real hyj = yin ? __ldg(Hy + g + pitch) : real(0);
-        const real hz1 = zin ? __ldg(Hz + gn) : real(0);
-        const real ox = __ldg(Ox + g), oy = __ldg(Oy + g), oz = __ldg(Oz + g);
-        const real oz1 = zin ? __ldg(Oz + gn) : real(0);
-        const real oxi = xin ? __ldg(Ox + g + 1) : real(0);
-        const real oyj = yin ? __ldg(Oy + g + pitch) : real(0);
+        const real ex1 = zin ? fld<NC>(Ex + gn) : real(0), ey1 = zin ? fld<NC>(Ey + gn) : real(0);
+        const real exj = yin ? fld<NC>(Ex + g + pitch) : real(0);
+        const real exj1 = (yin && zin) ? fld<NC>(Ex + gn + pitch) : real(0);
+        const real eyi = xin ? fld<NC>(Ey + g + 1) : real(0);
+        const real eyi1 = (xin && zin) ? fld<NC>(Ey + gn + 1) : real(0);
+        const real ezi = xin ? fld<NC>(Ez + g + 1) : real(0);
+        const real ezj = yin ? fld<NC>(Ez + g + pitch) : real(0);
+        const real ezij = (xin && yin) ? fld<NC>(Ez + g + pitch + 1) : real(0);
+        const real hxi = xin ? fld<NC>(Hx + g + 1) : real(0);
+        const real hyj = yin ? fld<NC>(Hy + g + pitch) : real(0);
+        const real hz1 = zin ? fld<NC>(Hz + gn) : real(0);
+        const real ox = fld<NC>(Ox + g), oy = fld<NC>(Oy + g), oz = fld<NC>(Oz + g);
+        const real oz1 = zin ? fld<NC>(Oz + gn) : real(0);
+        const real oxi = xin ? fld<NC>(Ox + g + 1) : real(0);
+        const real oyj = yin ? fld<NC>(Oy + g + pitch) : real(0);
         const real cx = (ex + exj) + (ex1 + exj1);
         const real cy = (ey + eyi) + (ey1 + eyi1);
         const real cc = (ez + ezi) + (ezj + ezij);

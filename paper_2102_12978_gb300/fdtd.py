@@ -92,6 +92,7 @@ _SIGS = {
                                     C.POINTER(C.c_void_p)]),
     "fdtd_batch_set_engine": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_batch_get_engine": (C.c_int, [C.c_void_p]),
+    "fdtd_batch_debug_inject_fault": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_batch_sync": (C.c_int, [C.c_void_p]),
     "fdtd_batch_work_items": (C.c_int, [C.c_void_p]),
@@ -384,12 +385,14 @@ class Grid:
             pass
 
 
-BATCH_PERSISTENT, BATCH_CELL = 0, 1
+BATCH_PERSISTENT, BATCH_CELL, BATCH_PERSISTENT_CELL = 0, 1, 2
 
 
 class Batch:
-    """Several Grid objects advanced together by the graph-replayed batched
-    step (fdtd_batch_*): engine BATCH_CELL (default) or BATCH_PERSISTENT."""
+    """Several Grid objects advanced together (fdtd_batch_*): engine
+    BATCH_CELL (graph-replayed cell passes, the default), BATCH_PERSISTENT
+    (graph-replayed persistent TMA step) or BATCH_PERSISTENT_CELL (one
+    cooperative launch per 64 steps)."""
 
     def __init__(self, grids, engine: int | None = None):
         import torch
@@ -417,6 +420,12 @@ class Batch:
     @property
     def engine(self) -> int:
         return int(lib().fdtd_batch_get_engine(C.c_void_p(self.handle)))
+
+    def inject_fault(self, kind: int = 1):
+        """Test hook: the next persistent cell launch loses one CTA, so that
+        the grid barrier's bounded wait expires (fdtd_batch_debug_inject_fault)."""
+        check(lib().fdtd_batch_debug_inject_fault(C.c_void_p(self.handle), int(kind)),
+              "fdtd_batch_debug_inject_fault")
 
     def step(self, n: int = 1):
         check(lib().fdtd_batch_step(C.c_void_p(self.handle), int(n)), "fdtd_batch_step")

@@ -23,15 +23,16 @@ def _cases():
     ]
 
 
-@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT])
+@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT, fdtd.BATCH_PERSISTENT_CELL])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_batched_equals_sequential_bitwise(precision, engine):
-    """130 steps = two replays of the 64-step graph plus a 2-step remainder;
-    each engine against the single-grid step of the same arithmetic (cell
-    engine: tile variant 5; persistent engine: the TMA one-pass variant 1)."""
+    """130 steps = two replays of the 64-step graph (or two 64-step
+    persistent launches) plus a 2-step remainder; each engine against the
+    single-grid step of the same arithmetic (cell engines: tile variant 5;
+    persistent TMA engine: the one-pass variant 1)."""
     ws = _cases()
     ty = 8 if precision == "f32" else 4
-    tile = (5, 4, 1) if engine == fdtd.BATCH_CELL else (1, ty, 32)
+    tile = (1, ty, 32) if engine == fdtd.BATCH_PERSISTENT else (5, 4, 1)
     seq = [gpu_grid(w, precision, tile=tile) for w in ws]
     bat = [gpu_grid(w, precision) for w in ws]
     b = fdtd.Batch(bat, engine=engine)
@@ -116,4 +117,34 @@ def test_batch_of_more_grids_than_one_launch_holds():
     for gs, gb in zip(seq, bat):
         for c in range(6):
             assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
+    b.close()
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_persistent_cell_engine_many_uneven_grids(precision):
+    """19 grids of uneven shapes (ragged tiles, nz from 1 to 20), 70 steps in
+    one persistent cell launch plus a 6-step one, bit for bit against each
+    grid's own variant-5 steps; then switched to the graph cell engine."""
+    rng = W.rng(W.SEED + 5)
+    ws = []
+    for q in range(19):
+        nx, ny = int(rng.integers(33, 90)), int(rng.integers(30, 80))
+        nz = int(rng.integers(1, 21))
+        ws.append(W.small(nx=nx, ny=ny, nz=nz, npml=6, r_center=min(nx, ny) / 2 - 9.0, ramp=1.0,
+                          m=int(q % 3), theta_deg=float(10 + 2 * q)))
+    seq = [gpu_grid(w, precision, tile=(5, 4, 1)) for w in ws]
+    bat = [gpu_grid(w, precision) for w in ws]
+    b = fdtd.Batch(bat, engine=fdtd.BATCH_PERSISTENT_CELL)
+    assert b.engine == fdtd.BATCH_PERSISTENT_CELL
+    b.step(70)
+    b.set_engine(fdtd.BATCH_CELL)
+    b.step(6)
+    b.sync()
+    for g in seq:
+        g.step(76)
+    for gs, gb in zip(seq, bat):
+        assert gb.n == gs.n == 76
+        for c in range(6):
+            assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
+        assert np.array_equal(host(gs.fluence()), host(gb.fluence()))
     b.close()

@@ -65,3 +65,39 @@ def test_fault_hook_rejects_unknown_kinds():
         g.inject_fault(7)
     assert e.value.status == fdtd.FDTD_EINVAL
     g.close()
+
+
+def test_expired_grid_barrier_reports_timeout():
+    """The persistent cell engine's grid barrier: a lost CTA (host-side fault
+    hook) makes the other CTAs' bounded waits expire; the host reads
+    FDTD_ETIMEOUT, the barrier and error word are reset, and the batch then
+    steps correctly (bit for bit against fresh single grids from the same
+    saved state)."""
+    from tests.gpu_cases import gpu_grid, host
+    ws = [W.small(nx=48, ny=40, nz=8, npml=6, r_center=11.0, ramp=1.0),
+          W.small(nx=37, ny=45, nz=6, npml=6, r_center=9.0, m=1, ramp=1.0)]
+    bat = [gpu_grid(w, "f32") for w in ws]
+    b = fdtd.Batch(bat, engine=fdtd.BATCH_PERSISTENT_CELL)
+    b.step(4)
+    b.sync()
+    b.inject_fault(1)
+    b.step(2)
+    with pytest.raises(fdtd.FDTDError) as e:
+        b.sync()
+    assert e.value.status == fdtd.FDTD_ETIMEOUT
+    b.sync()                      # cleared with the report
+    # restart every grid from a known state and compare with single grids
+    seq = [gpu_grid(w, "f32", tile=(5, 4, 1)) for w in ws]
+    for gs, gb in zip(seq, bat):
+        gb.load_state(gs.save_state())
+    b.step(10)
+    b.sync()
+    for g in seq:
+        g.step(10)
+    for gs, gb in zip(seq, bat):
+        for c in range(6):
+            assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
+    b.close()
+    with pytest.raises(fdtd.FDTDError) as e:
+        fdtd.Batch([gpu_grid(ws[0], "f32")]).inject_fault(5)
+    assert e.value.status == fdtd.FDTD_EINVAL

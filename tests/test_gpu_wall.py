@@ -144,11 +144,12 @@ def _walled_cases():
     ]
 
 
+@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT_CELL])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_batch_cell_engine_with_z_walls_bitwise(precision):
+def test_batch_cell_engine_with_z_walls_bitwise(precision, engine):
     """z-walled grids with wall sheets next to an antenna grid in one batch:
-    130 batched steps (two 64-step graph replays and a remainder) equal each
-    grid's own variant-5 steps bit for bit."""
+    130 batched steps (two 64-step graph replays or persistent launches and
+    a remainder) equal each grid's own variant-5 steps bit for bit."""
     ws = _walled_cases()
     seq = [gpu_wall_grid(w, precision) for w in ws]
     bat = [gpu_wall_grid(w, precision) for w in ws]
@@ -161,6 +162,7 @@ def test_batch_cell_engine_with_z_walls_bitwise(precision):
     with pytest.raises(fdtd.FDTDError) as e:
         b.set_engine(fdtd.BATCH_PERSISTENT)
     assert e.value.status == fdtd.FDTD_EINVAL
+    b.set_engine(engine)
     for g in seq:
         g.step(130)
     b.step(130)
