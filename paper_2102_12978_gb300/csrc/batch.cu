@@ -108,13 +108,27 @@ constexpr int kCellTY = 4;          // 32 x 4 x 1 cell blocks (tile variant 5)
 constexpr int kCellBranches = 16;   // concurrent graph branches (grids share them round-robin)
 
 // ---- persistent cell engine
+// Kernel parameter of one persistent cell launch: a group of at most
+// kPCellGroup grids.  Passed as a __grid_constant__ parameter, so that the
+// cell code reads each grid's arguments from the constant bank with a
+// uniform runtime index, as the single-grid kernels read theirs.
+constexpr int kPCellGroup = 24;
 template <typename real>
-struct alignas(128) CellGrid {
-    StepArgs<real> args[2];   // by copy being read
-    int ntx, nty, nz;         // 32 x 4 blocks along x, y; planes
-    int row0;                 // first row of the grid in the batch's row list
-    int wall;                 // z walls or a wall sheet: the wall code path
+struct PCellParams {
+    StepArgs<real> args[kPCellGroup][2];   // [grid][copy being read]
+    int ntx[kPCellGroup], nty[kPCellGroup];   // 32 x 4 blocks along x, y
+    int row0[kPCellGroup + 1];                // first row of each grid; row0[ngrids] = nrows
+    int wall[kPCellGroup];                    // z walls or a wall sheet: the wall code path
+    int ngrids, nrows;
+    int q0, nall;                             // the group's first grid in the batch; grids in the batch
+    int nsteps, parity0;
+    BatchHeader* hdr;
+    const StepTime<real>* times;              // [step][batch grid]
+    unsigned* bar;                            // barrier words (arrival count, generation)
 };
+// kernel parameters may take 32764 bytes (sm_70 and later, CUDA 12.1 and later)
+static_assert(sizeof(PCellParams<float>) <= 32764 && sizeof(PCellParams<double>) <= 32764,
+              "a group's arguments must fit in one kernel parameter");
 
 // Grid-wide barrier of a cooperative launch (every CTA resident).  Thread 0
 // of each CTA arrives on `count`; the last one resets it and advances `gen`;
@@ -154,42 +168,31 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
 template <typename real>
 struct BatchCellOcc { static constexpr int value = sizeof(real) == 8 ? 8 : 12; };
 
-// `nsteps` steps of every grid (time factors times[s * ngrids + q]).
+// `P.nsteps` steps of every grid of the group.
 template <typename real>
 __global__ void __launch_bounds__(32 * kCellTY, BatchCellOcc<real>::value)
-yee_batch_cell(BatchHeader* __restrict__ hdr, const CellGrid<real>* __restrict__ grids, int ngrids, int nrows,
-               const StepTime<real>* __restrict__ times, int nsteps, int parity0, unsigned* bar)
+yee_batch_cell(const __grid_constant__ PCellParams<real> P)
 {
-    __shared__ __align__(16) unsigned char sargs_raw[sizeof(StepArgs<real>)];
-    const StepArgs<real>& sa = *reinterpret_cast<const StepArgs<real>*>(sargs_raw);
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    if (hdr->fault == 1 && blockIdx.x == 0) return;   // fdtd_batch_debug_inject_fault
-    int cached = -1;   // grid * 2 + copy of the arguments in shared memory (uniform)
+    if (P.hdr->fault == 1 && blockIdx.x == 0) return;   // fdtd_batch_debug_inject_fault
+    const int nrows = P.nrows;
     #pragma unroll 1
-    for (int s = 0; s < nsteps; ++s) {
-        const int parity = parity0 ^ (s & 1);
+    for (int s = 0; s < P.nsteps; ++s) {
+        const int parity = P.parity0 ^ (s & 1);
         #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             #pragma unroll 1
             for (int w = blockIdx.x; w < nrows; w += gridDim.x) {
                 const int row = pass == 0 ? w : nrows - 1 - w;
                 int q = 0;
-                while (q + 1 < ngrids && grids[q + 1].row0 <= row) ++q;
-                const CellGrid<real>& G = grids[q];
-                if (q * 2 + parity != cached) {
-                    __syncthreads();   // every reader of the previous arguments is done
-                    const int* src = reinterpret_cast<const int*>(&G.args[parity]);
-                    int* dst = reinterpret_cast<int*>(sargs_raw);
-                    for (int v = tid; v < int(sizeof(StepArgs<real>) / 4); v += 32 * kCellTY) dst[v] = src[v];
-                    __syncthreads();
-                    cached = q * 2 + parity;
-                }
-                const int local = row - G.row0, k = local / G.nty, by = local - k * G.nty;
+                while (P.row0[q + 1] <= row) ++q;
+                const StepArgs<real>& sa = P.args[q][parity];
+                const int nty = P.nty[q];
+                const int local = row - P.row0[q], k = local / nty, by = local - k * nty;
                 const int j0 = by * kCellTY, j = j0 + threadIdx.y;
-                const int ntx = G.ntx;
-                const StepTime<real> T = times[s * ngrids + q];
+                const int ntx = P.ntx[q];
+                const StepTime<real> T = P.times[s * P.nall + P.q0 + q];
                 if (pass == 0) {
-                    if (G.wall) {
+                    if (P.wall[q]) {
                         #pragma unroll 1
                         for (int bx = 0; bx < ntx; ++bx) {
                             const int i0 = bx * 32, i = i0 + threadIdx.x;
@@ -206,7 +209,7 @@ yee_batch_cell(BatchHeader* __restrict__ hdr, const CellGrid<real>* __restrict__
                         }
                     }
                 } else {
-                    if (G.wall) {
+                    if (P.wall[q]) {
                         #pragma unroll 1
                         for (int bx = ntx - 1; bx >= 0; --bx) {
                             const int i0 = bx * 32, i = i0 + threadIdx.x;
@@ -224,7 +227,7 @@ yee_batch_cell(BatchHeader* __restrict__ hdr, const CellGrid<real>* __restrict__
                     }
                 }
             }
-            if (!grid_barrier(bar, bar + 1, gridDim.x, &hdr->err)) return;
+            if (!grid_barrier(P.bar, P.bar + 1, gridDim.x, &P.hdr->err)) return;
         }
     }
 }
@@ -246,9 +249,9 @@ struct fdtd_batch {
     int nitems;                      // persistent engine: work items
     int nblocks;                     // persistent engine: resident CTAs
     int cell_blocks;                 // cell engines: blocks per step and pass
-    int nrows;                       // persistent cell engine: rows of blocks per pass
-    int pc_blocks;                   // persistent cell engine: resident CTAs
-    size_t cell_off, bar_off;        // byte offsets of its grid table and barrier words
+    std::vector<unsigned char> pc_params;   // persistent cell engine: PCellParams of each group
+    std::vector<int> pc_blocks;             // resident CTAs of each group's launch
+    size_t bar_off;                         // byte offset of its barrier words
     int fault;                       // fdtd_batch_debug_inject_fault pending
     cudaStream_t branch[kCellBranches];
     int nbranch;
@@ -271,20 +274,10 @@ size_t time_entry_bytes(int precision)
     return precision == FDTD_F64 ? sizeof(StepTime<double>) : sizeof(StepTime<float>);
 }
 
-size_t cell_entry_bytes(int precision)
-{
-    return precision == FDTD_F64 ? sizeof(CellGrid<double>) : sizeof(CellGrid<float>);
-}
-
-// Table layout: header (256 B) | BatchGrid[n] | CellGrid[n] | barrier words (256 B) | time factors.
-size_t cell_offset(int n, int precision)
-{
-    return (256 + grid_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
-}
-
+// Table layout: header (256 B) | BatchGrid[n] | barrier words (256 B) | time factors.
 size_t bar_offset(int n, int precision)
 {
-    return (cell_offset(n, precision) + cell_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
+    return (256 + grid_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
 }
 
 size_t times_offset(int n, int precision)
@@ -342,48 +335,57 @@ template <typename real>
 fdtd_status pcell_fill(fdtd_batch* b)
 {
     const int n = int(b->grids.size());
-    std::vector<CellGrid<real>> host(n);
-    int rows = 0;
-    for (int q = 0; q < n; ++q) {
-        const fdtd_grid* g = b->grids[q];
-        CellGrid<real>& G = host[q];
-        std::memset(&G, 0, sizeof(G));
-        for (int cur = 0; cur < 2; ++cur) G.args[cur] = make_args<real>(g, cur);
-        G.ntx = (g->desc.nx + 31) / 32;
-        G.nty = (g->desc.ny + kCellTY - 1) / kCellTY;
-        G.nz = g->desc.nz;
-        G.row0 = rows;
-        G.wall = needs_cell_passes(g) ? 1 : 0;
-        rows += G.nty * G.nz;
-    }
-    b->nrows = rows;
+    const int ngroups = (n + kPCellGroup - 1) / kPCellGroup;
     char* tab = static_cast<char*>(b->table);
-    fdtd_status st = cuda_check(cudaMemcpy(tab + b->cell_off, host.data(), sizeof(CellGrid<real>) * n,
-                                           cudaMemcpyHostToDevice), "batch cell table");
-    if (st == FDTD_OK) st = cuda_check(cudaMemset(tab + b->bar_off, 0, 256), "batch barrier");
+    fdtd_status st = cuda_check(cudaMemset(tab + b->bar_off, 0, 256), "batch barrier");
     if (st != FDTD_OK) return st;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_batch_cell<real>, 32 * kCellTY, 0);
     if (e != cudaSuccess || per_sm < 1) return fail(FDTD_ECUDA, "persistent cell kernel does not fit on an SM");
     const int sms = b->grids[0]->sm_count > 0 ? b->grids[0]->sm_count : 152;
-    b->pc_blocks = per_sm * sms < rows ? per_sm * sms : rows;
+    b->pc_params.assign(sizeof(PCellParams<real>) * ngroups, 0);
+    b->pc_blocks.assign(ngroups, 1);
+    for (int gi = 0; gi < ngroups; ++gi) {
+        PCellParams<real>& P = reinterpret_cast<PCellParams<real>*>(b->pc_params.data())[gi];
+        std::memset(&P, 0, sizeof(P));
+        P.q0 = gi * kPCellGroup;
+        P.ngrids = n - P.q0 < kPCellGroup ? n - P.q0 : kPCellGroup;
+        P.nall = n;
+        int rows = 0;
+        for (int q = 0; q < P.ngrids; ++q) {
+            const fdtd_grid* g = b->grids[P.q0 + q];
+            for (int cur = 0; cur < 2; ++cur) P.args[q][cur] = make_args<real>(g, cur);
+            P.ntx[q] = (g->desc.nx + 31) / 32;
+            P.nty[q] = (g->desc.ny + kCellTY - 1) / kCellTY;
+            P.row0[q] = rows;
+            P.wall[q] = needs_cell_passes(g) ? 1 : 0;
+            rows += P.nty[q] * g->desc.nz;
+        }
+        P.row0[P.ngrids] = rows;
+        P.nrows = rows;
+        P.hdr = reinterpret_cast<BatchHeader*>(tab);
+        P.times = reinterpret_cast<const StepTime<real>*>(tab + b->times_off);
+        P.bar = reinterpret_cast<unsigned*>(tab + b->bar_off);
+        b->pc_blocks[gi] = per_sm * sms < rows ? per_sm * sms : rows;
+    }
     return FDTD_OK;
 }
 
-// `count` steps of every grid in one cooperative launch (time factors
-// already in the table).
+// `count` steps of every grid (time factors already in the table): one
+// cooperative launch per group of grids, in order on stream s.
 template <typename real>
 cudaError_t pcell_launch(fdtd_batch* b, int parity, int count, cudaStream_t s)
 {
-    char* tab = static_cast<char*>(b->table);
-    BatchHeader* hdr = reinterpret_cast<BatchHeader*>(tab);
-    const CellGrid<real>* grids = reinterpret_cast<const CellGrid<real>*>(tab + b->cell_off);
-    const StepTime<real>* times = reinterpret_cast<const StepTime<real>*>(tab + b->times_off);
-    unsigned* bar = reinterpret_cast<unsigned*>(tab + b->bar_off);
-    int ngrids = int(b->grids.size()), nrows = b->nrows;
-    void* args[] = {&hdr, &grids, &ngrids, &nrows, &times, &count, &parity, &bar};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(yee_batch_cell<real>), dim3(b->pc_blocks),
-                                       dim3(32, kCellTY), args, 0, s);
+    for (size_t gi = 0; gi < b->pc_blocks.size(); ++gi) {
+        PCellParams<real>& P = reinterpret_cast<PCellParams<real>*>(b->pc_params.data())[gi];
+        P.nsteps = count;
+        P.parity0 = parity;
+        void* args[] = {&P};
+        cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(yee_batch_cell<real>),
+                                                    dim3(b->pc_blocks[gi]), dim3(32, kCellTY), args, 0, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Time factors of the next `count` steps of every grid into the device table.
@@ -562,7 +564,6 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->step = 0;
     b->engine = FDTD_BATCH_CELL;
     b->times_off = times_offset(n, prec);
-    b->cell_off = cell_offset(n, prec);
     b->bar_off = bar_offset(n, prec);
     for (int e = 0; e < 2; ++e) b->built[e][0] = b->built[e][1] = false;
     bool need_cell = false, need_persistent = false;

@@ -122,12 +122,13 @@ def test_batch_of_more_grids_than_one_launch_holds():
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_persistent_cell_engine_many_uneven_grids(precision):
-    """19 grids of uneven shapes (ragged tiles, nz from 1 to 20), 70 steps in
-    one persistent cell launch plus a 6-step one, bit for bit against each
-    grid's own variant-5 steps; then switched to the graph cell engine."""
+    """27 grids of uneven shapes (ragged tiles, nz from 1 to 20): two groups
+    of launches (24 grids per cooperative launch, then 3), 70 steps (64 + 6)
+    on the persistent cell engine and 6 on the graph cell engine, bit for bit
+    against each grid's own variant-5 steps."""
     rng = W.rng(W.SEED + 5)
     ws = []
-    for q in range(19):
+    for q in range(27):
         nx, ny = int(rng.integers(33, 90)), int(rng.integers(30, 80))
         nz = int(rng.integers(1, 21))
         ws.append(W.small(nx=nx, ny=ny, nz=nz, npml=6, r_center=min(nx, ny) / 2 - 9.0, ramp=1.0,
