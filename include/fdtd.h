@@ -285,15 +285,14 @@ void fdtd_destroy_grid(fdtd_grid* g);
  *     arithmetic of tile variant 1, bit for bit); z-periodic grids without a
  *     wall source only (EINVAL otherwise).
  *   FDTD_BATCH_PERSISTENT_CELL: one cooperative kernel launch per 64 steps
- *     (no graph): every CTA stays resident and walks the rows of cell blocks
- *     of all grids, H pass, grid barrier, E pass, barrier, step after step
- *     (the arithmetic of tile variant 5, bit for bit; every grid kind; no
- *     limit on nz).  Its barrier waits are bounded: an expired wait raises
+ *     and per group of up to 24 grids (no graph): every CTA stays resident
+ *     and takes runs of cell blocks of all grids in order from a counter,
+ *     H pass, grid barrier, E pass, barrier, step after step (the
+ *     arithmetic of tile variant 5, bit for bit; every grid kind; no limit
+ *     on nz).  Its barrier waits are bounded: an expired wait raises
  *     the batch's error word and every CTA returns (ETIMEOUT from
  *     fdtd_batch_sync).
- * A batch whose grids need both the cell passes (z walls, wall sheet) and
- * nz > 65535 starts on FDTD_BATCH_PERSISTENT_CELL; one with nz > 65535 only
- * on FDTD_BATCH_PERSISTENT.
+ * A batch with a grid of nz > 65535 starts on FDTD_BATCH_PERSISTENT_CELL.
  * `dev_table` is a device buffer of fdtd_batch_required_bytes bytes
  * (256-byte aligned), owned by the caller and alive until
  * fdtd_batch_destroy; `stream` is a cudaStream_t.  A grid in a batch must

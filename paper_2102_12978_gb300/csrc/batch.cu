@@ -13,12 +13,15 @@
 //     one-thread kernel at the end of the graph advances the device step
 //     counter from which the source phases are taken.
 //   * persistent cell passes (FDTD_BATCH_PERSISTENT_CELL): one cooperative
-//     kernel launch runs up to K steps of every grid.  Its CTAs (one per
-//     resident slot) walk the rows of 32 x 4 cell blocks of all grids -- a
-//     row is one (grid, block row, plane) -- with a grid stride, doing the
-//     H pass of every grid, a grid barrier, the E pass (rows and blocks in
-//     reverse order), a barrier, and so on.  The cell arithmetic is that of
-//     tile variant 5, bit for bit; the barriers are bounded waits.
+//     kernel launch runs up to K steps of every grid.  The 32 x 4 cell
+//     blocks of all grids form one list; the CTAs (one per resident slot)
+//     take runs of kPCellChunk consecutive blocks, in order, from a per-pass
+//     counter (the E pass from the end of the list), so that the blocks in
+//     flight stay a narrow front whose neighbours are in L2, as under the
+//     hardware block scheduler, and a pass ends within one run of its
+//     average.  H pass of every grid, grid barrier, E pass, barrier, and so
+//     on.  The cell arithmetic is that of tile variant 5, bit for bit; the
+//     barriers are bounded waits.
 //   * cell passes (FDTD_BATCH_CELL, the default): each grid steps with the
 //     cell-parallel H and E passes of the single-grid variant 5 (32 x 4 x 1
 //     blocks, one thread per cell).  The graph gives every grid its own
@@ -113,30 +116,34 @@ constexpr int kCellBranches = 16;   // concurrent graph branches (grids share th
 // cell code reads each grid's arguments from the constant bank with a
 // uniform runtime index, as the single-grid kernels read theirs.
 constexpr int kPCellGroup = 24;
+constexpr int kPCellChunk = 4;   // consecutive blocks per counter ticket
 template <typename real>
 struct PCellParams {
     StepArgs<real> args[kPCellGroup][2];   // [grid][copy being read]
-    int ntx[kPCellGroup], nty[kPCellGroup];   // 32 x 4 blocks along x, y
-    int row0[kPCellGroup + 1];                // first row of each grid; row0[ngrids] = nrows
+    int ntx[kPCellGroup], nty[kPCellGroup], nz[kPCellGroup];   // 32 x 4 blocks along x, y; planes
+    int block0[kPCellGroup + 1];              // first block of each grid; block0[ngrids] = nblocks
     int wall[kPCellGroup];                    // z walls or a wall sheet: the wall code path
-    int ngrids, nrows;
+    int ngrids, nblocks;
     int q0, nall;                             // the group's first grid in the batch; grids in the batch
     int nsteps, parity0;
     BatchHeader* hdr;
     const StepTime<real>* times;              // [step][batch grid]
-    unsigned* bar;                            // barrier words (arrival count, generation)
+    unsigned* bar;                            // [0] arrivals, [1] generation, [2 + pass] block counters
 };
 // kernel parameters may take 32764 bytes (sm_70 and later, CUDA 12.1 and later)
 static_assert(sizeof(PCellParams<float>) <= 32764 && sizeof(PCellParams<double>) <= 32764,
               "a group's arguments must fit in one kernel parameter");
 
 // Grid-wide barrier of a cooperative launch (every CTA resident).  Thread 0
-// of each CTA arrives on `count`; the last one resets it and advances `gen`;
-// the others wait for `gen` to move, for at most 2^32 SM cycles, or until
-// another CTA has raised the error word.  Release / acquire fences on both
-// sides make the field writes of the pass before visible to the loads of the
-// pass after.  Returns false (error word set) if the wait gave up.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int* err)
+// of each CTA arrives on `count`; the last one resets it and the block
+// counter of the pass just finished (`done_ctr`: a CTA takes no more blocks
+// from it once it arrives), then advances `gen`; the others wait for `gen`
+// to move, for at most 2^32 SM cycles, or until another CTA has raised the
+// error word.  Release / acquire fences on both sides make the field writes
+// of the pass before visible to the loads of the pass after.  Returns false
+// (error word set) if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned* done_ctr, unsigned nblocks,
+                                             int* err)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -148,6 +155,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
         __threadfence();
         if (atomicAdd(count, 1u) == nblocks - 1) {
             *reinterpret_cast<volatile unsigned*>(count) = 0u;
+            *reinterpret_cast<volatile unsigned*>(done_ctr) = 0u;
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
@@ -174,60 +182,96 @@ __global__ void __launch_bounds__(32 * kCellTY, BatchCellOcc<real>::value)
 yee_batch_cell(const __grid_constant__ PCellParams<real> P)
 {
     if (P.hdr->fault == 1 && blockIdx.x == 0) return;   // fdtd_batch_debug_inject_fault
-    const int nrows = P.nrows;
+    __shared__ int4 s_blk;   // first block of the next run: grid, bx, by, k (grid < 0: the pass is done)
+    __shared__ int s_len;    // blocks in the run
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    const int nb = P.nblocks;
+    // run t of the pass -> its first block (grid, bx, by, k) and length; the
+    // E pass walks the list from its end
+    auto decode = [&](unsigned t, int pass) {
+        const long long b0 = (long long)t * kPCellChunk;
+        if (b0 >= nb) { s_blk = make_int4(-1, 0, 0, 0); s_len = 0; return; }
+        const int len = nb - b0 < kPCellChunk ? int(nb - b0) : kPCellChunk;
+        const int b = pass == 0 ? int(b0) : nb - 1 - int(b0);
+        int q = 0;
+        while (P.block0[q + 1] <= b) ++q;
+        const int ntx = P.ntx[q], per = ntx * P.nty[q];
+        int local = b - P.block0[q];
+        const int k = local / per;
+        local -= k * per;
+        const int by = local / ntx;
+        s_blk = make_int4(q, local - by * ntx, by, k);
+        s_len = len;
+    };
     #pragma unroll 1
     for (int s = 0; s < P.nsteps; ++s) {
         const int parity = P.parity0 ^ (s & 1);
         #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
+            unsigned* ctr = P.bar + 2 + pass;
+            if (lead) decode(atomicAdd(ctr, 1u), pass);
+            __syncthreads();
+            int4 cur = s_blk;
+            int len = s_len;
             #pragma unroll 1
-            for (int w = blockIdx.x; w < nrows; w += gridDim.x) {
-                const int row = pass == 0 ? w : nrows - 1 - w;
-                int q = 0;
-                while (P.row0[q + 1] <= row) ++q;
-                const StepArgs<real>& sa = P.args[q][parity];
-                const int nty = P.nty[q];
-                const int local = row - P.row0[q], k = local / nty, by = local - k * nty;
-                const int j0 = by * kCellTY, j = j0 + threadIdx.y;
-                const int ntx = P.ntx[q];
-                const StepTime<real> T = P.times[s * P.nall + P.q0 + q];
-                if (pass == 0) {
-                    if (P.wall[q]) {
-                        #pragma unroll 1
-                        for (int bx = 0; bx < ntx; ++bx) {
-                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+            while (cur.x >= 0) {
+                __syncthreads();   // every thread has read s_blk, s_len
+                unsigned t_next = 0;
+                if (lead) t_next = atomicAdd(ctr, 1u);   // fetched while this run is processed
+                int q = cur.x, bx = cur.y, by = cur.z, k = cur.w;
+                int ntx = P.ntx[q], nty = P.nty[q];
+                #pragma unroll 1
+                for (int n = len; n > 0; --n) {
+                    const StepArgs<real>& sa = P.args[q][parity];
+                    const StepTime<real>& T = P.times[s * P.nall + P.q0 + q];
+                    const int i0 = bx * 32, j0 = by * kCellTY;
+                    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+                    if (pass == 0) {
+                        if (P.wall[q]) {
                             if (cell_gen_h<real, kCellTY>(sa, i0, j0) || cell_gen_z(sa, k))
                                 h_cell<real, true, true, false>(sa, T.th, i, j, k);
                             else h_cell<real, false, true, false>(sa, T.th, i, j, k);
-                        }
-                    } else {
-                        #pragma unroll 1
-                        for (int bx = 0; bx < ntx; ++bx) {
-                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+                        } else {
                             if (cell_gen_h<real, kCellTY>(sa, i0, j0)) h_cell<real, true, false, false>(sa, T.th, i, j, k);
                             else h_cell<real, false, false, false>(sa, T.th, i, j, k);
                         }
-                    }
-                } else {
-                    if (P.wall[q]) {
-                        #pragma unroll 1
-                        for (int bx = ntx - 1; bx >= 0; --bx) {
-                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+                        // next block of the list (the last one of a run moves nowhere)
+                        if (n > 1 && ++bx == ntx) {
+                            bx = 0;
+                            if (++by == nty) {
+                                by = 0;
+                                if (++k == P.nz[q]) { k = 0; ++q; ntx = P.ntx[q]; nty = P.nty[q]; }
+                            }
+                        }
+                    } else {
+                        if (P.wall[q]) {
                             if (cell_gen_e<real, kCellTY>(sa, i0, j0) || cell_gen_z(sa, k))
                                 e_cell<real, true, true, false>(sa, T.te, T.tw, i, j, k);
                             else e_cell<real, false, true, false>(sa, T.te, T.tw, i, j, k);
-                        }
-                    } else {
-                        #pragma unroll 1
-                        for (int bx = ntx - 1; bx >= 0; --bx) {
-                            const int i0 = bx * 32, i = i0 + threadIdx.x;
+                        } else {
                             if (cell_gen_e<real, kCellTY>(sa, i0, j0)) e_cell<real, true, false, false>(sa, T.te, T.tw, i, j, k);
                             else e_cell<real, false, false, false>(sa, T.te, T.tw, i, j, k);
                         }
+                        // previous block of the list
+                        if (n > 1 && bx-- == 0) {
+                            bx = ntx - 1;
+                            if (by-- == 0) {
+                                by = nty - 1;
+                                if (k-- == 0) {
+                                    --q;
+                                    ntx = P.ntx[q]; nty = P.nty[q];
+                                    k = P.nz[q] - 1; by = nty - 1; bx = ntx - 1;
+                                }
+                            }
+                        }
                     }
                 }
+                if (lead) decode(t_next, pass);
+                __syncthreads();
+                cur = s_blk;
+                len = s_len;
             }
-            if (!grid_barrier(P.bar, P.bar + 1, gridDim.x, &P.hdr->err)) return;
+            if (!grid_barrier(P.bar, P.bar + 1, P.bar + 2 + pass, gridDim.x, &P.hdr->err)) return;
         }
     }
 }
@@ -357,12 +401,13 @@ fdtd_status pcell_fill(fdtd_batch* b)
             for (int cur = 0; cur < 2; ++cur) P.args[q][cur] = make_args<real>(g, cur);
             P.ntx[q] = (g->desc.nx + 31) / 32;
             P.nty[q] = (g->desc.ny + kCellTY - 1) / kCellTY;
-            P.row0[q] = rows;
+            P.nz[q] = g->desc.nz;
+            P.block0[q] = rows;
             P.wall[q] = needs_cell_passes(g) ? 1 : 0;
-            rows += P.nty[q] * g->desc.nz;
+            rows += P.ntx[q] * P.nty[q] * g->desc.nz;
         }
-        P.row0[P.ngrids] = rows;
-        P.nrows = rows;
+        P.block0[P.ngrids] = rows;
+        P.nblocks = rows;
         P.hdr = reinterpret_cast<BatchHeader*>(tab);
         P.times = reinterpret_cast<const StepTime<real>*>(tab + b->times_off);
         P.bar = reinterpret_cast<unsigned*>(tab + b->bar_off);
@@ -566,12 +611,9 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->times_off = times_offset(n, prec);
     b->bar_off = bar_offset(n, prec);
     for (int e = 0; e < 2; ++e) b->built[e][0] = b->built[e][1] = false;
-    bool need_cell = false, need_persistent = false;
-    for (int q = 0; q < n; ++q) {
-        need_persistent |= grids[q]->desc.nz > 65535;   // cell grids take nz <= 65535
-        need_cell |= needs_cell_passes(grids[q]);        // z walls / wall source: cell passes only
-    }
-    if (need_persistent) b->engine = need_cell ? FDTD_BATCH_PERSISTENT_CELL : FDTD_BATCH_PERSISTENT;
+    bool need_persistent = false;   // the graph cell engine takes nz <= 65535
+    for (int q = 0; q < n; ++q) need_persistent |= grids[q]->desc.nz > 65535;
+    if (need_persistent) b->engine = FDTD_BATCH_PERSISTENT_CELL;
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
     st = cuda_check(cudaStreamSynchronize(b->stream), "batch create");

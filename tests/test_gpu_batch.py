@@ -149,3 +149,32 @@ def test_persistent_cell_engine_many_uneven_grids(precision):
             assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
         assert np.array_equal(host(gs.fluence()), host(gb.fluence()))
     b.close()
+
+
+def test_tall_grid_batch_starts_on_the_persistent_cell_engine():
+    """A grid of 65540 planes (beyond the graph cell engine's 65535) makes
+    the batch start on the persistent cell engine, which decodes the plane
+    of each block from its list index: 6 FP64 steps from a seeded random
+    state against the oracle."""
+    w = W.small(nx=8, ny=8, nz=65540, npml=2, steps=6)
+    init = W.random_state((w.nz, w.ny, w.nx), seed=W.SEED + 21)
+    init[1][:, :, 0] = 0; init[2][:, :, 0] = 0     # tangential E on the i = 0 wall
+    init[0][:, 0, :] = 0; init[2][:, 0, :] = 0     # and on the j = 0 wall
+    g = gpu_grid(w, "f64", source=False, fluence=False)
+    for c in range(6):
+        g.set_field(c, init[c])
+    b = fdtd.Batch([g])
+    assert b.engine == fdtd.BATCH_PERSISTENT_CELL
+    with pytest.raises(fdtd.FDTDError):
+        b.set_engine(fdtd.BATCH_CELL)
+    b.step(w.steps)
+    b.sync()
+    og = oracle_grid(w)
+    st = oracle.State(og, fluence=False)
+    for c in range(3):
+        st.e[c][...] = init[c]
+        st.h[c][...] = init[3 + c]
+    oracle.run(og, None, st, w.steps)
+    for c, ref in enumerate(st.fields()):
+        assert rel_l2(host(g.field(c)), ref) <= 1e-11, c
+    b.close()
