@@ -173,6 +173,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
     return s_ok != 0;
 }
 
+// Resident CTAs per SM of the persistent cell kernel: 40 registers (FP32) or
+// 64 (FP64), the budgets of the single-grid E pass.
 template <typename real>
 struct BatchCellOcc { static constexpr int value = sizeof(real) == 8 ? 8 : 12; };
 
@@ -395,23 +397,23 @@ fdtd_status pcell_fill(fdtd_batch* b)
         P.q0 = gi * kPCellGroup;
         P.ngrids = n - P.q0 < kPCellGroup ? n - P.q0 : kPCellGroup;
         P.nall = n;
-        int rows = 0;
+        int blocks = 0;
         for (int q = 0; q < P.ngrids; ++q) {
             const fdtd_grid* g = b->grids[P.q0 + q];
             for (int cur = 0; cur < 2; ++cur) P.args[q][cur] = make_args<real>(g, cur);
             P.ntx[q] = (g->desc.nx + 31) / 32;
             P.nty[q] = (g->desc.ny + kCellTY - 1) / kCellTY;
             P.nz[q] = g->desc.nz;
-            P.block0[q] = rows;
+            P.block0[q] = blocks;
             P.wall[q] = needs_cell_passes(g) ? 1 : 0;
-            rows += P.ntx[q] * P.nty[q] * g->desc.nz;
+            blocks += P.ntx[q] * P.nty[q] * g->desc.nz;
         }
-        P.block0[P.ngrids] = rows;
-        P.nblocks = rows;
+        P.block0[P.ngrids] = blocks;
+        P.nblocks = blocks;
         P.hdr = reinterpret_cast<BatchHeader*>(tab);
         P.times = reinterpret_cast<const StepTime<real>*>(tab + b->times_off);
         P.bar = reinterpret_cast<unsigned*>(tab + b->bar_off);
-        b->pc_blocks[gi] = per_sm * sms < rows ? per_sm * sms : rows;
+        b->pc_blocks[gi] = per_sm * sms < blocks ? per_sm * sms : blocks;
     }
     return FDTD_OK;
 }
