@@ -276,7 +276,8 @@ void fdtd_destroy_grid(fdtd_grid* g);
 /* ---- Batched stepping of many independent grids --------------------------
  * Several grids (any sizes, sources, cone angles; one precision; all created
  * on the current device and at the same step parity) advance together, K =
- * 64 consecutive steps replayed from one CUDA graph.  Two engines:
+ * 64 consecutive steps per CUDA-graph replay or per persistent launch.
+ * Three engines:
  *   FDTD_BATCH_CELL (default): per step one launch of the H pass and one of
  *     the E pass over the cell blocks of every grid (the arithmetic of
  *     tile variant 5, bit for bit); needs nz <= 65535 on every grid.
@@ -298,7 +299,8 @@ void fdtd_destroy_grid(fdtd_grid* g);
  * fdtd_batch_destroy; `stream` is a cudaStream_t.  A grid in a batch must
  * not be stepped on its own until the batch is destroyed (ESTATE otherwise).
  * fdtd_batch_set_engine switches engines between steps (EINVAL for an
- * unknown engine, or the cell engine with nz > 65535).  fdtd_batch_sync
+ * unknown engine, the cell engine with nz > 65535, or the persistent TMA
+ * engine with z walls or a wall source).  fdtd_batch_sync
  * waits for the stream and reports CUDA errors or an expired device wait
  * (ETIMEOUT).  fdtd_batch_work_items: blocks per step of the current engine. */
 enum { FDTD_BATCH_PERSISTENT = 0, FDTD_BATCH_CELL = 1, FDTD_BATCH_PERSISTENT_CELL = 2 };
