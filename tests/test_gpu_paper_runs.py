@@ -69,6 +69,10 @@ def _run(name):
     r3 = special.jn_zeros(m, 3)[2] / K / dx
     inner = r < r_out - thick - 2
     out = {"ex_over_ey": float(ampx[inner].max() / amp[inner].max())}
+    # intensity of the central lobe plane by plane (Fig. 5: z-invariant within +-2 %)
+    core = torch.as_tensor(r < 0.5 * 0.383 / s / dx, device=acc.device)
+    per_z = (acc / win)[:, core].mean(dim=1).cpu().numpy()
+    out["z_spread"] = float(np.ptp(per_z) / per_z.mean())
     for key, mask in (("central", r < r3), ("interior", inner)):
         a = np.sum(amp[mask] * J[mask]) / np.sum(J[mask] ** 2)
         out[key] = float(np.linalg.norm(amp[mask] - a * J[mask]) / np.linalg.norm(a * J[mask]))
@@ -81,7 +85,7 @@ def runs():
     res = {name: _run(name) for name in "ABCDEFGHI"}
     for name, r in res.items():
         print(f"run {name}: central {100 * r['central']:.2f} %, interior {100 * r['interior']:.2f} %, "
-              f"|Ex|/|Ey| {r['ex_over_ey']:.1e}")
+              f"|Ex|/|Ey| {r['ex_over_ey']:.1e}, z spread {100 * r['z_spread']:.3f} %")
     return res
 
 
@@ -218,3 +222,12 @@ def test_pulse_larger_cone_angles_agree_better(pulse_runs):
     more, over the central lobes and over the interior."""
     for key in ("central", "interior"):
         assert pulse_runs["A"][key] < pulse_runs["D"][key] < pulse_runs["E"][key], key
+
+
+def test_intensity_is_z_invariant(runs):
+    """Section 5 (Fig. 5): the intensity of the central lobe is invariant
+    along z within +-2 % (peak-to-peak over the planes, relative to the
+    mean), for every Table 1 run."""
+    bound = GOLD["z_invariance_percent"]["value"] / 100.0
+    for name, r in runs.items():
+        assert r["z_spread"] < bound, (name, r)
