@@ -16,10 +16,10 @@
 //     kernel launch runs up to K steps of every grid.  The 32 x 4 cell
 //     blocks of all grids form one list; the CTAs (one per resident slot)
 //     take runs of kPCellChunk consecutive blocks, in order, from a per-pass
-//     counter (the E pass from the end of the list), so that the blocks in
-//     flight stay a narrow front whose neighbours are in L2, as under the
-//     hardware block scheduler, and a pass ends within one run of its
-//     average.  H pass of every grid, grid barrier, E pass, barrier, and so
+//     counter (the E pass from the end of the list), then single blocks near
+//     the end of the pass, so that the blocks in flight stay a narrow front
+//     whose neighbours are in L2, as under the hardware block scheduler, and
+//     a pass ends within about one block of its average.  H pass of every grid, grid barrier, E pass, barrier, and so
 //     on.  The cell arithmetic is that of tile variant 5, bit for bit; the
 //     barriers are bounded waits.
 //   * cell passes (FDTD_BATCH_CELL, the default): each grid steps with the
@@ -188,12 +188,16 @@ yee_batch_cell(const __grid_constant__ PCellParams<real> P)
     __shared__ int s_len;    // blocks in the run
     const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
     const int nb = P.nblocks;
-    // run t of the pass -> its first block (grid, bx, by, k) and length; the
-    // E pass walks the list from its end
+    // ticket t of the pass -> its first block (grid, bx, by, k) and run
+    // length: runs of kPCellChunk blocks, then single blocks for the last
+    // 2 x gridDim.x blocks so that the pass ends within one block of its
+    // average; the E pass walks the list from its end
+    const int tail = nb < 2 * int(gridDim.x) ? nb : 2 * int(gridDim.x);
+    const int nrun = (nb - tail) / kPCellChunk, head = nrun * kPCellChunk;
     auto decode = [&](unsigned t, int pass) {
-        const long long b0 = (long long)t * kPCellChunk;
+        const long long b0 = t < unsigned(nrun) ? (long long)t * kPCellChunk : head + ((long long)t - nrun);
         if (b0 >= nb) { s_blk = make_int4(-1, 0, 0, 0); s_len = 0; return; }
-        const int len = nb - b0 < kPCellChunk ? int(nb - b0) : kPCellChunk;
+        const int len = t < unsigned(nrun) ? kPCellChunk : 1;
         const int b = pass == 0 ? int(b0) : nb - 1 - int(b0);
         int q = 0;
         while (P.block0[q + 1] <= b) ++q;
