@@ -296,8 +296,13 @@ void fdtd_destroy_grid(fdtd_grid* g);
  * A batch with a grid of nz > 65535 starts on FDTD_BATCH_PERSISTENT_CELL.
  * `dev_table` is a device buffer of fdtd_batch_required_bytes bytes
  * (256-byte aligned), owned by the caller and alive until
- * fdtd_batch_destroy; `stream` is a cudaStream_t.  A grid in a batch must
- * not be stepped on its own until the batch is destroyed (ESTATE otherwise).
+ * fdtd_batch_destroy; `stream` is a cudaStream_t.  While a grid belongs to
+ * a batch (until fdtd_batch_destroy), fdtd_step, fdtd_step_timed,
+ * fdtd_autotune and the source calls (fdtd_set_annulus_source,
+ * fdtd_clear_source, fdtd_set_wall_source) on it return ESTATE: the batch
+ * holds copies of its arguments.  A grid must outlive its batches.  A grid
+ * whose copy parity no longer matches the batch's (fdtd_load_state of
+ * another parity) makes fdtd_batch_step return ESTATE.
  * fdtd_batch_set_engine switches engines between steps (EINVAL for an
  * unknown engine, the cell engine with nz > 65535, or the persistent TMA
  * engine with z walls or a wall source).  fdtd_batch_sync

@@ -638,6 +638,7 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
             return st;
         }
     }
+    for (fdtd_grid* g : b->grids) ++g->batch_refs;
     *out = b;
     return FDTD_OK;
 }
@@ -790,6 +791,7 @@ int fdtd_batch_work_items(const fdtd_batch* b)
 void fdtd_batch_destroy(fdtd_batch* b)
 {
     if (!b) return;
+    for (fdtd_grid* g : b->grids) --g->batch_refs;
     for (int e = 0; e < 2; ++e)
         for (int p = 0; p < 2; ++p)
             if (b->built[e][p]) cudaGraphExecDestroy(b->exec[e][p]);

@@ -440,6 +440,7 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->has_source = false;
     std::memset(&g->srct, 0, sizeof(g->srct));
     g->srct.dt = g->dt;
+    g->batch_refs = 0;
     g->has_wall = false;
     std::memset(&g->wall, 0, sizeof(g->wall));
     std::memset(&g->wallt, 0, sizeof(g->wallt));
@@ -479,9 +480,18 @@ static fdtd_status validate_source(const fdtd_grid_desc& d, const fdtd_annulus_d
     return FDTD_OK;
 }
 
+// Calls that change what a batch captured, or step the grid by itself, are
+// refused while the grid belongs to a batch.
+static fdtd_status not_batched(const fdtd_grid* g, const char* what)
+{
+    if (g->batch_refs > 0) return fail(FDTD_ESTATE, "%s: the grid belongs to a batch", what);
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
 {
     if (!g || !s) return fail(FDTD_EINVAL, "null argument");
+    if (g->batch_refs > 0) return not_batched(g, "fdtd_set_annulus_source");
     const fdtd_grid_desc& d = g->desc;
     fdtd_status vst = validate_source(d, s);
     if (vst != FDTD_OK) return vst;
@@ -597,6 +607,7 @@ static void wall_tables(const fdtd_grid_desc& d, const fdtd_wall_desc* w, std::v
 fdtd_status fdtd_set_wall_source(fdtd_grid* g, const fdtd_wall_desc* w)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (g->batch_refs > 0) return not_batched(g, "fdtd_set_wall_source");
     if (!w) {
         g->has_wall = false;
         return FDTD_OK;
@@ -646,6 +657,7 @@ fdtd_status fdtd_wall_coefficients(const fdtd_grid_desc* d, const fdtd_wall_desc
 fdtd_status fdtd_clear_source(fdtd_grid* g)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (g->batch_refs > 0) return not_batched(g, "fdtd_clear_source");
     g->has_source = false;
     for (int c = 0; c < 6; ++c) g->counts[c] = 0;
     return FDTD_OK;
@@ -655,6 +667,7 @@ fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
     if (nsteps < 0) return fail(FDTD_EINVAL, "nsteps < 0");
+    if (g->batch_refs > 0) return not_batched(g, "fdtd_step");
     nvtxRangePushA("fdtd_step");
     for (int s = 0; s < nsteps; ++s) {
         cudaError_t e = launch_step(g, g->cur, g->step, g->tile, g->stream);
@@ -678,6 +691,7 @@ fdtd_status fdtd_debug_inject_fault(fdtd_grid* g, int kind)
 fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_passes, int* n_passes)
 {
     if (!g || !pass_ms || !n_passes || nsteps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    if (g->batch_refs > 0) return not_batched(g, "fdtd_step_timed");
     const int np = passes_per_step(g->tile);
     if (max_passes < np) return fail(FDTD_EINVAL, "max_passes=%d < %d kernels per step", max_passes, np);
     std::vector<cudaEvent_t> ev(size_t(nsteps) * (np + 1), nullptr);
@@ -875,6 +889,7 @@ fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz)
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
 {
     if (!g || !scratch_state || steps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    if (g->batch_refs > 0) return not_batched(g, "fdtd_autotune");
     g->fault = 0;
     fdtd_status st = fdtd_save_state(g, scratch_state);
     if (st != FDTD_OK) return st;

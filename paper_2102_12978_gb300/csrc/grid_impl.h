@@ -72,6 +72,7 @@ struct fdtd_grid {
     fdtd::TmaMaps hmaps[2][3];  // the same for the boxes of yee_hflu_tma
     bool hmaps_ok[2][3];
     int fault;                  // fdtd_debug_inject_fault: applies to the next step only
+    int batch_refs;             // batches holding this grid (their kernels hold copies of its arguments)
     bool has_wall;              // fdtd_set_wall_source
     fdtd_wall_desc wall;
     fdtd::SrcTime wallt;        // time envelope of the wall source

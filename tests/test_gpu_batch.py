@@ -92,15 +92,28 @@ def test_batched_matches_oracle_f64(engine):
 
 
 def test_batched_grid_cannot_step_alone():
+    """While in a batch a grid refuses its own steps and source changes
+    (the batch holds copies of its arguments); a batch whose grid was put at
+    another copy parity refuses to step; after the batch is destroyed the
+    grid steps on its own again."""
     ws = _cases()[:2]
     grids = [gpu_grid(w, "f32") for w in ws]
     b = fdtd.Batch(grids)
     b.step(3)
-    grids[0].step(1)          # the grid's parity now differs from the batch's
+    for call in (lambda: grids[0].step(1), lambda: grids[0].step_timed(1), lambda: grids[0].autotune(1),
+                 lambda: grids[0].set_source(r_center=8.0), lambda: grids[0].clear_source(),
+                 lambda: grids[0].set_wall_source(plane=2)):
+        with pytest.raises(fdtd.FDTDError) as e:
+            call()
+        assert e.value.status == fdtd.FDTD_ESTATE
+    fresh = gpu_grid(ws[0], "f32")
+    grids[0].load_state(fresh.save_state())   # step 0, copy parity 0 -- the batch is at parity 1
     with pytest.raises(fdtd.FDTDError) as e:
         b.step(1)
     assert e.value.status == fdtd.FDTD_ESTATE
     b.close()
+    grids[0].step(1)
+    grids[0].sync()
 
 
 def test_batch_of_more_grids_than_one_launch_holds():
