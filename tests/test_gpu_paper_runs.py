@@ -153,11 +153,14 @@ def _pulse_run(name):
     g.step(n0)
     c = n // 2
     lines = []
+    xlines = []
     times = []
     for _ in range(win):
         g.step(1)
         ey = g.field(fdtd.EY)[0]
+        ex = g.field(fdtd.EX)[0]
         lines.append(torch.stack([ey[c, :], ey[:, c]]).double().cpu().numpy())   # along x (j = c), along y (i = c)
+        xlines.append(torch.stack([ex[c, :], ex[:, c]]).double().cpu().numpy())
         times.append(g.n * g.dt)
     g.close()
     lines = np.array(lines)                       # [time, line, point]
@@ -165,6 +168,7 @@ def _pulse_run(name):
     w0 = 2 * np.pi
     ph = np.exp(1j * w0 * times)[:, None, None]
     A = 2.0 / win * np.sum(lines * ph, axis=0)
+    Ax = 2.0 / win * np.sum(np.array(xlines) * ph, axis=0)
     # E_y points: (i, j + 1/2) from the axis at (n/2, n/2)
     idx = np.arange(n)
     xs = [(idx - n / 2) * dx, np.full(n, 0.0)]
@@ -191,6 +195,8 @@ def _pulse_run(name):
         if key == "central":
             out["phase_deg"] = float(np.degrees(np.angle(z)))
     out["t_star_periods"] = float(t_star)
+    # the cross-polarised E_x (zero in the injected solution) against E_y inside the antenna
+    out["ex_over_ey"] = float(np.abs(Ax[inner]).max() / np.abs(A[inner]).max())
     return out
 
 
@@ -200,7 +206,8 @@ def pulse_runs():
     for name, r in res.items():
         print(f"pulse run {name}: t* {r['t_star_periods']:.2f} periods, central {100 * r['central']:.2f} % "
               f"(complex {100 * r['central_complex']:.2f} %, phase {r['phase_deg']:.1f} deg), "
-              f"interior {100 * r['interior']:.2f} % (complex {100 * r['interior_complex']:.2f} %)")
+              f"interior {100 * r['interior']:.2f} % (complex {100 * r['interior_complex']:.2f} %), "
+              f"|Ex|/|Ey| {r['ex_over_ey']:.1e}")
     return res
 
 
