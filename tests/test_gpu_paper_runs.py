@@ -238,3 +238,13 @@ def test_intensity_is_z_invariant(runs):
     bound = GOLD["z_invariance_percent"]["value"] / 100.0
     for name, r in runs.items():
         assert r["z_spread"] < bound, (name, r)
+
+
+def test_pulse_cross_polarisation_four_orders_below(pulse_runs):
+    """Section 5 (last paragraph of results): E_x, zero in the injected TE
+    solution of the Pi_x potential, stays about four orders of magnitude
+    below E_y.  Checked on the m = 0 runs A, D, E at the peak time, along the
+    two lines through the axis inside the antenna."""
+    bound = GOLD["cross_polarisation_ratio"]["value"]
+    for name in "ADE":
+        assert pulse_runs[name]["ex_over_ey"] < bound, (name, pulse_runs[name])
