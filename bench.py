@@ -37,6 +37,13 @@ NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e, nominal
 TRAFFIC: dict[str, float] = {"yee_h_cell": 307.80e6, "yee_e_cell": 545.18e6}
 UNIT = "Gcell-updates/s"
 
+# FP64 instructions per cell of each FP64 cell pass on the 256x256x128 workload
+# (smsp__inst_executed_pipe_fp64.sum x 32 / cells from one ncu capture of the
+# kernels as they stand; summary and command in profiles/).  The FP64 passes
+# are bound by GB300's FP64 pipe: 2 FP64 instructions per SM per clock.
+FP64_INST_PER_CELL: dict[str, float] = {"yee_h_cell": 16.93, "yee_e_cell": 55.93}
+FP64_INST_PER_SM_CLK = 2.0
+
 
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -285,6 +292,17 @@ def run_gpu(args):
     ab64 = algorithmic_bytes_per_cell(w, 8)
     achieved64 = ab64 * cells / (ms64 / steps64 * 1e-3) / 1e9
     passes64, dom64 = kernel_roofline(w, tile64, pass64, steps64, 8, peak, cells)
+    # the FP64 pipe roofline of the dominant FP64 kernel
+    sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fp64_peak = props.multi_processor_count * FP64_INST_PER_SM_CLK * sm_mhz * 1e6 / 1e9   # G inst/s
+    ipc = FP64_INST_PER_CELL.get(dom64["kernel"]) if tile64[0] == 5 else None
+    fp64_alu = None
+    if ipc is not None:
+        ach = ipc * cells / (dom64["ms_per_launch"] * 1e-3) / 1e9
+        fp64_alu = {"bound": "alu", "kernel": dom64["kernel"], "unit": "G fp64 inst/s", "achieved": round(ach, 1),
+                    "peak": round(fp64_peak, 1), "frac": round(ach / fp64_peak, 4), "fp64_inst_per_cell": ipc,
+                    "peak_from": f"{props.multi_processor_count} SMs x {FP64_INST_PER_SM_CLK:g} FP64 inst/clk x "
+                                 f"{sm_mhz:g} MHz"}
 
     # FP32 vs FP64 agreement on the same number of steps (both GPU paths are
     # parity-checked against the oracle in the test suite)
@@ -335,6 +353,7 @@ def run_gpu(args):
         "fp64": {"value": round(gcell64, 3), "unit": UNIT, "steps": steps64,
                  "ms_per_step": round(ms64 / steps64, 5),
                  "roofline": {"bound": "alu", "kernels": passes64, "dominant": dom64["kernel"],
+                              "fp64_pipe": fp64_alu,
                               "step_achieved_gbs": round(achieved64, 1),
                               "step_frac_of_hbm": round(achieved64 / peak, 4),
                               "algorithmic_bytes_per_cell": ab64}},
