@@ -81,3 +81,42 @@ def test_config4_batched_full_size_f32():
         q = keys.index(key)
         _check(grids[q], _oracle_run(ws[q]), "f32", ws[q].name)
     b.close()
+
+
+def test_largest_grid_keeps_every_plane_exact():
+    """The largest grid the library takes: 2048 x 2048 x 503 FP32 cells, each
+    array just under its 2^31-element bound (about 140 GB on the device).
+    A z-independent state stays z-independent in a z-periodic box (every z
+    difference is exactly zero), so after 3 steps every plane of the fields
+    and of the fluence must equal, bit for bit, the single plane of the same
+    run on a one-plane grid: a wrong index anywhere up to the last plane
+    breaks that."""
+    import torch
+    nx, ny, nz, npml = 2048, 2048, 503, 16
+    d = fdtd.make_grid_desc(nx, ny, nz, npml, 1 / 20, 1 / 20, 1 / 20, precision="f32", fluence=True)
+    assert float(nz) * ny * (nx + 31) < 2 ** 31            # the library's bound, with room for the pitch
+    gen = torch.Generator().manual_seed(W.SEED + 31)
+    base = [torch.randn(ny, nx, generator=gen) for _ in range(6)]
+    base[1][:, 0] = 0; base[2][:, 0] = 0                    # tangential E on the i = 0 wall
+    base[0][0, :] = 0; base[2][0, :] = 0                    # and on the j = 0 wall
+    small = fdtd.Grid(fdtd.make_grid_desc(nx, ny, 1, npml, 1 / 20, 1 / 20, 1 / 20, precision="f32", fluence=True))
+    for c in range(6):
+        small.set_field(c, base[c][None])
+    small.step(3)
+    ref = [small.field(c)[0] for c in range(6)] + [small.fluence()[0]]
+    big = fdtd.Grid(d)
+    for c in range(6):
+        big.set_field(c, base[c].cuda()[None].expand(nz, ny, nx))
+    big.step(3)
+    big.sync()
+    for c in range(6):
+        f = big.field(c)
+        assert torch.equal(f, ref[c][None].expand_as(f)), c
+        del f
+        torch.cuda.empty_cache()
+    F = big.fluence()
+    assert torch.equal(F, ref[6][None].expand_as(F))
+    del F
+    big.close()
+    small.close()
+    torch.cuda.empty_cache()
