@@ -139,8 +139,9 @@ typedef struct {
  *     f(t) Re{ E0 exp(-r^2 / w0^2) e^{-i k r sin(theta)} e^{-i omega t'} }
  * with r the distance of the E_x point (i+1/2, j) from the beam axis
  * (nx/2, ny/2) in wavelengths, and f, t' as in fdtd_annulus_desc.  The sheet
- * radiates to both sides; put it just inside the low-z CPML of a z-walled
- * grid.  The column coefficients are evaluated on the host in FP64. */
+ * radiates to both sides; put it on the first plane past the low-z CPML
+ * of a z-walled grid (plane = npml_z), so that the backward half is
+ * absorbed.  The column coefficients are evaluated on the host in FP64. */
 typedef struct {
     double theta;            /* cone angle of the axicon, radians                  */
     double w0;               /* Gaussian waist, wavelengths (> 0)                  */

@@ -192,8 +192,8 @@ def bessel_gauss() -> WallWorkload:
     w0 = 6 um, a Gaussian amplitude of 100 fs FWHM (T = FWHM / (2 sqrt(ln 2)))
     centred at T0 = 2 T, run to t_run = 266 fs.  Mesh (not given for this
     run): dx = dz = lambda/20, 16 CPML cells on every face, Courant 0.95 of
-    the cubic Yee limit; the sheet sits on the first plane inside the low-z
-    CPML.  Interior 379 x 379 x 706 cells, 411 x 411 x 738 with the CPML."""
+    the cubic Yee limit; the sheet sits on the first plane past the low-z
+    CPML (k = 16).  Interior 379 x 379 x 706 cells, 411 x 411 x 738 with the CPML."""
     th, dx, npml = 25.0, 1.0 / 20, 16
     lam_xy = 1.0 / math.sin(math.radians(th))
     lam_z = 1.0 / math.cos(math.radians(th))
