@@ -128,36 +128,55 @@ struct PCellParams {
     int nsteps, parity0;
     BatchHeader* hdr;
     const StepTime<real>* times;              // [step][batch grid]
-    unsigned* bar;                            // [0] arrivals, [1] generation, [2 + pass] block counters
+    unsigned* bar;                            // barrier words (kBarBytes, layout at grid_barrier)
 };
 // kernel parameters may take 32764 bytes (sm_70 and later, CUDA 12.1 and later)
 static_assert(sizeof(PCellParams<float>) <= 32764 && sizeof(PCellParams<double>) <= 32764,
               "a group's arguments must fit in one kernel parameter");
 
-// Grid-wide barrier of a cooperative launch (every CTA resident).  Thread 0
-// of each CTA arrives on `count`; the last one resets it and the block
-// counter of the pass just finished (`done_ctr`: a CTA takes no more blocks
-// from it once it arrives), then advances `gen`; the others wait for `gen`
-// to move, for at most 2^32 SM cycles, or until another CTA has raised the
-// error word.  Release / acquire fences on both sides make the field writes
-// of the pass before visible to the loads of the pass after.  Returns false
-// (error word set) if the wait gave up.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned* done_ctr, unsigned nblocks,
-                                             int* err)
+// Barrier words of the persistent cell engine, one 128-byte line each:
+// [0] arrivals of group leaders, [32] generation, [64 + 32 pass] block
+// counter of each pass, [128 + 32 g] arrivals within group g of kBarGroup CTAs.
+constexpr int kBarGroup = 32;
+constexpr int kBarLine = 32;
+constexpr size_t kBarBytes = 32768;   // room for 4864 CTAs (32 per SM x 152 SMs)
+
+// Grid-wide barrier of a cooperative launch (every CTA resident), in two
+// levels so that no counter takes more than about kBarGroup arrivals: thread 0
+// of each CTA arrives on its group's counter; the last of a group resets it
+// and arrives on the leaders' counter; the last leader resets that and the
+// block counter of the pass just finished (every CTA has stopped taking
+// blocks from it), then advances the generation.  The others wait for the
+// generation to move, for at most 2^32 SM cycles, or until another CTA has
+// raised the error word.  Release / acquire fences on every arrival and
+// after the wait make the field writes of the pass before visible to the
+// loads of the pass after.  Returns false (error word set) if the wait gave
+// up.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int pass, unsigned nblocks, int* err)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         int ok = 1;
-        volatile unsigned* vgen = gen;
+        volatile unsigned* vgen = bar + kBarLine;
         volatile int* verr = err;
         const unsigned g0 = *vgen;
+        const unsigned grp = blockIdx.x / kBarGroup;
+        const unsigned gsize = nblocks - grp * kBarGroup < unsigned(kBarGroup) ? nblocks - grp * kBarGroup : kBarGroup;
+        const unsigned ngroups = (nblocks + kBarGroup - 1) / kBarGroup;
+        unsigned* gcount = bar + 4 * kBarLine + grp * kBarLine;
+        bool last = false;
         __threadfence();
-        if (atomicAdd(count, 1u) == nblocks - 1) {
-            *reinterpret_cast<volatile unsigned*>(count) = 0u;
-            *reinterpret_cast<volatile unsigned*>(done_ctr) = 0u;
+        if (atomicAdd(gcount, 1u) == gsize - 1) {
+            *reinterpret_cast<volatile unsigned*>(gcount) = 0u;
             __threadfence();
-            atomicAdd(gen, 1u);
+            last = atomicAdd(bar, 1u) == ngroups - 1;
+        }
+        if (last) {
+            *reinterpret_cast<volatile unsigned*>(bar) = 0u;
+            *reinterpret_cast<volatile unsigned*>(bar + (2 + pass) * kBarLine) = 0u;
+            __threadfence();
+            atomicAdd(bar + kBarLine, 1u);
         } else {
             const long long t0 = clock64();
             while (*vgen == g0) {
@@ -214,7 +233,7 @@ yee_batch_cell(const __grid_constant__ PCellParams<real> P)
         const int parity = P.parity0 ^ (s & 1);
         #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            unsigned* ctr = P.bar + 2 + pass;
+            unsigned* ctr = P.bar + (2 + pass) * kBarLine;
             if (lead) decode(atomicAdd(ctr, 1u), pass);
             __syncthreads();
             int4 cur = s_blk;
@@ -277,7 +296,7 @@ yee_batch_cell(const __grid_constant__ PCellParams<real> P)
                 cur = s_blk;
                 len = s_len;
             }
-            if (!grid_barrier(P.bar, P.bar + 1, P.bar + 2 + pass, gridDim.x, &P.hdr->err)) return;
+            if (!grid_barrier(P.bar, pass, gridDim.x, &P.hdr->err)) return;
         }
     }
 }
@@ -324,7 +343,7 @@ size_t time_entry_bytes(int precision)
     return precision == FDTD_F64 ? sizeof(StepTime<double>) : sizeof(StepTime<float>);
 }
 
-// Table layout: header (256 B) | BatchGrid[n] | barrier words (256 B) | time factors.
+// Table layout: header (256 B) | BatchGrid[n] | barrier words (kBarBytes) | time factors.
 size_t bar_offset(int n, int precision)
 {
     return (256 + grid_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
@@ -332,7 +351,7 @@ size_t bar_offset(int n, int precision)
 
 size_t times_offset(int n, int precision)
 {
-    return bar_offset(n, precision) + 256;
+    return bar_offset(n, precision) + kBarBytes;
 }
 
 // ---- cell engine
@@ -387,7 +406,7 @@ fdtd_status pcell_fill(fdtd_batch* b)
     const int n = int(b->grids.size());
     const int ngroups = (n + kPCellGroup - 1) / kPCellGroup;
     char* tab = static_cast<char*>(b->table);
-    fdtd_status st = cuda_check(cudaMemset(tab + b->bar_off, 0, 256), "batch barrier");
+    fdtd_status st = cuda_check(cudaMemset(tab + b->bar_off, 0, kBarBytes), "batch barrier");
     if (st != FDTD_OK) return st;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_batch_cell<real>, 32 * kCellTY, 0);
@@ -417,7 +436,10 @@ fdtd_status pcell_fill(fdtd_batch* b)
         P.hdr = reinterpret_cast<BatchHeader*>(tab);
         P.times = reinterpret_cast<const StepTime<real>*>(tab + b->times_off);
         P.bar = reinterpret_cast<unsigned*>(tab + b->bar_off);
-        b->pc_blocks[gi] = per_sm * sms < blocks ? per_sm * sms : blocks;
+        // resident CTAs, no more than the barrier words have group counters for
+        const int max_ctas = int((kBarBytes / 4 - 4 * kBarLine) / kBarLine) * kBarGroup;
+        int ctas = per_sm * sms < blocks ? per_sm * sms : blocks;
+        b->pc_blocks[gi] = ctas < max_ctas ? ctas : max_ctas;
     }
     return FDTD_OK;
 }
@@ -776,7 +798,7 @@ fdtd_status fdtd_batch_sync(fdtd_batch* b)
         cudaMemcpy(static_cast<char*>(b->table) + offsetof(BatchHeader, err), &zero, sizeof(int),
                    cudaMemcpyHostToDevice);
         // an expired grid barrier may have left its arrival count part-way
-        cudaMemset(static_cast<char*>(b->table) + b->bar_off, 0, 256);
+        cudaMemset(static_cast<char*>(b->table) + b->bar_off, 0, kBarBytes);
         return fail(FDTD_ETIMEOUT, "a bounded device-side wait expired in the batched step");
     }
     return FDTD_OK;
