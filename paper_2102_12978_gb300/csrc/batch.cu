@@ -3,7 +3,8 @@
 //
 // Each grid runs the unchanged method of its own descriptor (Section 4,
 // Eq. 12-13).  A CUDA graph holds K = 64 consecutive steps of every grid;
-// one replay advances them all by K steps.  Two engines:
+// one replay (or, for the persistent cell engine, one cooperative launch per
+// group of grids) advances them all by K steps.  Three engines:
 //   * persistent (FDTD_BATCH_PERSISTENT): the batch flattens every grid's
 //     (32 x TR tile, z segment) blocks into one work list; one persistent
 //     kernel launch per step, one CTA per resident slot (SM count x
@@ -315,8 +316,8 @@ struct fdtd_batch {
     size_t times_off;                // byte offset of the time table in `table`
     cudaStream_t stream;
     cudaStream_t capture;
-    int nitems;                      // persistent engine: work items
-    int nblocks;                     // persistent engine: resident CTAs
+    int nitems;                      // persistent TMA engine: work items
+    int nblocks;                     // persistent TMA engine: resident CTAs
     int cell_blocks;                 // cell engines: blocks per step and pass
     std::vector<unsigned char> pc_params;   // persistent cell engine: PCellParams of each group
     std::vector<int> pc_blocks;             // resident CTAs of each group's launch
