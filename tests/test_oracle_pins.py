@@ -596,3 +596,104 @@ def test_bessel_pulse_x_fronts_travel_at_c_over_sin_theta():
     assert a[np.abs(tau) < 0.5 * rho].max() < 0.35 * right
     # beyond the fronts it has died out (the spectrum's Gaussian tail)
     assert a[np.abs(tau) > rho + 4 * T].max() < 1e-3 * right
+
+
+# ------------------------------------------------ brute force on tiny grids
+
+def _numpy_yee_step(f, dx, dy, dz, dt, z_walls):
+    """One source-free Yee step (Section 4) written independently of the
+    oracle, with whole-array shifts: PEC walls at i = 0, j = 0 and the
+    virtual walls i = nx, j = ny (values past them read as zero), z periodic
+    or (z_walls) closed by PEC at z = 0 and z = nz dz."""
+    Ex, Ey, Ez, Hx, Hy, Hz = (a.copy() for a in f)
+
+    def fwd(a, ax):          # a at index + 1 along axis ax (0 = z, 1 = y, 2 = x)
+        if ax == 0 and not z_walls:
+            return np.roll(a, -1, axis=0)
+        out = np.zeros_like(a)
+        sl_dst = [slice(None)] * 3
+        sl_src = [slice(None)] * 3
+        sl_dst[ax] = slice(0, -1)
+        sl_src[ax] = slice(1, None)
+        out[tuple(sl_dst)] = a[tuple(sl_src)]
+        return out
+
+    def bwd(a, ax):          # a at index - 1 along axis ax
+        if ax == 0 and not z_walls:
+            return np.roll(a, 1, axis=0)
+        out = np.zeros_like(a)
+        sl_dst = [slice(None)] * 3
+        sl_src = [slice(None)] * 3
+        sl_dst[ax] = slice(1, None)
+        sl_src[ax] = slice(0, -1)
+        out[tuple(sl_dst)] = a[tuple(sl_src)]
+        return out
+
+    Hx -= dt * ((fwd(Ez, 1) - Ez) / dy - (fwd(Ey, 0) - Ey) / dz)
+    Hy -= dt * ((fwd(Ex, 0) - Ex) / dz - (fwd(Ez, 2) - Ez) / dx)
+    Hz -= dt * ((fwd(Ey, 2) - Ey) / dx - (fwd(Ex, 1) - Ex) / dy)
+    Ex += dt * ((Hz - bwd(Hz, 1)) / dy - (Hy - bwd(Hy, 0)) / dz)
+    Ey += dt * ((Hx - bwd(Hx, 0)) / dz - (Hz - bwd(Hz, 2)) / dx)
+    Ez += dt * ((Hy - bwd(Hy, 2)) / dx - (Hx - bwd(Hx, 1)) / dy)
+    Ex[:, 0, :] = 0; Ez[:, 0, :] = 0            # tangential E on the j = 0 wall
+    Ey[:, :, 0] = 0; Ez[:, :, 0] = 0            # and on the i = 0 wall
+    if z_walls:
+        Ex[0] = 0; Ey[0] = 0                    # and on the z = 0 wall
+    return [Ex, Ey, Ez, Hx, Hy, Hz]
+
+
+@pytest.mark.parametrize("z_walls", [False, True])
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 3, 4), (3, 5, 2), (6, 4, 1)])
+def test_oracle_step_equals_brute_force(shape, z_walls):
+    """The oracle's cell-by-cell step against the independent whole-array
+    step above (itself the linear update matrix applied to the state), on
+    tiny grids with seeded random states, for 5 steps."""
+    nx, ny, nz = shape
+    if z_walls and nz < 2:
+        pytest.skip("a z-walled box needs two planes")
+    g = oracle.Grid(nx, ny, nz, 0, 0.1, 0.13, 0.07, courant=0.9, z_walls=z_walls)
+    rng = np.random.default_rng(7)
+    st = oracle.State(g, fluence=False)
+    f = [rng.standard_normal((nz, ny, nx)) for _ in range(6)]
+    for c in range(3):
+        st.e[c][...] = f[c]
+        st.h[c][...] = f[3 + c]
+    for n in range(5):
+        f = _numpy_yee_step(f, g.dx, g.dy, g.dz, g.dt, z_walls)
+        oracle.run(g, None, st, 1)
+        for c, ref in enumerate(f):
+            np.testing.assert_allclose(st.fields()[c], ref, rtol=0, atol=1e-13 * max(1.0, np.abs(ref).max()))
+
+
+def test_brute_force_update_matrix_is_a_product_of_shears():
+    """The source-free PEC step is H <- H + A E, then E <- P (E + B H): built
+    column by column from unit vectors (on a 4x4x4 grid), the update matrix
+    restricted to the components the PEC walls leave free has determinant 1
+    (a product of two shears), and the oracle applies exactly that matrix."""
+    nx, ny, nz = 4, 4, 4
+    g = oracle.Grid(nx, ny, nz, 0, 0.1, 0.13, 0.07, courant=0.9)
+    ncomp = nx * ny * nz
+    free = np.ones((6, nz, ny, nx), bool)
+    free[0][:, 0, :] = False; free[2][:, 0, :] = False
+    free[1][:, :, 0] = False; free[2][:, :, 0] = False
+    idx = np.flatnonzero(free.ravel())
+    M = np.zeros((6 * ncomp, idx.size))
+    for col, q in enumerate(idx):
+        v = np.zeros(6 * ncomp)
+        v[q] = 1.0
+        out = _numpy_yee_step([v[c * ncomp:(c + 1) * ncomp].reshape(nz, ny, nx) for c in range(6)],
+                              g.dx, g.dy, g.dz, g.dt, False)
+        M[:, col] = np.concatenate([a.ravel() for a in out])
+    Mf = M[idx]
+    sign, logdet = np.linalg.slogdet(Mf)
+    assert sign > 0 and abs(logdet) < 1e-10
+    # the oracle applies the same matrix to a random free state
+    x = np.zeros(6 * ncomp)
+    x[idx] = np.random.default_rng(3).standard_normal(idx.size)
+    st = oracle.State(g, fluence=False)
+    for c in range(3):
+        st.e[c][...] = x[c * ncomp:(c + 1) * ncomp].reshape(nz, ny, nx)
+        st.h[c][...] = x[(3 + c) * ncomp:(4 + c) * ncomp].reshape(nz, ny, nx)
+    oracle.run(g, None, st, 1)
+    got = np.concatenate([a.ravel() for a in st.fields()])
+    np.testing.assert_allclose(got, M @ x[idx], rtol=0, atol=1e-13)
