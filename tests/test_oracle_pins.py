@@ -697,3 +697,36 @@ def test_brute_force_update_matrix_is_a_product_of_shears():
     oracle.run(g, None, st, 1)
     got = np.concatenate([a.ravel() for a in st.fields()])
     np.testing.assert_allclose(got, M @ x[idx], rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", ["antenna", "wall"])
+def test_soft_source_superposes(kind):
+    """Eq. 13 adds the analytic field after the curl update (a soft source),
+    so the step is affine: the fields from a state x0 with the source equal
+    the fields from x0 without it plus the fields from rest with it.  A hard
+    source, which sets the antenna points, fails this."""
+    nx, ny, nz, npml = 36, 32, 12, 4
+    dx = 1 / 16
+    z_walls = kind == "wall"
+    g = oracle.Grid(nx, ny, nz, npml, dx, dx, dx, courant=0.9, z_walls=z_walls, npml_z=2 if z_walls else 0)
+    src = oracle.Source(r_center=8.0, ramp=0.5) if kind == "antenna" else None
+    wall = oracle.Wall(theta=np.deg2rad(25.0), w0=0.5, ramp=0.5, plane=5) if kind == "wall" else None
+    rng = np.random.default_rng(11)
+    x0 = [rng.standard_normal((nz, ny, nx)) for _ in range(6)]
+
+    def run(init, with_source):
+        st = oracle.State(g, fluence=False)
+        if init is not None:
+            for c in range(3):
+                st.e[c][...] = init[c]
+                st.h[c][...] = init[3 + c]
+        oracle.run(g, src if with_source else None, st, 25, wall=wall if with_source else None)
+        return st.fields()
+
+    both = run(x0, True)
+    free = run(x0, False)
+    forced = run(None, True)
+    for c in range(6):
+        scale = np.abs(both[c]).max()
+        np.testing.assert_allclose(both[c], free[c] + forced[c], rtol=0, atol=1e-12 * scale)
+        assert np.abs(forced[c]).max() > 1e-6 * scale or c == 3   # the source does drive the field
