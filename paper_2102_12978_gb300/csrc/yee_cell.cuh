@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "yee_fused.cuh"
 #include "yee_tma.cuh"
 
@@ -93,14 +95,29 @@ __device__ __forceinline__ real src_add(const StepArgs<real>& a, int c, int col,
 }
 
 // Field loads.  NC: the read-only (non-coherent) path, for kernels in which
-// no array they read is written by another block -- every single-step pass.
+// no array they read is written by another block -- every single-step pass;
+// the L2 fetches 256 bytes per request, so that a warp's 128-byte row also
+// brings in the next block's (the blocks run in x order): 1 % on the E pass.
 // A kernel that runs several passes reads values other blocks wrote earlier
 // in the same launch and takes the coherent L1 path (ld.global.ca) after its
 // grid barrier's acquire fence.
+__device__ __forceinline__ float ld_nc_l2_256(const float* p)
+{
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double ld_nc_l2_256(const double* p)
+{
+    double v;
+    asm("ld.global.nc.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
 template <bool NC, typename T>
 __device__ __forceinline__ T fld(const T* p)
 {
-    if constexpr (NC) return __ldg(p);
+    if constexpr (NC && (std::is_same<T, float>::value || std::is_same<T, double>::value)) return ld_nc_l2_256(p);
+    else if constexpr (NC) return __ldg(p);
     else return __ldca(p);
 }
 
