@@ -113,11 +113,27 @@ __device__ __forceinline__ double ld_nc_l2_256(const double* p)
     asm("ld.global.nc.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
+// The coherent path with the same fetch hint; volatile with a memory
+// clobber, so that no load moves across the grid barrier's fences.
+__device__ __forceinline__ float ld_ca_l2_256(const float* p)
+{
+    float v;
+    asm volatile("ld.global.ca.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_ca_l2_256(const double* p)
+{
+    double v;
+    asm volatile("ld.global.ca.L2::256B.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
 template <bool NC, typename T>
 __device__ __forceinline__ T fld(const T* p)
 {
-    if constexpr (NC && (std::is_same<T, float>::value || std::is_same<T, double>::value)) return ld_nc_l2_256(p);
+    constexpr bool FP = std::is_same<T, float>::value || std::is_same<T, double>::value;
+    if constexpr (NC && FP) return ld_nc_l2_256(p);
     else if constexpr (NC) return __ldg(p);
+    else if constexpr (FP) return ld_ca_l2_256(p);
     else return __ldca(p);
 }
 
