@@ -33,6 +33,7 @@
 
 #include "../../include/fdtd.h"
 #include "grid_impl.h"
+#include "yee_cell.cuh"
 #include "yee_tma.cuh"
 
 namespace fdtd {
@@ -81,7 +82,7 @@ __device__ __forceinline__ void adj_t(const AdjArgs<real>& A, int i, int j, int 
         return;
     }
     const int g = pw * pitch * ny + j * pitch + i;
-    real ex = __ldg(A.ein[0] + g), ey = __ldg(A.ein[1] + g), ez = __ldg(A.ein[2] + g);
+    real ex = fld<true>(A.ein[0] + g), ey = fld<true>(A.ein[1] + g), ez = fld<true>(A.ein[2] + g);
     if (GEN) {
         if (j == 0) { ex = real(0); ez = real(0); }   // PEC: E^{n+1} forced to zero there
         if (i == 0) { ey = real(0); ez = real(0); }
@@ -131,7 +132,7 @@ __device__ __forceinline__ void adj_s(const AdjArgs<real>& A, int i, int j, int 
         return;
     }
     const int g = pw * pitch * ny + j * pitch + i;
-    const real hx = __ldg(A.hout[0] + g), hy = __ldg(A.hout[1] + g), hz = __ldg(A.hout[2] + g);
+    const real hx = fld<true>(A.hout[0] + g), hy = fld<true>(A.hout[1] + g), hz = fld<true>(A.hout[2] + g);
     const real chx = __ldg(a.chx + i), chy = __ldg(a.chy + j);
     s[0] = -chy * hx;      // on dEz/dy in Hx
     s[1] = a.cz * hx;      // on dEy/dz in Hx
@@ -177,7 +178,7 @@ __device__ __forceinline__ void adj_h_cell(const AdjArgs<real>& A, int i, int j,
     adj_t<real, GEN>(A, i, j + 1, k, false, ty, e);
     adj_t<real, GEN>(A, i, j, kp, false, tz, e);
     const int g = k * a.pitch * ny + j * a.pitch + i;
-    real hx = __ldg(A.hin[0] + g), hy = __ldg(A.hin[1] + g), hz = __ldg(A.hin[2] + g);
+    real hx = fld<true>(A.hin[0] + g), hy = fld<true>(A.hin[1] + g), hz = fld<true>(A.hin[2] + g);
     hx += (t[3] - tz[3]) + (t[5] - ty[5]);
     hy += (t[1] - tz[1]) + (t[4] - tx[4]);
     hz += (t[0] - ty[0]) + (t[2] - tx[2]);
@@ -197,7 +198,7 @@ __device__ __forceinline__ void adj_e_cell(const AdjArgs<real>& A, int i, int j,
     adj_s<real, GEN>(A, i, j - 1, k, false, sy);
     adj_s<real, GEN>(A, i, j, km, false, sz);
     const int g = k * a.pitch * ny + j * a.pitch + i;
-    real ex = __ldg(A.ein[0] + g), ey = __ldg(A.ein[1] + g), ez = __ldg(A.ein[2] + g);
+    real ex = fld<true>(A.ein[0] + g), ey = fld<true>(A.ein[1] + g), ez = fld<true>(A.ein[2] + g);
     if (GEN) {
         if (j == 0) { ex = real(0); ez = real(0); }
         if (i == 0) { ey = real(0); ez = real(0); }
