@@ -98,8 +98,8 @@ typedef struct {
 
 /* z boundary.  FDTD_Z_WALLS puts PEC walls at z = 0 and z = nz dz (tangential
  * E_x, E_y zero on the plane k = 0; fields past the last plane read as the
- * wall) with npml_z CPML cells inside each, and needs nz <= 65535.  A
- * z-walled grid runs on tile variant 5 and the cell batch engine only
+ * wall) with npml_z CPML cells inside each.  A z-walled grid runs on tile
+ * variant 5 and the cell batch engines only
  * (EINVAL elsewhere), takes no antenna (the antenna boxes are z-periodic,
  * Section 4) and has no adjoint (EINVAL). */
 enum { FDTD_Z_PERIODIC = 0, FDTD_Z_WALLS = 1 };
@@ -234,9 +234,10 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
  *   2  variant 1 with two rows of the tile per thread;
  *   3  two passes (H, then E with the fluence term), plain loads;
  *   4  two passes, a TMA-staged H pass with the fluence term, then E;
- *   5  two cell-parallel passes, one thread per cell (lz unused; needs
- *      nz <= 65535, else EINVAL);
- *   6  one cell-parallel pass, the neighbouring H recomputed per cell.
+ *   5  two cell-parallel passes, one thread per cell (lz unused; grids
+ *      of more than 65535 planes are launched in chunks of planes);
+ *   6  one cell-parallel pass, the neighbouring H recomputed per cell
+ *      (needs nz <= 65535, else EINVAL).
  * The TMA variants (1, 2, 4) have no FP64 32x16 tile (EINVAL).  A z-walled
  * grid or one with a wall source takes variant 5 only (EINVAL otherwise;
  * fdtd_autotune then times the ty of variant 5 only).
@@ -281,7 +282,7 @@ void fdtd_destroy_grid(fdtd_grid* g);
  * Three engines:
  *   FDTD_BATCH_CELL (default): per step one launch of the H pass and one of
  *     the E pass over the cell blocks of every grid (the arithmetic of
- *     tile variant 5, bit for bit); needs nz <= 65535 on every grid.
+ *     tile variant 5, bit for bit).
  *   FDTD_BATCH_PERSISTENT: one persistent kernel launch per step walks every
  *     grid's (tile, z segment) blocks with the TMA-staged one-pass step (the
  *     arithmetic of tile variant 1, bit for bit); z-periodic grids without a
@@ -294,7 +295,6 @@ void fdtd_destroy_grid(fdtd_grid* g);
  *     on nz).  Its barrier waits are bounded: an expired wait raises
  *     the batch's error word and every CTA returns (ETIMEOUT from
  *     fdtd_batch_sync).
- * A batch with a grid of nz > 65535 starts on FDTD_BATCH_PERSISTENT_CELL.
  * `dev_table` is a device buffer of fdtd_batch_required_bytes bytes
  * (256-byte aligned), owned by the caller and alive until
  * fdtd_batch_destroy; `stream` is a cudaStream_t.  While a grid belongs to
@@ -305,8 +305,8 @@ void fdtd_destroy_grid(fdtd_grid* g);
  * whose copy parity no longer matches the batch's (fdtd_load_state of
  * another parity) makes fdtd_batch_step return ESTATE.
  * fdtd_batch_set_engine switches engines between steps (EINVAL for an
- * unknown engine, the cell engine with nz > 65535, or the persistent TMA
- * engine with z walls or a wall source).  fdtd_batch_sync
+ * unknown engine, or the persistent TMA engine with z walls or a wall
+ * source).  fdtd_batch_sync
  * waits for the stream and reports CUDA errors or an expired device wait
  * (ETIMEOUT).  fdtd_batch_work_items: blocks per step of the current engine. */
 enum { FDTD_BATCH_PERSISTENT = 0, FDTD_BATCH_CELL = 1, FDTD_BATCH_PERSISTENT_CELL = 2 };

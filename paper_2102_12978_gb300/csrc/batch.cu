@@ -372,16 +372,29 @@ cudaError_t cell_launch_grid(fdtd_batch* b, int q, int parity, int step, cudaStr
         reinterpret_cast<const StepTime<real>*>(static_cast<char*>(b->table) + b->times_off);
     const int index = step * int(b->grids.size()) + q;
     const dim3 block(32, kCellTY);
-    const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + kCellTY - 1) / kCellTY, g->desc.nz);
-    const StepArgs<real> a = make_args<real>(g, parity);
+    constexpr int kMaxPlanes = 65535;   // gridDim.z limit: taller grids go in chunks of planes
+    const int nz = g->desc.nz, nchunk = (nz + kMaxPlanes - 1) / kMaxPlanes;
+    StepArgs<real> a = make_args<real>(g, parity);
     const bool wall = needs_cell_passes(g);   // z walls or a wall sheet
-    if (wall) yee_h_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
-    else yee_h_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (wall) yee_e_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
-    else yee_e_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
-    return cudaGetLastError();
+    for (int c = 0; c < nchunk; ++c) {
+        a.kbase = c * kMaxPlanes;
+        const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + kCellTY - 1) / kCellTY,
+                        nz - a.kbase < kMaxPlanes ? nz - a.kbase : kMaxPlanes);
+        if (wall) yee_h_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+        else yee_h_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    for (int c = nchunk - 1; c >= 0; --c) {
+        a.kbase = c * kMaxPlanes;
+        const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + kCellTY - 1) / kCellTY,
+                        nz - a.kbase < kMaxPlanes ? nz - a.kbase : kMaxPlanes);
+        if (wall) yee_e_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+        else yee_e_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t cell_launch_grid_any(fdtd_batch* b, int q, int parity, int step, cudaStream_t s)
@@ -640,9 +653,6 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->times_off = times_offset(n, prec);
     b->bar_off = bar_offset(n, prec);
     for (int e = 0; e < 2; ++e) b->built[e][0] = b->built[e][1] = false;
-    bool need_persistent = false;   // the graph cell engine takes nz <= 65535
-    for (int q = 0; q < n; ++q) need_persistent |= grids[q]->desc.nz > 65535;
-    if (need_persistent) b->engine = FDTD_BATCH_PERSISTENT_CELL;
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
     st = cuda_check(cudaStreamSynchronize(b->stream), "batch create");
@@ -671,9 +681,6 @@ fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine)
     if (!b) return fail(FDTD_EINVAL, "null batch");
     if (engine != FDTD_BATCH_PERSISTENT && engine != FDTD_BATCH_CELL && engine != FDTD_BATCH_PERSISTENT_CELL)
         return fail(FDTD_EINVAL, "engine %d is not FDTD_BATCH_PERSISTENT, _CELL or _PERSISTENT_CELL", engine);
-    if (engine == FDTD_BATCH_CELL)
-        for (fdtd_grid* g : b->grids)
-            if (g->desc.nz > 65535) return fail(FDTD_EINVAL, "the cell engine takes nz <= 65535");
     if (engine == FDTD_BATCH_PERSISTENT)
         for (fdtd_grid* g : b->grids)
             if (needs_cell_passes(g))

@@ -123,7 +123,6 @@ fdtd_status validate(const fdtd_grid_desc* d)
     if (d->z_boundary == FDTD_Z_WALLS) {
         if (d->npml_z < 0 || 2 * d->npml_z + 2 > d->nz)
             return fail(FDTD_EINVAL, "npml_z=%d must be >= 0 with 2*npml_z + 2 <= nz=%d", d->npml_z, d->nz);
-        if (d->nz > 65535) return fail(FDTD_EINVAL, "a z-walled grid takes nz <= 65535");
     }
     if ((d->npml > 0 || d->npml_z > 0) &&
         !(d->pml_order >= 0.0 && d->pml_sigma_scale >= 0.0 && d->pml_kappa_max >= 1.0 && d->pml_alpha_max >= 0.0))
@@ -269,6 +268,7 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
     a.wcoefr = !g->has_wall ? nullptr
                : sizeof(real) == 8 ? static_cast<const void*>(A + L.wcoef) : static_cast<const void*>(A + L.wcoef32);
     a.wplane = g->has_wall ? g->wall.plane : -1;
+    a.kbase = 0;
     return a;
 }
 
@@ -365,25 +365,14 @@ cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConf
     }
 }
 
-// Default tile: the cell-parallel two-pass step on 32 x 4 blocks; grids with
-// more than 65535 planes take the one-pass TMA step on 32 x 8 tiles, with z
-// split into segments so that about four CTAs per SM are in flight (152 SMs
-// on GB300).
+// Default tile: the cell-parallel two-pass step on 32 x 4 blocks (the
+// fastest on GB300 for every grid measured; grids of more than 65535 planes
+// are launched in chunks of planes).
 TileConfig default_tile(const fdtd_grid_desc& d, int sm_count)
 {
+    (void)sm_count;
     TileConfig tc;
-    if (d.nz <= 65535) {
-        tc.variant = 5; tc.tx = 32; tc.ty = 4; tc.lz = d.nz;
-        return tc;
-    }
-    tc.variant = 1; tc.tx = 32; tc.ty = 8;
-    long tiles = long((d.nx + 31) / 32) * long((d.ny + 7) / 8);
-    long want = 4L * (sm_count > 0 ? sm_count : 152);
-    long segs = (want + tiles - 1) / tiles;
-    if (segs < 1) segs = 1;
-    long max_segs = d.nz / 8 > 0 ? d.nz / 8 : 1;
-    if (segs > max_segs) segs = max_segs;
-    tc.lz = int((d.nz + segs - 1) / segs);
+    tc.variant = 5; tc.tx = 32; tc.ty = 4; tc.lz = d.nz;
     return tc;
 }
 
@@ -861,7 +850,7 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz)
     if (!g) return fail(FDTD_EINVAL, "null grid");
     if (variant < 0 || variant > 6) return fail(FDTD_EINVAL, "variant=%d not in {0, ..., 6}", variant);
     if (ty != 4 && ty != 8 && ty != 16) return fail(FDTD_EINVAL, "ty=%d not in {4, 8, 16}", ty);
-    if (variant >= 5 && g->desc.nz > 65535) return fail(FDTD_EINVAL, "variant %d takes nz <= 65535", variant);
+    if (variant == 6 && g->desc.nz > 65535) return fail(FDTD_EINVAL, "variant 6 takes nz <= 65535");
     if (variant != 5 && needs_cell_passes(g))
         return fail(FDTD_EINVAL, "a grid with z walls or a wall source takes tile variant 5");
     if ((variant == 1 || variant == 2 || variant == 4) && ty == 16 && g->desc.precision == FDTD_F64)
@@ -899,7 +888,7 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     if (g->desc.precision == FDTD_F64)
         cands = {{6, 4}, {6, 8}, {6, 16}, {5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {3, 4}, {3, 8}, {2, 8}, {2, 4},
                  {1, 4}, {1, 8}, {0, 4}, {0, 8}};
-    if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 6);
+    if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 3);   // variant 6 takes nz <= 65535
     if (needs_cell_passes(g)) cands = {{5, 4}, {5, 8}, {5, 16}};
     const int nz = g->desc.nz;
     std::vector<int> lzs;

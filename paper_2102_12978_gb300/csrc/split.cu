@@ -112,24 +112,36 @@ static cudaError_t launch_step_cell(const fdtd_grid* g, int cur, long long n, cu
 
 // Cell-parallel passes: yee_h_cell then yee_e_cell (with the fluence term),
 // or yee_h_cell_w then yee_e_cell_w on grids with z walls or a wall sheet;
-// 32 x TY threads, one cell each, one plane per grid z index.
+// 32 x TY threads, one cell each, one plane per grid z index.  Grids of more
+// than kMaxPlanes planes launch each pass in chunks of planes (the H pass's
+// chunks in order, the E pass's in reverse, as its blocks run).
+constexpr int kMaxPlanes = 65535;   // gridDim.z limit
 template <typename real, int TY>
 static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStream_t s, cudaEvent_t mid)
 {
-    if (g->desc.nz > 65535) return cudaErrorInvalidConfiguration;
     const StepTime<real> t = step_time<real>(g->srct, g->has_wall ? &g->wallt : nullptr, g->dt, n);
+    const int nz = g->desc.nz, nchunk = (nz + kMaxPlanes - 1) / kMaxPlanes;
     dim3 block(32, TY);
-    dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, g->desc.nz);
-    const StepArgs<real> a = make_args<real>(g, cur);
+    StepArgs<real> a = make_args<real>(g, cur);
     const bool wall = needs_cell_passes(g);   // z walls or a wall sheet: the *_w kernels
-    if (wall) yee_h_cell_w<real, TY><<<grid, block, 0, s>>>(a, t);
-    else yee_h_cell<real, TY><<<grid, block, 0, s>>>(a, t);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    for (int c = 0; c < nchunk; ++c) {
+        a.kbase = c * kMaxPlanes;
+        dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, nz - a.kbase < kMaxPlanes ? nz - a.kbase : kMaxPlanes);
+        if (wall) yee_h_cell_w<real, TY><<<grid, block, 0, s>>>(a, t);
+        else yee_h_cell<real, TY><<<grid, block, 0, s>>>(a, t);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (mid) cudaEventRecord(mid, s);
-    if (wall) yee_e_cell_w<real, TY><<<grid, block, 0, s>>>(a, t);
-    else yee_e_cell<real, TY><<<grid, block, 0, s>>>(a, t);
-    return cudaGetLastError();
+    for (int c = nchunk - 1; c >= 0; --c) {
+        a.kbase = c * kMaxPlanes;
+        dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, nz - a.kbase < kMaxPlanes ? nz - a.kbase : kMaxPlanes);
+        if (wall) yee_e_cell_w<real, TY><<<grid, block, 0, s>>>(a, t);
+        else yee_e_cell<real, TY><<<grid, block, 0, s>>>(a, t);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_split(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s,

@@ -335,14 +335,16 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
     }
 }
 
-// Grid: (ceil(nx/32), ceil(ny/TY), nz) CTAs of 32 x TY threads, one cell each.
+// Grid: (ceil(nx/32), ceil(ny/TY), planes) CTAs of 32 x TY threads, one cell
+// each, for planes a.kbase .. a.kbase + gridDim.z - 1 (all planes, or one
+// chunk of at most 65535).
 // The H pass takes the blocks in launch order, the E pass in reverse order:
 // it starts on the planes the H pass touched last, which are still in L2, and
 // ends where the next H pass starts.
 template <typename real, int TY, bool WALL>
 __device__ __forceinline__ void h_block(const StepArgs<real>& a, Cpx<real> th)
 {
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = blockIdx.z;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * TY, k = a.kbase + int(blockIdx.z);
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (cell_gen_h<real, TY>(a, i0, j0) || (WALL && cell_gen_z(a, k))) h_cell<real, true, WALL>(a, th, i, j, k);
     else h_cell<real, false, WALL>(a, th, i, j, k);
@@ -352,7 +354,7 @@ template <typename real, int TY, bool WALL>
 __device__ __forceinline__ void e_block(const StepArgs<real>& a, Cpx<real> te, Cpx<real> tw)
 {
     const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
-    const int k = gridDim.z - 1 - blockIdx.z;
+    const int k = a.kbase + int(gridDim.z - 1 - blockIdx.z);
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (cell_gen_e<real, TY>(a, i0, j0) || (WALL && cell_gen_z(a, k))) e_cell<real, true, WALL>(a, te, tw, i, j, k);
     else e_cell<real, false, WALL>(a, te, tw, i, j, k);

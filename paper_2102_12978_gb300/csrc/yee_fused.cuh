@@ -85,6 +85,9 @@ struct StepArgs {
     // wall source (Section 2): E_x on plane wplane += Re{ W[col] tw }
     const void* wcoefr;      // [ny][nx] in the field precision, or null
     int wplane;
+    // cell passes: plane of blockIdx.z = 0 (grids of more than 65535 planes
+    // are launched in chunks of planes)
+    int kbase;
 };
 
 // Time factor of the soft source at time t: cos / sin of the phase

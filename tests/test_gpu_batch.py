@@ -164,24 +164,26 @@ def test_persistent_cell_engine_many_uneven_grids(precision):
     b.close()
 
 
-def test_tall_grid_batch_starts_on_the_persistent_cell_engine():
-    """A grid of 65540 planes (beyond the graph cell engine's 65535) makes
-    the batch start on the persistent cell engine, which decodes the plane
-    of each block from its list index: 6 FP64 steps from a seeded random
-    state against the oracle."""
+def test_grid_taller_than_one_launch():
+    """A grid of 65540 planes, more than one launch's 65535 CTA rows along
+    z: tile variant 5 launches its passes in two chunks of planes.  6 FP64
+    steps from a seeded random state against the oracle; the graph cell and
+    persistent cell batch engines then repeat them bit for bit."""
     w = W.small(nx=8, ny=8, nz=65540, npml=2, steps=6)
     init = W.random_state((w.nz, w.ny, w.nx), seed=W.SEED + 21)
     init[1][:, :, 0] = 0; init[2][:, :, 0] = 0     # tangential E on the i = 0 wall
     init[0][:, 0, :] = 0; init[2][:, 0, :] = 0     # and on the j = 0 wall
-    g = gpu_grid(w, "f64", source=False, fluence=False)
-    for c in range(6):
-        g.set_field(c, init[c])
-    b = fdtd.Batch([g])
-    assert b.engine == fdtd.BATCH_PERSISTENT_CELL
-    with pytest.raises(fdtd.FDTDError):
-        b.set_engine(fdtd.BATCH_CELL)
-    b.step(w.steps)
-    b.sync()
+
+    def fresh():
+        g = gpu_grid(w, "f64", source=False, fluence=False)
+        for c in range(6):
+            g.set_field(c, init[c])
+        return g
+
+    g = fresh()
+    assert g.tile()[0] == 5
+    g.step(w.steps)
+    g.sync()
     og = oracle_grid(w)
     st = oracle.State(og, fluence=False)
     for c in range(3):
@@ -190,4 +192,11 @@ def test_tall_grid_batch_starts_on_the_persistent_cell_engine():
     oracle.run(og, None, st, w.steps)
     for c, ref in enumerate(st.fields()):
         assert rel_l2(host(g.field(c)), ref) <= 1e-11, c
-    b.close()
+    for engine in (fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT_CELL):
+        gb = fresh()
+        b = fdtd.Batch([gb], engine=engine)
+        b.step(w.steps)
+        b.sync()
+        for c in range(6):
+            assert np.array_equal(host(gb.field(c)), host(g.field(c))), (engine, c)
+        b.close()
