@@ -18,6 +18,15 @@
 // omega t)} of a plane is the product of a per-plane table e^{i beta z_k}
 // and the per-step factor f e^{-i omega t} evaluated on the host in FP64,
 // both in the field precision.
+//
+// Instantiations: yee_h_cell / yee_e_cell for z-periodic grids; *_w with the
+// z walls, their z CPML shell and the Bessel-Gauss wall sheet of Section 2
+// compiled in (kept apart, so that the periodic kernels carry none of it);
+// *_t / *_wt read the step's time factors from a device table (the batched
+// graph).  The cell functions also serve the persistent batch kernel, which
+// reads fields on the coherent path (template parameter NC = false).  A
+// launch covers at most 65535 planes; taller grids are launched in chunks
+// starting at plane a.kbase.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
