@@ -197,7 +197,10 @@ fdtd_status fdtd_wall_coefficients(const fdtd_grid_desc* d, const fdtd_wall_desc
  * step n: H^{n+1/2} (with CPML psi) -> H soft source at (n+1/2) dt ->
  * fluence += |E^n x (H^{n-1/2}+H^{n+1/2})/2| dt at cell centres ->
  * E^{n+1} (with CPML psi) -> E soft source at (n+1) dt (Eq. 13) -> wall
- * source at (n+1) dt.  One or two kernel launches per step (tile variant). */
+ * source at (n+1) dt.  One or two kernel launches per step (tile variant).
+ * Small grids, whose passes take a few microseconds, are bound by the cost
+ * of those launches; a batch of one grid (fdtd_batch_create with n = 1)
+ * replays 64 steps from one CUDA graph instead, with the same results. */
 fdtd_status fdtd_step(fdtd_grid* g, int nsteps);
 
 /* Copy the fluence (nz*ny*nx doubles, x fastest, dense) to dst (device if
