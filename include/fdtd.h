@@ -29,6 +29,9 @@
  *   - Work is queued on the caller's CUDA stream (a cudaStream_t passed as
  *     void*; NULL = legacy default stream).  Calls that return data to the host
  *     synchronise that stream and report asynchronous CUDA errors.
+ *   - A grid belongs to the device that was current at fdtd_create_grid.
+ *     Every call that queues work for a grid, or reads or writes its memory,
+ *     returns FDTD_EINVAL and queues nothing while another device is current.
  *   - Field storage: structure of arrays, one array per component, x fastest,
  *     rows padded to a pitch of 32 elements; two copies of E, H and the
  *     H-side CPML auxiliaries are kept (ping-pong), because the fused step
@@ -167,8 +170,10 @@ size_t fdtd_required_bytes(const fdtd_grid_desc* d);
  * at least fdtd_required_bytes(d) bytes, 256-byte aligned, owned by the caller;
  * `stream` is a cudaStream_t (or NULL).  Zeroes the fields, CPML auxiliaries
  * and fluence, uploads the CPML profiles (Section 4), and sets the step
- * counter to 0.  Returns EINVAL on a bad descriptor (Courant > 1, CPML wider
- * than a quarter of the box, ...), ENOMEM if arena_bytes is too small. */
+ * counter to 0.  Also makes the fixed staging array of fdtd_fluence_noalloc
+ * resident on the device (16 MiB, once per device; see that call).  Returns
+ * EINVAL on a bad descriptor (Courant > 1, CPML wider than a quarter of the
+ * box, ...), ENOMEM if arena_bytes is too small. */
 fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_bytes,
                              void* stream, fdtd_grid** out);
 
@@ -270,6 +275,12 @@ fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_pa
  * the device context stays usable.  kind 0 clears a pending fault; a fault
  * applies to one step only.  EINVAL for another kind. */
 fdtd_status fdtd_debug_inject_fault(fdtd_grid* g, int kind);
+
+/* Test hook: record `device` as the device the grid lives on, so that a test
+ * on one GPU can check that every entry point refuses (FDTD_EINVAL, nothing
+ * queued) a grid whose device is not the current one.  The grid is unusable
+ * until its own device is recorded again.  EINVAL for device < 0. */
+fdtd_status fdtd_debug_set_device(fdtd_grid* g, int device);
 fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz);
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state);
 
@@ -381,13 +392,19 @@ void fdtd_adjoint_destroy(fdtd_adjoint* a);
  * example inside a hook that must not grow a caching allocator, or on a
  * system whose device memory is reserved up front).  It returns exactly what
  * fdtd_fluence returns, but stages the export in a fixed 16 MiB array
- * compiled into the library (2^21 doubles, present on every device that
- * loads the library until the process exits) instead of the grid's arena,
+ * compiled into the library (2^21 doubles) instead of the grid's arena,
  * and calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The array becomes resident on a device when the first grid is created
+ *     there: fdtd_create_grid looks up its device address (under lazy module
+ *     loading that lookup loads the array's module, which takes the 16 MiB),
+ *     and it stays resident until the process exits.  The read-out itself
+ *     loads nothing and only uses the address cached by fdtd_create_grid.
+ *     Every grid creation on the device refreshes that address, so after a
+ *     cudaDeviceReset (which ends every grid of the device) the library is
+ *     used again by creating new grids.
  *   - Grids with more than fdtd_fluence_noalloc_max_cells() cells are
- *     rejected with FDTD_EINVAL.
- *   - The first call on a device looks up the array's device address; make
- *     that first call before any stream capture.
+ *     rejected with FDTD_EINVAL, as is a call made while a device other than
+ *     the grid's is current.
  *   - All calls share the one array, which keeps the last call's contents
  *     (every element read back is written by the call itself, so nothing has
  *     to be cleared first); calls that overlap on the GPU (different streams

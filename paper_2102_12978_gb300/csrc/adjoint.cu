@@ -473,6 +473,8 @@ fdtd_status fdtd_adjoint_create(fdtd_grid* g, int component, const int64_t* prob
     if (reinterpret_cast<uintptr_t>(arena) % 256 != 0) return fail(FDTD_EINVAL, "arena not 256-byte aligned");
     if (needs_cell_passes(g)) return fail(FDTD_EINVAL, "no adjoint for grids with z walls or a wall source");
     if (!g->has_source) return fail(FDTD_ESTATE, "set the antenna source before creating its adjoint");
+    const fdtd_status dev_st = check_device(g, "fdtd_adjoint_create");
+    if (dev_st != FDTD_OK) return dev_st;
     fdtd_adjoint* a = new (std::nothrow) fdtd_adjoint();
     if (!a) return fail(FDTD_ENOMEM, "host allocation failed");
     size_t total = 0;
@@ -521,6 +523,8 @@ fdtd_status fdtd_adjoint_create(fdtd_grid* g, int component, const int64_t* prob
 fdtd_status fdtd_adjoint_reset(fdtd_adjoint* a, int64_t n_end)
 {
     if (!a || n_end < 0) return fail(FDTD_EINVAL, "invalid argument");
+    const fdtd_status dev_st = check_device(a->g, "fdtd_adjoint_reset");
+    if (dev_st != FDTD_OK) return dev_st;
     a->n = n_end;
     a->cur = 0;
     return cuda_check(cudaMemsetAsync(a->arena, 0, a->dyn_bytes, a->g->stream), "reset adjoint");
@@ -529,6 +533,8 @@ fdtd_status fdtd_adjoint_reset(fdtd_adjoint* a, int64_t n_end)
 fdtd_status fdtd_probe_read(fdtd_adjoint* a, void* dev_out)
 {
     if (!a || !dev_out) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(a->g, "fdtd_probe_read");
+    if (dev_st != FDTD_OK) return dev_st;
     if (a->nprobes == 0) return FDTD_OK;
     cudaError_t e = a->g->desc.precision == FDTD_F64 ? launch_gather<double>(a, dev_out) : launch_gather<float>(a, dev_out);
     return cuda_check(e, "probe gather");
@@ -547,6 +553,8 @@ fdtd_status fdtd_adjoint_step(fdtd_adjoint* a, int nsteps, const void* dLdE, int
 static fdtd_status adjoint_steps(fdtd_adjoint* a, int nsteps, const void* dLdE, int64_t ld)
 {
     if (!a || nsteps < 0) return fail(FDTD_EINVAL, "invalid argument");
+    const fdtd_status dev_st = check_device(a->g, "fdtd_adjoint_step");
+    if (dev_st != FDTD_OK) return dev_st;
     if (nsteps > a->n) return fail(FDTD_EINVAL, "cannot step the adjoint before forward step 0");
     const size_t eb = a->g->L.elem;
     for (int s = 0; s < nsteps; ++s) {
@@ -569,6 +577,8 @@ int64_t fdtd_adjoint_position(const fdtd_adjoint* a) { return a ? a->n : -1; }
 fdtd_status fdtd_adjoint_get(fdtd_adjoint* a, int component, void* dst)
 {
     if (!a || !dst || component < 0 || component > 5) return fail(FDTD_EINVAL, "invalid argument");
+    const fdtd_status dev_st = check_device(a->g, "fdtd_adjoint_get");
+    if (dev_st != FDTD_OK) return dev_st;
     const fdtd_grid_desc& d = a->g->desc;
     const size_t b = a->g->L.elem;
     const size_t off = component < 3 ? a->e[a->cur][component] : a->h[a->cur][component - 3];
@@ -583,6 +593,8 @@ fdtd_status fdtd_adjoint_get(fdtd_adjoint* a, int component, void* dst)
 fdtd_status fdtd_adjoint_gradient(fdtd_adjoint* a, double* dLdw_amp, double* dLdw_phase, int on_device)
 {
     if (!a || !dLdw_amp || !dLdw_phase) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(a->g, "fdtd_adjoint_gradient");
+    if (dev_st != FDTD_OK) return dev_st;
     fdtd_grid* g = a->g;
     const int ncol = g->desc.nx * g->desc.ny;
     char* G = static_cast<char*>(g->arena);

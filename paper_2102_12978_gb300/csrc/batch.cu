@@ -637,6 +637,8 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
         if (!grids[q]) return fail(FDTD_EINVAL, "null grid %d", q);
         if (grids[q]->desc.precision != prec) return fail(FDTD_EINVAL, "mixed precisions in one batch");
         if (grids[q]->cur != grids[0]->cur) return fail(FDTD_ESTATE, "grids must start from the same copy parity");
+        const fdtd_status dev_st = check_device(grids[q], "fdtd_batch_create");
+        if (dev_st != FDTD_OK) return dev_st;
     }
     if (table_bytes < fdtd_batch_required_bytes(n, prec))
         return fail(FDTD_ENOMEM, "batch table of %zu bytes, %zu needed", table_bytes, fdtd_batch_required_bytes(n, prec));
@@ -726,6 +728,8 @@ fdtd_status fdtd_batch_step(fdtd_batch* b, int nsteps)
 static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps)
 {
     if (!b || nsteps < 0) return fail(FDTD_EINVAL, "invalid argument");
+    const fdtd_status dev_st = check_device(b->grids[0], "fdtd_batch_step");
+    if (dev_st != FDTD_OK) return dev_st;
     for (fdtd_grid* g : b->grids)
         if (g->cur != b->cur) return fail(FDTD_ESTATE, "a batched grid was stepped outside the batch");
     const bool cell = b->engine == FDTD_BATCH_CELL;
@@ -796,6 +800,8 @@ static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps)
 fdtd_status fdtd_batch_sync(fdtd_batch* b)
 {
     if (!b) return fail(FDTD_EINVAL, "null batch");
+    const fdtd_status dev_st = check_device(b->grids[0], "fdtd_batch_sync");
+    if (dev_st != FDTD_OK) return dev_st;
     fdtd_status st = cuda_check(cudaStreamSynchronize(b->stream), "batch synchronize");
     if (st != FDTD_OK) return st;
     BatchHeader h;

@@ -41,6 +41,16 @@ fdtd_status cuda_check(cudaError_t e, const char* what)
     return fail(FDTD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+fdtd_status check_device(const fdtd_grid* g, const char* what)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(e, what);
+    if (dev != g->device)
+        return fail(FDTD_EINVAL, "%s: the grid lives on device %d but device %d is current", what, g->device, dev);
+    return FDTD_OK;
+}
+
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Arena layout: the dynamic state (fields, CPML psi, fluence) first, then the
@@ -436,8 +446,13 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->fault = 0;
     for (int c = 0; c < 6; ++c) g->counts[c] = 0;
     int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    st = cuda_check(cudaGetDevice(&dev), "current device");
+    if (st != FDTD_OK) { delete g; return st; }
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     g->sm_count = sms;
+    g->device = dev;
+    st = noalloc_prepare(dev);
+    if (st != FDTD_OK) { delete g; return st; }
     g->tile = default_tile(*d, sms);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 3; ++b) g->maps_ok[a][b] = g->hmaps_ok[a][b] = false;
@@ -480,6 +495,8 @@ static fdtd_status not_batched(const fdtd_grid* g, const char* what)
 fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
 {
     if (!g || !s) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_set_annulus_source");
+    if (dev_st != FDTD_OK) return dev_st;
     if (g->batch_refs > 0) return not_batched(g, "fdtd_set_annulus_source");
     const fdtd_grid_desc& d = g->desc;
     fdtd_status vst = validate_source(d, s);
@@ -596,6 +613,8 @@ static void wall_tables(const fdtd_grid_desc& d, const fdtd_wall_desc* w, std::v
 fdtd_status fdtd_set_wall_source(fdtd_grid* g, const fdtd_wall_desc* w)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
+    const fdtd_status dev_st = check_device(g, "fdtd_set_wall_source");
+    if (dev_st != FDTD_OK) return dev_st;
     if (g->batch_refs > 0) return not_batched(g, "fdtd_set_wall_source");
     if (!w) {
         g->has_wall = false;
@@ -656,6 +675,8 @@ fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
     if (nsteps < 0) return fail(FDTD_EINVAL, "nsteps < 0");
+    const fdtd_status dev_st = check_device(g, "fdtd_step");
+    if (dev_st != FDTD_OK) return dev_st;
     if (g->batch_refs > 0) return not_batched(g, "fdtd_step");
     nvtxRangePushA("fdtd_step");
     for (int s = 0; s < nsteps; ++s) {
@@ -677,9 +698,18 @@ fdtd_status fdtd_debug_inject_fault(fdtd_grid* g, int kind)
     return FDTD_OK;
 }
 
+fdtd_status fdtd_debug_set_device(fdtd_grid* g, int device)
+{
+    if (!g || device < 0) return fail(FDTD_EINVAL, "invalid argument");
+    g->device = device;
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_passes, int* n_passes)
 {
     if (!g || !pass_ms || !n_passes || nsteps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_step_timed");
+    if (dev_st != FDTD_OK) return dev_st;
     if (g->batch_refs > 0) return not_batched(g, "fdtd_step_timed");
     const int np = passes_per_step(g->tile);
     if (max_passes < np) return fail(FDTD_EINVAL, "max_passes=%d < %d kernels per step", max_passes, np);
@@ -714,6 +744,8 @@ fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_pa
 fdtd_status fdtd_sync(fdtd_grid* g)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
+    const fdtd_status dev_st = check_device(g, "fdtd_sync");
+    if (dev_st != FDTD_OK) return dev_st;
     fdtd_status st = cuda_check(cudaStreamSynchronize(g->stream), "stream synchronize");
     if (st != FDTD_OK) return st;
     st = cuda_check(cudaGetLastError(), "pending CUDA error");
@@ -733,6 +765,8 @@ fdtd_status fdtd_sync(fdtd_grid* g)
 fdtd_status fdtd_fluence(fdtd_grid* g, void* dst, int on_device, int reset)
 {
     if (!g || !dst) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_fluence");
+    if (dev_st != FDTD_OK) return dev_st;
     if (!g->desc.fluence) return fail(FDTD_ESTATE, "grid created without a fluence accumulator");
     const fdtd_grid_desc& d = g->desc;
     char* A = static_cast<char*>(g->arena);
@@ -758,6 +792,8 @@ fdtd_status fdtd_fluence(fdtd_grid* g, void* dst, int on_device, int reset)
 fdtd_status fdtd_get_field(fdtd_grid* g, int component, void* dst, int on_device)
 {
     if (!g || !dst) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_get_field");
+    if (dev_st != FDTD_OK) return dev_st;
     if (component < 0 || component > 5) return fail(FDTD_EINVAL, "component %d out of range", component);
     const fdtd_grid_desc& d = g->desc;
     const size_t b = g->L.elem;
@@ -774,6 +810,8 @@ fdtd_status fdtd_get_field(fdtd_grid* g, int component, void* dst, int on_device
 fdtd_status fdtd_set_field(fdtd_grid* g, int component, const void* src, int on_device)
 {
     if (!g || !src) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_set_field");
+    if (dev_st != FDTD_OK) return dev_st;
     if (component < 0 || component > 5) return fail(FDTD_EINVAL, "component %d out of range", component);
     const fdtd_grid_desc& d = g->desc;
     const size_t b = g->L.elem;
@@ -796,6 +834,8 @@ size_t fdtd_state_bytes(const fdtd_grid* g)
 fdtd_status fdtd_save_state(fdtd_grid* g, void* dev_dst)
 {
     if (!g || !dev_dst) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_save_state");
+    if (dev_st != FDTD_OK) return dev_st;
     int64_t hdr[4] = {g->step, g->cur, 0x46445444, 0};
     char* D = static_cast<char*>(dev_dst);
     fdtd_status st = cuda_check(cudaMemcpyAsync(D, g->arena, g->L.dynamic_bytes, cudaMemcpyDeviceToDevice,
@@ -810,6 +850,8 @@ fdtd_status fdtd_save_state(fdtd_grid* g, void* dev_dst)
 fdtd_status fdtd_load_state(fdtd_grid* g, const void* dev_src)
 {
     if (!g || !dev_src) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_load_state");
+    if (dev_st != FDTD_OK) return dev_st;
     int64_t hdr[4];
     const char* S = static_cast<const char*>(dev_src);
     fdtd_status st = cuda_check(cudaMemcpyAsync(hdr, S + g->L.dynamic_bytes, sizeof(hdr), cudaMemcpyDeviceToHost,
@@ -878,6 +920,8 @@ fdtd_status fdtd_get_tile(const fdtd_grid* g, int* variant, int* ty, int* lz)
 fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
 {
     if (!g || !scratch_state || steps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_autotune");
+    if (dev_st != FDTD_OK) return dev_st;
     if (g->batch_refs > 0) return not_batched(g, "fdtd_autotune");
     g->fault = 0;
     fdtd_status st = fdtd_save_state(g, scratch_state);

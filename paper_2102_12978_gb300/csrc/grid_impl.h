@@ -47,6 +47,14 @@ fdtd_status fail(fdtd_status st, const char* fmt, ...);
 fdtd_status cuda_check(cudaError_t e, const char* what);
 bool compute_layout(const fdtd_grid_desc& d, Layout& L);
 fdtd_status validate(const fdtd_grid_desc* d);
+// EINVAL unless the current CUDA device is the one the grid was created on
+// (every entry point that queues work for a grid or reads its memory checks
+// this first: the grid's arena and stream belong to that device).
+fdtd_status check_device(const fdtd_grid* g, const char* what);
+// Looks up (again) the device address of the no-allocation read-out's fixed
+// staging array on the current device.  Called by fdtd_create_grid, where
+// allocating is allowed: the lookup loads the array's module on that device.
+fdtd_status noalloc_prepare(int device);
 double grid_dt(const fdtd_grid_desc& d);
 TileConfig default_tile(const fdtd_grid_desc& d, int sm_count);
 
@@ -66,6 +74,7 @@ struct fdtd_grid {
     fdtd::SrcTime srct;
     int64_t counts[6];
     int sm_count;
+    int device;                 // CUDA device current at fdtd_create_grid
     fdtd::TileConfig tile;
     fdtd::TmaMaps maps[2][3];   // [read copy][ty = 4, 8, 16]
     bool maps_ok[2][3];

@@ -7,7 +7,17 @@
 // front.  fdtd_fluence_noalloc gives them the same result with the staging
 // buffer in a file-scope device array of fixed size instead, and calls no
 // allocating routine.
+//
+// The array belongs to this file's module.  Under CUDA's lazy module loading
+// a module's globals become resident on a device only when the module is first
+// used there, and that load allocates.  So the array's device address is
+// looked up in fdtd_create_grid (noalloc_prepare), where allocating is
+// allowed: from the first grid created on a device on, the array is resident
+// there, and the read-out itself only reads the cached address.
 #include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
 
 #include "../../include/fdtd.h"
 #include "fluence.cuh"
@@ -15,29 +25,28 @@
 
 namespace fdtd {
 
-// Staging area of the export: 16 MiB (2^21 doubles), present on every device
-// that loads the library, for as long as the library stays loaded.
+// Staging area of the export: 16 MiB (2^21 doubles) per device, resident from
+// the first fdtd_create_grid on that device until the process exits.
 constexpr size_t kNoAllocScratchDoubles = size_t(1) << 21;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
-// Device address of the array, looked up once per device (the array's name
-// in host code is only a host-side handle, not a device address).
+// Device address of the array per device (the array's name in host code is
+// only a host-side handle, not a device address).  Written under the mutex
+// by every grid creation on the device, so that a grid created after a
+// cudaDeviceReset refreshes it; read without the lock by the read-out.
 constexpr int kMaxDevices = 64;
-static double* g_scratch_ptr[kMaxDevices] = {nullptr};
+static std::atomic<double*> g_scratch_ptr[kMaxDevices];
+static std::mutex g_scratch_mutex;
 
-static fdtd_status scratch_address(double** out)
+fdtd_status noalloc_prepare(int device)
 {
-    int dev = 0;
-    fdtd_status st = cuda_check(cudaGetDevice(&dev), "current device");
+    if (device < 0 || device >= kMaxDevices)
+        return fail(FDTD_EINVAL, "device %d beyond the %d the library supports", device, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    void* p = nullptr;
+    fdtd_status st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "no-allocation scratch address");
     if (st != FDTD_OK) return st;
-    if (dev < 0 || dev >= kMaxDevices) return fail(FDTD_EINVAL, "device %d beyond the supported %d", dev, kMaxDevices);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        st = cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "scratch symbol address");
-        if (st != FDTD_OK) return st;
-        g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_ptr[dev];
+    g_scratch_ptr[device].store(static_cast<double*>(p), std::memory_order_release);
     return FDTD_OK;
 }
 
@@ -53,14 +62,17 @@ fdtd_status fdtd_fluence_noalloc(fdtd_grid* g, void* dst, int on_device, int res
 {
     if (!g || !dst) return fail(FDTD_EINVAL, "null argument");
     if (!g->desc.fluence) return fail(FDTD_ESTATE, "grid created without a fluence accumulator");
+    const fdtd_status dev_st = check_device(g, "fdtd_fluence_noalloc");
+    if (dev_st != FDTD_OK) return dev_st;
     const fdtd_grid_desc& d = g->desc;
     const size_t cells = size_t(d.nx) * d.ny * d.nz;
     if (cells > kNoAllocScratchDoubles)
         return fail(FDTD_EINVAL, "grid of %zu cells exceeds the %zu-cell limit of fdtd_fluence_noalloc", cells,
                     kNoAllocScratchDoubles);
-    double* scratch = nullptr;
-    fdtd_status st = scratch_address(&scratch);
-    if (st != FDTD_OK) return st;
+    double* scratch = (g->device >= 0 && g->device < kMaxDevices)
+                          ? g_scratch_ptr[g->device].load(std::memory_order_acquire)
+                          : nullptr;
+    if (!scratch) return fail(FDTD_ESTATE, "no staging array on device %d", g->device);
     char* A = static_cast<char*>(g->arena);
     const int blocks = 4 * (g->sm_count > 0 ? g->sm_count : 152);
     if (d.precision == FDTD_F64)
@@ -69,7 +81,7 @@ fdtd_status fdtd_fluence_noalloc(fdtd_grid* g, void* dst, int on_device, int res
     else
         fluence_export<float2><<<blocks, 256, 0, g->stream>>>(reinterpret_cast<const float2*>(A + g->L.fluence),
                                                                scratch, d.nx, d.ny, d.nz, g->L.pitch, 1.0);
-    st = cuda_check(cudaGetLastError(), "fluence_export launch");
+    fdtd_status st = cuda_check(cudaGetLastError(), "fluence_export launch");
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(dst, scratch, cells * 8,
                                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream),

@@ -84,6 +84,7 @@ _SIGS = {
     "fdtd_set_tile": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "fdtd_step_timed": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "fdtd_debug_inject_fault": (C.c_int, [C.c_void_p, C.c_int]),
+    "fdtd_debug_set_device": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
@@ -312,6 +313,10 @@ class Grid:
         """Test hook: the next step of a TMA variant withholds one bulk copy,
         so that its bounded device wait expires (fdtd_debug_inject_fault)."""
         check(lib().fdtd_debug_inject_fault(C.c_void_p(self.handle), int(kind)), "fdtd_debug_inject_fault")
+
+    def debug_set_device(self, device: int):
+        """Test hook: record `device` as the grid's device (fdtd_debug_set_device)."""
+        check(lib().fdtd_debug_set_device(C.c_void_p(self.handle), int(device)), "fdtd_debug_set_device")
 
     def set_tile(self, variant: int, ty: int, lz: int):
         check(lib().fdtd_set_tile(C.c_void_p(self.handle), int(variant), int(ty), int(lz)), "fdtd_set_tile")

@@ -14,6 +14,10 @@ from tests.gpu_cases import gpu_grid, host
 
 pytestmark = pytest.mark.gpu
 
+# components of the adjoint state below this fraction of the state's norm are
+# compared against that fraction of the state's norm
+ADJ_FLOOR = 1e-2
+
 
 @pytest.mark.parametrize("precision,tol_f,tol_g", [("f64", 1e-11, 1e-10), ("f32", 1e-4, 1e-3)])
 def test_adjoint_matches_oracle(precision, tol_f, tol_g):
@@ -40,12 +44,18 @@ def test_adjoint_matches_oracle(precision, tol_f, tol_g):
         if r < window:
             np.add.at(ao.e[1].reshape(-1), probes, dlde[r])
         oracle.adjoint_step(og, src, ao, n, gao, gpo)
-    # errors per component against the norm of the whole adjoint state (a
-    # component can be orders of magnitude smaller than the others)
+    # per-component relative L2; a component whose norm is below FLOOR of the
+    # whole adjoint state's norm is measured against FLOOR x that norm instead
+    # (its rounding comes from the larger components it is coupled to)
     refs = ao.fields()
     total = np.sqrt(sum(float(np.sum(r ** 2)) for r in refs))
-    errs = [float(np.linalg.norm(host(adj.field(c)) - r)) / total for c, r in enumerate(refs)]
-    rels = [rel_l2(host(adj.field(c)), r) for c, r in enumerate(refs)]
+    errs, rels = [], []
+    for c, r in enumerate(refs):
+        diff = float(np.linalg.norm(host(adj.field(c)) - r))
+        errs.append(diff / max(float(np.linalg.norm(r)), ADJ_FLOOR * total))
+        rels.append(rel_l2(host(adj.field(c)), r))
+    print("adjoint per-component rel-L2", precision, rels, "norm / state norm",
+          [float(np.linalg.norm(r)) / total for r in refs])
     assert max(errs) <= tol_f, (errs, rels)
     assert rel_l2(ga, gao) <= tol_g, rel_l2(ga, gao)
     assert rel_l2(gp, gpo) <= tol_g, rel_l2(gp, gpo)

@@ -101,3 +101,35 @@ def test_expired_grid_barrier_reports_timeout():
     with pytest.raises(fdtd.FDTDError) as e:
         fdtd.Batch([gpu_grid(ws[0], "f32")]).inject_fault(5)
     assert e.value.status == fdtd.FDTD_EINVAL
+
+
+def test_entry_points_refuse_a_grid_of_another_device():
+    """A grid belongs to the device current at its creation: with another
+    device current, every call that would queue work for it or touch its
+    memory returns EINVAL and queues nothing (the step counter and the
+    fields stay as they were)."""
+    import torch
+    w = W.small(nx=40, ny=36, nz=8, npml=6, r_center=9.0, steps=4, ramp=1.0)
+    d = fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant, precision="f32")
+    g = fdtd.Grid(d)
+    g.set_source(m=w.m, theta=w.theta, r_center=w.r_center, thickness=w.thickness, ramp=w.ramp)
+    g.step(3)
+    before = g.field(fdtd.EY).clone()
+    dev = torch.cuda.current_device()
+    g.debug_set_device(dev + 1)
+    shape = (w.nz, w.ny, w.nx)
+    out = np.zeros(shape)
+    calls = {
+        "step": lambda: g.step(1),
+        "fluence": lambda: fdtd.fdtd_fluence(g.handle, out.ctypes.data, False, False),
+        "get_field": lambda: fdtd.fdtd_get_field(g.handle, fdtd.EY, out.ctypes.data, False),
+        "set_source": lambda: g.set_source(m=w.m, theta=w.theta, r_center=w.r_center, thickness=w.thickness),
+        "sync": lambda: g.sync(),
+    }
+    for name, call in calls.items():
+        with pytest.raises(fdtd.FDTDError) as e:
+            call()
+        assert e.value.status == fdtd.FDTD_EINVAL, name
+    g.debug_set_device(dev)
+    assert g.n == 3
+    assert torch.equal(g.field(fdtd.EY), before)
