@@ -246,7 +246,13 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
  *   5  two cell-parallel passes, one thread per cell (lz unused; grids
  *      of more than 65535 planes are launched in chunks of planes);
  *   6  one cell-parallel pass, the neighbouring H recomputed per cell
- *      (needs nz <= 65535, else EINVAL).
+ *      (needs nz <= 65535, else EINVAL);
+ *   7  two steps per launch (temporal blocking; FP32 grids, ty 8 or 16,
+ *      else EINVAL; lz unused): windows of 32 x ty columns march along z,
+ *      recomputing two rings of halo columns, so that fields, psi and the
+ *      fluence cross HBM once per two steps.  An odd step count ends with
+ *      one step of variant 5.  The CTAs' shares of the work are balanced on
+ *      per-window cost weights (fdtd_set_balance).
  * The TMA variants (1, 2, 4) have no FP64 32x16 tile (EINVAL).  A z-walled
  * grid or one with a wall source takes variant 5 only (EINVAL otherwise;
  * fdtd_autotune then times the ty of variant 5 only).
@@ -255,6 +261,16 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
  * restoring the state) and keeps the fastest.  Results agree to rounding
  * for every configuration. */
 fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
+
+/* Work-split weights of tile variant 7 (the paper has no counterpart): a
+ * window's plane is estimated to cost 1, plus w_shell if the window holds
+ * CPML shell columns, plus w_antenna if it holds antenna columns, and each
+ * CTA takes a contiguous range of (window, plane) work of equal estimated
+ * cost.  Weights in [0, 16] (else EINVAL); defaults 0.25 and 0.2;
+ * fdtd_autotune times a few pairs and keeps the fastest.  The results do not
+ * depend on the weights, only the time does. */
+fdtd_status fdtd_set_balance(fdtd_grid* g, float w_shell, float w_antenna);
+fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenna);
 
 /* Measurement (the paper has no counterpart): advance `nsteps` steps like
  * fdtd_step and time every kernel launch of a step with CUDA events recorded

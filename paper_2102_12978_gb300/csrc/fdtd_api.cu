@@ -73,10 +73,11 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
             L.phx[buf][c] = take(L.psx_elems * b);
             L.phy[buf][c] = take(L.psy_elems * b);
         }
-    for (int c = 0; c < 2; ++c) {
-        L.pex[c] = take(L.psx_elems * b);
-        L.pey[c] = take(L.psy_elems * b);
-    }
+    for (int buf = 0; buf < 2; ++buf)
+        for (int c = 0; c < 2; ++c) {
+            L.pex[buf][c] = take(L.psx_elems * b);
+            L.pey[buf][c] = take(L.psy_elems * b);
+        }
     const size_t w2z = d.z_boundary == FDTD_Z_WALLS ? 2 * size_t(d.npml_z) : 0;
     L.psz_elems = w2z * ny * p;
     for (int buf = 0; buf < 2; ++buf)
@@ -237,8 +238,10 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
         a.phx_out[c] = reinterpret_cast<real*>(A + L.phx[nxt][c]);
         a.phy_in[c] = reinterpret_cast<const real*>(A + L.phy[cur][c]);
         a.phy_out[c] = reinterpret_cast<real*>(A + L.phy[nxt][c]);
-        a.pex[c] = reinterpret_cast<real*>(A + L.pex[c]);
-        a.pey[c] = reinterpret_cast<real*>(A + L.pey[c]);
+        a.pex[c] = reinterpret_cast<real*>(A + L.pex[g->pe][c]);
+        a.pey[c] = reinterpret_cast<real*>(A + L.pey[g->pe][c]);
+        a.pex_out[c] = reinterpret_cast<real*>(A + L.pex[g->pe ^ 1][c]);
+        a.pey_out[c] = reinterpret_cast<real*>(A + L.pey[g->pe ^ 1][c]);
     }
     a.chx = reinterpret_cast<const real*>(A + L.chx);
     a.cex = reinterpret_cast<const real*>(A + L.cex);
@@ -331,6 +334,7 @@ cudaError_t launch_step(const fdtd_grid* g, int cur, long long n, const TileConf
                         cudaEvent_t mid)
 {
     if (tc.variant != 5 && needs_cell_passes(g)) return cudaErrorInvalidValue;   // z walls / wall source
+    if (tc.variant == 7) return cudaErrorInvalidValue;   // two steps per launch: launch_tb2
     if (tc.variant >= 3) return launch_split(g, cur, n, tc, s, mid);   // variants 3-6
     if (tc.variant == 1) {
         if (g->desc.precision == FDTD_F32) {
@@ -436,7 +440,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->dt = grid_dt(*d);
     g->step = 0;
     g->cur = 0;
+    g->pe = 0;
     g->has_source = false;
+    g->src_gen = 0;
+    g->tb2_key.ry = 0;
     std::memset(&g->srct, 0, sizeof(g->srct));
     g->srct.dt = g->dt;
     g->batch_refs = 0;
@@ -567,6 +574,8 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(g->stream), "upload source");
     if (st != FDTD_OK) return st;
     g->has_source = true;
+    g->hmask = mask;
+    g->src_gen += 1;
     g->src = *s;
     g->src.w_amp = nullptr;
     g->src.w_phase = nullptr;
@@ -667,8 +676,34 @@ fdtd_status fdtd_clear_source(fdtd_grid* g)
     if (!g) return fail(FDTD_EINVAL, "null grid");
     if (g->batch_refs > 0) return not_batched(g, "fdtd_clear_source");
     g->has_source = false;
+    g->hmask.clear();
+    g->src_gen += 1;
     for (int c = 0; c < 6; ++c) g->counts[c] = 0;
     return FDTD_OK;
+}
+
+// Advance the grid by nsteps with tile configuration tc on its stream: pairs
+// of steps as one launch of variant 7, every other step as one launch_step.
+static cudaError_t run_steps(fdtd_grid* g, int nsteps, const TileConfig& tc)
+{
+    int s = 0;
+    if (tc.variant == 7)
+        for (; s + 2 <= nsteps; s += 2) {
+            cudaError_t e = launch_tb2(g, g->cur, g->step, tc, g->stream);
+            if (e != cudaSuccess) return e;
+            g->cur ^= 1;
+            g->pe ^= 1;
+            g->step += 2;
+        }
+    const TileConfig one = single_step_tile(tc);
+    for (; s < nsteps; ++s) {
+        cudaError_t e = launch_step(g, g->cur, g->step, one, g->stream);
+        g->fault = 0;
+        if (e != cudaSuccess) return e;
+        g->cur ^= 1;
+        g->step += 1;
+    }
+    return cudaSuccess;
 }
 
 fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
@@ -679,15 +714,10 @@ fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
     if (dev_st != FDTD_OK) return dev_st;
     if (g->batch_refs > 0) return not_batched(g, "fdtd_step");
     nvtxRangePushA("fdtd_step");
-    for (int s = 0; s < nsteps; ++s) {
-        cudaError_t e = launch_step(g, g->cur, g->step, g->tile, g->stream);
-        g->fault = 0;
-        if (e != cudaSuccess) { nvtxRangePop(); return cuda_check(e, "step launch"); }
-        g->cur ^= 1;
-        g->step += 1;
-    }
+    const cudaError_t e = run_steps(g, nsteps, g->tile);
+    g->fault = 0;
     nvtxRangePop();
-    return FDTD_OK;
+    return cuda_check(e, "step launch");
 }
 
 fdtd_status fdtd_debug_inject_fault(fdtd_grid* g, int kind)
@@ -711,6 +741,33 @@ fdtd_status fdtd_step_timed(fdtd_grid* g, int nsteps, float* pass_ms, int max_pa
     const fdtd_status dev_st = check_device(g, "fdtd_step_timed");
     if (dev_st != FDTD_OK) return dev_st;
     if (g->batch_refs > 0) return not_batched(g, "fdtd_step_timed");
+    if (g->tile.variant == 7) {
+        // one kernel per two steps: pass_ms[0] sums the launches
+        if (nsteps % 2) return fail(FDTD_EINVAL, "variant 7 times an even number of steps (%d)", nsteps);
+        const int nl = nsteps / 2;
+        std::vector<cudaEvent_t> ev(size_t(nl) + 1, nullptr);
+        fdtd_status st = FDTD_OK;
+        for (auto& e : ev)
+            if (st == FDTD_OK) st = cuda_check(cudaEventCreate(&e), "event create");
+        if (st == FDTD_OK) cudaEventRecord(ev[0], g->stream);
+        for (int l = 0; l < nl && st == FDTD_OK; ++l) {
+            st = cuda_check(launch_tb2(g, g->cur, g->step, g->tile, g->stream), "step launch");
+            cudaEventRecord(ev[size_t(l) + 1], g->stream);
+            if (st == FDTD_OK) { g->cur ^= 1; g->pe ^= 1; g->step += 2; }
+        }
+        if (st == FDTD_OK) st = cuda_check(cudaEventSynchronize(ev.back()), "event synchronize");
+        pass_ms[0] = 0.0f;
+        for (int l = 0; l < nl && st == FDTD_OK; ++l) {
+            float ms = 0.0f;
+            st = cuda_check(cudaEventElapsedTime(&ms, ev[size_t(l)], ev[size_t(l) + 1]), "event elapsed time");
+            pass_ms[0] += ms;
+        }
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        *n_passes = 1;
+        if (st != FDTD_OK) return st;
+        return fdtd_sync(g);
+    }
     const int np = passes_per_step(g->tile);
     if (max_passes < np) return fail(FDTD_EINVAL, "max_passes=%d < %d kernels per step", max_passes, np);
     std::vector<cudaEvent_t> ev(size_t(nsteps) * (np + 1), nullptr);
@@ -836,7 +893,7 @@ fdtd_status fdtd_save_state(fdtd_grid* g, void* dev_dst)
     if (!g || !dev_dst) return fail(FDTD_EINVAL, "null argument");
     const fdtd_status dev_st = check_device(g, "fdtd_save_state");
     if (dev_st != FDTD_OK) return dev_st;
-    int64_t hdr[4] = {g->step, g->cur, 0x46445444, 0};
+    int64_t hdr[4] = {g->step, g->cur, 0x46445444, g->pe};
     char* D = static_cast<char*>(dev_dst);
     fdtd_status st = cuda_check(cudaMemcpyAsync(D, g->arena, g->L.dynamic_bytes, cudaMemcpyDeviceToDevice,
                                                 g->stream), "save state");
@@ -858,13 +915,14 @@ fdtd_status fdtd_load_state(fdtd_grid* g, const void* dev_src)
                                                 g->stream), "load state");
     if (st == FDTD_OK) st = fdtd_sync(g);
     if (st != FDTD_OK) return st;
-    if (hdr[2] != 0x46445444 || (hdr[1] != 0 && hdr[1] != 1))
+    if (hdr[2] != 0x46445444 || (hdr[1] != 0 && hdr[1] != 1) || (hdr[3] != 0 && hdr[3] != 1))
         return fail(FDTD_EINVAL, "state blob does not come from fdtd_save_state");
     st = cuda_check(cudaMemcpyAsync(g->arena, S, g->L.dynamic_bytes, cudaMemcpyDeviceToDevice, g->stream),
                     "load state");
     if (st != FDTD_OK) return st;
     g->step = hdr[0];
     g->cur = int(hdr[1]);
+    g->pe = int(hdr[3]);
     return fdtd_sync(g);
 }
 
@@ -890,8 +948,10 @@ void fdtd_destroy_grid(fdtd_grid* g) { delete g; }
 fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz)
 {
     if (!g) return fail(FDTD_EINVAL, "null grid");
-    if (variant < 0 || variant > 6) return fail(FDTD_EINVAL, "variant=%d not in {0, ..., 6}", variant);
+    if (variant < 0 || variant > 7) return fail(FDTD_EINVAL, "variant=%d not in {0, ..., 7}", variant);
     if (ty != 4 && ty != 8 && ty != 16) return fail(FDTD_EINVAL, "ty=%d not in {4, 8, 16}", ty);
+    if (variant == 7 && (ty == 4 || g->desc.precision != FDTD_F32))
+        return fail(FDTD_EINVAL, "variant 7 takes FP32 grids and ty 8 or 16");
     if (variant == 6 && g->desc.nz > 65535) return fail(FDTD_EINVAL, "variant 6 takes nz <= 65535");
     if (variant != 5 && needs_cell_passes(g))
         return fail(FDTD_EINVAL, "a grid with z walls or a wall source takes tile variant 5");
@@ -902,6 +962,24 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz)
     g->tile.tx = 32;
     g->tile.ty = ty;
     g->tile.lz = lz > g->desc.nz ? g->desc.nz : lz;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_set_balance(fdtd_grid* g, float w_shell, float w_antenna)
+{
+    if (!g) return fail(FDTD_EINVAL, "null grid");
+    if (!(w_shell >= 0.0f && w_shell <= 16.0f) || !(w_antenna >= 0.0f && w_antenna <= 16.0f))
+        return fail(FDTD_EINVAL, "balance weights %g, %g outside [0, 16]", w_shell, w_antenna);
+    g->tile.w_shell = w_shell;
+    g->tile.w_ant = w_antenna;
+    return FDTD_OK;
+}
+
+fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenna)
+{
+    if (!g || !w_shell || !w_antenna) return fail(FDTD_EINVAL, "null argument");
+    *w_shell = g->tile.w_shell;
+    *w_antenna = g->tile.w_ant;
     return FDTD_OK;
 }
 
@@ -926,13 +1004,16 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     g->fault = 0;
     fdtd_status st = fdtd_save_state(g, scratch_state);
     if (st != FDTD_OK) return st;
-    struct Cand { int variant, ty; };
+    struct Cand { int variant, ty; float w_shell = 0.0f, w_ant = 0.0f; };
     std::vector<Cand> cands = {{6, 4}, {6, 8}, {6, 16}, {5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {4, 16}, {3, 4},
                                {3, 8}, {3, 16}, {2, 8}, {2, 16}, {1, 4}, {1, 8}, {1, 16}, {0, 4}, {0, 8}, {0, 16}};
     if (g->desc.precision == FDTD_F64)
         cands = {{6, 4}, {6, 8}, {6, 16}, {5, 4}, {5, 8}, {5, 16}, {4, 4}, {4, 8}, {3, 4}, {3, 8}, {2, 8}, {2, 4},
                  {1, 4}, {1, 8}, {0, 4}, {0, 8}};
     if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 3);   // variant 6 takes nz <= 65535
+    if (g->desc.precision == FDTD_F32)   // variant 7 with its work-split weights (shell, antenna)
+        cands.insert(cands.begin(), {{7, 16, 0.0f, 0.0f}, {7, 16, 0.15f, 0.1f}, {7, 16, 0.3f, 0.2f},
+                                     {7, 16, 0.45f, 0.3f}, {7, 16, 0.3f, 0.4f}, {7, 8, 0.3f, 0.2f}});
     if (needs_cell_passes(g)) cands = {{5, 4}, {5, 8}, {5, 16}};
     const int nz = g->desc.nz;
     std::vector<int> lzs;
@@ -947,17 +1028,22 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(FDTD_ECUDA, "event create failed");
+    // every candidate runs the same even number of steps (variant 7 steps in pairs)
+    const int nrun = steps + (steps & 1);
     float best = 1e30f;
     TileConfig best_tc = g->tile;
+    cudaError_t err = cudaSuccess;
     for (const Cand& cd : cands)
         for (int lz : lzs) {
             if (cd.variant >= 5 && lz != lzs[0]) continue;   // one cell per thread: no z segments
             TileConfig tc; tc.variant = cd.variant; tc.tx = 32; tc.ty = cd.ty; tc.lz = lz;
-            cudaError_t e = launch_step(g, g->cur, g->step, tc, g->stream);   // warm-up
-            if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_check(e, "autotune"); }
+            if (cd.variant == 7) { tc.w_shell = cd.w_shell; tc.w_ant = cd.w_ant; }
+            err = run_steps(g, 2, tc);   // warm-up
+            if (err != cudaSuccess) break;
             cudaEventRecord(e0, g->stream);
-            for (int s = 0; s < steps; ++s) launch_step(g, (g->cur + 1 + s) & 1, g->step + 1 + s, tc, g->stream);
+            err = run_steps(g, nrun, tc);
             cudaEventRecord(e1, g->stream);
+            if (err != cudaSuccess) break;
             cudaEventSynchronize(e1);
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
@@ -965,8 +1051,11 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    g->fault = 0;
+    st = fdtd_load_state(g, scratch_state);
+    if (err != cudaSuccess) return cuda_check(err, "autotune");
     g->tile = best_tc;
-    return fdtd_load_state(g, scratch_state);
+    return st;
 }
 
 fdtd_status fdtd_source_coefficients(const fdtd_grid_desc* d, const fdtd_annulus_desc* s, double* out,

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "../../include/fdtd.h"
 #include "yee_fused.cuh"
@@ -17,7 +18,7 @@ struct Layout {
     size_t field_elems = 0, psx_elems = 0, psy_elems = 0;
     size_t field[2][6] = {};
     size_t phx[2][2] = {}, phy[2][2] = {};
-    size_t pex[2] = {}, pey[2] = {};
+    size_t pex[2][2] = {}, pey[2][2] = {};   // [copy][component]: E psi, updated in place except by variant 7
     size_t psz_elems = 0;                 // z shell psi of z-walled grids: [2 npml_z][ny][pitch]
     size_t phz[2][2] = {}, pez[2] = {};   // Hxz, Hyz (ping-pong); Exz, Eyz (in place)
     size_t fluence = 0;
@@ -38,9 +39,16 @@ struct Layout {
 // variant 3: two plain-load passes, H then E with the fluence term;
 // variant 4: two passes, TMA-staged H with the fluence term, then plain-load E;
 // variant 5: two cell-parallel passes, H then E with the fluence term;
-// variant 6: one cell-parallel pass, neighbour H recomputed in registers.
+// variant 6: one cell-parallel pass, neighbour H recomputed in registers;
+// variant 7: two steps per launch (temporal blocking, yee_tb2), FP32,
+//            windows of 32 x ty columns (ty = 8 or 16); an odd step count
+//            ends with one step of variant 5.
 struct TileConfig {
     int variant = 1, tx = 32, ty = 8, lz = 32;
+    // variant 7: extra cost per plane of a window holding CPML shell / antenna
+    // columns, relative to a plain window (the CTAs' work ranges are balanced
+    // on these estimates)
+    float w_shell = 0.25f, w_ant = 0.2f;
 };
 
 fdtd_status fail(fdtd_status st, const char* fmt, ...);
@@ -69,6 +77,7 @@ struct fdtd_grid {
     double dt;
     int64_t step;
     int cur;                 // which ping-pong copy holds the current state
+    int pe;                  // which copy of the E-side psi is current (flipped by variant 7)
     bool has_source;
     fdtd_annulus_desc src;
     fdtd::SrcTime srct;
@@ -85,6 +94,13 @@ struct fdtd_grid {
     bool has_wall;              // fdtd_set_wall_source
     fdtd_wall_desc wall;
     fdtd::SrcTime wallt;        // time envelope of the wall source
+    std::vector<uint8_t> hmask; // antenna component mask per (i, j) column (host copy), empty without a source
+    int src_gen;                // bumped whenever the antenna changes
+    std::vector<long long> tb2_start;   // variant 7: cached CTA work ranges
+    struct {
+        int ry, slots, src_gen;
+        float w_shell, w_ant;
+    } tb2_key;                          // what they were computed for (ry 0: nothing cached)
 };
 
 namespace fdtd {
@@ -100,8 +116,21 @@ inline bool needs_cell_passes(const fdtd_grid* g)
 {
     return g->desc.z_boundary == FDTD_Z_WALLS || g->has_wall;
 }
-// Kernel launches per step of a tile configuration (1 or 2).
+// Kernel launches per step of a tile configuration (1 or 2; variant 7 launches
+// once per two steps).
 inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 && tc.variant <= 5 ? 2 : 1; }
+// Tile variant 7: two steps n, n+1 from copy `cur` (fields, H psi) and E psi
+// copy g->pe into the other copies.  FP32, z-periodic grids without a wall
+// source only.
+cudaError_t launch_tb2(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
+// The tile of the single step that completes an odd step count of variant 7.
+inline TileConfig single_step_tile(const TileConfig& tc)
+{
+    if (tc.variant != 7) return tc;
+    TileConfig one;
+    one.variant = 5; one.tx = 32; one.ty = 4; one.lz = tc.lz;
+    return one;
+}
 // The cell-parallel and two-pass steps on stream s: variant 3 yee_h_pass then
 // yee_e_pass (with the fluence term); variant 4 yee_hflu_tma (with the
 // fluence term) then yee_e_pass; variant 5 yee_h_cell then yee_e_cell;

@@ -1,0 +1,98 @@
+// tb2.cu -- launch of the two-step temporally blocked kernel yee_tb2 (tile
+// variant 7): windows, the flattened (window, plane) work split into ranges
+// of equal estimated cost over one wave of resident CTAs, and the source time
+// factors of both steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "grid_impl.h"
+#include "yee_tb2.cuh"
+
+namespace fdtd {
+
+// CTA work ranges of variant 7 on grid g: windows of 32 x RY columns, `slots`
+// resident CTAs.  A window's plane costs 1, plus w_shell if the window holds
+// CPML shell columns, plus w_ant if it holds antenna columns; each CTA gets a
+// contiguous range of (window, plane) items of about the same total cost.
+// Cached on the grid until the antenna, the weights or the launch shape change.
+static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2Plan& P)
+{
+    const fdtd_grid_desc& d = g->desc;
+    P.T = d.nx <= kTb2Wx ? 1 : (d.nx - kTb2Wx + kTb2Sx - 1) / kTb2Sx + 1;
+    P.U = d.ny <= RY ? 1 : (d.ny - RY + (RY - 4) - 1) / (RY - 4) + 1;
+    auto& key = g->tb2_key;
+    if (key.ry != RY || key.slots != slots || key.src_gen != g->src_gen || key.w_shell != tc.w_shell ||
+        key.w_ant != tc.w_ant) {
+        const int nx = d.nx, ny = d.ny, nz = d.nz, npml = d.npml;
+        const int nw = P.T * P.U;
+        std::vector<double> cost(size_t(nw), 1.0);
+        for (int wy = 0; wy < P.U; ++wy)
+            for (int wx = 0; wx < P.T; ++wx) {
+                const int i0 = kTb2Sx * wx, i1 = std::min(i0 + kTb2Wx, nx);
+                const int j0 = (RY - 4) * wy, j1 = std::min(j0 + RY, ny);
+                const bool shell = npml > 0 && (i0 < npml || i1 > nx - npml || j0 < npml || j1 > ny - npml);
+                bool ant = false;
+                if (!g->hmask.empty())
+                    for (int j = j0; j < j1 && !ant; ++j)
+                        for (int i = i0; i < i1 && !ant; ++i) ant = g->hmask[size_t(j) * nx + i] != 0;
+                cost[size_t(wy) * P.T + wx] = 1.0 + (shell ? tc.w_shell : 0.0) + (ant ? tc.w_ant : 0.0);
+            }
+        double total = 0.0;
+        for (double c : cost) total += c * nz;
+        const double share = total / slots;
+        std::vector<long long> start(size_t(slots) + 1, (long long)nw * nz);
+        start[0] = 0;
+        int c = 1;
+        double cum = 0.0;
+        for (int w = 0; w < nw && c < slots; ++w) {
+            const double span = cost[size_t(w)] * nz;
+            while (c < slots && c * share < cum + span) {
+                long long k = (long long)std::ceil((c * share - cum) / cost[size_t(w)]);
+                k = std::max(0LL, std::min((long long)nz, k));
+                start[size_t(c)] = std::max(start[size_t(c) - 1], (long long)w * nz + k);
+                ++c;
+            }
+            cum += span;
+        }
+        g->tb2_start = start;
+        key.ry = RY; key.slots = slots; key.src_gen = g->src_gen;
+        key.w_shell = tc.w_shell; key.w_ant = tc.w_ant;
+    }
+    for (int c = 0; c <= slots; ++c) P.start[c] = g->tb2_start[size_t(c)];
+}
+
+template <int RY>
+static cudaError_t launch_tb2_t(const fdtd_grid* cg, int cur, long long n, const TileConfig& tc, cudaStream_t s)
+{
+    fdtd_grid* g = const_cast<fdtd_grid*>(cg);
+    using S = Tb2Smem<RY>;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(yee_tb2<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(S::bytes()));
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, yee_tb2<RY>, 32 * RY, S::bytes());
+        if (e != cudaSuccess) return e;
+        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const int slots = std::min(kTb2MaxCtas, (g->sm_count > 0 ? g->sm_count : 152) * blocks_per_sm);
+    Tb2Plan plan;
+    tb2_plan(g, RY, slots, tc, plan);
+    const StepTime<float> t0 = step_time<float>(g->srct, nullptr, g->dt, n);
+    const StepTime<float> t1 = step_time<float>(g->srct, nullptr, g->dt, n + 1);
+    Tb2Times tt;
+    tt.th0 = t0.th; tt.te0 = t0.te; tt.th1 = t1.th; tt.te1 = t1.te;
+    yee_tb2<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), tt, plan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tb2(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s)
+{
+    if (g->desc.precision != FDTD_F32 || needs_cell_passes(g)) return cudaErrorInvalidValue;
+    if (tc.ty == 8) return launch_tb2_t<8>(g, cur, n, tc, s);
+    return launch_tb2_t<16>(g, cur, n, tc, s);
+}
+
+}  // namespace fdtd

@@ -47,6 +47,8 @@ struct StepArgs {
     real* phy_out[2];
     real* pex[2];            // x shell E psi: Eyx, Ezx (in place)
     real* pey[2];            // y shell E psi: Exy, Ezy (in place)
+    real* pex_out[2];        // the other copy of the E psi: the two-step kernel reads
+    real* pey_out[2];        // pex / pey and writes here (ping-pong)
     const real* chx;         // dt / (kappa dx) at H x-positions (i+1/2), length nx
     const real* chy;         // dt / (kappa dy) at H y-positions (j+1/2), length ny
     const real* cex;         // dt / (kappa dx) at E x-positions i

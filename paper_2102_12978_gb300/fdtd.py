@@ -85,6 +85,8 @@ _SIGS = {
     "fdtd_step_timed": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "fdtd_debug_inject_fault": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_debug_set_device": (C.c_int, [C.c_void_p, C.c_int]),
+    "fdtd_set_balance": (C.c_int, [C.c_void_p, C.c_float, C.c_float]),
+    "fdtd_get_balance": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
@@ -320,6 +322,15 @@ class Grid:
 
     def set_tile(self, variant: int, ty: int, lz: int):
         check(lib().fdtd_set_tile(C.c_void_p(self.handle), int(variant), int(ty), int(lz)), "fdtd_set_tile")
+
+    def set_balance(self, w_shell: float, w_antenna: float):
+        """Work-split weights of tile variant 7 (fdtd_set_balance)."""
+        check(lib().fdtd_set_balance(C.c_void_p(self.handle), float(w_shell), float(w_antenna)), "fdtd_set_balance")
+
+    def balance(self):
+        ws, wa = C.c_float(), C.c_float()
+        check(lib().fdtd_get_balance(C.c_void_p(self.handle), C.byref(ws), C.byref(wa)), "fdtd_get_balance")
+        return ws.value, wa.value
 
     def tile(self):
         v, ty, lz = C.c_int(), C.c_int(), C.c_int()
