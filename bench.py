@@ -31,10 +31,16 @@ METRIC = "FDTD Gcell-updates/s FP32 vs FP64 at stated L2 error; % HBM roofline; 
 
 NOMINAL_HBM_GBS = 8000.0   # GB300 HBM3e, nominal
 
+# The timed block of --steps steps is repeated until this much GPU time has
+# passed (at least MIN_REPEATS times); the reported time is the median block.
+MIN_TIMED_S = 1.0
+MIN_REPEATS = 3
+MAX_REPEATS = 100000
+
 # DRAM bytes (read + write) per launch of a kernel on the 256x256x128 FP32
 # workload, from one ncu capture of the kernel as it stands (summary and
 # command in profiles/); None where no capture of the current kernel exists.
-TRAFFIC: dict[str, float] = {"yee_h_cell": 307.85e6, "yee_e_cell": 545.41e6}
+TRAFFIC: dict[str, float | None] = {"yee_h_cell": 307.85e6, "yee_e_cell": 545.41e6, "yee_tb2": 1078.57e6}
 UNIT = "Gcell-updates/s"
 
 # FP64 instructions per cell of each FP64 cell pass on the 256x256x128 workload
@@ -68,9 +74,21 @@ def algorithmic_bytes_per_cell(w, elem_bytes: int) -> float:
     return 12 * elem_bytes + 16 + 2 * elem_bytes * psi_per_cell(w)
 
 
+def launches_per_block(variant: int, steps: int) -> int:
+    """Kernel launches of `steps` steps: two per step for the two-pass
+    variants, one per two steps for variant 7 (plus one two-pass step for an
+    odd count), one per step otherwise."""
+    if variant == 7:
+        return steps // 2 + 2 * (steps % 2)
+    return steps * (2 if 3 <= variant <= 5 else 1)
+
+
 def pass_bytes_per_cell(w, variant: int, b: int) -> list[tuple[str, float]]:
     """(kernel, algorithmic bytes per cell) of each kernel of a step: the
-    distinct values that kernel itself must read and write.
+    distinct values that kernel itself must read and write.  Variant 7
+    advances two steps per launch: its figure is per launch, the method's
+    one-step minimum for each of the two cell-updates (the fluence, fields
+    and psi it actually moves once per launch are half of that).
       one pass:            E, H in and out, fluence in and out, all psi;
       H pass (3, 5):       E^n, H^{n-1/2} in, H^{n+1/2} out, H-side psi;
       E pass + fluence:    E^n, H^{n+1/2}, H^{n-1/2} in, E^{n+1} out,
@@ -90,16 +108,20 @@ def pass_bytes_per_cell(w, variant: int, b: int) -> list[tuple[str, float]]:
         return [("yee_hflu_tma", h + 16), ("yee_e_pass", 9 * b + b * psi)]
     if variant == 5:
         return [("yee_h_cell", h), ("yee_e_cell", 12 * b + 16 + b * psi)]
+    if variant == 7:
+        return [("yee_tb2", 2 * one)]
     return [("yee_step_cell", one)]
 
 
 def kernel_roofline(w, tile, pass_ms, steps, b, peak, cells):
     """Per-kernel achieved bandwidth (algorithmic bytes / CUDA-event duration)
-    and the dominant (longest) kernel."""
+    and the dominant (longest) kernel.  pass_ms[p] sums kernel p over `steps`
+    steps (variant 7: over its steps / 2 launches)."""
     table = pass_bytes_per_cell(w, tile[0], b)
+    launches = steps // 2 if tile[0] == 7 else steps
     rows = []
     for (name, bpc), ms in zip(table, pass_ms):
-        t = ms / steps
+        t = ms / launches
         ach = bpc * cells / (t * 1e-3) / 1e9
         rows.append({"kernel": name, "ms_per_launch": round(t, 5), "algorithmic_bytes_per_cell": round(bpc, 3),
                      "achieved_gbs": round(ach, 1), "frac": round(ach / peak, 4)})
@@ -123,7 +145,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -223,18 +245,26 @@ def run_gpu(args):
         return g
 
     def timed(g, steps, warmup):
+        """Median CUDA-event time of one block of `steps` steps: the block is
+        repeated until at least MIN_TIMED_S of GPU time has passed (and at
+        least MIN_REPEATS times), so that the clock sampler sees the load.
+        Returns (max over ranks of the median ms, repeats, total timed ms)."""
         stream = g.stream
         g.step(warmup)
         barrier(ws)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.step(steps)
-        e1.record(stream)
+        reps = []
+        while (sum(reps) < MIN_TIMED_S * 1e3 or len(reps) < MIN_REPEATS) and len(reps) < MAX_REPEATS:
+            e0.record(stream)
+            g.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            reps.append(e0.elapsed_time(e1))
         torch.cuda.synchronize(dev)
         barrier(ws)
-        return max_over_ranks(e0.elapsed_time(e1), ws, dev)
+        return max_over_ranks(statistics.median(reps), ws, dev), len(reps), sum(reps)
 
     peak, peak_kind = _peaks()
 
@@ -259,6 +289,8 @@ def run_gpu(args):
         g = make(args.only)
         if args.tile:
             g.set_tile(*[int(x) for x in args.tile.split(",")])
+        if args.balance:
+            g.set_balance(*[float(x) for x in args.balance.split(",")])
         g.step(args.warmup)
         g.step(args.steps)
         g.sync()
@@ -267,26 +299,30 @@ def run_gpu(args):
 
     # ---- FP32 (headline) ---------------------------------------------------
     g32 = make("f32")
-    tile32 = g32.autotune(steps=5)
+    tile32 = g32.autotune(steps=20)
+    balance32 = g32.balance()
     props = torch.cuda.get_device_properties(dev)
     gpu_id = f"GPU-{props.uuid}" if getattr(props, "uuid", None) else str(local)
+    # variant 7 times its launches over an even number of steps
+    steps_k = args.steps + (args.steps % 2 if tile32[0] == 7 else 0)
     with ClockSampler(gpu_id) as clk:
-        ms32 = timed(g32, args.steps, args.warmup)
-        # the same steps again with CUDA events around every kernel of a step
-        # (the dominant kernel's duration for the roofline)
-        pass32 = g32.step_timed(args.steps)
+        ms32, reps32, timed_ms32 = timed(g32, args.steps, args.warmup)
+        # the same steps again with CUDA events around every kernel launch
+        # (each kernel's duration for the per-kernel rooflines)
+        pass32 = g32.step_timed(steps_k)
     clocks = clk.summary()
     step_ms = ms32 / args.steps
     gcell32 = job_rate(cells, args.steps, ws, ms32)
     ab32 = algorithmic_bytes_per_cell(w, 4)
     step_achieved = ab32 * cells / (step_ms * 1e-3) / 1e9
-    passes32, dom32 = kernel_roofline(w, tile32, pass32, args.steps, 4, peak, cells)
+    passes32, dom32 = kernel_roofline(w, tile32, pass32, steps_k, 4, peak, cells)
+    traffic32 = step_traffic(tile32[0])
 
     # ---- FP64 (secondary) --------------------------------------------------
     g64 = make("f64")
     tile64 = g64.autotune(steps=3)
     steps64 = max(10, args.steps // 4)
-    ms64 = timed(g64, steps64, max(3, args.warmup // 4))
+    ms64, reps64, _ = timed(g64, steps64, max(3, args.warmup // 4))
     pass64 = g64.step_timed(steps64)
     gcell64 = job_rate(cells, steps64, ws, ms64)
     ab64 = algorithmic_bytes_per_cell(w, 8)
@@ -304,20 +340,14 @@ def run_gpu(args):
                     "peak_from": f"{props.multi_processor_count} SMs x {FP64_INST_PER_SM_CLK:g} FP64 inst/clk x "
                                  f"{sm_mhz:g} MHz"}
 
-    # FP32 vs FP64 agreement on the same number of steps (both GPU paths are
-    # parity-checked against the oracle in the test suite)
-    n_cmp = min(400, args.steps)
-    a = make("f32"); b = make("f64")
-    a.step(n_cmp); b.step(n_cmp)
-    num = den = 0.0
-    for c in range(6):
-        x = a.field(c).double(); y = b.field(c)
-        num += float(torch.sum((x - y) ** 2)); den += float(torch.sum(y ** 2))
-    f32_vs_f64 = (num / den) ** 0.5 if den > 0 else None
-    del a, b
+    # FP32 against FP64 on the GPU over the workload's full run (both GPU
+    # paths are parity-checked against the oracle in the test suite; FP64 is
+    # the transfer standard at full length)
+    l2_error = full_length_error(torch, make, w.steps if args.error_steps < 0 else args.error_steps, tile32,
+                                 balance32)
 
     # ---- end to end through the public API with host buffers --------------
-    e2e = run_e2e(torch, fdtd, w, dev, args.steps, _barrier, ws)
+    e2e = run_e2e(torch, fdtd, w, dev, args.steps, _barrier, ws, tile32, balance32)
 
     # ---- batched sweep: 16 uneven grids, one persistent launch per step ----
     batched = run_batched(torch, fdtd, W, dev, args.batch_steps) if args.batch_steps > 0 else None
@@ -340,16 +370,18 @@ def run_gpu(args):
                    "fluence": "fp64", "source_phase": "fp64",
                    "l2_flush": "inputs larger than L2 (fields + fluence = %.0f MB/step)"
                                % (ab32 * cells / 1e6),
-                   "tile_f32": list(tile32), "tile_f64": list(tile64), "parallelism": f"replicas{ws}"},
-        "roofline": {"bound": "hbm", "achieved": dom32["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": dom32["frac"], "traffic": TRAFFIC.get(dom32["kernel"]), "peak_kind": peak_kind,
-                     "peak_nominal": NOMINAL_HBM_GBS,
-                     "frac_nominal": round(dom32["achieved_gbs"] / NOMINAL_HBM_GBS, 4),
-                     "kernel": dom32["kernel"], "algorithmic_bytes_per_cell": dom32["algorithmic_bytes_per_cell"],
-                     "ms_per_launch": dom32["ms_per_launch"], "cells_per_launch": cells,
-                     "kernels": passes32,
-                     "step": {"achieved": round(step_achieved, 1), "frac": round(step_achieved / peak, 4),
-                              "algorithmic_bytes_per_cell": ab32, "ms_per_step": round(step_ms, 5)}},
+                   "tile_f32": list(tile32), "balance_f32": [round(x, 3) for x in balance32],
+                   "tile_f64": list(tile64), "parallelism": f"replicas{ws}",
+                   "timing": f"median of {reps32} repeats of the {args.steps}-step block (>= {MIN_TIMED_S:g} s "
+                             f"of GPU time)"},
+        "roofline": {"bound": "hbm", "achieved": round(step_achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(step_achieved / peak, 4), "traffic": traffic32,
+                     "basis": "whole step: the method's bytes per cell-update (E, H, fluence, CPML psi in and "
+                              "out once) x cells / ms_per_step; traffic = DRAM bytes per step (ncu)",
+                     "algorithmic_bytes_per_cell_update": ab32, "cell_updates_per_step": cells,
+                     "peak_kind": peak_kind, "peak_nominal": NOMINAL_HBM_GBS,
+                     "frac_nominal": round(step_achieved / NOMINAL_HBM_GBS, 4),
+                     "dominant_kernel": dom32["kernel"], "kernels": passes32},
         "fp64": {"value": round(gcell64, 3), "unit": UNIT, "steps": steps64,
                  "ms_per_step": round(ms64 / steps64, 5),
                  "roofline": {"bound": "alu", "kernels": passes64, "dominant": dom64["kernel"],
@@ -357,13 +389,13 @@ def run_gpu(args):
                               "step_achieved_gbs": round(achieved64, 1),
                               "step_frac_of_hbm": round(achieved64 / peak, 4),
                               "algorithmic_bytes_per_cell": ab64}},
-        "l2_error": {"f32_vs_f64_gpu_rel_l2_fields": f32_vs_f64, "after_steps": n_cmp,
-                     "f64_vs_oracle_tol": 1e-11, "f32_vs_oracle_tol": 1e-4},
+        "l2_error": l2_error,
         "e2e": e2e,
         "batched": batched,
         "adjoint": adjoint,
         "bessel_gauss": bessel_gauss,
-        "gpu_launches": args.steps * len(pass32),
+        "gpu_launches": reps32 * launches_per_block(tile32[0], args.steps),
+        "timed_repeats": reps32, "timed_gpu_s": round(timed_ms32 * 1e-3, 3),
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -373,6 +405,47 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def step_traffic(variant: int):
+    """DRAM bytes per step from the ncu captures in TRAFFIC (per launch):
+    the sum over a step's kernels, half a launch of variant 7; None when a
+    kernel of the step has no capture."""
+    kernels = {5: ["yee_h_cell", "yee_e_cell"], 7: ["yee_tb2"]}.get(variant)
+    if not kernels or any(TRAFFIC.get(k) is None for k in kernels):
+        return None
+    t = sum(TRAFFIC[k] for k in kernels)
+    return round(t / 2 if variant == 7 else t)
+
+
+def rel_l2_t(torch, x, y) -> float:
+    x = x.double(); y = y.double()
+    den = float(torch.linalg.vector_norm(y))
+    return float(torch.linalg.vector_norm(x - y)) / den if den > 0 else float(torch.linalg.vector_norm(x))
+
+
+def full_length_error(torch, make, steps, tile32, balance32):
+    """Relative L2 of the FP32 fields and fluence against the FP64 GPU run
+    after `steps` steps of the workload (its full run by default), per field
+    component and for the fluence, in the bench's FP32 launch configuration."""
+    a = make("f32")
+    a.set_tile(*tile32)
+    a.set_balance(*balance32)
+    b = make("f64")
+    a.step(steps)
+    b.step(steps)
+    per = {}
+    for c, name in enumerate(("Ex", "Ey", "Ez", "Hx", "Hy", "Hz")):
+        per[name] = rel_l2_t(torch, a.field(c), b.field(c))
+    per["fluence"] = rel_l2_t(torch, a.fluence(), b.fluence())
+    num = den = 0.0
+    for c in range(6):
+        x = a.field(c).double(); y = b.field(c)
+        num += float(torch.sum((x - y) ** 2)); den += float(torch.sum(y ** 2))
+    a.close(); b.close()
+    return {"f32_vs_f64_gpu": {k: float(f"{v:.3e}") for k, v in per.items()},
+            "f32_vs_f64_gpu_rel_l2_fields": float(f"{(num / den) ** 0.5:.3e}"), "after_steps": steps,
+            "f64_vs_oracle_tol": 1e-11, "f32_vs_oracle_tol": 1e-4}
 
 
 def run_batched(torch, fdtd, W, dev, steps):
@@ -512,11 +585,12 @@ def run_adjoint(torch, fdtd, W, dev, steps):
             "adjoint_gcell_per_s": round(wl.cells / (ms_adj * 1e-3) / 1e9, 3)}
 
 
-def run_e2e(torch, fdtd, w, dev, steps, barrier, ws):
+def run_e2e(torch, fdtd, w, dev, steps, barrier, ws, tile, balance):
     """Whole job through the public API with host buffers: the initial state
     (6 field arrays) and the source description go host -> device, `steps`
-    Yee steps run, and the fluence plus the dominant field come back to pinned
-    host memory, all inside the timed region."""
+    Yee steps run (in the tile configuration the autotuner chose), and the
+    fluence plus the dominant field come back to pinned host memory, all
+    inside the timed region."""
     import numpy as np
     shape = (w.nz, w.ny, w.nx)
     init = [torch.zeros(shape, dtype=torch.float32).pin_memory() for _ in range(6)]
@@ -525,6 +599,8 @@ def run_e2e(torch, fdtd, w, dev, steps, barrier, ws):
     d = fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant,
                             precision="f32", fluence=True)
     g = fdtd.Grid(d, device=dev)
+    g.set_tile(*tile)
+    g.set_balance(*balance)
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -617,12 +693,15 @@ def main():
     ap.add_argument("--only", default="all", choices=["all", "f32", "f64", "bessel_gauss"],
                     help="time only one precision (profiling runs)")
     ap.add_argument("--tile", default=None, help="variant,ty,lz for --only runs")
+    ap.add_argument("--balance", default=None, help="w_shell,w_antenna (variant 7 work split) for --only runs")
     ap.add_argument("--batch-steps", type=int, default=128,
                     help="steps of the 16-grid batched sweep (0 skips it)")
     ap.add_argument("--bg-steps", type=int, default=200,
                     help="steps of the Bessel-Gauss box timed (0: skip)")
     ap.add_argument("--bg-shrink", type=int, default=1,
                     help="--only bessel_gauss: divide the box's nx, ny, nz by this (profiling runs)")
+    ap.add_argument("--error-steps", type=int, default=-1,
+                    help="steps of the FP32-vs-FP64 comparison (default: the workload's full run)")
     ap.add_argument("--adjoint-steps", type=int, default=100,
                     help="reverse steps timed on the adjoint workload (0 skips it)")
     args = ap.parse_args()

@@ -47,3 +47,34 @@ def test_kernel_roofline_is_bytes_over_time():
 
 def test_job_rate_counts_every_rank():
     assert bench.job_rate(8 * 10 ** 6, 100, 2, 1000.0) == pytest.approx(1.6)
+
+
+def test_two_step_kernel_accounting():
+    """Variant 7 advances two steps per launch: its algorithmic bytes per
+    launch are the method's 72 B for each of the two cell-updates, a launch
+    lasts the summed event time over steps / 2 launches, and a block of K steps
+    takes K / 2 launches (an odd K adds one two-pass step)."""
+    w = W.config2()
+    cells = w.cells
+    assert bench.pass_bytes_per_cell(w, 7, 4) == [("yee_tb2", 144.0)]
+    rows, dom = bench.kernel_roofline(w, (7, 16, 1), [150.0], 1000, 4, 6768.4, cells)
+    assert dom["ms_per_launch"] == pytest.approx(0.3)
+    assert dom["achieved_gbs"] == pytest.approx(144 * cells / 0.3e-3 / 1e9, rel=1e-4)
+    assert bench.launches_per_block(7, 20) == 10
+    assert bench.launches_per_block(7, 21) == 12
+    assert bench.launches_per_block(5, 20) == 40
+    assert bench.launches_per_block(1, 20) == 20
+
+
+def test_step_traffic_is_per_step():
+    saved = dict(bench.TRAFFIC)
+    try:
+        bench.TRAFFIC.update({"yee_h_cell": 300e6, "yee_e_cell": 500e6, "yee_tb2": 1000e6})
+        assert bench.step_traffic(5) == 800e6
+        assert bench.step_traffic(7) == 500e6
+        bench.TRAFFIC["yee_tb2"] = None
+        assert bench.step_traffic(7) is None
+        assert bench.step_traffic(3) is None
+    finally:
+        bench.TRAFFIC.clear()
+        bench.TRAFFIC.update(saved)
