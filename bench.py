@@ -328,17 +328,29 @@ def run_gpu(args):
     ab64 = algorithmic_bytes_per_cell(w, 8)
     achieved64 = ab64 * cells / (ms64 / steps64 * 1e-3) / 1e9
     passes64, dom64 = kernel_roofline(w, tile64, pass64, steps64, 8, peak, cells)
-    # the FP64 pipe roofline of the dominant FP64 kernel
+    # the FP64 pipe roofline of the dominant FP64 kernel, against the FP64
+    # FMA rate measured on this device (8 independent chains per thread,
+    # 2048 threads per SM); the nominal rate beside it
+    with ClockSampler(gpu_id) as clk64:
+        fp64_rate, fp64_rate_ms = fdtd.measure_fp64_rate(chains=8, iters=60000)
+    fp64_dep, _ = fdtd.measure_fp64_rate(chains=1, iters=20000)
+    clocks64 = clk64.summary()
     sm_mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    fp64_peak = props.multi_processor_count * FP64_INST_PER_SM_CLK * sm_mhz * 1e6 / 1e9   # G inst/s
+    fp64_nominal = props.multi_processor_count * FP64_INST_PER_SM_CLK * sm_mhz * 1e6 / 1e9   # G inst/s
+    fp64_peak = fp64_rate / 1e9
     ipc = FP64_INST_PER_CELL.get(dom64["kernel"]) if tile64[0] == 5 else None
     fp64_alu = None
     if ipc is not None:
         ach = ipc * cells / (dom64["ms_per_launch"] * 1e-3) / 1e9
         fp64_alu = {"bound": "alu", "kernel": dom64["kernel"], "unit": "G fp64 inst/s", "achieved": round(ach, 1),
                     "peak": round(fp64_peak, 1), "frac": round(ach / fp64_peak, 4), "fp64_inst_per_cell": ipc,
-                    "peak_from": f"{props.multi_processor_count} SMs x {FP64_INST_PER_SM_CLK:g} FP64 inst/clk x "
-                                 f"{sm_mhz:g} MHz"}
+                    "peak_kind": "measured: FP64 FMA microbenchmark (fdtd_measure_fp64_rate, 8 independent "
+                                 f"chains x 2048 threads per SM, {fp64_rate_ms:.1f} ms)",
+                    "peak_clocks": clocks64,
+                    "dependent_chain_rate": round(fp64_dep / 1e9, 1),
+                    "peak_nominal": round(fp64_nominal, 1),
+                    "peak_nominal_from": f"{props.multi_processor_count} SMs x {FP64_INST_PER_SM_CLK:g} FP64 "
+                                         f"inst/clk x {sm_mhz:g} MHz"}
 
     # FP32 against FP64 on the GPU over the workload's full run (both GPU
     # paths are parity-checked against the oracle in the test suite; FP64 is
@@ -349,7 +361,7 @@ def run_gpu(args):
     # ---- end to end through the public API with host buffers --------------
     e2e = run_e2e(torch, fdtd, w, dev, args.steps, _barrier, ws, tile32, balance32)
 
-    # ---- batched sweep: 16 uneven grids, one persistent launch per step ----
+    # ---- batched sweep: 16 uneven grids advanced together ----------------
     batched = run_batched(torch, fdtd, W, dev, args.batch_steps) if args.batch_steps > 0 else None
 
     # ---- adjoint: 384x384x96 FP32 reverse steps ---------------------------
@@ -450,11 +462,12 @@ def full_length_error(torch, make, steps, tile32, balance32):
 
 def run_batched(torch, fdtd, W, dev, steps):
     """The 16-configuration sweep (l in 0..3 x theta in 5, 10, 20, 30 deg,
-    N^2 x 64 grids with N = 96 .. 640), all grids advanced together from a
-    64-step CUDA graph: the cell-pass engine (one H and one E launch per step
-    over every grid) and the persistent TMA engine (one persistent launch per
-    step); and the persistent cell engine (one cooperative launch per 64
-    steps); against the same grids stepped one grid at a time."""
+    N^2 x 64 grids with N = 96 .. 640), all grids advanced together: the
+    graph engine with every grid on the cell passes (its default), the
+    persistent cell engine (one cooperative launch per 64 steps), and the
+    batch as fdtd_batch_autotune leaves it (each grid's mode, then the
+    engine).  Against the same grids stepped one grid at a time, with the
+    default tile and with each grid's tuned tile."""
     ws_ = W.config4()
 
     def make(wl):
@@ -466,51 +479,61 @@ def run_batched(torch, fdtd, W, dev, steps):
         return g
 
     cells = sum(wl.cells for wl in ws_)
-    seq = [make(wl) for wl in ws_]
-    for g in seq:
-        g.step(2)
-    torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    stream = seq[0].stream
-    e0.record(stream)
-    for _ in range(steps):
+
+    def sequential(tiles):
+        seq = [make(wl) for wl in ws_]
+        for g, t in zip(seq, tiles):
+            if t is not None:
+                g.set_tile(*t)
         for g in seq:
-            g.step(1)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_seq = e0.elapsed_time(e1)
-    for g in seq:
-        g.close()
-    del seq
-    engines = {}
-    for name, engine in (("cell", fdtd.BATCH_CELL), ("persistent", fdtd.BATCH_PERSISTENT),
-                         ("persistent_cell", fdtd.BATCH_PERSISTENT_CELL)):
-        bat = [make(wl) for wl in ws_]
-        b = fdtd.Batch(bat, engine=engine)
-        b.step(64)                 # warm-up, builds the graph
-        b.sync()
+            g.step(2)
+        torch.cuda.synchronize(dev)
+        stream = seq[0].stream
         e0.record(stream)
-        b.step(steps)
+        for _ in range(steps // 2):
+            for g in seq:
+                g.step(2)
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        for g in seq:
+            g.close()
+        return ms
+
+    def batched(engine=None, tune=False):
+        bat = [make(wl) for wl in ws_]
+        b = fdtd.Batch(bat, engine=engine)
+        tuned = b.autotune(steps=8) if tune else None
+        b.step(64)                 # warm-up, builds the graph
         b.sync()
-        engines[name] = (e0.elapsed_time(e1), b.work_items)
+        e0.record(bat[0].stream)
+        b.step(steps)
+        e1.record(bat[0].stream)
+        torch.cuda.synchronize(dev)
+        b.sync()
+        ms = e0.elapsed_time(e1)
         b.close()
         for g in bat:
             g.close()
-    ms_per, items_per = engines["persistent"]
-    ms_pc, _ = engines["persistent_cell"]
-    best = min(("cell", "persistent_cell"), key=lambda k: engines[k][0])
-    ms_bat, items = engines[best]
-    return {"value": round(cells * steps / (ms_bat * 1e-3) / 1e9, 3), "unit": UNIT, "engine": best,
-            "cell_value": round(cells * steps / (engines["cell"][0] * 1e-3) / 1e9, 3),
-            "persistent_cell_value": round(cells * steps / (ms_pc * 1e-3) / 1e9, 3),
-            "sequential_value": round(cells * steps / (ms_seq * 1e-3) / 1e9, 3),
-            "persistent_value": round(cells * steps / (ms_per * 1e-3) / 1e9, 3),
-            "speedup_vs_sequential": round(ms_seq / ms_bat, 3), "grids": len(ws_), "cells": cells,
-            "steps": steps, "work_items": items, "persistent_work_items": items_per,
-            "ms_per_step": round(ms_bat / steps, 4), "persistent_ms_per_step": round(ms_per / steps, 4),
-            "sequential_ms_per_step": round(ms_seq / steps, 4)}
+        return ms, tuned
+
+    ms_seq = sequential([None] * len(ws_))
+    ms_cell, _ = batched(fdtd.BATCH_CELL)
+    ms_pc, _ = batched(fdtd.BATCH_PERSISTENT_CELL)
+    ms_tuned, (engine, modes) = batched(tune=True)
+    mode_tile = {0: (5, 4, 1), 1: (5, 8, 1), 2: (5, 16, 1), 3: (7, 16, 1)}
+    ms_seq_tuned = sequential([mode_tile[m] for m in modes])
+    rate = lambda ms: round(cells * steps / (ms * 1e-3) / 1e9, 3)
+    return {"value": rate(ms_tuned), "unit": UNIT, "engine": "graph" if engine == fdtd.BATCH_CELL else "persistent_cell",
+            "grid_modes": {wl.name: ["cell4", "cell8", "cell16", "two_step"][m] for wl, m in zip(ws_, modes)},
+            "tuned_by": "fdtd_batch_autotune (each grid's mode alone, then the engine over the batch)",
+            "cell_value": rate(ms_cell), "persistent_cell_value": rate(ms_pc),
+            "sequential_value": rate(ms_seq), "sequential_tuned_tiles_value": rate(ms_seq_tuned),
+            "speedup_vs_sequential": round(ms_seq / ms_tuned, 3),
+            "speedup_vs_sequential_same_kernels": round(ms_seq_tuned / ms_tuned, 3),
+            "grids": len(ws_), "cells": cells, "steps": steps,
+            "ms_per_step": round(ms_tuned / steps, 4), "sequential_ms_per_step": round(ms_seq / steps, 4)}
 
 
 def run_bessel_gauss(torch, fdtd, W, dev, steps, peak):

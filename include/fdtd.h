@@ -310,14 +310,16 @@ void fdtd_destroy_grid(fdtd_grid* g);
  * Several grids (any sizes, sources, cone angles; one precision; all created
  * on the current device and at the same step parity) advance together, K =
  * 64 consecutive steps per CUDA-graph replay or per persistent launch.
- * Three engines:
- *   FDTD_BATCH_CELL (default): per step one launch of the H pass and one of
- *     the E pass over the cell blocks of every grid (the arithmetic of
- *     tile variant 5, bit for bit).
- *   FDTD_BATCH_PERSISTENT: one persistent kernel launch per step walks every
- *     grid's (tile, z segment) blocks with the TMA-staged one-pass step (the
- *     arithmetic of tile variant 1, bit for bit); z-periodic grids without a
- *     wall source only (EINVAL otherwise).
+ * Two engines:
+ *   FDTD_BATCH_CELL (default): a CUDA graph of K steps with one branch per
+ *     grid (up to 16 concurrent streams, shared round-robin).  Each grid
+ *     steps in its own mode (fdtd_batch_set_grid_mode): the cell passes of
+ *     tile variant 5 on 32 x 4, 32 x 8 or 32 x 16 blocks (the arithmetic of
+ *     variant 5, bit for bit), or, for FP32 z-periodic grids without a wall
+ *     source, the two-step kernel of tile variant 7 on a share of the SMs
+ *     proportional to the grid's cells (the arithmetic of variant 7, bit for
+ *     bit).  Steps that do not fill a replay run one by one with the cell
+ *     passes.
  *   FDTD_BATCH_PERSISTENT_CELL: one cooperative kernel launch per 64 steps
  *     and per group of up to 24 grids (no graph): every CTA stays resident
  *     and takes runs of cell blocks of all grids in order from a counter,
@@ -326,6 +328,9 @@ void fdtd_destroy_grid(fdtd_grid* g);
  *     on nz).  Its barrier waits are bounded: an expired wait raises
  *     the batch's error word and every CTA returns (ETIMEOUT from
  *     fdtd_batch_sync).
+ * FDTD_BATCH_PERSISTENT (a persistent TMA engine of earlier versions, which
+ * ran slower than the grids stepped one by one) is no longer built:
+ * fdtd_batch_set_engine refuses it with EINVAL.
  * `dev_table` is a device buffer of fdtd_batch_required_bytes bytes
  * (256-byte aligned), owned by the caller and alive until
  * fdtd_batch_destroy; `stream` is a cudaStream_t.  While a grid belongs to
@@ -336,16 +341,33 @@ void fdtd_destroy_grid(fdtd_grid* g);
  * whose copy parity no longer matches the batch's (fdtd_load_state of
  * another parity) makes fdtd_batch_step return ESTATE.
  * fdtd_batch_set_engine switches engines between steps (EINVAL for an
- * unknown engine, or the persistent TMA engine with z walls or a wall
- * source).  fdtd_batch_sync
- * waits for the stream and reports CUDA errors or an expired device wait
- * (ETIMEOUT).  fdtd_batch_work_items: blocks per step of the current engine. */
+ * unknown engine).  fdtd_batch_sync waits for the stream and reports CUDA
+ * errors or an expired device wait (ETIMEOUT).  fdtd_batch_work_items: cell
+ * blocks per step and pass. */
 enum { FDTD_BATCH_PERSISTENT = 0, FDTD_BATCH_CELL = 1, FDTD_BATCH_PERSISTENT_CELL = 2 };
+/* Grid modes of the graph engine. */
+enum { FDTD_BATCH_MODE_CELL4 = 0, FDTD_BATCH_MODE_CELL8 = 1, FDTD_BATCH_MODE_CELL16 = 2,
+       FDTD_BATCH_MODE_TWO_STEP = 3 };
 size_t fdtd_batch_required_bytes(int n_grids, int precision);
 fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, size_t table_bytes, void* stream,
                               fdtd_batch** out);
 fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine);
 int fdtd_batch_get_engine(const fdtd_batch* b);
+/* Mode of grid q (0-based, creation order) in the graph engine; EINVAL for
+ * an unknown mode or the two-step mode on a grid that cannot take it.  The
+ * default is FDTD_BATCH_MODE_CELL4.  -1 from the getter for a bad index. */
+fdtd_status fdtd_batch_set_grid_mode(fdtd_batch* b, int q, int mode);
+int fdtd_batch_get_grid_mode(const fdtd_batch* b, int q);
+/* Autotuner of the batch (the paper has no counterpart).  Saves every grid's
+ * state into `scratch` (a device buffer of at least
+ * fdtd_batch_autotune_bytes bytes, owned by the caller; ENOMEM if smaller),
+ * times each grid alone in each of its modes over `steps` steps (rounded up
+ * to even) and keeps its fastest mode, then times both engines over 64 steps
+ * of the whole batch and keeps the faster, and restores every grid's state
+ * and step counter.  The results of later steps do not depend on the
+ * choices beyond the rounding of the chosen kernels. */
+size_t fdtd_batch_autotune_bytes(const fdtd_batch* b);
+fdtd_status fdtd_batch_autotune(fdtd_batch* b, int steps, void* scratch, size_t scratch_bytes);
 /* Test hook (the paper has no counterpart): kind 1 makes CTA 0 of the next
  * FDTD_BATCH_PERSISTENT_CELL launch return without arriving at the grid
  * barrier, so that the other CTAs' bounded waits (about 2^32 SM cycles)
@@ -428,6 +450,19 @@ void fdtd_adjoint_destroy(fdtd_adjoint* a);
  *   - dst, on_device and reset as for fdtd_fluence; synchronises the stream. */
 size_t fdtd_fluence_noalloc_max_cells(void);
 fdtd_status fdtd_fluence_noalloc(fdtd_grid* g, void* dst, int on_device, int reset);
+
+/* ---- Measurement of the FP64 pipe (the paper has no counterpart) ---------
+ * The FP64 cell passes are bound by the device's FP64 FMA rate, not by HBM.
+ * fdtd_measure_fp64_rate times one launch of a kernel in which every thread
+ * (2048 per SM) runs `chains` independent (8) or dependent (1) chains of
+ * `iters` FP64 fused multiply-adds, with CUDA events on `stream`, and returns
+ * the FMAs per second over all threads (*fma_per_s, thread-level: one FMA is
+ * one FP64 instruction of one thread) and the kernel time in ms.  dev_sink is
+ * a device buffer of at least 8 bytes owned by the caller (written only in a
+ * case that does not occur).  Synchronises the stream.  EINVAL for chains
+ * other than 1 or 8, or iters < 1. */
+fdtd_status fdtd_measure_fp64_rate(void* dev_sink, void* stream, int chains, int iters, double* fma_per_s,
+                                   double* ms);
 
 /* Host-only: the per-column source coefficients A_c (see fdtd_annulus_desc)
  * without weights, evaluated at z = 0 and at z = dz/2 as appropriate for the

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfdtd_gb300.so")
-SOURCES = ["fdtd_api.cu", "split.cu", "tb2.cu", "batch.cu", "adjoint.cu", "noalloc.cu", "source_precompute.cpp"]
+SOURCES = ["fdtd_api.cu", "split.cu", "tb2.cu", "batch.cu", "adjoint.cu", "noalloc.cu", "peak.cu", "source_precompute.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -2,17 +2,18 @@
 // angles, ring radii and transverse sizes) advanced together.
 //
 // Each grid runs the unchanged method of its own descriptor (Section 4,
-// Eq. 12-13).  A CUDA graph holds K = 64 consecutive steps of every grid;
-// one replay (or, for the persistent cell engine, one cooperative launch per
-// group of grids) advances them all by K steps.  Three engines:
-//   * persistent (FDTD_BATCH_PERSISTENT): the batch flattens every grid's
-//     (32 x TR tile, z segment) blocks into one work list; one persistent
-//     kernel launch per step, one CTA per resident slot (SM count x
-//     occupancy), walks the list with a grid stride and marches each block
-//     with the TMA-staged one-pass step (tma_march).  The CTA's mbarriers are
-//     initialised once and their phases carried from block to block; a
-//     one-thread kernel at the end of the graph advances the device step
-//     counter from which the source phases are taken.
+// Eq. 12-13).  Two engines:
+//   * graph (FDTD_BATCH_CELL, the default): a CUDA graph holds K = 64
+//     consecutive steps of every grid, one branch per grid (up to
+//     kCellBranches concurrent streams, shared round-robin), so that the
+//     launches of small grids run side by side instead of each leaving the
+//     GPU idle in its tail.  Each grid steps in its own mode: the
+//     cell-parallel H and E passes of tile variant 5 on 32 x 4, 8 or 16
+//     blocks, or (FP32 z-periodic grids without a wall sheet) the two-step
+//     kernel of tile variant 7 on a share of the SMs proportional to its
+//     cells.  The per-step source time factors of every grid are evaluated on
+//     the host in FP64, as for a single grid, and copied into a device table
+//     ahead of each replay; the kernels read their steps' entries.
 //   * persistent cell passes (FDTD_BATCH_PERSISTENT_CELL): one cooperative
 //     kernel launch runs up to K steps of every grid.  The 32 x 4 cell
 //     blocks of all grids form one list; the CTAs (one per resident slot)
@@ -20,96 +21,38 @@
 //     counter (the E pass from the end of the list), then single blocks near
 //     the end of the pass, so that the blocks in flight stay a narrow front
 //     whose neighbours are in L2, as under the hardware block scheduler, and
-//     a pass ends within about one block of its average.  H pass of every grid, grid barrier, E pass, barrier, and so
-//     on.  The cell arithmetic is that of tile variant 5, bit for bit; the
-//     barriers are bounded waits.
-//   * cell passes (FDTD_BATCH_CELL, the default): each grid steps with the
-//     cell-parallel H and E passes of the single-grid variant 5 (32 x 4 x 1
-//     blocks, one thread per cell).  The graph gives every grid its own
-//     branch (up to kCellBranches concurrent streams, shared round-robin), so
-//     the passes of small grids run side by side instead of each leaving the
-//     GPU idle in its tail.  The per-step source time factors of every grid
-//     are evaluated on the host in FP64, as for a single grid, and copied
-//     into a device table ahead of each replay; the kernels read their step's
-//     entry.
+//     a pass ends within about one block of its average.  H pass of every
+//     grid, grid barrier, E pass, barrier, and so on.  The cell arithmetic is
+//     that of tile variant 5, bit for bit; the barriers are bounded waits.
+// fdtd_batch_autotune times each grid's modes alone, then the two engines
+// over the whole batch, keeps the fastest, and restores every grid's state.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "../../include/fdtd.h"
 #include "grid_impl.h"
-#include "tma_host.h"
 #include "yee_cell.cuh"
-#include "yee_tma.cuh"
 
 namespace fdtd {
 
 struct BatchHeader {
-    int ngrids, nitems;
-    long long counter;   // steps taken by the batch since creation
+    int ngrids;
     int err;             // device error word
     int fault;           // test hook: 1 = CTA 0 of the next persistent cell launch never arrives
 };
 
-template <typename real>
-struct alignas(128) BatchGrid {
-    TmaMaps maps[2];        // by copy being read
-    StepArgs<real> args[2];
-    long long step0;        // the grid's step counter when the batch was created
-    int item0, ntx, nty, nseg, lz;
-};
-
-constexpr int kBatchLz = 32;   // z segment of a batched block
-
-// One CTA of 32 x (TR / R) threads per resident slot; each block is a
-// 32 x TR tile of one grid.
-template <typename real, int TR, int R, int S>
-__global__ void __launch_bounds__(32 * (TR / R), MinCtas<real, TR, R>::value)
-yee_batch_tma(BatchHeader* __restrict__ hdr, const BatchGrid<real>* __restrict__ grids, int parity, int offset)
-{
-    constexpr int NT = 32 * (TR / R);
-    const MarchSmem<real, TR, S> sm = march_smem_init<real, TR, S>(kBatchLz);
-    __shared__ __align__(16) unsigned char sargs_raw[sizeof(StepArgs<real>)];
-    const StepArgs<real>& sa = *reinterpret_cast<const StepArgs<real>*>(sargs_raw);
-    const int ngrids = hdr->ngrids, nitems = hdr->nitems;
-    const long long done = hdr->counter;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    int gq = 0;
-    #pragma unroll 1
-    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-        int g = 0;
-        while (g + 1 < ngrids && grids[g + 1].item0 <= item) ++g;
-        const BatchGrid<real>& G = grids[g];
-        __syncthreads();   // every reader of the previous block's arguments is done
-        const int* src = reinterpret_cast<const int*>(&G.args[parity]);
-        int* dst = reinterpret_cast<int*>(sargs_raw);
-        for (int w = tid; w < int(sizeof(StepArgs<real>) / 4); w += NT) dst[w] = src[w];
-        __syncthreads();   // publish the copied arguments before tma_march reads them
-        int local = item - G.item0;
-        const int bz = local % G.nseg;
-        local /= G.nseg;
-        const int bx = local % G.ntx, by = local / G.ntx;
-        const int kb = bz * G.lz;
-        const int nz = G.args[parity].nz;
-        gq = tma_march_any<real, TR, R, S>(sa, G.maps[parity], G.step0 + done + offset, bx * 32, by * TR, kb,
-                                           min(kb + G.lz, nz), &hdr->err, sm, gq);
-        if (gq < 0) return;
-    }
-}
-
-__global__ void batch_advance(BatchHeader* hdr, int k)
-{
-    hdr->counter += k;
-}
-
 constexpr int kBatchGraphSteps = 64;   // even, so a replay leaves the read copy unchanged
 
-// ---- cell-pass engine
-constexpr int kCellTY = 4;          // 32 x 4 x 1 cell blocks (tile variant 5)
+// ---- graph engine
+constexpr int kCellTY = 4;          // 32 x 4 x 1 cell blocks (tile variant 5) of the persistent cell engine
 constexpr int kCellBranches = 16;   // concurrent graph branches (grids share them round-robin)
+// Per-grid modes of the graph engine.
+enum { kModeCell4 = 0, kModeCell8 = 1, kModeCell16 = 2, kModeTwoStep = 3 };
 
 // ---- persistent cell engine
 // Kernel parameter of one persistent cell launch: a group of at most
@@ -309,53 +252,40 @@ using namespace fdtd;
 struct fdtd_batch {
     std::vector<fdtd_grid*> grids;
     int precision;
-    int engine;                      // FDTD_BATCH_PERSISTENT, _CELL or _PERSISTENT_CELL
-    int ty, S;
+    int engine;                      // FDTD_BATCH_CELL or FDTD_BATCH_PERSISTENT_CELL
     void* table;
     size_t table_bytes;
     size_t times_off;                // byte offset of the time table in `table`
+    size_t bar_off;                  // byte offset of the persistent engine's barrier words
     cudaStream_t stream;
     cudaStream_t capture;
-    int nitems;                      // persistent TMA engine: work items
-    int nblocks;                     // persistent TMA engine: resident CTAs
-    int cell_blocks;                 // cell engines: blocks per step and pass
+    int cell_blocks;                 // 32 x 4 cell blocks per step and pass
     std::vector<unsigned char> pc_params;   // persistent cell engine: PCellParams of each group
     std::vector<int> pc_blocks;             // resident CTAs of each group's launch
-    size_t bar_off;                         // byte offset of its barrier words
     int fault;                       // fdtd_batch_debug_inject_fault pending
     cudaStream_t branch[kCellBranches];
     int nbranch;
     std::vector<unsigned char> host_times;
+    std::vector<int> mode;           // graph engine: each grid's mode (kModeCell4 ... kModeTwoStep)
+    std::vector<int> ctas;           // two-step mode: CTAs of the grid's launches
     int cur;
     int64_t step;
-    cudaGraphExec_t exec[2][2];      // [engine][read copy at the replay's start]
-    bool built[2][2];
+    cudaGraphExec_t exec[2];         // graph engine, by read copy at the replay's start
+    bool built[2];
 };
 
 namespace {
-
-size_t grid_entry_bytes(int precision)
-{
-    return precision == FDTD_F64 ? sizeof(BatchGrid<double>) : sizeof(BatchGrid<float>);
-}
 
 size_t time_entry_bytes(int precision)
 {
     return precision == FDTD_F64 ? sizeof(StepTime<double>) : sizeof(StepTime<float>);
 }
 
-// Table layout: header (256 B) | BatchGrid[n] | barrier words (kBarBytes) | time factors.
-size_t bar_offset(int n, int precision)
-{
-    return (256 + grid_entry_bytes(precision) * size_t(n) + 255) / 256 * 256;
-}
+// Table layout: header (256 B) | barrier words (kBarBytes) | time factors.
+size_t bar_offset() { return 256; }
 
-size_t times_offset(int n, int precision)
-{
-    return bar_offset(n, precision) + kBarBytes;
-}
+size_t times_offset() { return bar_offset() + kBarBytes; }
 
-// ---- cell engine
 void cell_fill(fdtd_batch* b)
 {
     b->cell_blocks = 0;
@@ -363,44 +293,54 @@ void cell_fill(fdtd_batch* b)
         b->cell_blocks += ((g->desc.nx + 31) / 32) * ((g->desc.ny + kCellTY - 1) / kCellTY) * g->desc.nz;
 }
 
-// Step `step` of the replay for grid q on stream s (time factor times[step * n + q]).
-template <typename real>
+// Step `step` of the replay for grid q on stream s with the cell passes on
+// 32 x TY blocks (time factor times[step * n + q]).
+template <typename real, int TY>
 cudaError_t cell_launch_grid(fdtd_batch* b, int q, int parity, int step, cudaStream_t s)
 {
     const fdtd_grid* g = b->grids[q];
     const StepTime<real>* times =
         reinterpret_cast<const StepTime<real>*>(static_cast<char*>(b->table) + b->times_off);
     const int index = step * int(b->grids.size()) + q;
-    const dim3 block(32, kCellTY);
+    const dim3 block(32, TY);
     constexpr int kMaxPlanes = 65535;   // gridDim.z limit: taller grids go in chunks of planes
     const int nz = g->desc.nz, nchunk = (nz + kMaxPlanes - 1) / kMaxPlanes;
     StepArgs<real> a = make_args<real>(g, parity);
     const bool wall = needs_cell_passes(g);   // z walls or a wall sheet
     for (int c = 0; c < nchunk; ++c) {
         a.kbase = c * kMaxPlanes;
-        const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + kCellTY - 1) / kCellTY,
+        const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY,
                         nz - a.kbase < kMaxPlanes ? nz - a.kbase : kMaxPlanes);
-        if (wall) yee_h_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
-        else yee_h_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+        if (wall) yee_h_cell_wt<real, TY><<<grid, block, 0, s>>>(a, times, index);
+        else yee_h_cell_t<real, TY><<<grid, block, 0, s>>>(a, times, index);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     for (int c = nchunk - 1; c >= 0; --c) {
         a.kbase = c * kMaxPlanes;
-        const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + kCellTY - 1) / kCellTY,
+        const dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY,
                         nz - a.kbase < kMaxPlanes ? nz - a.kbase : kMaxPlanes);
-        if (wall) yee_e_cell_wt<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
-        else yee_e_cell_t<real, kCellTY><<<grid, block, 0, s>>>(a, times, index);
+        if (wall) yee_e_cell_wt<real, TY><<<grid, block, 0, s>>>(a, times, index);
+        else yee_e_cell_t<real, TY><<<grid, block, 0, s>>>(a, times, index);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
+// One step of grid q with the cell passes of its mode (the two-step mode
+// takes single steps on 32 x 4 blocks).
 cudaError_t cell_launch_grid_any(fdtd_batch* b, int q, int parity, int step, cudaStream_t s)
 {
-    return b->precision == FDTD_F64 ? cell_launch_grid<double>(b, q, parity, step, s)
-                                    : cell_launch_grid<float>(b, q, parity, step, s);
+    const int m = b->mode[size_t(q)];
+    if (b->precision == FDTD_F64) {
+        if (m == kModeCell8) return cell_launch_grid<double, 8>(b, q, parity, step, s);
+        if (m == kModeCell16) return cell_launch_grid<double, 16>(b, q, parity, step, s);
+        return cell_launch_grid<double, 4>(b, q, parity, step, s);
+    }
+    if (m == kModeCell8) return cell_launch_grid<float, 8>(b, q, parity, step, s);
+    if (m == kModeCell16) return cell_launch_grid<float, 16>(b, q, parity, step, s);
+    return cell_launch_grid<float, 4>(b, q, parity, step, s);
 }
 
 // One step of every grid on one stream (steps outside a graph replay).
@@ -408,6 +348,33 @@ cudaError_t cell_launch_any(fdtd_batch* b, int parity, int step, cudaStream_t s)
 {
     for (int q = 0; q < int(b->grids.size()); ++q) {
         cudaError_t e = cell_launch_grid_any(b, q, parity, step, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// The K steps of grid q in the graph: K / 2 two-step launches (copies and
+// E-side psi flip once per launch; K / 2 is even, so a replay leaves both as
+// they were) or K single steps.
+cudaError_t graph_grid(fdtd_batch* b, int q, int parity, cudaStream_t s)
+{
+    if (b->mode[size_t(q)] == kModeTwoStep) {
+        const StepTime<float>* times =
+            reinterpret_cast<const StepTime<float>*>(static_cast<char*>(b->table) + b->times_off);
+        const int n = int(b->grids.size());
+        fdtd_grid* g = b->grids[size_t(q)];
+        const int pe0 = g->pe;
+        cudaError_t e = cudaSuccess;
+        for (int l = 0; l < kBatchGraphSteps / 2 && e == cudaSuccess; ++l) {
+            g->pe = pe0 ^ (l & 1);   // make_args picks the E-side psi copy of this launch
+            e = launch_tb2_table(g, parity ^ (l & 1), times, 2 * l * n + q, (2 * l + 1) * n + q,
+                                 b->ctas[size_t(q)], s);
+        }
+        g->pe = pe0;
+        return e;
+    }
+    for (int st = 0; st < kBatchGraphSteps; ++st) {
+        cudaError_t e = cell_launch_grid_any(b, q, parity ^ (st & 1), st, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -492,82 +459,7 @@ fdtd_status cell_upload_times(fdtd_batch* b, int count)
                       "batch time table");
 }
 
-// Block shape of the batch: 32 x TR tiles, R rows per thread, S stages
-// (FP32: 32 x 8, FP64: 32 x 4, one row per thread, five stages).
-template <typename real, int TR, int R, int S>
-cudaError_t batch_launch(fdtd_batch* b, int parity, int offset, cudaStream_t s)
-{
-    using T = TmaTile<real, TR>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(yee_batch_tma<real, TR, R, S>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(T::smem_bytes(S, kBatchLz)));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    char* tab = static_cast<char*>(b->table);
-    yee_batch_tma<real, TR, R, S><<<b->nblocks, dim3(32, TR / R), T::smem_bytes(S, kBatchLz), s>>>(
-        reinterpret_cast<BatchHeader*>(tab), reinterpret_cast<const BatchGrid<real>*>(tab + 256), parity, offset);
-    return cudaGetLastError();
-}
-
-cudaError_t batch_launch_any(fdtd_batch* b, int parity, int offset, cudaStream_t s)
-{
-    if (b->precision == FDTD_F64) return batch_launch<double, 4, 1, 5>(b, parity, offset, s);
-    return batch_launch<float, 8, 1, 5>(b, parity, offset, s);
-}
-
-template <typename real, int TR, int R, int S>
-fdtd_status batch_fill(fdtd_batch* b)
-{
-    using T = TmaTile<real, TR>;
-    const int n = int(b->grids.size());
-    std::vector<BatchGrid<real>> host(n);
-    int items = 0;
-    for (int q = 0; q < n; ++q) {
-        fdtd_grid* g = b->grids[q];
-        BatchGrid<real>& G = host[q];
-        std::memset(&G, 0, sizeof(G));
-        for (int cur = 0; cur < 2; ++cur) {
-            TmaMaps* m = nullptr;
-            if (!tma_maps<real, TR>(g, cur, &m)) return fail(FDTD_ECUDA, "tensor map encoding failed");
-            G.maps[cur] = *m;
-            G.args[cur] = make_args<real>(g, cur);
-        }
-        G.step0 = g->step;
-        G.lz = g->desc.nz < kBatchLz ? g->desc.nz : kBatchLz;
-        G.nseg = (g->desc.nz + G.lz - 1) / G.lz;
-        G.ntx = (g->desc.nx + 31) / 32;
-        G.nty = (g->desc.ny + TR - 1) / TR;
-        G.item0 = items;
-        items += G.ntx * G.nty * G.nseg;
-    }
-    b->nitems = items;
-    BatchHeader h;
-    std::memset(&h, 0, sizeof(h));
-    h.ngrids = n;
-    h.nitems = items;
-    char* tab = static_cast<char*>(b->table);
-    fdtd_status st = cuda_check(cudaMemcpy(tab, &h, sizeof(h), cudaMemcpyHostToDevice), "batch table");
-    if (st == FDTD_OK)
-        st = cuda_check(cudaMemcpy(tab + 256, host.data(), sizeof(BatchGrid<real>) * n, cudaMemcpyHostToDevice),
-                        "batch table");
-    if (st != FDTD_OK) return st;
-    cudaError_t e = cudaFuncSetAttribute(yee_batch_tma<real, TR, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(T::smem_bytes(S, kBatchLz)));
-    if (e != cudaSuccess) return cuda_check(e, "batch kernel attribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, yee_batch_tma<real, TR, R, S>, 32 * (TR / R),
-                                                      T::smem_bytes(S, kBatchLz));
-    if (e != cudaSuccess || per_sm < 1) return fail(FDTD_ECUDA, "batch kernel does not fit on an SM");
-    const int sms = b->grids[0]->sm_count > 0 ? b->grids[0]->sm_count : 152;
-    b->nblocks = per_sm * sms < items ? per_sm * sms : items;
-    b->ty = TR;
-    b->S = S;
-    return FDTD_OK;
-}
-
-// The 64 steps of every grid, one branch per grid (streams shared
+// The K steps of every grid, one branch per grid (streams shared
 // round-robin), forked from and joined back into the capture stream.
 cudaError_t cell_capture(fdtd_batch* b, int parity)
 {
@@ -579,9 +471,7 @@ cudaError_t cell_capture(fdtd_batch* b, int parity)
     if (e == cudaSuccess) e = cudaEventRecord(fork, b->capture);
     for (int r = 0; r < b->nbranch && e == cudaSuccess; ++r) {
         e = cudaStreamWaitEvent(b->branch[r], fork, 0);
-        for (int q = r; q < int(b->grids.size()) && e == cudaSuccess; q += b->nbranch)
-            for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; ++s)
-                e = cell_launch_grid_any(b, q, parity ^ (s & 1), s, b->branch[r]);
+        for (int q = r; q < int(b->grids.size()) && e == cudaSuccess; q += b->nbranch) e = graph_grid(b, q, parity, b->branch[r]);
         if (e == cudaSuccess) e = cudaEventRecord(join[r], b->branch[r]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->capture, join[r], 0);
     }
@@ -595,24 +485,44 @@ fdtd_status build_graph(fdtd_batch* b, int parity)
     cudaGraph_t graph;
     fdtd_status st = cuda_check(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "capture");
     if (st != FDTD_OK) return st;
-    cudaError_t e = cudaSuccess;
-    if (b->engine == FDTD_BATCH_CELL)
-        e = cell_capture(b, parity);
-    else
-        for (int s = 0; s < kBatchGraphSteps && e == cudaSuccess; ++s)
-            e = batch_launch_any(b, parity ^ (s & 1), s, b->capture);
-    if (e == cudaSuccess && b->engine == FDTD_BATCH_PERSISTENT) {
-        batch_advance<<<1, 1, 0, b->capture>>>(reinterpret_cast<BatchHeader*>(b->table), kBatchGraphSteps);
-        e = cudaGetLastError();
-    }
+    cudaError_t e = cell_capture(b, parity);
     cudaError_t e2 = cudaStreamEndCapture(b->capture, &graph);
     if (e != cudaSuccess) return cuda_check(e, "capture batch launches");
     if (e2 != cudaSuccess) return cuda_check(e2, "end capture");
-    e = cudaGraphInstantiate(&b->exec[b->engine][parity], graph, 0);
+    e = cudaGraphInstantiate(&b->exec[parity], graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_check(e, "graph instantiate");
-    b->built[b->engine][parity] = true;
+    b->built[parity] = true;
     return FDTD_OK;
+}
+
+void drop_graphs(fdtd_batch* b)
+{
+    for (int p = 0; p < 2; ++p)
+        if (b->built[p]) {
+            cudaGraphExecDestroy(b->exec[p]);
+            b->built[p] = false;
+        }
+}
+
+// CTAs of grid q's two-step launches: a share of the resident slots
+// proportional to its cells, so that the grids' launches run side by side.
+void two_step_ctas(fdtd_batch* b)
+{
+    double total = 0.0;
+    for (const fdtd_grid* g : b->grids) total += double(g->desc.nx) * g->desc.ny * g->desc.nz;
+    const int sms = b->grids[0]->sm_count > 0 ? b->grids[0]->sm_count : 152;
+    b->ctas.assign(b->grids.size(), sms);
+    for (size_t q = 0; q < b->grids.size(); ++q) {
+        const fdtd_grid* g = b->grids[q];
+        const double share = double(g->desc.nx) * g->desc.ny * g->desc.nz / total;
+        b->ctas[q] = std::max(8, std::min(sms, int(share * sms + 0.5)));
+    }
+}
+
+bool two_step_eligible(const fdtd_batch* b, int q)
+{
+    return b->precision == FDTD_F32 && !needs_cell_passes(b->grids[size_t(q)]);
 }
 
 }  // namespace
@@ -622,7 +532,7 @@ extern "C" {
 size_t fdtd_batch_required_bytes(int n_grids, int precision)
 {
     if (n_grids < 1 || (precision != FDTD_F32 && precision != FDTD_F64)) return 0;
-    return times_offset(n_grids, precision) + size_t(kBatchGraphSteps) * n_grids * time_entry_bytes(precision);
+    return times_offset() + size_t(kBatchGraphSteps) * n_grids * time_entry_bytes(precision);
 }
 
 fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, size_t table_bytes, void* stream,
@@ -652,16 +562,22 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->cur = grids[0]->cur;
     b->step = 0;
     b->engine = FDTD_BATCH_CELL;
-    b->times_off = times_offset(n, prec);
-    b->bar_off = bar_offset(n, prec);
-    for (int e = 0; e < 2; ++e) b->built[e][0] = b->built[e][1] = false;
+    b->times_off = times_offset();
+    b->bar_off = bar_offset();
+    b->fault = 0;
+    b->mode.assign(size_t(n), kModeCell4);
+    two_step_ctas(b);
+    b->built[0] = b->built[1] = false;
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
+    BatchHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.ngrids = n;
     st = cuda_check(cudaStreamSynchronize(b->stream), "batch create");
-    if (st == FDTD_OK) st = prec == FDTD_F64 ? batch_fill<double, 4, 1, 5>(b) : batch_fill<float, 8, 1, 5>(b);
+    if (st == FDTD_OK) st = cuda_check(cudaMemcpy(b->table, &h, sizeof(h), cudaMemcpyHostToDevice), "batch table");
     if (st != FDTD_OK) { cudaStreamDestroy(b->capture); delete b; return st; }
     cell_fill(b);
-    if (st == FDTD_OK) st = prec == FDTD_F64 ? pcell_fill<double>(b) : pcell_fill<float>(b);
+    st = prec == FDTD_F64 ? pcell_fill<double>(b) : pcell_fill<float>(b);
     if (st != FDTD_OK) { cudaStreamDestroy(b->capture); delete b; return st; }
     b->nbranch = n < kCellBranches ? n : kCellBranches;
     for (int r = 0; r < b->nbranch && st == FDTD_OK; ++r) {
@@ -681,28 +597,36 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
 fdtd_status fdtd_batch_set_engine(fdtd_batch* b, int engine)
 {
     if (!b) return fail(FDTD_EINVAL, "null batch");
-    if (engine != FDTD_BATCH_PERSISTENT && engine != FDTD_BATCH_CELL && engine != FDTD_BATCH_PERSISTENT_CELL)
-        return fail(FDTD_EINVAL, "engine %d is not FDTD_BATCH_PERSISTENT, _CELL or _PERSISTENT_CELL", engine);
     if (engine == FDTD_BATCH_PERSISTENT)
-        for (fdtd_grid* g : b->grids)
-            if (needs_cell_passes(g))
-                return fail(FDTD_EINVAL, "the persistent engine takes z-periodic grids without a wall source");
-    if (engine == FDTD_BATCH_PERSISTENT && b->engine != engine) {
-        // the persistent kernel takes the source phase of grid g at step
-        // step0_g + counter: bring the device counter to the batch's step
-        const long long counter = b->step;
-        fdtd_status st = cuda_check(cudaMemcpyAsync(static_cast<char*>(b->table) + offsetof(BatchHeader, counter),
-                                                    &counter, sizeof(counter), cudaMemcpyHostToDevice, b->stream),
-                                    "batch counter");
-        if (st != FDTD_OK) return st;
-        st = cuda_check(cudaStreamSynchronize(b->stream), "batch counter");
-        if (st != FDTD_OK) return st;
-    }
+        return fail(FDTD_EINVAL, "the persistent TMA batch engine is no longer built (it ran slower than the "
+                                 "grids stepped one by one); use FDTD_BATCH_CELL or FDTD_BATCH_PERSISTENT_CELL");
+    if (engine != FDTD_BATCH_CELL && engine != FDTD_BATCH_PERSISTENT_CELL)
+        return fail(FDTD_EINVAL, "engine %d is not FDTD_BATCH_CELL or FDTD_BATCH_PERSISTENT_CELL", engine);
     b->engine = engine;
     return FDTD_OK;
 }
 
 int fdtd_batch_get_engine(const fdtd_batch* b) { return b ? b->engine : -1; }
+
+fdtd_status fdtd_batch_set_grid_mode(fdtd_batch* b, int q, int mode)
+{
+    if (!b || q < 0 || q >= int(b->grids.size())) return fail(FDTD_EINVAL, "invalid batch or grid index");
+    if (mode < FDTD_BATCH_MODE_CELL4 || mode > FDTD_BATCH_MODE_TWO_STEP)
+        return fail(FDTD_EINVAL, "mode %d is not a batch grid mode", mode);
+    if (mode == FDTD_BATCH_MODE_TWO_STEP && !two_step_eligible(b, q))
+        return fail(FDTD_EINVAL, "the two-step mode takes FP32 z-periodic grids without a wall source");
+    if (b->mode[size_t(q)] != mode) {
+        b->mode[size_t(q)] = mode;
+        drop_graphs(b);
+    }
+    return FDTD_OK;
+}
+
+int fdtd_batch_get_grid_mode(const fdtd_batch* b, int q)
+{
+    if (!b || q < 0 || q >= int(b->grids.size())) return -1;
+    return b->mode[size_t(q)];
+}
 
 fdtd_status fdtd_batch_debug_inject_fault(fdtd_batch* b, int kind)
 {
@@ -732,14 +656,13 @@ static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps)
     if (dev_st != FDTD_OK) return dev_st;
     for (fdtd_grid* g : b->grids)
         if (g->cur != b->cur) return fail(FDTD_ESTATE, "a batched grid was stepped outside the batch");
-    const bool cell = b->engine == FDTD_BATCH_CELL;
     int done = 0;
-    if (b->engine == FDTD_BATCH_PERSISTENT_CELL) {
-        while (done < nsteps) {
-            const int count = nsteps - done < kBatchGraphSteps ? nsteps - done : kBatchGraphSteps;
-            fdtd_status st = b->precision == FDTD_F64 ? cell_upload_times<double>(b, count)
-                                                      : cell_upload_times<float>(b, count);
-            if (st != FDTD_OK) return st;
+    while (done < nsteps) {
+        const int count = nsteps - done < kBatchGraphSteps ? nsteps - done : kBatchGraphSteps;
+        fdtd_status st = b->precision == FDTD_F64 ? cell_upload_times<double>(b, count)
+                                                  : cell_upload_times<float>(b, count);
+        if (st != FDTD_OK) return st;
+        if (b->engine == FDTD_BATCH_PERSISTENT_CELL) {
             cudaError_t e = b->precision == FDTD_F64 ? pcell_launch<double>(b, b->cur, count, b->stream)
                                                      : pcell_launch<float>(b, b->cur, count, b->stream);
             if (e != cudaSuccess) return cuda_check(e, "persistent cell launch");
@@ -751,39 +674,17 @@ static fdtd_status batch_step_ranges(fdtd_batch* b, int nsteps)
                 b->fault = 0;
             }
             b->cur ^= (count & 1);
-            done += count;
-            b->step += count;
-            for (fdtd_grid* g : b->grids) {
-                g->step += count;
-                g->cur = b->cur;
-            }
-        }
-        return FDTD_OK;
-    }
-    while (done < nsteps) {
-        const int count = nsteps - done < kBatchGraphSteps ? nsteps - done : kBatchGraphSteps;
-        if (cell) {
-            fdtd_status st = b->precision == FDTD_F64 ? cell_upload_times<double>(b, count)
-                                                      : cell_upload_times<float>(b, count);
-            if (st != FDTD_OK) return st;
-        }
-        if (count == kBatchGraphSteps) {
-            if (!b->built[b->engine][b->cur]) {
-                fdtd_status st = build_graph(b, b->cur);
+        } else if (count == kBatchGraphSteps) {
+            if (!b->built[b->cur]) {
+                st = build_graph(b, b->cur);
                 if (st != FDTD_OK) return st;
             }
-            fdtd_status st = cuda_check(cudaGraphLaunch(b->exec[b->engine][b->cur], b->stream), "graph launch");
+            st = cuda_check(cudaGraphLaunch(b->exec[b->cur], b->stream), "graph launch");
             if (st != FDTD_OK) return st;
         } else {
             for (int s = 0; s < count; ++s) {
-                cudaError_t e = cell ? cell_launch_any(b, b->cur ^ (s & 1), s, b->stream)
-                                     : batch_launch_any(b, b->cur ^ (s & 1), s, b->stream);
+                cudaError_t e = cell_launch_any(b, b->cur ^ (s & 1), s, b->stream);
                 if (e != cudaSuccess) return cuda_check(e, "batch launch");
-            }
-            if (!cell) {
-                batch_advance<<<1, 1, 0, b->stream>>>(reinterpret_cast<BatchHeader*>(b->table), count);
-                fdtd_status st = cuda_check(cudaGetLastError(), "batch advance");
-                if (st != FDTD_OK) return st;
             }
             b->cur ^= (count & 1);
         }
@@ -818,19 +719,131 @@ fdtd_status fdtd_batch_sync(fdtd_batch* b)
     return FDTD_OK;
 }
 
-int fdtd_batch_work_items(const fdtd_batch* b)
+int fdtd_batch_work_items(const fdtd_batch* b) { return b ? b->cell_blocks : -1; }
+
+size_t fdtd_batch_autotune_bytes(const fdtd_batch* b)
 {
-    if (!b) return -1;
-    return b->engine == FDTD_BATCH_PERSISTENT ? b->nitems : b->cell_blocks;
+    if (!b) return 0;
+    size_t total = 0;
+    for (const fdtd_grid* g : b->grids) total += (fdtd_state_bytes(g) + 255) / 256 * 256;
+    return total;
+}
+
+// Saves every grid (scratch: fdtd_batch_autotune_bytes), times each grid's
+// modes alone, then the two engines over the whole batch, restores every grid
+// and keeps the fastest.
+fdtd_status fdtd_batch_autotune(fdtd_batch* b, int steps, void* scratch, size_t scratch_bytes)
+{
+    if (!b || !scratch || steps < 1) return fail(FDTD_EINVAL, "invalid argument");
+    const fdtd_status dev_st = check_device(b->grids[0], "fdtd_batch_autotune");
+    if (dev_st != FDTD_OK) return dev_st;
+    if (scratch_bytes < fdtd_batch_autotune_bytes(b))
+        return fail(FDTD_ENOMEM, "autotune scratch of %zu bytes, %zu needed", scratch_bytes, fdtd_batch_autotune_bytes(b));
+    const int n = int(b->grids.size());
+    std::vector<size_t> offs(static_cast<size_t>(n), 0);
+    size_t o = 0;
+    for (int q = 0; q < n; ++q) {
+        offs[size_t(q)] = o;
+        o += (fdtd_state_bytes(b->grids[size_t(q)]) + 255) / 256 * 256;
+    }
+    char* S = static_cast<char*>(scratch);
+    const int64_t step0 = b->step;
+    const int cur0 = b->cur;
+    auto save_all = [&]() {
+        for (int q = 0; q < n; ++q) {
+            fdtd_grid* g = b->grids[size_t(q)];
+            const int refs = g->batch_refs;
+            g->batch_refs = 0;
+            fdtd_status st = fdtd_save_state(g, S + offs[size_t(q)]);
+            g->batch_refs = refs;
+            if (st != FDTD_OK) return st;
+        }
+        return FDTD_OK;
+    };
+    auto load_all = [&]() {
+        for (int q = 0; q < n; ++q) {
+            fdtd_grid* g = b->grids[size_t(q)];
+            fdtd_status st = fdtd_load_state(g, S + offs[size_t(q)]);
+            if (st != FDTD_OK) return st;
+        }
+        b->step = step0;
+        b->cur = cur0;
+        return FDTD_OK;
+    };
+    fdtd_status st = save_all();
+    if (st != FDTD_OK) return st;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(FDTD_ECUDA, "event create failed");
+    const int nrun = steps + (steps & 1);
+    auto elapsed = [&]() {
+        float ms = 0.0f;
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // each grid alone in each of its modes, single-grid launches on the batch stream
+    cudaError_t err = cudaSuccess;
+    for (int q = 0; q < n && err == cudaSuccess; ++q) {
+        fdtd_grid* g = b->grids[size_t(q)];
+        const int refs = g->batch_refs;
+        g->batch_refs = 0;
+        const cudaStream_t gs = g->stream;
+        const TileConfig keep = g->tile;
+        g->stream = b->stream;
+        float best = 1e30f;
+        int best_mode = kModeCell4;
+        const int last = two_step_eligible(b, q) ? kModeTwoStep : kModeCell16;
+        for (int m = kModeCell4; m <= last && err == cudaSuccess; ++m) {
+            TileConfig tc = keep;
+            tc.variant = m == kModeTwoStep ? 7 : 5;
+            tc.ty = m == kModeCell8 ? 8 : (m == kModeCell16 ? 16 : (m == kModeTwoStep ? 16 : 4));
+            g->tile = tc;
+            if (fdtd_step(g, 2) != FDTD_OK) err = cudaErrorUnknown;   // warm-up
+            cudaEventRecord(e0, b->stream);
+            if (err == cudaSuccess && fdtd_step(g, nrun) != FDTD_OK) err = cudaErrorUnknown;
+            cudaEventRecord(e1, b->stream);
+            const float ms = elapsed();
+            if (err == cudaSuccess && ms < best) { best = ms; best_mode = m; }
+        }
+        g->tile = keep;
+        g->stream = gs;
+        g->batch_refs = refs;
+        b->mode[size_t(q)] = best_mode;
+        if (fdtd_load_state(g, S + offs[size_t(q)]) != FDTD_OK && err == cudaSuccess) err = cudaErrorUnknown;
+    }
+    drop_graphs(b);
+    // the two engines over the whole batch, kBatchGraphSteps steps each after a warm-up replay
+    float t_engine[2] = {1e30f, 1e30f};
+    const int engines[2] = {FDTD_BATCH_CELL, FDTD_BATCH_PERSISTENT_CELL};
+    const int keep_engine = b->engine;
+    for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
+        b->engine = engines[k];
+        st = fdtd_batch_step(b, kBatchGraphSteps);
+        cudaEventRecord(e0, b->stream);
+        if (st == FDTD_OK) st = fdtd_batch_step(b, kBatchGraphSteps);
+        cudaEventRecord(e1, b->stream);
+        const float ms = elapsed();
+        if (st == FDTD_OK) st = fdtd_batch_sync(b);
+        if (st != FDTD_OK) { err = cudaErrorUnknown; break; }
+        t_engine[k] = ms;
+        st = load_all();
+        if (st != FDTD_OK) { err = cudaErrorUnknown; break; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->engine = err == cudaSuccess ? (t_engine[1] < t_engine[0] ? FDTD_BATCH_PERSISTENT_CELL : FDTD_BATCH_CELL)
+                                   : keep_engine;
+    const fdtd_status rst = load_all();
+    if (err != cudaSuccess) return st != FDTD_OK ? st : fail(FDTD_ECUDA, "batch autotune failed: %s", fdtd_last_error());
+    return rst;
 }
 
 void fdtd_batch_destroy(fdtd_batch* b)
 {
     if (!b) return;
     for (fdtd_grid* g : b->grids) --g->batch_refs;
-    for (int e = 0; e < 2; ++e)
-        for (int p = 0; p < 2; ++p)
-            if (b->built[e][p]) cudaGraphExecDestroy(b->exec[e][p]);
+    drop_graphs(b);
     for (int r = 0; r < b->nbranch; ++r) cudaStreamDestroy(b->branch[r]);
     cudaStreamDestroy(b->capture);
     delete b;

@@ -9,6 +9,7 @@
 #include "../../include/fdtd.h"
 #include "yee_fused.cuh"
 #include "yee_tma.cuh"
+#include "yee_cell.cuh"
 
 namespace fdtd {
 
@@ -123,6 +124,11 @@ inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 && tc.
 // copy g->pe into the other copies.  FP32, z-periodic grids without a wall
 // source only.
 cudaError_t launch_tb2(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
+// The same two steps with their time factors from a device table of
+// StepTime<float> (entries i0, i1), on at most max_ctas CTAs (a batch runs
+// several grids side by side): the batched graph's launch.
+cudaError_t launch_tb2_table(const fdtd_grid* g, int cur, const StepTime<float>* times, int i0, int i1,
+                             int max_ctas, cudaStream_t s);
 // The tile of the single step that completes an odd step count of variant 7.
 inline TileConfig single_step_tile(const TileConfig& tc)
 {

@@ -63,21 +63,38 @@ static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2P
     for (int c = 0; c <= slots; ++c) P.start[c] = g->tb2_start[size_t(c)];
 }
 
+// Resident CTAs per SM of the kernels of one RY (dynamic shared memory set
+// on first use).
 template <int RY>
-static cudaError_t launch_tb2_t(const fdtd_grid* cg, int cur, long long n, const TileConfig& tc, cudaStream_t s)
+static cudaError_t tb2_blocks_per_sm(int* out)
 {
-    fdtd_grid* g = const_cast<fdtd_grid*>(cg);
     using S = Tb2Smem<RY>;
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(yee_tb2<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(S::bytes()));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(yee_tb2_t<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::bytes()));
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, yee_tb2<RY>, 32 * RY, S::bytes());
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, yee_tb2<RY>, 32 * RY, S::bytes());
         if (e != cudaSuccess) return e;
-        if (blocks_per_sm < 1) return cudaErrorInvalidConfiguration;
+        if (n < 1) return cudaErrorInvalidConfiguration;
+        blocks_per_sm = n;
     }
-    const int slots = std::min(kTb2MaxCtas, (g->sm_count > 0 ? g->sm_count : 152) * blocks_per_sm);
+    *out = blocks_per_sm;
+    return cudaSuccess;
+}
+
+template <int RY>
+static cudaError_t launch_tb2_t(const fdtd_grid* cg, int cur, long long n, const TileConfig& tc, cudaStream_t s)
+{
+    fdtd_grid* g = const_cast<fdtd_grid*>(cg);
+    using S = Tb2Smem<RY>;
+    int per_sm = 0;
+    cudaError_t e = tb2_blocks_per_sm<RY>(&per_sm);
+    if (e != cudaSuccess) return e;
+    const int slots = std::min(kTb2MaxCtas, (g->sm_count > 0 ? g->sm_count : 152) * per_sm);
     Tb2Plan plan;
     tb2_plan(g, RY, slots, tc, plan);
     const StepTime<float> t0 = step_time<float>(g->srct, nullptr, g->dt, n);
@@ -93,6 +110,25 @@ cudaError_t launch_tb2(const fdtd_grid* g, int cur, long long n, const TileConfi
     if (g->desc.precision != FDTD_F32 || needs_cell_passes(g)) return cudaErrorInvalidValue;
     if (tc.ty == 8) return launch_tb2_t<8>(g, cur, n, tc, s);
     return launch_tb2_t<16>(g, cur, n, tc, s);
+}
+
+cudaError_t launch_tb2_table(const fdtd_grid* cg, int cur, const StepTime<float>* times, int i0, int i1,
+                             int max_ctas, cudaStream_t s)
+{
+    fdtd_grid* g = const_cast<fdtd_grid*>(cg);
+    if (g->desc.precision != FDTD_F32 || needs_cell_passes(g)) return cudaErrorInvalidValue;
+    constexpr int RY = 16;
+    using S = Tb2Smem<RY>;
+    int per_sm = 0;
+    cudaError_t e = tb2_blocks_per_sm<RY>(&per_sm);
+    if (e != cudaSuccess) return e;
+    const int all = std::min(kTb2MaxCtas, (g->sm_count > 0 ? g->sm_count : 152) * per_sm);
+    const int slots = std::max(1, std::min(all, max_ctas));
+    TileConfig tc = g->tile;
+    Tb2Plan plan;
+    tb2_plan(g, RY, slots, tc, plan);
+    yee_tb2_t<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), times, i0, i1, plan);
+    return cudaGetLastError();
 }
 
 }  // namespace fdtd

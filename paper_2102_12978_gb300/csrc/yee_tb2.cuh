@@ -560,8 +560,7 @@ __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Ti
 }
 
 template <int RY>
-__global__ void __launch_bounds__(32 * RY, 1)
-yee_tb2(const StepArgs<float> a, const Tb2Times tt, const __grid_constant__ Tb2Plan tw)
+__device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, R = S::R, NF = S::NF;
@@ -584,6 +583,28 @@ yee_tb2(const StepArgs<float> a, const Tb2Times tt, const __grid_constant__ Tb2P
         w += ke - kb;
         __syncthreads();   // the exchange buffers are reused by the next window
     }
+}
+
+// Steps n and n+1 with their source time factors as a parameter.
+template <int RY>
+__global__ void __launch_bounds__(32 * RY, 1)
+yee_tb2(const StepArgs<float> a, const Tb2Times tt, const __grid_constant__ Tb2Plan tw)
+{
+    tb2_run<RY>(a, tt, tw);
+}
+
+// The same with the time factors of the two steps read from a device table
+// (times[i0] for step n, times[i1] for step n+1): the batched graph replays
+// these launches with the table refreshed before each replay.
+template <int RY>
+__global__ void __launch_bounds__(32 * RY, 1)
+yee_tb2_t(const StepArgs<float> a, const StepTime<float>* __restrict__ times, int i0, int i1,
+          const __grid_constant__ Tb2Plan tw)
+{
+    Tb2Times tt;
+    tt.th0 = times[i0].th; tt.te0 = times[i0].te;
+    tt.th1 = times[i1].th; tt.te1 = times[i1].te;
+    tb2_run<RY>(a, tt, tw);
 }
 
 }  // namespace fdtd

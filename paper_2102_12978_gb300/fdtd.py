@@ -86,6 +86,12 @@ _SIGS = {
     "fdtd_debug_inject_fault": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_debug_set_device": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_set_balance": (C.c_int, [C.c_void_p, C.c_float, C.c_float]),
+    "fdtd_batch_set_grid_mode": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "fdtd_batch_get_grid_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "fdtd_batch_autotune_bytes": (C.c_size_t, [C.c_void_p]),
+    "fdtd_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
+    "fdtd_measure_fp64_rate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double)]),
     "fdtd_get_balance": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -181,6 +187,18 @@ def fdtd_fluence_noalloc(h: int, dst_ptr: int, on_device: bool, reset: bool):
     library: for callers that cannot allocate device memory."""
     check(lib().fdtd_fluence_noalloc(C.c_void_p(h), C.c_void_p(dst_ptr), int(on_device), int(reset)),
           "fdtd_fluence_noalloc")
+
+
+def measure_fp64_rate(chains: int = 8, iters: int = 20000, stream=None):
+    """FP64 FMAs per second over all threads of the current device, and the
+    kernel time in ms (fdtd_measure_fp64_rate)."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rate, ms = C.c_double(), C.c_double()
+    check(lib().fdtd_measure_fp64_rate(C.c_void_p(sink.data_ptr()), C.c_void_p(st.cuda_stream), int(chains),
+                                       int(iters), C.byref(rate), C.byref(ms)), "fdtd_measure_fp64_rate")
+    return rate.value, ms.value
 
 
 def fdtd_fluence_noalloc_max_cells() -> int:
@@ -402,13 +420,15 @@ class Grid:
 
 
 BATCH_PERSISTENT, BATCH_CELL, BATCH_PERSISTENT_CELL = 0, 1, 2
+BATCH_MODE_CELL4, BATCH_MODE_CELL8, BATCH_MODE_CELL16, BATCH_MODE_TWO_STEP = 0, 1, 2, 3
 
 
 class Batch:
     """Several Grid objects advanced together (fdtd_batch_*): engine
-    BATCH_CELL (graph-replayed cell passes, the default), BATCH_PERSISTENT
-    (graph-replayed persistent TMA step) or BATCH_PERSISTENT_CELL (one
-    cooperative launch per 64 steps)."""
+    BATCH_CELL (a 64-step CUDA graph with one branch per grid, each grid in
+    its own mode: cell passes on 32 x 4 / 8 / 16 blocks or the two-step
+    kernel; the default) or BATCH_PERSISTENT_CELL (one cooperative launch
+    per 64 steps)."""
 
     def __init__(self, grids, engine: int | None = None):
         import torch
@@ -436,6 +456,23 @@ class Batch:
     @property
     def engine(self) -> int:
         return int(lib().fdtd_batch_get_engine(C.c_void_p(self.handle)))
+
+    def set_grid_mode(self, q: int, mode: int):
+        """Mode of grid q in the graph engine (fdtd_batch_set_grid_mode)."""
+        check(lib().fdtd_batch_set_grid_mode(C.c_void_p(self.handle), int(q), int(mode)), "fdtd_batch_set_grid_mode")
+
+    def grid_mode(self, q: int) -> int:
+        return int(lib().fdtd_batch_get_grid_mode(C.c_void_p(self.handle), int(q)))
+
+    def autotune(self, steps: int = 8):
+        """fdtd_batch_autotune: each grid's mode, then the engine; the grids'
+        states are restored.  Returns (engine, [mode of each grid])."""
+        nbytes = int(lib().fdtd_batch_autotune_bytes(C.c_void_p(self.handle)))
+        scratch = self.torch.empty(nbytes, dtype=self.torch.uint8, device=self.grids[0].device)
+        check(lib().fdtd_batch_autotune(C.c_void_p(self.handle), int(steps), C.c_void_p(scratch.data_ptr()),
+                                        C.c_size_t(nbytes)), "fdtd_batch_autotune")
+        del scratch
+        return self.engine, [self.grid_mode(q) for q in range(len(self.grids))]
 
     def inject_fault(self, kind: int = 1):
         """Test hook: the next persistent cell launch loses one CTA, so that

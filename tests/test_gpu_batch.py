@@ -1,7 +1,8 @@
-"""Batched stepping of several uneven grids, graph-replayed (cell-pass engine
-and persistent TMA engine): each grid must match its own sequential run of
-the same arithmetic bit for bit, and the FP64 oracle within the parity
-tolerance."""
+"""Batched stepping of several uneven grids (graph engine with each grid in
+its own mode, persistent cell engine): each grid must match its own
+sequential run of the same arithmetic bit for bit, and the FP64 oracle
+within the parity tolerance.  The batch autotuner leaves every grid's state
+as it found it."""
 import numpy as np
 import pytest
 
@@ -23,17 +24,14 @@ def _cases():
     ]
 
 
-@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT, fdtd.BATCH_PERSISTENT_CELL])
+@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT_CELL])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_batched_equals_sequential_bitwise(precision, engine):
     """130 steps = two replays of the 64-step graph (or two 64-step
     persistent launches) plus a 2-step remainder; each engine against the
-    single-grid step of the same arithmetic (cell engines: tile variant 5;
-    persistent TMA engine: the one-pass variant 1)."""
+    single-grid step of the same arithmetic (tile variant 5)."""
     ws = _cases()
-    ty = 8 if precision == "f32" else 4
-    tile = (1, ty, 32) if engine == fdtd.BATCH_PERSISTENT else (5, 4, 1)
-    seq = [gpu_grid(w, precision, tile=tile) for w in ws]
+    seq = [gpu_grid(w, precision, tile=(5, 4, 1)) for w in ws]
     bat = [gpu_grid(w, precision) for w in ws]
     b = fdtd.Batch(bat, engine=engine)
     assert b.engine == engine
@@ -51,6 +49,77 @@ def test_batched_equals_sequential_bitwise(precision, engine):
     b.close()
 
 
+def test_graph_engine_grid_modes_bitwise():
+    """Each grid in its own mode of the graph engine -- cell passes on
+    32 x 8 and 32 x 16 blocks, the two-step kernel on a share of the SMs --
+    over two 64-step replays equals the same grid stepped alone with that
+    tile (tile variants 5 and 7), bit for bit."""
+    ws = _cases()
+    modes = [fdtd.BATCH_MODE_TWO_STEP, fdtd.BATCH_MODE_CELL8, fdtd.BATCH_MODE_CELL16, fdtd.BATCH_MODE_TWO_STEP]
+    tiles = {fdtd.BATCH_MODE_CELL8: (5, 8, 1), fdtd.BATCH_MODE_CELL16: (5, 16, 1), fdtd.BATCH_MODE_TWO_STEP: (7, 16, 1)}
+    seq = [gpu_grid(w, "f32", tile=tiles[m]) for w, m in zip(ws, modes)]
+    bat = [gpu_grid(w, "f32") for w in ws]
+    b = fdtd.Batch(bat)
+    for q, m in enumerate(modes):
+        b.set_grid_mode(q, m)
+        assert b.grid_mode(q) == m
+    for g in seq:
+        g.step(128)
+    b.step(128)
+    b.sync()
+    for gs, gb in zip(seq, bat):
+        assert gb.n == gs.n == 128
+        for c in range(6):
+            assert np.array_equal(host(gs.field(c)), host(gb.field(c))), c
+        assert np.array_equal(host(gs.fluence()), host(gb.fluence()))
+    b.close()
+
+
+def test_two_step_mode_refused_where_it_cannot_run():
+    ws = _cases()[:2]
+    b = fdtd.Batch([gpu_grid(w, "f64") for w in ws])
+    with pytest.raises(fdtd.FDTDError) as e:
+        b.set_grid_mode(0, fdtd.BATCH_MODE_TWO_STEP)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    with pytest.raises(fdtd.FDTDError) as e:
+        b.set_grid_mode(0, 7)
+    assert e.value.status == fdtd.FDTD_EINVAL
+    with pytest.raises(fdtd.FDTDError) as e:
+        b.set_engine(fdtd.BATCH_PERSISTENT)   # the persistent TMA engine is no longer built
+    assert e.value.status == fdtd.FDTD_EINVAL
+    b.close()
+
+
+def test_batch_autotune_restores_every_grid():
+    """The autotuner steps every grid while it times modes and engines; it
+    puts back each grid's fields, fluence, step counter and copy parity, and
+    the tuned batch then matches the FP64 oracle within the FP32 bound."""
+    ws = _cases()
+    bat = [gpu_grid(w, "f32") for w in ws]
+    b = fdtd.Batch(bat)
+    b.step(5)
+    b.sync()
+    before = [[g.field(c).clone() for c in range(6)] + [g.fluence().clone()] for g in bat]
+    engine, modes = b.autotune(steps=4)
+    assert engine in (fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT_CELL)
+    assert all(m in (0, 1, 2, 3) for m in modes)
+    for g, ref in zip(bat, before):
+        assert g.n == 5
+        for c in range(6):
+            assert np.array_equal(host(g.field(c)), host(ref[c])), c
+        assert np.array_equal(host(g.fluence()), host(ref[6]))
+    b.step(128 + 3 - 5)
+    b.sync()
+    for w, g in zip(ws, bat):
+        og, os_ = oracle_grid(w), oracle_source(w)
+        st = oracle.State(og)
+        oracle.run(og, os_, st, 128 + 3)
+        for c, ref in enumerate(st.fields()):
+            assert rel_l2(host(g.field(c)), ref) <= 1e-4, (w.name, c)
+        assert rel_l2(host(g.fluence()), st.fluence) <= 1e-4
+    b.close()
+
+
 def test_batch_engine_switch_keeps_source_phase():
     """Steps split between the engines (a switch between graph replays and
     remainders) match the single-grid steps within the FP64 parity bound."""
@@ -59,7 +128,7 @@ def test_batch_engine_switch_keeps_source_phase():
     bat = [gpu_grid(w, "f64") for w in ws]
     b = fdtd.Batch(bat)
     b.step(67)
-    b.set_engine(fdtd.BATCH_PERSISTENT)
+    b.set_engine(fdtd.BATCH_PERSISTENT_CELL)
     b.step(66)
     b.set_engine(fdtd.BATCH_CELL)
     b.step(5)
@@ -73,7 +142,7 @@ def test_batch_engine_switch_keeps_source_phase():
     b.close()
 
 
-@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT])
+@pytest.mark.parametrize("engine", [fdtd.BATCH_CELL, fdtd.BATCH_PERSISTENT_CELL])
 def test_batched_matches_oracle_f64(engine):
     ws = _cases()
     grids = [gpu_grid(w, "f64") for w in ws]
