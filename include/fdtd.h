@@ -358,14 +358,21 @@ int fdtd_batch_get_engine(const fdtd_batch* b);
  * default is FDTD_BATCH_MODE_CELL4.  -1 from the getter for a bad index. */
 fdtd_status fdtd_batch_set_grid_mode(fdtd_batch* b, int q, int mode);
 int fdtd_batch_get_grid_mode(const fdtd_batch* b, int q);
+/* CTAs of grid q's two-step launches in the graph engine (-1 for a bad index). */
+int fdtd_batch_get_grid_ctas(const fdtd_batch* b, int q);
 /* Autotuner of the batch (the paper has no counterpart).  Saves every grid's
  * state into `scratch` (a device buffer of at least
- * fdtd_batch_autotune_bytes bytes, owned by the caller; ENOMEM if smaller),
- * times each grid alone in each of its modes over `steps` steps (rounded up
- * to even) and keeps its fastest mode, then times both engines over 64 steps
- * of the whole batch and keeps the faster, and restores every grid's state
- * and step counter.  The results of later steps do not depend on the
- * choices beyond the rounding of the chosen kernels. */
+ * fdtd_batch_autotune_bytes bytes, owned by the caller; ENOMEM if smaller).
+ * Times each grid alone on the cell passes of each block height (32 x 4, 8,
+ * 16) over `steps` steps (rounded up to even) and keeps the fastest as its
+ * cell mode.  Then times, over 64 steps of the whole batch (the better of two
+ * replays): the graph engine with every grid of at least N cells on the
+ * two-step kernel, for N over the sizes of the grids that can take it (and
+ * with none), each with the two-step launches on shares of the SMs
+ * proportional to the grids' cells or on every SM; and the persistent cell
+ * engine.  Keeps the fastest, and restores every grid's state and step
+ * counter.  The results of later steps do not depend on the choices beyond
+ * the rounding of the chosen kernels. */
 size_t fdtd_batch_autotune_bytes(const fdtd_batch* b);
 fdtd_status fdtd_batch_autotune(fdtd_batch* b, int steps, void* scratch, size_t scratch_bytes);
 /* Test hook (the paper has no counterpart): kind 1 makes CTA 0 of the next
@@ -418,6 +425,14 @@ fdtd_status fdtd_adjoint_create(fdtd_grid* g, int component, const int64_t* prob
                                 void* arena, size_t bytes, fdtd_adjoint** out);
 fdtd_status fdtd_adjoint_reset(fdtd_adjoint* a, int64_t n_end);
 fdtd_status fdtd_probe_read(fdtd_adjoint* a, void* dev_out);
+/* Advance the adjoint's grid by nsteps single steps (the grid's tile, or one
+ * step of variant 5 when the grid runs variant 7) and after step s copy the
+ * probe values (as fdtd_probe_read) into row s of dev_rows (device, rows of
+ * ld >= n_probes elements of the field precision), all queued on the grid's
+ * stream with no host synchronisation: the forward pass of a gradient
+ * records its loss window in one call.  EINVAL for a bad argument, ESTATE
+ * while the grid belongs to a batch. */
+fdtd_status fdtd_probe_record(fdtd_adjoint* a, int nsteps, void* dev_rows, int64_t ld);
 fdtd_status fdtd_adjoint_step(fdtd_adjoint* a, int nsteps, const void* dLdE, int64_t ld);
 int64_t fdtd_adjoint_position(const fdtd_adjoint* a);
 fdtd_status fdtd_adjoint_get(fdtd_adjoint* a, int component, void* dst);

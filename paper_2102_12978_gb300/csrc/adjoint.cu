@@ -530,6 +530,31 @@ fdtd_status fdtd_adjoint_reset(fdtd_adjoint* a, int64_t n_end)
     return cuda_check(cudaMemsetAsync(a->arena, 0, a->dyn_bytes, a->g->stream), "reset adjoint");
 }
 
+fdtd_status fdtd_probe_record(fdtd_adjoint* a, int nsteps, void* dev_rows, int64_t ld)
+{
+    if (!a || nsteps < 0 || (nsteps > 0 && !dev_rows) || ld < a->nprobes)
+        return fail(FDTD_EINVAL, "fdtd_probe_record: invalid argument");
+    fdtd_grid* g = a->g;
+    const fdtd_status dev_st = check_device(g, "fdtd_probe_record");
+    if (dev_st != FDTD_OK) return dev_st;
+    if (g->batch_refs > 0) return fail(FDTD_ESTATE, "fdtd_probe_record: the grid belongs to a batch");
+    const TileConfig one = single_step_tile(g->tile);
+    const size_t elem = g->L.elem;
+    for (int s = 0; s < nsteps; ++s) {
+        cudaError_t e = launch_step(g, g->cur, g->step, one, g->stream);
+        g->fault = 0;
+        if (e != cudaSuccess) return cuda_check(e, "step launch");
+        g->cur ^= 1;
+        g->step += 1;
+        if (a->nprobes > 0) {
+            void* row = static_cast<char*>(dev_rows) + size_t(s) * size_t(ld) * elem;
+            e = g->desc.precision == FDTD_F64 ? launch_gather<double>(a, row) : launch_gather<float>(a, row);
+            if (e != cudaSuccess) return cuda_check(e, "probe gather");
+        }
+    }
+    return FDTD_OK;
+}
+
 fdtd_status fdtd_probe_read(fdtd_adjoint* a, void* dev_out)
 {
     if (!a || !dev_out) return fail(FDTD_EINVAL, "null argument");

@@ -24,8 +24,11 @@
 //     a pass ends within about one block of its average.  H pass of every
 //     grid, grid barrier, E pass, barrier, and so on.  The cell arithmetic is
 //     that of tile variant 5, bit for bit; the barriers are bounded waits.
-// fdtd_batch_autotune times each grid's modes alone, then the two engines
-// over the whole batch, keeps the fastest, and restores every grid's state.
+// fdtd_batch_autotune picks each grid's cell-pass block height alone, then
+// times the whole batch with the grids above each size threshold on the
+// two-step kernel (on proportional shares of the SMs or on all of them) and
+// on the persistent cell engine, keeps the fastest, and restores every
+// grid's state.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -268,6 +271,7 @@ struct fdtd_batch {
     std::vector<unsigned char> host_times;
     std::vector<int> mode;           // graph engine: each grid's mode (kModeCell4 ... kModeTwoStep)
     std::vector<int> ctas;           // two-step mode: CTAs of the grid's launches
+    bool shared_sms;                 // two-step launches on proportional shares of the SMs (else all)
     int cur;
     int64_t step;
     cudaGraphExec_t exec[2];         // graph engine, by read copy at the replay's start
@@ -505,14 +509,18 @@ void drop_graphs(fdtd_batch* b)
         }
 }
 
-// CTAs of grid q's two-step launches: a share of the resident slots
-// proportional to its cells, so that the grids' launches run side by side.
-void two_step_ctas(fdtd_batch* b)
+// CTAs of grid q's two-step launches: with `shared`, a share of the
+// resident slots proportional to its cells, so that the grids' launches run
+// side by side; otherwise every slot, each launch filling the SMs its
+// predecessors free as they finish.
+void two_step_ctas(fdtd_batch* b, bool shared)
 {
     double total = 0.0;
     for (const fdtd_grid* g : b->grids) total += double(g->desc.nx) * g->desc.ny * g->desc.nz;
     const int sms = b->grids[0]->sm_count > 0 ? b->grids[0]->sm_count : 152;
     b->ctas.assign(b->grids.size(), sms);
+    b->shared_sms = shared;
+    if (!shared) return;
     for (size_t q = 0; q < b->grids.size(); ++q) {
         const fdtd_grid* g = b->grids[q];
         const double share = double(g->desc.nx) * g->desc.ny * g->desc.nz / total;
@@ -566,7 +574,7 @@ fdtd_status fdtd_batch_create(fdtd_grid* const* grids, int n, void* dev_table, s
     b->bar_off = bar_offset();
     b->fault = 0;
     b->mode.assign(size_t(n), kModeCell4);
-    two_step_ctas(b);
+    two_step_ctas(b, true);
     b->built[0] = b->built[1] = false;
     fdtd_status st = cuda_check(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking), "capture stream");
     if (st != FDTD_OK) { delete b; return st; }
@@ -626,6 +634,12 @@ int fdtd_batch_get_grid_mode(const fdtd_batch* b, int q)
 {
     if (!b || q < 0 || q >= int(b->grids.size())) return -1;
     return b->mode[size_t(q)];
+}
+
+int fdtd_batch_get_grid_ctas(const fdtd_batch* b, int q)
+{
+    if (!b || q < 0 || q >= int(b->grids.size())) return -1;
+    return b->ctas[size_t(q)];
 }
 
 fdtd_status fdtd_batch_debug_inject_fault(fdtd_batch* b, int kind)
@@ -782,8 +796,10 @@ fdtd_status fdtd_batch_autotune(fdtd_batch* b, int steps, void* scratch, size_t 
         cudaEventElapsedTime(&ms, e0, e1);
         return ms;
     };
-    // each grid alone in each of its modes, single-grid launches on the batch stream
+    // 1. each grid alone on the cell passes of each block height, single-grid
+    //    launches on the batch stream: its cell mode
     cudaError_t err = cudaSuccess;
+    std::vector<int> cell_mode(size_t(n), kModeCell4);
     for (int q = 0; q < n && err == cudaSuccess; ++q) {
         fdtd_grid* g = b->grids[size_t(q)];
         const int refs = g->batch_refs;
@@ -792,48 +808,90 @@ fdtd_status fdtd_batch_autotune(fdtd_batch* b, int steps, void* scratch, size_t 
         const TileConfig keep = g->tile;
         g->stream = b->stream;
         float best = 1e30f;
-        int best_mode = kModeCell4;
-        const int last = two_step_eligible(b, q) ? kModeTwoStep : kModeCell16;
-        for (int m = kModeCell4; m <= last && err == cudaSuccess; ++m) {
+        for (int m = kModeCell4; m <= kModeCell16 && err == cudaSuccess; ++m) {
             TileConfig tc = keep;
-            tc.variant = m == kModeTwoStep ? 7 : 5;
-            tc.ty = m == kModeCell8 ? 8 : (m == kModeCell16 ? 16 : (m == kModeTwoStep ? 16 : 4));
+            tc.variant = 5;
+            tc.ty = m == kModeCell8 ? 8 : (m == kModeCell16 ? 16 : 4);
             g->tile = tc;
             if (fdtd_step(g, 2) != FDTD_OK) err = cudaErrorUnknown;   // warm-up
             cudaEventRecord(e0, b->stream);
             if (err == cudaSuccess && fdtd_step(g, nrun) != FDTD_OK) err = cudaErrorUnknown;
             cudaEventRecord(e1, b->stream);
             const float ms = elapsed();
-            if (err == cudaSuccess && ms < best) { best = ms; best_mode = m; }
+            if (err == cudaSuccess && ms < best) { best = ms; cell_mode[size_t(q)] = m; }
         }
         g->tile = keep;
         g->stream = gs;
         g->batch_refs = refs;
-        b->mode[size_t(q)] = best_mode;
         if (fdtd_load_state(g, S + offs[size_t(q)]) != FDTD_OK && err == cudaSuccess) err = cudaErrorUnknown;
     }
-    drop_graphs(b);
-    // the two engines over the whole batch, kBatchGraphSteps steps each after a warm-up replay
-    float t_engine[2] = {1e30f, 1e30f};
-    const int engines[2] = {FDTD_BATCH_CELL, FDTD_BATCH_PERSISTENT_CELL};
-    const int keep_engine = b->engine;
-    for (int k = 0; k < 2 && err == cudaSuccess; ++k) {
-        b->engine = engines[k];
-        st = fdtd_batch_step(b, kBatchGraphSteps);
-        cudaEventRecord(e0, b->stream);
-        if (st == FDTD_OK) st = fdtd_batch_step(b, kBatchGraphSteps);
-        cudaEventRecord(e1, b->stream);
-        const float ms = elapsed();
+    // 2. the whole batch, kBatchGraphSteps steps after a warm-up replay, best
+    //    of two: the graph with the grids of at least `thr` cells on the
+    //    two-step kernel (thr over every eligible grid's size, and none), on
+    //    shares of the SMs or on all of them; the persistent cell engine
+    std::vector<long long> thresholds = {-1};   // -1: no grid on the two-step kernel
+    for (int q = 0; q < n; ++q)
+        if (two_step_eligible(b, q)) {
+            const fdtd_grid* g = b->grids[size_t(q)];
+            const long long c = (long long)g->desc.nx * g->desc.ny * g->desc.nz;
+            if (std::find(thresholds.begin(), thresholds.end(), c) == thresholds.end()) thresholds.push_back(c);
+        }
+    auto apply = [&](long long thr) {
+        for (int q = 0; q < n; ++q) {
+            const fdtd_grid* g = b->grids[size_t(q)];
+            const long long c = (long long)g->desc.nx * g->desc.ny * g->desc.nz;
+            b->mode[size_t(q)] = (thr >= 0 && c >= thr && two_step_eligible(b, q)) ? kModeTwoStep : cell_mode[size_t(q)];
+        }
+        drop_graphs(b);
+    };
+    auto time_batch = [&](float* out) {
+        float best = 1e30f;
+        st = fdtd_batch_step(b, kBatchGraphSteps);   // warm-up (builds the graph)
+        for (int rep = 0; rep < 2 && st == FDTD_OK; ++rep) {
+            cudaEventRecord(e0, b->stream);
+            st = fdtd_batch_step(b, kBatchGraphSteps);
+            cudaEventRecord(e1, b->stream);
+            const float ms = elapsed();
+            if (ms < best) best = ms;
+        }
         if (st == FDTD_OK) st = fdtd_batch_sync(b);
-        if (st != FDTD_OK) { err = cudaErrorUnknown; break; }
-        t_engine[k] = ms;
-        st = load_all();
-        if (st != FDTD_OK) { err = cudaErrorUnknown; break; }
+        if (st == FDTD_OK) st = load_all();
+        *out = best;
+        return st == FDTD_OK;
+    };
+    const int keep_engine = b->engine;
+    float best_t = 1e30f;
+    long long best_thr = -1;
+    bool best_shared = true;
+    int best_engine = FDTD_BATCH_CELL;
+    b->engine = FDTD_BATCH_CELL;
+    for (long long thr : thresholds) {
+        for (int sh = 0; sh < 2 && err == cudaSuccess; ++sh) {
+            if (thr < 0 && sh == 1) break;   // no two-step grid: the shares do not matter
+            apply(thr);
+            two_step_ctas(b, sh == 0);
+            float t = 0.0f;
+            if (!time_batch(&t)) { err = cudaErrorUnknown; break; }
+            if (t < best_t) { best_t = t; best_thr = thr; best_shared = sh == 0; best_engine = FDTD_BATCH_CELL; }
+        }
+        if (err != cudaSuccess) break;
+    }
+    if (err == cudaSuccess) {
+        b->engine = FDTD_BATCH_PERSISTENT_CELL;
+        float t = 0.0f;
+        if (!time_batch(&t)) err = cudaErrorUnknown;
+        else if (t < best_t) { best_t = t; best_engine = FDTD_BATCH_PERSISTENT_CELL; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->engine = err == cudaSuccess ? (t_engine[1] < t_engine[0] ? FDTD_BATCH_PERSISTENT_CELL : FDTD_BATCH_CELL)
-                                   : keep_engine;
+    if (err == cudaSuccess) {
+        b->engine = best_engine;
+        apply(best_thr);
+        two_step_ctas(b, best_shared);
+    } else {
+        b->engine = keep_engine;
+        apply(-1);
+    }
     const fdtd_status rst = load_all();
     if (err != cudaSuccess) return st != FDTD_OK ? st : fail(FDTD_ECUDA, "batch autotune failed: %s", fdtd_last_error());
     return rst;

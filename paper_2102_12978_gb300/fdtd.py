@@ -87,7 +87,9 @@ _SIGS = {
     "fdtd_debug_set_device": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_set_balance": (C.c_int, [C.c_void_p, C.c_float, C.c_float]),
     "fdtd_batch_set_grid_mode": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "fdtd_probe_record": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "fdtd_batch_get_grid_mode": (C.c_int, [C.c_void_p, C.c_int]),
+    "fdtd_batch_get_grid_ctas": (C.c_int, [C.c_void_p, C.c_int]),
     "fdtd_batch_autotune_bytes": (C.c_size_t, [C.c_void_p]),
     "fdtd_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "fdtd_measure_fp64_rate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double),
@@ -464,6 +466,9 @@ class Batch:
     def grid_mode(self, q: int) -> int:
         return int(lib().fdtd_batch_get_grid_mode(C.c_void_p(self.handle), int(q)))
 
+    def grid_ctas(self, q: int) -> int:
+        return int(lib().fdtd_batch_get_grid_ctas(C.c_void_p(self.handle), int(q)))
+
     def autotune(self, steps: int = 8):
         """fdtd_batch_autotune: each grid's mode, then the engine; the grids'
         states are restored.  Returns (engine, [mode of each grid])."""
@@ -528,6 +533,15 @@ class Adjoint:
         if out is None:
             out = self.torch.empty(self.n_probes, dtype=self.grid.dtype, device=self.grid.device)
         check(lib().fdtd_probe_read(C.c_void_p(self.handle), C.c_void_p(out.data_ptr())), "fdtd_probe_read")
+        return out
+
+    def record(self, nsteps: int):
+        """Step the grid nsteps times, recording the probes after each step
+        (fdtd_probe_record): a (nsteps, n_probes) device tensor."""
+        out = self.torch.empty((nsteps, self.n_probes), dtype=self.grid.dtype, device=self.grid.device)
+        if nsteps > 0:
+            check(lib().fdtd_probe_record(C.c_void_p(self.handle), int(nsteps), C.c_void_p(out.data_ptr()),
+                                          self.n_probes), "fdtd_probe_record")
         return out
 
     def reset(self, n_end: int):

@@ -61,7 +61,7 @@ def test_adjoint_matches_oracle(precision, tol_f, tol_g):
     assert rel_l2(gp, gpo) <= tol_g, rel_l2(gp, gpo)
 
 
-def _problem(w, precision, steps, window, checkpoint, seed=4):
+def _problem(w, precision, steps, window, checkpoint, seed=4, tile=None):
     d = fdtd.make_grid_desc(w.nx, w.ny, w.nz, w.npml, w.dx, w.dx, w.dz, courant=w.courant,
                             precision=precision, fluence=False)
     rng = W.rng(seed)
@@ -74,14 +74,14 @@ def _problem(w, precision, steps, window, checkpoint, seed=4):
     probes = (np.arange(w.nz)[:, None] * (w.nx * w.ny) + cols[None, :]).ravel()
     target = torch.tensor(0.5 + rng.random(probes.size), dtype=torch.float64, device="cuda")
     src = dict(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness, ramp=w.ramp)
-    return BeamProblem(d, src, fdtd.EY, probes, target, steps, window, checkpoint)
+    return BeamProblem(d, src, fdtd.EY, probes, target, steps, window, checkpoint, tile=tile)
 
 
-def _fd_check(w, precision, steps, window, checkpoint, n_weights, h, tol, seed=4):
+def _fd_check(w, precision, steps, window, checkpoint, n_weights, h, tol, seed=4, tile=None):
     """Adjoint gradient in `precision` against central differences of the
     FP64 forward (one column moves the loss by ~1/n_columns of its value, far
     below FP32 rounding of the forward, so the differences are taken in FP64)."""
-    prob = _problem(w, precision, steps, window, checkpoint, seed)
+    prob = _problem(w, precision, steps, window, checkpoint, seed, tile=tile)
     prob64 = _problem(w, "f64", steps, window, checkpoint, seed)
     amp0, ph0 = W.random_weights(w.nx, w.ny, seed=seed)
     wa = torch.tensor(amp0, requires_grad=True)
@@ -125,7 +125,35 @@ def test_gradient_fd_small_f32():
 
 def test_gradient_fd_adjoint_workload_f32():
     """The 384x384x96 (lambda/20, theta = 15 deg, 3-cell ring at 0.8 of the
-    interior half-width) workload in FP32 with checkpoints every 250 steps:
-    20 random weights against central differences, <= 1e-3 relative."""
+    interior half-width) workload over its full 5000 steps in FP32 (the
+    steps before the loss window on the two-step kernel), checkpoints every
+    250 steps, the loss on the last 250 steps: 20 random weights against
+    central differences of the FP64 forward, <= 1e-3 relative."""
     w = W.config5()
-    _fd_check(w, "f32", steps=500, window=100, checkpoint=250, n_weights=20, h=1e-5, tol=1e-3)
+    assert w.steps == 5000
+    worst = _fd_check(w, "f32", steps=5000, window=250, checkpoint=250, n_weights=20, h=1e-5, tol=1e-3,
+                      tile=(7, 16, 1))
+    print("config 5, 5000 steps: worst relative gradient error", worst)
+
+
+def test_forward_reuses_one_grid():
+    """Every forward of a problem runs on the same grid, restarted from its
+    zeroed initial state: a loss evaluated twice, with other weights in
+    between, is the same to the last bit, and its gradient too."""
+    w = W.small(nx=40, ny=36, nz=8, npml=6, r_center=10.0, ramp=0.5, theta_deg=25.0)
+    prob = _problem(w, "f32", steps=40, window=10, checkpoint=16)
+    amp0, ph0 = W.random_weights(w.nx, w.ny, seed=8)
+    wa = torch.tensor(amp0, requires_grad=True)
+    wp = torch.tensor(ph0, requires_grad=True)
+    l1 = beam_loss(wa, wp, prob)
+    grid = prob.context()[0]
+    beam_loss(torch.tensor(amp0 * 1.1), torch.tensor(ph0 + 0.2), prob)
+    l1.backward()
+    g1 = (wa.grad.clone(), wp.grad.clone())
+    wa.grad = None
+    wp.grad = None
+    l2 = beam_loss(wa, wp, prob)
+    l2.backward()
+    assert prob.context()[0] is grid
+    assert l1.item() == l2.item()
+    assert torch.equal(g1[0], wa.grad) and torch.equal(g1[1], wp.grad)
