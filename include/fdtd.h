@@ -479,6 +479,16 @@ fdtd_status fdtd_fluence_noalloc(fdtd_grid* g, void* dst, int on_device, int res
 fdtd_status fdtd_measure_fp64_rate(void* dev_sink, void* stream, int chains, int iters, double* fma_per_s,
                                    double* ms);
 
+/* fdtd_debug_vec_norm: out[i] = |S| from x[i] = |S|^2 >= 0 for n FP64 values,
+ * computed by the device function every FP64 fluence term uses (Section 2's
+ * |E x Hbar|: one Newton step on s^2 = x from the single-precision reciprocal
+ * square root; relative error below 2.5e-13 for x in [2^-126, 2^128), the
+ * correctly rounded square root elsewhere, 0 for x = 0).  dev_x and dev_out
+ * are device arrays of n doubles owned by the caller; the kernel runs on
+ * `stream` and the call synchronises it; n = 0 does nothing.  EINVAL for
+ * n < 0, or for a null pointer with n > 0. */
+fdtd_status fdtd_debug_vec_norm(const void* dev_x, void* dev_out, int64_t n, void* stream);
+
 /* Host-only: the per-column source coefficients A_c (see fdtd_annulus_desc)
  * without weights, evaluated at z = 0 and at z = dz/2 as appropriate for the
  * component, into out[6][ny][nx] complex doubles (re, im interleaved:

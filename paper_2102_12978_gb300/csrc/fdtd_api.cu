@@ -257,6 +257,7 @@ StepArgs<real> make_args(const fdtd_grid* g, int cur)
     a.aey = reinterpret_cast<const real*>(A + L.prof[7]);
     a.cz = real(g->dt / g->desc.dz);
     a.dt = g->dt;
+    a.dt16 = g->dt * 0.0625;
     a.fluence = g->desc.fluence ? static_cast<void*>(A + L.fluence) : nullptr;
     a.smask = g->has_source ? reinterpret_cast<const uint8_t*>(A + L.smask) : nullptr;
     a.scoef = reinterpret_cast<const double2*>(A + L.scoef);

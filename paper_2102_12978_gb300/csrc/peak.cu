@@ -2,7 +2,8 @@
 // denominator of the FP64 passes' roofline.  GB300's FP64 pipe is a small
 // fraction of its FP32 rate, and the FP64 cell passes (one FP64 FMA or add
 // per operation of Section 4's update and of the Section 2 fluence) run into
-// that pipe before HBM.  The paper has no counterpart.
+// that pipe before HBM.  The paper has no counterpart.  Also the device
+// norm of the FP64 fluence term on an array, for its accuracy test.
 #include <cuda_runtime.h>
 
 #include "../../include/fdtd.h"
@@ -50,6 +51,12 @@ static cudaError_t time_fma(double* sink, cudaStream_t s, int blocks, int iters,
     return e;
 }
 
+__global__ void vec_norm_array(const double* __restrict__ x, double* __restrict__ out, long long n)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = vec_norm(x[i]);
+}
+
 }  // namespace fdtd
 
 using namespace fdtd;
@@ -76,6 +83,21 @@ fdtd_status fdtd_measure_fp64_rate(void* dev_sink, void* stream, int chains, int
     *ms = t;
     *fma_per_s = double(blocks) * 256.0 * double(iters) * chains / (t * 1e-3);
     return FDTD_OK;
+}
+
+fdtd_status fdtd_debug_vec_norm(const void* dev_x, void* dev_out, int64_t n, void* stream)
+{
+    if (n < 0) return fail(FDTD_EINVAL, "fdtd_debug_vec_norm: n < 0");
+    if (n == 0) return FDTD_OK;
+    if (!dev_x || !dev_out) return fail(FDTD_EINVAL, "fdtd_debug_vec_norm: null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long blocks = (n + 255) / 256;
+    if (blocks > 0x7fffffffLL) return fail(FDTD_EINVAL, "fdtd_debug_vec_norm: n too large");
+    vec_norm_array<<<unsigned(blocks), 256, 0, s>>>(static_cast<const double*>(dev_x), static_cast<double*>(dev_out),
+                                                    n);
+    fdtd_status st = cuda_check(cudaGetLastError(), "vec_norm kernel");
+    if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(s), "vec_norm kernel");
+    return st;
 }
 
 }  // extern "C"

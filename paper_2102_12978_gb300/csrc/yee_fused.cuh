@@ -63,6 +63,7 @@ struct StepArgs {
     const real* aey;
     real cz;                 // dt / dz
     double dt;
+    double dt16;             // dt / 16: the fluence term's factor (the 1/16 of its centre means folded in)
     void* fluence;           // [nz][ny][pitch] accumulator or null: double (FP64
                              // grids) or float2 (sum, Kahan compensation) (FP32)
     const uint8_t* smask;    // [ny][nx] or null (no source)

@@ -223,7 +223,7 @@ __device__ __forceinline__ void hflu_march(const StepArgs<real>& a, const TmaMap
             if (SRC && a.smask) hmk = a.smask[hcj * nx + hci];
         }
     }
-    const real dt16 = real(a.dt) * real(0.0625);
+    const real dt16 = real(a.dt16);
 
     real px = real(0), py = real(0), pz = real(0);   // own H^{n+1/2} of the previous plane
     int waited = -1;

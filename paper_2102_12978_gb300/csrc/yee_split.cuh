@@ -188,17 +188,22 @@ __device__ __forceinline__ void e_column(const StepArgs<real>& a, const Cpx<real
     const real* __restrict__ Oz = a.hin[2];
     acc_t* __restrict__ F = static_cast<acc_t*>(a.fluence);
     const bool do_flu = FLU && F != nullptr;
-    const real dt16 = real(a.dt) * real(0.0625);
+    const real dt16 = real(a.dt16);
 
     int g = kb * plane + col;
     const int gm = (kb == 0 ? nz - 1 : kb - 1) * plane + col;
     real ex0 = ldro(Ex + g), ey0 = ldro(Ey + g), ez0 = ldro(Ez + g);
     real hxm = ldro(Hx + gm), hym = ldro(Hy + gm), hz0 = ldro(Hz + g);
-    real exj0 = 0, eyi0 = 0, oz0 = 0;
+    // the plane-k halves of the fluence's z-pair sums, carried from plane to
+    // plane (each is the plane-(k+1) half of the plane before): E_x over the
+    // y edges, E_y over the x edges, H_z over the two times
+    real cxk = 0, cyk = 0, hzk = 0;
     if (do_flu) {
-        exj0 = yin ? ldro(Ex + g + pitch) : real(0);
-        eyi0 = xin ? ldro(Ey + g + 1) : real(0);
-        oz0 = ldro(Oz + g);
+        const real exj0 = yin ? ldro(Ex + g + pitch) : real(0);
+        const real eyi0 = xin ? ldro(Ey + g + 1) : real(0);
+        cxk = ex0 + exj0;
+        cyk = ey0 + eyi0;
+        hzk = ldro(Oz + g) + hz0;
     }
     #pragma unroll 2
     for (int k = kb; k < ke; ++k) {
@@ -255,17 +260,18 @@ __device__ __forceinline__ void e_column(const StepArgs<real>& a, const Cpx<real
             const real ox = ldro(Ox + g), oy = ldro(Oy + g), oz1 = ldro(Oz + gn);
             const real oxi = xin ? ldro(Ox + g + 1) : real(0);
             const real oyj = yin ? ldro(Oy + g + pitch) : real(0);
-            const real cx = (ex0 + exj0) + (ex1 + exj1);
-            const real cy = (ey0 + eyi0) + (ey1 + eyi1);
+            const real cxk1 = ex1 + exj1, cyk1 = ey1 + eyi1, hzk1 = oz1 + hz1;
+            const real cx = cxk + cxk1;
+            const real cy = cyk + cyk1;
             const real cz_ = (ez0 + ezi) + (ezj + ezij);
             const real hbx = (ox + hx) + (oxi + hxi);
             const real hby = (oy + hy) + (oyj + hyj);
-            const real hbz = (oz0 + hz) + (oz1 + hz1);
+            const real hbz = hzk + hzk1;
             const real sx = cy * hbz - cz_ * hby;
             const real sy = cz_ * hbx - cx * hbz;
             const real sz = cx * hby - cy * hbx;
             F[g] = Acc::add(F[g], vec_norm(sx * sx + sy * sy + sz * sz) * dt16);
-            exj0 = exj1; eyi0 = eyi1; oz0 = oz1;
+            cxk = cxk1; cyk = cyk1; hzk = hzk1;
         }
         ex0 = ex1; ey0 = ey1; ez0 = ez1; hz0 = hz1;
         hxm = hx; hym = hy;

@@ -195,7 +195,7 @@ __device__ __forceinline__ void step_cell(const StepArgs<real>& a, const StepTim
         const real sy = cc * hbx - cx * hbz;
         const real sz = cx * hby - cy * hbx;
         acc_t* F = static_cast<acc_t*>(a.fluence);
-        const real dt16 = real(a.dt) * real(0.0625);
+        const real dt16 = real(a.dt16);
         F[g] = Acc::add(F[g], vec_norm(sx * sx + sy * sy + sz * sz) * dt16);
     }
 }

@@ -29,8 +29,10 @@
 //     ring of four plane slots in shared memory; a thread waits only for its
 //     own copies, so the ring needs no barrier.  The psi of a plane are
 //     updated in place in its slot (n-1/2 -> n+1/2, n -> n+1) and read back
-//     by the second step's stages.  The plane loop is unrolled by the ring's
-//     four slots, so every slot and exchange-buffer address is a constant.
+//     by the second step's stages.  The plane loop is unrolled by two, so
+//     the exchange buffers' parities are constants; the ring slot is an index
+//     (a four-fold unroll that made it a constant too ran 1 % slower: its
+//     loop body is twice as large).
 //   * The antenna coefficients of a window's columns are staged in shared
 //     memory when the window starts; the per-plane phase e^{i beta z_k} is
 //     loaded one plane ahead.
@@ -205,16 +207,16 @@ __device__ __forceinline__ float tb2_src(const Tb2Bufs<RY>& b, const Tb2Col& c, 
     return b.SC[(2 * comp) * NT + c.tid] * u.x - b.SC[(2 * comp + 1) * NT + c.tid] * u.y;
 }
 
-// One plane p of the wavefront; U = (p - P0) mod 4 gives the ring slots and
-// exchange-buffer parities at compile time.
+// One plane p of the wavefront: u = (p - P0) mod 4 is its ring slot, and
+// U = (p - P0) mod 2 gives the exchange-buffer parities at compile time.
 template <int RY, int U>
 __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Col& c,
                                           const Tb2Bufs<RY>& b, Tb2Carry& s, bool valid, bool issue_next,
-                                          float dt16)
+                                          float dt16, int u)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF;
-    constexpr int SP = U, SQ = (U + 3) & 3, SR = (U + 2) & 3;   // slots of planes p, p-1, p-2
+    const int SP = u, SQ = (u + 3) & 3, SR = (u + 2) & 3;   // slots of planes p, p-1, p-2
     constexpr int PP = U & 1, PQ = PP ^ 1;                        // exchange parities of planes p, p-1
     const int lane = c.lane, row = c.row, tid = c.tid;
     auto xp = [&](float v) {   // value of the +x neighbour (0 past the window)
@@ -526,7 +528,7 @@ __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Ti
     }
     c.ant = __syncthreads_or(c.mk != 0) != 0;
 
-    const float dt16 = float(a.dt) * 0.0625f;
+    const float dt16 = float(a.dt16);
     const int P0 = kb - 2, P1 = ke + 1;   // planes streamed: kb-2 .. ke+1
     Tb2Carry s;
     for (int q = 0; q < 3; ++q) { s.e0[q] = 0.0f; s.h1p[q] = 0.0f; s.e1p[q] = 0.0f; }
@@ -544,16 +546,15 @@ __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Ti
     const int k1 = next_plane(s.kp, nz);
     tb2_issue<RY>(a, c, b, 1, k1, s.kr);
     s.ki = next_plane(k1, nz);
-    // the ring's four slots: plane p uses slot (p - P0) mod 4
+    // the ring's four slots: plane p uses slot u = (p - P0) mod 4
     int p = P0;
+    int u = 0;
     for (;;) {
-        tb2_plane<RY, 0>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16);
+        tb2_plane<RY, 0>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        u = (u + 1) & 3;
         if (++p > P1) break;
-        tb2_plane<RY, 1>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16);
-        if (++p > P1) break;
-        tb2_plane<RY, 2>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16);
-        if (++p > P1) break;
-        tb2_plane<RY, 3>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16);
+        tb2_plane<RY, 1>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        u = (u + 1) & 3;
         if (++p > P1) break;
     }
     cpa_wait0();

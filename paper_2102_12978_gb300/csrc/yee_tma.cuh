@@ -120,10 +120,43 @@ struct TmaTile {
 
 template <typename real> struct Cpx { real x, y; };
 
-// |S| from |S|^2: FP64 grids take the correctly rounded square root; FP32
-// grids take x * rsqrt(x) (a few ulp, far inside the FP32 tolerance of the
+// |S| from |S|^2.
+//
+// FP64: one Newton step on s^2 = x (Heron's method, s <- (s + x / s) / 2,
+// written with r ~ 1/sqrt(x) as s1 = s0 + (x - s0^2) r / 2 with s0 = x r),
+// seeded by the single-precision reciprocal square root.  The seed's float
+// argument and the conversion of r back to FP64 are made from the double's
+// bits with integer operations (x rounded toward zero to 24 bits; r exact),
+// and r / 2 by lowering r's exponent, so the FP64 pipe -- 1/64 of the FP32
+// rate on this GPU -- runs three operations (a multiply and two fused
+// multiply-adds).  With the seed's relative error e (rsqrtf's two ulp plus the
+// truncation of x: |e| < 2^-21.4), the step leaves -3 e^2 / 2 (< 2^-42, 2.3e-13)
+// plus the FP64 rounding of the three operations.  x = 0 returns 0; x outside
+// float's normal range [2^-126, 2^128) (or not finite) takes sqrt().
+//
+// FP32: x * rsqrt(x) (a few ulp, far inside the FP32 tolerance of the
 // fluence), which avoids the long correctly-rounded sequence per cell.
-__device__ __forceinline__ double vec_norm(double x) { return sqrt(x); }
+__device__ __forceinline__ double vec_norm(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = static_cast<unsigned>(__double2loint(x));
+    const int e = (hi >> 20) & 0x7ff;   // biased exponent (x >= 0)
+    if (e >= 1023 - 126 && e <= 1023 + 127) {
+        // float of x: exponent rebiased by 1023 - 127, the top 23 of 52 mantissa bits
+        const unsigned fb = (static_cast<unsigned>(e - 896) << 23) | ((static_cast<unsigned>(hi) & 0xfffffu) << 3) |
+                            (lo >> 29);
+        const unsigned rb = __float_as_uint(rsqrtf(__uint_as_float(fb)));   // in (2^-64, 2^63]
+        // the double of r: exponent rebiased by 896, the 23 mantissa bits on top
+        const int rhi = static_cast<int>((((rb >> 23) + 896u) << 20) | ((rb & 0x7fffffu) >> 3));
+        const int rlo = static_cast<int>(rb << 29);
+        const double r = __hiloint2double(rhi, rlo);
+        const double h = __hiloint2double(rhi - (1 << 20), rlo);   // r / 2
+        const double s0 = x * r;
+        return fma(fma(-s0, s0, x), h, s0);
+    }
+    if ((hi | static_cast<int>(lo)) == 0) return 0.0;
+    return sqrt(x);
+}
 __device__ __forceinline__ float vec_norm(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
 
 // Per-column constants of one H cell: curl coefficients, CPML shell indices

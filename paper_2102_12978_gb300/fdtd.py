@@ -94,6 +94,7 @@ _SIGS = {
     "fdtd_batch_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "fdtd_measure_fp64_rate": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double),
                                          C.POINTER(C.c_double)]),
+    "fdtd_debug_vec_norm": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p]),
     "fdtd_get_balance": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
@@ -201,6 +202,20 @@ def measure_fp64_rate(chains: int = 8, iters: int = 20000, stream=None):
     check(lib().fdtd_measure_fp64_rate(C.c_void_p(sink.data_ptr()), C.c_void_p(st.cuda_stream), int(chains),
                                        int(iters), C.byref(rate), C.byref(ms)), "fdtd_measure_fp64_rate")
     return rate.value, ms.value
+
+
+def debug_vec_norm(x, stream=None):
+    """|S| from |S|^2 for a float64 CUDA tensor, by the device function of
+    the FP64 fluence term (fdtd_debug_vec_norm)."""
+    import torch
+    x = x.contiguous()
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise TypeError("debug_vec_norm takes a float64 CUDA tensor")
+    out = torch.empty_like(x)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    check(lib().fdtd_debug_vec_norm(C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()), x.numel(),
+                                    C.c_void_p(st.cuda_stream)), "fdtd_debug_vec_norm")
+    return out
 
 
 def fdtd_fluence_noalloc_max_cells() -> int:
