@@ -220,13 +220,26 @@ __device__ __forceinline__ void h_cell(const StepArgs<real>& a, Cpx<real> th, in
     a.hout[0][g] = hx; a.hout[1][g] = hy; a.hout[2][g] = hz;
 }
 
-template <typename real, bool GEN, bool WALL, bool NC = true>
-__device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cpx<real> tw, int i, int j, int k)
+// SHY > 0 (FP64 only): the cell's block, of 32 x SHY threads, shares through
+// the shared array s_half (3 x 32 x SHY values) the fluence sums that a cell
+// and its +y neighbour both form (see the fluence below); every thread of the
+// block then runs to the block barrier, a thread past the box on the box's
+// last cell of its row / column, storing nothing.
+template <typename real, bool GEN, bool WALL, bool NC = true, int SHY = 0>
+__device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cpx<real> tw, int i, int j, int k,
+                                       real* s_half = nullptr)
 {
     using Acc = FluAcc<real>;
     using acc_t = typename Acc::T;
+    constexpr bool F64 = std::is_same<real, double>::value;
+    static_assert(SHY == 0 || F64, "the shared fluence sums are an FP64 path");
     const int nx = a.nx, ny = a.ny, nz = a.nz, pitch = a.pitch;
-    if (GEN && (i >= nx || j >= ny)) return;
+    const bool live = !GEN || (i < nx && j < ny);   // the cell lies in the box
+    if (SHY == 0 && !live) return;
+    if (SHY > 0 && GEN) {
+        i = i < nx ? i : nx - 1;
+        j = j < ny ? j : ny - 1;
+    }
     const int plane = pitch * ny, g = k * plane + j * pitch + i;
     const int gm = (k == 0) ? g + (nz - 1) * plane : g - plane;
     const real* __restrict__ Hx = a.hout[0];   // H^{n+1/2}
@@ -256,7 +269,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
             const real b = a.bex[ii], aa = a.aex[ii];
             const real p0 = b * a.pex[0][q] + aa * dHz_x;   // Eyx
             const real p1 = b * a.pex[1][q] + aa * dHy_x;   // Ezx
-            a.pex[0][q] = p0; a.pex[1][q] = p1;
+            if (live) { a.pex[0][q] = p0; a.pex[1][q] = p1; }
             ney -= p0;
             nez += p1;
         }
@@ -266,7 +279,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
             const real b = a.bey[jj], aa = a.aey[jj];
             const real p0 = b * a.pey[0][q] + aa * dHz_y;   // Exy
             const real p1 = b * a.pey[1][q] + aa * dHx_y;   // Ezy
-            a.pey[0][q] = p0; a.pey[1][q] = p1;
+            if (live) { a.pey[0][q] = p0; a.pey[1][q] = p1; }
             nex += p0;
             nez -= p1;
         }
@@ -277,7 +290,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
         const real b = a.bez[kk], aa = a.aez[kk];
         const real p0 = b * a.pez[0][q] + aa * dHy_z;   // Exz
         const real p1 = b * a.pez[1][q] + aa * dHx_z;   // Eyz
-        a.pez[0][q] = p0; a.pez[1][q] = p1;
+        if (live) { a.pez[0][q] = p0; a.pez[1][q] = p1; }
         nex -= p0;
         ney += p1;
     }
@@ -300,7 +313,7 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
         if (i == 0) { ney = real(0); nez = real(0); }
         if (zbot) { nex = real(0); ney = real(0); }
     }
-    a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez;
+    if (live) { a.eout[0][g] = nex; a.eout[1][g] = ney; a.eout[2][g] = nez; }
 
     if (a.fluence) {
         // cell centre (i+1/2, j+1/2, k+1/2): E over four edges, Hbar over two
@@ -315,32 +328,69 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
         const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
         const bool zin = !(WALL && GEN && a.zw) || k + 1 < nz;   // plane k+1 inside the z walls
         const real ex1 = zin ? fld<NC>(Ex + gn) : real(0), ey1 = zin ? fld<NC>(Ey + gn) : real(0);
-        const real exj = yin ? fld<NC>(Ex + g + pitch) : real(0);
-        const real exj1 = (yin && zin) ? fld<NC>(Ex + gn + pitch) : real(0);
         const real eyi = xin ? fld<NC>(Ey + g + 1) : real(0);
         const real eyi1 = (xin && zin) ? fld<NC>(Ey + gn + 1) : real(0);
         const real ezi = xin ? fld<NC>(Ez + g + 1) : real(0);
-        const real ezj = yin ? fld<NC>(Ez + g + pitch) : real(0);
-        const real ezij = (xin && yin) ? fld<NC>(Ez + g + pitch + 1) : real(0);
         const real hxi = xin ? fld<NC>(Hx + g + 1) : real(0);
-        const real hyj = yin ? fld<NC>(Hy + g + pitch) : real(0);
         const real hz1 = zin ? fld<NC>(Hz + gn) : real(0);
         const real ox = fld<NC>(Ox + g), oy = fld<NC>(Oy + g), oz = fld<NC>(Oz + g);
         const real oz1 = zin ? fld<NC>(Oz + gn) : real(0);
         const real oxi = xin ? fld<NC>(Ox + g + 1) : real(0);
-        const real oyj = yin ? fld<NC>(Oy + g + pitch) : real(0);
-        const real cx = (ex + exj) + (ex1 + exj1);
+        // the sums over the cell's two y faces: E_x over its four y-z edges,
+        // E_z over its four x-y edges, H_y over the two faces and two times.
+        // Each is the sum of a row-j half and a row-(j+1) half, and the row-j
+        // half of cell (i, j+1) is the row-(j+1) half of cell (i, j): FP64
+        // blocks (SHY) take the row-(j+1) halves from the thread of row j+1
+        // where it lies in the block and the box.  FP64 adds E_x's halves
+        // over z first (the same order on every FP64 path, shared or not),
+        // FP32 over y first (the order of the two-step kernel).
+        real cx, cc, hby;
+        if constexpr (F64) {
+            const real xh = ex + ex1, zh = ez + ezi, yh = oy + hy;   // row j
+            real xh1, zh1, yh1;                                       // row j+1
+            bool shared = false;
+            if constexpr (SHY > 0) {
+                constexpr int NB = 32 * SHY;
+                const int t = threadIdx.y * 32 + threadIdx.x;
+                s_half[t] = xh; s_half[NB + t] = zh; s_half[2 * NB + t] = yh;
+                __syncthreads();
+                shared = int(threadIdx.y) + 1 < SHY && yin;
+                if (shared) { xh1 = s_half[t + 32]; zh1 = s_half[NB + t + 32]; yh1 = s_half[2 * NB + t + 32]; }
+            }
+            if (!shared) {   // read row j+1 (zero past the box), same operands and order as its thread
+                const real e0 = yin ? fld<NC>(Ex + g + pitch) : real(0);
+                const real e1 = (yin && zin) ? fld<NC>(Ex + gn + pitch) : real(0);
+                const real z0 = yin ? fld<NC>(Ez + g + pitch) : real(0);
+                const real z1 = (yin && xin) ? fld<NC>(Ez + g + pitch + 1) : real(0);
+                const real o0 = yin ? fld<NC>(Oy + g + pitch) : real(0);
+                const real h0 = yin ? fld<NC>(Hy + g + pitch) : real(0);
+                xh1 = e0 + e1;
+                zh1 = z0 + z1;
+                yh1 = o0 + h0;
+            }
+            cx = xh + xh1;
+            cc = zh + zh1;
+            hby = yh + yh1;
+        } else {
+            const real exj = yin ? fld<NC>(Ex + g + pitch) : real(0);
+            const real exj1 = (yin && zin) ? fld<NC>(Ex + gn + pitch) : real(0);
+            const real ezj = yin ? fld<NC>(Ez + g + pitch) : real(0);
+            const real ezij = (xin && yin) ? fld<NC>(Ez + g + pitch + 1) : real(0);
+            const real hyj = yin ? fld<NC>(Hy + g + pitch) : real(0);
+            const real oyj = yin ? fld<NC>(Oy + g + pitch) : real(0);
+            cx = (ex + exj) + (ex1 + exj1);
+            cc = (ez + ezi) + (ezj + ezij);
+            hby = (oy + hy) + (oyj + hyj);
+        }
         const real cy = (ey + eyi) + (ey1 + eyi1);
-        const real cc = (ez + ezi) + (ezj + ezij);
         const real hbx = (ox + hx) + (oxi + hxi);
-        const real hby = (oy + hy) + (oyj + hyj);
         const real hbz = (oz + hz) + (oz1 + hz1);
         const real sx = cy * hbz - cc * hby;
         const real sy = cc * hbx - cx * hbz;
         const real sz = cx * hby - cy * hbx;
         acc_t* F = static_cast<acc_t*>(a.fluence);
         const real dt16 = real(a.dt16);
-        F[g] = Acc::add(F[g], vec_norm(sx * sx + sy * sy + sz * sz) * dt16);
+        if (live) F[g] = Acc::add(F[g], vec_norm(sx * sx + sy * sy + sz * sz) * dt16);
     }
 }
 
@@ -365,8 +415,11 @@ __device__ __forceinline__ void e_block(const StepArgs<real>& a, Cpx<real> te, C
     const int i0 = (gridDim.x - 1 - blockIdx.x) * 32, j0 = (gridDim.y - 1 - blockIdx.y) * TY;
     const int k = a.kbase + int(gridDim.z - 1 - blockIdx.z);
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (cell_gen_e<real, TY>(a, i0, j0) || (WALL && cell_gen_z(a, k))) e_cell<real, true, WALL>(a, te, tw, i, j, k);
-    else e_cell<real, false, WALL>(a, te, tw, i, j, k);
+    constexpr int SHY = std::is_same<real, double>::value ? TY : 0;   // FP64: fluence sums shared along y
+    __shared__ real s_half[SHY > 0 ? 3 * 32 * SHY : 1];
+    if (cell_gen_e<real, TY>(a, i0, j0) || (WALL && cell_gen_z(a, k)))
+        e_cell<real, true, WALL, true, SHY>(a, te, tw, i, j, k, s_half);
+    else e_cell<real, false, WALL, true, SHY>(a, te, tw, i, j, k, s_half);
 }
 
 // z-periodic grids without a wall sheet.
