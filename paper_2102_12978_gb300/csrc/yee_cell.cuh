@@ -327,25 +327,25 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
         const int gn = (k + 1 == nz) ? g - k * plane : g + plane;
         const bool xin = !GEN || i + 1 < nx, yin = !GEN || j + 1 < ny;
         const bool zin = !(WALL && GEN && a.zw) || k + 1 < nz;   // plane k+1 inside the z walls
-        const real ex1 = zin ? fld<NC>(Ex + gn) : real(0), ey1 = zin ? fld<NC>(Ey + gn) : real(0);
-        const real eyi = xin ? fld<NC>(Ey + g + 1) : real(0);
-        const real eyi1 = (xin && zin) ? fld<NC>(Ey + gn + 1) : real(0);
-        const real ezi = xin ? fld<NC>(Ez + g + 1) : real(0);
-        const real hxi = xin ? fld<NC>(Hx + g + 1) : real(0);
-        const real hz1 = zin ? fld<NC>(Hz + gn) : real(0);
-        const real ox = fld<NC>(Ox + g), oy = fld<NC>(Oy + g), oz = fld<NC>(Oz + g);
-        const real oz1 = zin ? fld<NC>(Oz + gn) : real(0);
-        const real oxi = xin ? fld<NC>(Ox + g + 1) : real(0);
-        // the sums over the cell's two y faces: E_x over its four y-z edges,
-        // E_z over its four x-y edges, H_y over the two faces and two times.
-        // Each is the sum of a row-j half and a row-(j+1) half, and the row-j
-        // half of cell (i, j+1) is the row-(j+1) half of cell (i, j): FP64
-        // blocks (SHY) take the row-(j+1) halves from the thread of row j+1
-        // where it lies in the block and the box.  FP64 adds E_x's halves
-        // over z first (the same order on every FP64 path, shared or not),
-        // FP32 over y first (the order of the two-step kernel).
-        real cx, cc, hby;
+        real cx, cy, cc, hbx, hby, hbz;
         if constexpr (F64) {
+            const real ex1 = zin ? fld<NC>(Ex + gn) : real(0), ey1 = zin ? fld<NC>(Ey + gn) : real(0);
+            const real eyi = xin ? fld<NC>(Ey + g + 1) : real(0);
+            const real eyi1 = (xin && zin) ? fld<NC>(Ey + gn + 1) : real(0);
+            const real ezi = xin ? fld<NC>(Ez + g + 1) : real(0);
+            const real hxi = xin ? fld<NC>(Hx + g + 1) : real(0);
+            const real hz1 = zin ? fld<NC>(Hz + gn) : real(0);
+            const real ox = fld<NC>(Ox + g), oy = fld<NC>(Oy + g), oz = fld<NC>(Oz + g);
+            const real oz1 = zin ? fld<NC>(Oz + gn) : real(0);
+            const real oxi = xin ? fld<NC>(Ox + g + 1) : real(0);
+            // The sums over the cell's two y faces (E_x over its four y-z
+            // edges, E_z over its four x-y edges, H_y over two faces and two
+            // times) are each a row-j half plus a row-(j+1) half, and the
+            // row-j half of cell (i, j+1) is the row-(j+1) half of cell
+            // (i, j).  SHY blocks take the row-(j+1) halves from the thread of
+            // row j+1 where it lies in the block and the box.  E_x's halves
+            // are summed over z first on every FP64 path, shared or not, so
+            // that all FP64 paths agree bit for bit.
             const real xh = ex + ex1, zh = ez + ezi, yh = oy + hy;   // row j
             real xh1, zh1, yh1;                                       // row j+1
             bool shared = false;
@@ -369,22 +369,34 @@ __device__ __forceinline__ void e_cell(const StepArgs<real>& a, Cpx<real> te, Cp
                 yh1 = o0 + h0;
             }
             cx = xh + xh1;
+            cy = (ey + eyi) + (ey1 + eyi1);
             cc = zh + zh1;
+            hbx = (ox + hx) + (oxi + hxi);
             hby = yh + yh1;
+            hbz = (oz + hz) + (oz1 + hz1);
         } else {
+            const real ex1 = zin ? fld<NC>(Ex + gn) : real(0), ey1 = zin ? fld<NC>(Ey + gn) : real(0);
             const real exj = yin ? fld<NC>(Ex + g + pitch) : real(0);
             const real exj1 = (yin && zin) ? fld<NC>(Ex + gn + pitch) : real(0);
+            const real eyi = xin ? fld<NC>(Ey + g + 1) : real(0);
+            const real eyi1 = (xin && zin) ? fld<NC>(Ey + gn + 1) : real(0);
+            const real ezi = xin ? fld<NC>(Ez + g + 1) : real(0);
             const real ezj = yin ? fld<NC>(Ez + g + pitch) : real(0);
             const real ezij = (xin && yin) ? fld<NC>(Ez + g + pitch + 1) : real(0);
+            const real hxi = xin ? fld<NC>(Hx + g + 1) : real(0);
             const real hyj = yin ? fld<NC>(Hy + g + pitch) : real(0);
+            const real hz1 = zin ? fld<NC>(Hz + gn) : real(0);
+            const real ox = fld<NC>(Ox + g), oy = fld<NC>(Oy + g), oz = fld<NC>(Oz + g);
+            const real oz1 = zin ? fld<NC>(Oz + gn) : real(0);
+            const real oxi = xin ? fld<NC>(Ox + g + 1) : real(0);
             const real oyj = yin ? fld<NC>(Oy + g + pitch) : real(0);
             cx = (ex + exj) + (ex1 + exj1);
+            cy = (ey + eyi) + (ey1 + eyi1);
             cc = (ez + ezi) + (ezj + ezij);
+            hbx = (ox + hx) + (oxi + hxi);
             hby = (oy + hy) + (oyj + hyj);
+            hbz = (oz + hz) + (oz1 + hz1);
         }
-        const real cy = (ey + eyi) + (ey1 + eyi1);
-        const real hbx = (ox + hx) + (oxi + hxi);
-        const real hbz = (oz + hz) + (oz1 + hz1);
         const real sx = cy * hbz - cc * hby;
         const real sy = cc * hbx - cx * hbz;
         const real sz = cx * hby - cy * hbx;
