@@ -85,11 +85,15 @@ struct Tb2Smem {
     static constexpr int NT = 32 * RY;   // threads (columns) per window
     static constexpr int R = 4;          // ring slots per thread (copies run two planes ahead)
     static constexpr int NF = 14;        // ring floats per slot: E^n 3, H^{n-1/2} 3, psi 8
+    // exchange arrays: one row of zeros before and after the window's RY rows
+    // (the values of the rows beyond it), so that a y neighbour is one plain
+    // shared load; thread tid's value at XO + tid
+    static constexpr int XS = NT + 64, XO = 32;
     static constexpr size_t bytes()
     {
         return size_t(R) * NT * 8                 // fluence accumulator (float2) per slot
                + size_t(R) * NF * NT * 4          // fields and psi per slot
-               + size_t(14) * NT * 4              // exchange: 2x2 E^n, 3 H^{n+1/2}, 2x2 E^{n+1}, 3 H^{n+3/2}
+               + size_t(14) * XS * 4              // exchange: 2x2 E^n, 3 H^{n+1/2}, 2x2 E^{n+1}, 3 H^{n+3/2}
                + size_t(12) * NT * 4;             // antenna coefficients of the column (6 complex)
     }
 };
@@ -155,10 +159,10 @@ template <int RY>
 struct Tb2Bufs {
     float2* fring;   // [R][NT]
     float* ring;     // [R][NF][NT]
-    float* EB;       // [2][Ez, Ex][NT]: E^n of a plane
-    float* HB;       // [Hx, Hz, Hy^{n-1/2} + Hy^{n+1/2}][NT]
-    float* E1B;      // [2][Ez, Ex][NT]: E^{n+1}
-    float* H1B;      // [Hx, Hz, Hy^{n+1/2} + Hy^{n+3/2}][NT]
+    float* EB;       // [2][Ez, Ex][XS]: E^n of a plane
+    float* HB;       // [Hx, Hz, Hy^{n-1/2} + Hy^{n+1/2}][XS]
+    float* E1B;      // [2][Ez, Ex][XS]: E^{n+1}
+    float* H1B;      // [Hx, Hz, Hy^{n+1/2} + Hy^{n+3/2}][XS]
     float* SC;       // [6][re, im][NT]: antenna coefficients
 };
 
@@ -215,10 +219,10 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
                                           float dt16, int u)
 {
     using S = Tb2Smem<RY>;
-    constexpr int NT = S::NT, NF = S::NF;
+    constexpr int NT = S::NT, NF = S::NF, XS = S::XS;
     const int SP = u, SQ = (u + 3) & 3, SR = (u + 2) & 3;   // slots of planes p, p-1, p-2
     constexpr int PP = U & 1, PQ = PP ^ 1;                        // exchange parities of planes p, p-1
-    const int lane = c.lane, row = c.row, tid = c.tid;
+    const int lane = c.lane, tid = c.tid;
     auto xp = [&](float v) {   // value of the +x neighbour (0 past the window)
         const float u = __shfl_down_sync(0xffffffffu, v, 1);
         return lane == 31 ? 0.0f : u;
@@ -227,8 +231,10 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         const float u = __shfl_up_sync(0xffffffffu, v, 1);
         return lane == 0 ? 0.0f : u;
     };
-    auto yp = [&](const float* q) { return row + 1 < RY ? q[tid + 32] : 0.0f; };
-    auto ym = [&](const float* q) { return row > 0 ? q[tid - 32] : 0.0f; };
+    // y neighbours from the padded exchange arrays (zero beyond the window)
+    auto yp = [&](const float* q) { return q[S::XO + tid + 32]; };
+    auto ym = [&](const float* q) { return q[S::XO + tid - 32]; };
+    auto put = [&](float* q, float v) { q[S::XO + tid] = v; };
     const float cz = a.cz;
 
     cpa_wait1();
@@ -246,8 +252,8 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     float nPEx = 0.0f, nPEy = 0.0f, ncz = 0.0f, nHsz = 0.0f, nhbx = 0.0f;
     if (c.needA) {
         const float ox = rq[3 * NT], oy = rq[4 * NT], oz = rq[5 * NT];   // H^{n-1/2}(q)
-        const float* EBq = b.EB + PQ * 2 * NT;
-        const float ezj = yp(EBq), exj = yp(EBq + NT);
+        const float* EBq = b.EB + PQ * 2 * XS;
+        const float ezj = yp(EBq), exj = yp(EBq + XS);
         const float ezi = xp(ez), eyi = xp(ey);
         const float dEz_y = ezj - ez, dEy_z = en1 - ey, dEx_z = en0 - ex;
         const float dEz_x = ezi - ez, dEy_x = eyi - ey, dEx_y = exj - ex;
@@ -284,12 +290,12 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         nhbx = hsx + xp(hsx);
     }
     {
-        float* EBp = b.EB + PP * 2 * NT;
-        EBp[tid] = en2;
-        EBp[NT + tid] = en0;
-        b.HB[tid] = hx;
-        b.HB[NT + tid] = hz;
-        b.HB[2 * NT + tid] = hsy;
+        float* EBp = b.EB + PP * 2 * XS;
+        put(EBp, en2);
+        put(EBp + XS, en0);
+        put(b.HB, hx);
+        put(b.HB + XS, hz);
+        put(b.HB + 2 * XS, hsy);
     }
     __syncthreads();
 
@@ -297,7 +303,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     float nex = 0.0f, ney = 0.0f, nez = 0.0f;
     if (c.needB) {
         const float hyi = xm(hy), hzi = xm(hz);
-        const float hxj = ym(b.HB), hzj = ym(b.HB + NT);
+        const float hxj = ym(b.HB), hzj = ym(b.HB + XS);
         const float dHz_y = hz - hzj, dHy_z = hy - s.h1p[1], dHx_z = hx - s.h1p[0];
         const float dHz_x = hz - hzi, dHy_x = hy - hyi, dHx_y = hx - hxj;
         nex = ex + c.cey * dHz_y - cz * dHy_z;
@@ -329,7 +335,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     // fluence term of step n for plane r (sums of planes r and q)
     float nhby = 0.0f, tn_new = 0.0f;
     if (c.needFl) {
-        nhby = hsy + yp(b.HB + 2 * NT);
+        nhby = hsy + yp(b.HB + 2 * XS);
         tn_new = tb2_flux(s.fPEx + nPEx, s.fPEy + nPEy, s.fcz, s.fhbx, s.fhby, s.fHsz + nHsz, dt16);
     }
 
@@ -337,8 +343,8 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     float h2x = 0.0f, h2y = 0.0f, h2z = 0.0f, gsy = 0.0f;
     float mPEx = 0.0f, mPEy = 0.0f, mcz = 0.0f, mHsz = 0.0f, mhbx = 0.0f;
     if (c.needC) {
-        const float* E1Br = b.E1B + PP * 2 * NT;   // written one plane ago (parity of r = parity of p)
-        const float fezj = yp(E1Br), fexj = yp(E1Br + NT);
+        const float* E1Br = b.E1B + PP * 2 * XS;   // written one plane ago (parity of r = parity of p)
+        const float fezj = yp(E1Br), fexj = yp(E1Br + XS);
         const float fezi = xp(s.e1p[2]), feyi = xp(s.e1p[1]);
         const float dEz_y = fezj - s.e1p[2], dEy_z = ney - s.e1p[1], dEx_z = nex - s.e1p[0];
         const float dEz_x = fezi - s.e1p[2], dEy_x = feyi - s.e1p[1], dEx_y = fexj - s.e1p[0];
@@ -381,19 +387,19 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         mhbx = gsx + xp(gsx);
     }
     {
-        float* E1Bq = b.E1B + PQ * 2 * NT;
-        E1Bq[tid] = nez;
-        E1Bq[NT + tid] = nex;
-        b.H1B[tid] = h2x;
-        b.H1B[NT + tid] = h2z;
-        b.H1B[2 * NT + tid] = gsy;
+        float* E1Bq = b.E1B + PQ * 2 * XS;
+        put(E1Bq, nez);
+        put(E1Bq + XS, nex);
+        put(b.H1B, h2x);
+        put(b.H1B + XS, h2z);
+        put(b.H1B + 2 * XS, gsy);
     }
     __syncthreads();
 
     // ---- stage D: E^{n+2} of plane r
     if (c.needD) {
         const float hyi = xm(h2y), hzi = xm(h2z);
-        const float hxj = ym(b.H1B), hzj = ym(b.H1B + NT);
+        const float hxj = ym(b.H1B), hzj = ym(b.H1B + XS);
         const float dHz_y = h2z - hzj, dHy_z = h2y - s.h2py, dHx_z = h2x - s.h2px;
         const float dHz_x = h2z - hzi, dHy_x = h2y - hyi, dHx_y = h2x - hxj;
         float fx = s.e1p[0] + c.cey * dHz_y - cz * dHy_z;
@@ -436,7 +442,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     // fluence of plane p-3: the step-n term from the last plane, then step n+1
     float mhby = 0.0f;
     if (c.needFl) {
-        mhby = gsy + yp(b.H1B + 2 * NT);
+        mhby = gsy + yp(b.H1B + 2 * XS);
         if (valid && c.fown) {
             const float t1 = tb2_flux(s.gPEx + mPEx, s.gPEy + mPEy, s.gcz, s.ghbx, s.ghby, s.gHsz + mHsz, dt16);
             float2 acc = b.fring[SP * NT + tid];
@@ -569,11 +575,18 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
     Tb2Bufs<RY> b;
     b.fring = reinterpret_cast<float2*>(tb2_smem);
     b.ring = reinterpret_cast<float*>(b.fring + R * NT);
+    constexpr int XS = S::XS;
     b.EB = b.ring + R * NF * NT;
-    b.HB = b.EB + 4 * NT;
-    b.E1B = b.HB + 3 * NT;
-    b.H1B = b.E1B + 4 * NT;
-    b.SC = b.H1B + 3 * NT;
+    b.HB = b.EB + 4 * XS;
+    b.E1B = b.HB + 3 * XS;
+    b.H1B = b.E1B + 4 * XS;
+    b.SC = b.H1B + 3 * XS;
+    // the zero rows of the 14 exchange arrays (never written again; the
+    // first window's barrier orders these stores before any read)
+    for (int q = threadIdx.y * 32 + threadIdx.x; q < 14 * 64; q += NT) {
+        const int arr = q / 64, e = q % 64;
+        b.EB[arr * XS + (e < 32 ? e : NT + e)] = 0.0f;
+    }
     long long w = tw.start[blockIdx.x];
     const long long wend = tw.start[blockIdx.x + 1];
     while (w < wend) {
