@@ -295,7 +295,7 @@ def run_gpu(args):
         if args.tile:
             g.set_tile(*[int(x) for x in args.tile.split(",")])
         if args.balance:
-            g.set_balance(*[float(x) for x in args.balance.split(",")])
+            apply_balance(g, [float(x) for x in args.balance.split(",")])
         g.step(args.warmup)
         g.step(args.steps)
         g.sync()
@@ -388,7 +388,8 @@ def run_gpu(args):
                    "fluence": "fp64", "source_phase": "fp64",
                    "l2_flush": "inputs larger than L2 (fields + fluence = %.0f MB/step)"
                                % (ab32 * cells / 1e6),
-                   "tile_f32": list(tile32), "balance_f32": [round(x, 3) for x in balance32],
+                   "tile_f32": list(tile32), "balance_f32": ("measured per-window costs" if balance32[0] < 0
+                                                  else [round(x, 3) for x in balance32]),
                    "tile_f64": list(tile64), "parallelism": f"replicas{ws}",
                    "timing": f"median of {reps32} repeats of the {args.steps}-step block (>= {MIN_TIMED_S:g} s "
                              f"of GPU time)"},
@@ -443,13 +444,23 @@ def rel_l2_t(torch, x, y) -> float:
     return float(torch.linalg.vector_norm(x - y)) / den if den > 0 else float(torch.linalg.vector_norm(x))
 
 
+def apply_balance(g, balance):
+    """The variant-7 balance the autotuner chose: weights, or (-1, -1) for
+    ranges balanced on measured per-window costs (measured again on g; the
+    grid's antenna must be set)."""
+    if balance[0] < 0:
+        g.measure_balance()
+    else:
+        g.set_balance(*balance)
+
+
 def full_length_error(torch, make, steps, tile32, balance32):
     """Relative L2 of the FP32 fields and fluence against the FP64 GPU run
     after `steps` steps of the workload (its full run by default), per field
     component and for the fluence, in the bench's FP32 launch configuration."""
     a = make("f32")
     a.set_tile(*tile32)
-    a.set_balance(*balance32)
+    apply_balance(a, balance32)
     b = make("f64")
     a.step(steps)
     b.step(steps)
@@ -658,7 +669,9 @@ def run_e2e(torch, fdtd, w, dev, steps, barrier, ws, tile, balance):
                             precision="f32", fluence=True)
     g = fdtd.Grid(d, device=dev)
     g.set_tile(*tile)
-    g.set_balance(*balance)
+    if balance[0] < 0:   # measured costs: measured with the antenna the timed region sets again
+        g.set_source(m=w.m, theta=w.theta, pol=w.pol, r_center=w.r_center, thickness=w.thickness, ramp=w.ramp)
+    apply_balance(g, balance)
     barrier()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()

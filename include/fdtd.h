@@ -252,7 +252,7 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
  *      recomputing two rings of halo columns, so that fields, psi and the
  *      fluence cross HBM once per two steps.  An odd step count ends with
  *      one step of variant 5.  The CTAs' shares of the work are balanced on
- *      per-window cost weights (fdtd_set_balance).
+ *      per-window costs (fdtd_set_balance).
  * The TMA variants (1, 2, 4) have no FP64 32x16 tile (EINVAL).  A z-walled
  * grid or one with a wall source takes variant 5 only (EINVAL otherwise;
  * fdtd_autotune then times the ty of variant 5 only).
@@ -266,11 +266,24 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
  * window's plane is estimated to cost 1, plus w_shell if the window holds
  * CPML shell columns, plus w_antenna if it holds antenna columns, and each
  * CTA takes a contiguous range of (window, plane) work of equal estimated
- * cost.  Weights in [0, 16] (else EINVAL); defaults 0.25 and 0.2;
- * fdtd_autotune times a few pairs and keeps the fastest.  The results do not
- * depend on the weights, only the time does. */
+ * cost; a window also costs three planes at its start (the two-step
+ * wavefront refills there).  Weights in [0, 16] (else EINVAL); defaults 0.25
+ * and 0.2.  fdtd_autotune times a few pairs, then measures every window's
+ * cost per plane in two launches of the fastest (SM cycles per window,
+ * recorded by the kernel) and times ranges balanced on those measured
+ * costs; it keeps the fastest.  While the measured costs are in use,
+ * fdtd_get_balance returns -1 for both weights; fdtd_set_balance returns to
+ * the weights.  The results do not depend on the balance, only the time
+ * does. */
 fdtd_status fdtd_set_balance(fdtd_grid* g, float w_shell, float w_antenna);
 fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenna);
+/* Measure the per-window costs of the grid's variant-7 tile in two launches
+ * (four steps, run from a copy of the state and undone: the state is saved to
+ * `scratch_state`, fdtd_state_bytes bytes of device memory the caller owns,
+ * and restored) and balance the CTAs' ranges on them from now on, as
+ * fdtd_autotune does (the paper has no counterpart).  EINVAL unless the tile
+ * is variant 7; the costs are dropped when the antenna's columns change. */
+fdtd_status fdtd_measure_balance(fdtd_grid* g, void* scratch_state);
 
 /* Measurement (the paper has no counterpart): advance `nsteps` steps like
  * fdtd_step and time every kernel launch of a step with CUDA events recorded

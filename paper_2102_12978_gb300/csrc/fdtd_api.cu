@@ -101,6 +101,12 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
     L.zph = take(nz * 16);
     L.zph32 = take(nz * 8);
     L.flu_out = d.fluence ? take(nz * ny * nx * 8) : 0;
+    L.alist = take(2 * nx * ny * 4);
+    {   // per-window counters of variant 7's measuring launch, for its most windows (ty 8)
+        int t = 0, u = 0;
+        tb2_windows(d, 8, &t, &u);
+        L.tb2prof = take(size_t(t) * u * 16);
+    }
     L.err = take(256);
     L.total = off;
     return true;
@@ -445,6 +451,12 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->has_source = false;
     g->src_gen = 0;
     g->tb2_key.ry = 0;
+    g->tb2_cost_ry = 0;
+    g->tb2_cost_src = -1;
+    g->tb2_cost_gen = 0;
+    g->tb2_profile = false;
+    g->ant_cols[0] = g->ant_cols[1] = 0;
+    g->ant_apart = false;
     std::memset(&g->srct, 0, sizeof(g->srct));
     g->srct.dt = g->dt;
     g->batch_refs = 0;
@@ -463,7 +475,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     if (st != FDTD_OK) { delete g; return st; }
     g->tile = default_tile(*d, sms);
     for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 3; ++b) g->maps_ok[a][b] = g->hmaps_ok[a][b] = false;
+        for (int b = 0; b < 3; ++b) {
+            g->maps_ok[a][b] = g->hmaps_ok[a][b] = false;
+            if (b < 2) g->tb2_maps_ok[a][b] = false;
+        }
     st = cuda_check(cudaMemsetAsync(arena, 0, L.total, g->stream), "zero arena");
     if (st == FDTD_OK)
         st = (d->precision == FDTD_F64) ? upload_tables<double>(g) : upload_tables<float>(g);
@@ -572,11 +587,30 @@ fdtd_status fdtd_set_annulus_source(fdtd_grid* g, const fdtd_annulus_desc* s)
     if (st == FDTD_OK)
         st = cuda_check(cudaMemcpyAsync(A + g->L.zph32, zph32.data(), zph32.size() * 4, cudaMemcpyHostToDevice,
                                         g->stream), "upload source");
+    // the antenna's columns as two lists (H points, E points) for antenna_add
+    std::vector<int> alist;
+    int ncol_h = 0;
+    bool on_wall = false;
+    for (int side = 0; side < 2; ++side)
+        for (int j = 0; j < d.ny; ++j)
+            for (int i = 0; i < d.nx; ++i) {
+                const uint8_t m = mask[size_t(j) * d.nx + i] & (side == 0 ? 0x38 : 0x07);
+                if (!m) continue;
+                alist.push_back(j * d.nx + i);
+                on_wall = on_wall || i == 0 || j == 0;
+                if (side == 0) ++ncol_h;
+            }
+    if (st == FDTD_OK && !alist.empty())
+        st = cuda_check(cudaMemcpyAsync(A + g->L.alist, alist.data(), alist.size() * 4, cudaMemcpyHostToDevice,
+                                        g->stream), "upload source");
     if (st == FDTD_OK) st = cuda_check(cudaStreamSynchronize(g->stream), "upload source");
     if (st != FDTD_OK) return st;
+    g->ant_cols[0] = ncol_h;
+    g->ant_cols[1] = int(alist.size()) - ncol_h;
+    g->ant_apart = !on_wall;
     g->has_source = true;
+    if (mask != g->hmask) g->src_gen += 1;   // the antenna's columns changed
     g->hmask = mask;
-    g->src_gen += 1;
     g->src = *s;
     g->src.w_amp = nullptr;
     g->src.w_phase = nullptr;
@@ -678,6 +712,7 @@ fdtd_status fdtd_clear_source(fdtd_grid* g)
     if (g->batch_refs > 0) return not_batched(g, "fdtd_clear_source");
     g->has_source = false;
     g->hmask.clear();
+    g->ant_cols[0] = g->ant_cols[1] = 0;
     g->src_gen += 1;
     for (int c = 0; c < 6; ++c) g->counts[c] = 0;
     return FDTD_OK;
@@ -705,6 +740,49 @@ static cudaError_t run_steps(fdtd_grid* g, int nsteps, const TileConfig& tc)
         g->step += 1;
     }
     return cudaSuccess;
+}
+
+// Launches of variant 7 in configuration tc that record every window's SM
+// cycles and wavefront iterations (kMeasureLaunches, counters summed), then
+// the per-window costs stored on the grid (tb2_store_costs).  Advances the
+// grid by 2 kMeasureLaunches steps.
+constexpr int kMeasureLaunches = 2;
+static cudaError_t tb2_measure(fdtd_grid* g, const TileConfig& tc)
+{
+    int T = 0, U = 0;
+    tb2_windows(g->desc, tc.ty, &T, &U);
+    const size_t nw = size_t(T) * U;
+    void* prof = static_cast<char*>(g->arena) + g->L.tb2prof;
+    cudaError_t err = cudaMemsetAsync(prof, 0, nw * 16, g->stream);
+    if (err != cudaSuccess) return err;
+    g->tb2_profile = true;
+    err = run_steps(g, 2 * kMeasureLaunches, tc);
+    g->tb2_profile = false;
+    if (err != cudaSuccess) return err;
+    std::vector<unsigned long long> counts(2 * nw);
+    err = cudaMemcpyAsync(counts.data(), prof, nw * 16, cudaMemcpyDeviceToHost, g->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(g->stream);
+    if (err != cudaSuccess) return err;
+    tb2_store_costs(g, tc.ty, counts.data());
+    return cudaSuccess;
+}
+
+fdtd_status fdtd_measure_balance(fdtd_grid* g, void* scratch_state)
+{
+    if (!g || !scratch_state) return fail(FDTD_EINVAL, "null argument");
+    const fdtd_status dev_st = check_device(g, "fdtd_measure_balance");
+    if (dev_st != FDTD_OK) return dev_st;
+    if (g->batch_refs > 0) return not_batched(g, "fdtd_measure_balance");
+    if (g->tile.variant != 7) return fail(FDTD_EINVAL, "fdtd_measure_balance needs tile variant 7");
+    fdtd_status st = fdtd_save_state(g, scratch_state);
+    if (st != FDTD_OK) return st;
+    TileConfig tc = g->tile;
+    const cudaError_t err = tb2_measure(g, tc);
+    st = fdtd_load_state(g, scratch_state);
+    if (err != cudaSuccess) return cuda_check(err, "fdtd_measure_balance");
+    if (st != FDTD_OK) return st;
+    g->tile.measured = true;
+    return FDTD_OK;
 }
 
 fdtd_status fdtd_step(fdtd_grid* g, int nsteps)
@@ -973,14 +1051,15 @@ fdtd_status fdtd_set_balance(fdtd_grid* g, float w_shell, float w_antenna)
         return fail(FDTD_EINVAL, "balance weights %g, %g outside [0, 16]", w_shell, w_antenna);
     g->tile.w_shell = w_shell;
     g->tile.w_ant = w_antenna;
+    g->tile.measured = false;
     return FDTD_OK;
 }
 
 fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenna)
 {
     if (!g || !w_shell || !w_antenna) return fail(FDTD_EINVAL, "null argument");
-    *w_shell = g->tile.w_shell;
-    *w_antenna = g->tile.w_ant;
+    *w_shell = g->tile.measured ? -1.0f : g->tile.w_shell;
+    *w_antenna = g->tile.measured ? -1.0f : g->tile.w_ant;
     return FDTD_OK;
 }
 
@@ -1050,6 +1129,24 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) { best = ms; best_tc = tc; }
         }
+    // variant 7: measure each window's cost in launches of the fastest
+    // configuration, then time the ranges balanced on the measured costs
+    if (err == cudaSuccess && best_tc.variant == 7) do {
+        err = tb2_measure(g, best_tc);
+        if (err != cudaSuccess) break;
+        TileConfig tc = best_tc;
+        tc.measured = true;
+        err = run_steps(g, 2, tc);   // warm-up
+        if (err != cudaSuccess) break;
+        cudaEventRecord(e0, g->stream);
+        err = run_steps(g, nrun, tc);
+        cudaEventRecord(e1, g->stream);
+        if (err != cudaSuccess) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_tc = tc; }
+    } while (false);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g->fault = 0;

@@ -10,6 +10,7 @@
 #include "yee_fused.cuh"
 #include "yee_tma.cuh"
 #include "yee_cell.cuh"
+#include "yee_tb2.cuh"
 
 namespace fdtd {
 
@@ -30,6 +31,8 @@ struct Layout {
     size_t smask = 0, scoef = 0, scoef32 = 0, zph = 0, zph32 = 0;
     size_t scoef_unw = 0, wamp = 0, wphase = 0;   // unweighted coefficients and the weights
     size_t flu_out = 0;    // dense FP64 export of the fluence
+    size_t tb2prof = 0;    // variant 7: per-window cycle and iteration counters of a measuring launch
+    size_t alist = 0;      // antenna columns (int): those with H points, then those with E points
     size_t err = 0;        // device error word (int)
     size_t total = 0;
 };
@@ -50,6 +53,9 @@ struct TileConfig {
     // columns, relative to a plain window (the CTAs' work ranges are balanced
     // on these estimates)
     float w_shell = 0.25f, w_ant = 0.2f;
+    // variant 7: balance on the per-window costs measured by the autotuner
+    // (fdtd_grid::tb2_cost) instead of the weights above
+    bool measured = false;
 };
 
 fdtd_status fail(fdtd_status st, const char* fmt, ...);
@@ -96,12 +102,23 @@ struct fdtd_grid {
     fdtd_wall_desc wall;
     fdtd::SrcTime wallt;        // time envelope of the wall source
     std::vector<uint8_t> hmask; // antenna component mask per (i, j) column (host copy), empty without a source
-    int src_gen;                // bumped whenever the antenna changes
+    int src_gen;                // bumped whenever the antenna's columns (hmask) change
+    int ant_cols[2];            // antenna columns with H points, with E points (lists at L.alist)
+    bool ant_apart;             // the FP64 cell passes may add the source in antenna_add (no antenna
+                                // column on the i = 0 or j = 0 wall, where the E pass zeroes after it)
     std::vector<long long> tb2_start;   // variant 7: cached CTA work ranges
     struct {
-        int ry, slots, src_gen;
+        int ry, slots, src_gen, cost_gen;
         float w_shell, w_ant;
+        bool measured;
     } tb2_key;                          // what they were computed for (ry 0: nothing cached)
+    std::vector<double> tb2_cost;       // variant 7: measured cost per window-plane (tb2_cost_ry windows)
+    int tb2_cost_ry;                    // the window height they were measured for (0: none)
+    int tb2_cost_src;                   // the antenna generation they were measured with
+    int tb2_cost_gen;                   // bumped whenever tb2_cost changes
+    bool tb2_profile;                   // the next variant-7 launches record per-window costs
+    fdtd::Tb2Maps tb2_maps[2][2];       // TMA maps of variant 7: [read copy][ty 8, 16]
+    bool tb2_maps_ok[2][2];
 };
 
 namespace fdtd {
@@ -124,6 +141,12 @@ inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 && tc.
 // copy g->pe into the other copies.  FP32, z-periodic grids without a wall
 // source only.
 cudaError_t launch_tb2(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
+// Windows of variant 7 with 32 x ry columns on grid d: t along x, u along y.
+void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u);
+// Per-window cost per wavefront iteration from the counters (2 per window) of
+// a measuring launch with windows of 32 x ry columns; windows no segment
+// covered take the mean.  Stored on the grid for the plans of tc.measured.
+void tb2_store_costs(fdtd_grid* g, int ry, const unsigned long long* prof);
 // The same two steps with their time factors from a device table of
 // StepTime<float> (entries i0, i1), on at most max_ctas CTAs (a batch runs
 // several grids side by side): the batched graph's launch.

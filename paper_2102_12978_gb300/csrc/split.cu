@@ -110,8 +110,27 @@ static cudaError_t launch_step_cell(const fdtd_grid* g, int cur, long long n, cu
     return cudaGetLastError();
 }
 
+// FP64 grids with an antenna (z-periodic, no wall sheet) add its source in
+// antenna_add after each pass instead of inside it.
+template <typename real>
+static cudaError_t antenna_pass(const fdtd_grid* g, const StepArgs<real>& a, int side, Cpx<real> t, cudaStream_t s)
+{
+    const int ncols = g->ant_cols[side];
+    if (ncols == 0) return cudaSuccess;
+    const int* cols = reinterpret_cast<const int*>(static_cast<const char*>(g->arena) + g->L.alist) +
+                      (side == 0 ? 0 : g->ant_cols[0]);
+    const long long pts = (long long)ncols * g->desc.nz;
+    const unsigned blocks = unsigned((pts + 255) / 256);
+    if (side == 0)
+        antenna_add<real><<<blocks, 256, 0, s>>>(a, cols, ncols, 3, t, a.hout[0], a.hout[1], a.hout[2]);
+    else
+        antenna_add<real><<<blocks, 256, 0, s>>>(a, cols, ncols, 0, t, a.eout[0], a.eout[1], a.eout[2]);
+    return cudaGetLastError();
+}
+
 // Cell-parallel passes: yee_h_cell then yee_e_cell (with the fluence term),
-// or yee_h_cell_w then yee_e_cell_w on grids with z walls or a wall sheet;
+// or yee_h_cell_w then yee_e_cell_w on grids with z walls or a wall sheet
+// (FP64 z-periodic grids: each pass followed by antenna_add);
 // 32 x TY threads, one cell each, one plane per grid z index.  Grids of more
 // than kMaxPlanes planes launch each pass in chunks of planes (the H pass's
 // chunks in order, the E pass's in reverse, as its blocks run).
@@ -122,14 +141,21 @@ static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStr
     const StepTime<real> t = step_time<real>(g->srct, g->has_wall ? &g->wallt : nullptr, g->dt, n);
     const int nz = g->desc.nz, nchunk = (nz + kMaxPlanes - 1) / kMaxPlanes;
     dim3 block(32, TY);
-    StepArgs<real> a = make_args<real>(g, cur);
     const bool wall = needs_cell_passes(g);   // z walls or a wall sheet: the *_w kernels
+    const bool apart = sizeof(real) == 8 && g->has_source && g->ant_apart && !wall;
+    const StepArgs<real> full = make_args<real>(g, cur);
+    StepArgs<real> a = full;
+    if (apart) a.smask = nullptr;   // the passes run without the antenna
     for (int c = 0; c < nchunk; ++c) {
         a.kbase = c * kMaxPlanes;
         dim3 grid((g->desc.nx + 31) / 32, (g->desc.ny + TY - 1) / TY, nz - a.kbase < kMaxPlanes ? nz - a.kbase : kMaxPlanes);
         if (wall) yee_h_cell_w<real, TY><<<grid, block, 0, s>>>(a, t);
         else yee_h_cell<real, TY><<<grid, block, 0, s>>>(a, t);
         cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (apart) {
+        const cudaError_t e = antenna_pass<real>(g, full, 0, t.th, s);
         if (e != cudaSuccess) return e;
     }
     if (mid) cudaEventRecord(mid, s);
@@ -141,6 +167,7 @@ static cudaError_t launch_cell(const fdtd_grid* g, int cur, long long n, cudaStr
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (apart) return antenna_pass<real>(g, full, 1, t.te, s);
     return cudaSuccess;
 }
 

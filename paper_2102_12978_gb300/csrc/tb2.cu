@@ -8,48 +8,86 @@
 #include <cmath>
 
 #include "grid_impl.h"
+#include "tma_host.h"
 #include "yee_tb2.cuh"
 
 namespace fdtd {
 
+void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u)
+{
+    *t = d.nx <= kTb2Wx ? 1 : (d.nx - kTb2Wx + kTb2Sx - 1) / kTb2Sx + 1;
+    *u = d.ny <= ry ? 1 : (d.ny - ry + (ry - 4) - 1) / (ry - 4) + 1;
+}
+
+void tb2_store_costs(fdtd_grid* g, int ry, const unsigned long long* prof)
+{
+    int T = 0, U = 0;
+    tb2_windows(g->desc, ry, &T, &U);
+    const size_t nw = size_t(T) * U;
+    std::vector<double> c(nw, 0.0);
+    double sum = 0.0;
+    size_t n = 0;
+    for (size_t w = 0; w < nw; ++w)
+        if (prof[2 * w + 1] > 0) {
+            c[w] = double(prof[2 * w]) / double(prof[2 * w + 1]);
+            sum += c[w];
+            ++n;
+        }
+    const double mean = n > 0 && sum > 0.0 ? sum / double(n) : 1.0;
+    for (size_t w = 0; w < nw; ++w) c[w] = (prof[2 * w + 1] > 0 ? c[w] : mean) / mean;
+    g->tb2_cost = c;
+    g->tb2_cost_ry = ry;
+    g->tb2_cost_src = g->src_gen;
+    g->tb2_cost_gen += 1;
+}
+
 // CTA work ranges of variant 7 on grid g: windows of 32 x RY columns, `slots`
-// resident CTAs.  A window's plane costs 1, plus w_shell if the window holds
-// CPML shell columns, plus w_ant if it holds antenna columns; each CTA gets a
-// contiguous range of (window, plane) items of about the same total cost.
-// Cached on the grid until the antenna, the weights or the launch shape change.
+// resident CTAs.  Each window-plane has a cost: measured per window by the
+// autotuner (tc.measured), or estimated as 1, plus w_shell if the window
+// holds CPML shell columns, plus w_ant if it holds antenna columns.  A window
+// also costs kRestart iterations at its start (the wavefront refills).  Each
+// CTA gets a contiguous range of (window, plane) items of about the same
+// total cost.  Cached on the grid until the antenna, the costs or the launch
+// shape change.
+constexpr double kRestart = 3.0;
 static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2Plan& P)
 {
     const fdtd_grid_desc& d = g->desc;
-    P.T = d.nx <= kTb2Wx ? 1 : (d.nx - kTb2Wx + kTb2Sx - 1) / kTb2Sx + 1;
-    P.U = d.ny <= RY ? 1 : (d.ny - RY + (RY - 4) - 1) / (RY - 4) + 1;
+    tb2_windows(d, RY, &P.T, &P.U);
+    P.prof = nullptr;
+    const bool meas = tc.measured && g->tb2_cost_ry == RY && g->tb2_cost_src == g->src_gen &&
+                      g->tb2_cost.size() == size_t(P.T) * P.U;
     auto& key = g->tb2_key;
-    if (key.ry != RY || key.slots != slots || key.src_gen != g->src_gen || key.w_shell != tc.w_shell ||
-        key.w_ant != tc.w_ant) {
+    if (key.ry != RY || key.slots != slots || key.src_gen != g->src_gen || key.measured != meas ||
+        (meas ? key.cost_gen != g->tb2_cost_gen : (key.w_shell != tc.w_shell || key.w_ant != tc.w_ant))) {
         const int nx = d.nx, ny = d.ny, nz = d.nz, npml = d.npml;
         const int nw = P.T * P.U;
         std::vector<double> cost(size_t(nw), 1.0);
-        for (int wy = 0; wy < P.U; ++wy)
-            for (int wx = 0; wx < P.T; ++wx) {
-                const int i0 = kTb2Sx * wx, i1 = std::min(i0 + kTb2Wx, nx);
-                const int j0 = (RY - 4) * wy, j1 = std::min(j0 + RY, ny);
-                const bool shell = npml > 0 && (i0 < npml || i1 > nx - npml || j0 < npml || j1 > ny - npml);
-                bool ant = false;
-                if (!g->hmask.empty())
-                    for (int j = j0; j < j1 && !ant; ++j)
-                        for (int i = i0; i < i1 && !ant; ++i) ant = g->hmask[size_t(j) * nx + i] != 0;
-                cost[size_t(wy) * P.T + wx] = 1.0 + (shell ? tc.w_shell : 0.0) + (ant ? tc.w_ant : 0.0);
-            }
+        if (meas) cost = g->tb2_cost;
+        else
+            for (int wy = 0; wy < P.U; ++wy)
+                for (int wx = 0; wx < P.T; ++wx) {
+                    const int i0 = kTb2Sx * wx, i1 = std::min(i0 + kTb2Wx, nx);
+                    const int j0 = (RY - 4) * wy, j1 = std::min(j0 + RY, ny);
+                    const bool shell = npml > 0 && (i0 < npml || i1 > nx - npml || j0 < npml || j1 > ny - npml);
+                    bool ant = false;
+                    if (!g->hmask.empty())
+                        for (int j = j0; j < j1 && !ant; ++j)
+                            for (int i = i0; i < i1 && !ant; ++i) ant = g->hmask[size_t(j) * nx + i] != 0;
+                    cost[size_t(wy) * P.T + wx] = 1.0 + (shell ? tc.w_shell : 0.0) + (ant ? tc.w_ant : 0.0);
+                }
         double total = 0.0;
-        for (double c : cost) total += c * nz;
+        for (double c : cost) total += c * (nz + kRestart);
         const double share = total / slots;
         std::vector<long long> start(size_t(slots) + 1, (long long)nw * nz);
         start[0] = 0;
         int c = 1;
         double cum = 0.0;
         for (int w = 0; w < nw && c < slots; ++w) {
-            const double span = cost[size_t(w)] * nz;
+            const double cw = cost[size_t(w)];
+            const double span = cw * (nz + kRestart), base = cum + cw * kRestart;
             while (c < slots && c * share < cum + span) {
-                long long k = (long long)std::ceil((c * share - cum) / cost[size_t(w)]);
+                long long k = (long long)std::ceil((c * share - base) / cw);
                 k = std::max(0LL, std::min((long long)nz, k));
                 start[size_t(c)] = std::max(start[size_t(c) - 1], (long long)w * nz + k);
                 ++c;
@@ -59,8 +97,29 @@ static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2P
         g->tb2_start = start;
         key.ry = RY; key.slots = slots; key.src_gen = g->src_gen;
         key.w_shell = tc.w_shell; key.w_ant = tc.w_ant;
+        key.measured = meas; key.cost_gen = g->tb2_cost_gen;
     }
     for (int c = 0; c <= slots; ++c) P.start[c] = g->tb2_start[size_t(c)];
+}
+
+// TMA maps of the copy `cur` for windows of 32 x RY columns (cached on the grid).
+template <int RY>
+static const Tb2Maps* tb2_maps(fdtd_grid* g, int cur)
+{
+    const int sl = RY == 8 ? 0 : 1;
+    Tb2Maps& m = g->tb2_maps[cur][sl];
+    if (!g->tb2_maps_ok[cur][sl]) {
+        char* A = static_cast<char*>(g->arena);
+        bool ok = true;
+        for (int c = 0; c < 6; ++c)
+            ok = ok && encode_map(&m.f[c], A + g->L.field[cur][c], 4, g->desc, g->L.pitch, kTb2Wx, RY);
+        void* fbase = g->desc.fluence ? static_cast<void*>(A + g->L.fluence) : static_cast<void*>(A + g->L.field[cur][0]);
+        ok = ok && encode_map(&m.flu, fbase, 8, g->desc, g->L.pitch, kTb2Wx, RY);
+        if (!ok) return nullptr;
+        m.err = reinterpret_cast<int*>(A + g->L.err);
+        g->tb2_maps_ok[cur][sl] = true;
+    }
+    return &m;
 }
 
 // Resident CTAs per SM of the kernels of one RY (dynamic shared memory set
@@ -69,10 +128,13 @@ template <int RY>
 static cudaError_t tb2_blocks_per_sm(int* out)
 {
     using S = Tb2Smem<RY>;
+    static_assert(S::bytes() <= 232448, "the window's shared memory exceeds the 227 KB a CTA can hold");
     static int blocks_per_sm = 0;
     if (blocks_per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(yee_tb2<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(S::bytes()));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(yee_tb2_tma<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::bytes()));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(yee_tb2_t<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::bytes()));
         if (e != cudaSuccess) return e;
@@ -97,11 +159,19 @@ static cudaError_t launch_tb2_t(const fdtd_grid* cg, int cur, long long n, const
     const int slots = std::min(kTb2MaxCtas, (g->sm_count > 0 ? g->sm_count : 152) * per_sm);
     Tb2Plan plan;
     tb2_plan(g, RY, slots, tc, plan);
+    if (g->tb2_profile)
+        plan.prof = reinterpret_cast<unsigned long long*>(static_cast<char*>(g->arena) + g->L.tb2prof);
     const StepTime<float> t0 = step_time<float>(g->srct, nullptr, g->dt, n);
     const StepTime<float> t1 = step_time<float>(g->srct, nullptr, g->dt, n + 1);
     Tb2Times tt;
     tt.th0 = t0.th; tt.te0 = t0.te; tt.th1 = t1.th; tt.te1 = t1.te;
-    yee_tb2<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), tt, plan);
+    if (tc.lz == 2) {
+        const Tb2Maps* m = tb2_maps<RY>(g, cur);
+        if (!m) return cudaErrorInvalidValue;
+        yee_tb2_tma<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), tt, plan, *m);
+    } else {
+        yee_tb2<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), tt, plan);
+    }
     return cudaGetLastError();
 }
 

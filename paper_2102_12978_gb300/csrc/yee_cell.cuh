@@ -89,18 +89,54 @@ __device__ __forceinline__ bool cell_gen_z(const StepArgs<real>& a, int k)
     return a.zw && (k == 0 || k + 1 == a.nz || k < a.npz || k >= a.nz - a.npz);
 }
 
+// Rounding of the source terms pinned by explicit operations (no contraction
+// left to the compiler), so that the term added inside a pass and the one
+// added by antenna_add round alike.
+__device__ __forceinline__ float mul_rn(float x, float y) { return __fmul_rn(x, y); }
+__device__ __forceinline__ double mul_rn(double x, double y) { return __dmul_rn(x, y); }
+__device__ __forceinline__ float fma_rn(float x, float y, float z) { return __fmaf_rn(x, y, z); }
+__device__ __forceinline__ double fma_rn(double x, double y, double z) { return __fma_rn(x, y, z); }
+
 template <typename real>
 __device__ __forceinline__ Cpx<real> plane_factor(const StepArgs<real>& a, int k, Cpx<real> t)
 {
     const Cpx<real> z = static_cast<const Cpx<real>*>(a.zphr)[k];
-    return Cpx<real>{z.x * t.x - z.y * t.y, z.x * t.y + z.y * t.x};
+    return Cpx<real>{fma_rn(z.x, t.x, -mul_rn(z.y, t.y)), fma_rn(z.x, t.y, mul_rn(z.y, t.x))};
 }
 
 template <typename real>
 __device__ __forceinline__ real src_add(const StepArgs<real>& a, int c, int col, Cpx<real> u)
 {
     const Cpx<real> b = static_cast<const Cpx<real>*>(a.scoefr)[c * a.nx * a.ny + col];
-    return b.x * u.x - b.y * u.y;
+    return fma_rn(b.x, u.x, -mul_rn(b.y, u.y));
+}
+
+// The soft source of Eq. 13 for one side of the antenna, as a pass of its
+// own over the antenna's columns only: F_c += Re{coef_c u_k} at every
+// antenna point (column cols[q], plane k) of the components c0 .. c0 + 2
+// (c0 = 0: E, 3: H) the column's mask holds, u_k = e^{i beta z_k} t.  The
+// cell passes then run without the source (smask null).  Used by the FP64
+// cell passes: there the FP64 pipe charges a warp instruction whatever the
+// number of its active lanes, and the antenna's warps hold about two antenna
+// lanes of 32, so the source terms cost an order of magnitude more inside the
+// passes than here.  The terms are those the passes add, added last as there
+// (the antenna lies outside the CPML shell and off the PEC walls).
+template <typename real>
+__global__ void __launch_bounds__(256)
+antenna_add(const StepArgs<real> a, const int* __restrict__ cols, int ncols, int c0, Cpx<real> t,
+            real* __restrict__ f0, real* __restrict__ f1, real* __restrict__ f2)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= (long long)ncols * a.nz) return;
+    const int q = int(idx % ncols), k = int(idx / ncols);
+    const int col = cols[q];
+    const int j = col / a.nx, i = col - j * a.nx;
+    const uint8_t mk = a.smask[col] >> c0;
+    const Cpx<real> u = plane_factor(a, k, t);
+    const long long g = (long long)k * a.pitch * a.ny + (long long)j * a.pitch + i;
+    if (mk & 1) f0[g] = f0[g] + src_add(a, c0, col, u);
+    if (mk & 2) f1[g] = f1[g] + src_add(a, c0 + 1, col, u);
+    if (mk & 4) f2[g] = f2[g] + src_add(a, c0 + 2, col, u);
 }
 
 // Field loads.  NC: the read-only (non-coherent) path, for kernels in which

@@ -70,9 +70,13 @@ struct Tb2Times {
 // [start[c], start[c + 1]): ranges of equal estimated cost (a window's planes
 // cost more where the window holds CPML shell or antenna columns), chosen on
 // the host.
+// prof, if not null, receives per window w the SM cycles its segments took
+// (prof[2 w]) and the wavefront iterations they ran (prof[2 w + 1]): the
+// measured per-window costs the host balances the ranges on.
 constexpr int kTb2MaxCtas = 512;
 struct Tb2Plan {
     int T, U;
+    unsigned long long* prof;
     long long start[kTb2MaxCtas + 1];
 };
 
@@ -80,21 +84,35 @@ struct Tb2Plan {
 constexpr int kTb2Wx = 32;
 constexpr int kTb2Sx = 28;
 
+// Tensor maps of the TMA-fed kernel: E^n and H^{n-1/2} of the copy being
+// read and the fluence accumulator, boxes of 32 x RY x 1 (a window's columns
+// in one plane; elements past the box read as zero), and the grid's error
+// word, raised by a CTA whose wait for a copy gave up.
+struct Tb2Maps {
+    CUtensorMap f[6];
+    CUtensorMap flu;
+    int* err;
+};
+
 template <int RY>
 struct Tb2Smem {
     static constexpr int NT = 32 * RY;   // threads (columns) per window
     static constexpr int R = 4;          // ring slots per thread (copies run two planes ahead)
     static constexpr int NF = 14;        // ring floats per slot: E^n 3, H^{n-1/2} 3, psi 8
-    // exchange arrays: one row of zeros before and after the window's RY rows
+    // exchange arrays: a row of zeros before and after the window's RY rows
     // (the values of the rows beyond it), so that a y neighbour is one plain
-    // shared load; thread tid's value at XO + tid
-    static constexpr int XS = NT + 64, XO = 32;
+    // shared load; thread tid's value at XO + tid.  Consecutive arrays share
+    // a zero row (the row after array a is the row before array a + 1), and
+    // one more zero row follows the last array.
+    static constexpr int XS = NT + 32, XO = 32;
+    static constexpr int NX = 14;         // 2x2 E^n, 3 H^{n+1/2}, 2x2 E^{n+1}, 3 H^{n+3/2}
     static constexpr size_t bytes()
     {
         return size_t(R) * NT * 8                 // fluence accumulator (float2) per slot
                + size_t(R) * NF * NT * 4          // fields and psi per slot
-               + size_t(14) * XS * 4              // exchange: 2x2 E^n, 3 H^{n+1/2}, 2x2 E^{n+1}, 3 H^{n+3/2}
-               + size_t(12) * NT * 4;             // antenna coefficients of the column (6 complex)
+               + (size_t(NX) * XS + 32) * 4       // exchange arrays and their zero rows
+               + size_t(12) * NT * 4              // antenna coefficients of the column (6 complex)
+               + size_t(R) * 8 + 8;               // mbarriers of the ring slots, abort flag (TMA-fed kernel)
     }
 };
 
@@ -164,25 +182,41 @@ struct Tb2Bufs {
     float* E1B;      // [2][Ez, Ex][XS]: E^{n+1}
     float* H1B;      // [Hx, Hz, Hy^{n+1/2} + Hy^{n+3/2}][XS]
     float* SC;       // [6][re, im][NT]: antenna coefficients
+    uint64_t* bar;   // [R]: completion of a slot's TMA copies (TMA-fed kernel)
+    int* abort;      // set when a wait for a copy gave up (TMA-fed kernel)
 };
 
 __device__ __forceinline__ int next_plane(int k, int nz) { return k + 1 == nz ? 0 : k + 1; }
 
 // Copies of plane k (fluence plane kf) into ring slot s of this thread.
-template <int RY>
+// TMA: thread 0 copies the whole window's E^n, H^{n-1/2} and fluence boxes
+// (one mbarrier per slot, after a proxy fence: the slot's previous contents
+// were read by every thread before the last CTA barrier); every thread still
+// copies its own column's psi.
+template <int RY, bool TMA>
 __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col& c, const Tb2Bufs<RY>& b, int s,
-                                          int k, int kf)
+                                          int k, int kf, const Tb2Maps* maps)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF;
     float* r = b.ring + s * NF * NT + c.tid;
-    const int g = k * (a.pitch * a.ny) + c.col;
-    cpa4(r + 0 * NT, a.ein[0] + g, c.indom);
-    cpa4(r + 1 * NT, a.ein[1] + g, c.indom);
-    cpa4(r + 2 * NT, a.ein[2] + g, c.indom);
-    cpa4(r + 3 * NT, a.hin[0] + g, c.indom);
-    cpa4(r + 4 * NT, a.hin[1] + g, c.indom);
-    cpa4(r + 5 * NT, a.hin[2] + g, c.indom);
+    if constexpr (TMA) {
+        if (c.tid == 0) {
+            const int x0 = c.i - c.lane, y0 = c.j - c.row;
+            fence_proxy_async();
+            mbar_expect_tx(b.bar + s, uint32_t(NT) * (6 * 4 + (a.fluence ? 8 : 0)));
+            for (int q = 0; q < 6; ++q) tma_load_3d(b.ring + (s * NF + q) * NT, &maps->f[q], b.bar + s, x0, y0, k);
+            if (a.fluence) tma_load_3d(b.fring + s * NT, &maps->flu, b.bar + s, x0, y0, kf);
+        }
+    } else {
+        const int g = k * (a.pitch * a.ny) + c.col;
+        cpa4(r + 0 * NT, a.ein[0] + g, c.indom);
+        cpa4(r + 1 * NT, a.ein[1] + g, c.indom);
+        cpa4(r + 2 * NT, a.ein[2] + g, c.indom);
+        cpa4(r + 3 * NT, a.hin[0] + g, c.indom);
+        cpa4(r + 4 * NT, a.hin[1] + g, c.indom);
+        cpa4(r + 5 * NT, a.hin[2] + g, c.indom);
+    }
     if (c.sx) {
         const int q = k * a.ny * (2 * a.npml) + c.colx;
         cpa4(r + 6 * NT, a.phx_in[0] + q, true);    // Hyx
@@ -197,9 +231,11 @@ __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col
         cpa4(r + 12 * NT, a.pey[0] + q, true);      // Exy
         cpa4(r + 13 * NT, a.pey[1] + q, true);      // Ezy
     }
-    const float2* F = static_cast<const float2*>(a.fluence);
-    cpa8(b.fring + s * NT + c.tid, c.fown ? F + kf * (a.pitch * a.ny) + c.col : reinterpret_cast<const float2*>(a.ein[0]),
-         c.fown);
+    if constexpr (!TMA) {
+        const float2* F = static_cast<const float2*>(a.fluence);
+        cpa8(b.fring + s * NT + c.tid,
+             c.fown ? F + kf * (a.pitch * a.ny) + c.col : reinterpret_cast<const float2*>(a.ein[0]), c.fown);
+    }
     cpa_commit();
 }
 
@@ -211,15 +247,18 @@ __device__ __forceinline__ float tb2_src(const Tb2Bufs<RY>& b, const Tb2Col& c, 
     return b.SC[(2 * comp) * NT + c.tid] * u.x - b.SC[(2 * comp + 1) * NT + c.tid] * u.y;
 }
 
-// One plane p of the wavefront: u = (p - P0) mod 4 is its ring slot, and
-// U = (p - P0) mod 2 gives the exchange-buffer parities at compile time.
-template <int RY, int U>
-__device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Col& c,
+// One plane p of the wavefront: q is its copy number in the CTA (ring slot
+// u = q mod 4, mbarrier parity (q / 4) mod 2), and U = (p - P0) mod 2 gives
+// the exchange-buffer parities at compile time.  Returns false if the wait
+// for the TMA copies of the plane gave up (the error word is raised).
+template <int RY, int U, bool TMA>
+__device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Col& c,
                                           const Tb2Bufs<RY>& b, Tb2Carry& s, bool valid, bool issue_next,
-                                          float dt16, int u)
+                                          float dt16, int q, const Tb2Maps* maps)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF, XS = S::XS;
+    const int u = q & 3;
     const int SP = u, SQ = (u + 3) & 3, SR = (u + 2) & 3;   // slots of planes p, p-1, p-2
     constexpr int PP = U & 1, PQ = PP ^ 1;                        // exchange parities of planes p, p-1
     const int lane = c.lane, tid = c.tid;
@@ -238,6 +277,15 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     const float cz = a.cz;
 
     cpa_wait1();
+    if constexpr (TMA) {
+        // a wait that gives up raises the error word and the CTA's abort flag;
+        // every thread reads the flag after the plane's first barrier, so that
+        // all of them leave at the same point
+        if (!mbar_wait_bounded(b.bar + SP, uint32_t(q >> 2) & 1u)) {
+            *maps->err = 1;
+            *b.abort = 1;
+        }
+    }
     float* rp = b.ring + SP * NF * NT + tid;
     float* rq = b.ring + SQ * NF * NT + tid;
     float* rr = b.ring + SR * NF * NT + tid;
@@ -298,6 +346,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         put(b.HB + 2 * XS, hsy);
     }
     __syncthreads();
+    if (TMA && *static_cast<volatile int*>(b.abort)) return false;
 
     // ---- stage B: E^{n+1} of plane q
     float nex = 0.0f, ney = 0.0f, nez = 0.0f;
@@ -463,18 +512,23 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     s.zr = s.zq; s.zq = zn;
     // refill: plane p + 2 (fluence plane p - 1) into the slot of plane p - 2,
     // whose last reader was this plane
-    if (issue_next) tb2_issue<RY>(a, c, b, SR, s.ki, s.kq);
+    if (issue_next) tb2_issue<RY, TMA>(a, c, b, SR, s.ki, s.kq, maps);
     else cpa_commit();
     s.k3 = s.kr; s.kr = s.kq; s.kq = s.kp;
     s.kp = next_plane(s.kp, a.nz);
     s.ki = next_plane(s.ki, a.nz);
+    return true;
 }
 
 // One window, planes [kb, ke) of its E^{n+2} / H^{n+3/2} output (fluence
-// planes [kb-1, ke-1), modulo nz).
-template <int RY>
-__device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw,
-                                           int window, int kb, int ke, const Tb2Bufs<RY>& b)
+// planes [kb-1, ke-1), modulo nz).  gq: the CTA's running copy number of the
+// window's first plane (TMA ring slots and mbarrier parities); returns the
+// number after the window, or -1 if a wait gave up (after draining the
+// window's copies still in flight).
+template <int RY, bool TMA>
+__device__ __forceinline__ int tb2_window(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw,
+                                          int window, int kb, int ke, const Tb2Bufs<RY>& b, int gq,
+                                          const Tb2Maps* maps)
 {
     constexpr int NT = Tb2Smem<RY>::NT;
     Tb2Col c;
@@ -547,31 +601,42 @@ __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Ti
     s.kq = s.kp == 0 ? nz - 1 : s.kp - 1;
     s.kr = s.kq == 0 ? nz - 1 : s.kq - 1;
     s.k3 = s.kr == 0 ? nz - 1 : s.kr - 1;
-    // prologue: planes P0, P0 + 1 into slots 0, 1 (their fluence planes P0 - 3, P0 - 2)
-    tb2_issue<RY>(a, c, b, 0, s.kp, s.k3);
+    // prologue: planes P0, P0 + 1 (their fluence planes P0 - 3, P0 - 2)
+    tb2_issue<RY, TMA>(a, c, b, gq & 3, s.kp, s.k3, maps);
     const int k1 = next_plane(s.kp, nz);
-    tb2_issue<RY>(a, c, b, 1, k1, s.kr);
+    tb2_issue<RY, TMA>(a, c, b, (gq + 1) & 3, k1, s.kr, maps);
     s.ki = next_plane(k1, nz);
-    // the ring's four slots: plane p uses slot u = (p - P0) mod 4
+    // the ring's four slots: plane p has copy number q = gq + p - P0, slot q mod 4
     int p = P0;
-    int u = 0;
+    int q = gq;
+    bool ok = true;
     for (;;) {
-        tb2_plane<RY, 0>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
-        u = (u + 1) & 3;
-        if (++p > P1) break;
-        tb2_plane<RY, 1>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
-        u = (u + 1) & 3;
-        if (++p > P1) break;
+        ok = tb2_plane<RY, 0, TMA>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, q, maps);
+        ++q;
+        if (!ok || ++p > P1) break;
+        ok = tb2_plane<RY, 1, TMA>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, q, maps);
+        ++q;
+        if (!ok || ++p > P1) break;
     }
     cpa_wait0();
+    if constexpr (TMA) {
+        if (!ok) {   // drain the copies of this plane and the next, if issued (bounded waits)
+            --q;
+            const int last = q + 1 < gq + (P1 - P0) ? q + 1 : gq + (P1 - P0);
+            for (int r = q; r <= last; ++r) mbar_wait_bounded(b.bar + (r & 3), uint32_t(r >> 2) & 1u);
+            return -1;
+        }
+    }
+    return gq + (P1 - P0 + 1);
 }
 
-template <int RY>
-__device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw)
+template <int RY, bool TMA>
+__device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw,
+                                        const Tb2Maps* maps)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, R = S::R, NF = S::NF;
-    extern __shared__ __align__(16) unsigned char tb2_smem[];
+    extern __shared__ __align__(128) unsigned char tb2_smem[];
     Tb2Bufs<RY> b;
     b.fring = reinterpret_cast<float2*>(tb2_smem);
     b.ring = reinterpret_cast<float*>(b.fring + R * NT);
@@ -580,22 +645,34 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
     b.HB = b.EB + 4 * XS;
     b.E1B = b.HB + 3 * XS;
     b.H1B = b.E1B + 4 * XS;
-    b.SC = b.H1B + 3 * XS;
-    // the zero rows of the 14 exchange arrays (never written again; the
-    // first window's barrier orders these stores before any read)
-    for (int q = threadIdx.y * 32 + threadIdx.x; q < 14 * 64; q += NT) {
-        const int arr = q / 64, e = q % 64;
-        b.EB[arr * XS + (e < 32 ? e : NT + e)] = 0.0f;
+    b.SC = b.H1B + 3 * XS + 32;
+    b.bar = reinterpret_cast<uint64_t*>(b.SC + 12 * NT);
+    b.abort = reinterpret_cast<int*>(b.bar + R);
+    if (TMA && threadIdx.x == 0 && threadIdx.y == 0) {
+        for (int q = 0; q < R; ++q) mbar_init(b.bar + q, 1);
+        *b.abort = 0;
+        mbar_fence_init();
     }
+    // the NX + 1 zero rows of the exchange arrays (never written again; the
+    // first window's barrier orders these stores before any read)
+    for (int q = threadIdx.y * 32 + threadIdx.x; q < (S::NX + 1) * 32; q += NT)
+        b.EB[(q / 32) * XS + q % 32] = 0.0f;
     long long w = tw.start[blockIdx.x];
     const long long wend = tw.start[blockIdx.x + 1];
+    int gq = 0;
     while (w < wend) {
         const int window = int(w / a.nz), kb = int(w % a.nz);
         const long long left = wend - w;
         const int ke = left < (long long)(a.nz - kb) ? kb + int(left) : a.nz;
-        tb2_window<RY>(a, tt, tw, window, kb, ke, b);
+        const long long t0 = tw.prof ? clock64() : 0;
+        gq = tb2_window<RY, TMA>(a, tt, tw, window, kb, ke, b, gq, maps);
+        if (TMA && gq < 0) return;   // a wait gave up (every thread): the CTA stops
         w += ke - kb;
         __syncthreads();   // the exchange buffers are reused by the next window
+        if (tw.prof && threadIdx.x == 0 && threadIdx.y == 0) {
+            atomicAdd(tw.prof + 2 * window, static_cast<unsigned long long>(clock64() - t0));
+            atomicAdd(tw.prof + 2 * window + 1, static_cast<unsigned long long>(ke - kb + 4));
+        }
     }
 }
 
@@ -604,7 +681,16 @@ template <int RY>
 __global__ void __launch_bounds__(32 * RY, 1)
 yee_tb2(const StepArgs<float> a, const Tb2Times tt, const __grid_constant__ Tb2Plan tw)
 {
-    tb2_run<RY>(a, tt, tw);
+    tb2_run<RY, false>(a, tt, tw, nullptr);
+}
+
+// The same with E^n, H^{n-1/2} and the fluence copied by TMA.
+template <int RY>
+__global__ void __launch_bounds__(32 * RY, 1)
+yee_tb2_tma(const StepArgs<float> a, const Tb2Times tt, const __grid_constant__ Tb2Plan tw,
+            const __grid_constant__ Tb2Maps maps)
+{
+    tb2_run<RY, true>(a, tt, tw, &maps);
 }
 
 // The same with the time factors of the two steps read from a device table
@@ -618,7 +704,7 @@ yee_tb2_t(const StepArgs<float> a, const StepTime<float>* __restrict__ times, in
     Tb2Times tt;
     tt.th0 = times[i0].th; tt.te0 = times[i0].te;
     tt.th1 = times[i1].th; tt.te1 = times[i1].te;
-    tb2_run<RY>(a, tt, tw);
+    tb2_run<RY, false>(a, tt, tw, nullptr);
 }
 
 }  // namespace fdtd

@@ -98,6 +98,7 @@ _SIGS = {
     "fdtd_get_balance": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
+    "fdtd_measure_balance": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
     "fdtd_batch_required_bytes": (C.c_size_t, [C.c_int, C.c_int]),
     "fdtd_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
@@ -366,6 +367,14 @@ class Grid:
         ws, wa = C.c_float(), C.c_float()
         check(lib().fdtd_get_balance(C.c_void_p(self.handle), C.byref(ws), C.byref(wa)), "fdtd_get_balance")
         return ws.value, wa.value
+
+    def measure_balance(self):
+        """Balance the variant-7 ranges on per-window costs measured in one
+        launch (fdtd_measure_balance; the state is saved and restored)."""
+        scratch = self.torch.empty(self.state_bytes(), dtype=self.torch.uint8, device=self.device)
+        check(lib().fdtd_measure_balance(C.c_void_p(self.handle), C.c_void_p(scratch.data_ptr())),
+              "fdtd_measure_balance")
+        del scratch
 
     def tile(self):
         v, ty, lz = C.c_int(), C.c_int(), C.c_int()

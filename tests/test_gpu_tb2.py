@@ -17,6 +17,7 @@ import pytest
 import torch
 
 import oracle
+from paper_2102_12978_gb300 import fdtd
 from paper_2102_12978_gb300 import workloads as W
 from tests.cases import oracle_grid, oracle_source, rel_l2
 from tests.gpu_cases import gpu_grid, host
@@ -47,14 +48,15 @@ def _random_pec_state(w, seed=17):
     return init
 
 
+@pytest.mark.parametrize("ty", [16, 8])
 @pytest.mark.parametrize("shape,npml", [((13, 7, 5), 1), ((8, 8, 8), 2), ((4, 4, 4), 0), ((33, 9, 3), 2),
                                         ((70, 44, 6), 8), ((29, 30, 4), 0)])
-def test_random_states_every_shell_busy(shape, npml):
+def test_random_states_every_shell_busy(shape, npml, ty):
     """A random state in every cell: the CPML shells, the walls and the
     window overlaps all carry values from the first step."""
     nx, ny, nz = shape
     w = W.small(nx=nx, ny=ny, nz=nz, npml=npml, steps=14)
-    _assert(_compare(w, "f32", tile=(7, 16, 1), npml=npml, source=False, init=_random_pec_state(w)), "f32")
+    _assert(_compare(w, "f32", tile=(7, ty, 1), npml=npml, source=False, init=_random_pec_state(w)), "f32")
 
 
 @pytest.mark.parametrize("kw", [
@@ -162,3 +164,38 @@ def test_work_split_weights_change_no_result():
     for other in runs[1:]:
         for x, y in zip(runs[0], other):
             assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("ty", [16, 8])
+def test_measured_balance_changes_no_result(ty):
+    """fdtd_measure_balance runs one measuring launch on a saved copy of the
+    state (the grid's state and step count are restored), then balances the
+    ranges on the measured per-window costs: the results are bit for bit
+    those of the weight-balanced ranges, and fdtd_set_balance returns to the
+    weights."""
+    w = W.small(nx=100, ny=90, nz=9, npml=8, r_center=20.0, steps=12, ramp=1.0)
+    a = gpu_grid(w, "f32", tile=(7, ty, 1))
+    b = gpu_grid(w, "f32", tile=(7, ty, 1))
+    a.step(4)
+    b.step(4)
+    n = b.n
+    before = [b.field(c).clone() for c in range(6)] + [b.fluence().clone()]
+    b.measure_balance()
+    assert b.balance() == (-1.0, -1.0) and b.n == n
+    for x, y in zip(before, [b.field(c) for c in range(6)] + [b.fluence()]):
+        assert torch.equal(x, y)
+    a.step(w.steps - 4)
+    b.step(w.steps - 4)
+    for c in range(6):
+        assert torch.equal(a.field(c), b.field(c))
+    assert torch.equal(a.fluence(), b.fluence())
+    b.set_balance(0.3, 0.2)
+    assert b.balance() == pytest.approx((0.3, 0.2))
+
+
+def test_measured_balance_needs_variant_7():
+    w = W.small(nx=48, ny=40, nz=8, npml=6, r_center=11.0, steps=4, ramp=1.0)
+    g = gpu_grid(w, "f32", tile=(5, 4, 1))
+    with pytest.raises(fdtd.FDTDError) as e:
+        g.measure_balance()
+    assert e.value.status == fdtd.FDTD_EINVAL
