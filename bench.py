@@ -40,7 +40,7 @@ MAX_REPEATS = 100000
 # DRAM bytes (read + write) per launch of a kernel on the 256x256x128 FP32
 # workload, from one ncu capture of the kernel as it stands (summary and
 # command in profiles/); None where no capture of the current kernel exists.
-TRAFFIC: dict[str, float | None] = {"yee_h_cell": 307.85e6, "yee_e_cell": 545.41e6, "yee_tb2": 1002.12e6}
+TRAFFIC: dict[str, float | None] = {"yee_h_cell": 307.85e6, "yee_e_cell": 545.41e6, "yee_tb2": None}
 UNIT = "Gcell-updates/s"
 
 # FP64 instructions per cell of each FP64 cell pass on the 256x256x128 workload
@@ -48,7 +48,7 @@ UNIT = "Gcell-updates/s"
 # capture of the kernels as they stand; summary and command in profiles/).
 # The FP64 passes are bound by GB300's FP64 pipe: 2 FP64 instructions per SM
 # per clock, whatever the number of active lanes of the warp instruction.
-FP64_INST_PER_CELL: dict[str, float] = {"yee_h_cell": 16.94, "yee_e_cell": 47.14}
+FP64_INST_PER_CELL: dict[str, float | None] = {"yee_h_cell": None, "yee_e_cell": None}
 # Steps run on the FP64 grid before its tiles are tuned and timed: the FP64
 # norm of the fluence term costs less on cells whose fields are still zero,
 # so the first steps of a run are cheaper than the rest of it.

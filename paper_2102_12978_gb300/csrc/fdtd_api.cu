@@ -475,10 +475,7 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     if (st != FDTD_OK) { delete g; return st; }
     g->tile = default_tile(*d, sms);
     for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 3; ++b) {
-            g->maps_ok[a][b] = g->hmaps_ok[a][b] = false;
-            if (b < 2) g->tb2_maps_ok[a][b] = false;
-        }
+        for (int b = 0; b < 3; ++b) g->maps_ok[a][b] = g->hmaps_ok[a][b] = false;
     st = cuda_check(cudaMemsetAsync(arena, 0, L.total, g->stream), "zero arena");
     if (st == FDTD_OK)
         st = (d->precision == FDTD_F64) ? upload_tables<double>(g) : upload_tables<float>(g);

@@ -10,7 +10,6 @@
 #include "yee_fused.cuh"
 #include "yee_tma.cuh"
 #include "yee_cell.cuh"
-#include "yee_tb2.cuh"
 
 namespace fdtd {
 
@@ -117,8 +116,6 @@ struct fdtd_grid {
     int tb2_cost_src;                   // the antenna generation they were measured with
     int tb2_cost_gen;                   // bumped whenever tb2_cost changes
     bool tb2_profile;                   // the next variant-7 launches record per-window costs
-    fdtd::Tb2Maps tb2_maps[2][2];       // TMA maps of variant 7: [read copy][ty 8, 16]
-    bool tb2_maps_ok[2][2];
 };
 
 namespace fdtd {

@@ -8,7 +8,6 @@
 #include <cmath>
 
 #include "grid_impl.h"
-#include "tma_host.h"
 #include "yee_tb2.cuh"
 
 namespace fdtd {
@@ -102,26 +101,6 @@ static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2P
     for (int c = 0; c <= slots; ++c) P.start[c] = g->tb2_start[size_t(c)];
 }
 
-// TMA maps of the copy `cur` for windows of 32 x RY columns (cached on the grid).
-template <int RY>
-static const Tb2Maps* tb2_maps(fdtd_grid* g, int cur)
-{
-    const int sl = RY == 8 ? 0 : 1;
-    Tb2Maps& m = g->tb2_maps[cur][sl];
-    if (!g->tb2_maps_ok[cur][sl]) {
-        char* A = static_cast<char*>(g->arena);
-        bool ok = true;
-        for (int c = 0; c < 6; ++c)
-            ok = ok && encode_map(&m.f[c], A + g->L.field[cur][c], 4, g->desc, g->L.pitch, kTb2Wx, RY);
-        void* fbase = g->desc.fluence ? static_cast<void*>(A + g->L.fluence) : static_cast<void*>(A + g->L.field[cur][0]);
-        ok = ok && encode_map(&m.flu, fbase, 8, g->desc, g->L.pitch, kTb2Wx, RY);
-        if (!ok) return nullptr;
-        m.err = reinterpret_cast<int*>(A + g->L.err);
-        g->tb2_maps_ok[cur][sl] = true;
-    }
-    return &m;
-}
-
 // Resident CTAs per SM of the kernels of one RY (dynamic shared memory set
 // on first use).
 template <int RY>
@@ -133,8 +112,7 @@ static cudaError_t tb2_blocks_per_sm(int* out)
     if (blocks_per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(yee_tb2<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(S::bytes()));
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(yee_tb2_tma<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::bytes()));
+
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(yee_tb2_t<RY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(S::bytes()));
         if (e != cudaSuccess) return e;
@@ -165,13 +143,7 @@ static cudaError_t launch_tb2_t(const fdtd_grid* cg, int cur, long long n, const
     const StepTime<float> t1 = step_time<float>(g->srct, nullptr, g->dt, n + 1);
     Tb2Times tt;
     tt.th0 = t0.th; tt.te0 = t0.te; tt.th1 = t1.th; tt.te1 = t1.te;
-    if (tc.lz == 2) {
-        const Tb2Maps* m = tb2_maps<RY>(g, cur);
-        if (!m) return cudaErrorInvalidValue;
-        yee_tb2_tma<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), tt, plan, *m);
-    } else {
-        yee_tb2<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), tt, plan);
-    }
+    yee_tb2<RY><<<unsigned(slots), dim3(32, RY), S::bytes(), s>>>(make_args<float>(g, cur), tt, plan);
     return cudaGetLastError();
 }
 

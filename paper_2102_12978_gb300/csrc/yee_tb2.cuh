@@ -44,6 +44,10 @@
 //   * Reading step n from one copy of the fields and psi and writing step
 //     n+2 into the other (ping-pong, E-side psi included) makes the halo
 //     recompute race-free.
+//   * Every row of a window runs every stage, whether or not a column the
+//     window writes depends on it, so that the stage code has no branches
+//     on the row; windows off the box faces and the CPML shells (GEN false)
+//     run code without the checks of PEC walls, psi and columns past the box.
 //   * A CTA takes a contiguous range of the flattened (window, plane) work;
 //     the ranges have equal estimated cost (windows with CPML shell or antenna
 //     columns weigh more, with weights the autotuner picks by timing).  Where
@@ -84,15 +88,6 @@ struct Tb2Plan {
 constexpr int kTb2Wx = 32;
 constexpr int kTb2Sx = 28;
 
-// Tensor maps of the TMA-fed kernel: E^n and H^{n-1/2} of the copy being
-// read and the fluence accumulator, boxes of 32 x RY x 1 (a window's columns
-// in one plane; elements past the box read as zero), and the grid's error
-// word, raised by a CTA whose wait for a copy gave up.
-struct Tb2Maps {
-    CUtensorMap f[6];
-    CUtensorMap flu;
-    int* err;
-};
 
 template <int RY>
 struct Tb2Smem {
@@ -111,8 +106,7 @@ struct Tb2Smem {
         return size_t(R) * NT * 8                 // fluence accumulator (float2) per slot
                + size_t(R) * NF * NT * 4          // fields and psi per slot
                + (size_t(NX) * XS + 32) * 4       // exchange arrays and their zero rows
-               + size_t(12) * NT * 4              // antenna coefficients of the column (6 complex)
-               + size_t(R) * 8 + 8;               // mbarriers of the ring slots, abort flag (TMA-fed kernel)
+               + size_t(12) * NT * 4;             // antenna coefficients of the column (6 complex)
     }
 };
 
@@ -132,28 +126,35 @@ __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_gro
 __device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Every sum of two products below is written with explicit roundings
+// (mul_rn / fma_rn): the plane loop runs two instantiations of tb2_plane
+// (the exchange parities), and which one computes a plane depends on where
+// the CTA's range of planes starts; left to the compiler, the two could
+// contract such a sum into a fused multiply-add in different ways, and the
+// results would depend on the CTAs' work split.
+
 // |E x Hbar| dt of a cell from its centre sums (the 1/16 of the four-edge E
 // means and the two-face, two-time H means is folded into dt16).
 __device__ __forceinline__ float tb2_flux(float cx, float cy, float cc, float hbx, float hby, float hbz, float dt16)
 {
-    const float sx = cy * hbz - cc * hby;
-    const float sy = cc * hbx - cx * hbz;
-    const float sz = cx * hby - cy * hbx;
-    return vec_norm(sx * sx + sy * sy + sz * sz) * dt16;
+    const float sx = fma_rn(cy, hbz, -mul_rn(cc, hby));
+    const float sy = fma_rn(cc, hbx, -mul_rn(cx, hbz));
+    const float sz = fma_rn(cx, hby, -mul_rn(cy, hbx));
+    return mul_rn(vec_norm(fma_rn(sz, sz, fma_rn(sy, sy, mul_rn(sx, sx)))), dt16);
 }
 
 __device__ __forceinline__ Cpx<float> cmul(Cpx<float> z, Cpx<float> t)
 {
-    return Cpx<float>{z.x * t.x - z.y * t.y, z.x * t.y + z.y * t.x};
+    return Cpx<float>{fma_rn(z.x, t.x, -mul_rn(z.y, t.y)), fma_rn(z.x, t.y, mul_rn(z.y, t.x))};
 }
+
+// CPML psi update b psi + a d.
+__device__ __forceinline__ float psi_rn(float b, float psi, float aa, float d) { return fma_rn(b, psi, mul_rn(aa, d)); }
 
 // Per-window constants of a thread's column.
 struct Tb2Col {
     int i, j, lane, row, tid;
     bool indom, own, fown, sx, sy, ant;   // ant: the window holds antenna columns
-    // warp-uniform (one warp = one row): which stages this row's results feed
-    // into an output of the window; the other rows skip them
-    bool needA, needB, needC, needD, needFl;
     uint8_t mk;
     int col, colx, coly;
     float chx, chy, cex, cey, bhx, ahx, bex, aex, bhy, ahy, bey, aey;
@@ -182,60 +183,42 @@ struct Tb2Bufs {
     float* E1B;      // [2][Ez, Ex][XS]: E^{n+1}
     float* H1B;      // [Hx, Hz, Hy^{n+1/2} + Hy^{n+3/2}][XS]
     float* SC;       // [6][re, im][NT]: antenna coefficients
-    uint64_t* bar;   // [R]: completion of a slot's TMA copies (TMA-fed kernel)
-    int* abort;      // set when a wait for a copy gave up (TMA-fed kernel)
 };
 
 __device__ __forceinline__ int next_plane(int k, int nz) { return k + 1 == nz ? 0 : k + 1; }
 
 // Copies of plane k (fluence plane kf) into ring slot s of this thread.
-// TMA: thread 0 copies the whole window's E^n, H^{n-1/2} and fluence boxes
-// (one mbarrier per slot, after a proxy fence: the slot's previous contents
-// were read by every thread before the last CTA barrier); every thread still
-// copies its own column's psi.
-template <int RY, bool TMA>
+template <int RY, bool GEN>
 __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col& c, const Tb2Bufs<RY>& b, int s,
-                                          int k, int kf, const Tb2Maps* maps)
+                                          int k, int kf)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF;
     float* r = b.ring + s * NF * NT + c.tid;
-    if constexpr (TMA) {
-        if (c.tid == 0) {
-            const int x0 = c.i - c.lane, y0 = c.j - c.row;
-            fence_proxy_async();
-            mbar_expect_tx(b.bar + s, uint32_t(NT) * (6 * 4 + (a.fluence ? 8 : 0)));
-            for (int q = 0; q < 6; ++q) tma_load_3d(b.ring + (s * NF + q) * NT, &maps->f[q], b.bar + s, x0, y0, k);
-            if (a.fluence) tma_load_3d(b.fring + s * NT, &maps->flu, b.bar + s, x0, y0, kf);
-        }
-    } else {
-        const int g = k * (a.pitch * a.ny) + c.col;
-        cpa4(r + 0 * NT, a.ein[0] + g, c.indom);
-        cpa4(r + 1 * NT, a.ein[1] + g, c.indom);
-        cpa4(r + 2 * NT, a.ein[2] + g, c.indom);
-        cpa4(r + 3 * NT, a.hin[0] + g, c.indom);
-        cpa4(r + 4 * NT, a.hin[1] + g, c.indom);
-        cpa4(r + 5 * NT, a.hin[2] + g, c.indom);
-    }
-    if (c.sx) {
+    const int g = k * (a.pitch * a.ny) + c.col;
+    cpa4(r + 0 * NT, a.ein[0] + g, !GEN || c.indom);
+    cpa4(r + 1 * NT, a.ein[1] + g, !GEN || c.indom);
+    cpa4(r + 2 * NT, a.ein[2] + g, !GEN || c.indom);
+    cpa4(r + 3 * NT, a.hin[0] + g, !GEN || c.indom);
+    cpa4(r + 4 * NT, a.hin[1] + g, !GEN || c.indom);
+    cpa4(r + 5 * NT, a.hin[2] + g, !GEN || c.indom);
+    if (GEN && c.sx) {
         const int q = k * a.ny * (2 * a.npml) + c.colx;
         cpa4(r + 6 * NT, a.phx_in[0] + q, true);    // Hyx
         cpa4(r + 7 * NT, a.phx_in[1] + q, true);    // Hzx
         cpa4(r + 10 * NT, a.pex[0] + q, true);      // Eyx
         cpa4(r + 11 * NT, a.pex[1] + q, true);      // Ezx
     }
-    if (c.sy) {
+    if (GEN && c.sy) {
         const int q = k * (2 * a.npml) * a.pitch + c.coly;
         cpa4(r + 8 * NT, a.phy_in[0] + q, true);    // Hxy
         cpa4(r + 9 * NT, a.phy_in[1] + q, true);    // Hzy
         cpa4(r + 12 * NT, a.pey[0] + q, true);      // Exy
         cpa4(r + 13 * NT, a.pey[1] + q, true);      // Ezy
     }
-    if constexpr (!TMA) {
-        const float2* F = static_cast<const float2*>(a.fluence);
-        cpa8(b.fring + s * NT + c.tid,
-             c.fown ? F + kf * (a.pitch * a.ny) + c.col : reinterpret_cast<const float2*>(a.ein[0]), c.fown);
-    }
+    const float2* F = static_cast<const float2*>(a.fluence);
+    cpa8(b.fring + s * NT + c.tid, c.fown ? F + kf * (a.pitch * a.ny) + c.col : reinterpret_cast<const float2*>(a.ein[0]),
+         c.fown);
     cpa_commit();
 }
 
@@ -244,31 +227,34 @@ template <int RY>
 __device__ __forceinline__ float tb2_src(const Tb2Bufs<RY>& b, const Tb2Col& c, int comp, Cpx<float> u)
 {
     constexpr int NT = Tb2Smem<RY>::NT;
-    return b.SC[(2 * comp) * NT + c.tid] * u.x - b.SC[(2 * comp + 1) * NT + c.tid] * u.y;
+    return fma_rn(b.SC[(2 * comp) * NT + c.tid], u.x, -mul_rn(b.SC[(2 * comp + 1) * NT + c.tid], u.y));
 }
 
-// One plane p of the wavefront: q is its copy number in the CTA (ring slot
-// u = q mod 4, mbarrier parity (q / 4) mod 2), and U = (p - P0) mod 2 gives
-// the exchange-buffer parities at compile time.  Returns false if the wait
-// for the TMA copies of the plane gave up (the error word is raised).
-template <int RY, int U, bool TMA>
-__device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Col& c,
+// One plane p of the wavefront: u = (p - P0) mod 4 is its ring slot, and
+// U = (p - P0) mod 2 gives the exchange-buffer parities at compile time.
+// Every row runs every stage: a row whose results no written column needs
+// computes values that reach no output (rows beyond the window read the zero
+// rows of the exchange arrays), and the stage code stays free of branches.
+template <int RY, int U, bool GEN>
+__device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Col& c,
                                           const Tb2Bufs<RY>& b, Tb2Carry& s, bool valid, bool issue_next,
-                                          float dt16, int q, const Tb2Maps* maps)
+                                          float dt16, int u)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF, XS = S::XS;
-    const int u = q & 3;
     const int SP = u, SQ = (u + 3) & 3, SR = (u + 2) & 3;   // slots of planes p, p-1, p-2
     constexpr int PP = U & 1, PQ = PP ^ 1;                        // exchange parities of planes p, p-1
     const int lane = c.lane, tid = c.tid;
+    // (an interior window, !GEN, takes the edge lane's own value past the
+    // window: lanes 0 and 31 are halo there, and what they compute reaches
+    // no column the window writes)
     auto xp = [&](float v) {   // value of the +x neighbour (0 past the window)
         const float u = __shfl_down_sync(0xffffffffu, v, 1);
-        return lane == 31 ? 0.0f : u;
+        return GEN && lane == 31 ? 0.0f : u;
     };
     auto xm = [&](float v) {   // value of the -x neighbour
         const float u = __shfl_up_sync(0xffffffffu, v, 1);
-        return lane == 0 ? 0.0f : u;
+        return GEN && lane == 0 ? 0.0f : u;
     };
     // y neighbours from the padded exchange arrays (zero beyond the window)
     auto yp = [&](const float* q) { return q[S::XO + tid + 32]; };
@@ -277,15 +263,6 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
     const float cz = a.cz;
 
     cpa_wait1();
-    if constexpr (TMA) {
-        // a wait that gives up raises the error word and the CTA's abort flag;
-        // every thread reads the flag after the plane's first barrier, so that
-        // all of them leave at the same point
-        if (!mbar_wait_bounded(b.bar + SP, uint32_t(q >> 2) & 1u)) {
-            *maps->err = 1;
-            *b.abort = 1;
-        }
-    }
     float* rp = b.ring + SP * NF * NT + tid;
     float* rq = b.ring + SQ * NF * NT + tid;
     float* rr = b.ring + SR * NF * NT + tid;
@@ -298,7 +275,7 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
     const float ex = s.e0[0], ey = s.e0[1], ez = s.e0[2];
     float hx = 0.0f, hy = 0.0f, hz = 0.0f, hsy = 0.0f;
     float nPEx = 0.0f, nPEy = 0.0f, ncz = 0.0f, nHsz = 0.0f, nhbx = 0.0f;
-    if (c.needA) {
+    {
         const float ox = rq[3 * NT], oy = rq[4 * NT], oz = rq[5 * NT];   // H^{n-1/2}(q)
         const float* EBq = b.EB + PQ * 2 * XS;
         const float ezj = yp(EBq), exj = yp(EBq + XS);
@@ -308,16 +285,16 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
         hx = ox - c.chy * dEz_y + cz * dEy_z;
         hy = oy - cz * dEx_z + c.chx * dEz_x;
         hz = oz - c.chx * dEy_x + c.chy * dEx_y;
-        if (c.sx) {
-            const float p0 = c.bhx * rq[6 * NT] + c.ahx * dEz_x;   // Hyx
-            const float p1 = c.bhx * rq[7 * NT] + c.ahx * dEy_x;   // Hzx
+        if (GEN && c.sx) {
+            const float p0 = psi_rn(c.bhx, rq[6 * NT], c.ahx, dEz_x);   // Hyx
+            const float p1 = psi_rn(c.bhx, rq[7 * NT], c.ahx, dEy_x);   // Hzx
             hy += p0;
             hz -= p1;
             rq[6 * NT] = p0; rq[7 * NT] = p1;
         }
-        if (c.sy) {
-            const float p0 = c.bhy * rq[8 * NT] + c.ahy * dEz_y;   // Hxy
-            const float p1 = c.bhy * rq[9 * NT] + c.ahy * dEx_y;   // Hzy
+        if (GEN && c.sy) {
+            const float p0 = psi_rn(c.bhy, rq[8 * NT], c.ahy, dEz_y);   // Hxy
+            const float p1 = psi_rn(c.bhy, rq[9 * NT], c.ahy, dEx_y);   // Hzy
             hx -= p0;
             hz += p1;
             rq[8 * NT] = p0; rq[9 * NT] = p1;
@@ -346,11 +323,10 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
         put(b.HB + 2 * XS, hsy);
     }
     __syncthreads();
-    if (TMA && *static_cast<volatile int*>(b.abort)) return false;
 
     // ---- stage B: E^{n+1} of plane q
     float nex = 0.0f, ney = 0.0f, nez = 0.0f;
-    if (c.needB) {
+    {
         const float hyi = xm(hy), hzi = xm(hz);
         const float hxj = ym(b.HB), hzj = ym(b.HB + XS);
         const float dHz_y = hz - hzj, dHy_z = hy - s.h1p[1], dHx_z = hx - s.h1p[0];
@@ -358,16 +334,16 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
         nex = ex + c.cey * dHz_y - cz * dHy_z;
         ney = ey + cz * dHx_z - c.cex * dHz_x;
         nez = ez + c.cex * dHy_x - c.cey * dHx_y;
-        if (c.sx) {
-            const float p0 = c.bex * rq[10 * NT] + c.aex * dHz_x;   // Eyx
-            const float p1 = c.bex * rq[11 * NT] + c.aex * dHy_x;   // Ezx
+        if (GEN && c.sx) {
+            const float p0 = psi_rn(c.bex, rq[10 * NT], c.aex, dHz_x);   // Eyx
+            const float p1 = psi_rn(c.bex, rq[11 * NT], c.aex, dHy_x);   // Ezx
             rq[10 * NT] = p0; rq[11 * NT] = p1;
             ney -= p0;
             nez += p1;
         }
-        if (c.sy) {
-            const float p0 = c.bey * rq[12 * NT] + c.aey * dHz_y;   // Exy
-            const float p1 = c.bey * rq[13 * NT] + c.aey * dHx_y;   // Ezy
+        if (GEN && c.sy) {
+            const float p0 = psi_rn(c.bey, rq[12 * NT], c.aey, dHz_y);   // Exy
+            const float p1 = psi_rn(c.bey, rq[13 * NT], c.aey, dHx_y);   // Ezy
             rq[12 * NT] = p0; rq[13 * NT] = p1;
             nex += p0;
             nez -= p1;
@@ -378,12 +354,12 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
             if (c.mk & 0x02) ney += tb2_src(b, c, 1, u);
             if (c.mk & 0x04) nez += tb2_src(b, c, 2, u);
         }
-        if (c.j == 0) { nex = 0.0f; nez = 0.0f; }   // PEC: tangential E
-        if (c.i == 0) { ney = 0.0f; nez = 0.0f; }
+        if (GEN && c.j == 0) { nex = 0.0f; nez = 0.0f; }   // PEC: tangential E
+        if (GEN && c.i == 0) { ney = 0.0f; nez = 0.0f; }
     }
     // fluence term of step n for plane r (sums of planes r and q)
     float nhby = 0.0f, tn_new = 0.0f;
-    if (c.needFl) {
+    {
         nhby = hsy + yp(b.HB + 2 * XS);
         tn_new = tb2_flux(s.fPEx + nPEx, s.fPEy + nPEy, s.fcz, s.fhbx, s.fhby, s.fHsz + nHsz, dt16);
     }
@@ -391,7 +367,7 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
     // ---- stage C: H^{n+3/2} of plane r = p-2
     float h2x = 0.0f, h2y = 0.0f, h2z = 0.0f, gsy = 0.0f;
     float mPEx = 0.0f, mPEy = 0.0f, mcz = 0.0f, mHsz = 0.0f, mhbx = 0.0f;
-    if (c.needC) {
+    {
         const float* E1Br = b.E1B + PP * 2 * XS;   // written one plane ago (parity of r = parity of p)
         const float fezj = yp(E1Br), fexj = yp(E1Br + XS);
         const float fezi = xp(s.e1p[2]), feyi = xp(s.e1p[1]);
@@ -400,9 +376,9 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
         h2x = s.h1p[0] - c.chy * dEz_y + cz * dEy_z;
         h2y = s.h1p[1] - cz * dEx_z + c.chx * dEz_x;
         h2z = s.h1p[2] - c.chx * dEy_x + c.chy * dEx_y;
-        if (c.sx) {
-            const float p0 = c.bhx * rr[6 * NT] + c.ahx * dEz_x;
-            const float p1 = c.bhx * rr[7 * NT] + c.ahx * dEy_x;
+        if (GEN && c.sx) {
+            const float p0 = psi_rn(c.bhx, rr[6 * NT], c.ahx, dEz_x);
+            const float p1 = psi_rn(c.bhx, rr[7 * NT], c.ahx, dEy_x);
             h2y += p0;
             h2z -= p1;
             if (valid && c.own) {
@@ -410,9 +386,9 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
                 a.phx_out[0][qo] = p0; a.phx_out[1][qo] = p1;
             }
         }
-        if (c.sy) {
-            const float p0 = c.bhy * rr[8 * NT] + c.ahy * dEz_y;
-            const float p1 = c.bhy * rr[9 * NT] + c.ahy * dEx_y;
+        if (GEN && c.sy) {
+            const float p0 = psi_rn(c.bhy, rr[8 * NT], c.ahy, dEz_y);
+            const float p1 = psi_rn(c.bhy, rr[9 * NT], c.ahy, dEx_y);
             h2x -= p0;
             h2z += p1;
             if (valid && c.own) {
@@ -446,7 +422,7 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
     __syncthreads();
 
     // ---- stage D: E^{n+2} of plane r
-    if (c.needD) {
+    {
         const float hyi = xm(h2y), hzi = xm(h2z);
         const float hxj = ym(b.H1B), hzj = ym(b.H1B + XS);
         const float dHz_y = h2z - hzj, dHy_z = h2y - s.h2py, dHx_z = h2x - s.h2px;
@@ -454,9 +430,9 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
         float fx = s.e1p[0] + c.cey * dHz_y - cz * dHy_z;
         float fy = s.e1p[1] + cz * dHx_z - c.cex * dHz_x;
         float fz = s.e1p[2] + c.cex * dHy_x - c.cey * dHx_y;
-        if (c.sx) {
-            const float p0 = c.bex * rr[10 * NT] + c.aex * dHz_x;
-            const float p1 = c.bex * rr[11 * NT] + c.aex * dHy_x;
+        if (GEN && c.sx) {
+            const float p0 = psi_rn(c.bex, rr[10 * NT], c.aex, dHz_x);
+            const float p1 = psi_rn(c.bex, rr[11 * NT], c.aex, dHy_x);
             fy -= p0;
             fz += p1;
             if (valid && c.own) {
@@ -464,9 +440,9 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
                 a.pex_out[0][qo] = p0; a.pex_out[1][qo] = p1;
             }
         }
-        if (c.sy) {
-            const float p0 = c.bey * rr[12 * NT] + c.aey * dHz_y;
-            const float p1 = c.bey * rr[13 * NT] + c.aey * dHx_y;
+        if (GEN && c.sy) {
+            const float p0 = psi_rn(c.bey, rr[12 * NT], c.aey, dHz_y);
+            const float p1 = psi_rn(c.bey, rr[13 * NT], c.aey, dHx_y);
             fx += p0;
             fz -= p1;
             if (valid && c.own) {
@@ -480,8 +456,8 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
             if (c.mk & 0x02) fy += tb2_src(b, c, 1, u);
             if (c.mk & 0x04) fz += tb2_src(b, c, 2, u);
         }
-        if (c.j == 0) { fx = 0.0f; fz = 0.0f; }
-        if (c.i == 0) { fy = 0.0f; fz = 0.0f; }
+        if (GEN && c.j == 0) { fx = 0.0f; fz = 0.0f; }
+        if (GEN && c.i == 0) { fy = 0.0f; fz = 0.0f; }
         if (valid && c.own) {
             const int g = s.kr * (a.pitch * a.ny) + c.col;
             a.eout[0][g] = fx; a.eout[1][g] = fy; a.eout[2][g] = fz;
@@ -490,7 +466,7 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
     }
     // fluence of plane p-3: the step-n term from the last plane, then step n+1
     float mhby = 0.0f;
-    if (c.needFl) {
+    {
         mhby = gsy + yp(b.H1B + 2 * XS);
         if (valid && c.fown) {
             const float t1 = tb2_flux(s.gPEx + mPEx, s.gPEy + mPEy, s.gcz, s.ghbx, s.ghby, s.gHsz + mHsz, dt16);
@@ -512,23 +488,18 @@ __device__ __forceinline__ bool tb2_plane(const StepArgs<float>& a, const Tb2Tim
     s.zr = s.zq; s.zq = zn;
     // refill: plane p + 2 (fluence plane p - 1) into the slot of plane p - 2,
     // whose last reader was this plane
-    if (issue_next) tb2_issue<RY, TMA>(a, c, b, SR, s.ki, s.kq, maps);
+    if (issue_next) tb2_issue<RY, GEN>(a, c, b, SR, s.ki, s.kq);
     else cpa_commit();
     s.k3 = s.kr; s.kr = s.kq; s.kq = s.kp;
     s.kp = next_plane(s.kp, a.nz);
     s.ki = next_plane(s.ki, a.nz);
-    return true;
 }
 
 // One window, planes [kb, ke) of its E^{n+2} / H^{n+3/2} output (fluence
-// planes [kb-1, ke-1), modulo nz).  gq: the CTA's running copy number of the
-// window's first plane (TMA ring slots and mbarrier parities); returns the
-// number after the window, or -1 if a wait gave up (after draining the
-// window's copies still in flight).
-template <int RY, bool TMA>
-__device__ __forceinline__ int tb2_window(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw,
-                                          int window, int kb, int ke, const Tb2Bufs<RY>& b, int gq,
-                                          const Tb2Maps* maps)
+// planes [kb-1, ke-1), modulo nz).
+template <int RY, bool GEN>
+__device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw,
+                                           int window, int kb, int ke, const Tb2Bufs<RY>& b)
 {
     constexpr int NT = Tb2Smem<RY>::NT;
     Tb2Col c;
@@ -545,24 +516,6 @@ __device__ __forceinline__ int tb2_window(const StepArgs<float>& a, const Tb2Tim
     const int fxa = wx == 0 ? 0 : xa - 1, fxb = wx == tw.T - 1 ? nx : xb - 1;
     const int fya = wy == 0 ? 0 : ya - 1, fyb = wy == tw.U - 1 ? ny : yb - 1;
     c.fown = a.fluence != nullptr && c.i >= fxa && c.i < fxb && c.j >= fya && c.j < fyb;
-    // stage needs of this row (see Tb2Col): D writes the own rows, the fluence
-    // runs on the fluence rows, and each earlier stage runs where a later one
-    // reads its result (same row, or the row above / below through the
-    // exchange buffers).  Rows past the box run every stage: their zeros are
-    // the wall values their neighbours read.
-    {
-        auto own_y = [&](int jj) { return jj >= ya && jj < yb; };
-        auto fl_y = [&](int jj) { return jj >= fya && jj < fyb; };
-        auto need_c = [&](int jj) { return own_y(jj) || own_y(jj + 1) || fl_y(jj) || fl_y(jj - 1); };
-        auto need_b = [&](int jj) { return need_c(jj) || need_c(jj - 1) || fl_y(jj) || fl_y(jj - 1) || own_y(jj); };
-        const int j = c.j;
-        const bool past = j >= ny;
-        c.needD = past || own_y(j);
-        c.needFl = past || fl_y(j);
-        c.needC = past || need_c(j);
-        c.needB = past || need_b(j);
-        c.needA = past || need_b(j) || need_b(j + 1) || fl_y(j) || fl_y(j - 1) || need_c(j);
-    }
     c.sx = c.indom && npml > 0 && (c.i < npml || c.i >= nx - npml);
     c.sy = c.indom && npml > 0 && (c.j < npml || c.j >= ny - npml);
     const int ii = c.sx ? (c.i < npml ? c.i : c.i - nx + w2) : 0;
@@ -601,42 +554,31 @@ __device__ __forceinline__ int tb2_window(const StepArgs<float>& a, const Tb2Tim
     s.kq = s.kp == 0 ? nz - 1 : s.kp - 1;
     s.kr = s.kq == 0 ? nz - 1 : s.kq - 1;
     s.k3 = s.kr == 0 ? nz - 1 : s.kr - 1;
-    // prologue: planes P0, P0 + 1 (their fluence planes P0 - 3, P0 - 2)
-    tb2_issue<RY, TMA>(a, c, b, gq & 3, s.kp, s.k3, maps);
+    // prologue: planes P0, P0 + 1 into slots 0, 1 (their fluence planes P0 - 3, P0 - 2)
+    tb2_issue<RY, GEN>(a, c, b, 0, s.kp, s.k3);
     const int k1 = next_plane(s.kp, nz);
-    tb2_issue<RY, TMA>(a, c, b, (gq + 1) & 3, k1, s.kr, maps);
+    tb2_issue<RY, GEN>(a, c, b, 1, k1, s.kr);
     s.ki = next_plane(k1, nz);
-    // the ring's four slots: plane p has copy number q = gq + p - P0, slot q mod 4
+    // the ring's four slots: plane p uses slot u = (p - P0) mod 4
     int p = P0;
-    int q = gq;
-    bool ok = true;
+    int u = 0;
     for (;;) {
-        ok = tb2_plane<RY, 0, TMA>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, q, maps);
-        ++q;
-        if (!ok || ++p > P1) break;
-        ok = tb2_plane<RY, 1, TMA>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, q, maps);
-        ++q;
-        if (!ok || ++p > P1) break;
+        tb2_plane<RY, 0, GEN>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        u = (u + 1) & 3;
+        if (++p > P1) break;
+        tb2_plane<RY, 1, GEN>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        u = (u + 1) & 3;
+        if (++p > P1) break;
     }
     cpa_wait0();
-    if constexpr (TMA) {
-        if (!ok) {   // drain the copies of this plane and the next, if issued (bounded waits)
-            --q;
-            const int last = q + 1 < gq + (P1 - P0) ? q + 1 : gq + (P1 - P0);
-            for (int r = q; r <= last; ++r) mbar_wait_bounded(b.bar + (r & 3), uint32_t(r >> 2) & 1u);
-            return -1;
-        }
-    }
-    return gq + (P1 - P0 + 1);
 }
 
-template <int RY, bool TMA>
-__device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw,
-                                        const Tb2Maps* maps)
+template <int RY>
+__device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, R = S::R, NF = S::NF;
-    extern __shared__ __align__(128) unsigned char tb2_smem[];
+    extern __shared__ __align__(16) unsigned char tb2_smem[];
     Tb2Bufs<RY> b;
     b.fring = reinterpret_cast<float2*>(tb2_smem);
     b.ring = reinterpret_cast<float*>(b.fring + R * NT);
@@ -646,27 +588,26 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
     b.E1B = b.HB + 3 * XS;
     b.H1B = b.E1B + 4 * XS;
     b.SC = b.H1B + 3 * XS + 32;
-    b.bar = reinterpret_cast<uint64_t*>(b.SC + 12 * NT);
-    b.abort = reinterpret_cast<int*>(b.bar + R);
-    if (TMA && threadIdx.x == 0 && threadIdx.y == 0) {
-        for (int q = 0; q < R; ++q) mbar_init(b.bar + q, 1);
-        *b.abort = 0;
-        mbar_fence_init();
-    }
     // the NX + 1 zero rows of the exchange arrays (never written again; the
     // first window's barrier orders these stores before any read)
     for (int q = threadIdx.y * 32 + threadIdx.x; q < (S::NX + 1) * 32; q += NT)
         b.EB[(q / 32) * XS + q % 32] = 0.0f;
     long long w = tw.start[blockIdx.x];
     const long long wend = tw.start[blockIdx.x + 1];
-    int gq = 0;
     while (w < wend) {
         const int window = int(w / a.nz), kb = int(w % a.nz);
         const long long left = wend - w;
         const int ke = left < (long long)(a.nz - kb) ? kb + int(left) : a.nz;
         const long long t0 = tw.prof ? clock64() : 0;
-        gq = tb2_window<RY, TMA>(a, tt, tw, window, kb, ke, b, gq, maps);
-        if (TMA && gq < 0) return;   // a wait gave up (every thread): the CTA stops
+        // a window off the box faces and the CPML shells runs without the
+        // checks of walls, shells and columns past the box
+        const int wx = window % tw.T, wy = window / tw.T;
+        const int L0 = kTb2Sx * wx, M0 = (RY - 4) * wy;
+        const bool gen = wx == 0 || wx == tw.T - 1 || wy == 0 || wy == tw.U - 1 ||
+                         (a.npml > 0 && (L0 < a.npml || L0 + kTb2Wx > a.nx - a.npml || M0 < a.npml ||
+                                         M0 + RY > a.ny - a.npml));
+        if (gen) tb2_window<RY, true>(a, tt, tw, window, kb, ke, b);
+        else tb2_window<RY, false>(a, tt, tw, window, kb, ke, b);
         w += ke - kb;
         __syncthreads();   // the exchange buffers are reused by the next window
         if (tw.prof && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -681,16 +622,7 @@ template <int RY>
 __global__ void __launch_bounds__(32 * RY, 1)
 yee_tb2(const StepArgs<float> a, const Tb2Times tt, const __grid_constant__ Tb2Plan tw)
 {
-    tb2_run<RY, false>(a, tt, tw, nullptr);
-}
-
-// The same with E^n, H^{n-1/2} and the fluence copied by TMA.
-template <int RY>
-__global__ void __launch_bounds__(32 * RY, 1)
-yee_tb2_tma(const StepArgs<float> a, const Tb2Times tt, const __grid_constant__ Tb2Plan tw,
-            const __grid_constant__ Tb2Maps maps)
-{
-    tb2_run<RY, true>(a, tt, tw, &maps);
+    tb2_run<RY>(a, tt, tw);
 }
 
 // The same with the time factors of the two steps read from a device table
@@ -704,7 +636,7 @@ yee_tb2_t(const StepArgs<float> a, const StepTime<float>* __restrict__ times, in
     Tb2Times tt;
     tt.th0 = times[i0].th; tt.te0 = times[i0].te;
     tt.th1 = times[i1].th; tt.te1 = times[i1].te;
-    tb2_run<RY, false>(a, tt, tw, nullptr);
+    tb2_run<RY>(a, tt, tw);
 }
 
 }  // namespace fdtd
