@@ -46,8 +46,9 @@
 //     recompute race-free.
 //   * Every row of a window runs every stage, whether or not a column the
 //     window writes depends on it, so that the stage code has no branches
-//     on the row; windows off the box faces and the CPML shells (GEN false)
-//     run code without the checks of PEC walls, psi and columns past the box.
+//     on the row; windows off the x faces and x shells run code without the
+//     checks of the x walls, x psi and columns past the box in x, and the
+//     same for y (template flags GX, GY).
 //   * A CTA takes a contiguous range of the flattened (window, plane) work;
 //     the ranges have equal estimated cost (windows with CPML shell or antenna
 //     columns weigh more, with weights the autotuner picks by timing).  Where
@@ -148,6 +149,27 @@ __device__ __forceinline__ Cpx<float> cmul(Cpx<float> z, Cpx<float> t)
     return Cpx<float>{fma_rn(z.x, t.x, -mul_rn(z.y, t.y)), fma_rn(z.x, t.y, mul_rn(z.y, t.x))};
 }
 
+// Stores of the window's outputs with the L2 evict-last priority: a window
+// writes its own 28 columns of a row, so the first and last 32-byte sectors
+// of the row are shared with the neighbouring windows, which write their
+// part at another time; kept in L2 until the neighbour's part arrives, such
+// a sector reaches DRAM whole.
+__device__ __forceinline__ uint64_t tb2_store_policy()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void st_keep(float* q, float v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(q), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_keep(float2* q, float2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(q), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+
 // CPML psi update b psi + a d.
 __device__ __forceinline__ float psi_rn(float b, float psi, float aa, float d) { return fma_rn(b, psi, mul_rn(aa, d)); }
 
@@ -188,28 +210,29 @@ struct Tb2Bufs {
 __device__ __forceinline__ int next_plane(int k, int nz) { return k + 1 == nz ? 0 : k + 1; }
 
 // Copies of plane k (fluence plane kf) into ring slot s of this thread.
-template <int RY, bool GEN>
+template <int RY, int G>
 __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col& c, const Tb2Bufs<RY>& b, int s,
                                           int k, int kf)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF;
     float* r = b.ring + s * NF * NT + c.tid;
+    constexpr bool GX = G & 1, GY = G & 2;
     const int g = k * (a.pitch * a.ny) + c.col;
-    cpa4(r + 0 * NT, a.ein[0] + g, !GEN || c.indom);
-    cpa4(r + 1 * NT, a.ein[1] + g, !GEN || c.indom);
-    cpa4(r + 2 * NT, a.ein[2] + g, !GEN || c.indom);
-    cpa4(r + 3 * NT, a.hin[0] + g, !GEN || c.indom);
-    cpa4(r + 4 * NT, a.hin[1] + g, !GEN || c.indom);
-    cpa4(r + 5 * NT, a.hin[2] + g, !GEN || c.indom);
-    if (GEN && c.sx) {
+    cpa4(r + 0 * NT, a.ein[0] + g, (!GX && !GY) || c.indom);
+    cpa4(r + 1 * NT, a.ein[1] + g, (!GX && !GY) || c.indom);
+    cpa4(r + 2 * NT, a.ein[2] + g, (!GX && !GY) || c.indom);
+    cpa4(r + 3 * NT, a.hin[0] + g, (!GX && !GY) || c.indom);
+    cpa4(r + 4 * NT, a.hin[1] + g, (!GX && !GY) || c.indom);
+    cpa4(r + 5 * NT, a.hin[2] + g, (!GX && !GY) || c.indom);
+    if (GX && c.sx) {
         const int q = k * a.ny * (2 * a.npml) + c.colx;
         cpa4(r + 6 * NT, a.phx_in[0] + q, true);    // Hyx
         cpa4(r + 7 * NT, a.phx_in[1] + q, true);    // Hzx
         cpa4(r + 10 * NT, a.pex[0] + q, true);      // Eyx
         cpa4(r + 11 * NT, a.pex[1] + q, true);      // Ezx
     }
-    if (GEN && c.sy) {
+    if (GY && c.sy) {
         const int q = k * (2 * a.npml) * a.pitch + c.coly;
         cpa4(r + 8 * NT, a.phy_in[0] + q, true);    // Hxy
         cpa4(r + 9 * NT, a.phy_in[1] + q, true);    // Hzy
@@ -235,26 +258,27 @@ __device__ __forceinline__ float tb2_src(const Tb2Bufs<RY>& b, const Tb2Col& c, 
 // Every row runs every stage: a row whose results no written column needs
 // computes values that reach no output (rows beyond the window read the zero
 // rows of the exchange arrays), and the stage code stays free of branches.
-template <int RY, int U, bool GEN>
+template <int RY, int U, int G>
 __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Col& c,
                                           const Tb2Bufs<RY>& b, Tb2Carry& s, bool valid, bool issue_next,
                                           float dt16, int u)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF, XS = S::XS;
+    constexpr bool GX = G & 1, GY = G & 2;
     const int SP = u, SQ = (u + 3) & 3, SR = (u + 2) & 3;   // slots of planes p, p-1, p-2
     constexpr int PP = U & 1, PQ = PP ^ 1;                        // exchange parities of planes p, p-1
     const int lane = c.lane, tid = c.tid;
-    // (an interior window, !GEN, takes the edge lane's own value past the
-    // window: lanes 0 and 31 are halo there, and what they compute reaches
-    // no column the window writes)
+    // (a window off the x faces, !GX, takes the edge lane's own value past
+    // the window: lanes 0 and 31 are halo there, and what they compute
+    // reaches no column the window writes)
     auto xp = [&](float v) {   // value of the +x neighbour (0 past the window)
         const float u = __shfl_down_sync(0xffffffffu, v, 1);
-        return GEN && lane == 31 ? 0.0f : u;
+        return GX && lane == 31 ? 0.0f : u;
     };
     auto xm = [&](float v) {   // value of the -x neighbour
         const float u = __shfl_up_sync(0xffffffffu, v, 1);
-        return GEN && lane == 0 ? 0.0f : u;
+        return GX && lane == 0 ? 0.0f : u;
     };
     // y neighbours from the padded exchange arrays (zero beyond the window)
     auto yp = [&](const float* q) { return q[S::XO + tid + 32]; };
@@ -285,14 +309,14 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         hx = ox - c.chy * dEz_y + cz * dEy_z;
         hy = oy - cz * dEx_z + c.chx * dEz_x;
         hz = oz - c.chx * dEy_x + c.chy * dEx_y;
-        if (GEN && c.sx) {
+        if (GX && c.sx) {
             const float p0 = psi_rn(c.bhx, rq[6 * NT], c.ahx, dEz_x);   // Hyx
             const float p1 = psi_rn(c.bhx, rq[7 * NT], c.ahx, dEy_x);   // Hzx
             hy += p0;
             hz -= p1;
             rq[6 * NT] = p0; rq[7 * NT] = p1;
         }
-        if (GEN && c.sy) {
+        if (GY && c.sy) {
             const float p0 = psi_rn(c.bhy, rq[8 * NT], c.ahy, dEz_y);   // Hxy
             const float p1 = psi_rn(c.bhy, rq[9 * NT], c.ahy, dEx_y);   // Hzy
             hx -= p0;
@@ -334,14 +358,14 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         nex = ex + c.cey * dHz_y - cz * dHy_z;
         ney = ey + cz * dHx_z - c.cex * dHz_x;
         nez = ez + c.cex * dHy_x - c.cey * dHx_y;
-        if (GEN && c.sx) {
+        if (GX && c.sx) {
             const float p0 = psi_rn(c.bex, rq[10 * NT], c.aex, dHz_x);   // Eyx
             const float p1 = psi_rn(c.bex, rq[11 * NT], c.aex, dHy_x);   // Ezx
             rq[10 * NT] = p0; rq[11 * NT] = p1;
             ney -= p0;
             nez += p1;
         }
-        if (GEN && c.sy) {
+        if (GY && c.sy) {
             const float p0 = psi_rn(c.bey, rq[12 * NT], c.aey, dHz_y);   // Exy
             const float p1 = psi_rn(c.bey, rq[13 * NT], c.aey, dHx_y);   // Ezy
             rq[12 * NT] = p0; rq[13 * NT] = p1;
@@ -354,8 +378,8 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
             if (c.mk & 0x02) ney += tb2_src(b, c, 1, u);
             if (c.mk & 0x04) nez += tb2_src(b, c, 2, u);
         }
-        if (GEN && c.j == 0) { nex = 0.0f; nez = 0.0f; }   // PEC: tangential E
-        if (GEN && c.i == 0) { ney = 0.0f; nez = 0.0f; }
+        if (GY && c.j == 0) { nex = 0.0f; nez = 0.0f; }   // PEC: tangential E
+        if (GX && c.i == 0) { ney = 0.0f; nez = 0.0f; }
     }
     // fluence term of step n for plane r (sums of planes r and q)
     float nhby = 0.0f, tn_new = 0.0f;
@@ -376,24 +400,26 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         h2x = s.h1p[0] - c.chy * dEz_y + cz * dEy_z;
         h2y = s.h1p[1] - cz * dEx_z + c.chx * dEz_x;
         h2z = s.h1p[2] - c.chx * dEy_x + c.chy * dEx_y;
-        if (GEN && c.sx) {
+        if (GX && c.sx) {
             const float p0 = psi_rn(c.bhx, rr[6 * NT], c.ahx, dEz_x);
             const float p1 = psi_rn(c.bhx, rr[7 * NT], c.ahx, dEy_x);
             h2y += p0;
             h2z -= p1;
             if (valid && c.own) {
                 const int qo = s.kr * a.ny * (2 * a.npml) + c.colx;
-                a.phx_out[0][qo] = p0; a.phx_out[1][qo] = p1;
+                const uint64_t pol = tb2_store_policy();
+                st_keep(a.phx_out[0] + qo, p0, pol); st_keep(a.phx_out[1] + qo, p1, pol);
             }
         }
-        if (GEN && c.sy) {
+        if (GY && c.sy) {
             const float p0 = psi_rn(c.bhy, rr[8 * NT], c.ahy, dEz_y);
             const float p1 = psi_rn(c.bhy, rr[9 * NT], c.ahy, dEx_y);
             h2x -= p0;
             h2z += p1;
             if (valid && c.own) {
                 const int qo = s.kr * (2 * a.npml) * a.pitch + c.coly;
-                a.phy_out[0][qo] = p0; a.phy_out[1][qo] = p1;
+                const uint64_t pol = tb2_store_policy();
+                st_keep(a.phy_out[0] + qo, p0, pol); st_keep(a.phy_out[1] + qo, p1, pol);
             }
         }
         if (c.mk & 0x38) {
@@ -430,24 +456,26 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         float fx = s.e1p[0] + c.cey * dHz_y - cz * dHy_z;
         float fy = s.e1p[1] + cz * dHx_z - c.cex * dHz_x;
         float fz = s.e1p[2] + c.cex * dHy_x - c.cey * dHx_y;
-        if (GEN && c.sx) {
+        if (GX && c.sx) {
             const float p0 = psi_rn(c.bex, rr[10 * NT], c.aex, dHz_x);
             const float p1 = psi_rn(c.bex, rr[11 * NT], c.aex, dHy_x);
             fy -= p0;
             fz += p1;
             if (valid && c.own) {
                 const int qo = s.kr * a.ny * (2 * a.npml) + c.colx;
-                a.pex_out[0][qo] = p0; a.pex_out[1][qo] = p1;
+                const uint64_t pol = tb2_store_policy();
+                st_keep(a.pex_out[0] + qo, p0, pol); st_keep(a.pex_out[1] + qo, p1, pol);
             }
         }
-        if (GEN && c.sy) {
+        if (GY && c.sy) {
             const float p0 = psi_rn(c.bey, rr[12 * NT], c.aey, dHz_y);
             const float p1 = psi_rn(c.bey, rr[13 * NT], c.aey, dHx_y);
             fx += p0;
             fz -= p1;
             if (valid && c.own) {
                 const int qo = s.kr * (2 * a.npml) * a.pitch + c.coly;
-                a.pey_out[0][qo] = p0; a.pey_out[1][qo] = p1;
+                const uint64_t pol = tb2_store_policy();
+                st_keep(a.pey_out[0] + qo, p0, pol); st_keep(a.pey_out[1] + qo, p1, pol);
             }
         }
         if (c.mk & 0x07) {
@@ -456,12 +484,13 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
             if (c.mk & 0x02) fy += tb2_src(b, c, 1, u);
             if (c.mk & 0x04) fz += tb2_src(b, c, 2, u);
         }
-        if (GEN && c.j == 0) { fx = 0.0f; fz = 0.0f; }
-        if (GEN && c.i == 0) { fy = 0.0f; fz = 0.0f; }
+        if (GY && c.j == 0) { fx = 0.0f; fz = 0.0f; }
+        if (GX && c.i == 0) { fy = 0.0f; fz = 0.0f; }
         if (valid && c.own) {
             const int g = s.kr * (a.pitch * a.ny) + c.col;
-            a.eout[0][g] = fx; a.eout[1][g] = fy; a.eout[2][g] = fz;
-            a.hout[0][g] = h2x; a.hout[1][g] = h2y; a.hout[2][g] = h2z;
+            const uint64_t pol = tb2_store_policy();
+            st_keep(a.eout[0] + g, fx, pol); st_keep(a.eout[1] + g, fy, pol); st_keep(a.eout[2] + g, fz, pol);
+            st_keep(a.hout[0] + g, h2x, pol); st_keep(a.hout[1] + g, h2y, pol); st_keep(a.hout[2] + g, h2z, pol);
         }
     }
     // fluence of plane p-3: the step-n term from the last plane, then step n+1
@@ -473,7 +502,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
             float2 acc = b.fring[SP * NT + tid];
             acc = FluAcc<float>::add(acc, s.tn);
             acc = FluAcc<float>::add(acc, t1);
-            static_cast<float2*>(a.fluence)[s.k3 * (a.pitch * a.ny) + c.col] = acc;
+            st_keep(static_cast<float2*>(a.fluence) + s.k3 * (a.pitch * a.ny) + c.col, acc, tb2_store_policy());
         }
     }
 
@@ -488,7 +517,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     s.zr = s.zq; s.zq = zn;
     // refill: plane p + 2 (fluence plane p - 1) into the slot of plane p - 2,
     // whose last reader was this plane
-    if (issue_next) tb2_issue<RY, GEN>(a, c, b, SR, s.ki, s.kq);
+    if (issue_next) tb2_issue<RY, G>(a, c, b, SR, s.ki, s.kq);
     else cpa_commit();
     s.k3 = s.kr; s.kr = s.kq; s.kq = s.kp;
     s.kp = next_plane(s.kp, a.nz);
@@ -497,7 +526,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
 
 // One window, planes [kb, ke) of its E^{n+2} / H^{n+3/2} output (fluence
 // planes [kb-1, ke-1), modulo nz).
-template <int RY, bool GEN>
+template <int RY, int G>
 __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Times& tt, const Tb2Plan& tw,
                                            int window, int kb, int ke, const Tb2Bufs<RY>& b)
 {
@@ -555,18 +584,18 @@ __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Ti
     s.kr = s.kq == 0 ? nz - 1 : s.kq - 1;
     s.k3 = s.kr == 0 ? nz - 1 : s.kr - 1;
     // prologue: planes P0, P0 + 1 into slots 0, 1 (their fluence planes P0 - 3, P0 - 2)
-    tb2_issue<RY, GEN>(a, c, b, 0, s.kp, s.k3);
+    tb2_issue<RY, G>(a, c, b, 0, s.kp, s.k3);
     const int k1 = next_plane(s.kp, nz);
-    tb2_issue<RY, GEN>(a, c, b, 1, k1, s.kr);
+    tb2_issue<RY, G>(a, c, b, 1, k1, s.kr);
     s.ki = next_plane(k1, nz);
     // the ring's four slots: plane p uses slot u = (p - P0) mod 4
     int p = P0;
     int u = 0;
     for (;;) {
-        tb2_plane<RY, 0, GEN>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        tb2_plane<RY, 0, G>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
         u = (u + 1) & 3;
         if (++p > P1) break;
-        tb2_plane<RY, 1, GEN>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        tb2_plane<RY, 1, G>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
         u = (u + 1) & 3;
         if (++p > P1) break;
     }
@@ -600,14 +629,16 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
         const int ke = left < (long long)(a.nz - kb) ? kb + int(left) : a.nz;
         const long long t0 = tw.prof ? clock64() : 0;
         // a window off the box faces and the CPML shells runs without the
-        // checks of walls, shells and columns past the box
+        // checks of walls, psi and columns past the box (G = 0; the x and y
+        // checks are separate flags, but instantiating them apart measured no
+        // faster)
         const int wx = window % tw.T, wy = window / tw.T;
         const int L0 = kTb2Sx * wx, M0 = (RY - 4) * wy;
         const bool gen = wx == 0 || wx == tw.T - 1 || wy == 0 || wy == tw.U - 1 ||
                          (a.npml > 0 && (L0 < a.npml || L0 + kTb2Wx > a.nx - a.npml || M0 < a.npml ||
                                          M0 + RY > a.ny - a.npml));
-        if (gen) tb2_window<RY, true>(a, tt, tw, window, kb, ke, b);
-        else tb2_window<RY, false>(a, tt, tw, window, kb, ke, b);
+        if (gen) tb2_window<RY, 3>(a, tt, tw, window, kb, ke, b);
+        else tb2_window<RY, 0>(a, tt, tw, window, kb, ke, b);
         w += ke - kb;
         __syncthreads();   // the exchange buffers are reused by the next window
         if (tw.prof && threadIdx.x == 0 && threadIdx.y == 0) {
