@@ -43,12 +43,14 @@ MAX_REPEATS = 100000
 TRAFFIC: dict[str, float | None] = {"yee_h_cell": 307.85e6, "yee_e_cell": 545.41e6, "yee_tb2": None}
 UNIT = "Gcell-updates/s"
 
-# FP64 instructions per cell of each FP64 cell pass on the 256x256x128 workload
-# after 600 steps (smsp__inst_executed_pipe_fp64.sum x 32 / cells from one ncu
-# capture of the kernels as they stand; summary and command in profiles/).
-# The FP64 passes are bound by GB300's FP64 pipe: 2 FP64 instructions per SM
-# per clock, whatever the number of active lanes of the warp instruction.
-FP64_INST_PER_CELL: dict[str, float | None] = {"yee_h_cell": None, "yee_e_cell": None}
+# FP64 instructions per cell of each FP64 pass (the cell pass and its antenna
+# pass) on the 256x256x128 workload after 600 steps
+# (smsp__inst_executed_pipe_fp64.sum x 32 / cells from one ncu capture of the
+# kernels as they stand; summary and command in profiles/).  The FP64 passes
+# are bound by GB300's FP64 pipe: 2 FP64 instructions per SM per clock,
+# whatever the number of active lanes of the warp instruction.
+FP64_INST_PER_CELL: dict[str, float | None] = {"yee_h_cell + antenna_add": 14.25 + 0.19,
+                                               "yee_e_cell + antenna_add": 44.34 + 0.19}
 # Steps run on the FP64 grid before its tiles are tuned and timed: the FP64
 # norm of the fluence term costs less on cells whose fields are still zero,
 # so the first steps of a run are cheaper than the rest of it.
@@ -112,6 +114,8 @@ def pass_bytes_per_cell(w, variant: int, b: int) -> list[tuple[str, float]]:
     if variant == 4:
         return [("yee_hflu_tma", h + 16), ("yee_e_pass", 9 * b + b * psi)]
     if variant == 5:
+        if b == 8:   # FP64: each pass is followed by its antenna pass (antenna_add), timed with it
+            return [("yee_h_cell + antenna_add", h), ("yee_e_cell + antenna_add", 12 * b + 16 + b * psi)]
         return [("yee_h_cell", h), ("yee_e_cell", 12 * b + 16 + b * psi)]
     if variant == 7:
         return [("yee_tb2", 2 * one)]

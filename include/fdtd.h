@@ -268,21 +268,23 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
  * CTA takes a contiguous range of (window, plane) work of equal estimated
  * cost; a window also costs three planes at its start (the two-step
  * wavefront refills there).  Weights in [0, 16] (else EINVAL); defaults 0.25
- * and 0.2.  fdtd_autotune times a few pairs, then measures every window's
- * cost per plane in two launches of the fastest (SM cycles per window,
- * recorded by the kernel) and times ranges balanced on those measured
- * costs; it keeps the fastest.  While the measured costs are in use,
- * fdtd_get_balance returns -1 for both weights; fdtd_set_balance returns to
- * the weights.  The results do not depend on the balance, only the time
- * does. */
+ * and 0.2.  fdtd_autotune times a few pairs, then refines the fastest pair's
+ * ranges on measured times (fdtd_measure_balance) and times those; it keeps
+ * the fastest.  While refined ranges are in use, fdtd_get_balance returns -1
+ * for both weights; fdtd_set_balance returns to the weights.  The results do
+ * not depend on the balance, only the time does. */
 fdtd_status fdtd_set_balance(fdtd_grid* g, float w_shell, float w_antenna);
 fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenna);
-/* Measure the per-window costs of the grid's variant-7 tile in two launches
- * (four steps, run from a copy of the state and undone: the state is saved to
+/* Refine the CTAs' work ranges of the grid's variant-7 tile on measured
+ * times (the paper has no counterpart): in three rounds, two launches record
+ * the SM cycles every CTA takes, and the ranges' boundaries move so that
+ * each CTA's share of the measured time becomes equal.  The twelve steps run
+ * from a copy of the state and are undone (the state is saved to
  * `scratch_state`, fdtd_state_bytes bytes of device memory the caller owns,
- * and restored) and balance the CTAs' ranges on them from now on, as
- * fdtd_autotune does (the paper has no counterpart).  EINVAL unless the tile
- * is variant 7; the costs are dropped when the antenna's columns change. */
+ * and restored).  The refined ranges are used from then on (fdtd_autotune
+ * does the same for its fastest weights).  EINVAL unless the tile is variant
+ * 7; the ranges are dropped when the antenna's columns change, and hold for
+ * single-grid steps only (a batch's two-step launches use the weights). */
 fdtd_status fdtd_measure_balance(fdtd_grid* g, void* scratch_state);
 
 /* Measurement (the paper has no counterpart): advance `nsteps` steps like

@@ -18,6 +18,7 @@
 #include "../../include/fdtd.h"
 #include "engine.h"
 #include "grid_impl.h"
+#include "yee_tb2.cuh"
 #include "tma_host.h"
 #include "yee_fused.cuh"
 #include "fluence.cuh"
@@ -102,11 +103,7 @@ bool compute_layout(const fdtd_grid_desc& d, Layout& L)
     L.zph32 = take(nz * 8);
     L.flu_out = d.fluence ? take(nz * ny * nx * 8) : 0;
     L.alist = take(2 * nx * ny * 4);
-    {   // per-window counters of variant 7's measuring launch, for its most windows (ty 8)
-        int t = 0, u = 0;
-        tb2_windows(d, 8, &t, &u);
-        L.tb2prof = take(size_t(t) * u * 16);
-    }
+    L.tb2prof = take(size_t(kTb2MaxCtas) * 8);   // per-CTA cycles of variant 7's measuring launches
     L.err = take(256);
     L.total = off;
     return true;
@@ -451,9 +448,10 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->has_source = false;
     g->src_gen = 0;
     g->tb2_key.ry = 0;
-    g->tb2_cost_ry = 0;
-    g->tb2_cost_src = -1;
-    g->tb2_cost_gen = 0;
+    g->tb2_ref_ry = 0;
+    g->tb2_ref_slots = 0;
+    g->tb2_ref_src = -1;
+    g->tb2_ref_gen = 0;
     g->tb2_profile = false;
     g->ant_cols[0] = g->ant_cols[1] = 0;
     g->ant_apart = false;
@@ -739,28 +737,32 @@ static cudaError_t run_steps(fdtd_grid* g, int nsteps, const TileConfig& tc)
     return cudaSuccess;
 }
 
-// Launches of variant 7 in configuration tc that record every window's SM
-// cycles and wavefront iterations (kMeasureLaunches, counters summed), then
-// the per-window costs stored on the grid (tb2_store_costs).  Advances the
-// grid by 2 kMeasureLaunches steps.
+// Variant 7 in configuration tc, measured and refined kRefineRounds times:
+// kMeasureLaunches launches record every CTA's SM cycles, and tb2_refine
+// moves the ranges' boundaries so that the CTAs' times become equal.
+// Advances the grid by 2 kMeasureLaunches kRefineRounds steps.
 constexpr int kMeasureLaunches = 2;
+constexpr int kRefineRounds = 3;
 static cudaError_t tb2_measure(fdtd_grid* g, const TileConfig& tc)
 {
-    int T = 0, U = 0;
-    tb2_windows(g->desc, tc.ty, &T, &U);
-    const size_t nw = size_t(T) * U;
+    const int slots = tb2_slots(g, tc.ty);
+    if (slots <= 0) return cudaErrorInvalidConfiguration;
     void* prof = static_cast<char*>(g->arena) + g->L.tb2prof;
-    cudaError_t err = cudaMemsetAsync(prof, 0, nw * 16, g->stream);
-    if (err != cudaSuccess) return err;
-    g->tb2_profile = true;
-    err = run_steps(g, 2 * kMeasureLaunches, tc);
-    g->tb2_profile = false;
-    if (err != cudaSuccess) return err;
-    std::vector<unsigned long long> counts(2 * nw);
-    err = cudaMemcpyAsync(counts.data(), prof, nw * 16, cudaMemcpyDeviceToHost, g->stream);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(g->stream);
-    if (err != cudaSuccess) return err;
-    tb2_store_costs(g, tc.ty, counts.data());
+    TileConfig t = tc;
+    for (int round = 0; round < kRefineRounds; ++round) {
+        cudaError_t err = cudaMemsetAsync(prof, 0, size_t(slots) * 8, g->stream);
+        if (err != cudaSuccess) return err;
+        g->tb2_profile = true;
+        err = run_steps(g, 2 * kMeasureLaunches, t);
+        g->tb2_profile = false;
+        if (err != cudaSuccess) return err;
+        std::vector<unsigned long long> cycles(static_cast<size_t>(slots));
+        err = cudaMemcpyAsync(cycles.data(), prof, size_t(slots) * 8, cudaMemcpyDeviceToHost, g->stream);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(g->stream);
+        if (err != cudaSuccess) return err;
+        tb2_refine(g, t.ty, slots, cycles.data());
+        t.measured = true;   // the next round measures the refined ranges
+    }
     return cudaSuccess;
 }
 

@@ -52,8 +52,8 @@ struct TileConfig {
     // columns, relative to a plain window (the CTAs' work ranges are balanced
     // on these estimates)
     float w_shell = 0.25f, w_ant = 0.2f;
-    // variant 7: balance on the per-window costs measured by the autotuner
-    // (fdtd_grid::tb2_cost) instead of the weights above
+    // variant 7: run the ranges refined from measured per-CTA times
+    // (fdtd_grid::tb2_refined) instead of those of the weights above
     bool measured = false;
 };
 
@@ -111,11 +111,11 @@ struct fdtd_grid {
         float w_shell, w_ant;
         bool measured;
     } tb2_key;                          // what they were computed for (ry 0: nothing cached)
-    std::vector<double> tb2_cost;       // variant 7: measured cost per window-plane (tb2_cost_ry windows)
-    int tb2_cost_ry;                    // the window height they were measured for (0: none)
-    int tb2_cost_src;                   // the antenna generation they were measured with
-    int tb2_cost_gen;                   // bumped whenever tb2_cost changes
-    bool tb2_profile;                   // the next variant-7 launches record per-window costs
+    std::vector<long long> tb2_refined; // variant 7: CTA ranges refined from measured per-CTA times
+    int tb2_ref_ry, tb2_ref_slots;      // the window height and CTA count they are for (ry 0: none)
+    int tb2_ref_src;                    // the antenna generation they were measured with
+    int tb2_ref_gen;                    // bumped whenever tb2_refined changes
+    bool tb2_profile;                   // the next variant-7 launches record per-CTA cycles
 };
 
 namespace fdtd {
@@ -140,10 +140,13 @@ inline int passes_per_step(const TileConfig& tc) { return tc.variant >= 3 && tc.
 cudaError_t launch_tb2(const fdtd_grid* g, int cur, long long n, const TileConfig& tc, cudaStream_t s);
 // Windows of variant 7 with 32 x ry columns on grid d: t along x, u along y.
 void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u);
-// Per-window cost per wavefront iteration from the counters (2 per window) of
-// a measuring launch with windows of 32 x ry columns; windows no segment
-// covered take the mean.  Stored on the grid for the plans of tc.measured.
-void tb2_store_costs(fdtd_grid* g, int ry, const unsigned long long* prof);
+// Moves the boundaries of the cached ranges (windows of 32 x ry columns,
+// `slots` CTAs) so that the CTAs' times, from the SM cycles each took in the
+// measured launches (cycles[c]) spread evenly over its items, become equal;
+// stored on the grid for the plans of tc.measured.
+void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles);
+// CTAs of one variant-7 launch on grid g with windows of 32 x ry columns.
+int tb2_slots(const fdtd_grid* g, int ry);
 // The same two steps with their time factors from a device table of
 // StepTime<float> (entries i0, i1), on at most max_ctas CTAs (a batch runs
 // several grids side by side): the batched graph's launch.

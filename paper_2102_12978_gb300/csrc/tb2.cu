@@ -18,52 +18,65 @@ void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u)
     *u = d.ny <= ry ? 1 : (d.ny - ry + (ry - 4) - 1) / (ry - 4) + 1;
 }
 
-void tb2_store_costs(fdtd_grid* g, int ry, const unsigned long long* prof)
+void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles)
 {
-    int T = 0, U = 0;
-    tb2_windows(g->desc, ry, &T, &U);
-    const size_t nw = size_t(T) * U;
-    std::vector<double> c(nw, 0.0);
-    double sum = 0.0;
-    size_t n = 0;
-    for (size_t w = 0; w < nw; ++w)
-        if (prof[2 * w + 1] > 0) {
-            c[w] = double(prof[2 * w]) / double(prof[2 * w + 1]);
-            sum += c[w];
-            ++n;
+    // the ranges the measured launches ran: the cached plan of this shape
+    if (g->tb2_key.ry != ry || g->tb2_key.slots != slots || g->tb2_start.size() != size_t(slots) + 1) return;
+    const std::vector<long long>& s = g->tb2_start;
+    double total = 0.0;
+    for (int c = 0; c < slots; ++c)
+        if (s[size_t(c) + 1] > s[size_t(c)]) total += double(cycles[c]);
+    if (!(total > 0.0)) return;
+    // cost of the items [0, x): piecewise linear, CTA c's items at cycles_c / (its item count) each
+    std::vector<long long> ns(size_t(slots) + 1, s.back());
+    ns[0] = 0;
+    int c = 0;
+    double cum = 0.0;
+    for (int k = 1; k < slots; ++k) {
+        const double target = total * k / slots;
+        while (c < slots && (s[size_t(c) + 1] == s[size_t(c)] || cum + double(cycles[c]) < target)) {
+            if (s[size_t(c) + 1] > s[size_t(c)]) cum += double(cycles[c]);
+            ++c;
         }
-    const double mean = n > 0 && sum > 0.0 ? sum / double(n) : 1.0;
-    for (size_t w = 0; w < nw; ++w) c[w] = (prof[2 * w + 1] > 0 ? c[w] : mean) / mean;
-    g->tb2_cost = c;
-    g->tb2_cost_ry = ry;
-    g->tb2_cost_src = g->src_gen;
-    g->tb2_cost_gen += 1;
+        long long x = s.back();
+        if (c < slots) {
+            const double frac = (target - cum) / double(cycles[c]);
+            x = s[size_t(c)] + (long long)std::llround(frac * double(s[size_t(c) + 1] - s[size_t(c)]));
+        }
+        ns[size_t(k)] = std::max(ns[size_t(k) - 1], std::min(x, s.back()));
+    }
+    g->tb2_refined = ns;
+    g->tb2_ref_ry = ry;
+    g->tb2_ref_slots = slots;
+    g->tb2_ref_src = g->src_gen;
+    g->tb2_ref_gen += 1;
 }
 
 // CTA work ranges of variant 7 on grid g: windows of 32 x RY columns, `slots`
-// resident CTAs.  Each window-plane has a cost: measured per window by the
-// autotuner (tc.measured), or estimated as 1, plus w_shell if the window
-// holds CPML shell columns, plus w_ant if it holds antenna columns.  A window
-// also costs kRestart iterations at its start (the wavefront refills).  Each
-// CTA gets a contiguous range of (window, plane) items of about the same
-// total cost.  Cached on the grid until the antenna, the costs or the launch
-// shape change.
+// resident CTAs.  Each CTA gets a contiguous range of (window, plane) items.
+// The ranges either have equal estimated cost -- a window-plane costs 1,
+// plus w_shell if the window holds CPML shell columns, plus w_ant if it holds
+// antenna columns, and a window costs kRestart more planes at its start (the
+// wavefront refills) -- or (tc.measured) are the ones tb2_refine moved until
+// the CTAs' measured times were equal.  Cached on the grid until the antenna,
+// the weights or the launch shape change.
 constexpr double kRestart = 3.0;
 static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2Plan& P)
 {
     const fdtd_grid_desc& d = g->desc;
     tb2_windows(d, RY, &P.T, &P.U);
     P.prof = nullptr;
-    const bool meas = tc.measured && g->tb2_cost_ry == RY && g->tb2_cost_src == g->src_gen &&
-                      g->tb2_cost.size() == size_t(P.T) * P.U;
+    const bool meas = tc.measured && g->tb2_ref_ry == RY && g->tb2_ref_slots == slots &&
+                      g->tb2_ref_src == g->src_gen && g->tb2_refined.size() == size_t(slots) + 1;
     auto& key = g->tb2_key;
     if (key.ry != RY || key.slots != slots || key.src_gen != g->src_gen || key.measured != meas ||
-        (meas ? key.cost_gen != g->tb2_cost_gen : (key.w_shell != tc.w_shell || key.w_ant != tc.w_ant))) {
-        const int nx = d.nx, ny = d.ny, nz = d.nz, npml = d.npml;
-        const int nw = P.T * P.U;
-        std::vector<double> cost(size_t(nw), 1.0);
-        if (meas) cost = g->tb2_cost;
-        else
+        (meas ? key.cost_gen != g->tb2_ref_gen : (key.w_shell != tc.w_shell || key.w_ant != tc.w_ant))) {
+        if (meas) {
+            g->tb2_start = g->tb2_refined;
+        } else {
+            const int nx = d.nx, ny = d.ny, nz = d.nz, npml = d.npml;
+            const int nw = P.T * P.U;
+            std::vector<double> cost(size_t(nw), 1.0);
             for (int wy = 0; wy < P.U; ++wy)
                 for (int wx = 0; wx < P.T; ++wx) {
                     const int i0 = kTb2Sx * wx, i1 = std::min(i0 + kTb2Wx, nx);
@@ -75,28 +88,29 @@ static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2P
                             for (int i = i0; i < i1 && !ant; ++i) ant = g->hmask[size_t(j) * nx + i] != 0;
                     cost[size_t(wy) * P.T + wx] = 1.0 + (shell ? tc.w_shell : 0.0) + (ant ? tc.w_ant : 0.0);
                 }
-        double total = 0.0;
-        for (double c : cost) total += c * (nz + kRestart);
-        const double share = total / slots;
-        std::vector<long long> start(size_t(slots) + 1, (long long)nw * nz);
-        start[0] = 0;
-        int c = 1;
-        double cum = 0.0;
-        for (int w = 0; w < nw && c < slots; ++w) {
-            const double cw = cost[size_t(w)];
-            const double span = cw * (nz + kRestart), base = cum + cw * kRestart;
-            while (c < slots && c * share < cum + span) {
-                long long k = (long long)std::ceil((c * share - base) / cw);
-                k = std::max(0LL, std::min((long long)nz, k));
-                start[size_t(c)] = std::max(start[size_t(c) - 1], (long long)w * nz + k);
-                ++c;
+            double total = 0.0;
+            for (double c : cost) total += c * (nz + kRestart);
+            const double share = total / slots;
+            std::vector<long long> start(size_t(slots) + 1, (long long)nw * nz);
+            start[0] = 0;
+            int c = 1;
+            double cum = 0.0;
+            for (int w = 0; w < nw && c < slots; ++w) {
+                const double cw = cost[size_t(w)];
+                const double span = cw * (nz + kRestart), base = cum + cw * kRestart;
+                while (c < slots && c * share < cum + span) {
+                    long long k = (long long)std::ceil((c * share - base) / cw);
+                    k = std::max(0LL, std::min((long long)nz, k));
+                    start[size_t(c)] = std::max(start[size_t(c) - 1], (long long)w * nz + k);
+                    ++c;
+                }
+                cum += span;
             }
-            cum += span;
+            g->tb2_start = start;
         }
-        g->tb2_start = start;
         key.ry = RY; key.slots = slots; key.src_gen = g->src_gen;
         key.w_shell = tc.w_shell; key.w_ant = tc.w_ant;
-        key.measured = meas; key.cost_gen = g->tb2_cost_gen;
+        key.measured = meas; key.cost_gen = g->tb2_ref_gen;
     }
     for (int c = 0; c <= slots; ++c) P.start[c] = g->tb2_start[size_t(c)];
 }
@@ -124,6 +138,14 @@ static cudaError_t tb2_blocks_per_sm(int* out)
     }
     *out = blocks_per_sm;
     return cudaSuccess;
+}
+
+int tb2_slots(const fdtd_grid* g, int ry)
+{
+    int per_sm = 0;
+    const cudaError_t e = ry == 8 ? tb2_blocks_per_sm<8>(&per_sm) : tb2_blocks_per_sm<16>(&per_sm);
+    if (e != cudaSuccess) return -1;
+    return std::min(kTb2MaxCtas, (g->sm_count > 0 ? g->sm_count : 152) * per_sm);
 }
 
 template <int RY>

@@ -75,9 +75,9 @@ struct Tb2Times {
 // [start[c], start[c + 1]): ranges of equal estimated cost (a window's planes
 // cost more where the window holds CPML shell or antenna columns), chosen on
 // the host.
-// prof, if not null, receives per window w the SM cycles its segments took
-// (prof[2 w]) and the wavefront iterations they ran (prof[2 w + 1]): the
-// measured per-window costs the host balances the ranges on.
+// prof, if not null, receives per CTA c the SM cycles it ran (prof[c] is
+// added to): the host moves the ranges' boundaries so that every CTA takes
+// the same time.
 constexpr int kTb2MaxCtas = 512;
 struct Tb2Plan {
     int T, U;
@@ -621,13 +621,13 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
     // first window's barrier orders these stores before any read)
     for (int q = threadIdx.y * 32 + threadIdx.x; q < (S::NX + 1) * 32; q += NT)
         b.EB[(q / 32) * XS + q % 32] = 0.0f;
+    const long long t0 = tw.prof ? clock64() : 0;
     long long w = tw.start[blockIdx.x];
     const long long wend = tw.start[blockIdx.x + 1];
     while (w < wend) {
         const int window = int(w / a.nz), kb = int(w % a.nz);
         const long long left = wend - w;
         const int ke = left < (long long)(a.nz - kb) ? kb + int(left) : a.nz;
-        const long long t0 = tw.prof ? clock64() : 0;
         // a window off the box faces and the CPML shells runs without the
         // checks of walls, psi and columns past the box (G = 0; the x and y
         // checks are separate flags, but instantiating them apart measured no
@@ -641,11 +641,9 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
         else tb2_window<RY, 0>(a, tt, tw, window, kb, ke, b);
         w += ke - kb;
         __syncthreads();   // the exchange buffers are reused by the next window
-        if (tw.prof && threadIdx.x == 0 && threadIdx.y == 0) {
-            atomicAdd(tw.prof + 2 * window, static_cast<unsigned long long>(clock64() - t0));
-            atomicAdd(tw.prof + 2 * window + 1, static_cast<unsigned long long>(ke - kb + 4));
-        }
     }
+    if (tw.prof && threadIdx.x == 0 && threadIdx.y == 0)
+        tw.prof[blockIdx.x] += static_cast<unsigned long long>(clock64() - t0);
 }
 
 // Steps n and n+1 with their source time factors as a parameter.
