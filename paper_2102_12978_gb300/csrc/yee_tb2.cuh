@@ -177,6 +177,7 @@ __device__ __forceinline__ float psi_rn(float b, float psi, float aa, float d) {
 struct Tb2Col {
     int i, j, lane, row, tid;
     bool indom, own, fown, sx, sy, ant;   // ant: the window holds antenna columns
+    bool anth, ante;                      // warp-uniform: the row holds antenna H / E points
     uint8_t mk;
     int col, colx, coly;
     float chx, chy, cex, cey, bhx, ahx, bex, aex, bhy, ahy, bey, aey;
@@ -204,7 +205,7 @@ struct Tb2Bufs {
     float* HB;       // [Hx, Hz, Hy^{n-1/2} + Hy^{n+1/2}][XS]
     float* E1B;      // [2][Ez, Ex][XS]: E^{n+1}
     float* H1B;      // [Hx, Hz, Hy^{n+1/2} + Hy^{n+3/2}][XS]
-    float* SC;       // [6][re, im][NT]: antenna coefficients
+    float2* SC;      // [6][NT]: antenna coefficients (zero where a column has no point of the component)
 };
 
 __device__ __forceinline__ int next_plane(int k, int nz) { return k + 1 == nz ? 0 : k + 1; }
@@ -225,12 +226,12 @@ __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col
     cpa4(r + 3 * NT, a.hin[0] + g, (!GX && !GY) || c.indom);
     cpa4(r + 4 * NT, a.hin[1] + g, (!GX && !GY) || c.indom);
     cpa4(r + 5 * NT, a.hin[2] + g, (!GX && !GY) || c.indom);
-    if (GX && c.sx) {
+    if (GX) {   // every lane: zeros where the column is not in an x shell
         const int q = k * a.ny * (2 * a.npml) + c.colx;
-        cpa4(r + 6 * NT, a.phx_in[0] + q, true);    // Hyx
-        cpa4(r + 7 * NT, a.phx_in[1] + q, true);    // Hzx
-        cpa4(r + 10 * NT, a.pex[0] + q, true);      // Eyx
-        cpa4(r + 11 * NT, a.pex[1] + q, true);      // Ezx
+        cpa4(r + 6 * NT, a.phx_in[0] + q, c.sx);    // Hyx
+        cpa4(r + 7 * NT, a.phx_in[1] + q, c.sx);    // Hzx
+        cpa4(r + 10 * NT, a.pex[0] + q, c.sx);      // Eyx
+        cpa4(r + 11 * NT, a.pex[1] + q, c.sx);      // Ezx
     }
     if (GY && c.sy) {
         const int q = k * (2 * a.npml) * a.pitch + c.coly;
@@ -245,12 +246,15 @@ __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col
     cpa_commit();
 }
 
-// Soft-source increment Re{coef_c u} of component comp (coefficients staged in SC).
+// Soft-source increment Re{coef_c u} of component comp (coefficients staged in
+// SC; zero, and the increment a signed zero, where the column has no point of
+// the component).
 template <int RY>
 __device__ __forceinline__ float tb2_src(const Tb2Bufs<RY>& b, const Tb2Col& c, int comp, Cpx<float> u)
 {
     constexpr int NT = Tb2Smem<RY>::NT;
-    return fma_rn(b.SC[(2 * comp) * NT + c.tid], u.x, -mul_rn(b.SC[(2 * comp + 1) * NT + c.tid], u.y));
+    const float2 v = b.SC[comp * NT + c.tid];
+    return fma_rn(v.x, u.x, -mul_rn(v.y, u.y));
 }
 
 // One plane p of the wavefront: u = (p - P0) mod 4 is its ring slot, and
@@ -309,7 +313,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         hx = ox - c.chy * dEz_y + cz * dEy_z;
         hy = oy - cz * dEx_z + c.chx * dEz_x;
         hz = oz - c.chx * dEy_x + c.chy * dEx_y;
-        if (GX && c.sx) {
+        if (GX) {   // every lane (zero coefficients and psi off the x shells)
             const float p0 = psi_rn(c.bhx, rq[6 * NT], c.ahx, dEz_x);   // Hyx
             const float p1 = psi_rn(c.bhx, rq[7 * NT], c.ahx, dEy_x);   // Hzx
             hy += p0;
@@ -323,11 +327,11 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
             hz += p1;
             rq[8 * NT] = p0; rq[9 * NT] = p1;
         }
-        if (c.mk & 0x38) {
+        if (c.anth) {   // the whole row: zero terms where a column has no point
             const Cpx<float> u = cmul(s.zq, tt.th0);
-            if (c.mk & 0x08) hx += tb2_src(b, c, 3, u);
-            if (c.mk & 0x10) hy += tb2_src(b, c, 4, u);
-            if (c.mk & 0x20) hz += tb2_src(b, c, 5, u);
+            hx += tb2_src(b, c, 3, u);
+            hy += tb2_src(b, c, 4, u);
+            hz += tb2_src(b, c, 5, u);
         }
         // centre sums of step n for plane q
         nPEx = ex + exj;
@@ -358,7 +362,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         nex = ex + c.cey * dHz_y - cz * dHy_z;
         ney = ey + cz * dHx_z - c.cex * dHz_x;
         nez = ez + c.cex * dHy_x - c.cey * dHx_y;
-        if (GX && c.sx) {
+        if (GX) {   // every lane (zero coefficients and psi off the x shells)
             const float p0 = psi_rn(c.bex, rq[10 * NT], c.aex, dHz_x);   // Eyx
             const float p1 = psi_rn(c.bex, rq[11 * NT], c.aex, dHy_x);   // Ezx
             rq[10 * NT] = p0; rq[11 * NT] = p1;
@@ -372,11 +376,11 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
             nex += p0;
             nez -= p1;
         }
-        if (c.mk & 0x07) {
+        if (c.ante) {   // the whole row: zero terms where a column has no point
             const Cpx<float> u = cmul(s.zq, tt.te0);
-            if (c.mk & 0x01) nex += tb2_src(b, c, 0, u);
-            if (c.mk & 0x02) ney += tb2_src(b, c, 1, u);
-            if (c.mk & 0x04) nez += tb2_src(b, c, 2, u);
+            nex += tb2_src(b, c, 0, u);
+            ney += tb2_src(b, c, 1, u);
+            nez += tb2_src(b, c, 2, u);
         }
         if (GY && c.j == 0) { nex = 0.0f; nez = 0.0f; }   // PEC: tangential E
         if (GX && c.i == 0) { ney = 0.0f; nez = 0.0f; }
@@ -400,12 +404,12 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         h2x = s.h1p[0] - c.chy * dEz_y + cz * dEy_z;
         h2y = s.h1p[1] - cz * dEx_z + c.chx * dEz_x;
         h2z = s.h1p[2] - c.chx * dEy_x + c.chy * dEx_y;
-        if (GX && c.sx) {
+        if (GX) {   // every lane (zero coefficients and psi off the x shells)
             const float p0 = psi_rn(c.bhx, rr[6 * NT], c.ahx, dEz_x);
             const float p1 = psi_rn(c.bhx, rr[7 * NT], c.ahx, dEy_x);
             h2y += p0;
             h2z -= p1;
-            if (valid && c.own) {
+            if (valid && c.own && c.sx) {
                 const int qo = s.kr * a.ny * (2 * a.npml) + c.colx;
                 const uint64_t pol = tb2_store_policy();
                 st_keep(a.phx_out[0] + qo, p0, pol); st_keep(a.phx_out[1] + qo, p1, pol);
@@ -422,11 +426,11 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
                 st_keep(a.phy_out[0] + qo, p0, pol); st_keep(a.phy_out[1] + qo, p1, pol);
             }
         }
-        if (c.mk & 0x38) {
+        if (c.anth) {   // the whole row: zero terms where a column has no point
             const Cpx<float> u = cmul(s.zr, tt.th1);
-            if (c.mk & 0x08) h2x += tb2_src(b, c, 3, u);
-            if (c.mk & 0x10) h2y += tb2_src(b, c, 4, u);
-            if (c.mk & 0x20) h2z += tb2_src(b, c, 5, u);
+            h2x += tb2_src(b, c, 3, u);
+            h2y += tb2_src(b, c, 4, u);
+            h2z += tb2_src(b, c, 5, u);
         }
         // centre sums of step n+1 for plane r
         mPEx = s.e1p[0] + fexj;
@@ -456,12 +460,12 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
         float fx = s.e1p[0] + c.cey * dHz_y - cz * dHy_z;
         float fy = s.e1p[1] + cz * dHx_z - c.cex * dHz_x;
         float fz = s.e1p[2] + c.cex * dHy_x - c.cey * dHx_y;
-        if (GX && c.sx) {
+        if (GX) {   // every lane (zero coefficients and psi off the x shells)
             const float p0 = psi_rn(c.bex, rr[10 * NT], c.aex, dHz_x);
             const float p1 = psi_rn(c.bex, rr[11 * NT], c.aex, dHy_x);
             fy -= p0;
             fz += p1;
-            if (valid && c.own) {
+            if (valid && c.own && c.sx) {
                 const int qo = s.kr * a.ny * (2 * a.npml) + c.colx;
                 const uint64_t pol = tb2_store_policy();
                 st_keep(a.pex_out[0] + qo, p0, pol); st_keep(a.pex_out[1] + qo, p1, pol);
@@ -478,11 +482,11 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
                 st_keep(a.pey_out[0] + qo, p0, pol); st_keep(a.pey_out[1] + qo, p1, pol);
             }
         }
-        if (c.mk & 0x07) {
+        if (c.ante) {   // the whole row: zero terms where a column has no point
             const Cpx<float> u = cmul(s.zr, tt.te1);
-            if (c.mk & 0x01) fx += tb2_src(b, c, 0, u);
-            if (c.mk & 0x02) fy += tb2_src(b, c, 1, u);
-            if (c.mk & 0x04) fz += tb2_src(b, c, 2, u);
+            fx += tb2_src(b, c, 0, u);
+            fy += tb2_src(b, c, 1, u);
+            fz += tb2_src(b, c, 2, u);
         }
         if (GY && c.j == 0) { fx = 0.0f; fz = 0.0f; }
         if (GX && c.i == 0) { fy = 0.0f; fz = 0.0f; }
@@ -560,15 +564,16 @@ __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Ti
     c.bhy = c.sy ? a.bhy[jj] : 0.0f; c.ahy = c.sy ? a.ahy[jj] : 0.0f;
     c.bey = c.sy ? a.bey[jj] : 0.0f; c.aey = c.sy ? a.aey[jj] : 0.0f;
     c.mk = (c.indom && a.smask) ? (a.smask[c.j * nx + c.i] & 0x3f) : uint8_t(0);
-    if (c.mk) {
+    c.ant = __syncthreads_or(c.mk != 0) != 0;
+    c.anth = __any_sync(0xffffffffu, (c.mk & 0x38) != 0);
+    c.ante = __any_sync(0xffffffffu, (c.mk & 0x07) != 0);
+    if (c.ant) {   // every column of the window, zeros where it has no point of a component
         const Cpx<float>* coef = static_cast<const Cpx<float>*>(a.scoefr);
         for (int q = 0; q < 6; ++q) {
             const Cpx<float> v = (c.mk >> q) & 1 ? coef[q * nx * ny + c.j * nx + c.i] : Cpx<float>{0.0f, 0.0f};
-            b.SC[(2 * q) * NT + c.tid] = v.x;
-            b.SC[(2 * q + 1) * NT + c.tid] = v.y;
+            b.SC[q * NT + c.tid] = make_float2(v.x, v.y);
         }
     }
-    c.ant = __syncthreads_or(c.mk != 0) != 0;
 
     const float dt16 = float(a.dt16);
     const int P0 = kb - 2, P1 = ke + 1;   // planes streamed: kb-2 .. ke+1
@@ -616,7 +621,7 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
     b.HB = b.EB + 4 * XS;
     b.E1B = b.HB + 3 * XS;
     b.H1B = b.E1B + 4 * XS;
-    b.SC = b.H1B + 3 * XS + 32;
+    b.SC = reinterpret_cast<float2*>(b.H1B + 3 * XS + 32);
     // the NX + 1 zero rows of the exchange arrays (never written again; the
     // first window's barrier orders these stores before any read)
     for (int q = threadIdx.y * 32 + threadIdx.x; q < (S::NX + 1) * 32; q += NT)
