@@ -248,7 +248,9 @@ int64_t fdtd_antenna_points(const fdtd_grid* g, int component);
  *   6  one cell-parallel pass, the neighbouring H recomputed per cell
  *      (needs nz <= 65535, else EINVAL);
  *   7  two steps per launch (temporal blocking; FP32 grids, ty 8 or 16,
- *      else EINVAL; lz unused): windows of 32 x ty columns march along z,
+ *      else EINVAL; lz 2 interleaves the window rows in the CTAs' work so
+ *      that x-neighbouring windows march side by side, any other lz takes
+ *      the windows row by row): windows of 32 x ty columns march along z,
  *      recomputing two rings of halo columns, so that fields, psi and the
  *      fluence cross HBM once per two steps.  An odd step count ends with
  *      one step of variant 5.  The CTAs' shares of the work are balanced on
@@ -269,17 +271,18 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
  * cost; a window also costs three planes at its start (the two-step
  * wavefront refills there).  Weights in [0, 16] (else EINVAL); defaults 0.25
  * and 0.2.  fdtd_autotune times a few pairs, then refines the fastest pair's
- * ranges on measured times (fdtd_measure_balance) and times those; it keeps
- * the fastest.  While refined ranges are in use, fdtd_get_balance returns -1
+ * ranges on measured times (fdtd_measure_balance), with the windows row by
+ * row and interleaved (lz 1 and 2), and times those; it keeps the fastest.  While refined ranges are in use, fdtd_get_balance returns -1
  * for both weights; fdtd_set_balance returns to the weights.  The results do
  * not depend on the balance, only the time does. */
 fdtd_status fdtd_set_balance(fdtd_grid* g, float w_shell, float w_antenna);
 fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenna);
 /* Refine the CTAs' work ranges of the grid's variant-7 tile on measured
- * times (the paper has no counterpart): in three rounds, two launches record
- * the SM cycles every CTA takes, and the ranges' boundaries move so that
- * each CTA's share of the measured time becomes equal.  The twelve steps run
- * from a copy of the state and are undone (the state is saved to
+ * times (the paper has no counterpart): in four rounds, three launches record
+ * the SM cycles every CTA takes, and the ranges' boundaries move toward equal
+ * shares of the measured time (all the way in the first round, three
+ * quarters of the way after it).  The 24 steps run from a copy of the state
+ * and are undone (the state is saved to
  * `scratch_state`, fdtd_state_bytes bytes of device memory the caller owns,
  * and restored).  The refined ranges are used from then on (fdtd_autotune
  * does the same for its fastest weights).  EINVAL unless the tile is variant

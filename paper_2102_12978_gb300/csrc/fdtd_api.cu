@@ -451,6 +451,7 @@ fdtd_status fdtd_create_grid(const fdtd_grid_desc* d, void* arena, size_t arena_
     g->tb2_ref_ry = 0;
     g->tb2_ref_slots = 0;
     g->tb2_ref_src = -1;
+    g->tb2_ref_order = 0;
     g->tb2_ref_gen = 0;
     g->tb2_profile = false;
     g->ant_cols[0] = g->ant_cols[1] = 0;
@@ -739,10 +740,11 @@ static cudaError_t run_steps(fdtd_grid* g, int nsteps, const TileConfig& tc)
 
 // Variant 7 in configuration tc, measured and refined kRefineRounds times:
 // kMeasureLaunches launches record every CTA's SM cycles, and tb2_refine
-// moves the ranges' boundaries so that the CTAs' times become equal.
-// Advances the grid by 2 kMeasureLaunches kRefineRounds steps.
-constexpr int kMeasureLaunches = 2;
-constexpr int kRefineRounds = 3;
+// moves the ranges' boundaries toward equal CTA times (all the way in the
+// first round, three quarters of the way after it).  Advances the grid by
+// 2 kMeasureLaunches kRefineRounds steps.
+constexpr int kMeasureLaunches = 3;
+constexpr int kRefineRounds = 4;
 static cudaError_t tb2_measure(fdtd_grid* g, const TileConfig& tc)
 {
     const int slots = tb2_slots(g, tc.ty);
@@ -760,7 +762,7 @@ static cudaError_t tb2_measure(fdtd_grid* g, const TileConfig& tc)
         err = cudaMemcpyAsync(cycles.data(), prof, size_t(slots) * 8, cudaMemcpyDeviceToHost, g->stream);
         if (err == cudaSuccess) err = cudaStreamSynchronize(g->stream);
         if (err != cudaSuccess) return err;
-        tb2_refine(g, t.ty, slots, cycles.data());
+        tb2_refine(g, t.ty, slots, cycles.data(), round == 0 ? 1.0 : 0.75);
         t.measured = true;   // the next round measures the refined ranges
     }
     return cudaSuccess;
@@ -1116,7 +1118,7 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
         for (int lz : lzs) {
             if (cd.variant >= 5 && lz != lzs[0]) continue;   // one cell per thread: no z segments
             TileConfig tc; tc.variant = cd.variant; tc.tx = 32; tc.ty = cd.ty; tc.lz = lz;
-            if (cd.variant == 7) { tc.w_shell = cd.w_shell; tc.w_ant = cd.w_ant; }
+            if (cd.variant == 7) { tc.w_shell = cd.w_shell; tc.w_ant = cd.w_ant; tc.lz = 1; }
             err = run_steps(g, 2, tc);   // warm-up
             if (err != cudaSuccess) break;
             cudaEventRecord(e0, g->stream);
@@ -1128,12 +1130,15 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) { best = ms; best_tc = tc; }
         }
-    // variant 7: measure each window's cost in launches of the fastest
-    // configuration, then time the ranges balanced on the measured costs
-    if (err == cudaSuccess && best_tc.variant == 7) do {
-        err = tb2_measure(g, best_tc);
+    // variant 7: the fastest weights' ranges refined on measured CTA times,
+    // with the windows row by row and with the rows interleaved; keep the
+    // fastest
+    const TileConfig weights_tc = best_tc;
+    for (int order = 1; order <= 2 && err == cudaSuccess && weights_tc.variant == 7; ++order) {
+        TileConfig tc = weights_tc;
+        tc.lz = order;
+        err = tb2_measure(g, tc);
         if (err != cudaSuccess) break;
-        TileConfig tc = best_tc;
         tc.measured = true;
         err = run_steps(g, 2, tc);   // warm-up
         if (err != cudaSuccess) break;
@@ -1145,7 +1150,7 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) { best = ms; best_tc = tc; }
-    } while (false);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g->fault = 0;

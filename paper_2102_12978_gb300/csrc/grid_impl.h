@@ -30,7 +30,7 @@ struct Layout {
     size_t smask = 0, scoef = 0, scoef32 = 0, zph = 0, zph32 = 0;
     size_t scoef_unw = 0, wamp = 0, wphase = 0;   // unweighted coefficients and the weights
     size_t flu_out = 0;    // dense FP64 export of the fluence
-    size_t tb2prof = 0;    // variant 7: per-window cycle and iteration counters of a measuring launch
+    size_t tb2prof = 0;    // variant 7: per-CTA cycle counters of a measuring launch
     size_t alist = 0;      // antenna columns (int): those with H points, then those with E points
     size_t err = 0;        // device error word (int)
     size_t total = 0;
@@ -107,13 +107,14 @@ struct fdtd_grid {
                                 // column on the i = 0 or j = 0 wall, where the E pass zeroes after it)
     std::vector<long long> tb2_start;   // variant 7: cached CTA work ranges
     struct {
-        int ry, slots, src_gen, cost_gen;
+        int ry, slots, src_gen, cost_gen, order;
         float w_shell, w_ant;
         bool measured;
     } tb2_key;                          // what they were computed for (ry 0: nothing cached)
     std::vector<long long> tb2_refined; // variant 7: CTA ranges refined from measured per-CTA times
     int tb2_ref_ry, tb2_ref_slots;      // the window height and CTA count they are for (ry 0: none)
     int tb2_ref_src;                    // the antenna generation they were measured with
+    int tb2_ref_order;                  // the window order they were refined for
     int tb2_ref_gen;                    // bumped whenever tb2_refined changes
     bool tb2_profile;                   // the next variant-7 launches record per-CTA cycles
 };
@@ -141,10 +142,11 @@ cudaError_t launch_tb2(const fdtd_grid* g, int cur, long long n, const TileConfi
 // Windows of variant 7 with 32 x ry columns on grid d: t along x, u along y.
 void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u);
 // Moves the boundaries of the cached ranges (windows of 32 x ry columns,
-// `slots` CTAs) so that the CTAs' times, from the SM cycles each took in the
-// measured launches (cycles[c]) spread evenly over its items, become equal;
-// stored on the grid for the plans of tc.measured.
-void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles);
+// `slots` CTAs) `step` (in (0, 1]) of the way to where the CTAs' times, from
+// the SM cycles each took in the measured launches (cycles[c]) spread evenly
+// over its items, become equal; stored on the grid for the plans of
+// tc.measured.
+void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles, double step);
 // CTAs of one variant-7 launch on grid g with windows of 32 x ry columns.
 int tb2_slots(const fdtd_grid* g, int ry);
 // The same two steps with their time factors from a device table of

@@ -18,7 +18,7 @@ void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u)
     *u = d.ny <= ry ? 1 : (d.ny - ry + (ry - 4) - 1) / (ry - 4) + 1;
 }
 
-void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles)
+void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles, double step)
 {
     // the ranges the measured launches ran: the cached plan of this shape
     if (g->tb2_key.ry != ry || g->tb2_key.slots != slots || g->tb2_start.size() != size_t(slots) + 1) return;
@@ -38,14 +38,17 @@ void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycle
             if (s[size_t(c) + 1] > s[size_t(c)]) cum += double(cycles[c]);
             ++c;
         }
-        long long x = s.back();
+        double x = double(s.back());
         if (c < slots) {
             const double frac = (target - cum) / double(cycles[c]);
-            x = s[size_t(c)] + (long long)std::llround(frac * double(s[size_t(c) + 1] - s[size_t(c)]));
+            x = double(s[size_t(c)]) + frac * double(s[size_t(c) + 1] - s[size_t(c)]);
         }
-        ns[size_t(k)] = std::max(ns[size_t(k) - 1], std::min(x, s.back()));
+        // move the boundary `step` of the way (damping against oscillation)
+        const long long y = std::llround(double(s[size_t(k)]) + step * (x - double(s[size_t(k)])));
+        ns[size_t(k)] = std::max(ns[size_t(k) - 1], std::min(y, s.back()));
     }
     g->tb2_refined = ns;
+    g->tb2_ref_order = g->tb2_key.order;
     g->tb2_ref_ry = ry;
     g->tb2_ref_slots = slots;
     g->tb2_ref_src = g->src_gen;
@@ -61,15 +64,46 @@ void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycle
 // the CTAs' measured times were equal.  Cached on the grid until the antenna,
 // the weights or the launch shape change.
 constexpr double kRestart = 3.0;
+// Rows interleaved by D (see Tb2Plan) for window order `mode` 2, row by row
+// (D = 1) otherwise: D in [1, 16] such that D windows of planes come closest
+// to a whole number of CTA shares.
+static int tb2_order_d(int T, int U, int nz, int slots, int mode)
+{
+    if (mode != 2) return 1;
+    const double share = double(T) * U * nz / slots;
+    int best = 1;
+    double bd = 1e30;
+    for (int D = 1; D <= 16 && D <= U; ++D) {
+        const double r = std::fmod(double(nz) * D, share), dist = std::min(r, share - r);
+        if (dist < bd - 1e-9) { bd = dist; best = D; }
+    }
+    return best;
+}
+
+// Window at flattened position pos (the host copy of tb2_window_at).
+static int tb2_window_host(int T, int U, int D, int pos)
+{
+    if (D <= 1) return pos;
+    const int grp = pos / (T * D);
+    const int rows = std::min(D, U - grp * D);
+    const int r = pos - grp * T * D;
+    const int wx = r / rows, l = r - wx * rows;
+    return (grp * D + l) * T + wx;
+}
+
 static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2Plan& P)
 {
     const fdtd_grid_desc& d = g->desc;
     tb2_windows(d, RY, &P.T, &P.U);
     P.prof = nullptr;
+    const int order = tc.lz == 2 ? 2 : 1;
+    P.D = tb2_order_d(P.T, P.U, d.nz, slots, order);
     const bool meas = tc.measured && g->tb2_ref_ry == RY && g->tb2_ref_slots == slots &&
-                      g->tb2_ref_src == g->src_gen && g->tb2_refined.size() == size_t(slots) + 1;
+                      g->tb2_ref_src == g->src_gen && g->tb2_refined.size() == size_t(slots) + 1 &&
+                      g->tb2_ref_order == order;
     auto& key = g->tb2_key;
     if (key.ry != RY || key.slots != slots || key.src_gen != g->src_gen || key.measured != meas ||
+        key.order != order ||
         (meas ? key.cost_gen != g->tb2_ref_gen : (key.w_shell != tc.w_shell || key.w_ant != tc.w_ant))) {
         if (meas) {
             g->tb2_start = g->tb2_refined;
@@ -88,6 +122,11 @@ static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2P
                             for (int i = i0; i < i1 && !ant; ++i) ant = g->hmask[size_t(j) * nx + i] != 0;
                     cost[size_t(wy) * P.T + wx] = 1.0 + (shell ? tc.w_shell : 0.0) + (ant ? tc.w_ant : 0.0);
                 }
+            if (P.D > 1) {   // costs by position
+                std::vector<double> byp(cost.size());
+                for (int m = 0; m < nw; ++m) byp[size_t(m)] = cost[size_t(tb2_window_host(P.T, P.U, P.D, m))];
+                cost.swap(byp);
+            }
             double total = 0.0;
             for (double c : cost) total += c * (nz + kRestart);
             const double share = total / slots;
@@ -110,7 +149,7 @@ static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2P
         }
         key.ry = RY; key.slots = slots; key.src_gen = g->src_gen;
         key.w_shell = tc.w_shell; key.w_ant = tc.w_ant;
-        key.measured = meas; key.cost_gen = g->tb2_ref_gen;
+        key.measured = meas; key.cost_gen = g->tb2_ref_gen; key.order = order;
     }
     for (int c = 0; c <= slots; ++c) P.start[c] = g->tb2_start[size_t(c)];
 }

@@ -79,11 +79,28 @@ struct Tb2Times {
 // added to): the host moves the ranges' boundaries so that every CTA takes
 // the same time.
 constexpr int kTb2MaxCtas = 512;
+// D > 1: the windows of D window rows are interleaved in the flattened
+// order (position item / nz): group g of rows gD .. gD + D - 1 (fewer in the
+// last group) takes the positions from g T D on, window (wx, gD + l) at
+// position g T D + wx * (rows in the group) + l, so that x-neighbours lie D
+// positions apart.  The host picks D so that D windows of planes are close to
+// a whole number of CTA shares: x-neighbours then start at nearly the same
+// plane and march side by side.  D = 1: row by row.
 struct Tb2Plan {
-    int T, U;
+    int T, U, D;
     unsigned long long* prof;
     long long start[kTb2MaxCtas + 1];
 };
+
+__device__ __forceinline__ int tb2_window_at(const Tb2Plan& tw, int pos)
+{
+    if (tw.D <= 1) return pos;
+    const int grp = pos / (tw.T * tw.D);
+    const int rows = tw.U - grp * tw.D < tw.D ? tw.U - grp * tw.D : tw.D;
+    const int r = pos - grp * tw.T * tw.D;
+    const int wx = r / rows, l = r - wx * rows;
+    return (grp * tw.D + l) * tw.T + wx;
+}
 
 // Columns per window along x, and the stride between windows.
 constexpr int kTb2Wx = 32;
@@ -499,15 +516,14 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     }
     // fluence of plane p-3: the step-n term from the last plane, then step n+1
     float mhby = 0.0f;
-    {
+    {   // every lane computes it (no divergent branch); the fluence cells store it
         mhby = gsy + yp(b.H1B + 2 * XS);
-        if (valid && c.fown) {
-            const float t1 = tb2_flux(s.gPEx + mPEx, s.gPEy + mPEy, s.gcz, s.ghbx, s.ghby, s.gHsz + mHsz, dt16);
-            float2 acc = b.fring[SP * NT + tid];
-            acc = FluAcc<float>::add(acc, s.tn);
-            acc = FluAcc<float>::add(acc, t1);
+        const float t1 = tb2_flux(s.gPEx + mPEx, s.gPEy + mPEy, s.gcz, s.ghbx, s.ghby, s.gHsz + mHsz, dt16);
+        float2 acc = b.fring[SP * NT + tid];   // zero-filled off the fluence cells
+        acc = FluAcc<float>::add(acc, s.tn);
+        acc = FluAcc<float>::add(acc, t1);
+        if (valid && c.fown)
             st_keep(static_cast<float2*>(a.fluence) + s.k3 * (a.pitch * a.ny) + c.col, acc, tb2_store_policy());
-        }
     }
 
     // ---- carry to the next plane
@@ -630,7 +646,7 @@ __device__ __forceinline__ void tb2_run(const StepArgs<float>& a, const Tb2Times
     long long w = tw.start[blockIdx.x];
     const long long wend = tw.start[blockIdx.x + 1];
     while (w < wend) {
-        const int window = int(w / a.nz), kb = int(w % a.nz);
+        const int window = tb2_window_at(tw, int(w / a.nz)), kb = int(w % a.nz);
         const long long left = wend - w;
         const int ke = left < (long long)(a.nz - kb) ? kb + int(left) : a.nz;
         // a window off the box faces and the CPML shells runs without the

@@ -199,3 +199,23 @@ def test_measured_balance_needs_variant_7():
     with pytest.raises(fdtd.FDTDError) as e:
         g.measure_balance()
     assert e.value.status == fdtd.FDTD_EINVAL
+
+
+@pytest.mark.parametrize("ty", [16, 8])
+@pytest.mark.parametrize("shape", [(100, 90, 9), (200, 150, 12), (61, 75, 3)])
+def test_interleaved_window_order_changes_no_result(shape, ty):
+    """lz = 2 interleaves the window rows in the CTAs' work (x-neighbours
+    march side by side); which CTA computes which window changes, the
+    results do not, with the weight-balanced and the refined ranges."""
+    nx, ny, nz = shape
+    w = W.small(nx=nx, ny=ny, nz=nz, npml=6, r_center=min(nx, ny) / 2 - 8.5, steps=14, ramp=1.0)
+    a = gpu_grid(w, "f32", tile=(7, ty, 1))
+    b = gpu_grid(w, "f32", tile=(7, ty, 2))
+    c = gpu_grid(w, "f32", tile=(7, ty, 2))
+    c.measure_balance()
+    for g in (a, b, c):
+        g.step(w.steps)
+    for g in (b, c):
+        for comp in range(6):
+            assert torch.equal(a.field(comp), g.field(comp))
+        assert torch.equal(a.fluence(), g.fluence())
