@@ -392,7 +392,7 @@ def run_gpu(args):
                    "fluence": "fp64", "source_phase": "fp64",
                    "l2_flush": "inputs larger than L2 (fields + fluence = %.0f MB/step)"
                                % (ab32 * cells / 1e6),
-                   "tile_f32": list(tile32), "balance_f32": ("measured per-window costs" if balance32[0] < 0
+                   "tile_f32": list(tile32), "balance_f32": ("ranges refined on measured per-CTA times" if balance32[0] < 0
                                                   else [round(x, 3) for x in balance32]),
                    "tile_f64": list(tile64), "parallelism": f"replicas{ws}",
                    "timing": f"median of {reps32} repeats of the {args.steps}-step block (>= {MIN_TIMED_S:g} s "
@@ -450,8 +450,8 @@ def rel_l2_t(torch, x, y) -> float:
 
 def apply_balance(g, balance):
     """The variant-7 balance the autotuner chose: weights, or (-1, -1) for
-    ranges balanced on measured per-window costs (measured again on g; the
-    grid's antenna must be set)."""
+    ranges refined on measured per-CTA times (refined again on g; the grid's
+    antenna must be set)."""
     if balance[0] < 0:
         g.measure_balance()
     else:
