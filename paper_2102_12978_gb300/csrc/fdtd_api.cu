@@ -1094,7 +1094,8 @@ fdtd_status fdtd_autotune(fdtd_grid* g, int steps, void* scratch_state)
     if (g->desc.nz > 65535) cands.erase(cands.begin(), cands.begin() + 3);   // variant 6 takes nz <= 65535
     if (g->desc.precision == FDTD_F32)   // variant 7 with its work-split weights (shell, antenna)
         cands.insert(cands.begin(), {{7, 16, 0.0f, 0.0f}, {7, 16, 0.15f, 0.1f}, {7, 16, 0.3f, 0.2f},
-                                     {7, 16, 0.45f, 0.3f}, {7, 16, 0.3f, 0.4f}, {7, 8, 0.3f, 0.2f}});
+                                     {7, 16, 0.45f, 0.3f}, {7, 16, 0.3f, 0.4f}, {7, 16, 0.6f, 0.4f},
+                                     {7, 8, 0.3f, 0.2f}});
     if (needs_cell_passes(g)) cands = {{5, 4}, {5, 8}, {5, 16}};
     const int nz = g->desc.nz;
     std::vector<int> lzs;
