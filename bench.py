@@ -399,8 +399,11 @@ def run_gpu(args):
                              f"of GPU time)"},
         "roofline": {"bound": "hbm", "achieved": round(step_achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(step_achieved / peak, 4), "traffic": traffic32,
+                     "traffic_gbs": (round(traffic32 / (step_ms * 1e-3) / 1e9, 1)
+                                     if traffic32 is not None else None),
                      "basis": "whole step: the method's bytes per cell-update (E, H, fluence, CPML psi in and "
-                              "out once) x cells / ms_per_step; traffic = DRAM bytes per step (ncu)",
+                              "out once) x cells / ms_per_step; traffic = DRAM bytes per step (ncu); "
+                              "traffic_gbs = traffic / ms_per_step",
                      "algorithmic_bytes_per_cell_update": ab32, "cell_updates_per_step": cells,
                      "peak_kind": peak_kind, "peak_nominal": NOMINAL_HBM_GBS,
                      "frac_nominal": round(step_achieved / NOMINAL_HBM_GBS, 4),
