@@ -46,14 +46,23 @@
 //     recompute race-free.
 //   * Every row of a window runs every stage, whether or not a column the
 //     window writes depends on it, so that the stage code has no branches
-//     on the row; windows off the x faces and x shells run code without the
-//     checks of the x walls, x psi and columns past the box in x, and the
-//     same for y (template flags GX, GY).
-//   * A CTA takes a contiguous range of the flattened (window, plane) work;
-//     the ranges have equal estimated cost (windows with CPML shell or antenna
-//     columns weigh more, with weights the autotuner picks by timing).  Where
-//     a range starts or crosses into the next window the wavefront restarts,
-//     which costs three planes of recompute.
+//     on the row; a row with antenna points adds the source terms on all its
+//     lanes (zero terms where a column has none), and the x-shell windows
+//     update the x psi on all lanes (zero coefficients off the shell).
+//     Windows off the box faces and the CPML shells run code without the
+//     checks of the walls, psi and columns past the box (template flags GX,
+//     GY).
+//   * A CTA takes a contiguous range of the flattened (window, plane) work:
+//     ranges of equal estimated cost (windows with CPML shell or antenna
+//     columns weigh more, with weights the autotuner picks by timing), or
+//     ranges the host refined until the CTAs' measured times were equal
+//     (the kernel records each CTA's SM cycles when asked).  The window rows
+//     may be interleaved in the flattened order, so that x-neighbouring
+//     windows march side by side (tb2_window_at).  Where a range starts or
+//     crosses into the next window the wavefront restarts, which costs three
+//     planes of recompute.
+//   * Outputs are stored with the L2 evict-last policy; every sum of two
+//     products is rounded explicitly (see below).
 // z-periodic grids only (the antenna boxes of Section 4); FP32 fields with the
 // Kahan FP32 fluence.
 #pragma once
