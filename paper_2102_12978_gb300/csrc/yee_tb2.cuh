@@ -23,10 +23,11 @@
 //     lane by warp shuffle, the +y / -y neighbours from per-plane shared
 //     exchange buffers (two CTA barriers per plane), the +z / -z neighbours
 //     from registers carried from plane to plane.
-//   * Each thread streams its own column: the E^n and H^{n-1/2} values, the
-//     CPML psi of shell columns and the fluence accumulator of plane p + 2
-//     are copied by cp.async (zero-filled past the box) into a per-thread
-//     ring of four plane slots in shared memory; a thread waits only for its
+//   * Each thread streams its own column: the E^n and H^{n-1/2} values and
+//     the fluence accumulator of plane p + 3 and the CPML psi of plane p + 2
+//     (shell columns) are copied by cp.async (zero-filled past the box) into
+//     a per-thread ring of four plane slots in shared memory (see
+//     tb2_issue); a thread waits only for its
 //     own copies, so the ring needs no barrier.  The psi of a plane are
 //     updated in place in its slot (n-1/2 -> n+1/2, n -> n+1) and read back
 //     by the second step's stages.  The plane loop is unrolled by two, so
@@ -119,7 +120,7 @@ constexpr int kTb2Sx = 28;
 template <int RY>
 struct Tb2Smem {
     static constexpr int NT = 32 * RY;   // threads (columns) per window
-    static constexpr int R = 4;          // ring slots per thread (copies run two planes ahead)
+    static constexpr int R = 4;          // ring slots per thread (see tb2_issue)
     static constexpr int NF = 14;        // ring floats per slot: E^n 3, H^{n-1/2} 3, psi 8
     // exchange arrays: a row of zeros before and after the window's RY rows
     // (the values of the rows beyond it), so that a y neighbour is one plain
@@ -150,7 +151,7 @@ __device__ __forceinline__ void cpa8(float2* dst, const float2* src, bool valid)
                  : "memory");
 }
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Every sum of two products below is written with explicit roundings
@@ -236,14 +237,22 @@ struct Tb2Bufs {
 
 __device__ __forceinline__ int next_plane(int k, int nz) { return k + 1 == nz ? 0 : k + 1; }
 
-// Copies of plane k (fluence plane kf) into ring slot s of this thread.
+// Copies of this thread's column, one cp.async group: E^n and H^{n-1/2} of
+// plane k and the fluence accumulator of plane kf into slot s, the psi of
+// plane kp into slot sp.  A plane's fields are first read at its own stage A
+// (E^n) and its psi one plane later (stage A of the next plane), so that at
+// the end of plane p the fields of p + 3 (fluence p) go into the slot the
+// fields of p - 1 have left and the psi of p + 2 into the slot the psi of
+// p - 2 have left: with four slots the fields are copied three planes ahead
+// of their first use, the psi two and a half.
 template <int RY, int G>
 __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col& c, const Tb2Bufs<RY>& b, int s,
-                                          int k, int kf)
+                                          int k, int kf, int sp, int kp)
 {
     using S = Tb2Smem<RY>;
     constexpr int NT = S::NT, NF = S::NF;
     float* r = b.ring + s * NF * NT + c.tid;
+    float* rs = b.ring + sp * NF * NT + c.tid;
     constexpr bool GX = G & 1, GY = G & 2;
     const int g = k * (a.pitch * a.ny) + c.col;
     cpa4(r + 0 * NT, a.ein[0] + g, (!GX && !GY) || c.indom);
@@ -253,18 +262,18 @@ __device__ __forceinline__ void tb2_issue(const StepArgs<float>& a, const Tb2Col
     cpa4(r + 4 * NT, a.hin[1] + g, (!GX && !GY) || c.indom);
     cpa4(r + 5 * NT, a.hin[2] + g, (!GX && !GY) || c.indom);
     if (GX) {   // every lane: zeros where the column is not in an x shell
-        const int q = k * a.ny * (2 * a.npml) + c.colx;
-        cpa4(r + 6 * NT, a.phx_in[0] + q, c.sx);    // Hyx
-        cpa4(r + 7 * NT, a.phx_in[1] + q, c.sx);    // Hzx
-        cpa4(r + 10 * NT, a.pex[0] + q, c.sx);      // Eyx
-        cpa4(r + 11 * NT, a.pex[1] + q, c.sx);      // Ezx
+        const int q = kp * a.ny * (2 * a.npml) + c.colx;
+        cpa4(rs + 6 * NT, a.phx_in[0] + q, c.sx);    // Hyx
+        cpa4(rs + 7 * NT, a.phx_in[1] + q, c.sx);    // Hzx
+        cpa4(rs + 10 * NT, a.pex[0] + q, c.sx);      // Eyx
+        cpa4(rs + 11 * NT, a.pex[1] + q, c.sx);      // Ezx
     }
     if (GY && c.sy) {
-        const int q = k * (2 * a.npml) * a.pitch + c.coly;
-        cpa4(r + 8 * NT, a.phy_in[0] + q, true);    // Hxy
-        cpa4(r + 9 * NT, a.phy_in[1] + q, true);    // Hzy
-        cpa4(r + 12 * NT, a.pey[0] + q, true);      // Exy
-        cpa4(r + 13 * NT, a.pey[1] + q, true);      // Ezy
+        const int q = kp * (2 * a.npml) * a.pitch + c.coly;
+        cpa4(rs + 8 * NT, a.phy_in[0] + q, true);    // Hxy
+        cpa4(rs + 9 * NT, a.phy_in[1] + q, true);    // Hzy
+        cpa4(rs + 12 * NT, a.pey[0] + q, true);      // Exy
+        cpa4(rs + 13 * NT, a.pey[1] + q, true);      // Ezy
     }
     const float2* F = static_cast<const float2*>(a.fluence);
     cpa8(b.fring + s * NT + c.tid, c.fown ? F + kf * (a.pitch * a.ny) + c.col : reinterpret_cast<const float2*>(a.ein[0]),
@@ -316,7 +325,7 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     auto put = [&](float* q, float v) { q[S::XO + tid] = v; };
     const float cz = a.cz;
 
-    cpa_wait1();
+    cpa_wait2();   // this plane's fields and the last plane's psi (planes p + 1, p + 2 may still run)
     float* rp = b.ring + SP * NF * NT + tid;
     float* rq = b.ring + SQ * NF * NT + tid;
     float* rr = b.ring + SR * NF * NT + tid;
@@ -544,9 +553,11 @@ __device__ __forceinline__ void tb2_plane(const StepArgs<float>& a, const Tb2Tim
     s.gPEx = mPEx; s.gPEy = mPEy; s.gcz = mcz; s.ghbx = mhbx; s.ghby = mhby; s.gHsz = mHsz;
     s.tn = tn_new;
     s.zr = s.zq; s.zq = zn;
-    // refill: plane p + 2 (fluence plane p - 1) into the slot of plane p - 2,
-    // whose last reader was this plane
-    if (issue_next) tb2_issue<RY, G>(a, c, b, SR, s.ki, s.kq);
+    // refill: the fields of plane p + 3 (fluence plane p) into the slot of
+    // plane p - 1, whose fields were last read at this plane's stage A, and
+    // the psi of plane p + 2 into the slot of plane p - 2, whose psi were last
+    // read at this plane's stage D
+    if (issue_next) tb2_issue<RY, G>(a, c, b, SQ, s.ki, s.kp, SR, next_plane(next_plane(s.kp, a.nz), a.nz));
     else cpa_commit();
     s.k3 = s.kr; s.kr = s.kq; s.kq = s.kp;
     s.kp = next_plane(s.kp, a.nz);
@@ -613,19 +624,22 @@ __device__ __forceinline__ void tb2_window(const StepArgs<float>& a, const Tb2Ti
     s.kq = s.kp == 0 ? nz - 1 : s.kp - 1;
     s.kr = s.kq == 0 ? nz - 1 : s.kq - 1;
     s.k3 = s.kr == 0 ? nz - 1 : s.kr - 1;
-    // prologue: planes P0, P0 + 1 into slots 0, 1 (their fluence planes P0 - 3, P0 - 2)
-    tb2_issue<RY, G>(a, c, b, 0, s.kp, s.k3);
-    const int k1 = next_plane(s.kp, nz);
-    tb2_issue<RY, G>(a, c, b, 1, k1, s.kr);
-    s.ki = next_plane(k1, nz);
+    // prologue: the fields of planes P0, P0 + 1, P0 + 2 into slots 0, 1, 2
+    // (their fluence planes P0 - 3, P0 - 2, P0 - 1), the psi of planes P0 - 1,
+    // P0, P0 + 1 into slots 3, 0, 1
+    const int k1 = next_plane(s.kp, nz), k2 = next_plane(k1, nz);
+    tb2_issue<RY, G>(a, c, b, 0, s.kp, s.k3, 3, s.kq);
+    tb2_issue<RY, G>(a, c, b, 1, k1, s.kr, 0, s.kp);
+    tb2_issue<RY, G>(a, c, b, 2, k2, s.kq, 1, k1);
+    s.ki = next_plane(k2, nz);
     // the ring's four slots: plane p uses slot u = (p - P0) mod 4
     int p = P0;
     int u = 0;
     for (;;) {
-        tb2_plane<RY, 0, G>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        tb2_plane<RY, 0, G>(a, tt, c, b, s, p >= kb + 2, p + 3 <= P1, dt16, u);
         u = (u + 1) & 3;
         if (++p > P1) break;
-        tb2_plane<RY, 1, G>(a, tt, c, b, s, p >= kb + 2, p + 2 <= P1, dt16, u);
+        tb2_plane<RY, 1, G>(a, tt, c, b, s, p >= kb + 2, p + 3 <= P1, dt16, u);
         u = (u + 1) & 3;
         if (++p > P1) break;
     }
