@@ -40,7 +40,7 @@ MAX_REPEATS = 100000
 # DRAM bytes (read + write) per launch of a kernel on the 256x256x128 FP32
 # workload, from one ncu capture of the kernel as it stands (summary and
 # command in profiles/); None where no capture of the current kernel exists.
-TRAFFIC: dict[str, float | None] = {"yee_h_cell": 307.85e6, "yee_e_cell": 545.41e6, "yee_tb2": 1003.02e6}
+TRAFFIC: dict[str, float | None] = {"yee_h_cell": 307.85e6, "yee_e_cell": 545.41e6, "yee_tb2": None}
 UNIT = "Gcell-updates/s"
 
 # FP64 instructions per cell of each FP64 pass (the cell pass and its antenna
