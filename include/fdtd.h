@@ -290,6 +290,24 @@ fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenn
  * single-grid steps only (a batch's two-step launches use the weights). */
 fdtd_status fdtd_measure_balance(fdtd_grid* g, void* scratch_state);
 
+/* Test hooks of tile variant 7's host logic (no device work; the paper has
+ * no counterpart).
+ * fdtd_debug_tb2_order writes to out[m] the window (wy * t + wx) that the
+ * CTAs take at flattened position m = 0 .. t*u - 1, for windows t along x by
+ * u along y, nz planes, `slots` CTAs and window order `order` (the lz of
+ * fdtd_set_tile: 2 interleaves the window rows, anything else takes them row
+ * by row).  out holds t*u ints.  Returns the interleave stride D (1: row by
+ * row), or -1 for an invalid argument.
+ * fdtd_debug_tb2_refine runs one refinement step of fdtd_measure_balance on
+ * host data: from the ranges' starts (slots + 1 items, starts[0] = 0, not
+ * decreasing, the last the item count) and each CTA's measured cycles, it
+ * writes the new starts to out (slots + 1 items), each boundary moved `step`
+ * (in (0, 1]) of the way to where every CTA's share of the total, spread
+ * evenly over the items it ran, is equal.  EINVAL for invalid arguments. */
+int fdtd_debug_tb2_order(int t, int u, int nz, int slots, int order, int* out);
+fdtd_status fdtd_debug_tb2_refine(int slots, const long long* starts, const unsigned long long* cycles, double step,
+                                  long long* out);
+
 /* Measurement (the paper has no counterpart): advance `nsteps` steps like
  * fdtd_step and time every kernel launch of a step with CUDA events recorded
  * on the grid's stream.  pass_ms[p] (host array of max_passes floats) gets

@@ -147,6 +147,10 @@ void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u);
 // over its items, become equal; stored on the grid for the plans of
 // tc.measured.
 void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles, double step);
+// The arithmetic of tb2_refine: new range starts from the starts s (slots + 1)
+// and the CTAs' cycles.
+std::vector<long long> tb2_refined_ranges(const std::vector<long long>& s, const unsigned long long* cycles,
+                                          double step);
 // CTAs of one variant-7 launch on grid g with windows of 32 x ry columns.
 int tb2_slots(const fdtd_grid* g, int ry);
 // The same two steps with their time factors from a device table of

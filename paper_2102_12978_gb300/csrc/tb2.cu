@@ -18,15 +18,14 @@ void tb2_windows(const fdtd_grid_desc& d, int ry, int* t, int* u)
     *u = d.ny <= ry ? 1 : (d.ny - ry + (ry - 4) - 1) / (ry - 4) + 1;
 }
 
-void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles, double step)
+std::vector<long long> tb2_refined_ranges(const std::vector<long long>& s, const unsigned long long* cycles,
+                                          double step)
 {
-    // the ranges the measured launches ran: the cached plan of this shape
-    if (g->tb2_key.ry != ry || g->tb2_key.slots != slots || g->tb2_start.size() != size_t(slots) + 1) return;
-    const std::vector<long long>& s = g->tb2_start;
+    const int slots = int(s.size()) - 1;
     double total = 0.0;
     for (int c = 0; c < slots; ++c)
         if (s[size_t(c) + 1] > s[size_t(c)]) total += double(cycles[c]);
-    if (!(total > 0.0)) return;
+    if (!(total > 0.0)) return s;
     // cost of the items [0, x): piecewise linear, CTA c's items at cycles_c / (its item count) each
     std::vector<long long> ns(size_t(slots) + 1, s.back());
     ns[0] = 0;
@@ -47,7 +46,14 @@ void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycle
         const long long y = std::llround(double(s[size_t(k)]) + step * (x - double(s[size_t(k)])));
         ns[size_t(k)] = std::max(ns[size_t(k) - 1], std::min(y, s.back()));
     }
-    g->tb2_refined = ns;
+    return ns;
+}
+
+void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycles, double step)
+{
+    // the ranges the measured launches ran: the cached plan of this shape
+    if (g->tb2_key.ry != ry || g->tb2_key.slots != slots || g->tb2_start.size() != size_t(slots) + 1) return;
+    g->tb2_refined = tb2_refined_ranges(g->tb2_start, cycles, step);
     g->tb2_ref_order = g->tb2_key.order;
     g->tb2_ref_ry = ry;
     g->tb2_ref_slots = slots;
@@ -55,15 +61,6 @@ void tb2_refine(fdtd_grid* g, int ry, int slots, const unsigned long long* cycle
     g->tb2_ref_gen += 1;
 }
 
-// CTA work ranges of variant 7 on grid g: windows of 32 x RY columns, `slots`
-// resident CTAs.  Each CTA gets a contiguous range of (window, plane) items.
-// The ranges either have equal estimated cost -- a window-plane costs 1,
-// plus w_shell if the window holds CPML shell columns, plus w_ant if it holds
-// antenna columns, and a window costs kRestart more planes at its start (the
-// wavefront refills) -- or (tc.measured) are the ones tb2_refine moved until
-// the CTAs' measured times were equal.  Cached on the grid until the antenna,
-// the weights or the launch shape change.
-constexpr double kRestart = 3.0;
 // Rows interleaved by D (see Tb2Plan) for window order `mode` 2, row by row
 // (D = 1) otherwise: D in [1, 16] such that D windows of planes come closest
 // to a whole number of CTA shares.
@@ -91,6 +88,15 @@ static int tb2_window_host(int T, int U, int D, int pos)
     return (grp * D + l) * T + wx;
 }
 
+// CTA work ranges of variant 7 on grid g: windows of 32 x RY columns, `slots`
+// resident CTAs.  Each CTA gets a contiguous range of (window, plane) items.
+// The ranges either have equal estimated cost -- a window-plane costs 1,
+// plus w_shell if the window holds CPML shell columns, plus w_ant if it holds
+// antenna columns, and a window costs kRestart more planes at its start (the
+// wavefront refills) -- or (tc.measured) are the ones tb2_refine moved until
+// the CTAs' measured times were equal.  Cached on the grid until the antenna,
+// the weights or the launch shape change.
+constexpr double kRestart = 3.0;
 static void tb2_plan(fdtd_grid* g, int RY, int slots, const TileConfig& tc, Tb2Plan& P)
 {
     const fdtd_grid_desc& d = g->desc;
@@ -235,3 +241,31 @@ cudaError_t launch_tb2_table(const fdtd_grid* cg, int cur, const StepTime<float>
 }
 
 }  // namespace fdtd
+
+using namespace fdtd;
+
+extern "C" {
+
+int fdtd_debug_tb2_order(int t, int u, int nz, int slots, int order, int* out)
+{
+    if (t < 1 || u < 1 || nz < 1 || slots < 1 || !out) return -1;
+    const int D = tb2_order_d(t, u, nz, slots, order == 2 ? 2 : 1);
+    for (int m = 0; m < t * u; ++m) out[m] = tb2_window_host(t, u, D, m);
+    return D;
+}
+
+fdtd_status fdtd_debug_tb2_refine(int slots, const long long* starts, const unsigned long long* cycles, double step,
+                                  long long* out)
+{
+    if (slots < 1 || !starts || !cycles || !out || !(step > 0.0 && step <= 1.0))
+        return fail(FDTD_EINVAL, "invalid argument");
+    std::vector<long long> s(starts, starts + slots + 1);
+    if (s[0] != 0) return fail(FDTD_EINVAL, "starts[0] must be 0");
+    for (int c = 0; c < slots; ++c)
+        if (s[size_t(c) + 1] < s[size_t(c)]) return fail(FDTD_EINVAL, "starts must not decrease");
+    const std::vector<long long> ns = tb2_refined_ranges(s, cycles, step);
+    for (int c = 0; c <= slots; ++c) out[c] = ns[size_t(c)];
+    return FDTD_OK;
+}
+
+}  // extern "C"

@@ -99,6 +99,8 @@ _SIGS = {
     "fdtd_get_tile": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "fdtd_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "fdtd_measure_balance": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fdtd_debug_tb2_order": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "fdtd_debug_tb2_refine": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     "fdtd_destroy_grid": (None, [C.c_void_p]),
     "fdtd_batch_required_bytes": (C.c_size_t, [C.c_int, C.c_int]),
     "fdtd_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p,
@@ -282,6 +284,29 @@ def wall_coefficients(d: fdtd_grid_desc, w: fdtd_wall_desc):
     out = np.zeros((d.ny, d.nx, 2))
     check(lib().fdtd_wall_coefficients(C.byref(d), C.byref(w), out.ctypes.data), "fdtd_wall_coefficients")
     return out[..., 0] + 1j * out[..., 1]
+
+
+def tb2_order(t: int, u: int, nz: int, slots: int, order: int):
+    """Host logic of tile variant 7 (fdtd_debug_tb2_order): (D, window at
+    each flattened position)."""
+    out = np.zeros(t * u, np.int32)
+    D = lib().fdtd_debug_tb2_order(int(t), int(u), int(nz), int(slots), int(order), out.ctypes.data)
+    if D < 0:
+        raise FDTDError(FDTD_EINVAL, "fdtd_debug_tb2_order", "invalid argument")
+    return D, out
+
+
+def tb2_refine(starts, cycles, step: float = 1.0):
+    """One refinement step of the variant-7 ranges on host data
+    (fdtd_debug_tb2_refine): the new starts."""
+    st = np.ascontiguousarray(starts, np.int64)
+    cy = np.ascontiguousarray(cycles, np.uint64)
+    if cy.size + 1 != st.size:
+        raise ValueError("cycles needs one entry per range")
+    out = np.zeros_like(st)
+    check(lib().fdtd_debug_tb2_refine(int(cy.size), st.ctypes.data, cy.ctypes.data, float(step), out.ctypes.data),
+          "fdtd_debug_tb2_refine")
+    return out
 
 
 def source_coefficients(d: fdtd_grid_desc, s: fdtd_annulus_desc):
