@@ -272,9 +272,10 @@ fdtd_status fdtd_set_tile(fdtd_grid* g, int variant, int ty, int lz);
  * wavefront refills there).  Weights in [0, 16] (else EINVAL); defaults 0.25
  * and 0.2.  fdtd_autotune times a few pairs, then refines the fastest pair's
  * ranges on measured times (fdtd_measure_balance), with the windows row by
- * row and interleaved (lz 1 and 2), and times those; it keeps the fastest.  While refined ranges are in use, fdtd_get_balance returns -1
- * for both weights; fdtd_set_balance returns to the weights.  The results do
- * not depend on the balance, only the time does. */
+ * row and interleaved (lz 1 and 2), and times those; it keeps the fastest.
+ * While refined ranges are in use, fdtd_get_balance returns -1 for both
+ * weights; fdtd_set_balance returns to the weights.  The results do not
+ * depend on the balance, only the time does. */
 fdtd_status fdtd_set_balance(fdtd_grid* g, float w_shell, float w_antenna);
 fdtd_status fdtd_get_balance(const fdtd_grid* g, float* w_shell, float* w_antenna);
 /* Refine the CTAs' work ranges of the grid's variant-7 tile on measured
